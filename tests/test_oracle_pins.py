@@ -1,0 +1,331 @@
+"""Pins of the FP64 CPU oracle against facts fixed by the paper and by mathematics.
+
+Each test checks the oracle against something other than itself: closed forms, library Bessel
+functions, brute-force truncated signatures, convergence orders, symmetries and invariants.
+"""
+from math import factorial
+
+import numpy as np
+import pytest
+import scipy.special as sps
+
+import oracle
+from paper_2502_08470_gb300 import workloads as W
+
+SCHEMES = ["fd1", "fd2", "approx", "interp"]
+
+
+def _seg(v0, v1):
+    return np.array([v0, v1], dtype=np.float64)
+
+
+def _i0_series(z, terms=60):
+    """0F1(;1;z) = sum z^n/(n!)^2 (Remark "mbf")."""
+    return sum(z ** n / factorial(n) ** 2 for n in range(terms))
+
+
+# --------------------------------------------------------------------------------------------
+# Polynomial approximation: single-cell and two-cell closed forms (Remark after
+# Definition "def:polyapproxscheme", with p = q = e_0; first-cell formula of Prop. multistepestimate)
+# --------------------------------------------------------------------------------------------
+@pytest.mark.parametrize("N", [2, 3, 4, 6, 9, 12])
+@pytest.mark.parametrize("M", [0.37, -0.81, 1.7, -2.3])
+def test_approx_single_cell_truncated_series(N, M):
+    # one segment each; <dx, dy> = M.  The scheme returns sum_{n<=N} M^n/(n!)^2 exactly.
+    x = _seg([0.0, 0.0], [1.0, 0.0])
+    y = _seg([0.0, 0.0], [M, 0.5])
+    want = sum(M ** n / factorial(n) ** 2 for n in range(N + 1))
+    got = oracle.kernel(x, y, "approx", N)
+    assert got == pytest.approx(want, rel=1e-14, abs=1e-15)
+    # the same with non-unit, non-uniform partitions (only C * ds * dt enters)
+    got2 = oracle.kernel(x, y, "approx", N, s=[0.3, 0.35], t=[-2.0, 5.0])
+    assert got2 == pytest.approx(want, rel=1e-13, abs=1e-14)
+
+
+@pytest.mark.parametrize("N", [2, 3, 5, 8])
+def test_approx_one_by_two_closed_form(N):
+    """x: one segment, y: two segments; M1, M2 the two cell constants.
+
+    Working the scheme's update by hand on these two cells (top edge of cell (0,1) is the
+    binomial convolution, right edge picks up the q-to-p coupling term of the Remark) gives
+      k_hat = 1/2 [ sum_{m<=N} (M1+M2)^m/(m!)^2 + sum_{n<=N} sum_{k<=N} M1^k M2^n/(k! n! (n+k)!) ].
+    """
+    rng = np.random.default_rng(11 + N)
+    dx = rng.normal(size=3)
+    dy1, dy2 = rng.normal(size=3), rng.normal(size=3)
+    x = np.stack([np.zeros(3), dx])
+    y = np.stack([np.zeros(3), dy1, dy1 + dy2])
+    M1, M2 = dx @ dy1, dx @ dy2
+    top = sum((M1 + M2) ** m / factorial(m) ** 2 for m in range(N + 1))
+    right = sum(M1 ** k * M2 ** n / (factorial(k) * factorial(n) * factorial(n + k))
+                for n in range(N + 1) for k in range(N + 1))
+    want = 0.5 * (top + right)
+    assert oracle.kernel(x, y, "approx", N) == pytest.approx(want, rel=1e-13)
+    # swapping the roles of x and y mirrors the grid (symmetry of the update)
+    assert oracle.kernel(y, x, "approx", N) == pytest.approx(want, rel=1e-13)
+
+
+# --------------------------------------------------------------------------------------------
+# Polynomial interpolation: the single-cell solution is 0F1(1; M) = I_0(2 sqrt M)  (Prop.
+# "propinterp" and the Remark after it); checked against scipy's Bessel functions.
+# --------------------------------------------------------------------------------------------
+@pytest.mark.parametrize("N", [2, 4, 7])
+@pytest.mark.parametrize("M", [0.05, 0.9, 3.0, -0.4, -1.4458, -4.0])
+def test_interp_single_cell_bessel(N, M):
+    x = _seg([0.0, 0.0], [1.0, 0.0])
+    y = _seg([0.0, 0.0], [M, -0.3])
+    if M >= 0:
+        want = sps.iv(0, 2.0 * np.sqrt(M))
+    else:
+        want = sps.j0(2.0 * np.sqrt(-M))
+    got = oracle.kernel(x, y, "interp", N)
+    assert got == pytest.approx(want, rel=1e-12, abs=1e-14)
+
+
+# --------------------------------------------------------------------------------------------
+# Linear paths x = s u, y = t v: exact kernel 0F1(;1;<u,v>)  (Remark "mbf")
+# --------------------------------------------------------------------------------------------
+@pytest.mark.parametrize("L", [5, 17, 33])
+def test_linear_paths_converge_to_0f1(L):
+    X = W.linear(6, L, 2, seed=2)
+    U = W.linear_directions(6, 2, seed=2)
+    for a in range(3):
+        x, y = X[2 * a], X[2 * a + 1]
+        z = U[2 * a] @ U[2 * a + 1]
+        want = _i0_series(z)
+        assert oracle.kernel(x, y, "approx", 14) == pytest.approx(want, rel=1e-13)
+        assert oracle.kernel(x, y, "interp", 9) == pytest.approx(want, rel=1e-12)
+        # FD is only O(4^-lambda) accurate (Section 2)
+        assert oracle.kernel(x, y, "fd2", 0, lam=3) == pytest.approx(want, rel=1e-4)
+
+
+# --------------------------------------------------------------------------------------------
+# Brute-force truncated signature kernel (Definition 1.1, Chen's identity) — the paper's own
+# accuracy benchmark at level 21 (Section 4).  First pin the brute force itself.
+# --------------------------------------------------------------------------------------------
+def test_signature_level1_level2_closed_forms():
+    rng = np.random.default_rng(5)
+    x = np.cumsum(rng.normal(size=(5, 3)), axis=0)
+    inc = np.diff(x, axis=0)
+    # level 1: total increment
+    np.testing.assert_allclose(oracle.signature_level(x, 1), x[-1] - x[0], rtol=1e-14, atol=1e-14)
+    # level 2 of a piecewise-linear path: sum_{i<j} d_i (x) d_j + 1/2 sum_i d_i (x) d_i
+    S2 = np.zeros((3, 3))
+    for i in range(len(inc)):
+        for j in range(i + 1, len(inc)):
+            S2 += np.outer(inc[i], inc[j])
+        S2 += 0.5 * np.outer(inc[i], inc[i])
+    np.testing.assert_allclose(oracle.signature_level(x, 2), S2.ravel(), rtol=1e-13, atol=1e-13)
+
+
+def test_signature_one_dimensional_and_tree_like():
+    # d = 1: S_n(x) = (x_T - x_0)^n / n!, so the kernel is sum (DX DY)^n/(n!)^2
+    x = np.array([[0.0], [0.4], [-0.2], [0.9]])
+    y = np.array([[1.0], [0.3], [1.5]])
+    DX, DY = 0.9, 0.5
+    want = sum((DX * DY) ** n / factorial(n) ** 2 for n in range(13))
+    assert oracle.sig_trunc(x, y, 12) == pytest.approx(want, rel=1e-14)
+    # a path followed by its reversal has trivial signature (Chen; the signature characterises
+    # paths up to tree-like equivalence, Section 1)
+    rng = np.random.default_rng(3)
+    p = np.cumsum(rng.normal(size=(4, 2)), axis=0)
+    tree = np.concatenate([p, p[-2::-1]], axis=0)
+    for n in (1, 2, 3, 4):
+        np.testing.assert_allclose(oracle.signature_level(tree, n), 0.0, atol=1e-12)
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_schemes_match_brute_force_signature_kernel(seed):
+    X = W.brownian(2, 7, 2, seed=100 + seed)
+    Y = W.brownian(2, 6, 2, seed=200 + seed)
+    for a in range(2):
+        x, y = X[a], Y[a]
+        truth = oracle.sig_trunc(x, y, 18)
+        assert oracle.kernel(x, y, "approx", 14) == pytest.approx(truth, rel=1e-13)
+        assert oracle.kernel(x, y, "interp", 10) == pytest.approx(truth, rel=1e-13)
+        assert oracle.kernel(x, y, "fd2", lam=4) == pytest.approx(truth, rel=1e-4)
+        assert oracle.kernel(x, y, "fd1", lam=4) == pytest.approx(truth, rel=1e-2)
+
+
+def test_three_dimensional_brute_force():
+    X = W.brownian(1, 5, 3, seed=41)
+    Y = W.brownian(1, 6, 3, seed=42)
+    truth = oracle.sig_trunc(X[0], Y[0], 12)
+    assert oracle.kernel(X[0], Y[0], "approx", 14) == pytest.approx(truth, rel=1e-12)
+    assert oracle.kernel(X[0], Y[0], "interp", 10) == pytest.approx(truth, rel=1e-12)
+
+
+# --------------------------------------------------------------------------------------------
+# Finite differences: closed forms on one cell, and the 2^{-2 lambda} convergence rate
+# (Definition "dyadic scheme"; Theorem 3.5 of Salvi et al. as quoted in Section 2)
+# --------------------------------------------------------------------------------------------
+@pytest.mark.parametrize("m", [0.3, -0.7, 1.9])
+def test_fd_single_cell_closed_forms(m):
+    x = _seg([0.0], [1.0])
+    y = _seg([0.0], [m])
+    # lambda = 0: one update from three unit corners
+    assert oracle.kernel(x, y, "fd1") == pytest.approx(1.0 + m, rel=1e-15)
+    assert oracle.kernel(x, y, "fd2") == pytest.approx(1.0 + m + m * m / 4.0, rel=1e-15)
+
+
+@pytest.mark.parametrize("scheme", ["fd1", "fd2"])
+def test_fd_convergence_rate(scheme):
+    X = W.linear(2, 9, 2, seed=7)
+    U = W.linear_directions(2, 2, seed=7)
+    want = _i0_series(U[0] @ U[1])
+    errs = [abs(oracle.kernel(X[0], X[1], scheme, lam=lam) - want) for lam in range(1, 6)]
+    ratios = [errs[k] / errs[k + 1] for k in range(len(errs) - 1)]
+    for r in ratios[1:]:
+        assert 3.5 < r < 4.5, ratios
+
+
+# --------------------------------------------------------------------------------------------
+# Symmetry, invariants and positive semi-definiteness
+# --------------------------------------------------------------------------------------------
+@pytest.mark.parametrize("scheme", SCHEMES)
+def test_symmetry_in_x_and_y(scheme):
+    X = W.brownian(2, 9, 3, seed=9)
+    Y = W.brownian(1, 12, 3, seed=10)
+    for x in X:
+        a = oracle.kernel(x, Y[0], scheme, 5, lam=1)
+        b = oracle.kernel(Y[0], x, scheme, 5, lam=1)
+        assert a == pytest.approx(b, rel=1e-13)
+
+
+@pytest.mark.parametrize("scheme", SCHEMES)
+def test_invariants(scheme):
+    X = W.brownian(2, 10, 2, seed=12)
+    x, y = X[0], X[1]
+    k = oracle.kernel(x, y, scheme, 6)
+    # constant path: M = 0 everywhere, k = 1 exactly
+    assert oracle.kernel(np.ones((7, 2)) * 0.3, y, scheme, 6) == 1.0
+    # translation invariance
+    assert oracle.kernel(x + 3.0, y - 1.0, scheme, 6) == pytest.approx(k, rel=1e-13)
+    # k(c x, y) = k(x, c y)
+    assert oracle.kernel(2.5 * x, y, scheme, 6) == pytest.approx(oracle.kernel(x, 2.5 * y, scheme, 6),
+                                                                 rel=1e-13)
+    # a path with a single point has trivial signature
+    assert oracle.kernel(x[:1], y, scheme, 6) == 1.0
+
+
+@pytest.mark.parametrize("scheme", ["approx", "interp"])
+def test_time_partition_invariance(scheme):
+    rng = np.random.default_rng(13)
+    X = W.brownian(2, 9, 2, seed=13)
+    k0 = oracle.kernel(X[0], X[1], scheme, 6)
+    s = np.concatenate([[0.0], np.cumsum(rng.uniform(0.2, 2.0, size=8))])
+    t = np.concatenate([[-1.0], -1.0 + np.cumsum(rng.uniform(0.05, 0.5, size=8))])
+    k1 = oracle.kernel(X[0], X[1], scheme, 6, s=s, t=t)
+    assert k1 == pytest.approx(k0, rel=1e-12)
+
+
+def test_tree_like_path_gives_one():
+    rng = np.random.default_rng(14)
+    p = np.cumsum(rng.normal(size=(5, 2)) * 0.4, axis=0)
+    tree = np.concatenate([p, p[-2::-1]], axis=0)
+    y = W.brownian(1, 8, 2, seed=15)[0]
+    assert oracle.kernel(tree, y, "approx", 16) == pytest.approx(1.0, abs=1e-12)
+    assert oracle.kernel(tree, y, "interp", 12) == pytest.approx(1.0, abs=1e-12)
+
+
+def test_gram_is_positive_semidefinite():
+    X = W.brownian(10, 9, 2, seed=16)
+    G = oracle.gram(list(X), list(X), "approx", 12)
+    np.testing.assert_allclose(G, G.T, rtol=1e-13)
+    ev = np.linalg.eigvalsh(0.5 * (G + G.T))
+    assert ev.min() >= -1e-12 * ev.max()
+
+
+# --------------------------------------------------------------------------------------------
+# Global truncation error bound (Theorem "prop:globalte"); the bound is loose, it must hold.
+# --------------------------------------------------------------------------------------------
+@pytest.mark.parametrize("N", [2, 3, 4, 6])
+def test_global_truncation_error_bound(N):
+    X = W.brownian(2, 6, 2, seed=17)
+    x, y = X[0], X[1]
+    truth = oracle.kernel(x, y, "approx", 18)
+    approx = oracle.kernel(x, y, "approx", N)
+    lx, ly = x.shape[0] - 1, y.shape[0] - 1
+    dxs, dys = np.diff(x, axis=0), np.diff(y, axis=0)
+    delta = max(1.0 / lx, 1.0 / ly)
+    K = np.abs(dxs @ dys.T).max() * lx * ly  # sup |C_ij| with uniform partitions
+    n = lx + ly - 1
+    f = np.prod([sps.iv(0, 2.0 * np.sqrt(m * K) * delta) for m in range(n + 1)])
+    xi = (K * delta ** 2) ** (N + 1) / factorial(N + 1) ** 2
+    bound = f * xi * (n ** (N + 2) / (N + 2) + n ** (N + 1))
+    assert abs(truth - approx) <= bound
+
+
+# --------------------------------------------------------------------------------------------
+# Complex-step gradients: central differences, and the single-cell closed form
+# --------------------------------------------------------------------------------------------
+@pytest.mark.parametrize("scheme", SCHEMES)
+def test_complex_step_matches_central_differences(scheme):
+    X = W.brownian(2, 6, 2, seed=18)
+    x, y = X[0], X[1]
+    gx, gy = oracle.grad(x, y, scheme, 5, lam=1)
+    h = 1e-5
+    for side, p, c in [(0, 0, 0), (0, 3, 1), (0, 5, 0), (1, 2, 1), (1, 0, 1)]:
+        a = (x if side == 0 else y).copy()
+        ap, am = a.copy(), a.copy()
+        ap[p, c] += h
+        am[p, c] -= h
+        if side == 0:
+            fd = (oracle.kernel(ap, y, scheme, 5, lam=1) - oracle.kernel(am, y, scheme, 5, lam=1)) / (2 * h)
+            g = gx[p, c]
+        else:
+            fd = (oracle.kernel(x, ap, scheme, 5, lam=1) - oracle.kernel(x, am, scheme, 5, lam=1)) / (2 * h)
+            g = gy[p, c]
+        assert g == pytest.approx(fd, rel=1e-6, abs=1e-9)
+
+
+def test_gradient_single_cell_closed_form():
+    N = 7
+    x = np.array([[0.1, 0.2], [0.5, -0.3]])
+    y = np.array([[0.0, 0.0], [0.9, 0.4]])
+    dxv, dyv = x[1] - x[0], y[1] - y[0]
+    M = dxv @ dyv
+    dk = sum(n * M ** (n - 1) / factorial(n) ** 2 for n in range(1, N + 1))
+    gx, gy = oracle.grad(x, y, "approx", N)
+    np.testing.assert_allclose(gx[1], dk * dyv, rtol=1e-13)
+    np.testing.assert_allclose(gx[0], -dk * dyv, rtol=1e-13)
+    np.testing.assert_allclose(gy[1], dk * dxv, rtol=1e-13)
+
+
+# --------------------------------------------------------------------------------------------
+# MMD^2 (Sections 1 and 4 name it; the estimator is the standard one)
+# --------------------------------------------------------------------------------------------
+def test_mmd2_estimators_and_gradient():
+    A = W.brownian(3, 5, 2, seed=19)
+    B = W.brownian(4, 5, 2, seed=20, drift=0.5, vol=1.2)
+    Kaa = oracle.gram(list(A), list(A), "approx", 6)
+    Kbb = oracle.gram(list(B), list(B), "approx", 6)
+    Kab = oracle.gram(list(A), list(B), "approx", 6)
+    biased = Kaa.mean() + Kbb.mean() - 2 * Kab.mean()
+    assert oracle.mmd2(A, B, "approx", 6) == pytest.approx(biased, rel=1e-13)
+    unb = ((Kaa.sum() - np.trace(Kaa)) / 6 + (Kbb.sum() - np.trace(Kbb)) / 12 - 2 * Kab.mean())
+    assert oracle.mmd2(A, B, "approx", 6, unbiased=True) == pytest.approx(unb, rel=1e-12)
+    # identical sets: biased MMD^2 = 0
+    assert abs(oracle.mmd2(A, A, "approx", 6)) < 1e-14
+    h = 1e-5
+    for side, path, p, c in [(0, 1, 2, 0), (1, 3, 4, 1)]:
+        g = oracle.mmd2_grad_entry(A, B, side, path, p, c, "approx", 6)
+        Ap, Am, Bp, Bm = A.copy(), A.copy(), B.copy(), B.copy()
+        if side == 0:
+            Ap[path, p, c] += h
+            Am[path, p, c] -= h
+        else:
+            Bp[path, p, c] += h
+            Bm[path, p, c] -= h
+        fd = (oracle.mmd2(Ap, Bp, "approx", 6) - oracle.mmd2(Am, Bm, "approx", 6)) / (2 * h)
+        assert g == pytest.approx(fd, rel=1e-6, abs=1e-10)
+
+
+def test_pairs_threads_agree_with_single_calls():
+    X = list(W.brownian(5, 8, 2, seed=21))
+    Y = [W.brownian(1, L, 2, seed=22 + L)[0] for L in (4, 9, 13)]
+    pa = [0, 4, 2, 1]
+    pb = [2, 0, 1, 2]
+    out = oracle.pairs(X, Y, pa, pb, "approx", 6, threads=3)
+    for k in range(4):
+        assert out[k] == oracle.kernel(X[pa[k]], Y[pb[k]], "approx", 6)
