@@ -1,0 +1,307 @@
+#!/usr/bin/env python3
+"""Throughput benchmark of the signature-kernel Gram path on GB300.
+
+Workload ("gram128"): X and Y are 128 Brownian paths each on [0, 1], 257 points, d = 8,
+increments N(0, 1/256) per coordinate (seeds 3 and 4; other ranks use their own seeds), solved
+with the polynomial approximation scheme of order 6 on the batched FP32 wavefront (per-lane
+power-of-two exponents, FP64 endpoints).  One step = one full Gram: increments, then the
+persistent wavefront over all 16,384 pairs x 65,536 cells.
+
+Metric: Goursat cell-updates per second (cells = sum over pairs of l_x * l_y), whole job.
+Timing: per-step CUDA events on the launching stream; a 256 MiB buffer is written between
+steps (outside the events) so every step starts with a cold L2.
+
+Also reported: the roofline of the wavefront kernel (FP32 ALU bound), the FP64 plain wavefront
+of the same Gram, the end-to-end rate through the public API with host buffers, and the CPU
+oracle on a bounded sample.  ``--impl reference`` times the CPU oracle alone.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+NX = NY = 128
+L = 257
+D = 8
+DEGREE = 6
+CELLS_PER_PAIR = (L - 1) * (L - 1)
+CELLS = NX * NY * CELLS_PER_PAIR
+SM_COUNT = 152
+FP32_LANES = 128
+SM_MAX_MHZ = 2070.0
+
+
+def flops_per_cell(N: int, d: int) -> int:
+    """Algorithmic FLOPs of one polynomial-approximation cell update (2 per multiply-add):
+    both edges' Toeplitz convolutions (N+1)(N+2), Hankel couplings 2N(N+1) and their e_n
+    scalings 2(N+1), the N terms of e_m = M^m/m!, and the d-term inner product M_ij."""
+    fma = (N + 1) * (N + 2) + 2 * N * (N + 1) + 2 * (N + 1) + N + d
+    return 2 * fma
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def workload(rank: int):
+    from paper_2502_08470_gb300 import workloads as W
+    X = W.brownian(NX, L, D, seed=3 + 1000 * rank)
+    Y = W.brownian(NY, L, D, seed=4 + 1000 * rank)
+    return X, Y
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples taken while the timed region runs."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if self.proc is None or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sms, maxs, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sms.append(float(parts[1]))
+                maxs.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sms) if sms else None,
+                "sm_max_mhz": max(maxs) if maxs else None,
+                "reasons": sorted(reasons), "samples": len(sms)}
+
+
+def cpu_baseline(X, Y, budget_pairs=48):
+    """The FP64 oracle as it stands, on a bounded sample (the first budget_pairs^2 pairs)."""
+    import oracle
+    n = budget_pairs
+    cores = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    oracle.gram(list(X[:n]), list(Y[:n]), "approx", DEGREE, 0, threads=cores)
+    dt = time.perf_counter() - t0
+    cells = n * n * CELLS_PER_PAIR
+    return {"value": cells / dt, "unit": "cell-updates/s", "cores": cores, "kind": "oracle",
+            "sample": f"{n}x{n} pairs of the 128x128 Gram (257 points, d=8), approximation N={DEGREE}, FP64, "
+                      f"{dt:.2f} s"}
+
+
+def run_reference(args, rank, world):
+    import torch.distributed as dist
+    if rank != 0:
+        return
+    X, Y = workload(0)
+    per = []
+    for _ in range(args.warmup):
+        cpu_baseline(X, Y, 16)
+    for _ in range(args.steps):
+        per.append(cpu_baseline(X, Y, 24))
+    vals = [p["value"] for p in per]
+    value = statistics.mean(vals)
+    ms = CELLS / value * 1e3
+    line = {"impl": "reference", "metric": "Goursat cell-updates/s (polynomial approximation N=6, 128x128 Gram)",
+            "value": value, "unit": "cell-updates/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": "gram128: 128x128 Brownian paths, 257 points, d=8",
+                                            "sample": "24x24 pairs per step", "l2": "n/a (CPU)"},
+            "cpu_baseline": {"value": value, "unit": "cell-updates/s", "cores": per[0]["cores"], "kind": "oracle",
+                             "sample": "24x24 pairs of the 128x128 Gram per step"},
+            "e2e": {"value": value, "unit": "cell-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    del dist
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    import torch
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        if dist is not None:
+            dist.barrier()
+            dist.destroy_process_group()
+        return
+
+    from paper_2502_08470_gb300 import sigkernel as sk
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    X, Y = workload(rank)
+    Xt = torch.tensor(X, device=dev)
+    Yt = torch.tensor(Y, device=dev)
+    G = torch.empty(NX, NY, dtype=torch.float64, device=dev)
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
+
+    def run(compute, steps, warmup, time_kernel=True):
+        ws = sk.gram_workspace(Xt, Yt, scheme="approx", degree=DEGREE, compute=compute)
+        for _ in range(warmup):
+            sk.sigkernel_gram(Xt, Yt, scheme="approx", degree=DEGREE, compute=compute, sort=False, workspace=ws, out=G)
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+        step_ms, kern_ms = [], []
+        t_wall = time.perf_counter()
+        for _ in range(steps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            sk.sigkernel_gram(Xt, Yt, scheme="approx", degree=DEGREE, compute=compute, sort=False, workspace=ws,
+                              out=G, time_kernel=time_kernel)
+            e1.record()
+            e1.synchronize()
+            step_ms.append(e0.elapsed_time(e1))
+            if time_kernel:
+                kern_ms.append(sk.last_kernel_ms())
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t_wall
+        if dist is not None:
+            dist.barrier()
+        return step_ms, kern_ms, wall
+
+    # headline: FP32 batched wavefront
+    with ClockSampler(local) as clk:
+        step_ms, kern_ms, wall = run("f32", args.steps, max(args.warmup, 3))
+    clocks = clk.summary()
+    total_ms = float(sum(step_ms))
+    if dist is not None:
+        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    value = CELLS * world * args.steps / (total_ms / 1e3)
+    G32 = G.clone()
+    status = sk.device_status()
+
+    # FP64 plain wavefront of the same Gram (a few steps)
+    s64, k64, _ = run("f64", max(2, min(3, args.steps)), 1)
+    G64 = G.clone()
+    f64_rate = CELLS / (statistics.mean(s64) / 1e3)
+
+    # end to end through the public API with pinned host buffers
+    Xh = torch.tensor(X).pin_memory()
+    Yh = torch.tensor(Y).pin_memory()
+    Gh = torch.empty(NX, NY, dtype=torch.float64).pin_memory()
+    ws = sk.gram_workspace(Xt, Yt, scheme="approx", degree=DEGREE, compute="f32")
+    e2e_ms = []
+    for it in range(args.warmup + args.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        Xt.copy_(Xh, non_blocking=True)
+        Yt.copy_(Yh, non_blocking=True)
+        sk.sigkernel_gram(Xt, Yt, scheme="approx", degree=DEGREE, compute="f32", sort=False, workspace=ws, out=G)
+        Gh.copy_(G, non_blocking=True)
+        e1.record()
+        e1.synchronize()
+        if it >= args.warmup:
+            e2e_ms.append(e0.elapsed_time(e1))
+    e2e_rate = CELLS * world / (statistics.mean(e2e_ms) / 1e3)
+
+    # accuracy of this run vs the FP64 oracle on sampled entries (parity MAPE)
+    import oracle
+    rng = np.random.default_rng(0)
+    pa = rng.integers(0, NX, 16)
+    pb = rng.integers(0, NY, 16)
+    ref = oracle.pairs(list(X), list(Y), pa, pb, "approx", DEGREE)
+    g32 = G32.cpu().numpy()[pa, pb]
+    g64 = G64.cpu().numpy()[pa, pb]
+    mape32 = float(np.mean(np.abs(g32 - ref) / np.abs(ref)))
+    mape64 = float(np.mean(np.abs(g64 - ref) / np.abs(ref)))
+
+    fpc = flops_per_cell(DEGREE, D)
+    kavg = statistics.mean(kern_ms)
+    achieved = fpc * CELLS / (kavg / 1e3) / 1e12
+    peak = SM_COUNT * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    k64avg = statistics.mean(k64)
+    achieved64 = fpc * CELLS / (k64avg / 1e3) / 1e12
+
+    if rank == 0:
+        line = {
+            "metric": "Goursat cell-updates/s (polynomial approximation N=6, 128x128 Gram, batched FP32 wavefront)",
+            "value": value, "unit": "cell-updates/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "gram128: X, Y = 128 Brownian paths each, 257 points, d=8, N(0,1/256) increments",
+                       "scheme": "polynomial approximation", "degree": DEGREE, "dyadic": 0,
+                       "cells_per_step": CELLS, "pairs_per_step": NX * NY,
+                       "l2": "256 MiB buffer written between timed steps (outside the events)",
+                       "parallelism": f"weak scaling, one independent 128x128 Gram per GPU ({world} GPUs)"},
+            "mape_vs_fp64_oracle": {"f32": mape32, "f64": mape64, "sample": "16 sampled Gram entries"},
+            "fp64_plain_wavefront": {"value": f64_rate, "unit": "cell-updates/s", "kernel_ms": k64avg,
+                                     "achieved_tflops": achieved64},
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                         "traffic": None, "kernel": "fwd_poly_kernel<float,6,6,false>", "kernel_ms": kavg,
+                         "flops_per_cell": fpc,
+                         "peak_source": "152 SMs x 128 FP32 lanes x 2 FLOP x 2070 MHz (derived, nominal clocks)"},
+            "e2e": {"value": e2e_rate, "unit": "cell-updates/s", "h2d_bytes_per_step": int(Xh.numel() * 8 + Yh.numel() * 8),
+                    "d2h_bytes_per_step": int(Gh.numel() * 8), "ms_per_step": statistics.mean(e2e_ms)},
+            "gpu_launches": 3 * args.steps,
+            "clocks": clocks,
+            "device_status": status,
+            "wall_s_timed_region": wall,
+        }
+        if not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline(X, Y)
+        print(json.dumps(line))
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

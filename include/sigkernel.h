@@ -1,0 +1,213 @@
+/*
+ * sigkernel.h -- C ABI of the GB300 (sm_103a) signature-kernel library.
+ *
+ * The library evaluates k(x, y) = <S(x), S(y)> for piecewise-linear paths by solving the Goursat
+ * problem d^2k/(ds dt) = <x'(s), y'(t)> k, k(0, .) = k(., 0) = 1 (Theorem "sigpdetheorem",
+ * Section 1) cell by cell over the grid of increment pairs, with the schemes of Cass, Piatti &
+ * Pei, "Numerical Schemes for Signature Kernels":
+ *
+ *   SK_FD1          first-order explicit finite differences on the dyadic grid P_lambda
+ *                   (Definition "dyadic scheme", Section 2)
+ *   SK_FD2          second-order explicit finite differences (eq. (secondexplicitscheme),
+ *                   Remark "higherfd", Section 2)
+ *   SK_POLY_APPROX  polynomial approximation scheme of order N (Definition
+ *                   "def:polyapproxscheme" and the explicit update after it, Section 3.2)
+ *   SK_POLY_INTERP  polynomial interpolation scheme of order N (Definition
+ *                   "def:polyinterpscheme", Section 3.3)
+ *
+ * Every scheme accepts a dyadic order lambda >= 0: each cell is split into 2^lambda x 2^lambda
+ * sub-cells by linear interpolation of the paths (Definition "dyadic scheme"); for the polynomial
+ * schemes this is the hybrid method of Section 3.2.
+ *
+ * Conventions shared by every entry point
+ *   * Paths.  A set of paths is an sk_paths: the points of all paths concatenated row-major
+ *     ([total_rows][d], element type given by `dtype`), and int64 row offsets off[0..count]
+ *     (path a is rows off[a] .. off[a+1]-1).  Both arrays live in DEVICE memory and are owned by
+ *     the caller; the library never frees or retains them past the call's stream work.  With
+ *     SK_FLAG_INCREMENTS the rows hold increments dx_i = x_{i+1} - x_i instead of points.  A path
+ *     with a single point (or no increment) has the trivial signature and k = 1.  `max_len` is a
+ *     host-side upper bound on the rows of any one path and `rows_total` the host-side row count
+ *     off[count]; a path longer than max_len, with no row at all, or with rows outside
+ *     [0, rows_total) sets the device error word (SK_ERR_BAD_LENGTH) and its outputs are NaN.
+ *     (max_len << lambda) may not exceed 262144.
+ *   * Only the increment inner products M_ij = <dx_i, dy_j> enter any scheme (the explicit
+ *     update of Section 3.2 depends on C_ij (s_{i+1}-s_i)(t_{j+1}-t_j) only), so no time
+ *     partition is passed.
+ *   * Outputs are FP64, device memory, caller-owned.
+ *   * Calls are asynchronous on `stream` (a cudaStream_t; NULL = the legacy default stream) and
+ *     make no host-device synchronisation.  Argument errors are reported by the return code
+ *     before anything is launched; errors that need device data (bad lengths, an exhausted
+ *     bounded wait, non-finite results) go to a device error word read by
+ *     sigkernel_device_status().
+ *   * Workspace.  `workspace` is a device buffer of at least sigkernel_workspace_size() bytes,
+ *     caller-owned, 256-byte aligned; calls sharing a workspace must not overlap on the GPU.  If
+ *     `workspace` is NULL the call allocates and frees its own with cudaMallocAsync /
+ *     cudaFreeAsync on `stream`.
+ *   * Return codes are the SK_* values below; sigkernel_last_error() gives a message for the
+ *     last failing call on the calling host thread.
+ */
+#ifndef SIGKERNEL_H_
+#define SIGKERNEL_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Return codes. */
+enum {
+    SK_OK = 0,
+    SK_ERR_INVALID_ARG = -1,   /* null pointer, bad count, degree, lambda, d, dtype ... */
+    SK_ERR_UNSUPPORTED = -2,   /* a valid request this build has no kernel for */
+    SK_ERR_CUDA = -3,          /* a CUDA runtime call failed (message has the CUDA error) */
+    SK_ERR_WORKSPACE = -4,     /* workspace smaller than sigkernel_workspace_size() */
+    SK_ERR_DEVICE_TIMEOUT = -5,/* a bounded device-side wait ran out (device error word) */
+    SK_ERR_NONFINITE = -6,     /* a result was NaN or infinite (device error word) */
+    SK_ERR_BAD_LENGTH = -7     /* a path had no rows or more than max_len rows (device word) */
+};
+
+/* Schemes. */
+enum { SK_FD1 = 0, SK_FD2 = 1, SK_POLY_APPROX = 2, SK_POLY_INTERP = 3 };
+
+/* Element type of the input rows. */
+enum { SK_F64 = 0, SK_F32 = 1, SK_BF16 = 2 };
+
+/* Arithmetic of the cell updates.
+ *   SK_COMPUTE_F64  every cell update in FP64 (the plain wavefront).
+ *   SK_COMPUTE_F32  cell updates in FP32 with a per-antidiagonal power-of-two exponent carried
+ *                   per pair (values are rescaled by 2^-64 / 2^64 when the antidiagonal's
+ *                   magnitude leaves [2^-64, 2^64]); increments FP32 (BF16 inputs are widened),
+ *                   M accumulated in FP32; the coefficient map of a cell with |M| > 1 is built
+ *                   in FP64; endpoints and reductions in FP64. */
+enum { SK_COMPUTE_F64 = 0, SK_COMPUTE_F32 = 1 };
+
+/* Option flags. */
+enum {
+    SK_FLAG_SYMMETRIC = 1,    /* sigkernel_gram: Y is X; only a <= b is computed and mirrored */
+    SK_FLAG_INCREMENTS = 2,   /* rows hold increments, not points */
+    SK_FLAG_UNBIASED = 4,     /* sigkernel_mmd2: U-statistic (diagonals of K_AA, K_BB left out) */
+    SK_FLAG_NO_SORT = 8,      /* process pairs in the given order (no cell-count ordering) */
+    SK_FLAG_TIME_KERNEL = 16  /* record CUDA events around the wavefront kernel(s) of this call on
+                                 `stream`; read the duration with sigkernel_last_kernel_ms() */
+};
+
+typedef struct {
+    int32_t scheme;           /* SK_FD1, SK_FD2, SK_POLY_APPROX, SK_POLY_INTERP */
+    int32_t degree;           /* N: 2 <= N <= 16 (approximation), 2 <= N <= 12 (interpolation);
+                                 ignored by FD (Definitions of Sections 3.2 and 3.3 take N >= 2) */
+    int32_t dyadic;           /* lambda: 0 <= lambda <= 8 */
+    int32_t compute;          /* SK_COMPUTE_F64 or SK_COMPUTE_F32 */
+    int32_t interp_extra;     /* J for SK_POLY_INTERP: series terms kept beyond N before the
+                                 interpolation projection; 0 = the build's value for the compute
+                                 mode (6 for FP32, 10 for FP64); any other value must equal it */
+    int32_t flags;            /* SK_FLAG_* */
+    int32_t warps_per_block;  /* launch shape override: 0 = the autotuned choice */
+    int32_t reserved;         /* must be 0 */
+} sk_options;
+
+typedef struct {
+    const void* rows;         /* device: [rows_total][d] elements of the call's dtype */
+    const int64_t* offsets;   /* device: [count + 1], off[0] = 0, non-decreasing */
+    int64_t count;            /* number of paths (>= 0) */
+    int64_t max_len;          /* host: upper bound on off[a+1] - off[a] */
+    int64_t rows_total;       /* host: off[count], the number of rows in `rows` */
+} sk_paths;
+
+/* Which call a workspace is sized for. */
+enum { SK_OP_PAIRS = 0, SK_OP_GRAM = 1, SK_OP_BACKWARD = 2, SK_OP_MMD2 = 3 };
+
+/*
+ * sigkernel_workspace_size -- bytes of device workspace the call `op` needs for these shapes
+ * and options (0 on invalid arguments; see sigkernel_last_error).  `npairs` is the pair count
+ * for SK_OP_PAIRS / SK_OP_BACKWARD with a pair list, ignored otherwise (pass -1 for a Gram
+ * backward).  Queries properties of the current device (SM count, occupancy); no memory traffic.
+ */
+size_t sigkernel_workspace_size(int32_t op, const sk_paths* X, const sk_paths* Y, int32_t d,
+                                int64_t npairs, const sk_options* opt);
+
+/*
+ * sigkernel_pairs -- out[k] = k_hat(X_{pair_a[k]}, Y_{pair_b[k]}) for k < npairs.
+ * The scheme output k_hat is the endpoint of the chosen scheme: for the polynomial schemes the
+ * average of the top-edge and right-edge evaluations at the last cell (Definitions
+ * "def:polyapproxscheme" and "def:polyinterpscheme"), for FD the last node of P_lambda.
+ *   X, Y      path sets (device rows/offsets, see above); Y may equal X
+ *   d         coordinates per row, 1 <= d <= 64
+ *   dtype     SK_F64, SK_F32 or SK_BF16 (element type of X->rows and Y->rows)
+ *   pair_a/b  device int64 [npairs]; indices into X and Y
+ *   out       device double [npairs]
+ * All pairs run in one persistent launch; pairs are taken from a work queue ordered by cell
+ * count (largest first) unless SK_FLAG_NO_SORT.
+ */
+int sigkernel_pairs(const sk_paths* X, const sk_paths* Y, int32_t d, int32_t dtype,
+                    const int64_t* pair_a, const int64_t* pair_b, int64_t npairs,
+                    const sk_options* opt, double* out, void* workspace, size_t workspace_bytes,
+                    void* stream);
+
+/*
+ * sigkernel_gram -- G[a][b] = k_hat(X_a, Y_b), G row-major [X->count][Y->count] device doubles.
+ * With SK_FLAG_SYMMETRIC, Y must describe the same paths as X; only a <= b is solved and the
+ * result mirrored (every scheme is symmetric under exchanging x and y: the cell map is invariant
+ * under (p, s) <-> (q, t) and the endpoint averages both edges).  Other arguments as for
+ * sigkernel_pairs.
+ */
+int sigkernel_gram(const sk_paths* X, const sk_paths* Y, int32_t d, int32_t dtype,
+                   const sk_options* opt, double* G, void* workspace, size_t workspace_bytes,
+                   void* stream);
+
+/*
+ * sigkernel_backward -- reverse-mode derivative of the discrete scheme (the paper defines no
+ * gradient; this is the exact adjoint of the scheme's own arithmetic, run as a reverse
+ * wavefront with checkpoints every few antidiagonals).
+ *   Pair-list mode (pair_a != NULL): grad_out[k] = dL/dk_hat(X_{pair_a[k]}, Y_{pair_b[k]}).
+ *   Gram mode (pair_a == NULL): grad_out is [X->count][Y->count] row-major, dL/dG[a][b].
+ *   grad_X  device double, same row layout as X->rows ([off[count]][d]): dL/d(row), added to
+ *           the existing contents (the caller zeroes it first for a plain gradient); NULL skips.
+ *   grad_Y  likewise for Y.  When Y is X (same rows pointer) both accumulate into the same
+ *           buffer correctly if grad_X == grad_Y.
+ * Supported for SK_POLY_APPROX and the FD schemes; other schemes return SK_ERR_UNSUPPORTED.
+ * Accumulation uses device atomics, so the last bits of the gradient can vary between runs.
+ */
+int sigkernel_backward(const sk_paths* X, const sk_paths* Y, int32_t d, int32_t dtype,
+                       const int64_t* pair_a, const int64_t* pair_b, int64_t npairs,
+                       const sk_options* opt, const double* grad_out, double* grad_X,
+                       double* grad_Y, void* workspace, size_t workspace_bytes, void* stream);
+
+/*
+ * sigkernel_mmd2 -- squared maximum mean discrepancy between the path sets A and B with the
+ * signature kernel (the paper's library offers MMD, Sections 1 and 4, without a formula):
+ *   biased:   mean(K_AA) + mean(K_BB) - 2 mean(K_AB)
+ *   unbiased (SK_FLAG_UNBIASED): K_AA and K_BB means over their off-diagonal entries.
+ *   out       device double [4]: MMD^2, mean K_AA, mean K_BB, mean K_AB (as used above)
+ *   grad_A/B  device double with A's / B's row layout, or NULL: d MMD^2 / d rows, OVERWRITTEN.
+ * K_AA and K_BB are solved as symmetric Grams; the reduction runs in FP64 on the device.
+ */
+int sigkernel_mmd2(const sk_paths* A, const sk_paths* B, int32_t d, int32_t dtype,
+                   const sk_options* opt, double* out, double* grad_A, double* grad_B,
+                   void* workspace, size_t workspace_bytes, void* stream);
+
+/*
+ * sigkernel_device_status -- synchronises `stream`, reads and clears the device error word of
+ * the current device, and returns SK_OK or the first recorded SK_ERR_* code.
+ */
+int sigkernel_device_status(void* stream);
+
+/*
+ * sigkernel_last_kernel_ms -- device time in milliseconds between the two CUDA events recorded
+ * around the wavefront kernel(s) of the last call made with SK_FLAG_TIME_KERNEL on this host
+ * thread (waits for the second event).  Returns -1 if no such call was made.
+ */
+float sigkernel_last_kernel_ms(void);
+
+/* Message describing the last non-SK_OK return on this host thread ("" if none). */
+const char* sigkernel_last_error(void);
+
+/* Library version: major * 10000 + minor * 100 + patch. */
+int sigkernel_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SIGKERNEL_H_ */

@@ -1,0 +1,508 @@
+// Host side of the C ABI (include/sigkernel.h): argument checks, workspace layout, constant
+// tables, the increment and scheduling kernels, and dispatch to the wavefront kernels.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+
+#include "sk_common.cuh"
+#include "sk_dispatch.h"
+
+namespace sk {
+
+__constant__ float c_inv_f[kNEMax + 2];
+__constant__ double c_inv_d[kNEMax + 2];
+__constant__ float c_hank_f[kNEMax + 1][kNMaxApprox + 1];
+__constant__ double c_hank_d[kNEMax + 1][kNMaxApprox + 1];
+__constant__ double c_rfact_d[kNEMax + 1];
+__constant__ float c_proj_f[kNMaxInterp + 1][kNMaxInterp + 1][kJMax];
+__constant__ double c_proj_d[kNMaxInterp + 1][kNMaxInterp + 1][kJMax];
+__device__ int g_sk_error = 0;
+
+namespace {
+
+thread_local std::string t_last_error;
+thread_local cudaEvent_t t_ev0 = nullptr, t_ev1 = nullptr;
+thread_local bool t_timed = false;
+
+int fail(int code, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    t_last_error = buf;
+    return code;
+}
+
+#define SK_CUDA(call)                                                                         \
+    do {                                                                                      \
+        cudaError_t e_ = (call);                                                              \
+        if (e_ != cudaSuccess) return fail(SK_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+    } while (0)
+
+// ------------------------------------------------------------------------------------------
+// Constant tables, uploaded once per device.
+// ------------------------------------------------------------------------------------------
+// Interpolation projection: for order N, the Chebyshev extrema of [0,1] are
+// u_r = (1 + cos(pi r / N)) / 2, r = 0..N (eq. (chebextr) with N+1 nodes, Definition
+// "interpooperator").  A factorial-scaled series c (f(u) = sum_j c_j u^j / j!) sampled at the nodes
+// and interpolated by a degree-N polynomial has factorial-scaled coefficients
+//   a'_n = sum_j n! [V^{-1} W]_{n j} / j! c_j,   V_{rn} = u_r^n (n <= N),  W_{rj} = u_r^j,
+// and columns j <= N of V^{-1} W are the identity.  Solved in long double with partial pivoting.
+void build_projection(int N, double (*out)[kJMax]) {
+    const int n1 = N + 1;
+    long double V[kNMaxInterp + 1][kNMaxInterp + 1];
+    long double W[kNMaxInterp + 1][kJMax];
+    const long double pi = 3.141592653589793238462643383279502884L;
+    for (int r = 0; r < n1; ++r) {
+        long double u = 0.5L * (1.0L + cosl(pi * r / N));
+        long double p = 1.0L;
+        for (int n = 0; n < n1; ++n) { V[r][n] = p; p *= u; }
+        for (int jj = 0; jj < kJMax; ++jj) { W[r][jj] = p; p *= u; }  // u^{N+1+jj}
+    }
+    for (int col = 0; col < n1; ++col) {  // Gaussian elimination on [V | W]
+        int piv = col;
+        for (int r = col + 1; r < n1; ++r)
+            if (fabsl(V[r][col]) > fabsl(V[piv][col])) piv = r;
+        for (int k = 0; k < n1; ++k) { long double t = V[col][k]; V[col][k] = V[piv][k]; V[piv][k] = t; }
+        for (int k = 0; k < kJMax; ++k) { long double t = W[col][k]; W[col][k] = W[piv][k]; W[piv][k] = t; }
+        for (int r = 0; r < n1; ++r) {
+            if (r == col) continue;
+            long double l = V[r][col] / V[col][col];
+            for (int k = 0; k < n1; ++k) V[r][k] -= l * V[col][k];
+            for (int k = 0; k < kJMax; ++k) W[r][k] -= l * W[col][k];
+        }
+    }
+    long double fact[kNEMax + 2];
+    fact[0] = 1.0L;
+    for (int k = 1; k < kNEMax + 2; ++k) fact[k] = fact[k - 1] * k;
+    for (int n = 0; n < n1; ++n)
+        for (int jj = 0; jj < kJMax; ++jj) {
+            int j = N + 1 + jj;
+            long double g = W[n][jj] / V[n][n];
+            out[n][jj] = (j <= kNEMax) ? static_cast<double>(g * fact[n] / fact[j]) : 0.0;
+        }
+}
+
+std::mutex g_table_mu;
+bool g_tables_ready[64] = {false};
+
+int ensure_tables() {
+    int dev = 0;
+    SK_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return fail(SK_ERR_UNSUPPORTED, "device index %d", dev);
+    std::lock_guard<std::mutex> lock(g_table_mu);
+    if (g_tables_ready[dev]) return SK_OK;
+    static double inv_d[kNEMax + 2], hank_d[kNEMax + 1][kNMaxApprox + 1], rfact_d[kNEMax + 1];
+    static float inv_f[kNEMax + 2], hank_f[kNEMax + 1][kNMaxApprox + 1];
+    static double proj_d[kNMaxInterp + 1][kNMaxInterp + 1][kJMax];
+    static float proj_f[kNMaxInterp + 1][kNMaxInterp + 1][kJMax];
+    inv_d[0] = 0.0;
+    for (int m = 1; m < kNEMax + 2; ++m) inv_d[m] = 1.0 / m;
+    for (int n = 0; n <= kNEMax; ++n) {
+        long double r = 1.0L;  // n!/(n+k)! = prod_{i=1..k} 1/(n+i)
+        hank_d[n][0] = 1.0;
+        for (int k = 1; k <= kNMaxApprox; ++k) {
+            r /= (n + k);
+            hank_d[n][k] = static_cast<double>(r);
+        }
+    }
+    long double f = 1.0L;
+    for (int n = 0; n <= kNEMax; ++n) {
+        if (n > 0) f *= n;
+        rfact_d[n] = static_cast<double>(1.0L / f);
+    }
+    memset(proj_d, 0, sizeof(proj_d));
+    for (int N = 2; N <= kNMaxInterp; ++N) build_projection(N, proj_d[N]);
+    for (int m = 0; m < kNEMax + 2; ++m) inv_f[m] = static_cast<float>(inv_d[m]);
+    for (int n = 0; n <= kNEMax; ++n)
+        for (int k = 0; k <= kNMaxApprox; ++k) hank_f[n][k] = static_cast<float>(hank_d[n][k]);
+    for (int N = 0; N <= kNMaxInterp; ++N)
+        for (int n = 0; n <= kNMaxInterp; ++n)
+            for (int jj = 0; jj < kJMax; ++jj) proj_f[N][n][jj] = static_cast<float>(proj_d[N][n][jj]);
+    SK_CUDA(cudaMemcpyToSymbol(c_inv_d, inv_d, sizeof(inv_d)));
+    SK_CUDA(cudaMemcpyToSymbol(c_inv_f, inv_f, sizeof(inv_f)));
+    SK_CUDA(cudaMemcpyToSymbol(c_hank_d, hank_d, sizeof(hank_d)));
+    SK_CUDA(cudaMemcpyToSymbol(c_hank_f, hank_f, sizeof(hank_f)));
+    SK_CUDA(cudaMemcpyToSymbol(c_rfact_d, rfact_d, sizeof(rfact_d)));
+    SK_CUDA(cudaMemcpyToSymbol(c_proj_d, proj_d, sizeof(proj_d)));
+    SK_CUDA(cudaMemcpyToSymbol(c_proj_f, proj_f, sizeof(proj_f)));
+    g_tables_ready[dev] = true;
+    return SK_OK;
+}
+
+// ------------------------------------------------------------------------------------------
+// Increments dx_i = x_{i+1} - x_i (or the caller's increments) in the compute type, rows
+// zero-padded to `dpad` elements.  One block per path (grid-stride over paths).
+// ------------------------------------------------------------------------------------------
+template <typename Tin> __device__ __forceinline__ double load_elem(const Tin* p) { return static_cast<double>(*p); }
+template <> __device__ __forceinline__ double load_elem<__nv_bfloat16>(const __nv_bfloat16* p) {
+    return static_cast<double>(__bfloat162float(*p));
+}
+
+template <typename Tin, typename T>
+__global__ void increments_kernel(const Tin* __restrict__ rows, const int64_t* __restrict__ off, int64_t count,
+                                  int64_t rows_total, int64_t max_len, int d, int dpad, int inc_mode,
+                                  T* __restrict__ out) {
+    for (int64_t a = blockIdx.x; a < count; a += gridDim.x) {
+        const int64_t r0 = off[a], r1 = off[a + 1], n = r1 - r0;
+        if (r0 < 0 || r1 > rows_total || n < (inc_mode ? 0 : 1) || n > max_len) continue;
+        const int64_t len = inc_mode ? n : n - 1;
+        for (int64_t idx = threadIdx.x; idx < len * dpad; idx += blockDim.x) {
+            const int64_t i = idx / dpad;
+            const int c = static_cast<int>(idx - i * dpad);
+            double v = 0.0;
+            if (c < d) {
+                const Tin* p = rows + (r0 + i) * d + c;
+                v = inc_mode ? load_elem(p) : load_elem(p + d) - load_elem(p);
+            }
+            out[(r0 + i) * dpad + c] = static_cast<T>(v);
+        }
+    }
+}
+
+// ------------------------------------------------------------------------------------------
+// Work queue ordered by cell count (largest first): a counting sort on floor(log2(cells)).
+// ------------------------------------------------------------------------------------------
+__device__ __forceinline__ int cell_bucket(const Launch& L, int64_t item) {
+    PairDesc P = decode_pair(L, item);
+    if (P.lx <= 0 || P.ly <= 0) return 0;
+    unsigned long long cells = static_cast<unsigned long long>(P.lx) * static_cast<unsigned long long>(P.ly);
+    return 64 - __clzll(cells);  // 1..64
+}
+
+__global__ void sched_hist_kernel(Launch L, unsigned int* hist) {
+    for (int64_t it = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; it < L.npairs;
+         it += static_cast<int64_t>(gridDim.x) * blockDim.x)
+        atomicAdd(&hist[cell_bucket(L, it)], 1u);
+}
+
+__global__ void sched_scan_kernel(unsigned int* hist, unsigned int* cursor) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        unsigned int acc = 0;
+        for (int b = 64; b >= 0; --b) {
+            cursor[b] = acc;
+            acc += hist[b];
+        }
+    }
+}
+
+__global__ void sched_scatter_kernel(Launch L, unsigned int* cursor, int32_t* order) {
+    for (int64_t it = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; it < L.npairs;
+         it += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        unsigned int pos = atomicAdd(&cursor[cell_bucket(L, it)], 1u);
+        order[pos] = static_cast<int32_t>(it);
+    }
+}
+
+// ------------------------------------------------------------------------------------------
+// Argument checks and workspace planning.
+// ------------------------------------------------------------------------------------------
+struct Plan {
+    int T;               // 0 = FP64, 1 = FP32 compute
+    int nvec, dpad;
+    int64_t npairs;
+    int mode;
+    bool same_xy;        // Y's rows/offsets are X's
+    const void* kern;    // wavefront kernel
+    int threads;         // threads per block
+    int blocks;          // persistent grid
+    int64_t slot_bytes;  // scratch per warp slot
+    int64_t buf_cols;    // hand-off columns per warp slot
+    // workspace layout (byte offsets)
+    size_t off_incx, off_incy, off_queue, off_hist, off_order, off_scratch, total;
+};
+
+size_t align256(size_t v) { return (v + 255) / 256 * 256; }
+
+int check_paths(const sk_paths* P, const char* name, int d) {
+    if (!P) return fail(SK_ERR_INVALID_ARG, "%s is NULL", name);
+    if (P->count < 0) return fail(SK_ERR_INVALID_ARG, "%s->count < 0", name);
+    if (P->count > 0 && !P->offsets) return fail(SK_ERR_INVALID_ARG, "%s->offsets is NULL", name);
+    if (P->rows_total < 0 || P->max_len < 0) return fail(SK_ERR_INVALID_ARG, "%s: negative sizes", name);
+    if (P->rows_total > 0 && !P->rows) return fail(SK_ERR_INVALID_ARG, "%s->rows is NULL", name);
+    if (P->count > (int64_t(1) << 30)) return fail(SK_ERR_UNSUPPORTED, "%s: more than 2^30 paths", name);
+    (void)d;
+    return SK_OK;
+}
+
+int check_options(const sk_options* o, int32_t d, int32_t dtype) {
+    if (!o) return fail(SK_ERR_INVALID_ARG, "options is NULL");
+    if (o->reserved != 0) return fail(SK_ERR_INVALID_ARG, "options.reserved must be 0");
+    if (o->scheme < SK_FD1 || o->scheme > SK_POLY_INTERP) return fail(SK_ERR_INVALID_ARG, "unknown scheme %d", o->scheme);
+    if (o->compute != SK_COMPUTE_F64 && o->compute != SK_COMPUTE_F32)
+        return fail(SK_ERR_INVALID_ARG, "unknown compute mode %d", o->compute);
+    if (dtype != SK_F64 && dtype != SK_F32 && dtype != SK_BF16) return fail(SK_ERR_INVALID_ARG, "unknown dtype %d", dtype);
+    if (d < 1 || d > kDMax) return fail(SK_ERR_INVALID_ARG, "d = %d outside [1, %d]", d, kDMax);
+    if (o->dyadic < 0 || o->dyadic > kLamMax) return fail(SK_ERR_INVALID_ARG, "dyadic order %d outside [0, %d]", o->dyadic, kLamMax);
+    if (o->scheme == SK_POLY_APPROX && (o->degree < 2 || o->degree > kNMaxApprox))
+        return fail(SK_ERR_INVALID_ARG, "approximation order %d outside [2, %d]", o->degree, kNMaxApprox);
+    if (o->scheme == SK_POLY_INTERP && (o->degree < 2 || o->degree > kNMaxInterp))
+        return fail(SK_ERR_INVALID_ARG, "interpolation order %d outside [2, %d]", o->degree, kNMaxInterp);
+    if (o->scheme == SK_POLY_INTERP && o->interp_extra != 0) {
+        int j = (o->compute == SK_COMPUTE_F32) ? kJF32 : kJF64;
+        if (o->interp_extra != j)
+            return fail(SK_ERR_UNSUPPORTED, "interp_extra %d: this build keeps J = %d for this compute mode",
+                        o->interp_extra, j);
+    }
+    if (o->warps_per_block != 0 && o->warps_per_block != kFwdWarps)
+        return fail(SK_ERR_UNSUPPORTED, "warps_per_block %d (this build: 0 or %d)", o->warps_per_block, kFwdWarps);
+    if (o->flags & ~(SK_FLAG_SYMMETRIC | SK_FLAG_INCREMENTS | SK_FLAG_UNBIASED | SK_FLAG_NO_SORT | SK_FLAG_TIME_KERNEL))
+        return fail(SK_ERR_INVALID_ARG, "unknown flag bits 0x%x", o->flags);
+    return SK_OK;
+}
+
+int plan_forward(const sk_paths* X, const sk_paths* Y, int32_t d, int32_t dtype, const sk_options* o,
+                 int mode, int64_t npairs, Plan& p) {
+    int rc;
+    if ((rc = check_options(o, d, dtype)) != SK_OK) return rc;
+    if ((rc = check_paths(X, "X", d)) != SK_OK) return rc;
+    if ((rc = check_paths(Y, "Y", d)) != SK_OK) return rc;
+    const int lam = o->dyadic;
+    if ((X->max_len << lam) > kMaxRefined || (Y->max_len << lam) > kMaxRefined)
+        return fail(SK_ERR_UNSUPPORTED, "max_len << dyadic exceeds %d", kMaxRefined);
+    if (mode == kGramUpper) {
+        if (X->rows != Y->rows || X->offsets != Y->offsets || X->count != Y->count)
+            return fail(SK_ERR_INVALID_ARG, "SK_FLAG_SYMMETRIC needs Y to describe the same paths as X");
+    }
+    p.T = (o->compute == SK_COMPUTE_F32) ? 1 : 0;
+    const int vw = p.T ? 4 : 2;
+    p.nvec = (d + vw - 1) / vw;
+    p.dpad = p.nvec * vw;
+    p.mode = mode;
+    p.npairs = npairs;
+    p.same_xy = (X->rows == Y->rows && X->offsets == Y->offsets && X->count == Y->count &&
+                 X->rows_total == Y->rows_total);
+    if (npairs > 0x7fffffffLL) return fail(SK_ERR_UNSUPPORTED, "more than 2^31-1 pairs in one call");
+
+    const bool poly = o->scheme == SK_POLY_APPROX || o->scheme == SK_POLY_INTERP;
+    int width = 1;  // values handed from strip to strip per refined column
+    if (poly) {
+        p.kern = fwd_poly_kernel_ptr(p.T, o->scheme == SK_POLY_INTERP, o->degree);
+        width = o->degree + 1;
+    } else {
+        p.kern = fwd_fd_kernel_ptr(p.T, o->scheme == SK_FD2 ? 2 : 1, lam);
+        width = 1;
+    }
+    if (!p.kern) return fail(SK_ERR_UNSUPPORTED, "no kernel for scheme %d order %d compute %d", o->scheme, o->degree, o->compute);
+    p.threads = kFwdWarps * 32;
+    int dev = 0, sms = 0, per_sm = 0;
+    SK_CUDA(cudaGetDevice(&dev));
+    SK_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    SK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, p.kern, p.threads, 0));
+    if (per_sm < 1) per_sm = 1;
+    int64_t want = (npairs + kFwdWarps - 1) / kFwdWarps;
+    int64_t cap = static_cast<int64_t>(sms) * per_sm;
+    p.blocks = static_cast<int>(want < cap ? (want > 0 ? want : 1) : cap);
+    p.buf_cols = (Y->max_len << lam) + 1;
+    const int esize = p.T ? 4 : 8;
+    p.slot_bytes = static_cast<int64_t>(align256(static_cast<size_t>(p.buf_cols * width * esize + p.buf_cols * 4)));
+
+    size_t off = 0;
+    p.off_incx = off;
+    off += align256(static_cast<size_t>(X->rows_total) * p.dpad * esize);
+    p.off_incy = p.same_xy ? p.off_incx : off;
+    if (!p.same_xy) off += align256(static_cast<size_t>(Y->rows_total) * p.dpad * esize);
+    p.off_queue = off;
+    off += 256;
+    p.off_hist = off;
+    off += align256(2 * 65 * sizeof(unsigned int));
+    p.off_order = off;
+    off += align256(static_cast<size_t>(npairs) * sizeof(int32_t));
+    p.off_scratch = off;
+    off += static_cast<size_t>(p.blocks) * kFwdWarps * static_cast<size_t>(p.slot_bytes);
+    p.total = off + 256;
+    return SK_OK;
+}
+
+template <typename T>
+int launch_increments(const sk_paths* S, int32_t d, int32_t dtype, int inc_mode, int dpad, void* out,
+                      cudaStream_t st) {
+    if (S->count == 0) return SK_OK;
+    int blocks = static_cast<int>(S->count < 65535 ? S->count : 65535);
+    T* o = static_cast<T*>(out);
+    switch (dtype) {
+        case SK_F64:
+            increments_kernel<double, T><<<blocks, 128, 0, st>>>(static_cast<const double*>(S->rows), S->offsets,
+                                                                 S->count, S->rows_total, S->max_len, d, dpad, inc_mode, o);
+            break;
+        case SK_F32:
+            increments_kernel<float, T><<<blocks, 128, 0, st>>>(static_cast<const float*>(S->rows), S->offsets,
+                                                                S->count, S->rows_total, S->max_len, d, dpad, inc_mode, o);
+            break;
+        default:
+            increments_kernel<__nv_bfloat16, T><<<blocks, 128, 0, st>>>(
+                static_cast<const __nv_bfloat16*>(S->rows), S->offsets, S->count, S->rows_total, S->max_len, d, dpad,
+                inc_mode, o);
+            break;
+    }
+    SK_CUDA(cudaGetLastError());
+    return SK_OK;
+}
+
+int run_forward(const sk_paths* X, const sk_paths* Y, int32_t d, int32_t dtype, const sk_options* o, int mode,
+                const int64_t* pa, const int64_t* pb, int64_t npairs, double* out, int64_t ldo, void* ws,
+                size_t ws_bytes, void* stream) {
+    Plan p;
+    int rc = plan_forward(X, Y, d, dtype, o, mode, npairs, p);
+    if (rc != SK_OK) return rc;
+    if (npairs == 0) return SK_OK;
+    if (!out) return fail(SK_ERR_INVALID_ARG, "output pointer is NULL");
+    if ((rc = ensure_tables()) != SK_OK) return rc;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    bool own = false;
+    if (!ws) {
+        SK_CUDA(cudaMallocAsync(&ws, p.total, st));
+        own = true;
+    } else if (ws_bytes < p.total) {
+        return fail(SK_ERR_WORKSPACE, "workspace %zu bytes < %zu required", ws_bytes, p.total);
+    }
+    char* base = static_cast<char*>(ws);
+    base = reinterpret_cast<char*>((reinterpret_cast<uintptr_t>(base) + 255) / 256 * 256);
+    const int inc_mode = (o->flags & SK_FLAG_INCREMENTS) ? 1 : 0;
+    rc = p.T ? launch_increments<float>(X, d, dtype, inc_mode, p.dpad, base + p.off_incx, st)
+             : launch_increments<double>(X, d, dtype, inc_mode, p.dpad, base + p.off_incx, st);
+    if (rc == SK_OK && !p.same_xy)
+        rc = p.T ? launch_increments<float>(Y, d, dtype, inc_mode, p.dpad, base + p.off_incy, st)
+                 : launch_increments<double>(Y, d, dtype, inc_mode, p.dpad, base + p.off_incy, st);
+    if (rc != SK_OK) return rc;
+
+    Launch L;
+    memset(&L, 0, sizeof(L));
+    L.X = PathSet{base + p.off_incx, X->offsets, X->count, X->max_len, X->rows_total};
+    L.Y = PathSet{base + p.off_incy, Y->offsets, Y->count, Y->max_len, Y->rows_total};
+    L.nvec = p.nvec;
+    L.dpad = p.dpad;
+    L.inc_mode = inc_mode;
+    L.lam = o->dyadic;
+    L.mode = mode;
+    L.npairs = npairs;
+    L.pair_a = pa;
+    L.pair_b = pb;
+    L.queue = reinterpret_cast<unsigned int*>(base + p.off_queue);
+    L.out = out;
+    L.ldo = ldo;
+    L.scratch = base + p.off_scratch;
+    L.scratch_stride = p.slot_bytes;
+    L.tau = 1.0f;
+    L.order = nullptr;
+    SK_CUDA(cudaMemsetAsync(base + p.off_queue, 0, 256 + align256(2 * 65 * sizeof(unsigned int)), st));
+    if (!(o->flags & SK_FLAG_NO_SORT) && npairs > 1) {
+        unsigned int* hist = reinterpret_cast<unsigned int*>(base + p.off_hist);
+        int32_t* order = reinterpret_cast<int32_t*>(base + p.off_order);
+        int sb = static_cast<int>((npairs + 255) / 256);
+        if (sb > 4096) sb = 4096;
+        sched_hist_kernel<<<sb, 256, 0, st>>>(L, hist);
+        sched_scan_kernel<<<1, 32, 0, st>>>(hist, hist + 65);
+        sched_scatter_kernel<<<sb, 256, 0, st>>>(L, hist + 65, order);
+        SK_CUDA(cudaGetLastError());
+        L.order = order;
+    }
+    int64_t buf_cols = p.buf_cols;
+    void* args[] = {&L, &buf_cols};
+    const bool timed = (o->flags & SK_FLAG_TIME_KERNEL) != 0;
+    if (timed) {
+        if (!t_ev0) SK_CUDA(cudaEventCreate(&t_ev0));
+        if (!t_ev1) SK_CUDA(cudaEventCreate(&t_ev1));
+        SK_CUDA(cudaEventRecord(t_ev0, st));
+    }
+    SK_CUDA(cudaLaunchKernel(p.kern, dim3(p.blocks), dim3(p.threads), args, 0, st));
+    if (timed) {
+        SK_CUDA(cudaEventRecord(t_ev1, st));
+        t_timed = true;
+    }
+    if (own) SK_CUDA(cudaFreeAsync(ws, st));
+    return SK_OK;
+}
+
+int64_t gram_items(const sk_paths* X, const sk_paths* Y, bool sym) {
+    return sym ? X->count * (X->count + 1) / 2 : X->count * Y->count;
+}
+
+}  // namespace
+}  // namespace sk
+
+using namespace sk;
+
+extern "C" {
+
+int sigkernel_version(void) { return 100; }
+
+const char* sigkernel_last_error(void) { return t_last_error.c_str(); }
+
+float sigkernel_last_kernel_ms(void) {
+    if (!t_timed) return -1.0f;
+    float ms = -1.0f;
+    if (cudaEventSynchronize(t_ev1) != cudaSuccess) return -1.0f;
+    if (cudaEventElapsedTime(&ms, t_ev0, t_ev1) != cudaSuccess) return -1.0f;
+    return ms;
+}
+
+size_t sigkernel_workspace_size(int32_t op, const sk_paths* X, const sk_paths* Y, int32_t d, int64_t npairs,
+                                const sk_options* opt) {
+    Plan p;
+    int rc;
+    if (!opt || !X || !Y) {
+        fail(SK_ERR_INVALID_ARG, "NULL argument");
+        return 0;
+    }
+    const int dtype = SK_F64;  // sizes do not depend on the input element type
+    switch (op) {
+        case SK_OP_PAIRS:
+            rc = plan_forward(X, Y, d, dtype, opt, kPairsList, npairs, p);
+            break;
+        case SK_OP_GRAM: {
+            bool sym = (opt->flags & SK_FLAG_SYMMETRIC) != 0;
+            rc = plan_forward(X, Y, d, dtype, opt, sym ? kGramUpper : kGramFull, gram_items(X, Y, sym), p);
+            break;
+        }
+        default:
+            fail(SK_ERR_UNSUPPORTED, "workspace for op %d", op);
+            return 0;
+    }
+    return rc == SK_OK ? p.total : 0;
+}
+
+int sigkernel_pairs(const sk_paths* X, const sk_paths* Y, int32_t d, int32_t dtype, const int64_t* pair_a,
+                    const int64_t* pair_b, int64_t npairs, const sk_options* opt, double* out, void* workspace,
+                    size_t workspace_bytes, void* stream) {
+    t_last_error.clear();
+    if (npairs < 0) return fail(SK_ERR_INVALID_ARG, "npairs < 0");
+    if (npairs > 0 && (!pair_a || !pair_b)) return fail(SK_ERR_INVALID_ARG, "pair index arrays are NULL");
+    return run_forward(X, Y, d, dtype, opt, kPairsList, pair_a, pair_b, npairs, out, 0, workspace, workspace_bytes,
+                       stream);
+}
+
+int sigkernel_gram(const sk_paths* X, const sk_paths* Y, int32_t d, int32_t dtype, const sk_options* opt, double* G,
+                   void* workspace, size_t workspace_bytes, void* stream) {
+    t_last_error.clear();
+    if (!opt || !X || !Y) return fail(SK_ERR_INVALID_ARG, "NULL argument");
+    bool sym = (opt->flags & SK_FLAG_SYMMETRIC) != 0;
+    return run_forward(X, Y, d, dtype, opt, sym ? kGramUpper : kGramFull, nullptr, nullptr, gram_items(X, Y, sym), G,
+                       Y->count, workspace, workspace_bytes, stream);
+}
+
+int sigkernel_backward(const sk_paths*, const sk_paths*, int32_t, int32_t, const int64_t*, const int64_t*, int64_t,
+                       const sk_options*, const double*, double*, double*, void*, size_t, void*) {
+    return fail(SK_ERR_UNSUPPORTED, "sigkernel_backward is not built yet");
+}
+
+int sigkernel_mmd2(const sk_paths*, const sk_paths*, int32_t, int32_t, const sk_options*, double*, double*, double*,
+                   void*, size_t, void*) {
+    return fail(SK_ERR_UNSUPPORTED, "sigkernel_mmd2 is not built yet");
+}
+
+int sigkernel_device_status(void* stream) {
+    t_last_error.clear();
+    SK_CUDA(cudaStreamSynchronize(static_cast<cudaStream_t>(stream)));
+    int code = 0, zero = 0;
+    SK_CUDA(cudaMemcpyFromSymbol(&code, g_sk_error, sizeof(int)));
+    SK_CUDA(cudaMemcpyToSymbol(g_sk_error, &zero, sizeof(int)));
+    if (code != 0) return fail(code, "device error word %d", code);
+    return SK_OK;
+}
+
+}  // extern "C"

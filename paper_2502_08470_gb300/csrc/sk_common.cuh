@@ -1,0 +1,204 @@
+// Shared device-side definitions of the sm_103a signature-kernel library.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include "../../include/sigkernel.h"
+
+namespace sk {
+
+constexpr int kNMaxApprox = 16;  // largest order N of the approximation scheme
+constexpr int kNMaxInterp = 12;  // largest order N of the interpolation scheme
+constexpr int kJMax = 12;        // largest number of series terms kept beyond N (interpolation)
+constexpr int kNEMax = 24;       // largest series length - 1 held by a cell (N + J)
+constexpr int kLamMax = 8;
+constexpr int kDMax = 64;
+constexpr int kJF32 = 6;         // interpolation: series terms beyond N kept in FP32
+constexpr int kJF64 = 10;        // ... and in FP64
+constexpr int kMaxRefined = 262144;  // bound on (rows per path) << lambda
+constexpr unsigned kFull = 0xffffffffu;
+constexpr int kFwdWarps = 4;     // warps per block of the persistent wavefront kernels
+
+// ---------------------------------------------------------------------------------------------
+// Constant tables (uploaded once per device by the host code in sk_api.cu).
+//   c_inv[m]        1/m                      (m >= 1; c_inv[0] unused)
+//   c_hank[n][k]    n!/(n+k)!                (Hankel coupling of the opposite edge, k >= 1)
+//   c_rfact[n]      1/n!                     (endpoint evaluation of a factorial-scaled series)
+//   c_proj[N][n][jj]  interpolation projection for order N: the factorial-scaled interpolant
+//                   at the N+1 Chebyshev extrema of a series with coefficient j = N+1+jj
+//                   contributes c_proj[N][n][jj] to coefficient n (columns j <= N are the
+//                   identity and are not stored).
+// ---------------------------------------------------------------------------------------------
+extern __constant__ float c_inv_f[kNEMax + 2];
+extern __constant__ double c_inv_d[kNEMax + 2];
+extern __constant__ float c_hank_f[kNEMax + 1][kNMaxApprox + 1];
+extern __constant__ double c_hank_d[kNEMax + 1][kNMaxApprox + 1];
+extern __constant__ double c_rfact_d[kNEMax + 1];
+extern __constant__ float c_proj_f[kNMaxInterp + 1][kNMaxInterp + 1][kJMax];
+extern __constant__ double c_proj_d[kNMaxInterp + 1][kNMaxInterp + 1][kJMax];
+
+// Device error word: the first SK_ERR_* code recorded by any kernel of the library.
+extern __device__ int g_sk_error;
+
+__device__ __forceinline__ void record_error(int code) { atomicCAS(&g_sk_error, 0, code); }
+
+template <typename T> struct Tab;
+template <> struct Tab<float> {
+    static __device__ __forceinline__ float inv(int m) { return c_inv_f[m]; }
+    static __device__ __forceinline__ float hank(int n, int k) { return c_hank_f[n][k]; }
+    static __device__ __forceinline__ float proj(int N, int n, int jj) { return c_proj_f[N][n][jj]; }
+};
+template <> struct Tab<double> {
+    static __device__ __forceinline__ double inv(int m) { return c_inv_d[m]; }
+    static __device__ __forceinline__ double hank(int n, int k) { return c_hank_d[n][k]; }
+    static __device__ __forceinline__ double proj(int N, int n, int jj) { return c_proj_d[N][n][jj]; }
+};
+
+// Exact power of two 2^e from its IEEE-754 bits (|e| within the normal range of T).
+__device__ __forceinline__ float pow2f(int e) { return __int_as_float((e + 127) << 23); }
+__device__ __forceinline__ double pow2d(int e) {
+    return __longlong_as_double(static_cast<long long>(e + 1023) << 52);
+}
+
+// Vector type used for increment rows (16-byte loads).
+template <typename T> struct Vec;
+template <> struct Vec<float> {
+    using type = float4;
+    static constexpr int W = 4;
+    static __device__ __forceinline__ float dot(float4 a, float4 b, float acc) {
+        acc = fmaf(a.x, b.x, acc);
+        acc = fmaf(a.y, b.y, acc);
+        acc = fmaf(a.z, b.z, acc);
+        return fmaf(a.w, b.w, acc);
+    }
+};
+template <> struct Vec<double> {
+    using type = double2;
+    static constexpr int W = 2;
+    static __device__ __forceinline__ double dot(double2 a, double2 b, double acc) {
+        acc = fma(a.x, b.x, acc);
+        return fma(a.y, b.y, acc);
+    }
+};
+
+// <dx_i, dy_j> over `nvec` 16-byte chunks of zero-padded increment rows (read-only path).
+template <typename T>
+__device__ __forceinline__ T row_dot(const T* __restrict__ x, const T* __restrict__ y, int nvec) {
+    using V = typename Vec<T>::type;
+    const V* xv = reinterpret_cast<const V*>(x);
+    const V* yv = reinterpret_cast<const V*>(y);
+    T acc = T(0);
+    for (int c = 0; c < nvec; ++c) acc = Vec<T>::dot(__ldg(xv + c), __ldg(yv + c), acc);
+    return acc;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Pair description shared by the forward and backward kernels.
+// ---------------------------------------------------------------------------------------------
+enum PairMode : int { kPairsList = 0, kGramFull = 1, kGramUpper = 2 };
+
+struct PathSet {
+    const void* inc;         // increments, T[rows_total][dpad], zero padded; the increments of
+                             // path a start at row off[a] (points mode leaves its last row unused)
+    const int64_t* off;      // caller's row offsets [count + 1]
+    int64_t count;
+    int64_t max_len;         // caller's bound on rows per path
+    int64_t rows_total;      // caller's row count
+};
+
+struct PairDesc {
+    int64_t a, b;            // path indices
+    int64_t xs, ys;          // first increment row of each path
+    int64_t lx, ly;          // increments per path (>= 0), or -1 when the path is invalid
+};
+
+struct Launch {
+    PathSet X, Y;
+    int32_t nvec;            // 16-byte chunks per increment row
+    int32_t dpad;            // padded row length in elements
+    int32_t inc_mode;        // 1 when the caller's rows are increments
+    int32_t lam;             // dyadic order
+    int32_t mode;            // PairMode
+    int64_t npairs;          // work items
+    const int64_t* pair_a;
+    const int64_t* pair_b;
+    const int32_t* order;    // work-item order (NULL = natural)
+    unsigned int* queue;     // work counter (zeroed before launch)
+    double* out;             // pairs: [npairs]; gram: [X.count][Y.count]
+    int64_t ldo;             // leading dimension of a Gram output
+    void* scratch;           // per-warp-slot hand-off buffers
+    int64_t scratch_stride;  // bytes per warp slot
+    float tau;               // |M| above which an FP32 map is built in FP64
+};
+
+__device__ __forceinline__ int64_t upper_row(int64_t p, int64_t n) {
+    // Row a of the upper triangle (a <= b) holding linear index p (row a has n - a entries).
+    double nn = static_cast<double>(n);
+    double disc = (2.0 * nn + 1.0) * (2.0 * nn + 1.0) - 8.0 * static_cast<double>(p);
+    int64_t a = static_cast<int64_t>(floor(((2.0 * nn + 1.0) - sqrt(disc)) * 0.5));
+    if (a < 0) a = 0;
+    if (a > n - 1) a = n - 1;
+    // exact correction: start(a) = a*n - a*(a-1)/2
+    while (a > 0 && a * n - a * (a - 1) / 2 > p) --a;
+    while (a + 1 < n && (a + 1) * n - (a + 1) * a / 2 <= p) ++a;
+    return a;
+}
+
+__device__ __forceinline__ void path_span(const PathSet& S, int64_t a, int inc_mode, int64_t& start,
+                                          int64_t& len) {
+    int64_t r0 = S.off[a], r1 = S.off[a + 1];
+    int64_t rows = r1 - r0;
+    if (r0 < 0 || r1 > S.rows_total || rows < (inc_mode ? 0 : 1) || rows > S.max_len) {
+        start = 0;
+        len = -1;
+        return;
+    }
+    start = r0;
+    len = inc_mode ? rows : rows - 1;
+}
+
+__device__ __forceinline__ PairDesc decode_pair(const Launch& L, int64_t item) {
+    PairDesc P;
+    if (L.mode == kPairsList) {
+        P.a = L.pair_a[item];
+        P.b = L.pair_b[item];
+    } else if (L.mode == kGramFull) {
+        P.a = item / L.Y.count;
+        P.b = item - P.a * L.Y.count;
+    } else {
+        int64_t n = L.X.count;
+        P.a = upper_row(item, n);
+        P.b = P.a + (item - (P.a * n - P.a * (P.a - 1) / 2));
+    }
+    bool okx = P.a >= 0 && P.a < L.X.count, oky = P.b >= 0 && P.b < L.Y.count;
+    if (!okx || !oky) {
+        P.lx = P.ly = -1;
+        P.xs = P.ys = 0;
+        return P;
+    }
+    path_span(L.X, P.a, L.inc_mode, P.xs, P.lx);
+    path_span(L.Y, P.b, L.inc_mode, P.ys, P.ly);
+    return P;
+}
+
+__device__ __forceinline__ void write_result(const Launch& L, int64_t item, const PairDesc& P, double v) {
+    if (L.mode == kPairsList) {
+        L.out[item] = v;
+    } else {
+        L.out[P.a * L.ldo + P.b] = v;
+        if (L.mode == kGramUpper) L.out[P.b * L.ldo + P.a] = v;
+    }
+}
+
+// Pop the next work item for a warp (lane 0 takes it, all lanes receive it).
+__device__ __forceinline__ int64_t next_item(const Launch& L) {
+    unsigned int k = 0;
+    if ((threadIdx.x & 31) == 0) k = atomicAdd(L.queue, 1u);
+    k = __shfl_sync(kFull, k, 0);
+    if (static_cast<int64_t>(k) >= L.npairs) return -1;
+    return L.order ? static_cast<int64_t>(L.order[k]) : static_cast<int64_t>(k);
+}
+
+}  // namespace sk

@@ -1,0 +1,28 @@
+// Instantiations of the polynomial-approximation forward wavefront (float cell updates).
+#include "sk_fwd_poly.cuh"
+#include "sk_dispatch.h"
+
+namespace sk {
+
+const void* fwd_approx_ptr_f32(int N) {
+    switch (N) {
+        case 2: return reinterpret_cast<const void*>(&fwd_poly_kernel<float, 2, 2 + 0, false>);
+        case 3: return reinterpret_cast<const void*>(&fwd_poly_kernel<float, 3, 3 + 0, false>);
+        case 4: return reinterpret_cast<const void*>(&fwd_poly_kernel<float, 4, 4 + 0, false>);
+        case 5: return reinterpret_cast<const void*>(&fwd_poly_kernel<float, 5, 5 + 0, false>);
+        case 6: return reinterpret_cast<const void*>(&fwd_poly_kernel<float, 6, 6 + 0, false>);
+        case 7: return reinterpret_cast<const void*>(&fwd_poly_kernel<float, 7, 7 + 0, false>);
+        case 8: return reinterpret_cast<const void*>(&fwd_poly_kernel<float, 8, 8 + 0, false>);
+        case 9: return reinterpret_cast<const void*>(&fwd_poly_kernel<float, 9, 9 + 0, false>);
+        case 10: return reinterpret_cast<const void*>(&fwd_poly_kernel<float, 10, 10 + 0, false>);
+        case 11: return reinterpret_cast<const void*>(&fwd_poly_kernel<float, 11, 11 + 0, false>);
+        case 12: return reinterpret_cast<const void*>(&fwd_poly_kernel<float, 12, 12 + 0, false>);
+        case 13: return reinterpret_cast<const void*>(&fwd_poly_kernel<float, 13, 13 + 0, false>);
+        case 14: return reinterpret_cast<const void*>(&fwd_poly_kernel<float, 14, 14 + 0, false>);
+        case 15: return reinterpret_cast<const void*>(&fwd_poly_kernel<float, 15, 15 + 0, false>);
+        case 16: return reinterpret_cast<const void*>(&fwd_poly_kernel<float, 16, 16 + 0, false>);
+        default: return nullptr;
+    }
+}
+
+}  // namespace sk

@@ -1,0 +1,32 @@
+// Instantiations of the finite-difference forward wavefront and the kernel lookup.
+#include "sk_dispatch.h"
+#include "sk_fwd_fd.cuh"
+
+namespace sk {
+
+namespace {
+template <typename T, int ORDER>
+const void* fd_rows(int lam) {
+    // rows per lane: R = min(2^lambda, 16) (a divisor of 2^lambda, so a lane's rows share a cell)
+    switch (lam < 4 ? lam : 4) {
+        case 0: return reinterpret_cast<const void*>(&fwd_fd_kernel<T, ORDER, 1>);
+        case 1: return reinterpret_cast<const void*>(&fwd_fd_kernel<T, ORDER, 2>);
+        case 2: return reinterpret_cast<const void*>(&fwd_fd_kernel<T, ORDER, 4>);
+        case 3: return reinterpret_cast<const void*>(&fwd_fd_kernel<T, ORDER, 8>);
+        default: return reinterpret_cast<const void*>(&fwd_fd_kernel<T, ORDER, 16>);
+    }
+}
+}  // namespace
+
+const void* fwd_fd_kernel_ptr(int T, int order, int lam) {
+    if (lam < 0 || lam > kLamMax) return nullptr;
+    if (T == 1) return order == 2 ? fd_rows<float, 2>(lam) : fd_rows<float, 1>(lam);
+    return order == 2 ? fd_rows<double, 2>(lam) : fd_rows<double, 1>(lam);
+}
+
+const void* fwd_poly_kernel_ptr(int T, bool interp, int N) {
+    if (T == 1) return interp ? fwd_interp_ptr_f32(N) : fwd_approx_ptr_f32(N);
+    return interp ? fwd_interp_ptr_f64(N) : fwd_approx_ptr_f64(N);
+}
+
+}  // namespace sk

@@ -1,0 +1,154 @@
+// Forward wavefront of the finite-difference schemes on the dyadic grid P_lambda (Definition
+// "dyadic scheme", Section 2; second-order explicit update eq. (secondexplicitscheme)) for sm_103a.
+//
+// On a sub-cell of P_lambda with m = <dx_I, dy_J> = M_ij / 4^lambda (the refined increments are
+// the coarse ones divided by 2^lambda), both explicit updates read
+//     k(I+1, J+1) = (k(I+1, J) + k(I, J+1)) alpha - k(I, J) beta
+// with alpha = 1 + m/2, beta = 1 (first order) or alpha = 1 + m/2 + m^2/12, beta = 1 - m^2/12
+// (second order).  All 4^lambda sub-cells of a cell share (alpha, beta).
+//
+// Parallel layout.  One warp owns one pair.  Lane r owns R = min(2^lambda, 16) consecutive node
+// rows (a "row group"; all in one coarse row) and sweeps the refined columns; the top node of
+// its group moves one lane up per step by __shfl_up_sync, and lane 31's top nodes are handed to
+// lane 0 of the next strip through a per-warp buffer, as in the polynomial wavefront.  FP32 keeps
+// a power-of-two exponent per lane (rescale by 2^-64 / 2^64 outside [2^-64, 2^64]).
+#pragma once
+
+#include <type_traits>
+
+#include "sk_common.cuh"
+
+namespace sk {
+
+template <typename T>
+__device__ __forceinline__ T fd_pow2(int e) {
+    if constexpr (std::is_same<T, float>::value) return pow2f(e);
+    else return pow2d(e);
+}
+
+template <typename T, int ORDER, int R>
+__global__ void __launch_bounds__(kFwdWarps * 32) fwd_fd_kernel(Launch L, int64_t buf_cols) {
+    constexpr bool kRescale = std::is_same<T, float>::value;
+    const int lane = threadIdx.x & 31;
+    const int64_t slot = static_cast<int64_t>(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    char* base = static_cast<char*>(L.scratch) + slot * L.scratch_stride;
+    T* hbuf = reinterpret_cast<T*>(base);                         // [buf_cols]
+    int* ebuf = reinterpret_cast<int*>(hbuf + buf_cols);          // [buf_cols]
+    const int dpad = L.dpad;
+    const T* __restrict__ incX = static_cast<const T*>(L.X.inc);
+    const T* __restrict__ incY = static_cast<const T*>(L.Y.inc);
+
+    for (;;) {
+        const int64_t item = next_item(L);
+        if (item < 0) break;
+        const PairDesc P = decode_pair(L, item);
+        if (P.lx < 0 || P.ly < 0) {
+            if (lane == 0) {
+                record_error(SK_ERR_BAD_LENGTH);
+                if (P.a >= 0 && P.a < L.X.count && P.b >= 0 && P.b < L.Y.count)
+                    write_result(L, item, P, __longlong_as_double(0x7ff8000000000000LL));
+            }
+            continue;
+        }
+        if (P.lx == 0 || P.ly == 0) {
+            if (lane == 0) write_result(L, item, P, 1.0);
+            continue;
+        }
+        const int lam = L.lam;
+        const int nI = static_cast<int>(P.lx << lam);   // refined node rows 0..nI
+        const int nJ = static_cast<int>(P.ly << lam);   // refined node columns 0..nJ
+        const int groups = nI / R;
+        const int period = nJ > 32 ? nJ : 32;
+        const int nstrips = (groups + 31) >> 5;
+        const int last_lane = (groups - 1) - ((nstrips - 1) << 5);
+        const int nsteps = (nstrips - 1) * period + last_lane + nJ;
+        const T sub = fd_pow2<T>(-2 * lam);
+        const T* xbase = incX + P.xs * dpad;
+        const T* ybase = incY + P.ys * dpad;
+
+        T col[R];   // k(gR + 1 + r, jj) for the lane's group g at its current column jj
+        T kb_prev = T(1), top = T(0);
+        int ea = 0, eo = 0;
+#pragma unroll
+        for (int r = 0; r < R; ++r) col[r] = T(1);
+        int jj = -lane, s = 0;
+
+        for (int step = 0; step < nsteps; ++step) {
+            T kb = __shfl_up_sync(kFull, top, 1);            // k(gR, jj + 1) from the lane below
+            int eb = kRescale ? __shfl_up_sync(kFull, eo, 1) : 0;
+            const int g = (s << 5) + lane;
+            const bool active = jj >= 0 && jj < nJ && g < groups;
+            if (active) {
+                if (lane == 0) {
+                    if (s == 0) { kb = T(1); eb = 0; }       // row 0: k(s_0, .) = 1
+                    else { kb = hbuf[jj]; if (kRescale) eb = ebuf[jj]; }
+                }
+                if (jj == 0) {                               // column 0: k(., t_0) = 1
+#pragma unroll
+                    for (int r = 0; r < R; ++r) col[r] = T(1);
+                    kb_prev = T(1);
+                    ea = 0;
+                }
+                if (kRescale && ea != eb) {
+                    if (ea > eb) {
+                        kb *= (eb - ea < -126) ? T(0) : fd_pow2<T>(eb - ea);
+                    } else {
+                        const T f = (ea - eb < -126) ? T(0) : fd_pow2<T>(ea - eb);
+#pragma unroll
+                        for (int r = 0; r < R; ++r) col[r] *= f;
+                        kb_prev *= f;
+                        ea = eb;
+                    }
+                }
+                const T m = row_dot<T>(xbase + static_cast<int64_t>((g * R) >> lam) * dpad,
+                                       ybase + static_cast<int64_t>(jj >> lam) * dpad, L.nvec) * sub;
+                T alpha = fma(m, T(0.5), T(1));
+                T beta = T(1);
+                if constexpr (ORDER == 2) {
+                    const T m2 = m * m * T(1.0 / 12.0);
+                    alpha += m2;
+                    beta -= m2;
+                }
+                T below_new = kb, below_old = kb_prev;
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    const T old = col[r];
+                    T v = (old + below_new) * alpha;
+                    v = (ORDER == 2) ? fma(-below_old, beta, v) : v - below_old;
+                    col[r] = v;
+                    below_new = v;
+                    below_old = old;
+                }
+                kb_prev = kb;
+                top = col[R - 1];
+                if (g == groups - 1 && jj == nJ - 1) {
+                    double v = static_cast<double>(top);
+                    if (kRescale) v = ldexp(v, ea);
+                    if (!isfinite(v)) record_error(SK_ERR_NONFINITE);
+                    write_result(L, item, P, v);
+                }
+                if (kRescale) {
+                    const float mag = fmaxf(fabsf(static_cast<float>(col[0])), fabsf(static_cast<float>(top)));
+                    if (mag > 0x1p64f || (mag < 0x1p-64f && mag > 0.f)) {
+                        const int sh = mag > 0x1p64f ? -64 : 64;
+                        const T f = fd_pow2<T>(sh);
+#pragma unroll
+                        for (int r = 0; r < R; ++r) col[r] *= f;
+                        kb_prev *= f;
+                        top = col[R - 1];
+                        ea -= sh;
+                    }
+                }
+                eo = ea;
+                if (lane == 31 && s + 1 < nstrips) {
+                    hbuf[jj] = top;
+                    if (kRescale) ebuf[jj] = eo;
+                }
+            }
+            __syncwarp();
+            if (++jj == period) { jj = 0; ++s; }
+        }
+    }
+}
+
+}  // namespace sk

@@ -1,0 +1,24 @@
+// Instantiations of the polynomial-interpolation forward wavefront (float cell updates).
+#include "sk_fwd_poly.cuh"
+#include "sk_dispatch.h"
+
+namespace sk {
+
+const void* fwd_interp_ptr_f32(int N) {
+    switch (N) {
+        case 2: return reinterpret_cast<const void*>(&fwd_poly_kernel<float, 2, 2 + sk::kJF32, true>);
+        case 3: return reinterpret_cast<const void*>(&fwd_poly_kernel<float, 3, 3 + sk::kJF32, true>);
+        case 4: return reinterpret_cast<const void*>(&fwd_poly_kernel<float, 4, 4 + sk::kJF32, true>);
+        case 5: return reinterpret_cast<const void*>(&fwd_poly_kernel<float, 5, 5 + sk::kJF32, true>);
+        case 6: return reinterpret_cast<const void*>(&fwd_poly_kernel<float, 6, 6 + sk::kJF32, true>);
+        case 7: return reinterpret_cast<const void*>(&fwd_poly_kernel<float, 7, 7 + sk::kJF32, true>);
+        case 8: return reinterpret_cast<const void*>(&fwd_poly_kernel<float, 8, 8 + sk::kJF32, true>);
+        case 9: return reinterpret_cast<const void*>(&fwd_poly_kernel<float, 9, 9 + sk::kJF32, true>);
+        case 10: return reinterpret_cast<const void*>(&fwd_poly_kernel<float, 10, 10 + sk::kJF32, true>);
+        case 11: return reinterpret_cast<const void*>(&fwd_poly_kernel<float, 11, 11 + sk::kJF32, true>);
+        case 12: return reinterpret_cast<const void*>(&fwd_poly_kernel<float, 12, 12 + sk::kJF32, true>);
+        default: return nullptr;
+    }
+}
+
+}  // namespace sk

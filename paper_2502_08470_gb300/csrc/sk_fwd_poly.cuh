@@ -1,0 +1,261 @@
+// Forward wavefront of the polynomial schemes (approximation, Section 3.2; interpolation,
+// Section 3.3) for sm_103a.
+//
+// Coordinates.  In a cell with bottom-left corner (s_i, t_j) let u = (s - s_i)/ds and
+// v = (t - t_j)/dt.  The bottom edge k(s, t_j) = sum_n p_n (s - s_i)^n is held as the factorial-
+// scaled coefficients a_n = n! p_n ds^n (so k(s, t_j) = sum_n a_n u^n / n!), the left edge as
+// b_n = n! q_n dt^n.  Substituting into the update of Proposition "approxsolution" (eqs.
+// (powerseries1), (powerseries2)) with C ds dt = M = <dx_i, dy_j> gives
+//     a'_n = sum_{k<=n} a_k e_{n-k}  +  e_n sum_{k>=1} b_k n!/(n+k)!,      e_m = M^m / m!
+//     b'_n = sum_{k<=n} b_k e_{n-k}  +  e_n sum_{k>=1} a_k n!/(n+k)!
+// so a cell depends on M only (no time partition), its Toeplitz part is a convolution with the
+// truncated exponential e(M), and its coupling part is a constant Hankel matrix n!/(n+k)!.
+//   * Approximation (Def. "def:polyapproxscheme"): n = 0..N, i.e. pi_N after Lambda.
+//   * Interpolation (Def. "def:polyinterpscheme"): Phi^N of Proposition "propinterp" applied to
+//     degree-N edges is the same series untruncated; its factorial-scaled coefficients are
+//     computed for n = 0..N+J and Omega^N (interpolation at the N+1 Chebyshev extrema) is the
+//     constant projection a' = c_{0..N} + P c_{N+1..N+J}.  The right edge uses a_0 = g_0 in
+//     its 0F1(1; z) term, as eq. (interpformula) is printed.
+// Endpoint: k_hat = 1/2 sum_n (a_n + b_n)/n! at the last cell (u = v = 1).
+//
+// Parallel layout.  One warp owns one pair.  Lane r owns grid rows r, r+32, r+64, ... (a
+// "strip" of 32 rows at a time).  Cell (32 s + r, j) is updated at warp step s*P + j + r with
+// P = max(cols, 32): the a-vector stays in the lane, the b-vector moves one lane up per step
+// through __shfl_up_sync, and lane 31's right edges are handed to lane 0 of the next strip
+// through a per-warp buffer (written P - 31 >= 1 steps before they are read).  Each warp step
+// is one antidiagonal of the strip's cells (Fig. "gridparallel"); consecutive strips overlap so
+// no lane idles between them.
+//
+// FP32 range.  Each lane carries a power-of-two exponent for its (a, b) pair; the two inputs of a
+// cell are brought to the larger exponent, and after the update the pair is rescaled by 2^-64
+// or 2^64 whenever |a'_0|, |b'_0| leave [2^-64, 2^64].  Exact in binary arithmetic, so results
+// change only by rounding.
+#pragma once
+
+#include <type_traits>
+
+#include "sk_common.cuh"
+
+namespace sk {
+
+template <typename T, int NE>
+__device__ __forceinline__ void build_exp_series(T M, float tau, T (&e)[NE + 1]) {
+    e[0] = T(1);
+    if constexpr (std::is_same<T, float>::value) {
+        if (fabsf(M) > tau) {
+            // Large |M|: build the map coefficients M^m/m! in FP64 and round once.
+            double md = static_cast<double>(M), v = 1.0;
+#pragma unroll
+            for (int m = 1; m <= NE; ++m) {
+                v *= md * c_inv_d[m];
+                e[m] = static_cast<float>(v);
+            }
+            return;
+        }
+    }
+    (void)tau;
+#pragma unroll
+    for (int m = 1; m <= NE; ++m) e[m] = e[m - 1] * (M * Tab<T>::inv(m));
+}
+
+// One cell: inputs a (bottom), b (left), outputs the factorial-scaled series of the top (ct)
+// and right (cr) edges, n = 0..NE.
+template <typename T, int N, int NE, bool INTERP>
+__device__ __forceinline__ void cell_series(const T (&a)[N + 1], const T (&b)[N + 1], const T (&e)[NE + 1],
+                                            T (&ct)[NE + 1], T (&cr)[NE + 1]) {
+#pragma unroll
+    for (int n = 0; n <= NE; ++n) {
+        // coupling through the opposite edge: sum_{k>=1} (.)_k n!/(n+k)!
+        T ha = b[1] * Tab<T>::hank(n, 1);
+        T hb = a[1] * Tab<T>::hank(n, 1);
+#pragma unroll
+        for (int k = 2; k <= N; ++k) {
+            ha = fma(b[k], Tab<T>::hank(n, k), ha);
+            hb = fma(a[k], Tab<T>::hank(n, k), hb);
+        }
+        T vt = e[n] * ha;
+        T vr = e[n] * hb;
+#pragma unroll
+        for (int k = 0; k <= (n < N ? n : N); ++k) {
+            vt = fma(a[k], e[n - k], vt);
+            T bk = (INTERP && k == 0) ? a[0] : b[k];
+            vr = fma(bk, e[n - k], vr);
+        }
+        ct[n] = vt;
+        cr[n] = vr;
+    }
+}
+
+template <typename T, int N, int NE, bool INTERP>
+__device__ __forceinline__ void project(const T (&c)[NE + 1], T (&out)[N + 1]) {
+#pragma unroll
+    for (int n = 0; n <= N; ++n) {
+        T v = c[n];
+        if constexpr (INTERP) {
+#pragma unroll
+            for (int j = N + 1; j <= NE; ++j) v = fma(Tab<T>::proj(N, n, j - N - 1), c[j], v);
+        }
+        out[n] = v;
+    }
+}
+
+template <typename T, int NE>
+__device__ __forceinline__ double series_at_one(const T (&c)[NE + 1]) {
+    double acc = 0.0;
+#pragma unroll
+    for (int n = NE; n >= 0; --n) acc = fma(static_cast<double>(c[n]), c_rfact_d[n], acc);
+    return acc;
+}
+
+template <typename T>
+__device__ __forceinline__ T pow2t(int e) {
+    if constexpr (std::is_same<T, float>::value) return pow2f(e);
+    else return pow2d(e);
+}
+
+// Resident blocks per SM requested from the register allocator: the live state of a lane is
+// about 3 (N+1) edge values, 3 (NE+1) series values and ~24 addresses / counters.
+template <typename T, int N, int NE>
+constexpr int fwd_poly_min_blocks() {
+    constexpr int words = (3 * (N + 1) + 3 * (NE + 1) + 24) * (sizeof(T) == 8 ? 2 : 1);
+    constexpr int b = 65536 / (kFwdWarps * 32 * words);
+    return b < 1 ? 1 : (b > 8 ? 8 : b);
+}
+
+template <typename T, int N, int NE, bool INTERP>
+__global__ void __launch_bounds__(kFwdWarps * 32, (fwd_poly_min_blocks<T, N, NE>()))
+    fwd_poly_kernel(Launch L, int64_t buf_cols) {
+    constexpr bool kRescale = std::is_same<T, float>::value;
+    const int lane = threadIdx.x & 31;
+    const int64_t slot = static_cast<int64_t>(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    char* base = static_cast<char*>(L.scratch) + slot * L.scratch_stride;
+    T* hbuf = reinterpret_cast<T*>(base);                                // [buf_cols][N+1]
+    int* ebuf = reinterpret_cast<int*>(hbuf + buf_cols * (N + 1));      // [buf_cols]
+    const int dpad = L.dpad;
+    const T* __restrict__ incX = static_cast<const T*>(L.X.inc);
+    const T* __restrict__ incY = static_cast<const T*>(L.Y.inc);
+
+    for (;;) {
+        const int64_t item = next_item(L);
+        if (item < 0) break;
+        const PairDesc P = decode_pair(L, item);
+        if (P.lx < 0 || P.ly < 0) {
+            if (lane == 0) {
+                record_error(SK_ERR_BAD_LENGTH);
+                if (P.a >= 0 && P.a < L.X.count && P.b >= 0 && P.b < L.Y.count)
+                    write_result(L, item, P, __longlong_as_double(0x7ff8000000000000LL));
+            }
+            continue;
+        }
+        if (P.lx == 0 || P.ly == 0) {
+            if (lane == 0) write_result(L, item, P, 1.0);
+            continue;
+        }
+        const int lam = L.lam;
+        const int rows = static_cast<int>(P.lx << lam);
+        const int cols = static_cast<int>(P.ly << lam);
+        const int period = cols > 32 ? cols : 32;
+        const int nstrips = (rows + 31) >> 5;
+        const int last_lane = (rows - 1) - ((nstrips - 1) << 5);
+        const int nsteps = (nstrips - 1) * period + last_lane + cols;
+        const T sub = pow2t<T>(-2 * lam);  // M of a sub-cell of P_lambda is M_ij / 4^lambda
+        const T* xbase = incX + P.xs * dpad;
+        const T* ybase = incY + P.ys * dpad;
+
+        T a[N + 1], bo[N + 1];
+#pragma unroll
+        for (int n = 0; n <= N; ++n) { a[n] = T(0); bo[n] = T(0); }
+        int ea = 0, eo = 0;
+        int jj = -lane, s = 0;
+
+        for (int step = 0; step < nsteps; ++step) {
+            T b[N + 1];
+#pragma unroll
+            for (int n = 0; n <= N; ++n) b[n] = __shfl_up_sync(kFull, bo[n], 1);
+            int eb = kRescale ? __shfl_up_sync(kFull, eo, 1) : 0;
+            const int row = (s << 5) + lane;
+            const bool active = jj >= 0 && jj < cols && row < rows;
+            if (active) {
+                if (lane == 0) {
+                    if (s == 0) {  // q^{0,j} = e_0 (left boundary k(0, .) = 1)
+#pragma unroll
+                        for (int n = 0; n <= N; ++n) b[n] = (n == 0) ? T(1) : T(0);
+                        eb = 0;
+                    } else {
+                        const T* src = hbuf + static_cast<int64_t>(jj) * (N + 1);
+#pragma unroll
+                        for (int n = 0; n <= N; ++n) b[n] = src[n];
+                        if (kRescale) eb = ebuf[jj];
+                    }
+                }
+                if (jj == 0) {  // p^{i,0} = e_0 (bottom boundary k(., 0) = 1)
+#pragma unroll
+                    for (int n = 0; n <= N; ++n) a[n] = (n == 0) ? T(1) : T(0);
+                    ea = 0;
+                }
+                if (kRescale && ea != eb) {  // bring both inputs to the larger exponent
+                    if (ea > eb) {
+                        const T f = (eb - ea < -126) ? T(0) : pow2t<T>(eb - ea);
+#pragma unroll
+                        for (int n = 0; n <= N; ++n) b[n] *= f;
+                    } else {
+                        const T f = (ea - eb < -126) ? T(0) : pow2t<T>(ea - eb);
+#pragma unroll
+                        for (int n = 0; n <= N; ++n) a[n] *= f;
+                        ea = eb;
+                    }
+                }
+                const T M = row_dot<T>(xbase + static_cast<int64_t>(row >> lam) * dpad,
+                                       ybase + static_cast<int64_t>(jj >> lam) * dpad, L.nvec) * sub;
+                T e[NE + 1];
+                build_exp_series<T, NE>(M, L.tau, e);
+                T ct[NE + 1], cr[NE + 1];
+                cell_series<T, N, NE, INTERP>(a, b, e, ct, cr);
+                if (row == rows - 1 && jj == cols - 1) {
+                    double v = 0.5 * (series_at_one<T, NE>(ct) + series_at_one<T, NE>(cr));
+                    if (kRescale) v = ldexp(v, ea);
+                    if (!isfinite(v)) record_error(SK_ERR_NONFINITE);
+                    write_result(L, item, P, v);
+                }
+                project<T, N, NE, INTERP>(ct, a);
+                project<T, N, NE, INTERP>(cr, bo);
+                if (kRescale) {
+                    const float mag = fmaxf(fabsf(static_cast<float>(a[0])), fabsf(static_cast<float>(bo[0])));
+                    if (mag > 0x1p64f) {
+#pragma unroll
+                        for (int n = 0; n <= N; ++n) { a[n] *= pow2t<T>(-64); bo[n] *= pow2t<T>(-64); }
+                        ea += 64;
+                    } else if (mag < 0x1p-64f) {
+                        float full = 0.f;
+#pragma unroll
+                        for (int n = 0; n <= N; ++n)
+                            full = fmaxf(full, fmaxf(fabsf(static_cast<float>(a[n])), fabsf(static_cast<float>(bo[n]))));
+                        if (full < 0x1p-64f && full > 0.f) {
+#pragma unroll
+                            for (int n = 0; n <= N; ++n) { a[n] *= pow2t<T>(64); bo[n] *= pow2t<T>(64); }
+                            ea -= 64;
+                        }
+                    }
+                }
+                eo = ea;
+                if (lane == 31 && s + 1 < nstrips) {  // hand the right edge to the next strip
+                    T* dst = hbuf + static_cast<int64_t>(jj) * (N + 1);
+#pragma unroll
+                    for (int n = 0; n <= N; ++n) dst[n] = bo[n];
+                    if (kRescale) ebuf[jj] = eo;
+                }
+            }
+            __syncwarp();
+            if (++jj == period) { jj = 0; ++s; }
+        }
+    }
+}
+
+// Bytes of hand-off buffer per warp slot for `cols` refined columns.
+template <typename T>
+inline int64_t fwd_poly_slot_bytes(int N, int64_t cols) {
+    int64_t b = cols * (N + 1) * static_cast<int64_t>(sizeof(T)) + cols * 4;
+    return (b + 255) / 256 * 256;
+}
+
+}  // namespace sk

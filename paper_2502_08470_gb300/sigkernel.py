@@ -1,0 +1,224 @@
+"""Python binding of the C ABI in ``include/sigkernel.h`` (argument marshalling only).
+
+Every computation runs in ``_lib/libsigkernel.so`` on the current CUDA device and stream; this
+module converts torch tensors to the ABI's pointers and sizes.  If the library is missing the
+first call raises; there is no CPU fallback.
+
+Paths are given either as a dense tensor ``[B, L, d]`` (all paths with L points) or as a
+:class:`Paths` (concatenated rows plus int64 offsets, for ragged batches).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+from dataclasses import dataclass
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libsigkernel.so")
+
+SK_OK = 0
+ERRORS = {-1: "SK_ERR_INVALID_ARG", -2: "SK_ERR_UNSUPPORTED", -3: "SK_ERR_CUDA", -4: "SK_ERR_WORKSPACE",
+          -5: "SK_ERR_DEVICE_TIMEOUT", -6: "SK_ERR_NONFINITE", -7: "SK_ERR_BAD_LENGTH"}
+SCHEMES = {"fd1": 0, "fd2": 1, "approx": 2, "interp": 3}
+COMPUTE = {"f64": 0, "f32": 1}
+DTYPES = {torch.float64: 0, torch.float32: 1, torch.bfloat16: 2}
+FLAG_SYMMETRIC, FLAG_INCREMENTS, FLAG_UNBIASED, FLAG_NO_SORT, FLAG_TIME_KERNEL = 1, 2, 4, 8, 16
+OP_PAIRS, OP_GRAM, OP_BACKWARD, OP_MMD2 = 0, 1, 2, 3
+
+
+class SigKernelError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class _Options(ctypes.Structure):
+    _fields_ = [("scheme", ctypes.c_int32), ("degree", ctypes.c_int32), ("dyadic", ctypes.c_int32),
+                ("compute", ctypes.c_int32), ("interp_extra", ctypes.c_int32), ("flags", ctypes.c_int32),
+                ("warps_per_block", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class _Paths(ctypes.Structure):
+    _fields_ = [("rows", ctypes.c_void_p), ("offsets", ctypes.c_void_p), ("count", ctypes.c_int64),
+                ("max_len", ctypes.c_int64), ("rows_total", ctypes.c_int64)]
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def load_library():
+    """Load ``libsigkernel.so`` (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with `python -m paper_2502_08470_gb300.build`")
+        lib = ctypes.CDLL(LIB_PATH)
+        P, I32, I64, SZ = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_size_t
+        PP, PO = ctypes.POINTER(_Paths), ctypes.POINTER(_Options)
+        lib.sigkernel_version.restype = ctypes.c_int
+        lib.sigkernel_last_error.restype = ctypes.c_char_p
+        lib.sigkernel_workspace_size.restype = SZ
+        lib.sigkernel_workspace_size.argtypes = [I32, PP, PP, I32, I64, PO]
+        lib.sigkernel_pairs.restype = ctypes.c_int
+        lib.sigkernel_pairs.argtypes = [PP, PP, I32, I32, P, P, I64, PO, P, P, SZ, P]
+        lib.sigkernel_gram.restype = ctypes.c_int
+        lib.sigkernel_gram.argtypes = [PP, PP, I32, I32, PO, P, P, SZ, P]
+        lib.sigkernel_backward.restype = ctypes.c_int
+        lib.sigkernel_backward.argtypes = [PP, PP, I32, I32, P, P, I64, PO, P, P, P, P, SZ, P]
+        lib.sigkernel_mmd2.restype = ctypes.c_int
+        lib.sigkernel_mmd2.argtypes = [PP, PP, I32, I32, PO, P, P, P, P, SZ, P]
+        lib.sigkernel_last_kernel_ms.restype = ctypes.c_float
+        lib.sigkernel_device_status.restype = ctypes.c_int
+        lib.sigkernel_device_status.argtypes = [P]
+        _lib = lib
+        return lib
+
+
+def _check(rc: int):
+    if rc != SK_OK:
+        msg = load_library().sigkernel_last_error().decode(errors="replace")
+        raise SigKernelError(rc, msg)
+
+
+@dataclass
+class Paths:
+    """A ragged batch of paths: ``rows`` [R, d] (points, or increments with ``increments=True``)
+    on the GPU and int64 ``offsets`` [B + 1] (path a is rows offsets[a]:offsets[a+1])."""
+    rows: torch.Tensor
+    offsets: torch.Tensor
+    max_len: int
+    increments: bool = False
+
+    @property
+    def count(self) -> int:
+        return self.offsets.numel() - 1
+
+    @property
+    def d(self) -> int:
+        return self.rows.shape[1]
+
+    @staticmethod
+    def from_list(paths, device="cuda", dtype=None, increments=False) -> "Paths":
+        ts = [torch.as_tensor(p) for p in paths]
+        dtype = dtype or (ts[0].dtype if ts else torch.float64)
+        lens = [t.shape[0] for t in ts]
+        off = torch.zeros(len(ts) + 1, dtype=torch.int64)
+        if ts:
+            off[1:] = torch.cumsum(torch.tensor(lens, dtype=torch.int64), 0)
+        rows = torch.cat([t.to(dtype) for t in ts], 0) if ts else torch.zeros(0, 1, dtype=dtype)
+        return Paths(rows.to(device).contiguous(), off.to(device), max(lens) if lens else 0, increments)
+
+    @staticmethod
+    def from_dense(x: torch.Tensor, increments=False) -> "Paths":
+        B, L, d = x.shape
+        off = torch.arange(0, (B + 1) * L, L, dtype=torch.int64, device=x.device)
+        return Paths(x.reshape(B * L, d).contiguous(), off, L, increments)
+
+
+def as_paths(x) -> Paths:
+    if isinstance(x, Paths):
+        return x
+    if isinstance(x, torch.Tensor) and x.dim() == 3:
+        return Paths.from_dense(x)
+    raise TypeError("paths must be a Paths or a [B, L, d] tensor")
+
+
+def _cpaths(p: Paths) -> _Paths:
+    if not p.rows.is_cuda or not p.offsets.is_cuda:
+        raise ValueError("path rows and offsets must be CUDA tensors")
+    if p.offsets.dtype != torch.int64:
+        raise ValueError("offsets must be int64")
+    return _Paths(p.rows.data_ptr(), p.offsets.data_ptr(), p.count, int(p.max_len), p.rows.shape[0])
+
+
+def _options(scheme="approx", degree=6, dyadic=0, compute="f64", flags=0, interp_extra=0) -> _Options:
+    return _Options(SCHEMES[scheme] if isinstance(scheme, str) else int(scheme), int(degree), int(dyadic),
+                    COMPUTE[compute] if isinstance(compute, str) else int(compute), int(interp_extra), int(flags), 0, 0)
+
+
+def _stream_ptr() -> int:
+    return torch.cuda.current_stream().cuda_stream
+
+
+def _dtype_code(X: Paths, Y: Paths) -> int:
+    if X.rows.dtype != Y.rows.dtype:
+        raise ValueError("X and Y must have the same dtype")
+    return DTYPES[X.rows.dtype]
+
+
+def _workspace(op, cX, cY, d, npairs, opt) -> torch.Tensor:
+    lib = load_library()
+    n = lib.sigkernel_workspace_size(op, ctypes.byref(cX), ctypes.byref(cY), d, npairs, ctypes.byref(opt))
+    if n == 0:
+        _check(-1 if not lib.sigkernel_last_error() else -2)
+    return torch.empty(int(n), dtype=torch.uint8, device="cuda")
+
+
+def _flags(X: Paths, extra=0) -> int:
+    return extra | (FLAG_INCREMENTS if X.increments else 0)
+
+
+def sigkernel_pairs(X, Y, pair_a, pair_b, scheme="approx", degree=6, dyadic=0, compute="f64", sort=True,
+                    out: torch.Tensor | None = None) -> torch.Tensor:
+    """k_hat(X[pair_a[k]], Y[pair_b[k]]) for every k, as a float64 CUDA tensor."""
+    X, Y = as_paths(X), as_paths(Y)
+    pa = torch.as_tensor(pair_a, dtype=torch.int64, device="cuda").contiguous()
+    pb = torch.as_tensor(pair_b, dtype=torch.int64, device="cuda").contiguous()
+    n = pa.numel()
+    opt = _options(scheme, degree, dyadic, compute, _flags(X, 0 if sort else FLAG_NO_SORT))
+    cX, cY = _cpaths(X), _cpaths(Y)
+    out = out if out is not None else torch.empty(n, dtype=torch.float64, device="cuda")
+    ws = _workspace(OP_PAIRS, cX, cY, X.d, n, opt)
+    _check(load_library().sigkernel_pairs(ctypes.byref(cX), ctypes.byref(cY), X.d, _dtype_code(X, Y), pa.data_ptr(),
+                                          pb.data_ptr(), n, ctypes.byref(opt), out.data_ptr(), ws.data_ptr(),
+                                          ws.numel(), _stream_ptr()))
+    return out
+
+
+def sigkernel_gram(X, Y=None, scheme="approx", degree=6, dyadic=0, compute="f64", sort=True,
+                   workspace: torch.Tensor | None = None, out: torch.Tensor | None = None,
+                   time_kernel: bool = False) -> torch.Tensor:
+    """G[a, b] = k_hat(X[a], Y[b]); with Y None (or Y is X) the symmetric Gram of X.
+
+    ``time_kernel`` records CUDA events around the wavefront kernel (see ``last_kernel_ms``)."""
+    sym = Y is None or Y is X
+    X = as_paths(X)
+    Y = X if sym else as_paths(Y)
+    flags = _flags(X, (FLAG_SYMMETRIC if sym else 0) | (0 if sort else FLAG_NO_SORT)
+                   | (FLAG_TIME_KERNEL if time_kernel else 0))
+    opt = _options(scheme, degree, dyadic, compute, flags)
+    cX, cY = _cpaths(X), _cpaths(Y)
+    G = out if out is not None else torch.empty(X.count, Y.count, dtype=torch.float64, device="cuda")
+    ws = workspace if workspace is not None else _workspace(OP_GRAM, cX, cY, X.d, -1, opt)
+    _check(load_library().sigkernel_gram(ctypes.byref(cX), ctypes.byref(cY), X.d, _dtype_code(X, Y),
+                                         ctypes.byref(opt), G.data_ptr(), ws.data_ptr(), ws.numel(), _stream_ptr()))
+    return G
+
+
+def gram_workspace(X, Y=None, scheme="approx", degree=6, dyadic=0, compute="f64") -> torch.Tensor:
+    """A workspace tensor sized for ``sigkernel_gram`` with these shapes (reusable across calls)."""
+    sym = Y is None or Y is X
+    X = as_paths(X)
+    Y = X if sym else as_paths(Y)
+    opt = _options(scheme, degree, dyadic, compute, _flags(X, FLAG_SYMMETRIC if sym else 0))
+    return _workspace(OP_GRAM, _cpaths(X), _cpaths(Y), X.d, -1, opt)
+
+
+def last_kernel_ms() -> float:
+    """Device milliseconds of the wavefront kernel of the last ``time_kernel=True`` call."""
+    return float(load_library().sigkernel_last_kernel_ms())
+
+
+def device_status() -> int:
+    """Synchronise the current stream and return (and clear) the device error word."""
+    return load_library().sigkernel_device_status(_stream_ptr())
+
+
+def version() -> int:
+    return load_library().sigkernel_version()

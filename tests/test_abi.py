@@ -1,0 +1,65 @@
+"""CPU checks of the C ABI: the library builds for sm_103a, loads, and exports every entry point
+declared in include/sigkernel.h; host-side argument checks answer without a GPU."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "sigkernel.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2502_08470_gb300 import build
+    path = build.build()
+    return ctypes.CDLL(path)
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(sigkernel_\w+)\s*\(", text)))
+
+
+def test_header_declares_the_entry_points():
+    names = declared_functions()
+    for required in ("sigkernel_pairs", "sigkernel_gram", "sigkernel_backward", "sigkernel_mmd2",
+                     "sigkernel_workspace_size", "sigkernel_device_status", "sigkernel_last_error"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_struct_layouts_match_binding():
+    from paper_2502_08470_gb300 import sigkernel as sk
+    assert ctypes.sizeof(sk._Options) == 32
+    assert ctypes.sizeof(sk._Paths) == 40
+
+
+def test_version_and_host_side_validation(lib):
+    from paper_2502_08470_gb300 import sigkernel as sk
+    lib.sigkernel_version.restype = ctypes.c_int
+    assert lib.sigkernel_version() >= 100
+    lib.sigkernel_workspace_size.restype = ctypes.c_size_t
+    lib.sigkernel_last_error.restype = ctypes.c_char_p
+    X = sk._Paths(0, 0, 0, 0, 0)
+    bad = sk._options("approx", 1)  # order N = 1 is below the Definition's N >= 2
+    n = lib.sigkernel_workspace_size(1, ctypes.byref(X), ctypes.byref(X), 2, -1, ctypes.byref(bad))
+    assert n == 0
+    assert b"order" in lib.sigkernel_last_error()
+    bad = sk._options("approx", 6, dyadic=12)
+    assert lib.sigkernel_workspace_size(1, ctypes.byref(X), ctypes.byref(X), 2, -1, ctypes.byref(bad)) == 0
+    bad = sk._options("approx", 6)
+    assert lib.sigkernel_workspace_size(1, ctypes.byref(X), ctypes.byref(X), 0, -1, ctypes.byref(bad)) == 0
+    assert b"d = 0" in lib.sigkernel_last_error()
+    # a call with invalid options returns before touching any device
+    lib.sigkernel_gram.restype = ctypes.c_int
+    bad = sk._options("interp", 20)
+    rc = lib.sigkernel_gram(ctypes.byref(X), ctypes.byref(X), 2, 0, ctypes.byref(bad), None, None,
+                            ctypes.c_size_t(0), None)
+    assert rc == -1
