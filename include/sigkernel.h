@@ -29,7 +29,7 @@
  *     host-side upper bound on the rows of any one path and `rows_total` the host-side row count
  *     off[count]; a path longer than max_len, with no row at all, or with rows outside
  *     [0, rows_total) sets the device error word (SK_ERR_BAD_LENGTH) and its outputs are NaN.
- *     (max_len << lambda) may not exceed 262144.
+ *     (max_len << lambda) may not exceed 131072.
  *   * Only the increment inner products M_ij = <dx_i, dy_j> enter any scheme (the explicit
  *     update of Section 3.2 depends on C_ij (s_{i+1}-s_i)(t_{j+1}-t_j) only), so no time
  *     partition is passed.

@@ -17,7 +17,7 @@ constexpr int kLamMax = 8;
 constexpr int kDMax = 64;
 constexpr int kJF32 = 6;         // interpolation: series terms beyond N kept in FP32
 constexpr int kJF64 = 10;        // ... and in FP64
-constexpr int kMaxRefined = 262144;  // bound on (rows per path) << lambda
+constexpr int kMaxRefined = 131072;  // bound on (rows per path) << lambda (keeps step counters in int32)
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kFwdWarps = 4;     // warps per block of the persistent wavefront kernels
 
