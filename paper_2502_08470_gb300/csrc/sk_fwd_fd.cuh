@@ -7,6 +7,13 @@
 // with alpha = 1 + m/2, beta = 1 (first order) or alpha = 1 + m/2 + m^2/12, beta = 1 - m^2/12
 // (second order).  All 4^lambda sub-cells of a cell share (alpha, beta).
 //
+// Difference form.  Writing v(I+1, J) = k(I+1, J) - k(I, J), the same update is
+//     v(I+1, J+1) = v(I+1, J) + (alpha - 1)(k(I+1, J) + k(I, J+1)) - (beta - 1) k(I, J),
+//     k(I+1, J+1) = k(I, J+1) + v(I+1, J+1).
+// A lane carries v for its rows along the sweep and rebuilds k upward from the node below, so
+// rounding in the long sweep direction is relative to |v| (small) rather than to |k|; in the
+// direct form every node's O(eps |k|) rounding reaches the whole quadrant above and to its right.
+//
 // Parallel layout.  One warp owns one pair.  Lane r owns R = min(2^lambda, 16) consecutive node
 // rows (a "row group"; all in one coarse row) and sweeps the refined columns; the top node of
 // its group moves one lane up per step by __shfl_up_sync, and lane 31's top nodes are handed to
@@ -66,11 +73,11 @@ __global__ void __launch_bounds__(kFwdWarps * 32) fwd_fd_kernel(Launch L, int64_
         const T* xbase = incX + P.xs * dpad;
         const T* ybase = incY + P.ys * dpad;
 
-        T col[R];   // k(gR + 1 + r, jj) for the lane's group g at its current column jj
+        T v[R];     // k(gR + 1 + r, jj) - k(gR + r, jj) for the lane's group g at its column jj
         T kb_prev = T(1), top = T(0);
         int ea = 0, eo = 0;
 #pragma unroll
-        for (int r = 0; r < R; ++r) col[r] = T(1);
+        for (int r = 0; r < R; ++r) v[r] = T(0);
         int jj = -lane, s = 0;
 
         for (int step = 0; step < nsteps; ++step) {
@@ -83,9 +90,9 @@ __global__ void __launch_bounds__(kFwdWarps * 32) fwd_fd_kernel(Launch L, int64_
                     if (s == 0) { kb = T(1); eb = 0; }       // row 0: k(s_0, .) = 1
                     else { kb = hbuf[jj]; if (kRescale) eb = ebuf[jj]; }
                 }
-                if (jj == 0) {                               // column 0: k(., t_0) = 1
+                if (jj == 0) {                               // column 0: k(., t_0) = 1, so v = 0
 #pragma unroll
-                    for (int r = 0; r < R; ++r) col[r] = T(1);
+                    for (int r = 0; r < R; ++r) v[r] = T(0);
                     kb_prev = T(1);
                     ea = 0;
                 }
@@ -95,47 +102,45 @@ __global__ void __launch_bounds__(kFwdWarps * 32) fwd_fd_kernel(Launch L, int64_
                     } else {
                         const T f = (ea - eb < -126) ? T(0) : fd_pow2<T>(ea - eb);
 #pragma unroll
-                        for (int r = 0; r < R; ++r) col[r] *= f;
+                        for (int r = 0; r < R; ++r) v[r] *= f;
                         kb_prev *= f;
                         ea = eb;
                     }
                 }
                 const T m = row_dot<T>(xbase + static_cast<int64_t>((g * R) >> lam) * dpad,
                                        ybase + static_cast<int64_t>(jj >> lam) * dpad, L.nvec) * sub;
-                T alpha = fma(m, T(0.5), T(1));
-                T beta = T(1);
-                if constexpr (ORDER == 2) {
-                    const T m2 = m * m * T(1.0 / 12.0);
-                    alpha += m2;
-                    beta -= m2;
-                }
-                T below_new = kb, below_old = kb_prev;
+                const T a1 = m * T(0.5);                     // alpha - 1
+                T m2 = T(0);                                 // (1 - beta) = alpha - 1 - m/2
+                if constexpr (ORDER == 2) m2 = m * m * T(1.0 / 12.0);
+                T k00 = kb_prev, k01 = kb;                   // k(I, J), k(I, J+1) for I = gR + r
 #pragma unroll
                 for (int r = 0; r < R; ++r) {
-                    const T old = col[r];
-                    T v = (old + below_new) * alpha;
-                    v = (ORDER == 2) ? fma(-below_old, beta, v) : v - below_old;
-                    col[r] = v;
-                    below_new = v;
-                    below_old = old;
+                    const T k10 = k00 + v[r];                // k(I+1, J)
+                    const T sum = k10 + k01;
+                    T d2 = a1 * sum;
+                    if constexpr (ORDER == 2) d2 = fma(m2, sum + k00, d2);
+                    v[r] += d2;
+                    const T k11 = k01 + v[r];                // k(I+1, J+1)
+                    k00 = k10;
+                    k01 = k11;
                 }
                 kb_prev = kb;
-                top = col[R - 1];
+                top = k01;
                 if (g == groups - 1 && jj == nJ - 1) {
-                    double v = static_cast<double>(top);
-                    if (kRescale) v = ldexp(v, ea);
-                    if (!isfinite(v)) record_error(SK_ERR_NONFINITE);
-                    write_result(L, item, P, v);
+                    double res = static_cast<double>(top);
+                    if (kRescale) res = ldexp(res, ea);
+                    if (!isfinite(res)) record_error(SK_ERR_NONFINITE);
+                    write_result(L, item, P, res);
                 }
                 if (kRescale) {
-                    const float mag = fmaxf(fabsf(static_cast<float>(col[0])), fabsf(static_cast<float>(top)));
+                    const float mag = fmaxf(fabsf(static_cast<float>(kb_prev)), fabsf(static_cast<float>(top)));
                     if (mag > 0x1p64f || (mag < 0x1p-64f && mag > 0.f)) {
                         const int sh = mag > 0x1p64f ? -64 : 64;
                         const T f = fd_pow2<T>(sh);
 #pragma unroll
-                        for (int r = 0; r < R; ++r) col[r] *= f;
+                        for (int r = 0; r < R; ++r) v[r] *= f;
                         kb_prev *= f;
-                        top = col[R - 1];
+                        top *= f;
                         ea -= sh;
                     }
                 }
