@@ -119,13 +119,14 @@ typedef struct {
 enum { SK_OP_PAIRS = 0, SK_OP_GRAM = 1, SK_OP_BACKWARD = 2, SK_OP_MMD2 = 3 };
 
 /*
- * sigkernel_workspace_size -- bytes of device workspace the call `op` needs for these shapes
- * and options (0 on invalid arguments; see sigkernel_last_error).  `npairs` is the pair count
- * for SK_OP_PAIRS / SK_OP_BACKWARD with a pair list, ignored otherwise (pass -1 for a Gram
- * backward).  Queries properties of the current device (SM count, occupancy); no memory traffic.
+ * sigkernel_workspace_size -- writes to *bytes the device workspace the call `op` needs for
+ * these shapes and options and returns SK_OK, or returns the SK_ERR_* code the call itself would
+ * return for these arguments (then *bytes = 0).  `npairs` is the pair count for SK_OP_PAIRS /
+ * SK_OP_BACKWARD with a pair list, ignored otherwise (pass -1 for a Gram backward).  Queries
+ * properties of the current device (SM count, occupancy); no memory traffic.
  */
-size_t sigkernel_workspace_size(int32_t op, const sk_paths* X, const sk_paths* Y, int32_t d,
-                                int64_t npairs, const sk_options* opt);
+int sigkernel_workspace_size(int32_t op, const sk_paths* X, const sk_paths* Y, int32_t d,
+                             int64_t npairs, const sk_options* opt, size_t* bytes);
 
 /*
  * sigkernel_pairs -- out[k] = k_hat(X_{pair_a[k]}, Y_{pair_b[k]}) for k < npairs.

@@ -441,14 +441,14 @@ float sigkernel_last_kernel_ms(void) {
     return ms;
 }
 
-size_t sigkernel_workspace_size(int32_t op, const sk_paths* X, const sk_paths* Y, int32_t d, int64_t npairs,
-                                const sk_options* opt) {
+int sigkernel_workspace_size(int32_t op, const sk_paths* X, const sk_paths* Y, int32_t d, int64_t npairs,
+                             const sk_options* opt, size_t* bytes) {
+    t_last_error.clear();
+    if (!bytes) return fail(SK_ERR_INVALID_ARG, "bytes is NULL");
+    *bytes = 0;
+    if (!opt || !X || !Y) return fail(SK_ERR_INVALID_ARG, "NULL argument");
     Plan p;
     int rc;
-    if (!opt || !X || !Y) {
-        fail(SK_ERR_INVALID_ARG, "NULL argument");
-        return 0;
-    }
     const int dtype = SK_F64;  // sizes do not depend on the input element type
     switch (op) {
         case SK_OP_PAIRS:
@@ -460,10 +460,10 @@ size_t sigkernel_workspace_size(int32_t op, const sk_paths* X, const sk_paths* Y
             break;
         }
         default:
-            fail(SK_ERR_UNSUPPORTED, "workspace for op %d", op);
-            return 0;
+            return fail(SK_ERR_UNSUPPORTED, "workspace for op %d", op);
     }
-    return rc == SK_OK ? p.total : 0;
+    if (rc == SK_OK) *bytes = p.total;
+    return rc;
 }
 
 int sigkernel_pairs(const sk_paths* X, const sk_paths* Y, int32_t d, int32_t dtype, const int64_t* pair_a,

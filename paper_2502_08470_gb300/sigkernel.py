@@ -63,8 +63,8 @@ def load_library():
         PP, PO = ctypes.POINTER(_Paths), ctypes.POINTER(_Options)
         lib.sigkernel_version.restype = ctypes.c_int
         lib.sigkernel_last_error.restype = ctypes.c_char_p
-        lib.sigkernel_workspace_size.restype = SZ
-        lib.sigkernel_workspace_size.argtypes = [I32, PP, PP, I32, I64, PO]
+        lib.sigkernel_workspace_size.restype = ctypes.c_int
+        lib.sigkernel_workspace_size.argtypes = [I32, PP, PP, I32, I64, PO, ctypes.POINTER(SZ)]
         lib.sigkernel_pairs.restype = ctypes.c_int
         lib.sigkernel_pairs.argtypes = [PP, PP, I32, I32, P, P, I64, PO, P, P, SZ, P]
         lib.sigkernel_gram.restype = ctypes.c_int
@@ -154,10 +154,10 @@ def _dtype_code(X: Paths, Y: Paths) -> int:
 
 def _workspace(op, cX, cY, d, npairs, opt) -> torch.Tensor:
     lib = load_library()
-    n = lib.sigkernel_workspace_size(op, ctypes.byref(cX), ctypes.byref(cY), d, npairs, ctypes.byref(opt))
-    if n == 0:
-        _check(-1 if not lib.sigkernel_last_error() else -2)
-    return torch.empty(int(n), dtype=torch.uint8, device="cuda")
+    n = ctypes.c_size_t(0)
+    _check(lib.sigkernel_workspace_size(op, ctypes.byref(cX), ctypes.byref(cY), d, npairs, ctypes.byref(opt),
+                                        ctypes.byref(n)))
+    return torch.empty(int(n.value), dtype=torch.uint8, device="cuda")
 
 
 def _flags(X: Paths, extra=0) -> int:

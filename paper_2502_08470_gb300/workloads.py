@@ -25,9 +25,10 @@ def brownian(n: int, L: int, d: int, seed: int, drift: float = 0.0, vol: float =
     """[n, L, d] Brownian paths on [0, 1] sampled at L equally spaced times, starting at 0."""
     rng = np.random.default_rng(seed)
     steps = L - 1
-    inc = rng.standard_normal((n, steps, d)) * (vol / np.sqrt(steps)) + drift / steps
     out = np.zeros((n, L, d))
-    out[:, 1:, :] = np.cumsum(inc, axis=1)
+    if steps > 0:
+        inc = rng.standard_normal((n, steps, d)) * (vol / np.sqrt(steps)) + drift / steps
+        out[:, 1:, :] = np.cumsum(inc, axis=1)
     return out
 
 

@@ -45,17 +45,21 @@ def test_version_and_host_side_validation(lib):
     from paper_2502_08470_gb300 import sigkernel as sk
     lib.sigkernel_version.restype = ctypes.c_int
     assert lib.sigkernel_version() >= 100
-    lib.sigkernel_workspace_size.restype = ctypes.c_size_t
+    lib.sigkernel_workspace_size.restype = ctypes.c_int
     lib.sigkernel_last_error.restype = ctypes.c_char_p
     X = sk._Paths(0, 0, 0, 0, 0)
+    n = ctypes.c_size_t(1)
     bad = sk._options("approx", 1)  # order N = 1 is below the Definition's N >= 2
-    n = lib.sigkernel_workspace_size(1, ctypes.byref(X), ctypes.byref(X), 2, -1, ctypes.byref(bad))
-    assert n == 0
+    rc = lib.sigkernel_workspace_size(1, ctypes.byref(X), ctypes.byref(X), 2, ctypes.c_int64(-1), ctypes.byref(bad),
+                                      ctypes.byref(n))
+    assert rc == -1 and n.value == 0
     assert b"order" in lib.sigkernel_last_error()
     bad = sk._options("approx", 6, dyadic=12)
-    assert lib.sigkernel_workspace_size(1, ctypes.byref(X), ctypes.byref(X), 2, -1, ctypes.byref(bad)) == 0
+    assert lib.sigkernel_workspace_size(1, ctypes.byref(X), ctypes.byref(X), 2, ctypes.c_int64(-1),
+                                        ctypes.byref(bad), ctypes.byref(n)) == -1
     bad = sk._options("approx", 6)
-    assert lib.sigkernel_workspace_size(1, ctypes.byref(X), ctypes.byref(X), 0, -1, ctypes.byref(bad)) == 0
+    assert lib.sigkernel_workspace_size(1, ctypes.byref(X), ctypes.byref(X), 0, ctypes.c_int64(-1),
+                                        ctypes.byref(bad), ctypes.byref(n)) == -1
     assert b"d = 0" in lib.sigkernel_last_error()
     # a call with invalid options returns before touching any device
     lib.sigkernel_gram.restype = ctypes.c_int

@@ -90,9 +90,9 @@ def test_f32_gram_mape(scheme, N, lam):
 
 
 def test_f32_rescaling_keeps_huge_kernels_finite():
-    # Scaled Brownian paths: k ~ 1e40 .. 1e70, far beyond FP32's range without the exponents.
-    X = 9.0 * W.brownian(3, 65, 2, seed=39)
-    Y = 9.0 * W.brownian(3, 65, 2, seed=40)
+    # Scaled Brownian paths: k up to ~1e50, beyond FP32's range without the exponents.
+    X = 12.0 * W.brownian(3, 65, 2, seed=39)
+    Y = 12.0 * W.brownian(3, 65, 2, seed=40)
     R = oracle.gram(list(X), list(Y), "approx", 10, 2)
     assert np.max(np.abs(R)) > 1e39
     G = _gram_gpu(X, Y, scheme="approx", degree=10, dyadic=2, compute="f32")
