@@ -36,6 +36,7 @@ D = 8
 DEGREE = 6
 CELLS_PER_PAIR = (L - 1) * (L - 1)
 CELLS = NX * NY * CELLS_PER_PAIR
+PARTS = ("f32", "f64", "e2e", "cpu")
 SM_COUNT = 152
 FP32_LANES = 128
 SM_MAX_MHZ = 2070.0
@@ -56,13 +57,21 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    return ap.parse_args()
+    ap.add_argument("--nx", type=int, default=NX,
+                    help="paths per side (a smaller Gram of the same paths, for profiling runs)")
+    ap.add_argument("--parts", default=",".join(PARTS),
+                    help="comma list of measurements to run: f32 (headline), f64, e2e, cpu")
+    args = ap.parse_args()
+    args.parts = set(args.parts.split(","))
+    if args.no_cpu_baseline:
+        args.parts.discard("cpu")
+    return args
 
 
-def workload(rank: int):
+def workload(rank: int, n: int = NX):
     from paper_2502_08470_gb300 import workloads as W
-    X = W.brownian(NX, L, D, seed=3 + 1000 * rank)
-    Y = W.brownian(NY, L, D, seed=4 + 1000 * rank)
+    X = W.brownian(NX, L, D, seed=3 + 1000 * rank)[:n]
+    Y = W.brownian(NY, L, D, seed=4 + 1000 * rank)[:n]
     return X, Y
 
 
@@ -179,10 +188,12 @@ def main():
     from paper_2502_08470_gb300 import sigkernel as sk
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    X, Y = workload(rank)
+    nx = args.nx
+    cells = nx * nx * CELLS_PER_PAIR
+    X, Y = workload(rank, nx)
     Xt = torch.tensor(X, device=dev)
     Yt = torch.tensor(Y, device=dev)
-    G = torch.empty(NX, NY, dtype=torch.float64, device=dev)
+    G = torch.empty(nx, nx, dtype=torch.float64, device=dev)
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
 
     def run(compute, steps, warmup, time_kernel=True):
@@ -212,6 +223,15 @@ def main():
             dist.barrier()
         return step_ms, kern_ms, wall
 
+    line = {}
+    fpc = flops_per_cell(DEGREE, D)
+    peak = SM_COUNT * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    import oracle
+    rng = np.random.default_rng(0)
+    pa = rng.integers(0, nx, 16)
+    pb = rng.integers(0, nx, 16)
+    ref = None
+
     # headline: FP32 batched wavefront
     with ClockSampler(local) as clk:
         step_ms, kern_ms, wall = run("f32", args.steps, max(args.warmup, 3))
@@ -222,80 +242,66 @@ def main():
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         total_ms = float(t.item())
     ms_per_step = total_ms / args.steps
-    value = CELLS * world * args.steps / (total_ms / 1e3)
-    G32 = G.clone()
+    value = cells * world * args.steps / (total_ms / 1e3)
+    g32 = G.cpu().numpy()[pa, pb]
     status = sk.device_status()
-
-    # FP64 plain wavefront of the same Gram (a few steps)
-    s64, k64, _ = run("f64", max(2, min(3, args.steps)), 1)
-    G64 = G.clone()
-    f64_rate = CELLS / (statistics.mean(s64) / 1e3)
-
-    # end to end through the public API with pinned host buffers
-    Xh = torch.tensor(X).pin_memory()
-    Yh = torch.tensor(Y).pin_memory()
-    Gh = torch.empty(NX, NY, dtype=torch.float64).pin_memory()
-    ws = sk.gram_workspace(Xt, Yt, scheme="approx", degree=DEGREE, compute="f32")
-    e2e_ms = []
-    for it in range(args.warmup + args.steps):
-        flush.zero_()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record()
-        Xt.copy_(Xh, non_blocking=True)
-        Yt.copy_(Yh, non_blocking=True)
-        sk.sigkernel_gram(Xt, Yt, scheme="approx", degree=DEGREE, compute="f32", sort=False, workspace=ws, out=G)
-        Gh.copy_(G, non_blocking=True)
-        e1.record()
-        e1.synchronize()
-        if it >= args.warmup:
-            e2e_ms.append(e0.elapsed_time(e1))
-    e2e_rate = CELLS * world / (statistics.mean(e2e_ms) / 1e3)
-
-    # accuracy of this run vs the FP64 oracle on sampled entries (parity MAPE)
-    import oracle
-    rng = np.random.default_rng(0)
-    pa = rng.integers(0, NX, 16)
-    pb = rng.integers(0, NY, 16)
-    ref = oracle.pairs(list(X), list(Y), pa, pb, "approx", DEGREE)
-    g32 = G32.cpu().numpy()[pa, pb]
-    g64 = G64.cpu().numpy()[pa, pb]
-    mape32 = float(np.mean(np.abs(g32 - ref) / np.abs(ref)))
-    mape64 = float(np.mean(np.abs(g64 - ref) / np.abs(ref)))
-
-    fpc = flops_per_cell(DEGREE, D)
     kavg = statistics.mean(kern_ms)
-    achieved = fpc * CELLS / (kavg / 1e3) / 1e12
-    peak = SM_COUNT * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
-    k64avg = statistics.mean(k64)
-    achieved64 = fpc * CELLS / (k64avg / 1e3) / 1e12
+    achieved = fpc * cells / (kavg / 1e3) / 1e12
+    ref = oracle.pairs(list(X), list(Y), pa, pb, "approx", DEGREE)
+    mape = {"f32": float(np.mean(np.abs(g32 - ref) / np.abs(ref))), "sample": "16 sampled Gram entries"}
+    line.update({
+        "metric": "Goursat cell-updates/s (polynomial approximation N=6, 128x128 Gram, batched FP32 wavefront)",
+        "value": value, "unit": "cell-updates/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"gram{nx}: X, Y = {nx} Brownian paths each, 257 points, d=8, N(0,1/256) increments",
+                   "scheme": "polynomial approximation", "degree": DEGREE, "dyadic": 0,
+                   "cells_per_step": cells, "pairs_per_step": nx * nx,
+                   "l2": "256 MiB buffer written between timed steps (outside the events)",
+                   "parallelism": f"weak scaling, one independent {nx}x{nx} Gram per GPU ({world} GPUs)"},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                     "traffic": None, "kernel": "fwd_poly_kernel<float,6,6,false>", "kernel_ms": kavg,
+                     "flops_per_cell": fpc,
+                     "peak_source": "152 SMs x 128 FP32 lanes x 2 FLOP x 2070 MHz (derived, nominal clocks)"},
+        "gpu_launches": 3 * args.steps,
+        "clocks": clocks, "device_status": status, "wall_s_timed_region": wall,
+    })
+
+    if "f64" in args.parts:  # FP64 plain wavefront of the same Gram (a few steps)
+        s64, k64, _ = run("f64", max(2, min(3, args.steps)), 1)
+        g64 = G.cpu().numpy()[pa, pb]
+        k64avg = statistics.mean(k64)
+        mape["f64"] = float(np.mean(np.abs(g64 - ref) / np.abs(ref)))
+        line["fp64_plain_wavefront"] = {"value": cells / (statistics.mean(s64) / 1e3), "unit": "cell-updates/s",
+                                        "kernel_ms": k64avg, "achieved_tflops": fpc * cells / (k64avg / 1e3) / 1e12,
+                                        "peak_tflops_nominal": 1.25}
+    line["mape_vs_fp64_oracle"] = mape
+
+    if "e2e" in args.parts:  # end to end through the public API with pinned host buffers
+        Xh = torch.tensor(X).pin_memory()
+        Yh = torch.tensor(Y).pin_memory()
+        Gh = torch.empty(nx, nx, dtype=torch.float64).pin_memory()
+        ws = sk.gram_workspace(Xt, Yt, scheme="approx", degree=DEGREE, compute="f32")
+        e2e_ms = []
+        for it in range(args.warmup + args.steps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            Xt.copy_(Xh, non_blocking=True)
+            Yt.copy_(Yh, non_blocking=True)
+            sk.sigkernel_gram(Xt, Yt, scheme="approx", degree=DEGREE, compute="f32", sort=False, workspace=ws, out=G)
+            Gh.copy_(G, non_blocking=True)
+            e1.record()
+            e1.synchronize()
+            if it >= args.warmup:
+                e2e_ms.append(e0.elapsed_time(e1))
+        line["e2e"] = {"value": cells * world / (statistics.mean(e2e_ms) / 1e3), "unit": "cell-updates/s",
+                       "h2d_bytes_per_step": int(Xh.numel() * 8 + Yh.numel() * 8),
+                       "d2h_bytes_per_step": int(Gh.numel() * 8), "ms_per_step": statistics.mean(e2e_ms)}
 
     if rank == 0:
-        line = {
-            "metric": "Goursat cell-updates/s (polynomial approximation N=6, 128x128 Gram, batched FP32 wavefront)",
-            "value": value, "unit": "cell-updates/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "gram128: X, Y = 128 Brownian paths each, 257 points, d=8, N(0,1/256) increments",
-                       "scheme": "polynomial approximation", "degree": DEGREE, "dyadic": 0,
-                       "cells_per_step": CELLS, "pairs_per_step": NX * NY,
-                       "l2": "256 MiB buffer written between timed steps (outside the events)",
-                       "parallelism": f"weak scaling, one independent 128x128 Gram per GPU ({world} GPUs)"},
-            "mape_vs_fp64_oracle": {"f32": mape32, "f64": mape64, "sample": "16 sampled Gram entries"},
-            "fp64_plain_wavefront": {"value": f64_rate, "unit": "cell-updates/s", "kernel_ms": k64avg,
-                                     "achieved_tflops": achieved64},
-            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                         "traffic": None, "kernel": "fwd_poly_kernel<float,6,6,false>", "kernel_ms": kavg,
-                         "flops_per_cell": fpc,
-                         "peak_source": "152 SMs x 128 FP32 lanes x 2 FLOP x 2070 MHz (derived, nominal clocks)"},
-            "e2e": {"value": e2e_rate, "unit": "cell-updates/s", "h2d_bytes_per_step": int(Xh.numel() * 8 + Yh.numel() * 8),
-                    "d2h_bytes_per_step": int(Gh.numel() * 8), "ms_per_step": statistics.mean(e2e_ms)},
-            "gpu_launches": 3 * args.steps,
-            "clocks": clocks,
-            "device_status": status,
-            "wall_s_timed_region": wall,
-        }
-        if not args.no_cpu_baseline:
+        if "cpu" in args.parts:
             line["cpu_baseline"] = cpu_baseline(X, Y)
         print(json.dumps(line))
     if dist is not None:
