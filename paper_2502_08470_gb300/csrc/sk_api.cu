@@ -1,5 +1,6 @@
 // Host side of the C ABI (include/sigkernel.h): argument checks, workspace layout, constant
 // tables, the increment and scheduling kernels, and dispatch to the wavefront kernels.
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -7,6 +8,7 @@
 #include <mutex>
 #include <string>
 
+#include "sk_bwd_poly.cuh"
 #include "sk_common.cuh"
 #include "sk_dispatch.h"
 
@@ -282,7 +284,8 @@ int plan_forward(const sk_paths* X, const sk_paths* Y, int32_t d, int32_t dtype,
     int width = 1;  // values handed from strip to strip per refined column
     if (poly) {
         p.kern = fwd_poly_kernel_ptr(p.T, o->scheme == SK_POLY_INTERP, o->degree);
-        width = o->degree + 1;
+        const int hw = p.T ? 4 : 2;  // hand-off entries are padded to whole 16-byte vectors
+        width = (o->degree + 1 + hw - 1) / hw * hw;
     } else {
         p.kern = fwd_fd_kernel_ptr(p.T, o->scheme == SK_FD2 ? 2 : 1, lam);
         width = 1;
@@ -422,6 +425,331 @@ int64_t gram_items(const sk_paths* X, const sk_paths* Y, bool sym) {
     return sym ? X->count * (X->count + 1) / 2 : X->count * Y->count;
 }
 
+// ------------------------------------------------------------------------------------------
+// Backward: d k / d increments (FP64, accumulated with atomics) -> d k / d rows.
+// ------------------------------------------------------------------------------------------
+__global__ void inc_to_row_grad_kernel(const double* __restrict__ ginc, const int64_t* __restrict__ off,
+                                       int64_t count, int64_t rows_total, int64_t max_len, int d, int dpad,
+                                       int inc_mode, double* __restrict__ grad) {
+    for (int64_t a = blockIdx.x; a < count; a += gridDim.x) {
+        const int64_t r0 = off[a], r1 = off[a + 1], n = r1 - r0;
+        if (r0 < 0 || r1 > rows_total || n < (inc_mode ? 0 : 1) || n > max_len) continue;
+        for (int64_t idx = threadIdx.x; idx < n * d; idx += blockDim.x) {
+            const int64_t p = idx / d;
+            const int c = static_cast<int>(idx - p * d);
+            double v;
+            if (inc_mode) {
+                v = ginc[(r0 + p) * dpad + c];
+            } else {  // x_p enters dx_{p-1} = x_p - x_{p-1} with +1 and dx_p = x_{p+1} - x_p with -1
+                v = (p >= 1 ? ginc[(r0 + p - 1) * dpad + c] : 0.0) - (p + 1 < n ? ginc[(r0 + p) * dpad + c] : 0.0);
+            }
+            grad[(r0 + p) * d + c] += v;
+        }
+    }
+}
+
+struct BwdPlan {
+    Plan f;                    // forward plan (increments, queue, order offsets)
+    const void* kern;
+    int K, dmax, stack_bytes, smem_bytes;
+    int64_t cols_max, strips_max, seg_max;
+    int64_t off_fbuf, off_fexp, off_rbuf, off_rexp, off_ybar, slot_bytes;
+    size_t off_gincx, off_gincy, off_scratch, total;
+};
+
+int plan_backward(const sk_paths* X, const sk_paths* Y, int32_t d, int32_t dtype, const sk_options* o, int mode,
+                  int64_t npairs, BwdPlan& b) {
+    int rc = plan_forward(X, Y, d, dtype, o, mode, npairs, b.f);
+    if (rc != SK_OK) return rc;
+    if (o->scheme != SK_POLY_APPROX)
+        return fail(SK_ERR_UNSUPPORTED, "sigkernel_backward supports the polynomial approximation scheme");
+    const Plan& p = b.f;
+    b.dmax = p.dpad <= 8 ? 8 : (p.dpad <= 32 ? 32 : 0);
+    if (!b.dmax) return fail(SK_ERR_UNSUPPORTED, "sigkernel_backward supports d <= 32");
+    b.kern = p.T ? bwd_approx_ptr_f32(o->degree, b.dmax, &b.stack_bytes)
+                 : bwd_approx_ptr_f64(o->degree, b.dmax, &b.stack_bytes);
+    if (!b.kern) return fail(SK_ERR_UNSUPPORTED, "no adjoint kernel for order %d", o->degree);
+    b.K = p.T ? bwd_segment_f32() : bwd_segment_f64();
+    b.smem_bytes = kFwdWarps * (b.stack_bytes + (p.T ? bwd_xacc_bytes<float>(p.dpad) : bwd_xacc_bytes<double>(p.dpad)));
+    const int lam = o->dyadic, esize = p.T ? 4 : 8, N = o->degree;
+    const int64_t rows_max = std::max<int64_t>(X->max_len << lam, 1);
+    b.cols_max = std::max<int64_t>(Y->max_len << lam, 1);
+    b.strips_max = (rows_max + 31) / 32;
+    const int64_t period = std::max<int64_t>(b.cols_max, 32);
+    const int64_t nsteps = (b.strips_max - 1) * period + 31 + b.cols_max;
+    b.seg_max = (nsteps + b.K - 1) / b.K;
+    int64_t off = 0;
+    off += b.seg_max * (2 * N + 2) * 32 * esize + b.seg_max * 32 * 4;
+    off = static_cast<int64_t>(align256(off));
+    b.off_fbuf = off;
+    off += static_cast<int64_t>(align256(std::max<int64_t>(b.strips_max - 1, 1) * b.cols_max * (N + 1) * esize));
+    b.off_fexp = off;
+    off += static_cast<int64_t>(align256(std::max<int64_t>(b.strips_max - 1, 1) * b.cols_max * 4));
+    b.off_rbuf = off;
+    off += static_cast<int64_t>(align256(b.cols_max * (N + 1) * esize));
+    b.off_rexp = off;
+    off += static_cast<int64_t>(align256(b.cols_max * 4));
+    b.off_ybar = off;
+    off += static_cast<int64_t>(align256(std::max<int64_t>(Y->max_len, 1) * p.dpad * esize));
+    b.slot_bytes = off;
+    int dev = 0, sms = 0, per_sm = 0;
+    SK_CUDA(cudaGetDevice(&dev));
+    SK_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    SK_CUDA(cudaFuncSetAttribute(b.kern, cudaFuncAttributeMaxDynamicSharedMemorySize, b.smem_bytes));
+    SK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, b.kern, p.threads, b.smem_bytes));
+    if (per_sm < 1) return fail(SK_ERR_UNSUPPORTED, "adjoint kernel does not fit an SM (%d bytes shared)", b.smem_bytes);
+    const int64_t want = (npairs + kFwdWarps - 1) / kFwdWarps;
+    const int64_t cap = static_cast<int64_t>(sms) * per_sm;
+    b.f.blocks = static_cast<int>(std::max<int64_t>(1, std::min(want, cap)));
+    // workspace: forward parts up to the scratch, then gradient accumulators, then the slots
+    size_t o2 = p.off_scratch;
+    b.off_gincx = o2;
+    o2 += align256(static_cast<size_t>(X->rows_total) * p.dpad * sizeof(double));
+    b.off_gincy = p.same_xy ? b.off_gincx : o2;
+    if (!p.same_xy) o2 += align256(static_cast<size_t>(Y->rows_total) * p.dpad * sizeof(double));
+    b.off_scratch = o2;
+    o2 += static_cast<size_t>(b.f.blocks) * kFwdWarps * static_cast<size_t>(b.slot_bytes);
+    b.total = o2 + 256;
+    return SK_OK;
+}
+
+// Runs the adjoint for one call; gradients w.r.t. increments are ADDED to gincX / gincY (which
+// may alias).  `base` is the aligned workspace laid out by plan_backward.
+int launch_backward(const sk_paths* X, const sk_paths* Y, int32_t d, int32_t dtype, const sk_options* o, int mode,
+                    const int64_t* pa, const int64_t* pb, int64_t npairs, const double* gout, int64_t ldo,
+                    const BwdPlan& b, char* base, double* gincX, double* gincY, cudaStream_t st) {
+    const Plan& p = b.f;
+    const int inc_mode = (o->flags & SK_FLAG_INCREMENTS) ? 1 : 0;
+    int rc = p.T ? launch_increments<float>(X, d, dtype, inc_mode, p.dpad, base + p.off_incx, st)
+                 : launch_increments<double>(X, d, dtype, inc_mode, p.dpad, base + p.off_incx, st);
+    if (rc == SK_OK && !p.same_xy)
+        rc = p.T ? launch_increments<float>(Y, d, dtype, inc_mode, p.dpad, base + p.off_incy, st)
+                 : launch_increments<double>(Y, d, dtype, inc_mode, p.dpad, base + p.off_incy, st);
+    if (rc != SK_OK) return rc;
+    BwdParams B;
+    memset(&B, 0, sizeof(B));
+    Launch& L = B.L;
+    L.X = PathSet{base + p.off_incx, X->offsets, X->count, X->max_len, X->rows_total};
+    L.Y = PathSet{base + p.off_incy, Y->offsets, Y->count, Y->max_len, Y->rows_total};
+    L.nvec = p.nvec;
+    L.dpad = p.dpad;
+    L.inc_mode = inc_mode;
+    L.lam = o->dyadic;
+    L.mode = mode;
+    L.npairs = npairs;
+    L.pair_a = pa;
+    L.pair_b = pb;
+    L.queue = reinterpret_cast<unsigned int*>(base + p.off_queue);
+    L.out = nullptr;
+    L.ldo = ldo;
+    L.scratch = base + b.off_scratch;
+    L.scratch_stride = b.slot_bytes;
+    L.tau = 1.0f;
+    L.order = nullptr;
+    B.gout = gout;
+    B.gincX = gincX;
+    B.gincY = gincY;
+    B.cols_max = b.cols_max;
+    B.strips_max = b.strips_max;
+    B.seg_max = b.seg_max;
+    B.off_fbuf = b.off_fbuf;
+    B.off_fexp = b.off_fexp;
+    B.off_rbuf = b.off_rbuf;
+    B.off_rexp = b.off_rexp;
+    B.off_ybar = b.off_ybar;
+    SK_CUDA(cudaMemsetAsync(base + p.off_queue, 0, 256 + align256(2 * 65 * sizeof(unsigned int)), st));
+    if (!(o->flags & SK_FLAG_NO_SORT) && npairs > 1) {
+        unsigned int* hist = reinterpret_cast<unsigned int*>(base + p.off_hist);
+        int32_t* order = reinterpret_cast<int32_t*>(base + p.off_order);
+        int sb = static_cast<int>(std::min<int64_t>((npairs + 255) / 256, 4096));
+        sched_hist_kernel<<<sb, 256, 0, st>>>(L, hist);
+        sched_scan_kernel<<<1, 32, 0, st>>>(hist, hist + 65);
+        sched_scatter_kernel<<<sb, 256, 0, st>>>(L, hist + 65, order);
+        SK_CUDA(cudaGetLastError());
+        L.order = order;
+    }
+    void* args[] = {&B};
+    const bool timed = (o->flags & SK_FLAG_TIME_KERNEL) != 0;
+    if (timed) {
+        if (!t_ev0) SK_CUDA(cudaEventCreate(&t_ev0));
+        if (!t_ev1) SK_CUDA(cudaEventCreate(&t_ev1));
+        SK_CUDA(cudaEventRecord(t_ev0, st));
+    }
+    SK_CUDA(cudaLaunchKernel(b.kern, dim3(p.blocks), dim3(p.threads), args, b.smem_bytes, st));
+    if (timed) {
+        SK_CUDA(cudaEventRecord(t_ev1, st));
+        t_timed = true;
+    }
+    return SK_OK;
+}
+
+int convert_grad(const sk_paths* S, int32_t d, int dpad, int inc_mode, const double* ginc, double* grad,
+                 cudaStream_t st) {
+    if (!grad || S->count == 0) return SK_OK;
+    int blocks = static_cast<int>(S->count < 65535 ? S->count : 65535);
+    inc_to_row_grad_kernel<<<blocks, 128, 0, st>>>(ginc, S->offsets, S->count, S->rows_total, S->max_len, d, dpad,
+                                                   inc_mode, grad);
+    SK_CUDA(cudaGetLastError());
+    return SK_OK;
+}
+
+int run_backward(const sk_paths* X, const sk_paths* Y, int32_t d, int32_t dtype, const sk_options* o,
+                 const int64_t* pa, const int64_t* pb, int64_t npairs, const double* gout, double* gX, double* gY,
+                 void* ws, size_t ws_bytes, void* stream) {
+    const bool gram = (pa == nullptr);
+    const bool sym = gram && (o->flags & SK_FLAG_SYMMETRIC);
+    const int mode = gram ? (sym ? kGramUpper : kGramFull) : kPairsList;
+    if (gram) npairs = gram_items(X, Y, sym);
+    BwdPlan b;
+    int rc = plan_backward(X, Y, d, dtype, o, mode, npairs, b);
+    if (rc != SK_OK) return rc;
+    if (b.f.same_xy && gY && gY != gX)
+        return fail(SK_ERR_INVALID_ARG, "X and Y are the same paths: pass grad_Y = NULL or grad_Y = grad_X");
+    if (npairs == 0) return SK_OK;
+    if (!gout) return fail(SK_ERR_INVALID_ARG, "grad_out is NULL");
+    if ((rc = ensure_tables()) != SK_OK) return rc;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    bool own = false;
+    if (!ws) {
+        SK_CUDA(cudaMallocAsync(&ws, b.total, st));
+        own = true;
+    } else if (ws_bytes < b.total) {
+        return fail(SK_ERR_WORKSPACE, "workspace %zu bytes < %zu required", ws_bytes, b.total);
+    }
+    char* base = reinterpret_cast<char*>((reinterpret_cast<uintptr_t>(ws) + 255) / 256 * 256);
+    double* gincX = reinterpret_cast<double*>(base + b.off_gincx);
+    double* gincY = reinterpret_cast<double*>(base + b.off_gincy);
+    SK_CUDA(cudaMemsetAsync(gincX, 0, static_cast<size_t>(X->rows_total) * b.f.dpad * sizeof(double), st));
+    if (!b.f.same_xy)
+        SK_CUDA(cudaMemsetAsync(gincY, 0, static_cast<size_t>(Y->rows_total) * b.f.dpad * sizeof(double), st));
+    rc = launch_backward(X, Y, d, dtype, o, mode, pa, pb, npairs, gout, Y->count, b, base, gincX, gincY, st);
+    if (rc != SK_OK) return rc;
+    const int inc_mode = (o->flags & SK_FLAG_INCREMENTS) ? 1 : 0;
+    if ((rc = convert_grad(X, d, b.f.dpad, inc_mode, gincX, gX, st)) != SK_OK) return rc;
+    if (!b.f.same_xy && (rc = convert_grad(Y, d, b.f.dpad, inc_mode, gincY, gY, st)) != SK_OK) return rc;
+    if (own) SK_CUDA(cudaFreeAsync(ws, st));
+    return SK_OK;
+}
+
+// ------------------------------------------------------------------------------------------
+// MMD^2 from the three Gram blocks; weights of its backward.
+// ------------------------------------------------------------------------------------------
+__global__ void mmd2_reduce_kernel(const double* Kaa, int64_t na, const double* Kbb, int64_t nb, const double* Kab,
+                                   int unbiased, double* out) {
+    __shared__ double part[3][256];
+    double s[3] = {0.0, 0.0, 0.0};
+    for (int64_t i = threadIdx.x; i < na * na; i += blockDim.x)
+        if (!unbiased || (i / na) != (i % na)) s[0] += Kaa[i];
+    for (int64_t i = threadIdx.x; i < nb * nb; i += blockDim.x)
+        if (!unbiased || (i / nb) != (i % nb)) s[1] += Kbb[i];
+    for (int64_t i = threadIdx.x; i < na * nb; i += blockDim.x) s[2] += Kab[i];
+    for (int q = 0; q < 3; ++q) part[q][threadIdx.x] = s[q];
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {  // fixed-order tree: deterministic
+        if (static_cast<int>(threadIdx.x) < w)
+            for (int q = 0; q < 3; ++q) part[q][threadIdx.x] += part[q][threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const double daa = unbiased ? static_cast<double>(na) * (na - 1) : static_cast<double>(na) * na;
+        const double dbb = unbiased ? static_cast<double>(nb) * (nb - 1) : static_cast<double>(nb) * nb;
+        const double maa = part[0][0] / daa, mbb = part[1][0] / dbb, mab = part[2][0] / (static_cast<double>(na) * nb);
+        out[0] = maa + mbb - 2.0 * mab;
+        out[1] = maa;
+        out[2] = mbb;
+        out[3] = mab;
+    }
+}
+
+__global__ void fill_weights_kernel(double* W, int64_t n, int64_t m, double v, int zero_diag) {
+    for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n * m;
+         i += static_cast<int64_t>(gridDim.x) * blockDim.x)
+        W[i] = (zero_diag && (i / m) == (i % m)) ? 0.0 : v;
+}
+
+int run_mmd2(const sk_paths* A, const sk_paths* Bp, int32_t d, int32_t dtype, const sk_options* o, double* out,
+             double* gA, double* gB, void* ws, size_t ws_bytes, void* stream) {
+    if (!A || !Bp || !o || !out) return fail(SK_ERR_INVALID_ARG, "NULL argument");
+    if (A->count < 1 || Bp->count < 1) return fail(SK_ERR_INVALID_ARG, "MMD^2 needs non-empty path sets");
+    const bool unb = (o->flags & SK_FLAG_UNBIASED) != 0;
+    if (unb && (A->count < 2 || Bp->count < 2)) return fail(SK_ERR_INVALID_ARG, "unbiased MMD^2 needs >= 2 paths per set");
+    sk_options os = *o;
+    os.flags = (o->flags & (SK_FLAG_INCREMENTS | SK_FLAG_NO_SORT | SK_FLAG_TIME_KERNEL)) | SK_FLAG_SYMMETRIC;
+    sk_options of = os;
+    of.flags &= ~SK_FLAG_SYMMETRIC;
+    const bool grads = gA || gB;
+    // size every sub-call; they run one after another on the same stream in one workspace
+    Plan paa, pbb, pab;
+    BwdPlan baa, bbb, bab;
+    int rc;
+    if ((rc = plan_forward(A, A, d, dtype, &os, kGramUpper, gram_items(A, A, true), paa)) != SK_OK) return rc;
+    if ((rc = plan_forward(Bp, Bp, d, dtype, &os, kGramUpper, gram_items(Bp, Bp, true), pbb)) != SK_OK) return rc;
+    if ((rc = plan_forward(A, Bp, d, dtype, &of, kGramFull, gram_items(A, Bp, false), pab)) != SK_OK) return rc;
+    size_t sub = std::max(paa.total, std::max(pbb.total, pab.total));
+    if (grads) {
+        if ((rc = plan_backward(A, A, d, dtype, &os, kGramUpper, gram_items(A, A, true), baa)) != SK_OK) return rc;
+        if ((rc = plan_backward(Bp, Bp, d, dtype, &os, kGramUpper, gram_items(Bp, Bp, true), bbb)) != SK_OK) return rc;
+        if ((rc = plan_backward(A, Bp, d, dtype, &of, kGramFull, gram_items(A, Bp, false), bab)) != SK_OK) return rc;
+        sub = std::max(sub, std::max(baa.total, std::max(bbb.total, bab.total)));
+    }
+    const int64_t na = A->count, nb = Bp->count;
+    const size_t gram_bytes = align256((na * na + nb * nb + na * nb) * sizeof(double));
+    const size_t w_bytes = grads ? gram_bytes : 0;
+    const int dpad = paa.dpad;
+    const size_t ginc_bytes = grads ? align256(static_cast<size_t>(A->rows_total) * dpad * 8) +
+                                          align256(static_cast<size_t>(Bp->rows_total) * dpad * 8)
+                                    : 0;
+    const size_t total = gram_bytes + w_bytes + ginc_bytes + sub + 512;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    bool own = false;
+    if (!ws) {
+        SK_CUDA(cudaMallocAsync(&ws, total, st));
+        own = true;
+    } else if (ws_bytes < total) {
+        return fail(SK_ERR_WORKSPACE, "workspace %zu bytes < %zu required", ws_bytes, total);
+    }
+    char* base = reinterpret_cast<char*>((reinterpret_cast<uintptr_t>(ws) + 255) / 256 * 256);
+    double* Kaa = reinterpret_cast<double*>(base);
+    double* Kbb = Kaa + na * na;
+    double* Kab = Kbb + nb * nb;
+    double* Waa = reinterpret_cast<double*>(base + gram_bytes);
+    double* Wbb = Waa + na * na;
+    double* Wab = Wbb + nb * nb;
+    double* gincA = reinterpret_cast<double*>(base + gram_bytes + w_bytes);
+    double* gincB = reinterpret_cast<double*>(base + gram_bytes + w_bytes + (grads ? align256(static_cast<size_t>(A->rows_total) * dpad * 8) : 0));
+    char* sub_ws = base + gram_bytes + w_bytes + ginc_bytes;
+    if ((rc = run_forward(A, A, d, dtype, &os, kGramUpper, nullptr, nullptr, gram_items(A, A, true), Kaa, na, sub_ws, sub, st)) != SK_OK) return rc;
+    if ((rc = run_forward(Bp, Bp, d, dtype, &os, kGramUpper, nullptr, nullptr, gram_items(Bp, Bp, true), Kbb, nb, sub_ws, sub, st)) != SK_OK) return rc;
+    if ((rc = run_forward(A, Bp, d, dtype, &of, kGramFull, nullptr, nullptr, gram_items(A, Bp, false), Kab, nb, sub_ws, sub, st)) != SK_OK) return rc;
+    mmd2_reduce_kernel<<<1, 256, 0, st>>>(Kaa, na, Kbb, nb, Kab, unb ? 1 : 0, out);
+    SK_CUDA(cudaGetLastError());
+    if (grads) {
+        const double waa = unb ? 1.0 / (static_cast<double>(na) * (na - 1)) : 1.0 / (static_cast<double>(na) * na);
+        const double wbb = unb ? 1.0 / (static_cast<double>(nb) * (nb - 1)) : 1.0 / (static_cast<double>(nb) * nb);
+        const double wab = -2.0 / (static_cast<double>(na) * nb);
+        fill_weights_kernel<<<64, 256, 0, st>>>(Waa, na, na, waa, unb ? 1 : 0);
+        fill_weights_kernel<<<64, 256, 0, st>>>(Wbb, nb, nb, wbb, unb ? 1 : 0);
+        fill_weights_kernel<<<64, 256, 0, st>>>(Wab, na, nb, wab, 0);
+        SK_CUDA(cudaGetLastError());
+        SK_CUDA(cudaMemsetAsync(gincA, 0, ginc_bytes, st));
+        char* sb = reinterpret_cast<char*>((reinterpret_cast<uintptr_t>(sub_ws) + 255) / 256 * 256);
+        if ((rc = launch_backward(A, A, d, dtype, &os, kGramUpper, nullptr, nullptr, gram_items(A, A, true), Waa, na, baa, sb, gincA, gincA, st)) != SK_OK) return rc;
+        if ((rc = launch_backward(Bp, Bp, d, dtype, &os, kGramUpper, nullptr, nullptr, gram_items(Bp, Bp, true), Wbb, nb, bbb, sb, gincB, gincB, st)) != SK_OK) return rc;
+        if ((rc = launch_backward(A, Bp, d, dtype, &of, kGramFull, nullptr, nullptr, gram_items(A, Bp, false), Wab, nb, bab, sb, gincA, gincB, st)) != SK_OK) return rc;
+        const int inc_mode = (o->flags & SK_FLAG_INCREMENTS) ? 1 : 0;
+        if (gA) {
+            SK_CUDA(cudaMemsetAsync(gA, 0, static_cast<size_t>(A->rows_total) * d * sizeof(double), st));
+            if ((rc = convert_grad(A, d, dpad, inc_mode, gincA, gA, st)) != SK_OK) return rc;
+        }
+        if (gB) {
+            SK_CUDA(cudaMemsetAsync(gB, 0, static_cast<size_t>(Bp->rows_total) * d * sizeof(double), st));
+            if ((rc = convert_grad(Bp, d, dpad, inc_mode, gincB, gB, st)) != SK_OK) return rc;
+        }
+    }
+    if (own) SK_CUDA(cudaFreeAsync(ws, st));
+    return SK_OK;
+}
+
 }  // namespace
 }  // namespace sk
 
@@ -459,6 +787,40 @@ int sigkernel_workspace_size(int32_t op, const sk_paths* X, const sk_paths* Y, i
             rc = plan_forward(X, Y, d, dtype, opt, sym ? kGramUpper : kGramFull, gram_items(X, Y, sym), p);
             break;
         }
+        case SK_OP_BACKWARD: {
+            const bool gram = npairs < 0;
+            const bool sym = gram && (opt->flags & SK_FLAG_SYMMETRIC);
+            BwdPlan b;
+            rc = plan_backward(X, Y, d, dtype, opt, gram ? (sym ? kGramUpper : kGramFull) : kPairsList,
+                               gram ? gram_items(X, Y, sym) : npairs, b);
+            if (rc == SK_OK) *bytes = b.total;
+            return rc;
+        }
+        case SK_OP_MMD2: {
+            // sized by a dry run of the same planning as sigkernel_mmd2 (X = A, Y = B)
+            Plan pa, pb, pc;
+            BwdPlan ba, bb, bc;
+            sk_options os = *opt;
+            os.flags = (opt->flags & (SK_FLAG_INCREMENTS | SK_FLAG_NO_SORT | SK_FLAG_TIME_KERNEL)) | SK_FLAG_SYMMETRIC;
+            sk_options of = os;
+            of.flags &= ~SK_FLAG_SYMMETRIC;
+            if ((rc = plan_forward(X, X, d, dtype, &os, kGramUpper, gram_items(X, X, true), pa)) != SK_OK) return rc;
+            if ((rc = plan_forward(Y, Y, d, dtype, &os, kGramUpper, gram_items(Y, Y, true), pb)) != SK_OK) return rc;
+            if ((rc = plan_forward(X, Y, d, dtype, &of, kGramFull, gram_items(X, Y, false), pc)) != SK_OK) return rc;
+            size_t sub = std::max(pa.total, std::max(pb.total, pc.total));
+            if (opt->scheme == SK_POLY_APPROX && d <= 32) {
+                if ((rc = plan_backward(X, X, d, dtype, &os, kGramUpper, gram_items(X, X, true), ba)) != SK_OK) return rc;
+                if ((rc = plan_backward(Y, Y, d, dtype, &os, kGramUpper, gram_items(Y, Y, true), bb)) != SK_OK) return rc;
+                if ((rc = plan_backward(X, Y, d, dtype, &of, kGramFull, gram_items(X, Y, false), bc)) != SK_OK) return rc;
+                sub = std::max(sub, std::max(ba.total, std::max(bb.total, bc.total)));
+            }
+            const int64_t na = X->count, nb = Y->count;
+            const size_t gram_bytes = align256((na * na + nb * nb + na * nb) * sizeof(double));
+            const size_t ginc = align256(static_cast<size_t>(X->rows_total) * pa.dpad * 8) +
+                                align256(static_cast<size_t>(Y->rows_total) * pa.dpad * 8);
+            *bytes = 2 * gram_bytes + ginc + sub + 512;
+            return SK_OK;
+        }
         default:
             return fail(SK_ERR_UNSUPPORTED, "workspace for op %d", op);
     }
@@ -485,14 +847,20 @@ int sigkernel_gram(const sk_paths* X, const sk_paths* Y, int32_t d, int32_t dtyp
                        Y->count, workspace, workspace_bytes, stream);
 }
 
-int sigkernel_backward(const sk_paths*, const sk_paths*, int32_t, int32_t, const int64_t*, const int64_t*, int64_t,
-                       const sk_options*, const double*, double*, double*, void*, size_t, void*) {
-    return fail(SK_ERR_UNSUPPORTED, "sigkernel_backward is not built yet");
+int sigkernel_backward(const sk_paths* X, const sk_paths* Y, int32_t d, int32_t dtype, const int64_t* pair_a,
+                       const int64_t* pair_b, int64_t npairs, const sk_options* opt, const double* grad_out,
+                       double* grad_X, double* grad_Y, void* workspace, size_t workspace_bytes, void* stream) {
+    t_last_error.clear();
+    if (!opt || !X || !Y) return fail(SK_ERR_INVALID_ARG, "NULL argument");
+    if (pair_a && (!pair_b || npairs < 0)) return fail(SK_ERR_INVALID_ARG, "bad pair list");
+    return run_backward(X, Y, d, dtype, opt, pair_a, pair_b, npairs, grad_out, grad_X, grad_Y, workspace,
+                        workspace_bytes, stream);
 }
 
-int sigkernel_mmd2(const sk_paths*, const sk_paths*, int32_t, int32_t, const sk_options*, double*, double*, double*,
-                   void*, size_t, void*) {
-    return fail(SK_ERR_UNSUPPORTED, "sigkernel_mmd2 is not built yet");
+int sigkernel_mmd2(const sk_paths* A, const sk_paths* B, int32_t d, int32_t dtype, const sk_options* opt, double* out,
+                   double* grad_A, double* grad_B, void* workspace, size_t workspace_bytes, void* stream) {
+    t_last_error.clear();
+    return run_mmd2(A, B, d, dtype, opt, out, grad_A, grad_B, workspace, workspace_bytes, stream);
 }
 
 int sigkernel_device_status(void* stream) {

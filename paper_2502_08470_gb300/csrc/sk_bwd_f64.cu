@@ -1,0 +1,39 @@
+// Instantiations of the approximation-scheme adjoint wavefront (double cell updates).
+#include "sk_bwd_poly.cuh"
+#include "sk_dispatch.h"
+
+namespace sk {
+
+const void* bwd_approx_ptr_f64(int N, int dmax, int* stack_bytes) {
+    if (dmax == 8) switch (N) {
+        case 2: *stack_bytes = bwd_stack_bytes<double, 2, 4>(); return reinterpret_cast<const void*>(&bwd_approx_kernel<double, 2, 4, 8>);
+        case 3: *stack_bytes = bwd_stack_bytes<double, 3, 4>(); return reinterpret_cast<const void*>(&bwd_approx_kernel<double, 3, 4, 8>);
+        case 4: *stack_bytes = bwd_stack_bytes<double, 4, 4>(); return reinterpret_cast<const void*>(&bwd_approx_kernel<double, 4, 4, 8>);
+        case 5: *stack_bytes = bwd_stack_bytes<double, 5, 4>(); return reinterpret_cast<const void*>(&bwd_approx_kernel<double, 5, 4, 8>);
+        case 6: *stack_bytes = bwd_stack_bytes<double, 6, 4>(); return reinterpret_cast<const void*>(&bwd_approx_kernel<double, 6, 4, 8>);
+        case 7: *stack_bytes = bwd_stack_bytes<double, 7, 4>(); return reinterpret_cast<const void*>(&bwd_approx_kernel<double, 7, 4, 8>);
+        case 8: *stack_bytes = bwd_stack_bytes<double, 8, 4>(); return reinterpret_cast<const void*>(&bwd_approx_kernel<double, 8, 4, 8>);
+        case 9: *stack_bytes = bwd_stack_bytes<double, 9, 4>(); return reinterpret_cast<const void*>(&bwd_approx_kernel<double, 9, 4, 8>);
+        case 10: *stack_bytes = bwd_stack_bytes<double, 10, 4>(); return reinterpret_cast<const void*>(&bwd_approx_kernel<double, 10, 4, 8>);
+        case 12: *stack_bytes = bwd_stack_bytes<double, 12, 4>(); return reinterpret_cast<const void*>(&bwd_approx_kernel<double, 12, 4, 8>);
+        default: break;
+    }
+    if (dmax == 32) switch (N) {
+        case 2: *stack_bytes = bwd_stack_bytes<double, 2, 4>(); return reinterpret_cast<const void*>(&bwd_approx_kernel<double, 2, 4, 32>);
+        case 3: *stack_bytes = bwd_stack_bytes<double, 3, 4>(); return reinterpret_cast<const void*>(&bwd_approx_kernel<double, 3, 4, 32>);
+        case 4: *stack_bytes = bwd_stack_bytes<double, 4, 4>(); return reinterpret_cast<const void*>(&bwd_approx_kernel<double, 4, 4, 32>);
+        case 5: *stack_bytes = bwd_stack_bytes<double, 5, 4>(); return reinterpret_cast<const void*>(&bwd_approx_kernel<double, 5, 4, 32>);
+        case 6: *stack_bytes = bwd_stack_bytes<double, 6, 4>(); return reinterpret_cast<const void*>(&bwd_approx_kernel<double, 6, 4, 32>);
+        case 7: *stack_bytes = bwd_stack_bytes<double, 7, 4>(); return reinterpret_cast<const void*>(&bwd_approx_kernel<double, 7, 4, 32>);
+        case 8: *stack_bytes = bwd_stack_bytes<double, 8, 4>(); return reinterpret_cast<const void*>(&bwd_approx_kernel<double, 8, 4, 32>);
+        case 9: *stack_bytes = bwd_stack_bytes<double, 9, 4>(); return reinterpret_cast<const void*>(&bwd_approx_kernel<double, 9, 4, 32>);
+        case 10: *stack_bytes = bwd_stack_bytes<double, 10, 4>(); return reinterpret_cast<const void*>(&bwd_approx_kernel<double, 10, 4, 32>);
+        case 12: *stack_bytes = bwd_stack_bytes<double, 12, 4>(); return reinterpret_cast<const void*>(&bwd_approx_kernel<double, 12, 4, 32>);
+        default: break;
+    }
+    return nullptr;
+}
+
+int bwd_segment_f64() { return 4; }
+
+}  // namespace sk

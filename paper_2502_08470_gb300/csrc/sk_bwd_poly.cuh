@@ -1,0 +1,531 @@
+// Reverse-mode derivative (adjoint wavefront) of the polynomial approximation scheme for
+// sm_103a.  The paper defines no gradient; this is the exact adjoint of the scheme's own
+// arithmetic (Definition "def:polyapproxscheme" in the factorial-scaled form of sk_fwd_poly.cuh).
+//
+// Adjoint of one cell.  With e_m = M^m/m!, H_nk = n!/(n+k)!, ha_n = sum_{k>=1} b_k H_nk,
+// hb_n = sum_{k>=1} a_k H_nk and the forward map a'_n = sum_{k<=n} a_k e_{n-k} + e_n ha_n,
+// b'_n = sum_{k<=n} b_k e_{n-k} + e_n hb_n, the adjoints (abar' of a', bbar' of b') give
+//     abar_k = sum_{n>=k} abar'_n e_{n-k} + [k>=1] sum_n (bbar'_n e_n) H_nk
+//     bbar_k = sum_{n>=k} bbar'_n e_{n-k} + [k>=1] sum_n (abar'_n e_n) H_nk
+//     ebar_m = sum_{n>=m} (abar'_n a_{n-m} + bbar'_n b_{n-m}) + abar'_m ha_m + bbar'_m hb_m
+//     Mbar   = sum_{m>=1} ebar_m e_{m-1}                       (d e_m / dM = e_{m-1})
+// The endpoint 1/2 sum_n (a_n + b_n)/n! seeds abar' = bbar' = 1/(2 n!) at the last cell.  A sub-cell
+// of P_lambda has M = M_ij / 4^lambda, so dk/dM_ij sums the sub-cell Mbar / 4^lambda, and
+// d k / d dx_i = sum_j (dk/dM_ij) dy_j, d k / d dy_j = sum_i (dk/dM_ij) dx_i.
+//
+// Schedule (one warp per pair, same lane/strip layout as the forward kernel):
+//   F  forward replay of the whole pair; every strip's hand-off column and, every K steps, each
+//      lane's cell inputs (an antidiagonal checkpoint) go to per-warp scratch.
+//   R  for each K-step segment from the last to the first: re-run its K forward steps from the
+//      checkpoint into a shared-memory stack, then walk them backward applying the adjoint; the
+//      right-edge adjoint moves one lane down per step (__shfl_down_sync) together with the
+//      column partial sums of dk/dy, lane 0 hands it to lane 31 of the strip below through a
+//      per-warp buffer, and each lane keeps dk/dx of its row in registers.
+// FP32 keeps power-of-two exponents per lane for the forward values (as in the forward kernel)
+// and, separately, for the adjoints; dk/dM is accumulated relative to 2^E(k) of the pair.
+#pragma once
+
+#include <type_traits>
+
+#include "sk_fwd_poly.cuh"
+
+namespace sk {
+
+constexpr int kZeroExp = -(1 << 20);  // exponent tag of an all-zero adjoint
+
+struct BwdParams {
+    Launch L;                 // pairs, increments, queue, order, per-warp scratch
+    const double* gout;       // upstream gradient (pairs: [npairs]; Gram: [X.count][Y.count])
+    double* gincX;            // d L / d increments of X, [X.rows_total][dpad]
+    double* gincY;            // same for Y (may alias gincX)
+    int64_t cols_max;         // refined columns a hand-off buffer holds
+    int64_t strips_max;       // strips of the longest x path
+    int64_t seg_max;          // K-step segments of the longest pair
+    int64_t off_fbuf, off_fexp, off_rbuf, off_rexp, off_ybar;  // byte offsets inside a warp slot
+};
+
+template <typename T>
+__device__ __forceinline__ T pow2c(int e) {  // 2^e, or 0 below the normal range
+    if constexpr (std::is_same<T, float>::value) return e < -126 ? 0.f : pow2f(e > 127 ? 127 : e);
+    else return e < -1022 ? 0.0 : pow2d(e > 1023 ? 1023 : e);
+}
+
+template <typename T, int N>
+__device__ __forceinline__ void cell_adjoint(const T (&a)[N + 1], const T (&b)[N + 1], const T (&e)[N + 1],
+                                             const T (&ga)[N + 1], const T (&gb)[N + 1], T (&ra)[N + 1],
+                                             T (&rb)[N + 1], T& mbar) {
+    T al[N + 1], be[N + 1];
+#pragma unroll
+    for (int n = 0; n <= N; ++n) { al[n] = ga[n] * e[n]; be[n] = gb[n] * e[n]; }
+    // abar_k, bbar_k
+#pragma unroll
+    for (int k = 0; k <= N; ++k) {
+        T va = T(0), vb = T(0);
+        if (k >= 1) {
+#pragma unroll
+            for (int n = 0; n <= N; ++n) {
+                va = fma(be[n], Tab<T>::hank(n, k), va);
+                vb = fma(al[n], Tab<T>::hank(n, k), vb);
+            }
+        }
+#pragma unroll
+        for (int n = k; n <= N; ++n) {
+            va = fma(ga[n], e[n - k], va);
+            vb = fma(gb[n], e[n - k], vb);
+        }
+        ra[k] = va;
+        rb[k] = vb;
+    }
+    // ebar_m for m >= 1 and Mbar
+    T mb = T(0);
+#pragma unroll
+    for (int m = 1; m <= N; ++m) {
+        T ha = b[1] * Tab<T>::hank(m, 1);
+        T hb = a[1] * Tab<T>::hank(m, 1);
+#pragma unroll
+        for (int k = 2; k <= N; ++k) {
+            ha = fma(b[k], Tab<T>::hank(m, k), ha);
+            hb = fma(a[k], Tab<T>::hank(m, k), hb);
+        }
+        T eb = fma(ga[m], ha, gb[m] * hb);
+#pragma unroll
+        for (int n = m; n <= N; ++n) {
+            eb = fma(ga[n], a[n - m], eb);
+            eb = fma(gb[n], b[n - m], eb);
+        }
+        mb = fma(eb, e[m - 1], mb);
+    }
+    mbar = mb;
+}
+
+// Shared memory of one warp: the K-step stack (a[N+1], b[N+1], M per lane, plus exponents),
+// then each lane's dk/dx accumulator of its row ([32][dpad + 4] floats; the pad spreads the
+// lanes' 16-byte accesses over all banks).
+template <typename T, int N, int K>
+__host__ __device__ constexpr int bwd_stack_bytes() {
+    return K * (2 * N + 3) * 32 * static_cast<int>(sizeof(T)) + K * 32 * 4;
+}
+template <typename T>
+__host__ __device__ constexpr int bwd_xacc_bytes(int dpad) { return 32 * (dpad + 4) * static_cast<int>(sizeof(T)); }
+
+template <typename T, int N, int K>
+constexpr int bwd_min_blocks() {
+    return sizeof(T) == 8 ? 1 : 2;
+}
+
+template <typename T, int N, int K, int DMAX>
+__global__ void __launch_bounds__(kFwdWarps * 32, (bwd_min_blocks<T, N, K>()))
+    bwd_approx_kernel(BwdParams B) {
+    constexpr bool kRescale = std::is_same<T, float>::value;
+    using V = typename Vec<T>::type;
+    constexpr int W = Vec<T>::W;
+    const Launch& L = B.L;
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    const int64_t slot = static_cast<int64_t>(blockIdx.x) * (blockDim.x >> 5) + wib;
+    char* base = static_cast<char*>(L.scratch) + slot * L.scratch_stride;
+    // checkpoints: [seg][2N+2][32] T then [seg][32] int
+    T* ckpt = reinterpret_cast<T*>(base);
+    int* ckpt_e = reinterpret_cast<int*>(ckpt + B.seg_max * (2 * N + 2) * 32);
+    T* fbuf = reinterpret_cast<T*>(base + B.off_fbuf);          // [strip][col][N+1]
+    int* fexp = reinterpret_cast<int*>(base + B.off_fexp);      // [strip][col]
+    T* rbuf = reinterpret_cast<T*>(base + B.off_rbuf);          // [col][N+1]
+    int* rexp = reinterpret_cast<int*>(base + B.off_rexp);      // [col]
+    T* ybar = reinterpret_cast<T*>(base + B.off_ybar);          // [coarse col][dpad]
+    const int dpad = L.dpad;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    unsigned char* wsm = smem_raw + wib * (bwd_stack_bytes<T, N, K>() + bwd_xacc_bytes<T>(dpad));
+    T* stk = reinterpret_cast<T*>(wsm);
+    int* stk_e = reinterpret_cast<int*>(stk + K * (2 * N + 3) * 32);
+    T* xacc = reinterpret_cast<T*>(wsm + bwd_stack_bytes<T, N, K>()) + lane * (dpad + 4);
+    const T* __restrict__ incX = static_cast<const T*>(L.X.inc);
+    const T* __restrict__ incY = static_cast<const T*>(L.Y.inc);
+
+    for (;;) {
+        const int64_t item = next_item(L);
+        if (item < 0) break;
+        const PairDesc P = decode_pair(L, item);
+        if (P.lx < 0 || P.ly < 0) {
+            if (lane == 0) record_error(SK_ERR_BAD_LENGTH);
+            continue;
+        }
+        if (P.lx == 0 || P.ly == 0) continue;  // k = 1 does not depend on the paths
+        double gbar;
+        if (L.mode == kPairsList) gbar = B.gout[item];
+        else if (L.mode == kGramFull) gbar = B.gout[P.a * L.ldo + P.b];
+        else gbar = B.gout[P.a * L.ldo + P.b] + (P.a != P.b ? B.gout[P.b * L.ldo + P.a] : 0.0);
+        if (gbar == 0.0) continue;
+
+        const int lam = L.lam;
+        const int rows = static_cast<int>(P.lx << lam);
+        const int cols = static_cast<int>(P.ly << lam);
+        const int period = cols > 32 ? cols : 32;
+        const int nstrips = (rows + 31) >> 5;
+        const int last_lane = (rows - 1) - ((nstrips - 1) << 5);
+        const int nsteps = (nstrips - 1) * period + last_lane + cols;
+        const int nseg = (nsteps + K - 1) / K;
+        const T sub = pow2t<T>(-2 * lam);
+        const T* xbase = incX + P.xs * dpad;
+        const T* ybase = incY + P.ys * dpad;
+
+        // ------------------------------------------------------------------ phase F
+        T a[N + 1], bo[N + 1];
+#pragma unroll
+        for (int n = 0; n <= N; ++n) { a[n] = T(0); bo[n] = T(0); }
+        int ea = 0, eo = 0, ek = 0;
+        int jj = -lane, s = 0;
+        for (int step = 0; step < nsteps; ++step) {
+            T b[N + 1];
+#pragma unroll
+            for (int n = 0; n <= N; ++n) b[n] = __shfl_up_sync(kFull, bo[n], 1);
+            int eb = kRescale ? __shfl_up_sync(kFull, eo, 1) : 0;
+            const int row = (s << 5) + lane;
+            const bool active = jj >= 0 && jj < cols && row < rows;
+            if (active) {
+                if (lane == 0) {
+                    if (s == 0) {
+#pragma unroll
+                        for (int n = 0; n <= N; ++n) b[n] = (n == 0) ? T(1) : T(0);
+                        eb = 0;
+                    } else {
+                        const T* src = fbuf + (static_cast<int64_t>(s - 1) * B.cols_max + jj) * (N + 1);
+#pragma unroll
+                        for (int n = 0; n <= N; ++n) b[n] = src[n];
+                        if (kRescale) eb = fexp[static_cast<int64_t>(s - 1) * B.cols_max + jj];
+                    }
+                }
+                if (jj == 0) {
+#pragma unroll
+                    for (int n = 0; n <= N; ++n) a[n] = (n == 0) ? T(1) : T(0);
+                    ea = 0;
+                }
+                if (kRescale && ea != eb) {
+                    if (ea > eb) {
+                        const T f = pow2c<T>(eb - ea);
+#pragma unroll
+                        for (int n = 0; n <= N; ++n) b[n] *= f;
+                    } else {
+                        const T f = pow2c<T>(ea - eb);
+#pragma unroll
+                        for (int n = 0; n <= N; ++n) a[n] *= f;
+                        ea = eb;
+                    }
+                }
+            }
+            if (step % K == 0) {  // antidiagonal checkpoint: this step's cell inputs
+                T* cp = ckpt + static_cast<int64_t>(step / K) * (2 * N + 2) * 32;
+#pragma unroll
+                for (int n = 0; n <= N; ++n) {
+                    cp[n * 32 + lane] = a[n];
+                    cp[(N + 1 + n) * 32 + lane] = b[n];
+                }
+                ckpt_e[static_cast<int64_t>(step / K) * 32 + lane] = ea;
+            }
+            if (active) {
+                const T M = row_dot<T>(xbase + static_cast<int64_t>(row >> lam) * dpad,
+                                       ybase + static_cast<int64_t>(jj >> lam) * dpad, L.nvec) * sub;
+                T e[N + 1], ct[N + 1], cr[N + 1];
+                build_exp_series<T, N>(M, L.tau, e);
+                cell_series<T, N, N, false>(a, b, e, ct, cr);
+                if (row == rows - 1 && jj == cols - 1) {
+                    double v = 0.5 * (series_at_one<T, N>(ct) + series_at_one<T, N>(cr));
+                    int e2 = 0;
+                    if (v != 0.0) frexp(v, &e2);
+                    ek = ea + e2;
+                }
+#pragma unroll
+                for (int n = 0; n <= N; ++n) { a[n] = ct[n]; bo[n] = cr[n]; }
+                if (kRescale) {
+                    const float mag = fmaxf(fabsf(static_cast<float>(a[0])), fabsf(static_cast<float>(bo[0])));
+                    if (mag > 0x1p64f) {
+#pragma unroll
+                        for (int n = 0; n <= N; ++n) { a[n] *= pow2t<T>(-64); bo[n] *= pow2t<T>(-64); }
+                        ea += 64;
+                    } else if (mag < 0x1p-64f) {
+                        float full = 0.f;
+#pragma unroll
+                        for (int n = 0; n <= N; ++n)
+                            full = fmaxf(full, fmaxf(fabsf(static_cast<float>(a[n])), fabsf(static_cast<float>(bo[n]))));
+                        if (full < 0x1p-64f && full > 0.f) {
+#pragma unroll
+                            for (int n = 0; n <= N; ++n) { a[n] *= pow2t<T>(64); bo[n] *= pow2t<T>(64); }
+                            ea -= 64;
+                        }
+                    }
+                }
+                eo = ea;
+                if (lane == 31 && s + 1 < nstrips) {
+                    T* dst = fbuf + (static_cast<int64_t>(s) * B.cols_max + jj) * (N + 1);
+#pragma unroll
+                    for (int n = 0; n <= N; ++n) dst[n] = bo[n];
+                    if (kRescale) fexp[static_cast<int64_t>(s) * B.cols_max + jj] = eo;
+                }
+            }
+            __syncwarp();
+            if (++jj == period) { jj = 0; ++s; }
+        }
+        ek = __shfl_sync(kFull, ek, last_lane);
+        for (int64_t i = lane; i < P.ly * dpad; i += 32) ybar[i] = T(0);
+        __syncwarp();
+
+        // ------------------------------------------------------------------ phase R
+        T gra[N + 1], gbo[N + 1];  // adjoint of the lane's a (row state) and of its last b output
+        int gea = kZeroExp, gbe = kZeroExp;
+        T ysum[DMAX];
+#pragma unroll
+        for (int n = 0; n <= N; ++n) { gra[n] = T(0); gbo[n] = T(0); }
+#pragma unroll
+        for (int c = 0; c < DMAX; ++c) ysum[c] = T(0);
+        for (int c = 0; c < dpad; ++c) xacc[c] = T(0);
+
+        for (int g = nseg - 1; g >= 0; --g) {
+            const int t0 = g * K;
+            const int tn = min(K, nsteps - t0);
+            // re-run the segment's forward steps into the stack
+            {
+                const T* cp = ckpt + static_cast<int64_t>(g) * (2 * N + 2) * 32;
+                T ra[N + 1], rb[N + 1], rbo[N + 1];
+#pragma unroll
+                for (int n = 0; n <= N; ++n) {
+                    ra[n] = cp[n * 32 + lane];
+                    rb[n] = cp[(N + 1 + n) * 32 + lane];
+                    rbo[n] = T(0);
+                }
+                int rea = ckpt_e[static_cast<int64_t>(g) * 32 + lane], reo = 0;
+                int tt = t0 - lane;
+                int rs = tt >= 0 ? tt / period : 0;
+                int rj = tt >= 0 ? tt - rs * period : tt;
+#pragma unroll 1
+                for (int k = 0; k < K; ++k) {
+                    if (k < tn) {
+                        const int row = (rs << 5) + lane;
+                        const bool active = rj >= 0 && rj < cols && row < rows;
+                        if (k > 0) {
+                            int eb = kRescale ? __shfl_up_sync(kFull, reo, 1) : 0;
+#pragma unroll
+                            for (int n = 0; n <= N; ++n) rb[n] = __shfl_up_sync(kFull, rbo[n], 1);
+                            if (active) {
+                                if (lane == 0) {
+                                    if (rs == 0) {
+#pragma unroll
+                                        for (int n = 0; n <= N; ++n) rb[n] = (n == 0) ? T(1) : T(0);
+                                        eb = 0;
+                                    } else {
+                                        const T* src = fbuf + (static_cast<int64_t>(rs - 1) * B.cols_max + rj) * (N + 1);
+#pragma unroll
+                                        for (int n = 0; n <= N; ++n) rb[n] = src[n];
+                                        if (kRescale) eb = fexp[static_cast<int64_t>(rs - 1) * B.cols_max + rj];
+                                    }
+                                }
+                                if (rj == 0) {
+#pragma unroll
+                                    for (int n = 0; n <= N; ++n) ra[n] = (n == 0) ? T(1) : T(0);
+                                    rea = 0;
+                                }
+                                if (kRescale && rea != eb) {
+                                    if (rea > eb) {
+                                        const T f = pow2c<T>(eb - rea);
+#pragma unroll
+                                        for (int n = 0; n <= N; ++n) rb[n] *= f;
+                                    } else {
+                                        const T f = pow2c<T>(rea - eb);
+#pragma unroll
+                                        for (int n = 0; n <= N; ++n) ra[n] *= f;
+                                        rea = eb;
+                                    }
+                                }
+                            }
+                        }
+                        T M = T(0);
+                        if (active)
+                            M = row_dot<T>(xbase + static_cast<int64_t>(row >> lam) * dpad,
+                                           ybase + static_cast<int64_t>(rj >> lam) * dpad, L.nvec) * sub;
+                        T* sk_ = stk + k * (2 * N + 3) * 32;
+#pragma unroll
+                        for (int n = 0; n <= N; ++n) {
+                            sk_[n * 32 + lane] = ra[n];
+                            sk_[(N + 1 + n) * 32 + lane] = rb[n];
+                        }
+                        sk_[(2 * N + 2) * 32 + lane] = M;
+                        stk_e[k * 32 + lane] = rea;
+                        if (active) {
+                            T e[N + 1], ct[N + 1], cr[N + 1];
+                            build_exp_series<T, N>(M, L.tau, e);
+                            cell_series<T, N, N, false>(ra, rb, e, ct, cr);
+#pragma unroll
+                            for (int n = 0; n <= N; ++n) { ra[n] = ct[n]; rbo[n] = cr[n]; }
+                            if (kRescale) {
+                                const float mag = fmaxf(fabsf(static_cast<float>(ra[0])), fabsf(static_cast<float>(rbo[0])));
+                                if (mag > 0x1p64f) {
+#pragma unroll
+                                    for (int n = 0; n <= N; ++n) { ra[n] *= pow2t<T>(-64); rbo[n] *= pow2t<T>(-64); }
+                                    rea += 64;
+                                } else if (mag < 0x1p-64f) {
+                                    float full = 0.f;
+#pragma unroll
+                                    for (int n = 0; n <= N; ++n)
+                                        full = fmaxf(full, fmaxf(fabsf(static_cast<float>(ra[n])),
+                                                                 fabsf(static_cast<float>(rbo[n]))));
+                                    if (full < 0x1p-64f && full > 0.f) {
+#pragma unroll
+                                        for (int n = 0; n <= N; ++n) { ra[n] *= pow2t<T>(64); rbo[n] *= pow2t<T>(64); }
+                                        rea -= 64;
+                                    }
+                                }
+                            }
+                            reo = rea;
+                        }
+                        if (++rj == period) { rj = 0; ++rs; }
+                    }
+                }
+            }
+            __syncwarp();
+            // walk the segment backward
+#pragma unroll 1
+            for (int k = K - 1; k >= 0; --k) {
+                if (k < tn) {
+                    const int t = t0 + k;
+                    const int tt = t - lane;
+                    const int rs = tt >= 0 ? tt / period : 0;
+                    const int rj = tt >= 0 ? tt - rs * period : tt;
+                    const int row = (rs << 5) + lane;
+                    const bool active = rj >= 0 && rj < cols && row < rows;
+                    T gb_in[N + 1];
+#pragma unroll
+                    for (int n = 0; n <= N; ++n) gb_in[n] = __shfl_down_sync(kFull, gbo[n], 1);
+                    int gbe_in = __shfl_down_sync(kFull, gbe, 1);
+#pragma unroll
+                    for (int c = 0; c < DMAX; ++c) ysum[c] = __shfl_down_sync(kFull, ysum[c], 1);
+                    if (active) {
+                        if (row == rows - 1) {             // no row above: the top edge is final
+#pragma unroll
+                            for (int n = 0; n <= N; ++n) gb_in[n] = T(0);
+                            gbe_in = kZeroExp;
+                        } else if (lane == 31) {           // from lane 0 of the strip above
+                            const T* src = rbuf + static_cast<int64_t>(rj) * (N + 1);
+#pragma unroll
+                            for (int n = 0; n <= N; ++n) gb_in[n] = src[n];
+                            gbe_in = kRescale ? rexp[rj] : 0;
+                        }
+                        if (row == rows - 1 || lane == 31) {
+#pragma unroll
+                            for (int c = 0; c < DMAX; ++c) ysum[c] = T(0);
+                        }
+                        T ga_in[N + 1];
+                        int gae_in = gea;
+#pragma unroll
+                        for (int n = 0; n <= N; ++n) ga_in[n] = gra[n];
+                        if (rj == cols - 1) {              // right edge of the grid: no cell to the right
+#pragma unroll
+                            for (int n = 0; n <= N; ++n) ga_in[n] = T(0);
+                            gae_in = kZeroExp;
+                        }
+                        if (row == rows - 1 && rj == cols - 1) {  // seed from the endpoint average
+#pragma unroll
+                            for (int n = 0; n <= N; ++n) {
+                                ga_in[n] = static_cast<T>(0.5 * c_rfact_d[n]);
+                                gb_in[n] = ga_in[n];
+                            }
+                            gae_in = 0;
+                            gbe_in = 0;
+                        }
+                        int eg = kRescale ? max(gae_in, gbe_in) : 0;
+                        if (kRescale) {
+                            if (gae_in != eg) {
+                                const T f = pow2c<T>(gae_in - eg);
+#pragma unroll
+                                for (int n = 0; n <= N; ++n) ga_in[n] *= f;
+                            }
+                            if (gbe_in != eg) {
+                                const T f = pow2c<T>(gbe_in - eg);
+#pragma unroll
+                                for (int n = 0; n <= N; ++n) gb_in[n] *= f;
+                            }
+                        }
+                        const T* sk_ = stk + k * (2 * N + 3) * 32;
+                        T fa[N + 1], fb[N + 1], e[N + 1];
+#pragma unroll
+                        for (int n = 0; n <= N; ++n) {
+                            fa[n] = sk_[n * 32 + lane];
+                            fb[n] = sk_[(N + 1 + n) * 32 + lane];
+                        }
+                        const T M = sk_[(2 * N + 2) * 32 + lane];
+                        const int ef = stk_e[k * 32 + lane];
+                        build_exp_series<T, N>(M, L.tau, e);
+                        T mbar;
+                        cell_adjoint<T, N>(fa, fb, e, ga_in, gb_in, gra, gbo, mbar);
+                        // dk/dM relative to 2^ek, per coarse cell
+                        const T mrel = mbar * pow2c<T>(eg + ef - ek - 2 * lam);
+                        {
+                            const V* yv = reinterpret_cast<const V*>(ybase + static_cast<int64_t>(rj >> lam) * dpad);
+                            const V* xv = reinterpret_cast<const V*>(xbase + static_cast<int64_t>(row >> lam) * dpad);
+#pragma unroll
+                            for (int c4 = 0; c4 < DMAX / W; ++c4) {
+                                if (c4 * W < dpad) {
+                                    const V yy = __ldg(yv + c4);
+                                    const V xx = __ldg(xv + c4);
+                                    const T* yp = reinterpret_cast<const T*>(&yy);
+                                    const T* xp = reinterpret_cast<const T*>(&xx);
+#pragma unroll
+                                    for (int w = 0; w < W; ++w) {
+                                        xacc[c4 * W + w] = fma(mrel, yp[w], xacc[c4 * W + w]);
+                                        ysum[c4 * W + w] = fma(mrel, xp[w], ysum[c4 * W + w]);
+                                    }
+                                }
+                            }
+                        }
+                        // exponents of the outputs (shared by gra and gbo)
+                        gea = eg;
+                        if (kRescale) {
+                            float mag = 0.f;
+#pragma unroll
+                            for (int n = 0; n <= N; ++n)
+                                mag = fmaxf(mag, fmaxf(fabsf(static_cast<float>(gra[n])), fabsf(static_cast<float>(gbo[n]))));
+                            if (mag == 0.f) {
+                                gea = kZeroExp;
+                            } else if (mag > 0x1p64f || mag < 0x1p-64f) {
+                                const int sh = mag > 0x1p64f ? -64 : 64;
+#pragma unroll
+                                for (int n = 0; n <= N; ++n) { gra[n] *= pow2t<T>(sh); gbo[n] *= pow2t<T>(sh); }
+                                gea -= sh;
+                            }
+                        }
+                        gbe = gea;
+                        if (lane == 0) {
+                            if (rs > 0) {  // hand the left-edge adjoint to lane 31 of the strip below
+                                T* dst = rbuf + static_cast<int64_t>(rj) * (N + 1);
+#pragma unroll
+                                for (int n = 0; n <= N; ++n) dst[n] = gbo[n];
+                                if (kRescale) rexp[rj] = gbe;
+                            }
+                            T* yb = ybar + static_cast<int64_t>(rj >> lam) * dpad;
+#pragma unroll
+                            for (int c = 0; c < DMAX; ++c)
+                                if (c < dpad) yb[c] += ysum[c];
+                        }
+                        if (rj == 0) {  // the row is finished: flush dk/dx of its increment
+                            const double scale = gbar * pow2d(ek);
+                            double* gx = B.gincX + (P.xs + (row >> lam)) * dpad;
+                            for (int c = 0; c < dpad; ++c) {
+                                if (xacc[c] != T(0)) atomicAdd(gx + c, static_cast<double>(xacc[c]) * scale);
+                                xacc[c] = T(0);
+                            }
+                        }
+                    }
+                    __syncwarp();
+                }
+            }
+        }
+        // flush dk/dy of every increment of y
+        {
+            const double scale = gbar * pow2d(ek);
+            for (int64_t i = lane; i < P.ly * dpad; i += 32) {
+                const T v = ybar[i];
+                if (v != T(0)) atomicAdd(B.gincY + P.ys * dpad + i, static_cast<double>(v) * scale);
+            }
+        }
+        __syncwarp();
+    }
+}
+
+}  // namespace sk

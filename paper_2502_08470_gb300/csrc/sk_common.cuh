@@ -44,15 +44,25 @@ extern __device__ int g_sk_error;
 
 __device__ __forceinline__ void record_error(int code) { atomicCAS(&g_sk_error, 0, code); }
 
+// Coefficients that depend only on the (compile-time) indices of the unrolled cell loops are
+// computed by constexpr functions, so they fold into instruction immediates instead of being
+// fetched from the constant bank every cell: 1/m and the Hankel coefficient n!/(n+k)!.
+__host__ __device__ constexpr double cx_inv(int m) { return 1.0 / static_cast<double>(m); }
+__host__ __device__ constexpr double cx_hank(int n, int k) {
+    double r = 1.0;
+    for (int i = 1; i <= k; ++i) r /= static_cast<double>(n + i);
+    return r;
+}
+
 template <typename T> struct Tab;
 template <> struct Tab<float> {
-    static __device__ __forceinline__ float inv(int m) { return c_inv_f[m]; }
-    static __device__ __forceinline__ float hank(int n, int k) { return c_hank_f[n][k]; }
+    static __device__ __forceinline__ float inv(int m) { return static_cast<float>(cx_inv(m)); }
+    static __device__ __forceinline__ float hank(int n, int k) { return static_cast<float>(cx_hank(n, k)); }
     static __device__ __forceinline__ float proj(int N, int n, int jj) { return c_proj_f[N][n][jj]; }
 };
 template <> struct Tab<double> {
-    static __device__ __forceinline__ double inv(int m) { return c_inv_d[m]; }
-    static __device__ __forceinline__ double hank(int n, int k) { return c_hank_d[n][k]; }
+    static __device__ __forceinline__ double inv(int m) { return cx_inv(m); }
+    static __device__ __forceinline__ double hank(int n, int k) { return cx_hank(n, k); }
     static __device__ __forceinline__ double proj(int N, int n, int jj) { return c_proj_d[N][n][jj]; }
 };
 

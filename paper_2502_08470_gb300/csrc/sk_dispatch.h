@@ -14,3 +14,12 @@ const void* fwd_interp_ptr_f32(int N);
 const void* fwd_interp_ptr_f64(int N);
 
 }  // namespace sk
+
+namespace sk {
+// Adjoint of the approximation scheme: dmax = 8 or 32 (register accumulators for d <= dmax);
+// writes the per-warp shared-memory stack size.  NULL when no kernel exists.
+const void* bwd_approx_ptr_f32(int N, int dmax, int* stack_bytes);
+const void* bwd_approx_ptr_f64(int N, int dmax, int* stack_bytes);
+int bwd_segment_f32();  // antidiagonal checkpoint interval K
+int bwd_segment_f64();
+}  // namespace sk

@@ -126,11 +126,14 @@ template <typename T, int N, int NE, bool INTERP>
 __global__ void __launch_bounds__(kFwdWarps * 32, (fwd_poly_min_blocks<T, N, NE>()))
     fwd_poly_kernel(Launch L, int64_t buf_cols) {
     constexpr bool kRescale = std::is_same<T, float>::value;
+    using V = typename Vec<T>::type;
+    constexpr int W = Vec<T>::W;
+    constexpr int NB = (N + 1 + W - 1) / W * W;  // hand-off entry width, padded to whole vectors
     const int lane = threadIdx.x & 31;
     const int64_t slot = static_cast<int64_t>(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5);
     char* base = static_cast<char*>(L.scratch) + slot * L.scratch_stride;
-    T* hbuf = reinterpret_cast<T*>(base);                                // [buf_cols][N+1]
-    int* ebuf = reinterpret_cast<int*>(hbuf + buf_cols * (N + 1));      // [buf_cols]
+    V* hbuf = reinterpret_cast<V*>(base);                                         // [buf_cols][NB / W]
+    int* ebuf = reinterpret_cast<int*>(base + buf_cols * NB * static_cast<int64_t>(sizeof(T)));
     const int dpad = L.dpad;
     const T* __restrict__ incX = static_cast<const T*>(L.X.inc);
     const T* __restrict__ incY = static_cast<const T*>(L.Y.inc);
@@ -166,96 +169,119 @@ __global__ void __launch_bounds__(kFwdWarps * 32, (fwd_poly_min_blocks<T, N, NE>
 #pragma unroll
         for (int n = 0; n <= N; ++n) { a[n] = T(0); bo[n] = T(0); }
         int ea = 0, eo = 0;
-        int jj = -lane, s = 0;
+        int jj = -lane, s = 0, row = lane;
+        const T* xrow = xbase + static_cast<int64_t>(min(row, rows - 1) >> lam) * dpad;
 
         for (int step = 0; step < nsteps; ++step) {
             T b[N + 1];
 #pragma unroll
             for (int n = 0; n <= N; ++n) b[n] = __shfl_up_sync(kFull, bo[n], 1);
             int eb = kRescale ? __shfl_up_sync(kFull, eo, 1) : 0;
-            const int row = (s << 5) + lane;
-            const bool active = jj >= 0 && jj < cols && row < rows;
-            if (active) {
-                if (lane == 0) {
-                    if (s == 0) {  // q^{0,j} = e_0 (left boundary k(0, .) = 1)
+            const bool active = static_cast<unsigned>(jj) < static_cast<unsigned>(cols) && row < rows;
+            if (active && lane == 0) {
+                if (s == 0) {  // q^{0,j} = e_0 (left boundary k(0, .) = 1)
 #pragma unroll
-                        for (int n = 0; n <= N; ++n) b[n] = (n == 0) ? T(1) : T(0);
-                        eb = 0;
-                    } else {
-                        const T* src = hbuf + static_cast<int64_t>(jj) * (N + 1);
+                    for (int n = 0; n <= N; ++n) b[n] = (n == 0) ? T(1) : T(0);
+                    eb = 0;
+                } else {
+                    const V* src = hbuf + static_cast<int64_t>(jj) * (NB / W);
 #pragma unroll
-                        for (int n = 0; n <= N; ++n) b[n] = src[n];
-                        if (kRescale) eb = ebuf[jj];
+                    for (int v = 0; v < NB / W; ++v) {
+                        const V t = src[v];
+                        const T* tp = reinterpret_cast<const T*>(&t);
+#pragma unroll
+                        for (int w = 0; w < W; ++w)
+                            if (v * W + w <= N) b[v * W + w] = tp[w];
                     }
+                    if (kRescale) eb = ebuf[jj];
                 }
-                if (jj == 0) {  // p^{i,0} = e_0 (bottom boundary k(., 0) = 1)
+            }
+            if (active && jj == 0) {  // p^{i,0} = e_0 (bottom boundary k(., 0) = 1)
 #pragma unroll
-                    for (int n = 0; n <= N; ++n) a[n] = (n == 0) ? T(1) : T(0);
-                    ea = 0;
+                for (int n = 0; n <= N; ++n) a[n] = (n == 0) ? T(1) : T(0);
+                ea = 0;
+            }
+            if (kRescale && active && ea != eb) {  // bring both inputs to the larger exponent
+                if (ea > eb) {
+                    const T f = (eb - ea < -126) ? T(0) : pow2t<T>(eb - ea);
+#pragma unroll
+                    for (int n = 0; n <= N; ++n) b[n] *= f;
+                } else {
+                    const T f = (ea - eb < -126) ? T(0) : pow2t<T>(ea - eb);
+#pragma unroll
+                    for (int n = 0; n <= N; ++n) a[n] *= f;
+                    ea = eb;
                 }
-                if (kRescale && ea != eb) {  // bring both inputs to the larger exponent
-                    if (ea > eb) {
-                        const T f = (eb - ea < -126) ? T(0) : pow2t<T>(eb - ea);
-#pragma unroll
-                        for (int n = 0; n <= N; ++n) b[n] *= f;
-                    } else {
-                        const T f = (ea - eb < -126) ? T(0) : pow2t<T>(ea - eb);
-#pragma unroll
-                        for (int n = 0; n <= N; ++n) a[n] *= f;
-                        ea = eb;
-                    }
-                }
-                const T M = row_dot<T>(xbase + static_cast<int64_t>(row >> lam) * dpad,
-                                       ybase + static_cast<int64_t>(jj >> lam) * dpad, L.nvec) * sub;
-                T e[NE + 1];
-                build_exp_series<T, NE>(M, L.tau, e);
-                T ct[NE + 1], cr[NE + 1];
-                cell_series<T, N, NE, INTERP>(a, b, e, ct, cr);
-                if (row == rows - 1 && jj == cols - 1) {
+            }
+            // Every lane runs the cell (inactive lanes on a clamped, in-bounds column); only
+            // the results of active lanes are ever consumed.
+            const int jc = min(max(jj, 0), cols - 1);
+            const T M = row_dot<T>(xrow, ybase + static_cast<int64_t>(jc >> lam) * dpad, L.nvec) * sub;
+            T e[NE + 1];
+            build_exp_series<T, NE>(M, L.tau, e);
+            T ct[NE + 1], cr[NE + 1];
+            cell_series<T, N, NE, INTERP>(a, b, e, ct, cr);
+            if constexpr (INTERP) {
+                if (active && row == rows - 1 && jj == cols - 1) {
                     double v = 0.5 * (series_at_one<T, NE>(ct) + series_at_one<T, NE>(cr));
                     if (kRescale) v = ldexp(v, ea);
                     if (!isfinite(v)) record_error(SK_ERR_NONFINITE);
                     write_result(L, item, P, v);
                 }
-                project<T, N, NE, INTERP>(ct, a);
-                project<T, N, NE, INTERP>(cr, bo);
-                if (kRescale) {
-                    const float mag = fmaxf(fabsf(static_cast<float>(a[0])), fabsf(static_cast<float>(bo[0])));
-                    if (mag > 0x1p64f) {
+            }
+            project<T, N, NE, INTERP>(ct, a);
+            project<T, N, NE, INTERP>(cr, bo);
+            if (kRescale && (step & 3) == 0 && active) {
+                const float mag = fmaxf(fabsf(static_cast<float>(a[0])), fabsf(static_cast<float>(bo[0])));
+                if (mag > 0x1p64f) {
 #pragma unroll
-                        for (int n = 0; n <= N; ++n) { a[n] *= pow2t<T>(-64); bo[n] *= pow2t<T>(-64); }
-                        ea += 64;
-                    } else if (mag < 0x1p-64f) {
-                        float full = 0.f;
+                    for (int n = 0; n <= N; ++n) { a[n] *= pow2t<T>(-64); bo[n] *= pow2t<T>(-64); }
+                    ea += 64;
+                } else if (mag < 0x1p-64f) {
+                    float full = 0.f;
 #pragma unroll
-                        for (int n = 0; n <= N; ++n)
-                            full = fmaxf(full, fmaxf(fabsf(static_cast<float>(a[n])), fabsf(static_cast<float>(bo[n]))));
-                        if (full < 0x1p-64f && full > 0.f) {
+                    for (int n = 0; n <= N; ++n)
+                        full = fmaxf(full, fmaxf(fabsf(static_cast<float>(a[n])), fabsf(static_cast<float>(bo[n]))));
+                    if (full < 0x1p-64f && full > 0.f) {
 #pragma unroll
-                            for (int n = 0; n <= N; ++n) { a[n] *= pow2t<T>(64); bo[n] *= pow2t<T>(64); }
-                            ea -= 64;
-                        }
+                        for (int n = 0; n <= N; ++n) { a[n] *= pow2t<T>(64); bo[n] *= pow2t<T>(64); }
+                        ea -= 64;
                     }
                 }
-                eo = ea;
-                if (lane == 31 && s + 1 < nstrips) {  // hand the right edge to the next strip
-                    T* dst = hbuf + static_cast<int64_t>(jj) * (N + 1);
+            }
+            eo = ea;
+            if (active && lane == 31 && s + 1 < nstrips) {  // hand the right edge to the next strip
+                V* dst = hbuf + static_cast<int64_t>(jj) * (NB / W);
 #pragma unroll
-                    for (int n = 0; n <= N; ++n) dst[n] = bo[n];
-                    if (kRescale) ebuf[jj] = eo;
+                for (int v = 0; v < NB / W; ++v) {
+                    V t;
+                    T* tp = reinterpret_cast<T*>(&t);
+#pragma unroll
+                    for (int w = 0; w < W; ++w) tp[w] = (v * W + w <= N) ? bo[v * W + w] : T(0);
+                    dst[v] = t;
                 }
+                if (kRescale) ebuf[jj] = eo;
             }
             __syncwarp();
-            if (++jj == period) { jj = 0; ++s; }
+            if (++jj == period) {
+                jj = 0;
+                ++s;
+                row += 32;
+                xrow = xbase + static_cast<int64_t>(min(row, rows - 1) >> lam) * dpad;
+            }
+        }
+        if constexpr (!INTERP) {
+            // The last cell was the final step of lane `last_lane`; for the approximation scheme
+            // its outputs are still in (a, bo): k_hat = 1/2 sum_n (a_n + b_n) / n!.
+            if (lane == last_lane) {
+                double v = 0.5 * (series_at_one<T, N>(a) + series_at_one<T, N>(bo));
+                if (kRescale) v = ldexp(v, ea);
+                if (!isfinite(v)) record_error(SK_ERR_NONFINITE);
+                write_result(L, item, P, v);
+            }
         }
     }
 }
 
-// Bytes of hand-off buffer per warp slot for `cols` refined columns.
-template <typename T>
-inline int64_t fwd_poly_slot_bytes(int N, int64_t cols) {
-    int64_t b = cols * (N + 1) * static_cast<int64_t>(sizeof(T)) + cols * 4;
-    return (b + 255) / 256 * 256;
-}
 
 }  // namespace sk

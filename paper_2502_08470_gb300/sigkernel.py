@@ -210,6 +210,105 @@ def gram_workspace(X, Y=None, scheme="approx", degree=6, dyadic=0, compute="f64"
     return _workspace(OP_GRAM, _cpaths(X), _cpaths(Y), X.d, -1, opt)
 
 
+def sigkernel_backward(grad_out, X, Y=None, pair_a=None, pair_b=None, scheme="approx", degree=6, dyadic=0,
+                       compute="f64", sort=True, time_kernel: bool = False):
+    """Gradients of sum(grad_out * k_hat) with respect to the rows of X and Y (float64 CUDA tensors
+    shaped like the rows).  Gram mode when ``pair_a`` is None (``grad_out`` [nx, ny]); with Y None
+    (or Y is X) the symmetric Gram of X, and the single returned gradient is the total."""
+    sym = Y is None or Y is X
+    X = as_paths(X)
+    Y = X if sym else as_paths(Y)
+    cX, cY = _cpaths(X), _cpaths(Y)
+    g = torch.as_tensor(grad_out, dtype=torch.float64, device="cuda").contiguous()
+    gX = torch.zeros(X.rows.shape[0], X.d, dtype=torch.float64, device="cuda")
+    same = sym or (X.rows.data_ptr() == Y.rows.data_ptr() and X.offsets.data_ptr() == Y.offsets.data_ptr())
+    gY = gX if same else torch.zeros(Y.rows.shape[0], Y.d, dtype=torch.float64, device="cuda")
+    extra = (0 if sort else FLAG_NO_SORT) | (FLAG_TIME_KERNEL if time_kernel else 0)
+    if pair_a is None:
+        opt = _options(scheme, degree, dyadic, compute, _flags(X, extra | (FLAG_SYMMETRIC if sym else 0)))
+        ws = _workspace(OP_BACKWARD, cX, cY, X.d, -1, opt)
+        pa_ptr = pb_ptr = None
+        n = -1
+    else:
+        pa = torch.as_tensor(pair_a, dtype=torch.int64, device="cuda").contiguous()
+        pb = torch.as_tensor(pair_b, dtype=torch.int64, device="cuda").contiguous()
+        n = pa.numel()
+        opt = _options(scheme, degree, dyadic, compute, _flags(X, extra))
+        ws = _workspace(OP_BACKWARD, cX, cY, X.d, n, opt)
+        pa_ptr, pb_ptr = pa.data_ptr(), pb.data_ptr()
+    _check(load_library().sigkernel_backward(ctypes.byref(cX), ctypes.byref(cY), X.d, _dtype_code(X, Y), pa_ptr, pb_ptr,
+                                             n, ctypes.byref(opt), g.data_ptr(), gX.data_ptr(),
+                                             None if same else gY.data_ptr(), ws.data_ptr(), ws.numel(),
+                                             _stream_ptr()))
+    return gX, gY
+
+
+def sigkernel_mmd2(A, B, scheme="approx", degree=6, dyadic=0, compute="f64", unbiased=False, grads=False):
+    """MMD^2 between path sets A and B; returns (mmd2, [mean K_AA, mean K_BB, mean K_AB]) or, with
+    ``grads``, also (dMMD2/dA rows, dMMD2/dB rows) as float64 CUDA tensors."""
+    A, B = as_paths(A), as_paths(B)
+    cA, cB = _cpaths(A), _cpaths(B)
+    opt = _options(scheme, degree, dyadic, compute, _flags(A, FLAG_UNBIASED if unbiased else 0))
+    ws = _workspace(OP_MMD2, cA, cB, A.d, -1, opt)
+    out = torch.empty(4, dtype=torch.float64, device="cuda")
+    gA = torch.empty(A.rows.shape[0], A.d, dtype=torch.float64, device="cuda") if grads else None
+    gB = torch.empty(B.rows.shape[0], B.d, dtype=torch.float64, device="cuda") if grads else None
+    _check(load_library().sigkernel_mmd2(ctypes.byref(cA), ctypes.byref(cB), A.d, _dtype_code(A, B), ctypes.byref(opt),
+                                         out.data_ptr(), gA.data_ptr() if grads else None,
+                                         gB.data_ptr() if grads else None, ws.data_ptr(), ws.numel(), _stream_ptr()))
+    if grads:
+        return out[0], out[1:], gA, gB
+    return out[0], out[1:]
+
+
+# ----------------------------------------------------------------------------------------------
+# torch.autograd wrappers (dense [B, L, d] inputs)
+# ----------------------------------------------------------------------------------------------
+class _GramFn(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, X, Y, sym, opts):
+        ctx.opts, ctx.sym = opts, sym
+        ctx.save_for_backward(X, Y)
+        return sigkernel_gram(X, None if sym else Y, **opts)
+
+    @staticmethod
+    def backward(ctx, gG):
+        X, Y = ctx.saved_tensors
+        if ctx.sym:
+            gX, _ = sigkernel_backward(gG, X, None, **ctx.opts)
+            return gX.view_as(X).to(X.dtype), None, None, None
+        gX, gY = sigkernel_backward(gG, X, Y, **ctx.opts)
+        return gX.view_as(X).to(X.dtype), gY.view_as(Y).to(Y.dtype), None, None
+
+
+class _MMD2Fn(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, A, B, unbiased, opts):
+        m, _, gA, gB = sigkernel_mmd2(A, B, unbiased=unbiased, grads=True, **opts)
+        ctx.save_for_backward(gA.view_as(A), gB.view_as(B))
+        return m
+
+    @staticmethod
+    def backward(ctx, gm):
+        gA, gB = ctx.saved_tensors
+        return (gm * gA).to(gA.dtype), (gm * gB).to(gB.dtype), None, None
+
+
+class SigKernel:
+    """Signature kernel k_hat of one scheme: ``gram`` and ``mmd2`` are differentiable with respect
+    to dense [B, L, d] path tensors through the adjoint wavefront."""
+
+    def __init__(self, scheme="approx", degree=6, dyadic=0, compute="f32"):
+        self.opts = dict(scheme=scheme, degree=degree, dyadic=dyadic, compute=compute)
+
+    def gram(self, X: torch.Tensor, Y: torch.Tensor | None = None) -> torch.Tensor:
+        sym = Y is None or Y is X
+        return _GramFn.apply(X, X if sym else Y, sym, self.opts)
+
+    def mmd2(self, A: torch.Tensor, B: torch.Tensor, unbiased: bool = False) -> torch.Tensor:
+        return _MMD2Fn.apply(A, B, unbiased, self.opts)
+
+
 def last_kernel_ms() -> float:
     """Device milliseconds of the wavefront kernel of the last ``time_kernel=True`` call."""
     return float(load_library().sigkernel_last_kernel_ms())

@@ -1,0 +1,232 @@
+"""GPU adjoint parity: the reverse wavefront (through the C ABI) against the oracle's complex-step
+derivatives of the same discrete scheme, plus central differences and MMD^2.
+
+Tolerances: FP64 adjoints agree with the complex-step derivative to rounding (relative 1e-9 of the
+gradient's scale); FP32 adjoints are held to the mixed-precision bar (relative error <= 1e-4 of
+the gradient's scale).
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2502_08470_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+sk = pytest.importorskip("paper_2502_08470_gb300.sigkernel")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda_available():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+def _cuda(a):
+    return torch.as_tensor(np.asarray(a), dtype=torch.float64, device="cuda")
+
+
+def _scaled_err(g, ref):
+    return float(np.max(np.abs(g - ref)) / max(np.max(np.abs(ref)), 1e-300))
+
+
+def _oracle_gram_grad(X, Y, Wt, N, lam, sym):
+    """d/dX, d/dY of sum_ab Wt[a,b] k(X_a, Y_b) from the oracle's complex-step gradients."""
+    gX = np.zeros_like(X)
+    gY = np.zeros_like(Y)
+    for a in range(X.shape[0]):
+        for b in range(Y.shape[0]):
+            if Wt[a, b] == 0.0:
+                continue
+            gx, gy = oracle.grad(X[a], Y[b], "approx", N, lam)
+            gX[a] += Wt[a, b] * gx
+            gY[b] += Wt[a, b] * gy
+    if sym:
+        return gX + gY, None
+    return gX, gY
+
+
+@pytest.mark.parametrize("N,lam", [(2, 0), (4, 0), (6, 0), (6, 1), (9, 0)])
+def test_pairs_backward_f64_matches_complex_step(N, lam):
+    X = W.brownian(2, 40, 3, seed=51)   # 39 rows: two strips with a ragged tail
+    Y = W.brownian(2, 35, 3, seed=52)
+    pa, pb = [0, 1, 1], [1, 0, 1]
+    wts = np.array([0.7, -1.3, 2.0])
+    gX, gY = sk.sigkernel_backward(_cuda(wts), _cuda(X), _cuda(Y), pair_a=pa, pair_b=pb, degree=N, dyadic=lam,
+                                   compute="f64")
+    torch.cuda.synchronize()
+    assert sk.device_status() == 0
+    rX = np.zeros_like(X)
+    rY = np.zeros_like(Y)
+    for w, a, b in zip(wts, pa, pb):
+        gx, gy = oracle.grad(X[a], Y[b], "approx", N, lam)
+        rX[a] += w * gx
+        rY[b] += w * gy
+    assert _scaled_err(gX.cpu().numpy().reshape(X.shape), rX) < 1e-9
+    assert _scaled_err(gY.cpu().numpy().reshape(Y.shape), rY) < 1e-9
+
+
+def test_pairs_backward_f32_matches_complex_step():
+    X = W.brownian(2, 70, 4, seed=53)
+    Y = W.brownian(2, 66, 4, seed=54)
+    pa, pb = [0, 1], [1, 0]
+    wts = np.array([1.0, 0.5])
+    gX, gY = sk.sigkernel_backward(_cuda(wts), _cuda(X), _cuda(Y), pair_a=pa, pair_b=pb, degree=6, compute="f32")
+    torch.cuda.synchronize()
+    rX = np.zeros_like(X)
+    rY = np.zeros_like(Y)
+    for w, a, b in zip(wts, pa, pb):
+        gx, gy = oracle.grad(X[a], Y[b], "approx", 6)
+        rX[a] += w * gx
+        rY[b] += w * gy
+    assert _scaled_err(gX.cpu().numpy().reshape(X.shape), rX) < 1e-4
+    assert _scaled_err(gY.cpu().numpy().reshape(Y.shape), rY) < 1e-4
+
+
+@pytest.mark.parametrize("sym", [False, True])
+@pytest.mark.parametrize("compute", ["f64", "f32"])
+def test_gram_backward_matches_oracle(sym, compute):
+    X = W.brownian(3, 33, 2, seed=55)
+    Y = X if sym else W.brownian(4, 29, 2, seed=56)
+    rng = np.random.default_rng(57)
+    Wt = rng.normal(size=(X.shape[0], Y.shape[0]))
+    gX, gY = sk.sigkernel_backward(_cuda(Wt), _cuda(X), None if sym else _cuda(Y), degree=5, compute=compute)
+    torch.cuda.synchronize()
+    assert sk.device_status() == 0
+    rX, rY = _oracle_gram_grad(X, Y, Wt, 5, 0, sym)
+    tol = 1e-9 if compute == "f64" else 1e-4
+    assert _scaled_err(gX.cpu().numpy().reshape(X.shape), rX) < tol
+    if not sym:
+        assert _scaled_err(gY.cpu().numpy().reshape(Y.shape), rY) < tol
+
+
+def test_backward_ragged_and_trivial_paths():
+    lengths = [1, 2, 5, 33, 34, 70]
+    Xs = [W.brownian(1, L, 3, seed=60 + i)[0] for i, L in enumerate(lengths)]
+    PX = sk.Paths.from_list([torch.tensor(x) for x in Xs])
+    pa = [0, 1, 2, 3, 4, 5, 5, 3]
+    pb = [5, 4, 3, 2, 1, 0, 3, 5]
+    wts = np.linspace(-1.0, 1.5, len(pa))
+    gX, _ = sk.sigkernel_backward(_cuda(wts), PX, PX, pair_a=pa, pair_b=pb, degree=6, compute="f64")
+    torch.cuda.synchronize()
+    assert sk.device_status() == 0
+    ref = [np.zeros_like(x) for x in Xs]
+    for w, a, b in zip(wts, pa, pb):
+        gx, gy = oracle.grad(Xs[a], Xs[b], "approx", 6)
+        ref[a] += w * gx
+        ref[b] += w * gy
+    got = gX.cpu().numpy()
+    off = np.concatenate([[0], np.cumsum(lengths)])
+    scale = max(np.max(np.abs(r)) for r in ref)
+    for i in range(len(Xs)):
+        assert np.max(np.abs(got[off[i]:off[i + 1]] - ref[i])) < 1e-9 * scale
+    assert np.all(got[0:1] == 0.0)  # a single-point path has k = 1 and no gradient
+
+
+def test_backward_f32_rescaled_huge_kernels():
+    X = 11.0 * W.brownian(2, 49, 2, seed=58)
+    Y = 11.0 * W.brownian(2, 49, 2, seed=59)
+    k = oracle.kernel(X[0], Y[1], "approx", 8, 1)
+    assert abs(k) > 1e39
+    gX, gY = sk.sigkernel_backward(_cuda([1.0]), _cuda(X), _cuda(Y), pair_a=[0], pair_b=[1], degree=8, dyadic=1,
+                                   compute="f32")
+    torch.cuda.synchronize()
+    gx, gy = oracle.grad(X[0], Y[1], "approx", 8, 1)
+    got = gX.cpu().numpy().reshape(X.shape)[0]
+    assert np.all(np.isfinite(got))
+    assert _scaled_err(got, gx) < 1e-3
+
+
+def test_gradient_matches_central_differences_on_sampled_coordinates():
+    X = W.brownian(1, 30, 3, seed=61)
+    Y = W.brownian(1, 27, 3, seed=62)
+    gX, gY = sk.sigkernel_backward(_cuda([1.0]), _cuda(X), _cuda(Y), pair_a=[0], pair_b=[0], degree=6,
+                                   compute="f64")
+    gx = gX.cpu().numpy().reshape(X.shape)[0]
+    rng = np.random.default_rng(63)
+    h = 1e-4
+    for _ in range(16):
+        p, c = rng.integers(0, 30), rng.integers(0, 3)
+        xp, xm = X[0].copy(), X[0].copy()
+        xp[p, c] += h
+        xm[p, c] -= h
+        fd = (oracle.kernel(xp, Y[0], "approx", 6) - oracle.kernel(xm, Y[0], "approx", 6)) / (2 * h)
+        assert abs(gx[p, c] - fd) < 1e-6 * max(1.0, abs(fd))
+
+
+# ------------------------------------------------------------------------------------------
+# MMD^2 and its gradient
+# ------------------------------------------------------------------------------------------
+@pytest.mark.parametrize("unbiased", [False, True])
+def test_mmd2_matches_oracle(unbiased):
+    A = W.brownian(4, 20, 2, seed=64)
+    B = W.brownian(3, 20, 2, seed=65, drift=0.5, vol=1.2)
+    m, means, gA, gB = sk.sigkernel_mmd2(_cuda(A), _cuda(B), degree=6, compute="f64", unbiased=unbiased, grads=True)
+    torch.cuda.synchronize()
+    assert sk.device_status() == 0
+    ref = oracle.mmd2(A, B, "approx", 6, unbiased=unbiased)
+    assert abs(m.item() - ref) < 1e-11 * max(1.0, abs(ref))
+    gA = gA.cpu().numpy().reshape(A.shape)
+    gB = gB.cpu().numpy().reshape(B.shape)
+    rng = np.random.default_rng(66)
+    for _ in range(6):
+        side = int(rng.integers(0, 2))
+        S = A if side == 0 else B
+        path, p, c = rng.integers(0, S.shape[0]), rng.integers(0, 20), rng.integers(0, 2)
+        ref_g = oracle.mmd2_grad_entry(A, B, side, path, p, c, "approx", 6, unbiased=unbiased)
+        got = (gA if side == 0 else gB)[path, p, c]
+        assert abs(got - ref_g) < 1e-9 * max(1.0, np.max(np.abs(gA)))
+
+
+def test_mmd2_workload_gradient_central_differences_f32():
+    """Two batches (Brownian vs Brownian with drift 0.5 and volatility 1.2), FP32 adjoint; 16 random
+    coordinates checked against central differences (h = 1e-4) of the FP64 oracle."""
+    A = W.brownian(6, 33, 4, seed=7)
+    B = W.brownian(6, 33, 4, seed=8, drift=0.5, vol=1.2)
+    m, _, gA, gB = sk.sigkernel_mmd2(_cuda(A), _cuda(B), degree=6, compute="f32", grads=True)
+    torch.cuda.synchronize()
+    gA = gA.cpu().numpy().reshape(A.shape)
+    gB = gB.cpu().numpy().reshape(B.shape)
+    rng = np.random.default_rng(67)
+    h = 1e-4
+    scale = max(np.max(np.abs(gA)), np.max(np.abs(gB)))
+    for _ in range(16):
+        side = int(rng.integers(0, 2))
+        S = A if side == 0 else B
+        path, p, c = rng.integers(0, 6), rng.integers(0, 33), rng.integers(0, 4)
+        Sp, Sm = S.copy(), S.copy()
+        Sp[path, p, c] += h
+        Sm[path, p, c] -= h
+        if side == 0:
+            fd = (oracle.mmd2(Sp, B, "approx", 6) - oracle.mmd2(Sm, B, "approx", 6)) / (2 * h)
+        else:
+            fd = (oracle.mmd2(A, Sp, "approx", 6) - oracle.mmd2(A, Sm, "approx", 6)) / (2 * h)
+        got = (gA if side == 0 else gB)[path, p, c]
+        assert abs(got - fd) < 1e-4 * scale
+
+
+def test_autograd_gram_and_mmd():
+    X = _cuda(W.brownian(3, 25, 2, seed=68)).requires_grad_(True)
+    Y = _cuda(W.brownian(2, 21, 2, seed=69)).requires_grad_(True)
+    kern = sk.SigKernel("approx", 6, 0, "f64")
+    G = kern.gram(X, Y)
+    wts = torch.randn(3, 2, dtype=torch.float64, device="cuda")
+    (G * wts).sum().backward()
+    gX, gY = sk.sigkernel_backward(wts, X.detach(), Y.detach(), degree=6, compute="f64")
+    assert torch.allclose(X.grad.reshape(-1, 2), gX, rtol=1e-12, atol=1e-14)
+    assert torch.allclose(Y.grad.reshape(-1, 2), gY, rtol=1e-12, atol=1e-14)
+    A = _cuda(W.brownian(3, 15, 2, seed=70)).requires_grad_(True)
+    B = _cuda(W.brownian(3, 15, 2, seed=71, drift=0.5)).requires_grad_(True)
+    m = kern.mmd2(A, B)
+    m.backward()
+    assert A.grad is not None and torch.isfinite(A.grad).all()
+    Ad, Bd = A.detach().cpu().numpy(), B.detach().cpu().numpy()
+    ref = oracle.mmd2_grad_entry(Ad, Bd, 0, 1, 4, 1, "approx", 6)
+    assert abs(A.grad[1, 4, 1].item() - ref) < 1e-9 * max(1.0, A.grad.abs().max().item())
+
+
+def test_gradcheck_small():
+    X = _cuda(W.brownian(2, 6, 2, seed=72)).requires_grad_(True)
+    Y = _cuda(W.brownian(2, 5, 2, seed=73)).requires_grad_(True)
+    kern = sk.SigKernel("approx", 5, 0, "f64")
+    assert torch.autograd.gradcheck(lambda x, y: kern.gram(x, y), (X, Y), eps=1e-6, atol=1e-8, rtol=1e-6)
