@@ -124,15 +124,15 @@ def test_backward_ragged_and_trivial_paths():
 
 
 def test_backward_f32_rescaled_huge_kernels():
-    X = 11.0 * W.brownian(2, 49, 2, seed=58)
-    Y = 11.0 * W.brownian(2, 49, 2, seed=59)
-    k = oracle.kernel(X[0], Y[1], "approx", 8, 1)
-    assert abs(k) > 1e39
-    gX, gY = sk.sigkernel_backward(_cuda([1.0]), _cuda(X), _cuda(Y), pair_a=[0], pair_b=[1], degree=8, dyadic=1,
+    X = 14.0 * W.brownian(2, 49, 2, seed=58)
+    Y = 14.0 * W.brownian(2, 49, 2, seed=59)
+    k = oracle.kernel(X[1], Y[0], "approx", 8, 1)
+    assert abs(k) > 1e39  # |k| ~ 3e51: beyond FP32 without the exponents
+    gX, gY = sk.sigkernel_backward(_cuda([1.0]), _cuda(X), _cuda(Y), pair_a=[1], pair_b=[0], degree=8, dyadic=1,
                                    compute="f32")
     torch.cuda.synchronize()
-    gx, gy = oracle.grad(X[0], Y[1], "approx", 8, 1)
-    got = gX.cpu().numpy().reshape(X.shape)[0]
+    gx, gy = oracle.grad(X[1], Y[0], "approx", 8, 1)
+    got = gX.cpu().numpy().reshape(X.shape)[1]
     assert np.all(np.isfinite(got))
     assert _scaled_err(got, gx) < 1e-3
 
