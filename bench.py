@@ -3,17 +3,20 @@
 
 Workload ("gram128"): X and Y are 128 Brownian paths each on [0, 1], 257 points, d = 8,
 increments N(0, 1/256) per coordinate (seeds 3 and 4; other ranks use their own seeds), solved
-with the polynomial approximation scheme of order 6 on the batched FP32 wavefront (per-lane
-power-of-two exponents, FP64 endpoints).  One step = one full Gram: increments, then the
-persistent wavefront over all 16,384 pairs x 65,536 cells.
+with the polynomial approximation scheme of order 6 in the batched FP32 form (per-lane
+power-of-two exponents, FP64 endpoints and gradient accumulation).
 
-Metric: Goursat cell-updates per second (cells = sum over pairs of l_x * l_y), whole job.
+One step = forward Gram G = k_hat(X_a, Y_b) over all 16,384 pairs x 65,536 cells, then the
+adjoint: d(sum_ab W_ab G_ab)/dX and /dY for a fixed seeded upstream gradient W.
+Metric: Goursat cell-updates per second of the fwd+bwd step, counting each of the Gram's
+1.07e9 cells once (value = cells / step time), plus the step's milliseconds.
 Timing: per-step CUDA events on the launching stream; a 256 MiB buffer is written between
 steps (outside the events) so every step starts with a cold L2.
 
-Also reported: the roofline of the wavefront kernel (FP32 ALU bound), the FP64 plain wavefront
-of the same Gram, the end-to-end rate through the public API with host buffers, and the CPU
-oracle on a bounded sample.  ``--impl reference`` times the CPU oracle alone.
+Also reported: the forward-only rate, the FP64 plain wavefront of the same Gram, the roofline of
+the dominant kernel (the adjoint, FP32 ALU bound), the end-to-end rate through the public API
+with host buffers, and the CPU oracle on a bounded sample.  ``--impl reference`` times the CPU
+oracle alone.
 """
 from __future__ import annotations
 
@@ -36,7 +39,7 @@ D = 8
 DEGREE = 6
 CELLS_PER_PAIR = (L - 1) * (L - 1)
 CELLS = NX * NY * CELLS_PER_PAIR
-PARTS = ("f32", "f64", "e2e", "cpu")
+PARTS = ("f32", "fwd", "f64", "e2e", "cpu")
 SM_COUNT = 152
 FP32_LANES = 128
 SM_MAX_MHZ = 2070.0
@@ -50,6 +53,15 @@ def flops_per_cell(N: int, d: int) -> int:
     return 2 * fma
 
 
+def bwd_flops_per_cell(N: int, d: int) -> int:
+    """Algorithmic FLOPs of one cell of the adjoint (2 per multiply-add): the forward cell whose
+    values it needs, its transpose (Toeplitz (N+1)(N+2), Hankel 2N(N+1), weights 2(N+1)), the
+    e_m adjoint with recomputed Hankel sums 3N^2 + 4N, and the two d-term contractions
+    dk/dx += Mbar dy, dk/dy += Mbar dx.  Checkpoint replays are not counted."""
+    adj = 2 * (N + 1) + (N + 1) * (N + 2) + 2 * N * (N + 1) + 3 * N * N + 4 * N + 2 * d
+    return flops_per_cell(N, d) + 2 * adj
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -60,7 +72,8 @@ def parse():
     ap.add_argument("--nx", type=int, default=NX,
                     help="paths per side (a smaller Gram of the same paths, for profiling runs)")
     ap.add_argument("--parts", default=",".join(PARTS),
-                    help="comma list of measurements to run: f32 (headline), f64, e2e, cpu")
+                    help="comma list: f32 (headline fwd+bwd step), fwd (forward only), f64 (FP64 forward), "
+                         "e2e, cpu")
     args = ap.parse_args()
     args.parts = set(args.parts.split(","))
     if args.no_cpu_baseline:
@@ -129,18 +142,33 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sms)}
 
 
-def cpu_baseline(X, Y, budget_pairs=48):
-    """The FP64 oracle as it stands, on a bounded sample (the first budget_pairs^2 pairs)."""
+def cpu_fwd_bwd(X, Y, points=L):
+    """The FP64 oracle as it stands on one pair (prefixes of `points` points): the forward scheme
+    and its complex-step gradient with respect to both paths.  Returns (cells, seconds)."""
     import oracle
-    n = budget_pairs
     cores = os.cpu_count() or 1
+    x, y = X[0][:points], Y[0][:points]
+    t0 = time.perf_counter()
+    oracle.kernel(x, y, "approx", DEGREE)
+    oracle.grad(x, y, "approx", DEGREE, 0, threads=cores)
+    return (points - 1) ** 2, time.perf_counter() - t0
+
+
+def cpu_baseline(X, Y, budget_pairs=48):
+    """The FP64 oracle as it stands, on bounded samples of the step: one full pair forward +
+    gradient (the headline unit), and the first budget_pairs^2 pairs forward only."""
+    import oracle
+    cores = os.cpu_count() or 1
+    cells, dt = cpu_fwd_bwd(X, Y)
+    n = budget_pairs
     t0 = time.perf_counter()
     oracle.gram(list(X[:n]), list(Y[:n]), "approx", DEGREE, 0, threads=cores)
-    dt = time.perf_counter() - t0
-    cells = n * n * CELLS_PER_PAIR
+    dtf = time.perf_counter() - t0
     return {"value": cells / dt, "unit": "cell-updates/s", "cores": cores, "kind": "oracle",
-            "sample": f"{n}x{n} pairs of the 128x128 Gram (257 points, d=8), approximation N={DEGREE}, FP64, "
-                      f"{dt:.2f} s"}
+            "sample": f"fwd+bwd of 1 pair (257 points, d=8, {dt:.1f} s: forward scheme + complex-step gradient "
+                      f"of both paths, threads over coordinates)",
+            "forward_only": {"value": n * n * CELLS_PER_PAIR / dtf, "unit": "cell-updates/s",
+                             "sample": f"{n}x{n} pairs of the Gram, {dtf:.2f} s"}}
 
 
 def run_reference(args, rank, world):
@@ -148,21 +176,25 @@ def run_reference(args, rank, world):
     if rank != 0:
         return
     X, Y = workload(0)
-    per = []
+    cores = os.cpu_count() or 1
     for _ in range(args.warmup):
-        cpu_baseline(X, Y, 16)
+        cpu_fwd_bwd(X, Y, 65)
+    cells = secs = 0.0
     for _ in range(args.steps):
-        per.append(cpu_baseline(X, Y, 24))
-    vals = [p["value"] for p in per]
-    value = statistics.mean(vals)
+        c, t = cpu_fwd_bwd(X, Y, 129)
+        cells += c
+        secs += t
+    value = cells / secs
     ms = CELLS / value * 1e3
-    line = {"impl": "reference", "metric": "Goursat cell-updates/s (polynomial approximation N=6, 128x128 Gram)",
+    sample = "per step: fwd + complex-step gradient of one pair of 129-point prefixes (128x128 cells)"
+    line = {"impl": "reference",
+            "metric": "Goursat cell-updates/s of the fwd+bwd Gram step (polynomial approximation N=6, 128x128 Gram)",
             "value": value, "unit": "cell-updates/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": "gram128: 128x128 Brownian paths, 257 points, d=8",
-                                            "sample": "24x24 pairs per step", "l2": "n/a (CPU)"},
-            "cpu_baseline": {"value": value, "unit": "cell-updates/s", "cores": per[0]["cores"], "kind": "oracle",
-                             "sample": "24x24 pairs of the 128x128 Gram per step"},
+                                            "sample": sample, "l2": "n/a (CPU)"},
+            "cpu_baseline": {"value": value, "unit": "cell-updates/s", "cores": cores, "kind": "oracle",
+                             "sample": sample},
             "e2e": {"value": value, "unit": "cell-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     del dist
@@ -196,45 +228,59 @@ def main():
     G = torch.empty(nx, nx, dtype=torch.float64, device=dev)
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
 
-    def run(compute, steps, warmup, time_kernel=True):
+    Wt = torch.tensor(np.random.default_rng(11 + rank).standard_normal((nx, nx)), device=dev)
+    opts = dict(scheme="approx", degree=DEGREE, sort=False)
+
+    def run(compute, steps, warmup, backward=True):
+        """Timed fwd(+bwd) steps; returns per-step ms, forward-kernel ms, adjoint-kernel ms, wall s."""
         ws = sk.gram_workspace(Xt, Yt, scheme="approx", degree=DEGREE, compute=compute)
+
+        def step(timed):
+            sk.sigkernel_gram(Xt, Yt, compute=compute, workspace=ws, out=G, time_kernel=timed, **opts)
+            kf = sk.last_kernel_ms() if timed else None
+            kb = None
+            if backward:
+                sk.sigkernel_backward(Wt, Xt, Yt, compute=compute, time_kernel=timed, **opts)
+                kb = sk.last_kernel_ms() if timed else None
+            return kf, kb
+
         for _ in range(warmup):
-            sk.sigkernel_gram(Xt, Yt, scheme="approx", degree=DEGREE, compute=compute, sort=False, workspace=ws, out=G)
+            step(False)
         torch.cuda.synchronize()
         if dist is not None:
             dist.barrier()
-        step_ms, kern_ms = [], []
+        step_ms, kf_ms, kb_ms = [], [], []
         t_wall = time.perf_counter()
         for _ in range(steps):
             flush.zero_()
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record()
-            sk.sigkernel_gram(Xt, Yt, scheme="approx", degree=DEGREE, compute=compute, sort=False, workspace=ws,
-                              out=G, time_kernel=time_kernel)
+            kf, kb = step(True)
             e1.record()
             e1.synchronize()
             step_ms.append(e0.elapsed_time(e1))
-            if time_kernel:
-                kern_ms.append(sk.last_kernel_ms())
+            kf_ms.append(kf)
+            if kb is not None:
+                kb_ms.append(kb)
         torch.cuda.synchronize()
         wall = time.perf_counter() - t_wall
         if dist is not None:
             dist.barrier()
-        return step_ms, kern_ms, wall
+        return step_ms, kf_ms, kb_ms, wall
 
     line = {}
     fpc = flops_per_cell(DEGREE, D)
+    bpc = bwd_flops_per_cell(DEGREE, D)
     peak = SM_COUNT * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
     import oracle
     rng = np.random.default_rng(0)
     pa = rng.integers(0, nx, 16)
     pb = rng.integers(0, nx, 16)
-    ref = None
 
-    # headline: FP32 batched wavefront
+    # headline: fwd + bwd step, batched FP32 form
     with ClockSampler(local) as clk:
-        step_ms, kern_ms, wall = run("f32", args.steps, max(args.warmup, 3))
+        step_ms, kf_ms, kb_ms, wall = run("f32", args.steps, max(args.warmup, 3))
     clocks = clk.summary()
     total_ms = float(sum(step_ms))
     if dist is not None:
@@ -245,30 +291,42 @@ def main():
     value = cells * world * args.steps / (total_ms / 1e3)
     g32 = G.cpu().numpy()[pa, pb]
     status = sk.device_status()
-    kavg = statistics.mean(kern_ms)
-    achieved = fpc * cells / (kavg / 1e3) / 1e12
+    kf = statistics.mean(kf_ms)
+    kb = statistics.mean(kb_ms)
+    ach_b = bpc * cells / (kb / 1e3) / 1e12
+    ach_f = fpc * cells / (kf / 1e3) / 1e12
     ref = oracle.pairs(list(X), list(Y), pa, pb, "approx", DEGREE)
     mape = {"f32": float(np.mean(np.abs(g32 - ref) / np.abs(ref))), "sample": "16 sampled Gram entries"}
     line.update({
-        "metric": "Goursat cell-updates/s (polynomial approximation N=6, 128x128 Gram, batched FP32 wavefront)",
+        "metric": "Goursat cell-updates/s of the fwd+bwd Gram step (polynomial approximation N=6, 128x128 Gram, "
+                  "batched FP32)",
         "value": value, "unit": "cell-updates/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32", "data": "synthetic",
-        "config": {"workload": f"gram{nx}: X, Y = {nx} Brownian paths each, 257 points, d=8, N(0,1/256) increments",
+        "config": {"workload": f"gram{nx}: X, Y = {nx} Brownian paths each, 257 points, d=8, N(0,1/256) increments; "
+                               "step = forward Gram + adjoint for a seeded upstream gradient",
                    "scheme": "polynomial approximation", "degree": DEGREE, "dyadic": 0,
                    "cells_per_step": cells, "pairs_per_step": nx * nx,
                    "l2": "256 MiB buffer written between timed steps (outside the events)",
                    "parallelism": f"weak scaling, one independent {nx}x{nx} Gram per GPU ({world} GPUs)"},
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                     "traffic": None, "kernel": "fwd_poly_kernel<float,6,6,false>", "kernel_ms": kavg,
-                     "flops_per_cell": fpc,
+        "roofline": {"bound": "alu", "achieved": ach_b, "peak": peak, "unit": "TFLOP/s", "frac": ach_b / peak,
+                     "traffic": None, "kernel": "bwd_approx_kernel<float,6,8,8> (adjoint wavefront)", "kernel_ms": kb,
+                     "flops_per_cell": bpc,
                      "peak_source": "152 SMs x 128 FP32 lanes x 2 FLOP x 2070 MHz (derived, nominal clocks)"},
-        "gpu_launches": 3 * args.steps,
+        "forward_kernel": {"kernel": "fwd_poly_kernel<float,6,6,false>", "kernel_ms": kf, "achieved_tflops": ach_f,
+                           "frac": ach_f / peak, "flops_per_cell": fpc,
+                           "cell_updates_per_s": cells / (kf / 1e3)},
+        "gpu_launches": 8 * args.steps,  # forward: 2 increments + wavefront; adjoint: 2 increments + adjoint + 2 gradient conversions
         "clocks": clocks, "device_status": status, "wall_s_timed_region": wall,
     })
 
+    if "fwd" in args.parts:  # forward only (the Gram alone)
+        sf, kff, _, _ = run("f32", args.steps, 2, backward=False)
+        line["forward_only"] = {"value": cells / (statistics.mean(sf) / 1e3), "unit": "cell-updates/s",
+                                "ms_per_step": statistics.mean(sf), "kernel_ms": statistics.mean(kff)}
+
     if "f64" in args.parts:  # FP64 plain wavefront of the same Gram (a few steps)
-        s64, k64, _ = run("f64", max(2, min(3, args.steps)), 1)
+        s64, k64, _, _ = run("f64", max(2, min(3, args.steps)), 1, backward=False)
         g64 = G.cpu().numpy()[pa, pb]
         k64avg = statistics.mean(k64)
         mape["f64"] = float(np.mean(np.abs(g64 - ref) / np.abs(ref)))
@@ -280,8 +338,12 @@ def main():
     if "e2e" in args.parts:  # end to end through the public API with pinned host buffers
         Xh = torch.tensor(X).pin_memory()
         Yh = torch.tensor(Y).pin_memory()
+        Wh = Wt.cpu().pin_memory()
         Gh = torch.empty(nx, nx, dtype=torch.float64).pin_memory()
+        gXh = torch.empty(nx * L, D, dtype=torch.float64).pin_memory()
+        gYh = torch.empty(nx * L, D, dtype=torch.float64).pin_memory()
         ws = sk.gram_workspace(Xt, Yt, scheme="approx", degree=DEGREE, compute="f32")
+        Wd = torch.empty_like(Wt)
         e2e_ms = []
         for it in range(args.warmup + args.steps):
             flush.zero_()
@@ -290,15 +352,20 @@ def main():
             e0.record()
             Xt.copy_(Xh, non_blocking=True)
             Yt.copy_(Yh, non_blocking=True)
-            sk.sigkernel_gram(Xt, Yt, scheme="approx", degree=DEGREE, compute="f32", sort=False, workspace=ws, out=G)
+            Wd.copy_(Wh, non_blocking=True)
+            sk.sigkernel_gram(Xt, Yt, compute="f32", workspace=ws, out=G, **opts)
+            gX, gY = sk.sigkernel_backward(Wd, Xt, Yt, compute="f32", **opts)
             Gh.copy_(G, non_blocking=True)
+            gXh.copy_(gX, non_blocking=True)
+            gYh.copy_(gY, non_blocking=True)
             e1.record()
             e1.synchronize()
             if it >= args.warmup:
                 e2e_ms.append(e0.elapsed_time(e1))
         line["e2e"] = {"value": cells * world / (statistics.mean(e2e_ms) / 1e3), "unit": "cell-updates/s",
-                       "h2d_bytes_per_step": int(Xh.numel() * 8 + Yh.numel() * 8),
-                       "d2h_bytes_per_step": int(Gh.numel() * 8), "ms_per_step": statistics.mean(e2e_ms)}
+                       "h2d_bytes_per_step": int((Xh.numel() + Yh.numel() + Wh.numel()) * 8),
+                       "d2h_bytes_per_step": int((Gh.numel() + gXh.numel() + gYh.numel()) * 8),
+                       "ms_per_step": statistics.mean(e2e_ms)}
 
     if rank == 0:
         if "cpu" in args.parts:

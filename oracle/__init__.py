@@ -58,7 +58,7 @@ def _load():
         lib.sko_grad_entry.restype = d
         lib.sko_grad_entry.argtypes = [i32, P, i64, P, i64, i32, i32, i32, i32, i64, i32]
         lib.sko_grad_pair.restype = None
-        lib.sko_grad_pair.argtypes = [i32, P, i64, P, i64, i32, i32, i32, P, P]
+        lib.sko_grad_pair.argtypes = [i32, P, i64, P, i64, i32, i32, i32, P, P, i32]
         lib.sko_sig_trunc.restype = d
         lib.sko_sig_trunc.argtypes = [P, i64, P, i64, i32, i32]
         lib.sko_signature_level.restype = None
@@ -129,13 +129,14 @@ def grad_entry(x, y, side, p, c, scheme="approx", N=6, lam=0) -> float:
                                   lam, side, p, c)
 
 
-def grad(x, y, scheme="approx", N=6, lam=0):
-    """Full gradients (dk/dx [Lx, d], dk/dy [Ly, d]) of one pair, complex step."""
+def grad(x, y, scheme="approx", N=6, lam=0, threads=0):
+    """Full gradients (dk/dx [Lx, d], dk/dy [Ly, d]) of one pair, complex step, coordinates split
+    over ``threads`` threads (0 = all cores)."""
     x, y = _f64(x), _f64(y)
     gx = np.empty_like(x)
     gy = np.empty_like(y)
     _load().sko_grad_pair(_sid(scheme), _ptr(x), x.shape[0], _ptr(y), y.shape[0], x.shape[1], N, lam,
-                          _ptr(gx), _ptr(gy))
+                          _ptr(gx), _ptr(gy), threads)
     return gx, gy
 
 

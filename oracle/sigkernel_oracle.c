@@ -127,15 +127,42 @@ double sko_grad_entry(int scheme, const double* x, int64_t Lx, const double* y, 
     return cimag(k) / h;
 }
 
-/* Full gradients of one pair: gx[Lx][d] = dk/dx, gy[Ly][d] = dk/dy (either may be NULL). */
+/* Full gradients of one pair: gx[Lx][d] = dk/dx, gy[Ly][d] = dk/dy (either may be NULL); the
+ * coordinates are split over nthreads POSIX threads (0 = all cores). */
+typedef struct {
+    int scheme, d, N, lam;
+    const double *x, *y;
+    int64_t Lx, Ly, first, stride;
+    double *gx, *gy;
+} grad_job_;
+
+static void* grad_worker_(void* arg) {
+    grad_job_* j = (grad_job_*)arg;
+    int64_t nx = j->gx ? j->Lx * j->d : 0, ny = j->gy ? j->Ly * j->d : 0;
+    for (int64_t q = j->first; q < nx + ny; q += j->stride) {
+        if (q < nx)
+            j->gx[q] = sko_grad_entry(j->scheme, j->x, j->Lx, j->y, j->Ly, j->d, j->N, j->lam, 0, q / j->d,
+                                      (int)(q % j->d));
+        else
+            j->gy[q - nx] = sko_grad_entry(j->scheme, j->x, j->Lx, j->y, j->Ly, j->d, j->N, j->lam, 1,
+                                           (q - nx) / j->d, (int)((q - nx) % j->d));
+    }
+    return NULL;
+}
+
 void sko_grad_pair(int scheme, const double* x, int64_t Lx, const double* y, int64_t Ly, int d, int N,
-                   int lam, double* gx, double* gy) {
-    if (gx)
-        for (int64_t p = 0; p < Lx; ++p)
-            for (int c = 0; c < d; ++c) gx[p * d + c] = sko_grad_entry(scheme, x, Lx, y, Ly, d, N, lam, 0, p, c);
-    if (gy)
-        for (int64_t p = 0; p < Ly; ++p)
-            for (int c = 0; c < d; ++c) gy[p * d + c] = sko_grad_entry(scheme, x, Lx, y, Ly, d, N, lam, 1, p, c);
+                   int lam, double* gx, double* gy, int nthreads) {
+    if (nthreads <= 0) nthreads = (int)sysconf(_SC_NPROCESSORS_ONLN);
+    if (nthreads < 1) nthreads = 1;
+    if (nthreads > 512) nthreads = 512;
+    pthread_t th[512];
+    grad_job_ jobs[512];
+    for (int t = 0; t < nthreads; ++t) {
+        grad_job_ jb = {scheme, d, N, lam, x, y, Lx, Ly, t, nthreads, gx, gy};
+        jobs[t] = jb;
+        pthread_create(&th[t], NULL, grad_worker_, &jobs[t]);
+    }
+    for (int t = 0; t < nthreads; ++t) pthread_join(th[t], NULL);
 }
 
 /* ----------------------------------------------------------------------------------------- */
