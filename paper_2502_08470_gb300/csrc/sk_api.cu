@@ -14,13 +14,6 @@
 
 namespace sk {
 
-__constant__ float c_inv_f[kNEMax + 2];
-__constant__ double c_inv_d[kNEMax + 2];
-__constant__ float c_hank_f[kNEMax + 1][kNMaxApprox + 1];
-__constant__ double c_hank_d[kNEMax + 1][kNMaxApprox + 1];
-__constant__ double c_rfact_d[kNEMax + 1];
-__constant__ float c_proj_f[kNMaxInterp + 1][kNMaxInterp + 1][kJMax];
-__constant__ double c_proj_d[kNMaxInterp + 1][kNMaxInterp + 1][kJMax];
 __device__ int g_sk_error = 0;
 
 namespace {
@@ -44,97 +37,6 @@ int fail(int code, const char* fmt, ...) {
         cudaError_t e_ = (call);                                                              \
         if (e_ != cudaSuccess) return fail(SK_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
     } while (0)
-
-// ------------------------------------------------------------------------------------------
-// Constant tables, uploaded once per device.
-// ------------------------------------------------------------------------------------------
-// Interpolation projection: for order N, the Chebyshev extrema of [0,1] are
-// u_r = (1 + cos(pi r / N)) / 2, r = 0..N (eq. (chebextr) with N+1 nodes, Definition
-// "interpooperator").  A factorial-scaled series c (f(u) = sum_j c_j u^j / j!) sampled at the nodes
-// and interpolated by a degree-N polynomial has factorial-scaled coefficients
-//   a'_n = sum_j n! [V^{-1} W]_{n j} / j! c_j,   V_{rn} = u_r^n (n <= N),  W_{rj} = u_r^j,
-// and columns j <= N of V^{-1} W are the identity.  Solved in long double with partial pivoting.
-void build_projection(int N, double (*out)[kJMax]) {
-    const int n1 = N + 1;
-    long double V[kNMaxInterp + 1][kNMaxInterp + 1];
-    long double W[kNMaxInterp + 1][kJMax];
-    const long double pi = 3.141592653589793238462643383279502884L;
-    for (int r = 0; r < n1; ++r) {
-        long double u = 0.5L * (1.0L + cosl(pi * r / N));
-        long double p = 1.0L;
-        for (int n = 0; n < n1; ++n) { V[r][n] = p; p *= u; }
-        for (int jj = 0; jj < kJMax; ++jj) { W[r][jj] = p; p *= u; }  // u^{N+1+jj}
-    }
-    for (int col = 0; col < n1; ++col) {  // Gaussian elimination on [V | W]
-        int piv = col;
-        for (int r = col + 1; r < n1; ++r)
-            if (fabsl(V[r][col]) > fabsl(V[piv][col])) piv = r;
-        for (int k = 0; k < n1; ++k) { long double t = V[col][k]; V[col][k] = V[piv][k]; V[piv][k] = t; }
-        for (int k = 0; k < kJMax; ++k) { long double t = W[col][k]; W[col][k] = W[piv][k]; W[piv][k] = t; }
-        for (int r = 0; r < n1; ++r) {
-            if (r == col) continue;
-            long double l = V[r][col] / V[col][col];
-            for (int k = 0; k < n1; ++k) V[r][k] -= l * V[col][k];
-            for (int k = 0; k < kJMax; ++k) W[r][k] -= l * W[col][k];
-        }
-    }
-    long double fact[kNEMax + 2];
-    fact[0] = 1.0L;
-    for (int k = 1; k < kNEMax + 2; ++k) fact[k] = fact[k - 1] * k;
-    for (int n = 0; n < n1; ++n)
-        for (int jj = 0; jj < kJMax; ++jj) {
-            int j = N + 1 + jj;
-            long double g = W[n][jj] / V[n][n];
-            out[n][jj] = (j <= kNEMax) ? static_cast<double>(g * fact[n] / fact[j]) : 0.0;
-        }
-}
-
-std::mutex g_table_mu;
-bool g_tables_ready[64] = {false};
-
-int ensure_tables() {
-    int dev = 0;
-    SK_CUDA(cudaGetDevice(&dev));
-    if (dev < 0 || dev >= 64) return fail(SK_ERR_UNSUPPORTED, "device index %d", dev);
-    std::lock_guard<std::mutex> lock(g_table_mu);
-    if (g_tables_ready[dev]) return SK_OK;
-    static double inv_d[kNEMax + 2], hank_d[kNEMax + 1][kNMaxApprox + 1], rfact_d[kNEMax + 1];
-    static float inv_f[kNEMax + 2], hank_f[kNEMax + 1][kNMaxApprox + 1];
-    static double proj_d[kNMaxInterp + 1][kNMaxInterp + 1][kJMax];
-    static float proj_f[kNMaxInterp + 1][kNMaxInterp + 1][kJMax];
-    inv_d[0] = 0.0;
-    for (int m = 1; m < kNEMax + 2; ++m) inv_d[m] = 1.0 / m;
-    for (int n = 0; n <= kNEMax; ++n) {
-        long double r = 1.0L;  // n!/(n+k)! = prod_{i=1..k} 1/(n+i)
-        hank_d[n][0] = 1.0;
-        for (int k = 1; k <= kNMaxApprox; ++k) {
-            r /= (n + k);
-            hank_d[n][k] = static_cast<double>(r);
-        }
-    }
-    long double f = 1.0L;
-    for (int n = 0; n <= kNEMax; ++n) {
-        if (n > 0) f *= n;
-        rfact_d[n] = static_cast<double>(1.0L / f);
-    }
-    memset(proj_d, 0, sizeof(proj_d));
-    for (int N = 2; N <= kNMaxInterp; ++N) build_projection(N, proj_d[N]);
-    for (int m = 0; m < kNEMax + 2; ++m) inv_f[m] = static_cast<float>(inv_d[m]);
-    for (int n = 0; n <= kNEMax; ++n)
-        for (int k = 0; k <= kNMaxApprox; ++k) hank_f[n][k] = static_cast<float>(hank_d[n][k]);
-    for (int N = 0; N <= kNMaxInterp; ++N)
-        for (int n = 0; n <= kNMaxInterp; ++n)
-            for (int jj = 0; jj < kJMax; ++jj) proj_f[N][n][jj] = static_cast<float>(proj_d[N][n][jj]);
-    SK_CUDA(cudaMemcpyToSymbol(c_inv_d, inv_d, sizeof(inv_d)));
-    SK_CUDA(cudaMemcpyToSymbol(c_inv_f, inv_f, sizeof(inv_f)));
-    SK_CUDA(cudaMemcpyToSymbol(c_hank_d, hank_d, sizeof(hank_d)));
-    SK_CUDA(cudaMemcpyToSymbol(c_hank_f, hank_f, sizeof(hank_f)));
-    SK_CUDA(cudaMemcpyToSymbol(c_rfact_d, rfact_d, sizeof(rfact_d)));
-    SK_CUDA(cudaMemcpyToSymbol(c_proj_d, proj_d, sizeof(proj_d)));
-    SK_CUDA(cudaMemcpyToSymbol(c_proj_f, proj_f, sizeof(proj_f)));
-    g_tables_ready[dev] = true;
-    return SK_OK;
-}
 
 // ------------------------------------------------------------------------------------------
 // Increments dx_i = x_{i+1} - x_i (or the caller's increments) in the compute type, rows
@@ -354,7 +256,6 @@ int run_forward(const sk_paths* X, const sk_paths* Y, int32_t d, int32_t dtype, 
     if (rc != SK_OK) return rc;
     if (npairs == 0) return SK_OK;
     if (!out) return fail(SK_ERR_INVALID_ARG, "output pointer is NULL");
-    if ((rc = ensure_tables()) != SK_OK) return rc;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     bool own = false;
     if (!ws) {
@@ -607,7 +508,6 @@ int run_backward(const sk_paths* X, const sk_paths* Y, int32_t d, int32_t dtype,
         return fail(SK_ERR_INVALID_ARG, "X and Y are the same paths: pass grad_Y = NULL or grad_Y = grad_X");
     if (npairs == 0) return SK_OK;
     if (!gout) return fail(SK_ERR_INVALID_ARG, "grad_out is NULL");
-    if ((rc = ensure_tables()) != SK_OK) return rc;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     bool own = false;
     if (!ws) {

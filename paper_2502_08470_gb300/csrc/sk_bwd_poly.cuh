@@ -423,7 +423,7 @@ __global__ void __launch_bounds__(kFwdWarps * 32, (bwd_min_blocks<T, N, K>()))
                         if (row == rows - 1 && rj == cols - 1) {  // seed from the endpoint average
 #pragma unroll
                             for (int n = 0; n <= N; ++n) {
-                                ga_in[n] = static_cast<T>(0.5 * c_rfact_d[n]);
+                                ga_in[n] = static_cast<T>(0.5 * cx_rfact(n));
                                 gb_in[n] = ga_in[n];
                             }
                             gae_in = 0;

@@ -6,6 +6,7 @@
 #include <stdint.h>
 
 #include "../../include/sigkernel.h"
+#include "sk_projection_table.h"
 
 namespace sk {
 
@@ -21,49 +22,33 @@ constexpr int kMaxRefined = 131072;  // bound on (rows per path) << lambda (keep
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kFwdWarps = 4;     // warps per block of the persistent wavefront kernels
 
-// ---------------------------------------------------------------------------------------------
-// Constant tables (uploaded once per device by the host code in sk_api.cu).
-//   c_inv[m]        1/m                      (m >= 1; c_inv[0] unused)
-//   c_hank[n][k]    n!/(n+k)!                (Hankel coupling of the opposite edge, k >= 1)
-//   c_rfact[n]      1/n!                     (endpoint evaluation of a factorial-scaled series)
-//   c_proj[N][n][jj]  interpolation projection for order N: the factorial-scaled interpolant
-//                   at the N+1 Chebyshev extrema of a series with coefficient j = N+1+jj
-//                   contributes c_proj[N][n][jj] to coefficient n (columns j <= N are the
-//                   identity and are not stored).
-// ---------------------------------------------------------------------------------------------
-extern __constant__ float c_inv_f[kNEMax + 2];
-extern __constant__ double c_inv_d[kNEMax + 2];
-extern __constant__ float c_hank_f[kNEMax + 1][kNMaxApprox + 1];
-extern __constant__ double c_hank_d[kNEMax + 1][kNMaxApprox + 1];
-extern __constant__ double c_rfact_d[kNEMax + 1];
-extern __constant__ float c_proj_f[kNMaxInterp + 1][kNMaxInterp + 1][kJMax];
-extern __constant__ double c_proj_d[kNMaxInterp + 1][kNMaxInterp + 1][kJMax];
-
 // Device error word: the first SK_ERR_* code recorded by any kernel of the library.
 extern __device__ int g_sk_error;
 
 __device__ __forceinline__ void record_error(int code) { atomicCAS(&g_sk_error, 0, code); }
 
 // Coefficients that depend only on the (compile-time) indices of the unrolled cell loops are
-// computed by constexpr functions, so they fold into instruction immediates instead of being
-// fetched from the constant bank every cell: 1/m and the Hankel coefficient n!/(n+k)!.
+// constexpr, so they fold into instruction immediates instead of being fetched from the constant
+// bank every cell: 1/m, the Hankel coefficient n!/(n+k)!, and the interpolation projection
+// kProj (sk_projection_table.h, generated by gen_projection_table.py).
 __host__ __device__ constexpr double cx_inv(int m) { return 1.0 / static_cast<double>(m); }
 __host__ __device__ constexpr double cx_hank(int n, int k) {
     double r = 1.0;
     for (int i = 1; i <= k; ++i) r /= static_cast<double>(n + i);
     return r;
 }
+__host__ __device__ constexpr double cx_rfact(int n) { return cx_hank(0, n); }  // 1/n!
 
 template <typename T> struct Tab;
 template <> struct Tab<float> {
     static __device__ __forceinline__ float inv(int m) { return static_cast<float>(cx_inv(m)); }
     static __device__ __forceinline__ float hank(int n, int k) { return static_cast<float>(cx_hank(n, k)); }
-    static __device__ __forceinline__ float proj(int N, int n, int jj) { return c_proj_f[N][n][jj]; }
+    static __device__ __forceinline__ float proj(int N, int n, int jj) { return static_cast<float>(kProj[N][n][jj]); }
 };
 template <> struct Tab<double> {
     static __device__ __forceinline__ double inv(int m) { return cx_inv(m); }
     static __device__ __forceinline__ double hank(int n, int k) { return cx_hank(n, k); }
-    static __device__ __forceinline__ double proj(int N, int n, int jj) { return c_proj_d[N][n][jj]; }
+    static __device__ __forceinline__ double proj(int N, int n, int jj) { return kProj[N][n][jj]; }
 };
 
 // Exact power of two 2^e from its IEEE-754 bits (|e| within the normal range of T).

@@ -47,7 +47,7 @@ __device__ __forceinline__ void build_exp_series(T M, float tau, T (&e)[NE + 1])
             double md = static_cast<double>(M), v = 1.0;
 #pragma unroll
             for (int m = 1; m <= NE; ++m) {
-                v *= md * c_inv_d[m];
+                v *= md * cx_inv(m);
                 e[m] = static_cast<float>(v);
             }
             return;
@@ -103,7 +103,7 @@ template <typename T, int NE>
 __device__ __forceinline__ double series_at_one(const T (&c)[NE + 1]) {
     double acc = 0.0;
 #pragma unroll
-    for (int n = NE; n >= 0; --n) acc = fma(static_cast<double>(c[n]), c_rfact_d[n], acc);
+    for (int n = NE; n >= 0; --n) acc = fma(static_cast<double>(c[n]), cx_rfact(n), acc);
     return acc;
 }
 
