@@ -88,26 +88,27 @@ def projection(N):
 
 def main():
     print("// Generated by gen_projection_table.py; do not edit.  Interpolation projection of the")
-    print("// polynomial interpolation scheme in factorial-scaled coordinates: kProj[N][n][jj] is the")
-    print("// weight of series coefficient j = N + 1 + jj in interpolant coefficient n (order N).")
+    print("// polynomial interpolation scheme in factorial-scaled coordinates: proj_coef(N, n, jj) is the")
+    print("// weight of series coefficient j = N + 1 + jj in interpolant coefficient n (order N).  A")
+    print("// constexpr function of its indices, so unrolled device loops fold it into immediates.")
     print("#pragma once")
     print("")
     print("namespace sk {")
     print("")
     print(f"constexpr int kProjNMax = {NMAX};")
     print(f"constexpr int kProjJMax = {JMAX};")
-    print(f"__host__ __device__ constexpr double kProj[{NMAX + 1}][{NMAX + 1}][{JMAX}] = {{")
-    for N in range(NMAX + 1):
-        if N < 2:
-            print("    {},")
-            continue
+    print("__host__ __device__ constexpr double proj_coef(int N, int n, int jj) {")
+    print("    switch (N * 1024 + n * 32 + jj) {")
+    for N in range(2, NMAX + 1):
         P = projection(N)
-        print("    {")
         for n in range(N + 1):
-            vals = ", ".join(f"{float(v):.17g}" for v in P[n])
-            print(f"        {{{vals}}},")
-        print("    },")
-    print("};")
+            for jj in range(JMAX):
+                v = float(P[n][jj])
+                if v != 0.0:
+                    print(f"        case {N * 1024 + n * 32 + jj}: return {v:.17g};")
+    print("        default: return 0.0;")
+    print("    }")
+    print("}")
     print("")
     print("}  // namespace sk")
 

@@ -376,9 +376,7 @@ int plan_backward(const sk_paths* X, const sk_paths* Y, int32_t d, int32_t dtype
     const int64_t rows_max = std::max<int64_t>(X->max_len << lam, 1);
     b.cols_max = std::max<int64_t>(Y->max_len << lam, 1);
     b.strips_max = (rows_max + 31) / 32;
-    const int64_t period = std::max<int64_t>(b.cols_max, 32);
-    const int64_t nsteps = (b.strips_max - 1) * period + 31 + b.cols_max;
-    b.seg_max = (nsteps + b.K - 1) / b.K;
+    b.seg_max = (b.cols_max + 31 + b.K - 1) / b.K;  // checkpoints of one strip
     int64_t off = 0;
     off += b.seg_max * (2 * N + 2) * 32 * esize + b.seg_max * 32 * 4;
     off = static_cast<int64_t>(align256(off));
@@ -391,7 +389,6 @@ int plan_backward(const sk_paths* X, const sk_paths* Y, int32_t d, int32_t dtype
     b.off_rexp = off;
     off += static_cast<int64_t>(align256(b.cols_max * 4));
     b.off_ybar = off;
-    off += static_cast<int64_t>(align256(std::max<int64_t>(Y->max_len, 1) * p.dpad * esize));
     b.slot_bytes = off;
     int dev = 0, sms = 0, per_sm = 0;
     SK_CUDA(cudaGetDevice(&dev));

@@ -14,13 +14,17 @@
 // d k / d dx_i = sum_j (dk/dM_ij) dy_j, d k / d dy_j = sum_i (dk/dM_ij) dx_i.
 //
 // Schedule (one warp per pair, same lane/strip layout as the forward kernel):
-//   F  forward replay of the whole pair; every strip's hand-off column and, every K steps, each
-//      lane's cell inputs (an antidiagonal checkpoint) go to per-warp scratch.
-//   R  for each K-step segment from the last to the first: re-run its K forward steps from the
-//      checkpoint into a shared-memory stack, then walk them backward applying the adjoint; the
-//      right-edge adjoint moves one lane down per step (__shfl_down_sync) together with the
-//      column partial sums of dk/dy, lane 0 hands it to lane 31 of the strip below through a
-//      per-warp buffer, and each lane keeps dk/dx of its row in registers.
+//   F  forward replay of the whole pair; every strip's hand-off column goes to per-warp scratch
+//      and the exponent of k_hat is kept.
+//   for each 32-row strip, from the top one down:
+//   R1 re-run the strip's forward from its hand-off column, storing every K steps each lane's
+//      cell inputs (an antidiagonal checkpoint) in a per-warp buffer small enough for L2;
+//   R2 for each K-step segment from the last to the first: re-run its K forward steps from the
+//      checkpoint into a shared-memory stack, then walk them backward applying the adjoint.  The
+//      right-edge adjoint moves one lane down per step (__shfl_down_sync) together with the column
+//      partial sums of dk/dy (lane 0 adds them to the y gradient with atomics), lane 0 hands the
+//      adjoint to lane 31 of the strip below through a per-warp buffer, and each lane keeps dk/dx
+//      of its row in shared memory.
 // FP32 keeps power-of-two exponents per lane for the forward values (as in the forward kernel)
 // and, separately, for the adjoints; dk/dM is accumulated relative to 2^E(k) of the pair.
 #pragma once
@@ -51,13 +55,63 @@ __device__ __forceinline__ T pow2c(int e) {  // 2^e, or 0 below the normal range
 }
 
 template <typename T, int N>
+__device__ __forceinline__ void set_unit(T (&v)[N + 1]) {
+#pragma unroll
+    for (int n = 0; n <= N; ++n) v[n] = (n == 0) ? T(1) : T(0);
+}
+
+// Bring (a, ea) and (b, eb) to the larger exponent (FP32 only).
+template <typename T, int N>
+__device__ __forceinline__ void align_inputs(T (&a)[N + 1], int& ea, T (&b)[N + 1], int eb) {
+    if (ea == eb) return;
+    if (ea > eb) {
+        const T f = pow2c<T>(eb - ea);
+#pragma unroll
+        for (int n = 0; n <= N; ++n) b[n] *= f;
+    } else {
+        const T f = pow2c<T>(ea - eb);
+#pragma unroll
+        for (int n = 0; n <= N; ++n) a[n] *= f;
+        ea = eb;
+    }
+}
+
+// One forward cell of the approximation scheme with the forward kernel's renormalisation:
+// (a, b) -> (a, bo) in place, exponent ea.
+template <typename T, int N>
+__device__ __forceinline__ void fwd_cell(T (&a)[N + 1], const T (&b)[N + 1], T M, float tau, T (&bo)[N + 1],
+                                         int& ea) {
+    T e[N + 1], ct[N + 1], cr[N + 1];
+    build_exp_series<T, N>(M, tau, e);
+    cell_series<T, N, N, false>(a, b, e, ct, cr);
+#pragma unroll
+    for (int n = 0; n <= N; ++n) { a[n] = ct[n]; bo[n] = cr[n]; }
+    if constexpr (std::is_same<T, float>::value) {
+        const float mag = fmaxf(fabsf(a[0]), fabsf(bo[0]));
+        if (mag > 0x1p64f) {
+#pragma unroll
+            for (int n = 0; n <= N; ++n) { a[n] *= 0x1p-64f; bo[n] *= 0x1p-64f; }
+            ea += 64;
+        } else if (mag < 0x1p-64f) {
+            float full = 0.f;
+#pragma unroll
+            for (int n = 0; n <= N; ++n) full = fmaxf(full, fmaxf(fabsf(a[n]), fabsf(bo[n])));
+            if (full < 0x1p-64f && full > 0.f) {
+#pragma unroll
+                for (int n = 0; n <= N; ++n) { a[n] *= 0x1p64f; bo[n] *= 0x1p64f; }
+                ea -= 64;
+            }
+        }
+    }
+}
+
+template <typename T, int N>
 __device__ __forceinline__ void cell_adjoint(const T (&a)[N + 1], const T (&b)[N + 1], const T (&e)[N + 1],
                                              const T (&ga)[N + 1], const T (&gb)[N + 1], T (&ra)[N + 1],
                                              T (&rb)[N + 1], T& mbar) {
     T al[N + 1], be[N + 1];
 #pragma unroll
     for (int n = 0; n <= N; ++n) { al[n] = ga[n] * e[n]; be[n] = gb[n] * e[n]; }
-    // abar_k, bbar_k
 #pragma unroll
     for (int k = 0; k <= N; ++k) {
         T va = T(0), vb = T(0);
@@ -76,7 +130,6 @@ __device__ __forceinline__ void cell_adjoint(const T (&a)[N + 1], const T (&b)[N
         ra[k] = va;
         rb[k] = vb;
     }
-    // ebar_m for m >= 1 and Mbar
     T mb = T(0);
 #pragma unroll
     for (int m = 1; m <= N; ++m) {
@@ -99,8 +152,8 @@ __device__ __forceinline__ void cell_adjoint(const T (&a)[N + 1], const T (&b)[N
 }
 
 // Shared memory of one warp: the K-step stack (a[N+1], b[N+1], M per lane, plus exponents),
-// then each lane's dk/dx accumulator of its row ([32][dpad + 4] floats; the pad spreads the
-// lanes' 16-byte accesses over all banks).
+// then each lane's dk/dx accumulator of its row ([32][dpad + 4]; the pad spreads the lanes'
+// accesses over all banks).
 template <typename T, int N, int K>
 __host__ __device__ constexpr int bwd_stack_bytes() {
     return K * (2 * N + 3) * 32 * static_cast<int>(sizeof(T)) + K * 32 * 4;
@@ -110,7 +163,7 @@ __host__ __device__ constexpr int bwd_xacc_bytes(int dpad) { return 32 * (dpad +
 
 template <typename T, int N, int K>
 constexpr int bwd_min_blocks() {
-    return sizeof(T) == 8 ? 1 : 2;
+    return sizeof(T) == 8 ? 1 : 3;
 }
 
 template <typename T, int N, int K, int DMAX>
@@ -124,14 +177,13 @@ __global__ void __launch_bounds__(kFwdWarps * 32, (bwd_min_blocks<T, N, K>()))
     const int wib = threadIdx.x >> 5;
     const int64_t slot = static_cast<int64_t>(blockIdx.x) * (blockDim.x >> 5) + wib;
     char* base = static_cast<char*>(L.scratch) + slot * L.scratch_stride;
-    // checkpoints: [seg][2N+2][32] T then [seg][32] int
+    // strip checkpoints: [seg][2N+2][32] T then [seg][32] int
     T* ckpt = reinterpret_cast<T*>(base);
     int* ckpt_e = reinterpret_cast<int*>(ckpt + B.seg_max * (2 * N + 2) * 32);
     T* fbuf = reinterpret_cast<T*>(base + B.off_fbuf);          // [strip][col][N+1]
     int* fexp = reinterpret_cast<int*>(base + B.off_fexp);      // [strip][col]
     T* rbuf = reinterpret_cast<T*>(base + B.off_rbuf);          // [col][N+1]
     int* rexp = reinterpret_cast<int*>(base + B.off_rexp);      // [col]
-    T* ybar = reinterpret_cast<T*>(base + B.off_ybar);          // [coarse col][dpad]
     const int dpad = L.dpad;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     unsigned char* wsm = smem_raw + wib * (bwd_stack_bytes<T, N, K>() + bwd_xacc_bytes<T>(dpad));
@@ -163,113 +215,68 @@ __global__ void __launch_bounds__(kFwdWarps * 32, (bwd_min_blocks<T, N, K>()))
         const int nstrips = (rows + 31) >> 5;
         const int last_lane = (rows - 1) - ((nstrips - 1) << 5);
         const int nsteps = (nstrips - 1) * period + last_lane + cols;
-        const int nseg = (nsteps + K - 1) / K;
         const T sub = pow2t<T>(-2 * lam);
         const T* xbase = incX + P.xs * dpad;
         const T* ybase = incY + P.ys * dpad;
 
-        // ------------------------------------------------------------------ phase F
-        T a[N + 1], bo[N + 1];
+        // ------------------------------------------------------------------ F
+        int ek = 0;
+        {
+            T a[N + 1], bo[N + 1];
 #pragma unroll
-        for (int n = 0; n <= N; ++n) { a[n] = T(0); bo[n] = T(0); }
-        int ea = 0, eo = 0, ek = 0;
-        int jj = -lane, s = 0;
-        for (int step = 0; step < nsteps; ++step) {
-            T b[N + 1];
+            for (int n = 0; n <= N; ++n) { a[n] = T(0); bo[n] = T(0); }
+            int ea = 0, eo = 0;
+            int jj = -lane, s = 0;
+            for (int step = 0; step < nsteps; ++step) {
+                T b[N + 1];
 #pragma unroll
-            for (int n = 0; n <= N; ++n) b[n] = __shfl_up_sync(kFull, bo[n], 1);
-            int eb = kRescale ? __shfl_up_sync(kFull, eo, 1) : 0;
-            const int row = (s << 5) + lane;
-            const bool active = jj >= 0 && jj < cols && row < rows;
-            if (active) {
-                if (lane == 0) {
-                    if (s == 0) {
+                for (int n = 0; n <= N; ++n) b[n] = __shfl_up_sync(kFull, bo[n], 1);
+                int eb = kRescale ? __shfl_up_sync(kFull, eo, 1) : 0;
+                const int row = (s << 5) + lane;
+                const bool active = jj >= 0 && jj < cols && row < rows;
+                if (active) {
+                    if (lane == 0) {
+                        if (s == 0) {
+                            set_unit<T, N>(b);
+                            eb = 0;
+                        } else {
+                            const T* src = fbuf + (static_cast<int64_t>(s - 1) * B.cols_max + jj) * (N + 1);
 #pragma unroll
-                        for (int n = 0; n <= N; ++n) b[n] = (n == 0) ? T(1) : T(0);
-                        eb = 0;
-                    } else {
-                        const T* src = fbuf + (static_cast<int64_t>(s - 1) * B.cols_max + jj) * (N + 1);
-#pragma unroll
-                        for (int n = 0; n <= N; ++n) b[n] = src[n];
-                        if (kRescale) eb = fexp[static_cast<int64_t>(s - 1) * B.cols_max + jj];
-                    }
-                }
-                if (jj == 0) {
-#pragma unroll
-                    for (int n = 0; n <= N; ++n) a[n] = (n == 0) ? T(1) : T(0);
-                    ea = 0;
-                }
-                if (kRescale && ea != eb) {
-                    if (ea > eb) {
-                        const T f = pow2c<T>(eb - ea);
-#pragma unroll
-                        for (int n = 0; n <= N; ++n) b[n] *= f;
-                    } else {
-                        const T f = pow2c<T>(ea - eb);
-#pragma unroll
-                        for (int n = 0; n <= N; ++n) a[n] *= f;
-                        ea = eb;
-                    }
-                }
-            }
-            if (step % K == 0) {  // antidiagonal checkpoint: this step's cell inputs
-                T* cp = ckpt + static_cast<int64_t>(step / K) * (2 * N + 2) * 32;
-#pragma unroll
-                for (int n = 0; n <= N; ++n) {
-                    cp[n * 32 + lane] = a[n];
-                    cp[(N + 1 + n) * 32 + lane] = b[n];
-                }
-                ckpt_e[static_cast<int64_t>(step / K) * 32 + lane] = ea;
-            }
-            if (active) {
-                const T M = row_dot<T>(xbase + static_cast<int64_t>(row >> lam) * dpad,
-                                       ybase + static_cast<int64_t>(jj >> lam) * dpad, L.nvec) * sub;
-                T e[N + 1], ct[N + 1], cr[N + 1];
-                build_exp_series<T, N>(M, L.tau, e);
-                cell_series<T, N, N, false>(a, b, e, ct, cr);
-                if (row == rows - 1 && jj == cols - 1) {
-                    double v = 0.5 * (series_at_one<T, N>(ct) + series_at_one<T, N>(cr));
-                    int e2 = 0;
-                    if (v != 0.0) frexp(v, &e2);
-                    ek = ea + e2;
-                }
-#pragma unroll
-                for (int n = 0; n <= N; ++n) { a[n] = ct[n]; bo[n] = cr[n]; }
-                if (kRescale) {
-                    const float mag = fmaxf(fabsf(static_cast<float>(a[0])), fabsf(static_cast<float>(bo[0])));
-                    if (mag > 0x1p64f) {
-#pragma unroll
-                        for (int n = 0; n <= N; ++n) { a[n] *= pow2t<T>(-64); bo[n] *= pow2t<T>(-64); }
-                        ea += 64;
-                    } else if (mag < 0x1p-64f) {
-                        float full = 0.f;
-#pragma unroll
-                        for (int n = 0; n <= N; ++n)
-                            full = fmaxf(full, fmaxf(fabsf(static_cast<float>(a[n])), fabsf(static_cast<float>(bo[n]))));
-                        if (full < 0x1p-64f && full > 0.f) {
-#pragma unroll
-                            for (int n = 0; n <= N; ++n) { a[n] *= pow2t<T>(64); bo[n] *= pow2t<T>(64); }
-                            ea -= 64;
+                            for (int n = 0; n <= N; ++n) b[n] = src[n];
+                            if (kRescale) eb = fexp[static_cast<int64_t>(s - 1) * B.cols_max + jj];
                         }
                     }
-                }
-                eo = ea;
-                if (lane == 31 && s + 1 < nstrips) {
-                    T* dst = fbuf + (static_cast<int64_t>(s) * B.cols_max + jj) * (N + 1);
+                    if (jj == 0) {
+                        set_unit<T, N>(a);
+                        ea = 0;
+                    }
+                    if (kRescale) align_inputs<T, N>(a, ea, b, eb);
+                    const T M = row_dot<T>(xbase + static_cast<int64_t>(row >> lam) * dpad,
+                                           ybase + static_cast<int64_t>(jj >> lam) * dpad, L.nvec) * sub;
+                    fwd_cell<T, N>(a, b, M, L.tau, bo, ea);
+                    if (row == rows - 1 && jj == cols - 1) {
+                        double v = 0.5 * (series_at_one<T, N>(a) + series_at_one<T, N>(bo));
+                        int e2 = 0;
+                        if (v != 0.0) frexp(v, &e2);
+                        ek = ea + e2;
+                    }
+                    eo = ea;
+                    if (lane == 31 && s + 1 < nstrips) {
+                        T* dst = fbuf + (static_cast<int64_t>(s) * B.cols_max + jj) * (N + 1);
 #pragma unroll
-                    for (int n = 0; n <= N; ++n) dst[n] = bo[n];
-                    if (kRescale) fexp[static_cast<int64_t>(s) * B.cols_max + jj] = eo;
+                        for (int n = 0; n <= N; ++n) dst[n] = bo[n];
+                        if (kRescale) fexp[static_cast<int64_t>(s) * B.cols_max + jj] = eo;
+                    }
                 }
+                __syncwarp();
+                if (++jj == period) { jj = 0; ++s; }
             }
-            __syncwarp();
-            if (++jj == period) { jj = 0; ++s; }
         }
         ek = __shfl_sync(kFull, ek, last_lane);
-        for (int64_t i = lane; i < P.ly * dpad; i += 32) ybar[i] = T(0);
-        __syncwarp();
+        const double gscale = gbar * pow2d(ek);
 
-        // ------------------------------------------------------------------ phase R
-        T gra[N + 1], gbo[N + 1];  // adjoint of the lane's a (row state) and of its last b output
+        // adjoint state of the lane
+        T gra[N + 1], gbo[N + 1];
         int gea = kZeroExp, gbe = kZeroExp;
         T ysum[DMAX];
 #pragma unroll
@@ -278,68 +285,103 @@ __global__ void __launch_bounds__(kFwdWarps * 32, (bwd_min_blocks<T, N, K>()))
         for (int c = 0; c < DMAX; ++c) ysum[c] = T(0);
         for (int c = 0; c < dpad; ++c) xacc[c] = T(0);
 
-        for (int g = nseg - 1; g >= 0; --g) {
-            const int t0 = g * K;
-            const int tn = min(K, nsteps - t0);
-            // re-run the segment's forward steps into the stack
+        for (int s = nstrips - 1; s >= 0; --s) {
+            const int row = (s << 5) + lane;
+            const int ts = (s == nstrips - 1 ? last_lane : 31) + cols;  // steps of this strip
+            const int nseg = (ts + K - 1) / K;
+            const T* xrow = xbase + static_cast<int64_t>(min(row, rows - 1) >> lam) * dpad;
+            // -------------------------------------------------------------- R1
             {
-                const T* cp = ckpt + static_cast<int64_t>(g) * (2 * N + 2) * 32;
-                T ra[N + 1], rb[N + 1], rbo[N + 1];
+                T a[N + 1], bo[N + 1];
 #pragma unroll
-                for (int n = 0; n <= N; ++n) {
-                    ra[n] = cp[n * 32 + lane];
-                    rb[n] = cp[(N + 1 + n) * 32 + lane];
-                    rbo[n] = T(0);
+                for (int n = 0; n <= N; ++n) { a[n] = T(0); bo[n] = T(0); }
+                int ea = 0, eo = 0;
+                for (int tt = 0; tt < ts; ++tt) {
+                    T b[N + 1];
+#pragma unroll
+                    for (int n = 0; n <= N; ++n) b[n] = __shfl_up_sync(kFull, bo[n], 1);
+                    int eb = kRescale ? __shfl_up_sync(kFull, eo, 1) : 0;
+                    const int jj = tt - lane;
+                    const bool active = jj >= 0 && jj < cols && row < rows;
+                    if (active) {
+                        if (lane == 0) {
+                            if (s == 0) {
+                                set_unit<T, N>(b);
+                                eb = 0;
+                            } else {
+                                const T* src = fbuf + (static_cast<int64_t>(s - 1) * B.cols_max + jj) * (N + 1);
+#pragma unroll
+                                for (int n = 0; n <= N; ++n) b[n] = src[n];
+                                if (kRescale) eb = fexp[static_cast<int64_t>(s - 1) * B.cols_max + jj];
+                            }
+                        }
+                        if (jj == 0) {
+                            set_unit<T, N>(a);
+                            ea = 0;
+                        }
+                        if (kRescale) align_inputs<T, N>(a, ea, b, eb);
+                    }
+                    if (tt % K == 0) {  // antidiagonal checkpoint: this step's cell inputs
+                        T* cp = ckpt + static_cast<int64_t>(tt / K) * (2 * N + 2) * 32;
+#pragma unroll
+                        for (int n = 0; n <= N; ++n) {
+                            cp[n * 32 + lane] = a[n];
+                            cp[(N + 1 + n) * 32 + lane] = b[n];
+                        }
+                        ckpt_e[static_cast<int64_t>(tt / K) * 32 + lane] = ea;
+                    }
+                    if (active) {
+                        const T M = row_dot<T>(xrow, ybase + static_cast<int64_t>(jj >> lam) * dpad, L.nvec) * sub;
+                        fwd_cell<T, N>(a, b, M, L.tau, bo, ea);
+                        eo = ea;
+                    }
                 }
-                int rea = ckpt_e[static_cast<int64_t>(g) * 32 + lane], reo = 0;
-                int tt = t0 - lane;
-                int rs = tt >= 0 ? tt / period : 0;
-                int rj = tt >= 0 ? tt - rs * period : tt;
+            }
+            __syncwarp();
+            // -------------------------------------------------------------- R2
+            for (int g = nseg - 1; g >= 0; --g) {
+                const int t0 = g * K;
+                const int tn = min(K, ts - t0);
+                {   // re-run the segment's forward steps into the stack
+                    const T* cp = ckpt + static_cast<int64_t>(g) * (2 * N + 2) * 32;
+                    T ra[N + 1], rb[N + 1], rbo[N + 1];
+#pragma unroll
+                    for (int n = 0; n <= N; ++n) {
+                        ra[n] = cp[n * 32 + lane];
+                        rb[n] = cp[(N + 1 + n) * 32 + lane];
+                        rbo[n] = T(0);
+                    }
+                    int rea = ckpt_e[static_cast<int64_t>(g) * 32 + lane], reo = 0;
 #pragma unroll 1
-                for (int k = 0; k < K; ++k) {
-                    if (k < tn) {
-                        const int row = (rs << 5) + lane;
-                        const bool active = rj >= 0 && rj < cols && row < rows;
+                    for (int k = 0; k < tn; ++k) {
+                        const int jj = t0 + k - lane;
+                        const bool active = jj >= 0 && jj < cols && row < rows;
                         if (k > 0) {
                             int eb = kRescale ? __shfl_up_sync(kFull, reo, 1) : 0;
 #pragma unroll
                             for (int n = 0; n <= N; ++n) rb[n] = __shfl_up_sync(kFull, rbo[n], 1);
                             if (active) {
                                 if (lane == 0) {
-                                    if (rs == 0) {
-#pragma unroll
-                                        for (int n = 0; n <= N; ++n) rb[n] = (n == 0) ? T(1) : T(0);
+                                    if (s == 0) {
+                                        set_unit<T, N>(rb);
                                         eb = 0;
                                     } else {
-                                        const T* src = fbuf + (static_cast<int64_t>(rs - 1) * B.cols_max + rj) * (N + 1);
+                                        const T* src = fbuf + (static_cast<int64_t>(s - 1) * B.cols_max + jj) * (N + 1);
 #pragma unroll
                                         for (int n = 0; n <= N; ++n) rb[n] = src[n];
-                                        if (kRescale) eb = fexp[static_cast<int64_t>(rs - 1) * B.cols_max + rj];
+                                        if (kRescale) eb = fexp[static_cast<int64_t>(s - 1) * B.cols_max + jj];
                                     }
                                 }
-                                if (rj == 0) {
-#pragma unroll
-                                    for (int n = 0; n <= N; ++n) ra[n] = (n == 0) ? T(1) : T(0);
+                                if (jj == 0) {
+                                    set_unit<T, N>(ra);
                                     rea = 0;
                                 }
-                                if (kRescale && rea != eb) {
-                                    if (rea > eb) {
-                                        const T f = pow2c<T>(eb - rea);
-#pragma unroll
-                                        for (int n = 0; n <= N; ++n) rb[n] *= f;
-                                    } else {
-                                        const T f = pow2c<T>(rea - eb);
-#pragma unroll
-                                        for (int n = 0; n <= N; ++n) ra[n] *= f;
-                                        rea = eb;
-                                    }
-                                }
+                                if (kRescale) align_inputs<T, N>(ra, rea, rb, eb);
                             }
                         }
                         T M = T(0);
                         if (active)
-                            M = row_dot<T>(xbase + static_cast<int64_t>(row >> lam) * dpad,
-                                           ybase + static_cast<int64_t>(rj >> lam) * dpad, L.nvec) * sub;
+                            M = row_dot<T>(xrow, ybase + static_cast<int64_t>(jj >> lam) * dpad, L.nvec) * sub;
                         T* sk_ = stk + k * (2 * N + 3) * 32;
 #pragma unroll
                         for (int n = 0; n <= N; ++n) {
@@ -349,47 +391,17 @@ __global__ void __launch_bounds__(kFwdWarps * 32, (bwd_min_blocks<T, N, K>()))
                         sk_[(2 * N + 2) * 32 + lane] = M;
                         stk_e[k * 32 + lane] = rea;
                         if (active) {
-                            T e[N + 1], ct[N + 1], cr[N + 1];
-                            build_exp_series<T, N>(M, L.tau, e);
-                            cell_series<T, N, N, false>(ra, rb, e, ct, cr);
-#pragma unroll
-                            for (int n = 0; n <= N; ++n) { ra[n] = ct[n]; rbo[n] = cr[n]; }
-                            if (kRescale) {
-                                const float mag = fmaxf(fabsf(static_cast<float>(ra[0])), fabsf(static_cast<float>(rbo[0])));
-                                if (mag > 0x1p64f) {
-#pragma unroll
-                                    for (int n = 0; n <= N; ++n) { ra[n] *= pow2t<T>(-64); rbo[n] *= pow2t<T>(-64); }
-                                    rea += 64;
-                                } else if (mag < 0x1p-64f) {
-                                    float full = 0.f;
-#pragma unroll
-                                    for (int n = 0; n <= N; ++n)
-                                        full = fmaxf(full, fmaxf(fabsf(static_cast<float>(ra[n])),
-                                                                 fabsf(static_cast<float>(rbo[n]))));
-                                    if (full < 0x1p-64f && full > 0.f) {
-#pragma unroll
-                                        for (int n = 0; n <= N; ++n) { ra[n] *= pow2t<T>(64); rbo[n] *= pow2t<T>(64); }
-                                        rea -= 64;
-                                    }
-                                }
-                            }
+                            fwd_cell<T, N>(ra, rb, M, L.tau, rbo, rea);
                             reo = rea;
                         }
-                        if (++rj == period) { rj = 0; ++rs; }
                     }
                 }
-            }
-            __syncwarp();
-            // walk the segment backward
+                __syncwarp();
+                // walk the segment backward
 #pragma unroll 1
-            for (int k = K - 1; k >= 0; --k) {
-                if (k < tn) {
-                    const int t = t0 + k;
-                    const int tt = t - lane;
-                    const int rs = tt >= 0 ? tt / period : 0;
-                    const int rj = tt >= 0 ? tt - rs * period : tt;
-                    const int row = (rs << 5) + lane;
-                    const bool active = rj >= 0 && rj < cols && row < rows;
+                for (int k = tn - 1; k >= 0; --k) {
+                    const int jj = t0 + k - lane;
+                    const bool active = jj >= 0 && jj < cols && row < rows;
                     T gb_in[N + 1];
 #pragma unroll
                     for (int n = 0; n <= N; ++n) gb_in[n] = __shfl_down_sync(kFull, gbo[n], 1);
@@ -402,10 +414,10 @@ __global__ void __launch_bounds__(kFwdWarps * 32, (bwd_min_blocks<T, N, K>()))
                             for (int n = 0; n <= N; ++n) gb_in[n] = T(0);
                             gbe_in = kZeroExp;
                         } else if (lane == 31) {           // from lane 0 of the strip above
-                            const T* src = rbuf + static_cast<int64_t>(rj) * (N + 1);
+                            const T* src = rbuf + static_cast<int64_t>(jj) * (N + 1);
 #pragma unroll
                             for (int n = 0; n <= N; ++n) gb_in[n] = src[n];
-                            gbe_in = kRescale ? rexp[rj] : 0;
+                            gbe_in = kRescale ? rexp[jj] : 0;
                         }
                         if (row == rows - 1 || lane == 31) {
 #pragma unroll
@@ -415,12 +427,12 @@ __global__ void __launch_bounds__(kFwdWarps * 32, (bwd_min_blocks<T, N, K>()))
                         int gae_in = gea;
 #pragma unroll
                         for (int n = 0; n <= N; ++n) ga_in[n] = gra[n];
-                        if (rj == cols - 1) {              // right edge of the grid: no cell to the right
+                        if (jj == cols - 1) {              // right edge of the grid
 #pragma unroll
                             for (int n = 0; n <= N; ++n) ga_in[n] = T(0);
                             gae_in = kZeroExp;
                         }
-                        if (row == rows - 1 && rj == cols - 1) {  // seed from the endpoint average
+                        if (row == rows - 1 && jj == cols - 1) {  // seed from the endpoint average
 #pragma unroll
                             for (int n = 0; n <= N; ++n) {
                                 ga_in[n] = static_cast<T>(0.5 * cx_rfact(n));
@@ -429,8 +441,9 @@ __global__ void __launch_bounds__(kFwdWarps * 32, (bwd_min_blocks<T, N, K>()))
                             gae_in = 0;
                             gbe_in = 0;
                         }
-                        int eg = kRescale ? max(gae_in, gbe_in) : 0;
+                        int eg = 0;
                         if (kRescale) {
+                            eg = max(gae_in, gbe_in);
                             if (gae_in != eg) {
                                 const T f = pow2c<T>(gae_in - eg);
 #pragma unroll
@@ -454,11 +467,11 @@ __global__ void __launch_bounds__(kFwdWarps * 32, (bwd_min_blocks<T, N, K>()))
                         build_exp_series<T, N>(M, L.tau, e);
                         T mbar;
                         cell_adjoint<T, N>(fa, fb, e, ga_in, gb_in, gra, gbo, mbar);
-                        // dk/dM relative to 2^ek, per coarse cell
+                        // dk/dM of the coarse cell, relative to 2^ek
                         const T mrel = mbar * pow2c<T>(eg + ef - ek - 2 * lam);
                         {
-                            const V* yv = reinterpret_cast<const V*>(ybase + static_cast<int64_t>(rj >> lam) * dpad);
-                            const V* xv = reinterpret_cast<const V*>(xbase + static_cast<int64_t>(row >> lam) * dpad);
+                            const V* yv = reinterpret_cast<const V*>(ybase + static_cast<int64_t>(jj >> lam) * dpad);
+                            const V* xv = reinterpret_cast<const V*>(xrow);
 #pragma unroll
                             for (int c4 = 0; c4 < DMAX / W; ++c4) {
                                 if (c4 * W < dpad) {
@@ -474,7 +487,6 @@ __global__ void __launch_bounds__(kFwdWarps * 32, (bwd_min_blocks<T, N, K>()))
                                 }
                             }
                         }
-                        // exponents of the outputs (shared by gra and gbo)
                         gea = eg;
                         if (kRescale) {
                             float mag = 0.f;
@@ -492,36 +504,29 @@ __global__ void __launch_bounds__(kFwdWarps * 32, (bwd_min_blocks<T, N, K>()))
                         }
                         gbe = gea;
                         if (lane == 0) {
-                            if (rs > 0) {  // hand the left-edge adjoint to lane 31 of the strip below
-                                T* dst = rbuf + static_cast<int64_t>(rj) * (N + 1);
+                            if (s > 0) {  // hand the left-edge adjoint to lane 31 of the strip below
+                                T* dst = rbuf + static_cast<int64_t>(jj) * (N + 1);
 #pragma unroll
                                 for (int n = 0; n <= N; ++n) dst[n] = gbo[n];
-                                if (kRescale) rexp[rj] = gbe;
+                                if (kRescale) rexp[jj] = gbe;
                             }
-                            T* yb = ybar + static_cast<int64_t>(rj >> lam) * dpad;
+                            // the column's partial dk/dy over this strip is complete
+                            double* gy = B.gincY + (P.ys + (jj >> lam)) * dpad;
 #pragma unroll
                             for (int c = 0; c < DMAX; ++c)
-                                if (c < dpad) yb[c] += ysum[c];
+                                if (c < dpad && ysum[c] != T(0))
+                                    atomicAdd(gy + c, static_cast<double>(ysum[c]) * gscale);
                         }
-                        if (rj == 0) {  // the row is finished: flush dk/dx of its increment
-                            const double scale = gbar * pow2d(ek);
+                        if (jj == 0) {  // the row is finished: flush dk/dx of its increment
                             double* gx = B.gincX + (P.xs + (row >> lam)) * dpad;
                             for (int c = 0; c < dpad; ++c) {
-                                if (xacc[c] != T(0)) atomicAdd(gx + c, static_cast<double>(xacc[c]) * scale);
+                                if (xacc[c] != T(0)) atomicAdd(gx + c, static_cast<double>(xacc[c]) * gscale);
                                 xacc[c] = T(0);
                             }
                         }
                     }
                     __syncwarp();
                 }
-            }
-        }
-        // flush dk/dy of every increment of y
-        {
-            const double scale = gbar * pow2d(ek);
-            for (int64_t i = lane; i < P.ly * dpad; i += 32) {
-                const T v = ybar[i];
-                if (v != T(0)) atomicAdd(B.gincY + P.ys * dpad + i, static_cast<double>(v) * scale);
             }
         }
         __syncwarp();

@@ -43,12 +43,12 @@ template <typename T> struct Tab;
 template <> struct Tab<float> {
     static __device__ __forceinline__ float inv(int m) { return static_cast<float>(cx_inv(m)); }
     static __device__ __forceinline__ float hank(int n, int k) { return static_cast<float>(cx_hank(n, k)); }
-    static __device__ __forceinline__ float proj(int N, int n, int jj) { return static_cast<float>(kProj[N][n][jj]); }
+    static __device__ __forceinline__ float proj(int N, int n, int jj) { return static_cast<float>(proj_coef(N, n, jj)); }
 };
 template <> struct Tab<double> {
     static __device__ __forceinline__ double inv(int m) { return cx_inv(m); }
     static __device__ __forceinline__ double hank(int n, int k) { return cx_hank(n, k); }
-    static __device__ __forceinline__ double proj(int N, int n, int jj) { return kProj[N][n][jj]; }
+    static __device__ __forceinline__ double proj(int N, int n, int jj) { return proj_coef(N, n, jj); }
 };
 
 // Exact power of two 2^e from its IEEE-754 bits (|e| within the normal range of T).

@@ -16,16 +16,11 @@ CSRC = os.path.join(ROOT, "paper_2502_08470_gb300", "csrc")
 
 def _table():
     txt = open(os.path.join(CSRC, "sk_projection_table.h")).read()
-    body = txt[txt.index("kProj["):]
-    T = {}
-    nums = re.compile(r"-?\d+(?:\.\d+)?(?:e[-+]?\d+)?")
-    # every "{...}," row of 12 numbers in order, grouped by N = 2..12 with N+1 rows each
-    rows = [list(map(float, nums.findall(r))) for r in re.findall(r"\{([^{}]+)\}", body)]
-    rows = [r for r in rows if len(r) == 12]
-    k = 0
-    for N in range(2, 13):
-        T[N] = np.array(rows[k:k + N + 1])
-        k += N + 1
+    T = {N: np.zeros((N + 1, 12)) for N in range(2, 13)}
+    for key, val in re.findall(r"case (\d+): return ([-+0-9.eE]+);", txt):
+        key = int(key)
+        N, n, jj = key // 1024, (key % 1024) // 32, key % 32
+        T[N][n, jj] = float(val)
     return T
 
 
