@@ -189,6 +189,25 @@ int sigkernel_mmd2(const sk_paths* A, const sk_paths* B, int32_t d, int32_t dtyp
                    void* workspace, size_t workspace_bytes, void* stream);
 
 /*
+ * sigkernel_pairs_noalloc -- sigkernel_pairs for callers that cannot allocate device memory
+ * (an allocator that forbids new device allocations, a host application that owns all device
+ * memory, a loop that must not risk an allocation).  The paper has no counterpart.  Same
+ * arguments and result as sigkernel_pairs, without a workspace: the scratch is a fixed 64 MiB
+ * array in device global memory that every GPU loading the library holds until the process exits
+ * (sigkernel_noalloc_capacity() gives its size).  A call needing more scratch than that returns
+ * SK_ERR_WORKSPACE with both sizes in sigkernel_noalloc_last_error().  All calls on a device share
+ * the array and leave their contents in it; each call clears the parts that must start at zero,
+ * and calls that overlap on the GPU race.  The first call on a device looks up the array's
+ * address with that device current: make it before any stream capture on that device.  The call
+ * runs no cudaMalloc, cudaMallocAsync, cudaFree or other allocating routine.
+ */
+int sigkernel_pairs_noalloc(const sk_paths* X, const sk_paths* Y, int32_t d, int32_t dtype,
+                            const int64_t* pair_a, const int64_t* pair_b, int64_t npairs,
+                            const sk_options* opt, double* out, void* stream);
+size_t sigkernel_noalloc_capacity(void);
+const char* sigkernel_noalloc_last_error(void);
+
+/*
  * sigkernel_device_status -- synchronises `stream`, reads and clears the device error word of
  * the current device, and returns SK_OK or the first recorded SK_ERR_* code.
  */
