@@ -116,7 +116,7 @@ typedef struct {
 } sk_paths;
 
 /* Which call a workspace is sized for. */
-enum { SK_OP_PAIRS = 0, SK_OP_GRAM = 1, SK_OP_BACKWARD = 2, SK_OP_MMD2 = 3 };
+enum { SK_OP_PAIRS = 0, SK_OP_GRAM = 1, SK_OP_BACKWARD = 2, SK_OP_MMD2 = 3, SK_OP_BACKWARD_TAPE = 4 };
 
 /*
  * sigkernel_workspace_size -- writes to *bytes the device workspace the call `op` needs for
@@ -174,6 +174,32 @@ int sigkernel_backward(const sk_paths* X, const sk_paths* Y, int32_t d, int32_t 
                        const int64_t* pair_a, const int64_t* pair_b, int64_t npairs,
                        const sk_options* opt, const double* grad_out, double* grad_X,
                        double* grad_Y, void* workspace, size_t workspace_bytes, void* stream);
+
+/*
+ * Forward tape (approximation scheme only).  sigkernel_forward_tape computes the same results as
+ * sigkernel_pairs / sigkernel_gram (Gram mode when pair_a is NULL; `out` is then [X->count][Y->count]
+ * and SK_FLAG_SYMMETRIC applies) and also records, in the caller's `tape`, every cell's inputs
+ * (the two incoming edge coefficient vectors and their exponent) and the exponent of each k_hat.
+ * sigkernel_backward_tape then runs the adjoint from the tape without recomputing the forward
+ * sweep.  Both calls must use the same X, Y, pair list, options and path contents.
+ *   tape        device buffer, 256-byte aligned, caller-owned, >= sigkernel_tape_size() bytes;
+ *               the size grows as npairs x (max_len << lambda)^2 x ~64 B (FP32) or ~128 B (FP64):
+ *               about 70 GB for 16,384 pairs of 257-point paths in FP32.
+ *   sigkernel_tape_size: `npairs` = -1 for a Gram; writes the bytes and returns SK_OK or SK_ERR_*.
+ * The backward's workspace is sized with SK_OP_BACKWARD_TAPE.  Other arguments and the gradient
+ * semantics are those of sigkernel_backward.
+ */
+int sigkernel_tape_size(const sk_paths* X, const sk_paths* Y, int32_t d, int64_t npairs,
+                        const sk_options* opt, size_t* bytes);
+int sigkernel_forward_tape(const sk_paths* X, const sk_paths* Y, int32_t d, int32_t dtype,
+                           const int64_t* pair_a, const int64_t* pair_b, int64_t npairs,
+                           const sk_options* opt, double* out, void* tape, size_t tape_bytes,
+                           void* workspace, size_t workspace_bytes, void* stream);
+int sigkernel_backward_tape(const sk_paths* X, const sk_paths* Y, int32_t d, int32_t dtype,
+                            const int64_t* pair_a, const int64_t* pair_b, int64_t npairs,
+                            const sk_options* opt, const void* tape, size_t tape_bytes,
+                            const double* grad_out, double* grad_X, double* grad_Y,
+                            void* workspace, size_t workspace_bytes, void* stream);
 
 /*
  * sigkernel_mmd2 -- squared maximum mean discrepancy between the path sets A and B with the

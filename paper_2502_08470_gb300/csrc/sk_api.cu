@@ -248,12 +248,37 @@ int launch_increments(const sk_paths* S, int32_t d, int32_t dtype, int inc_mode,
     return SK_OK;
 }
 
+// Tape of the forward pass (approximation scheme): [npairs] int exponents of k_hat, then one
+// fixed-stride block per work item of nsteps_max x 32 lanes x tape_row<T>(N) elements.
+struct TapePlan {
+    size_t ek_bytes, stride, total;
+};
+
+int plan_tape(const sk_paths* X, const sk_paths* Y, const sk_options* o, int T, int64_t npairs, TapePlan& t) {
+    if (o->scheme != SK_POLY_APPROX) return fail(SK_ERR_UNSUPPORTED, "a forward tape is recorded for the approximation scheme");
+    const int lam = o->dyadic;
+    const int64_t rows = std::max<int64_t>(X->max_len << lam, 1), cols = std::max<int64_t>(Y->max_len << lam, 1);
+    const int64_t nsteps = ((rows + 31) / 32 - 1) * std::max<int64_t>(cols, 32) + 31 + cols;
+    const int row = T ? tape_row<float>(o->degree) : tape_row<double>(o->degree);
+    const int esize = T ? 4 : 8;
+    t.ek_bytes = align256(static_cast<size_t>(npairs) * sizeof(int));
+    t.stride = align256(static_cast<size_t>(nsteps) * 32 * row * esize);
+    t.total = t.ek_bytes + static_cast<size_t>(npairs) * t.stride;
+    return SK_OK;
+}
+
 int run_forward(const sk_paths* X, const sk_paths* Y, int32_t d, int32_t dtype, const sk_options* o, int mode,
                 const int64_t* pa, const int64_t* pb, int64_t npairs, double* out, int64_t ldo, void* ws,
-                size_t ws_bytes, void* stream) {
+                size_t ws_bytes, void* stream, void* tape = nullptr, size_t tape_bytes = 0) {
     Plan p;
     int rc = plan_forward(X, Y, d, dtype, o, mode, npairs, p);
     if (rc != SK_OK) return rc;
+    TapePlan tp{0, 0, 0};
+    if (tape) {
+        if ((rc = plan_tape(X, Y, o, p.T, npairs, tp)) != SK_OK) return rc;
+        if (tape_bytes < tp.total) return fail(SK_ERR_WORKSPACE, "tape %zu bytes < %zu required", tape_bytes, tp.total);
+        if (reinterpret_cast<uintptr_t>(tape) % 256) return fail(SK_ERR_INVALID_ARG, "tape must be 256-byte aligned");
+    }
     if (npairs == 0) return SK_OK;
     if (!out) return fail(SK_ERR_INVALID_ARG, "output pointer is NULL");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -293,6 +318,9 @@ int run_forward(const sk_paths* X, const sk_paths* Y, int32_t d, int32_t dtype, 
     L.scratch_stride = p.slot_bytes;
     L.tau = 1.0f;
     L.order = nullptr;
+    L.tape = tape ? static_cast<char*>(tape) + tp.ek_bytes : nullptr;
+    L.tape_stride = static_cast<int64_t>(tp.stride);
+    L.tape_ek = tape ? static_cast<int*>(tape) : nullptr;
     SK_CUDA(cudaMemsetAsync(base + p.off_queue, 0, 256 + align256(2 * 65 * sizeof(unsigned int)), st));
     if (!(o->flags & SK_FLAG_NO_SORT) && npairs > 1) {
         unsigned int* hist = reinterpret_cast<unsigned int*>(base + p.off_hist);
@@ -528,6 +556,148 @@ int run_backward(const sk_paths* X, const sk_paths* Y, int32_t d, int32_t dtype,
     return SK_OK;
 }
 
+
+// ------------------------------------------------------------------------------------------
+// Backward from a forward tape.
+// ------------------------------------------------------------------------------------------
+struct TapeBwdPlan {
+    Plan f;
+    TapePlan t;
+    const void* kern;
+    int smem_bytes;
+    int64_t cols_max, off_rbuf, off_rexp, slot_bytes;
+    size_t off_gincx, off_gincy, off_scratch, total;
+};
+
+int plan_backward_tape(const sk_paths* X, const sk_paths* Y, int32_t d, int32_t dtype, const sk_options* o, int mode,
+                       int64_t npairs, TapeBwdPlan& b) {
+    int rc = plan_forward(X, Y, d, dtype, o, mode, npairs, b.f);
+    if (rc != SK_OK) return rc;
+    const Plan& p = b.f;
+    if ((rc = plan_tape(X, Y, o, p.T, npairs, b.t)) != SK_OK) return rc;
+    const int dmax = p.dpad <= 8 ? 8 : (p.dpad <= 32 ? 32 : 0);
+    if (!dmax) return fail(SK_ERR_UNSUPPORTED, "the adjoint supports d <= 32");
+    b.kern = p.T ? bwd_tape_ptr_f32(o->degree, dmax) : bwd_tape_ptr_f64(o->degree, dmax);
+    if (!b.kern) return fail(SK_ERR_UNSUPPORTED, "no adjoint kernel for order %d", o->degree);
+    b.smem_bytes = kFwdWarps * (p.T ? bwd_xacc_bytes<float>(p.dpad) : bwd_xacc_bytes<double>(p.dpad));
+    const int esize = p.T ? 4 : 8, N = o->degree;
+    b.cols_max = std::max<int64_t>(Y->max_len << o->dyadic, 1);
+    b.off_rbuf = 0;
+    int64_t off = static_cast<int64_t>(align256(b.cols_max * (N + 1) * esize));
+    b.off_rexp = off;
+    off += static_cast<int64_t>(align256(b.cols_max * 4));
+    b.slot_bytes = off;
+    int dev = 0, sms = 0, per_sm = 0;
+    SK_CUDA(cudaGetDevice(&dev));
+    SK_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    SK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, b.kern, p.threads, b.smem_bytes));
+    if (per_sm < 1) return fail(SK_ERR_UNSUPPORTED, "adjoint kernel does not fit an SM");
+    const int64_t want = (npairs + kFwdWarps - 1) / kFwdWarps;
+    b.f.blocks = static_cast<int>(std::max<int64_t>(1, std::min(want, static_cast<int64_t>(sms) * per_sm)));
+    size_t o2 = p.off_scratch;
+    b.off_gincx = o2;
+    o2 += align256(static_cast<size_t>(X->rows_total) * p.dpad * sizeof(double));
+    b.off_gincy = p.same_xy ? b.off_gincx : o2;
+    if (!p.same_xy) o2 += align256(static_cast<size_t>(Y->rows_total) * p.dpad * sizeof(double));
+    b.off_scratch = o2;
+    o2 += static_cast<size_t>(b.f.blocks) * kFwdWarps * static_cast<size_t>(b.slot_bytes);
+    b.total = o2 + 256;
+    return SK_OK;
+}
+
+int run_backward_tape(const sk_paths* X, const sk_paths* Y, int32_t d, int32_t dtype, const sk_options* o,
+                      const int64_t* pa, const int64_t* pb, int64_t npairs, const void* tape, size_t tape_bytes,
+                      const double* gout, double* gX, double* gY, void* ws, size_t ws_bytes, void* stream) {
+    const bool gram = (pa == nullptr);
+    const bool sym = gram && (o->flags & SK_FLAG_SYMMETRIC);
+    const int mode = gram ? (sym ? kGramUpper : kGramFull) : kPairsList;
+    if (gram) npairs = gram_items(X, Y, sym);
+    TapeBwdPlan b;
+    int rc = plan_backward_tape(X, Y, d, dtype, o, mode, npairs, b);
+    if (rc != SK_OK) return rc;
+    if (b.f.same_xy && gY && gY != gX)
+        return fail(SK_ERR_INVALID_ARG, "X and Y are the same paths: pass grad_Y = NULL or grad_Y = grad_X");
+    if (!tape || tape_bytes < b.t.total) return fail(SK_ERR_WORKSPACE, "tape missing or smaller than %zu bytes", b.t.total);
+    if (npairs == 0) return SK_OK;
+    if (!gout) return fail(SK_ERR_INVALID_ARG, "grad_out is NULL");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    bool own = false;
+    if (!ws) {
+        SK_CUDA(cudaMallocAsync(&ws, b.total, st));
+        own = true;
+    } else if (ws_bytes < b.total) {
+        return fail(SK_ERR_WORKSPACE, "workspace %zu bytes < %zu required", ws_bytes, b.total);
+    }
+    char* base = reinterpret_cast<char*>((reinterpret_cast<uintptr_t>(ws) + 255) / 256 * 256);
+    const Plan& p = b.f;
+    const int inc_mode = (o->flags & SK_FLAG_INCREMENTS) ? 1 : 0;
+    double* gincX = reinterpret_cast<double*>(base + b.off_gincx);
+    double* gincY = reinterpret_cast<double*>(base + b.off_gincy);
+    SK_CUDA(cudaMemsetAsync(gincX, 0, static_cast<size_t>(X->rows_total) * p.dpad * sizeof(double), st));
+    if (!p.same_xy) SK_CUDA(cudaMemsetAsync(gincY, 0, static_cast<size_t>(Y->rows_total) * p.dpad * sizeof(double), st));
+    rc = p.T ? launch_increments<float>(X, d, dtype, inc_mode, p.dpad, base + p.off_incx, st)
+             : launch_increments<double>(X, d, dtype, inc_mode, p.dpad, base + p.off_incx, st);
+    if (rc == SK_OK && !p.same_xy)
+        rc = p.T ? launch_increments<float>(Y, d, dtype, inc_mode, p.dpad, base + p.off_incy, st)
+                 : launch_increments<double>(Y, d, dtype, inc_mode, p.dpad, base + p.off_incy, st);
+    if (rc != SK_OK) return rc;
+    BwdParams B;
+    memset(&B, 0, sizeof(B));
+    Launch& L = B.L;
+    L.X = PathSet{base + p.off_incx, X->offsets, X->count, X->max_len, X->rows_total};
+    L.Y = PathSet{base + p.off_incy, Y->offsets, Y->count, Y->max_len, Y->rows_total};
+    L.nvec = p.nvec;
+    L.dpad = p.dpad;
+    L.inc_mode = inc_mode;
+    L.lam = o->dyadic;
+    L.mode = mode;
+    L.npairs = npairs;
+    L.pair_a = pa;
+    L.pair_b = pb;
+    L.queue = reinterpret_cast<unsigned int*>(base + p.off_queue);
+    L.ldo = Y->count;
+    L.scratch = base + b.off_scratch;
+    L.scratch_stride = b.slot_bytes;
+    L.tau = 1.0f;
+    L.tape = const_cast<char*>(static_cast<const char*>(tape)) + b.t.ek_bytes;
+    L.tape_stride = static_cast<int64_t>(b.t.stride);
+    L.tape_ek = const_cast<int*>(static_cast<const int*>(tape));
+    B.gout = gout;
+    B.gincX = gincX;
+    B.gincY = gincY;
+    B.cols_max = b.cols_max;
+    B.off_rbuf = b.off_rbuf;
+    B.off_rexp = b.off_rexp;
+    SK_CUDA(cudaMemsetAsync(base + p.off_queue, 0, 256, st));
+    if (!(o->flags & SK_FLAG_NO_SORT) && npairs > 1) {
+        unsigned int* hist = reinterpret_cast<unsigned int*>(base + p.off_hist);
+        int32_t* order = reinterpret_cast<int32_t*>(base + p.off_order);
+        SK_CUDA(cudaMemsetAsync(hist, 0, align256(2 * 65 * sizeof(unsigned int)), st));
+        int sb = static_cast<int>(std::min<int64_t>((npairs + 255) / 256, 4096));
+        sched_hist_kernel<<<sb, 256, 0, st>>>(L, hist);
+        sched_scan_kernel<<<1, 32, 0, st>>>(hist, hist + 65);
+        sched_scatter_kernel<<<sb, 256, 0, st>>>(L, hist + 65, order);
+        SK_CUDA(cudaGetLastError());
+        L.order = order;
+    }
+    void* args[] = {&B};
+    const bool timed = (o->flags & SK_FLAG_TIME_KERNEL) != 0;
+    if (timed) {
+        if (!t_ev0) SK_CUDA(cudaEventCreate(&t_ev0));
+        if (!t_ev1) SK_CUDA(cudaEventCreate(&t_ev1));
+        SK_CUDA(cudaEventRecord(t_ev0, st));
+    }
+    SK_CUDA(cudaLaunchKernel(b.kern, dim3(p.blocks), dim3(p.threads), args, b.smem_bytes, st));
+    if (timed) {
+        SK_CUDA(cudaEventRecord(t_ev1, st));
+        t_timed = true;
+    }
+    if ((rc = convert_grad(X, d, p.dpad, inc_mode, gincX, gX, st)) != SK_OK) return rc;
+    if (!p.same_xy && (rc = convert_grad(Y, d, p.dpad, inc_mode, gincY, gY, st)) != SK_OK) return rc;
+    if (own) SK_CUDA(cudaFreeAsync(ws, st));
+    return SK_OK;
+}
+
 // ------------------------------------------------------------------------------------------
 // MMD^2 from the three Gram blocks; weights of its backward.
 // ------------------------------------------------------------------------------------------
@@ -693,6 +863,15 @@ int sigkernel_workspace_size(int32_t op, const sk_paths* X, const sk_paths* Y, i
             if (rc == SK_OK) *bytes = b.total;
             return rc;
         }
+        case SK_OP_BACKWARD_TAPE: {
+            const bool gram = npairs < 0;
+            const bool sym = gram && (opt->flags & SK_FLAG_SYMMETRIC);
+            TapeBwdPlan b;
+            rc = plan_backward_tape(X, Y, d, dtype, opt, gram ? (sym ? kGramUpper : kGramFull) : kPairsList,
+                                    gram ? gram_items(X, Y, sym) : npairs, b);
+            if (rc == SK_OK) *bytes = b.total;
+            return rc;
+        }
         case SK_OP_MMD2: {
             // sized by a dry run of the same planning as sigkernel_mmd2 (X = A, Y = B)
             Plan pa, pb, pc;
@@ -752,6 +931,51 @@ int sigkernel_backward(const sk_paths* X, const sk_paths* Y, int32_t d, int32_t 
     if (pair_a && (!pair_b || npairs < 0)) return fail(SK_ERR_INVALID_ARG, "bad pair list");
     return run_backward(X, Y, d, dtype, opt, pair_a, pair_b, npairs, grad_out, grad_X, grad_Y, workspace,
                         workspace_bytes, stream);
+}
+
+int sigkernel_tape_size(const sk_paths* X, const sk_paths* Y, int32_t d, int64_t npairs, const sk_options* opt,
+                        size_t* bytes) {
+    t_last_error.clear();
+    if (!bytes) return fail(SK_ERR_INVALID_ARG, "bytes is NULL");
+    *bytes = 0;
+    if (!opt || !X || !Y) return fail(SK_ERR_INVALID_ARG, "NULL argument");
+    const bool gram = npairs < 0;
+    const bool sym = gram && (opt->flags & SK_FLAG_SYMMETRIC);
+    Plan p;
+    int rc = plan_forward(X, Y, d, SK_F64, opt, gram ? (sym ? kGramUpper : kGramFull) : kPairsList,
+                          gram ? gram_items(X, Y, sym) : npairs, p);
+    if (rc != SK_OK) return rc;
+    TapePlan t;
+    if ((rc = plan_tape(X, Y, opt, p.T, p.npairs, t)) != SK_OK) return rc;
+    *bytes = t.total;
+    return SK_OK;
+}
+
+int sigkernel_forward_tape(const sk_paths* X, const sk_paths* Y, int32_t d, int32_t dtype, const int64_t* pair_a,
+                           const int64_t* pair_b, int64_t npairs, const sk_options* opt, double* out, void* tape,
+                           size_t tape_bytes, void* workspace, size_t workspace_bytes, void* stream) {
+    t_last_error.clear();
+    if (!opt || !X || !Y) return fail(SK_ERR_INVALID_ARG, "NULL argument");
+    if (!tape) return fail(SK_ERR_INVALID_ARG, "tape is NULL");
+    if (pair_a == nullptr) {
+        const bool sym = (opt->flags & SK_FLAG_SYMMETRIC) != 0;
+        return run_forward(X, Y, d, dtype, opt, sym ? kGramUpper : kGramFull, nullptr, nullptr, gram_items(X, Y, sym),
+                           out, Y->count, workspace, workspace_bytes, stream, tape, tape_bytes);
+    }
+    if (!pair_b || npairs < 0) return fail(SK_ERR_INVALID_ARG, "bad pair list");
+    return run_forward(X, Y, d, dtype, opt, kPairsList, pair_a, pair_b, npairs, out, 0, workspace, workspace_bytes,
+                       stream, tape, tape_bytes);
+}
+
+int sigkernel_backward_tape(const sk_paths* X, const sk_paths* Y, int32_t d, int32_t dtype, const int64_t* pair_a,
+                            const int64_t* pair_b, int64_t npairs, const sk_options* opt, const void* tape,
+                            size_t tape_bytes, const double* grad_out, double* grad_X, double* grad_Y, void* workspace,
+                            size_t workspace_bytes, void* stream) {
+    t_last_error.clear();
+    if (!opt || !X || !Y) return fail(SK_ERR_INVALID_ARG, "NULL argument");
+    if (pair_a && (!pair_b || npairs < 0)) return fail(SK_ERR_INVALID_ARG, "bad pair list");
+    return run_backward_tape(X, Y, d, dtype, opt, pair_a, pair_b, npairs, tape, tape_bytes, grad_out, grad_X, grad_Y,
+                             workspace, workspace_bytes, stream);
 }
 
 int sigkernel_mmd2(const sk_paths* A, const sk_paths* B, int32_t d, int32_t dtype, const sk_options* opt, double* out,

@@ -152,14 +152,14 @@ __device__ __forceinline__ void cell_adjoint(const T (&a)[N + 1], const T (&b)[N
 }
 
 // Shared memory of one warp: the K-step stack (a[N+1], b[N+1], M per lane, plus exponents),
-// then each lane's dk/dx accumulator of its row ([32][dpad + 4]; the pad spreads the lanes'
-// accesses over all banks).
+// then each lane's dk/dx accumulator of its row ([32][dpad + 1]; the odd stride puts the lanes'
+// scalar accesses in distinct banks).
 template <typename T, int N, int K>
 __host__ __device__ constexpr int bwd_stack_bytes() {
     return K * (2 * N + 3) * 32 * static_cast<int>(sizeof(T)) + K * 32 * 4;
 }
 template <typename T>
-__host__ __device__ constexpr int bwd_xacc_bytes(int dpad) { return 32 * (dpad + 4) * static_cast<int>(sizeof(T)); }
+__host__ __device__ constexpr int bwd_xacc_bytes(int dpad) { return 32 * (dpad + 1) * static_cast<int>(sizeof(T)); }
 
 template <typename T, int N, int K>
 constexpr int bwd_min_blocks() {
@@ -189,7 +189,7 @@ __global__ void __launch_bounds__(kFwdWarps * 32, (bwd_min_blocks<T, N, K>()))
     unsigned char* wsm = smem_raw + wib * (bwd_stack_bytes<T, N, K>() + bwd_xacc_bytes<T>(dpad));
     T* stk = reinterpret_cast<T*>(wsm);
     int* stk_e = reinterpret_cast<int*>(stk + K * (2 * N + 3) * 32);
-    T* xacc = reinterpret_cast<T*>(wsm + bwd_stack_bytes<T, N, K>()) + lane * (dpad + 4);
+    T* xacc = reinterpret_cast<T*>(wsm + bwd_stack_bytes<T, N, K>()) + lane * (dpad + 1);
     const T* __restrict__ incX = static_cast<const T*>(L.X.inc);
     const T* __restrict__ incY = static_cast<const T*>(L.Y.inc);
 
@@ -527,6 +527,231 @@ __global__ void __launch_bounds__(kFwdWarps * 32, (bwd_min_blocks<T, N, K>()))
                     }
                     __syncwarp();
                 }
+            }
+        }
+        __syncwarp();
+    }
+}
+
+
+// ---------------------------------------------------------------------------------------------
+// Adjoint from a forward tape.  The forward kernel recorded, for every warp step and lane, the
+// cell's inputs (a, b, exponent) and the exponent of k_hat; this kernel walks the same steps
+// backward (the reverse of the forward schedule, strips overlapping exactly as there) and needs
+// no forward recomputation.  Tape rows are prefetched one step ahead.
+// ---------------------------------------------------------------------------------------------
+template <typename T, int N, int DMAX>
+__host__ __device__ constexpr int bwd_tape_min_blocks() {
+    return sizeof(T) == 8 ? 1 : 3;
+}
+
+template <typename T, int N, int DMAX>
+__global__ void __launch_bounds__(kFwdWarps * 32, (bwd_tape_min_blocks<T, N, DMAX>()))
+    bwd_tape_kernel(BwdParams B) {
+    constexpr bool kRescale = std::is_same<T, float>::value;
+    using V = typename Vec<T>::type;
+    constexpr int W = Vec<T>::W;
+    constexpr int TR = tape_row<T>(N);
+    const Launch& L = B.L;
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    const int64_t slot = static_cast<int64_t>(blockIdx.x) * (blockDim.x >> 5) + wib;
+    char* base = static_cast<char*>(L.scratch) + slot * L.scratch_stride;
+    T* rbuf = reinterpret_cast<T*>(base + B.off_rbuf);          // [col][N+1]
+    int* rexp = reinterpret_cast<int*>(base + B.off_rexp);      // [col]
+    const int dpad = L.dpad;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* xacc = reinterpret_cast<T*>(smem_raw + wib * bwd_xacc_bytes<T>(dpad)) + lane * (dpad + 1);
+    const T* __restrict__ incX = static_cast<const T*>(L.X.inc);
+    const T* __restrict__ incY = static_cast<const T*>(L.Y.inc);
+
+    for (;;) {
+        const int64_t item = next_item(L);
+        if (item < 0) break;
+        const PairDesc P = decode_pair(L, item);
+        if (P.lx < 0 || P.ly < 0) {
+            if (lane == 0) record_error(SK_ERR_BAD_LENGTH);
+            continue;
+        }
+        if (P.lx == 0 || P.ly == 0) continue;
+        double gbar;
+        if (L.mode == kPairsList) gbar = B.gout[item];
+        else if (L.mode == kGramFull) gbar = B.gout[P.a * L.ldo + P.b];
+        else gbar = B.gout[P.a * L.ldo + P.b] + (P.a != P.b ? B.gout[P.b * L.ldo + P.a] : 0.0);
+        if (gbar == 0.0) continue;
+
+        const int lam = L.lam;
+        const int rows = static_cast<int>(P.lx << lam);
+        const int cols = static_cast<int>(P.ly << lam);
+        const int period = cols > 32 ? cols : 32;
+        const int nstrips = (rows + 31) >> 5;
+        const int last_lane = (rows - 1) - ((nstrips - 1) << 5);
+        const int nsteps = (nstrips - 1) * period + last_lane + cols;
+        const T* xbase = incX + P.xs * dpad;
+        const T* ybase = incY + P.ys * dpad;
+        const int ek = L.tape_ek[item];
+        const double gscale = gbar * pow2d(ek);
+        const V* tape = reinterpret_cast<const V*>(static_cast<const char*>(L.tape) + item * L.tape_stride);
+
+        T gra[N + 1], gbo[N + 1];
+        int gea = kZeroExp, gbe = kZeroExp;
+        T ysum[DMAX];
+#pragma unroll
+        for (int n = 0; n <= N; ++n) { gra[n] = T(0); gbo[n] = T(0); }
+#pragma unroll
+        for (int c = 0; c < DMAX; ++c) ysum[c] = T(0);
+        for (int c = 0; c < dpad; ++c) xacc[c] = T(0);
+
+        // position of this lane at the last step, then walked backward one step at a time
+        int tt = nsteps - 1 - lane;
+        int s = tt >= 0 ? tt / period : -1;
+        int jj = tt >= 0 ? tt - s * period : -1;
+        V cur[TR / W], nxt[TR / W];
+        {
+            const V* src = tape + (static_cast<int64_t>(nsteps - 1) * 32 + lane) * (TR / W);
+#pragma unroll
+            for (int v = 0; v < TR / W; ++v) cur[v] = src[v];
+        }
+        for (int step = nsteps - 1; step >= 0; --step) {
+            if (step > 0) {  // prefetch the previous step's row (lanes whose cell is real read real data)
+                const V* src = tape + (static_cast<int64_t>(step - 1) * 32 + lane) * (TR / W);
+#pragma unroll
+                for (int v = 0; v < TR / W; ++v) nxt[v] = src[v];
+            }
+            T gb_in[N + 1];
+#pragma unroll
+            for (int n = 0; n <= N; ++n) gb_in[n] = __shfl_down_sync(kFull, gbo[n], 1);
+            int gbe_in = __shfl_down_sync(kFull, gbe, 1);
+#pragma unroll
+            for (int c = 0; c < DMAX; ++c) ysum[c] = __shfl_down_sync(kFull, ysum[c], 1);
+            const int row = (s << 5) + lane;
+            const bool active = s >= 0 && jj < cols && row < rows;
+            if (active) {
+                if (row == rows - 1) {             // no row above: the top edge is final
+#pragma unroll
+                    for (int n = 0; n <= N; ++n) gb_in[n] = T(0);
+                    gbe_in = kZeroExp;
+                } else if (lane == 31) {           // from lane 0 of the strip above
+                    const T* src = rbuf + static_cast<int64_t>(jj) * (N + 1);
+#pragma unroll
+                    for (int n = 0; n <= N; ++n) gb_in[n] = src[n];
+                    gbe_in = kRescale ? rexp[jj] : 0;
+                }
+                if (row == rows - 1 || lane == 31) {
+#pragma unroll
+                    for (int c = 0; c < DMAX; ++c) ysum[c] = T(0);
+                }
+                T ga_in[N + 1];
+                int gae_in = gea;
+#pragma unroll
+                for (int n = 0; n <= N; ++n) ga_in[n] = gra[n];
+                if (jj == cols - 1) {              // right edge of the grid
+#pragma unroll
+                    for (int n = 0; n <= N; ++n) ga_in[n] = T(0);
+                    gae_in = kZeroExp;
+                }
+                if (row == rows - 1 && jj == cols - 1) {  // seed from the endpoint average
+#pragma unroll
+                    for (int n = 0; n <= N; ++n) {
+                        ga_in[n] = static_cast<T>(0.5 * cx_rfact(n));
+                        gb_in[n] = ga_in[n];
+                    }
+                    gae_in = 0;
+                    gbe_in = 0;
+                }
+                int eg = 0;
+                if (kRescale) {
+                    eg = max(gae_in, gbe_in);
+                    if (gae_in != eg) {
+                        const T f = pow2c<T>(gae_in - eg);
+#pragma unroll
+                        for (int n = 0; n <= N; ++n) ga_in[n] *= f;
+                    }
+                    if (gbe_in != eg) {
+                        const T f = pow2c<T>(gbe_in - eg);
+#pragma unroll
+                        for (int n = 0; n <= N; ++n) gb_in[n] *= f;
+                    }
+                }
+                T fa[N + 1], fb[N + 1], e[N + 1];
+                int ef;
+                {
+                    const T* tp = reinterpret_cast<const T*>(cur);
+#pragma unroll
+                    for (int n = 0; n <= N; ++n) {
+                        fa[n] = tp[n];
+                        fb[n] = tp[N + 1 + n];
+                    }
+                    if constexpr (std::is_same<T, float>::value) ef = __float_as_int(tp[2 * N + 2]);
+                    else ef = static_cast<int>(__double_as_longlong(tp[2 * N + 2]));
+                }
+                const T* xrow = xbase + static_cast<int64_t>(row >> lam) * dpad;
+                const T* yrow = ybase + static_cast<int64_t>(jj >> lam) * dpad;
+                const T M = row_dot<T>(xrow, yrow, L.nvec) * pow2t<T>(-2 * lam);
+                build_exp_series<T, N>(M, L.tau, e);
+                T mbar;
+                cell_adjoint<T, N>(fa, fb, e, ga_in, gb_in, gra, gbo, mbar);
+                const T mrel = mbar * pow2c<T>(eg + ef - ek - 2 * lam);
+                {
+                    const V* yv = reinterpret_cast<const V*>(yrow);
+                    const V* xv = reinterpret_cast<const V*>(xrow);
+#pragma unroll
+                    for (int c4 = 0; c4 < DMAX / W; ++c4) {
+                        if (c4 * W < dpad) {
+                            const V yy = __ldg(yv + c4);
+                            const V xx = __ldg(xv + c4);
+                            const T* yp = reinterpret_cast<const T*>(&yy);
+                            const T* xp = reinterpret_cast<const T*>(&xx);
+#pragma unroll
+                            for (int w = 0; w < W; ++w) {
+                                xacc[c4 * W + w] = fma(mrel, yp[w], xacc[c4 * W + w]);
+                                ysum[c4 * W + w] = fma(mrel, xp[w], ysum[c4 * W + w]);
+                            }
+                        }
+                    }
+                }
+                gea = eg;
+                if (kRescale) {
+                    float mag = 0.f;
+#pragma unroll
+                    for (int n = 0; n <= N; ++n)
+                        mag = fmaxf(mag, fmaxf(fabsf(static_cast<float>(gra[n])), fabsf(static_cast<float>(gbo[n]))));
+                    if (mag == 0.f) {
+                        gea = kZeroExp;
+                    } else if (mag > 0x1p64f || mag < 0x1p-64f) {
+                        const int sh = mag > 0x1p64f ? -64 : 64;
+#pragma unroll
+                        for (int n = 0; n <= N; ++n) { gra[n] *= pow2t<T>(sh); gbo[n] *= pow2t<T>(sh); }
+                        gea -= sh;
+                    }
+                }
+                gbe = gea;
+                if (lane == 0) {
+                    if (s > 0) {  // hand the left-edge adjoint to lane 31 of the strip below
+                        T* dst = rbuf + static_cast<int64_t>(jj) * (N + 1);
+#pragma unroll
+                        for (int n = 0; n <= N; ++n) dst[n] = gbo[n];
+                        if (kRescale) rexp[jj] = gbe;
+                    }
+                    double* gy = B.gincY + (P.ys + (jj >> lam)) * dpad;
+#pragma unroll
+                    for (int c = 0; c < DMAX; ++c)
+                        if (c < dpad && ysum[c] != T(0)) atomicAdd(gy + c, static_cast<double>(ysum[c]) * gscale);
+                }
+                if (jj == 0) {  // the row is finished: flush dk/dx of its increment
+                    double* gx = B.gincX + (P.xs + (row >> lam)) * dpad;
+                    for (int c = 0; c < dpad; ++c) {
+                        if (xacc[c] != T(0)) atomicAdd(gx + c, static_cast<double>(xacc[c]) * gscale);
+                        xacc[c] = T(0);
+                    }
+                }
+            }
+            __syncwarp();
+#pragma unroll
+            for (int v = 0; v < TR / W; ++v) cur[v] = nxt[v];
+            if (s >= 0 && --jj < 0) {
+                jj = period - 1;
+                --s;
             }
         }
         __syncwarp();

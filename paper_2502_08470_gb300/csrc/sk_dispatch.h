@@ -23,3 +23,9 @@ const void* bwd_approx_ptr_f64(int N, int dmax, int* stack_bytes);
 int bwd_segment_f32();  // antidiagonal checkpoint interval K
 int bwd_segment_f64();
 }  // namespace sk
+
+namespace sk {
+// Tape-driven adjoint of the approximation scheme (dmax = 8 or 32).  NULL when no kernel exists.
+const void* bwd_tape_ptr_f32(int N, int dmax);
+const void* bwd_tape_ptr_f64(int N, int dmax);
+}  // namespace sk

@@ -213,6 +213,28 @@ __global__ void __launch_bounds__(kFwdWarps * 32, (fwd_poly_min_blocks<T, N, NE>
                     ea = eb;
                 }
             }
+            if constexpr (!INTERP) {
+                if (L.tape != nullptr && active) {  // record the cell's inputs for the adjoint
+                    constexpr int TR = tape_row<T>(N);
+                    V* dst = reinterpret_cast<V*>(static_cast<char*>(L.tape) + item * L.tape_stride) +
+                             (static_cast<int64_t>(step) * 32 + lane) * (TR / W);
+#pragma unroll
+                    for (int v = 0; v < TR / W; ++v) {
+                        V t;
+                        T* tp = reinterpret_cast<T*>(&t);
+#pragma unroll
+                        for (int w = 0; w < W; ++w) {
+                            const int q = v * W + w;
+                            tp[w] = q <= N ? a[q] : (q <= 2 * N + 1 ? b[q - N - 1] : T(0));
+                            if (q == 2 * N + 2) {
+                                if constexpr (std::is_same<T, float>::value) tp[w] = __int_as_float(ea);
+                                else tp[w] = __longlong_as_double(static_cast<long long>(ea));
+                            }
+                        }
+                        dst[v] = t;
+                    }
+                }
+            }
             // Every lane runs the cell (inactive lanes on a clamped, in-bounds column); only
             // the results of active lanes are ever consumed.
             const int jc = min(max(jj, 0), cols - 1);
@@ -274,10 +296,15 @@ __global__ void __launch_bounds__(kFwdWarps * 32, (fwd_poly_min_blocks<T, N, NE>
             // The last cell was the final step of lane `last_lane`; for the approximation scheme
             // its outputs are still in (a, bo): k_hat = 1/2 sum_n (a_n + b_n) / n!.
             if (lane == last_lane) {
-                double v = 0.5 * (series_at_one<T, N>(a) + series_at_one<T, N>(bo));
-                if (kRescale) v = ldexp(v, ea);
+                const double v0 = 0.5 * (series_at_one<T, N>(a) + series_at_one<T, N>(bo));
+                const double v = kRescale ? ldexp(v0, ea) : v0;
                 if (!isfinite(v)) record_error(SK_ERR_NONFINITE);
                 write_result(L, item, P, v);
+                if (L.tape_ek != nullptr) {
+                    int e2 = 0;
+                    if (v0 != 0.0) frexp(v0, &e2);
+                    L.tape_ek[item] = (kRescale ? ea : 0) + e2;
+                }
             }
         }
     }

@@ -26,7 +26,7 @@ SCHEMES = {"fd1": 0, "fd2": 1, "approx": 2, "interp": 3}
 COMPUTE = {"f64": 0, "f32": 1}
 DTYPES = {torch.float64: 0, torch.float32: 1, torch.bfloat16: 2}
 FLAG_SYMMETRIC, FLAG_INCREMENTS, FLAG_UNBIASED, FLAG_NO_SORT, FLAG_TIME_KERNEL = 1, 2, 4, 8, 16
-OP_PAIRS, OP_GRAM, OP_BACKWARD, OP_MMD2 = 0, 1, 2, 3
+OP_PAIRS, OP_GRAM, OP_BACKWARD, OP_MMD2, OP_BACKWARD_TAPE = 0, 1, 2, 3, 4
 
 
 class SigKernelError(RuntimeError):
@@ -73,6 +73,12 @@ def load_library():
         lib.sigkernel_backward.argtypes = [PP, PP, I32, I32, P, P, I64, PO, P, P, P, P, SZ, P]
         lib.sigkernel_mmd2.restype = ctypes.c_int
         lib.sigkernel_mmd2.argtypes = [PP, PP, I32, I32, PO, P, P, P, P, SZ, P]
+        lib.sigkernel_tape_size.restype = ctypes.c_int
+        lib.sigkernel_tape_size.argtypes = [PP, PP, I32, I64, PO, ctypes.POINTER(SZ)]
+        lib.sigkernel_forward_tape.restype = ctypes.c_int
+        lib.sigkernel_forward_tape.argtypes = [PP, PP, I32, I32, P, P, I64, PO, P, P, SZ, P, SZ, P]
+        lib.sigkernel_backward_tape.restype = ctypes.c_int
+        lib.sigkernel_backward_tape.argtypes = [PP, PP, I32, I32, P, P, I64, PO, P, SZ, P, P, P, P, SZ, P]
         lib.sigkernel_last_kernel_ms.restype = ctypes.c_float
         lib.sigkernel_device_status.restype = ctypes.c_int
         lib.sigkernel_device_status.argtypes = [P]
@@ -243,6 +249,65 @@ def sigkernel_backward(grad_out, X, Y=None, pair_a=None, pair_b=None, scheme="ap
     return gX, gY
 
 
+def _pair_args(X, pair_a, pair_b, sym):
+    if pair_a is None:
+        return None, None, -1, None
+    pa = torch.as_tensor(pair_a, dtype=torch.int64, device="cuda").contiguous()
+    pb = torch.as_tensor(pair_b, dtype=torch.int64, device="cuda").contiguous()
+    return pa.data_ptr(), pb.data_ptr(), pa.numel(), (pa, pb)
+
+
+def sigkernel_forward_tape(X, Y=None, pair_a=None, pair_b=None, scheme="approx", degree=6, dyadic=0, compute="f32",
+                           sort=True, time_kernel=False, tape: torch.Tensor | None = None,
+                           workspace: torch.Tensor | None = None, out: torch.Tensor | None = None):
+    """Forward values (Gram when ``pair_a`` is None) plus the tape the adjoint replays from.
+    Returns (values, tape)."""
+    sym = pair_a is None and (Y is None or Y is X)
+    X = as_paths(X)
+    Y = X if (Y is None or Y is X) else as_paths(Y)
+    cX, cY = _cpaths(X), _cpaths(Y)
+    pa_ptr, pb_ptr, n, keep = _pair_args(X, pair_a, pair_b, sym)
+    flags = _flags(X, (FLAG_SYMMETRIC if sym else 0) | (0 if sort else FLAG_NO_SORT)
+                   | (FLAG_TIME_KERNEL if time_kernel else 0))
+    opt = _options(scheme, degree, dyadic, compute, flags)
+    lib = load_library()
+    nb = ctypes.c_size_t(0)
+    _check(lib.sigkernel_tape_size(ctypes.byref(cX), ctypes.byref(cY), X.d, n, ctypes.byref(opt), ctypes.byref(nb)))
+    if tape is None or tape.numel() < nb.value:
+        tape = torch.empty(int(nb.value), dtype=torch.uint8, device="cuda")
+    if out is None:
+        out = torch.empty((X.count, Y.count) if pair_a is None else (n,), dtype=torch.float64, device="cuda")
+    ws = workspace if workspace is not None else _workspace(OP_GRAM if pair_a is None else OP_PAIRS, cX, cY, X.d,
+                                                            n, opt)
+    _check(lib.sigkernel_forward_tape(ctypes.byref(cX), ctypes.byref(cY), X.d, _dtype_code(X, Y), pa_ptr, pb_ptr, n,
+                                      ctypes.byref(opt), out.data_ptr(), tape.data_ptr(), tape.numel(), ws.data_ptr(),
+                                      ws.numel(), _stream_ptr()))
+    return out, tape
+
+
+def sigkernel_backward_tape(tape, grad_out, X, Y=None, pair_a=None, pair_b=None, scheme="approx", degree=6, dyadic=0,
+                            compute="f32", sort=True, time_kernel=False):
+    """Gradients from a tape recorded by ``sigkernel_forward_tape`` with the same arguments."""
+    sym = pair_a is None and (Y is None or Y is X)
+    X = as_paths(X)
+    Y = X if (Y is None or Y is X) else as_paths(Y)
+    cX, cY = _cpaths(X), _cpaths(Y)
+    pa_ptr, pb_ptr, n, keep = _pair_args(X, pair_a, pair_b, sym)
+    flags = _flags(X, (FLAG_SYMMETRIC if sym else 0) | (0 if sort else FLAG_NO_SORT)
+                   | (FLAG_TIME_KERNEL if time_kernel else 0))
+    opt = _options(scheme, degree, dyadic, compute, flags)
+    g = torch.as_tensor(grad_out, dtype=torch.float64, device="cuda").contiguous()
+    gX = torch.zeros(X.rows.shape[0], X.d, dtype=torch.float64, device="cuda")
+    same = X is Y or (X.rows.data_ptr() == Y.rows.data_ptr() and X.offsets.data_ptr() == Y.offsets.data_ptr())
+    gY = gX if same else torch.zeros(Y.rows.shape[0], Y.d, dtype=torch.float64, device="cuda")
+    ws = _workspace(OP_BACKWARD_TAPE, cX, cY, X.d, n, opt)
+    _check(load_library().sigkernel_backward_tape(ctypes.byref(cX), ctypes.byref(cY), X.d, _dtype_code(X, Y), pa_ptr,
+                                                  pb_ptr, n, ctypes.byref(opt), tape.data_ptr(), tape.numel(),
+                                                  g.data_ptr(), gX.data_ptr(), None if same else gY.data_ptr(),
+                                                  ws.data_ptr(), ws.numel(), _stream_ptr()))
+    return gX, gY
+
+
 def sigkernel_mmd2(A, B, scheme="approx", degree=6, dyadic=0, compute="f64", unbiased=False, grads=False):
     """MMD^2 between path sets A and B; returns (mmd2, [mean K_AA, mean K_BB, mean K_AB]) or, with
     ``grads``, also (dMMD2/dA rows, dMMD2/dB rows) as float64 CUDA tensors."""
@@ -266,19 +331,25 @@ def sigkernel_mmd2(A, B, scheme="approx", degree=6, dyadic=0, compute="f64", unb
 # ----------------------------------------------------------------------------------------------
 class _GramFn(torch.autograd.Function):
     @staticmethod
-    def forward(ctx, X, Y, sym, opts):
-        ctx.opts, ctx.sym = opts, sym
+    def forward(ctx, X, Y, sym, opts, use_tape):
+        ctx.opts, ctx.sym, ctx.use_tape = opts, sym, use_tape
         ctx.save_for_backward(X, Y)
+        if use_tape:
+            G, ctx.tape = sigkernel_forward_tape(X, None if sym else Y, **opts)
+            return G
         return sigkernel_gram(X, None if sym else Y, **opts)
 
     @staticmethod
     def backward(ctx, gG):
         X, Y = ctx.saved_tensors
+        if ctx.use_tape:
+            gX, gY = sigkernel_backward_tape(ctx.tape, gG, X, None if ctx.sym else Y, **ctx.opts)
+            ctx.tape = None
+        else:
+            gX, gY = sigkernel_backward(gG, X, None if ctx.sym else Y, **ctx.opts)
         if ctx.sym:
-            gX, _ = sigkernel_backward(gG, X, None, **ctx.opts)
-            return gX.view_as(X).to(X.dtype), None, None, None
-        gX, gY = sigkernel_backward(gG, X, Y, **ctx.opts)
-        return gX.view_as(X).to(X.dtype), gY.view_as(Y).to(Y.dtype), None, None
+            return gX.view_as(X).to(X.dtype), None, None, None, None
+        return gX.view_as(X).to(X.dtype), gY.view_as(Y).to(Y.dtype), None, None, None
 
 
 class _MMD2Fn(torch.autograd.Function):
@@ -296,14 +367,17 @@ class _MMD2Fn(torch.autograd.Function):
 
 class SigKernel:
     """Signature kernel k_hat of one scheme: ``gram`` and ``mmd2`` are differentiable with respect
-    to dense [B, L, d] path tensors through the adjoint wavefront."""
+    to dense [B, L, d] path tensors through the adjoint wavefront.  With ``tape=True`` the Gram's
+    forward records every cell's inputs (about 64 B per cell in FP32) and the adjoint replays them
+    instead of recomputing the forward sweep."""
 
-    def __init__(self, scheme="approx", degree=6, dyadic=0, compute="f32"):
+    def __init__(self, scheme="approx", degree=6, dyadic=0, compute="f32", tape=False):
         self.opts = dict(scheme=scheme, degree=degree, dyadic=dyadic, compute=compute)
+        self.tape = tape
 
     def gram(self, X: torch.Tensor, Y: torch.Tensor | None = None) -> torch.Tensor:
         sym = Y is None or Y is X
-        return _GramFn.apply(X, X if sym else Y, sym, self.opts)
+        return _GramFn.apply(X, X if sym else Y, sym, self.opts, self.tape)
 
     def mmd2(self, A: torch.Tensor, B: torch.Tensor, unbiased: bool = False) -> torch.Tensor:
         return _MMD2Fn.apply(A, B, unbiased, self.opts)

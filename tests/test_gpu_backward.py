@@ -230,3 +230,55 @@ def test_gradcheck_small():
     Y = _cuda(W.brownian(2, 5, 2, seed=73)).requires_grad_(True)
     kern = sk.SigKernel("approx", 5, 0, "f64")
     assert torch.autograd.gradcheck(lambda x, y: kern.gram(x, y), (X, Y), eps=1e-6, atol=1e-8, rtol=1e-6)
+
+
+# ------------------------------------------------------------------------------------------
+# Adjoint from a forward tape: same gradients as the checkpointing adjoint and the oracle
+# ------------------------------------------------------------------------------------------
+@pytest.mark.parametrize("compute,tol", [("f64", 1e-9), ("f32", 1e-4)])
+@pytest.mark.parametrize("sym", [False, True])
+def test_tape_backward_matches_oracle(compute, tol, sym):
+    X = W.brownian(3, 41, 3, seed=74)
+    Y = X if sym else W.brownian(4, 37, 3, seed=75)
+    rng = np.random.default_rng(76)
+    Wt = rng.normal(size=(X.shape[0], Y.shape[0]))
+    Xt = _cuda(X)
+    Yt = None if sym else _cuda(Y)
+    G, tape = sk.sigkernel_forward_tape(Xt, Yt, degree=6, compute=compute)
+    G2 = sk.sigkernel_gram(Xt, Yt, degree=6, compute=compute)
+    torch.cuda.synchronize()
+    assert torch.equal(G, G2)  # recording the tape does not change the forward
+    gX, gY = sk.sigkernel_backward_tape(tape, _cuda(Wt), Xt, Yt, degree=6, compute=compute)
+    cX, cY = sk.sigkernel_backward(_cuda(Wt), Xt, Yt, degree=6, compute=compute)
+    torch.cuda.synchronize()
+    assert sk.device_status() == 0
+    assert _scaled_err(gX.cpu().numpy(), cX.cpu().numpy()) < 1e-12
+    rX, rY = _oracle_gram_grad(X, Y, Wt, 6, 0, sym)
+    assert _scaled_err(gX.cpu().numpy().reshape(X.shape), rX) < tol
+    if not sym:
+        assert _scaled_err(gY.cpu().numpy().reshape(Y.shape), rY) < tol
+
+
+def test_tape_backward_pairs_dyadic_and_rescaled():
+    X = 14.0 * W.brownian(2, 49, 2, seed=58)
+    Y = 14.0 * W.brownian(2, 49, 2, seed=59)
+    pa, pb = [1, 0], [0, 1]
+    out, tape = sk.sigkernel_forward_tape(_cuda(X), _cuda(Y), pair_a=pa, pair_b=pb, degree=8, dyadic=1,
+                                          compute="f32")
+    gX, gY = sk.sigkernel_backward_tape(tape, _cuda([1.0, 0.0]), _cuda(X), _cuda(Y), pair_a=pa, pair_b=pb,
+                                        degree=8, dyadic=1, compute="f32")
+    torch.cuda.synchronize()
+    gx, gy = oracle.grad(X[1], Y[0], "approx", 8, 1)
+    got = gX.cpu().numpy().reshape(X.shape)[1]
+    assert np.all(np.isfinite(got))
+    assert _scaled_err(got, gx) < 1e-3
+
+
+def test_autograd_with_tape():
+    X = _cuda(W.brownian(4, 30, 2, seed=77)).requires_grad_(True)
+    kern = sk.SigKernel("approx", 6, 0, "f64", tape=True)
+    G = kern.gram(X)
+    wts = torch.randn(4, 4, dtype=torch.float64, device="cuda")
+    (G * wts).sum().backward()
+    gX, _ = sk.sigkernel_backward(wts, X.detach(), None, degree=6, compute="f64")
+    assert torch.allclose(X.grad.reshape(-1, 2), gX, rtol=1e-11, atol=1e-14)
