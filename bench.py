@@ -39,7 +39,7 @@ D = 8
 DEGREE = 6
 CELLS_PER_PAIR = (L - 1) * (L - 1)
 CELLS = NX * NY * CELLS_PER_PAIR
-PARTS = ("f32", "fwd", "f64", "e2e", "cpu")
+PARTS = ("f32", "ckpt", "fwd", "f64", "e2e", "cpu")
 SM_COUNT = 152
 FP32_LANES = 128
 SM_MAX_MHZ = 2070.0
@@ -231,16 +231,26 @@ def main():
     Wt = torch.tensor(np.random.default_rng(11 + rank).standard_normal((nx, nx)), device=dev)
     opts = dict(scheme="approx", degree=DEGREE, sort=False)
 
-    def run(compute, steps, warmup, backward=True):
-        """Timed fwd(+bwd) steps; returns per-step ms, forward-kernel ms, adjoint-kernel ms, wall s."""
+    tape_buf = [None]
+
+    def run(compute, steps, warmup, backward=True, tape=True):
+        """Timed fwd(+bwd) steps; returns per-step ms, forward-kernel ms, adjoint-kernel ms, wall s.
+        With `tape` the forward records the cell inputs and the adjoint replays them."""
         ws = sk.gram_workspace(Xt, Yt, scheme="approx", degree=DEGREE, compute=compute)
 
         def step(timed):
-            sk.sigkernel_gram(Xt, Yt, compute=compute, workspace=ws, out=G, time_kernel=timed, **opts)
+            if backward and tape:
+                _, tape_buf[0] = sk.sigkernel_forward_tape(Xt, Yt, compute=compute, workspace=ws, out=G,
+                                                           tape=tape_buf[0], time_kernel=timed, **opts)
+            else:
+                sk.sigkernel_gram(Xt, Yt, compute=compute, workspace=ws, out=G, time_kernel=timed, **opts)
             kf = sk.last_kernel_ms() if timed else None
             kb = None
             if backward:
-                sk.sigkernel_backward(Wt, Xt, Yt, compute=compute, time_kernel=timed, **opts)
+                if tape:
+                    sk.sigkernel_backward_tape(tape_buf[0], Wt, Xt, Yt, compute=compute, time_kernel=timed, **opts)
+                else:
+                    sk.sigkernel_backward(Wt, Xt, Yt, compute=compute, time_kernel=timed, **opts)
                 kb = sk.last_kernel_ms() if timed else None
             return kf, kb
 
@@ -299,7 +309,7 @@ def main():
     mape = {"f32": float(np.mean(np.abs(g32 - ref) / np.abs(ref))), "sample": "16 sampled Gram entries"}
     line.update({
         "metric": "Goursat cell-updates/s of the fwd+bwd Gram step (polynomial approximation N=6, 128x128 Gram, "
-                  "batched FP32)",
+                  "batched FP32, forward tape)",
         "value": value, "unit": "cell-updates/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32", "data": "synthetic",
@@ -308,17 +318,28 @@ def main():
                    "scheme": "polynomial approximation", "degree": DEGREE, "dyadic": 0,
                    "cells_per_step": cells, "pairs_per_step": nx * nx,
                    "l2": "256 MiB buffer written between timed steps (outside the events)",
+                   "tape_gb": round(tape_buf[0].numel() / 1e9, 2),
                    "parallelism": f"weak scaling, one independent {nx}x{nx} Gram per GPU ({world} GPUs)"},
         "roofline": {"bound": "alu", "achieved": ach_b, "peak": peak, "unit": "TFLOP/s", "frac": ach_b / peak,
-                     "traffic": None, "kernel": "bwd_approx_kernel<float,6,8,8> (adjoint wavefront)", "kernel_ms": kb,
+                     "traffic": None, "kernel": "bwd_tape_kernel<float,6,8> (adjoint wavefront from the tape)",
+                     "kernel_ms": kb,
                      "flops_per_cell": bpc,
                      "peak_source": "152 SMs x 128 FP32 lanes x 2 FLOP x 2070 MHz (derived, nominal clocks)"},
-        "forward_kernel": {"kernel": "fwd_poly_kernel<float,6,6,false>", "kernel_ms": kf, "achieved_tflops": ach_f,
+        "forward_kernel": {"kernel": "fwd_poly_kernel<float,6,6,false> (recording the tape)", "kernel_ms": kf,
+                           "achieved_tflops": ach_f,
                            "frac": ach_f / peak, "flops_per_cell": fpc,
                            "cell_updates_per_s": cells / (kf / 1e3)},
         "gpu_launches": 8 * args.steps,  # forward: 2 increments + wavefront; adjoint: 2 increments + adjoint + 2 gradient conversions
         "clocks": clocks, "device_status": status, "wall_s_timed_region": wall,
     })
+
+    if "ckpt" in args.parts:  # the same step with the checkpointing adjoint (no tape)
+        sc, kfc, kbc, _ = run("f32", max(2, min(3, args.steps)), 1, tape=False)
+        line["checkpoint_adjoint"] = {"value": cells / (statistics.mean(sc) / 1e3), "unit": "cell-updates/s",
+                                      "ms_per_step": statistics.mean(sc), "forward_kernel_ms": statistics.mean(kfc),
+                                      "adjoint_kernel_ms": statistics.mean(kbc)}
+    tape_buf[0] = None
+    torch.cuda.empty_cache()
 
     if "fwd" in args.parts:  # forward only (the Gram alone)
         sf, kff, _, _ = run("f32", args.steps, 2, backward=False)
@@ -353,8 +374,9 @@ def main():
             Xt.copy_(Xh, non_blocking=True)
             Yt.copy_(Yh, non_blocking=True)
             Wd.copy_(Wh, non_blocking=True)
-            sk.sigkernel_gram(Xt, Yt, compute="f32", workspace=ws, out=G, **opts)
-            gX, gY = sk.sigkernel_backward(Wd, Xt, Yt, compute="f32", **opts)
+            _, tape_buf[0] = sk.sigkernel_forward_tape(Xt, Yt, compute="f32", workspace=ws, out=G, tape=tape_buf[0],
+                                                       **opts)
+            gX, gY = sk.sigkernel_backward_tape(tape_buf[0], Wd, Xt, Yt, compute="f32", **opts)
             Gh.copy_(G, non_blocking=True)
             gXh.copy_(gX, non_blocking=True)
             gYh.copy_(gY, non_blocking=True)
@@ -366,6 +388,7 @@ def main():
                        "h2d_bytes_per_step": int((Xh.numel() + Yh.numel() + Wh.numel()) * 8),
                        "d2h_bytes_per_step": int((Gh.numel() + gXh.numel() + gYh.numel()) * 8),
                        "ms_per_step": statistics.mean(e2e_ms)}
+        tape_buf[0] = None
 
     if rank == 0:
         if "cpu" in args.parts:
