@@ -105,6 +105,23 @@ __device__ __forceinline__ void fwd_cell(T (&a)[N + 1], const T (&b)[N + 1], T M
     }
 }
 
+// Scale a cell's forward inputs to magnitude ~1 by an exact power of two (FP32), folding the shift
+// into their exponent, so that products with adjoints (kept within 2^+-64) cannot overflow.
+template <typename T, int N>
+__device__ __forceinline__ void unit_scale(T (&fa)[N + 1], T (&fb)[N + 1], int& ef) {
+    if constexpr (std::is_same<T, float>::value) {
+        const float m = fmaxf(fabsf(fa[0]), fabsf(fb[0]));
+        if (m > 0x1p16f || (m < 0x1p-16f && m > 0.f)) {
+            int sh = 0;
+            frexpf(m, &sh);
+            const float f = pow2c<float>(-sh);
+#pragma unroll
+            for (int n = 0; n <= N; ++n) { fa[n] *= f; fb[n] *= f; }
+            ef += sh;
+        }
+    }
+}
+
 template <typename T, int N>
 __device__ __forceinline__ void cell_adjoint(const T (&a)[N + 1], const T (&b)[N + 1], const T (&e)[N + 1],
                                              const T (&ga)[N + 1], const T (&gb)[N + 1], T (&ra)[N + 1],
@@ -463,7 +480,8 @@ __global__ void __launch_bounds__(kFwdWarps * 32, (bwd_min_blocks<T, N, K>()))
                             fb[n] = sk_[(N + 1 + n) * 32 + lane];
                         }
                         const T M = sk_[(2 * N + 2) * 32 + lane];
-                        const int ef = stk_e[k * 32 + lane];
+                        int ef = stk_e[k * 32 + lane];
+                        unit_scale<T, N>(fa, fb, ef);
                         build_exp_series<T, N>(M, L.tau, e);
                         T mbar;
                         cell_adjoint<T, N>(fa, fb, e, ga_in, gb_in, gra, gbo, mbar);
@@ -685,6 +703,7 @@ __global__ void __launch_bounds__(kFwdWarps * 32, (bwd_tape_min_blocks<T, N, DMA
                     if constexpr (std::is_same<T, float>::value) ef = __float_as_int(tp[2 * N + 2]);
                     else ef = static_cast<int>(__double_as_longlong(tp[2 * N + 2]));
                 }
+                unit_scale<T, N>(fa, fb, ef);
                 const T* xrow = xbase + static_cast<int64_t>(row >> lam) * dpad;
                 const T* yrow = ybase + static_cast<int64_t>(jj >> lam) * dpad;
                 const T M = row_dot<T>(xrow, yrow, L.nvec) * pow2t<T>(-2 * lam);
