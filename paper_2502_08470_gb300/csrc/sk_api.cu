@@ -335,13 +335,19 @@ int run_forward(const sk_paths* X, const sk_paths* Y, int32_t d, int32_t dtype, 
     }
     int64_t buf_cols = p.buf_cols;
     void* args[] = {&L, &buf_cols};
+    int smem = 0;
+    if (tape) {  // two staging slots per warp for the tape's bulk copies
+        const int step_bytes = 32 * (p.T ? tape_row<float>(o->degree) * 4 : tape_row<double>(o->degree) * 8);
+        smem = kFwdWarps * 2 * step_bytes;
+        if (smem > 48 * 1024) SK_CUDA(cudaFuncSetAttribute(p.kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    }
     const bool timed = (o->flags & SK_FLAG_TIME_KERNEL) != 0;
     if (timed) {
         if (!t_ev0) SK_CUDA(cudaEventCreate(&t_ev0));
         if (!t_ev1) SK_CUDA(cudaEventCreate(&t_ev1));
         SK_CUDA(cudaEventRecord(t_ev0, st));
     }
-    SK_CUDA(cudaLaunchKernel(p.kern, dim3(p.blocks), dim3(p.threads), args, 0, st));
+    SK_CUDA(cudaLaunchKernel(p.kern, dim3(p.blocks), dim3(p.threads), args, smem, st));
     if (timed) {
         SK_CUDA(cudaEventRecord(t_ev1, st));
         t_timed = true;
@@ -579,7 +585,11 @@ int plan_backward_tape(const sk_paths* X, const sk_paths* Y, int32_t d, int32_t 
     if (!dmax) return fail(SK_ERR_UNSUPPORTED, "the adjoint supports d <= 32");
     b.kern = p.T ? bwd_tape_ptr_f32(o->degree, dmax) : bwd_tape_ptr_f64(o->degree, dmax);
     if (!b.kern) return fail(SK_ERR_UNSUPPORTED, "no adjoint kernel for order %d", o->degree);
-    b.smem_bytes = kFwdWarps * (p.T ? bwd_xacc_bytes<float>(p.dpad) : bwd_xacc_bytes<double>(p.dpad));
+    {
+        const int step_bytes = 32 * (p.T ? tape_row<float>(o->degree) * 4 : tape_row<double>(o->degree) * 8);
+        const int xacc = p.T ? bwd_xacc_bytes<float>(p.dpad) : bwd_xacc_bytes<double>(p.dpad);
+        b.smem_bytes = kFwdWarps * (kTapeRing * step_bytes + kTapeRing * 8 + xacc);
+    }
     const int esize = p.T ? 4 : 8, N = o->degree;
     b.cols_max = std::max<int64_t>(Y->max_len << o->dyadic, 1);
     b.off_rbuf = 0;
@@ -590,6 +600,7 @@ int plan_backward_tape(const sk_paths* X, const sk_paths* Y, int32_t d, int32_t 
     int dev = 0, sms = 0, per_sm = 0;
     SK_CUDA(cudaGetDevice(&dev));
     SK_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    SK_CUDA(cudaFuncSetAttribute(b.kern, cudaFuncAttributeMaxDynamicSharedMemorySize, b.smem_bytes));
     SK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, b.kern, p.threads, b.smem_bytes));
     if (per_sm < 1) return fail(SK_ERR_UNSUPPORTED, "adjoint kernel does not fit an SM");
     const int64_t want = (npairs + kFwdWarps - 1) / kFwdWarps;

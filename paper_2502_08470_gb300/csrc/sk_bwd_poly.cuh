@@ -32,6 +32,7 @@
 #include <type_traits>
 
 #include "sk_fwd_poly.cuh"
+#include "sk_tma.cuh"
 
 namespace sk {
 
@@ -553,14 +554,24 @@ __global__ void __launch_bounds__(kFwdWarps * 32, (bwd_min_blocks<T, N, K>()))
 
 
 // ---------------------------------------------------------------------------------------------
-// Adjoint from a forward tape.  The forward kernel recorded, for every warp step and lane, the
-// cell's inputs (a, b, exponent) and the exponent of k_hat; this kernel walks the same steps
-// backward (the reverse of the forward schedule, strips overlapping exactly as there) and needs
-// no forward recomputation.  Tape rows are prefetched one step ahead.
+// Adjoint from a forward tape.  The forward kernel recorded, for every warp step, the 32 lanes'
+// cell inputs (a, b, exponent; laid out [vector][lane]) and the exponent of k_hat; this kernel
+// walks the same steps backward (the reverse of the forward schedule, strips overlapping exactly
+// as there) and needs no forward recomputation.  The steps stream into a ring of kTapeRing
+// shared-memory slots per warp with bulk copies issued kTapeRing steps ahead by lane 0, each slot
+// completing on its own mbarrier.
 // ---------------------------------------------------------------------------------------------
+constexpr int kTapeRing = 8;
+
 template <typename T, int N, int DMAX>
 __host__ __device__ constexpr int bwd_tape_min_blocks() {
     return sizeof(T) == 8 ? 1 : 3;
+}
+
+// Shared memory of one warp for the tape adjoint: the ring, its mbarriers, dk/dx accumulators.
+template <typename T, int N>
+__host__ __device__ constexpr int bwd_tape_warp_bytes(int dpad) {
+    return kTapeRing * fwd_tape_step_bytes<T, N>() + kTapeRing * 8 + bwd_xacc_bytes<T>(dpad);
 }
 
 template <typename T, int N, int DMAX>
@@ -578,13 +589,24 @@ __global__ void __launch_bounds__(kFwdWarps * 32, (bwd_tape_min_blocks<T, N, DMA
     T* rbuf = reinterpret_cast<T*>(base + B.off_rbuf);          // [col][N+1]
     int* rexp = reinterpret_cast<int*>(base + B.off_rexp);      // [col]
     const int dpad = L.dpad;
+    constexpr int kStepBytes = fwd_tape_step_bytes<T, N>();
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    T* xacc = reinterpret_cast<T*>(smem_raw + wib * bwd_xacc_bytes<T>(dpad)) + lane * (dpad + 1);
+    unsigned char* wsm = smem_raw + wib * bwd_tape_warp_bytes<T, N>(dpad);
+    unsigned char* ring = wsm;
+    uint64_t* bars = reinterpret_cast<uint64_t*>(wsm + kTapeRing * kStepBytes);
+    T* xacc = reinterpret_cast<T*>(wsm + kTapeRing * kStepBytes + kTapeRing * 8) + lane * (dpad + 1);
     const T* __restrict__ incX = static_cast<const T*>(L.X.inc);
     const T* __restrict__ incY = static_cast<const T*>(L.Y.inc);
+    if (lane == 0) {
+        for (int k = 0; k < kTapeRing; ++k) mbar_init(bars + k, 1);
+        fence_mbar_init();
+    }
+    __syncwarp();
+    uint32_t parity = 0;  // bit k: phase of slot k's barrier awaited next (warp-uniform)
+    bool stuck = false;
 
     for (;;) {
-        const int64_t item = next_item(L);
+        const int64_t item = stuck ? -1 : next_item(L);
         if (item < 0) break;
         const PairDesc P = decode_pair(L, item);
         if (P.lx < 0 || P.ly < 0) {
@@ -609,7 +631,7 @@ __global__ void __launch_bounds__(kFwdWarps * 32, (bwd_tape_min_blocks<T, N, DMA
         const T* ybase = incY + P.ys * dpad;
         const int ek = L.tape_ek[item];
         const double gscale = gbar * pow2d(ek);
-        const V* tape = reinterpret_cast<const V*>(static_cast<const char*>(L.tape) + item * L.tape_stride);
+        const char* tape = static_cast<const char*>(L.tape) + item * L.tape_stride;
 
         T gra[N + 1], gbo[N + 1];
         int gea = kZeroExp, gbe = kZeroExp;
@@ -620,21 +642,39 @@ __global__ void __launch_bounds__(kFwdWarps * 32, (bwd_tape_min_blocks<T, N, DMA
         for (int c = 0; c < DMAX; ++c) ysum[c] = T(0);
         for (int c = 0; c < dpad; ++c) xacc[c] = T(0);
 
+        // fill the ring with the last kTapeRing steps (step t lives in slot t % kTapeRing)
+        if (lane == 0) {
+            for (int k = 0; k < kTapeRing && nsteps - 1 - k >= 0; ++k) {
+                const int t = nsteps - 1 - k;
+                const int sl = t % kTapeRing;
+                mbar_arrive_expect_tx(bars + sl, kStepBytes);
+                bulk_load(ring + sl * kStepBytes, tape + static_cast<int64_t>(t) * kStepBytes, kStepBytes, bars + sl);
+            }
+        }
         // position of this lane at the last step, then walked backward one step at a time
         int tt = nsteps - 1 - lane;
         int s = tt >= 0 ? tt / period : -1;
         int jj = tt >= 0 ? tt - s * period : -1;
-        V cur[TR / W], nxt[TR / W];
-        {
-            const V* src = tape + (static_cast<int64_t>(nsteps - 1) * 32 + lane) * (TR / W);
-#pragma unroll
-            for (int v = 0; v < TR / W; ++v) cur[v] = src[v];
-        }
+        int stuck_step = -1;
         for (int step = nsteps - 1; step >= 0; --step) {
-            if (step > 0) {  // prefetch the previous step's row (lanes whose cell is real read real data)
-                const V* src = tape + (static_cast<int64_t>(step - 1) * 32 + lane) * (TR / W);
+            const int sl = step % kTapeRing;
+            if (!mbar_wait(bars + sl, (parity >> sl) & 1u)) {
+                stuck = true;  // the device error word is set; drain what is in flight and stop
+                stuck_step = step;
+                break;
+            }
+            parity ^= 1u << sl;
+            T cur[TR];
+            {
+                const V* src = reinterpret_cast<const V*>(ring + sl * kStepBytes);
 #pragma unroll
-                for (int v = 0; v < TR / W; ++v) nxt[v] = src[v];
+                for (int v = 0; v < TR / W; ++v) reinterpret_cast<V*>(cur)[v] = src[v * 32 + lane];
+            }
+            __syncwarp();  // every lane has its row: the slot can be refilled
+            if (lane == 0 && step - kTapeRing >= 0) {
+                mbar_arrive_expect_tx(bars + sl, kStepBytes);
+                bulk_load(ring + sl * kStepBytes, tape + static_cast<int64_t>(step - kTapeRing) * kStepBytes,
+                          kStepBytes, bars + sl);
             }
             T gb_in[N + 1];
 #pragma unroll
@@ -693,16 +733,13 @@ __global__ void __launch_bounds__(kFwdWarps * 32, (bwd_tape_min_blocks<T, N, DMA
                 }
                 T fa[N + 1], fb[N + 1], e[N + 1];
                 int ef;
-                {
-                    const T* tp = reinterpret_cast<const T*>(cur);
 #pragma unroll
-                    for (int n = 0; n <= N; ++n) {
-                        fa[n] = tp[n];
-                        fb[n] = tp[N + 1 + n];
-                    }
-                    if constexpr (std::is_same<T, float>::value) ef = __float_as_int(tp[2 * N + 2]);
-                    else ef = static_cast<int>(__double_as_longlong(tp[2 * N + 2]));
+                for (int n = 0; n <= N; ++n) {
+                    fa[n] = cur[n];
+                    fb[n] = cur[N + 1 + n];
                 }
+                if constexpr (std::is_same<T, float>::value) ef = __float_as_int(cur[2 * N + 2]);
+                else ef = static_cast<int>(__double_as_longlong(cur[2 * N + 2]));
                 unit_scale<T, N>(fa, fb, ef);
                 const T* xrow = xbase + static_cast<int64_t>(row >> lam) * dpad;
                 const T* yrow = ybase + static_cast<int64_t>(jj >> lam) * dpad;
@@ -766,12 +803,21 @@ __global__ void __launch_bounds__(kFwdWarps * 32, (bwd_tape_min_blocks<T, N, DMA
                 }
             }
             __syncwarp();
-#pragma unroll
-            for (int v = 0; v < TR / W; ++v) cur[v] = nxt[v];
             if (s >= 0 && --jj < 0) {
                 jj = period - 1;
                 --s;
             }
+        }
+        if (stuck) {
+            // Wait (bounded) for the copies still in flight into this warp's ring (steps stuck_step
+            // down to stuck_step - kTapeRing + 1) before leaving.
+            if (lane == 0)
+                for (int k = 0; k < kTapeRing && stuck_step - k >= 0; ++k) {
+                    const int sl = (stuck_step - k) % kTapeRing;
+                    mbar_wait(bars + sl, (parity >> sl) & 1u);
+                }
+            __syncwarp();
+            break;
         }
         __syncwarp();
     }

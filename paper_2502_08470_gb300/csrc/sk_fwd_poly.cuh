@@ -35,6 +35,7 @@
 #include <type_traits>
 
 #include "sk_common.cuh"
+#include "sk_tma.cuh"
 
 namespace sk {
 
@@ -113,6 +114,12 @@ __device__ __forceinline__ T pow2t(int e) {
     else return pow2d(e);
 }
 
+// Bytes of one warp step of the tape (32 lanes x one padded row of cell inputs).
+template <typename T, int N>
+__host__ __device__ constexpr int fwd_tape_step_bytes() {
+    return 32 * tape_row<T>(N) * static_cast<int>(sizeof(T));
+}
+
 // Resident blocks per SM requested from the register allocator: the live state of a lane is
 // about 3 (N+1) edge values, 3 (NE+1) series values and ~24 addresses / counters.
 template <typename T, int N, int NE>
@@ -137,6 +144,9 @@ __global__ void __launch_bounds__(kFwdWarps * 32, (fwd_poly_min_blocks<T, N, NE>
     const int dpad = L.dpad;
     const T* __restrict__ incX = static_cast<const T*>(L.X.inc);
     const T* __restrict__ incY = static_cast<const T*>(L.Y.inc);
+    // tape staging (two step slots per warp) in dynamic shared memory, used only with a tape
+    extern __shared__ __align__(128) unsigned char fwd_smem[];
+    unsigned char* tape_stage = fwd_smem + (threadIdx.x >> 5) * 2 * fwd_tape_step_bytes<T, N>();
 
     for (;;) {
         const int64_t item = next_item(L);
@@ -214,10 +224,16 @@ __global__ void __launch_bounds__(kFwdWarps * 32, (fwd_poly_min_blocks<T, N, NE>
                 }
             }
             if constexpr (!INTERP) {
-                if (L.tape != nullptr && active) {  // record the cell's inputs for the adjoint
+                if (L.tape != nullptr) {
+                    // Record the cell's inputs for the adjoint: each lane writes its row into a
+                    // shared-memory slot laid out [vector][lane], then one lane moves the whole step
+                    // (32 rows) to the tape with a bulk copy.  Two slots alternate; a slot is
+                    // rewritten only after the copy issued from it two steps ago has read it.
                     constexpr int TR = tape_row<T>(N);
-                    V* dst = reinterpret_cast<V*>(static_cast<char*>(L.tape) + item * L.tape_stride) +
-                             (static_cast<int64_t>(step) * 32 + lane) * (TR / W);
+                    constexpr int kStepBytes = 32 * TR * static_cast<int>(sizeof(T));
+                    V* slot_v = reinterpret_cast<V*>(tape_stage + (step & 1) * kStepBytes);
+                    if (lane == 0) bulk_wait_read<1>();
+                    __syncwarp();
 #pragma unroll
                     for (int v = 0; v < TR / W; ++v) {
                         V t;
@@ -231,7 +247,14 @@ __global__ void __launch_bounds__(kFwdWarps * 32, (fwd_poly_min_blocks<T, N, NE>
                                 else tp[w] = __longlong_as_double(static_cast<long long>(ea));
                             }
                         }
-                        dst[v] = t;
+                        slot_v[v * 32 + lane] = t;
+                    }
+                    fence_proxy_async_smem();
+                    __syncwarp();
+                    if (lane == 0) {
+                        bulk_store(static_cast<char*>(L.tape) + item * L.tape_stride + static_cast<int64_t>(step) * kStepBytes,
+                                   slot_v, kStepBytes);
+                        bulk_commit();
                     }
                 }
             }
@@ -308,6 +331,7 @@ __global__ void __launch_bounds__(kFwdWarps * 32, (fwd_poly_min_blocks<T, N, NE>
             }
         }
     }
+    if (!INTERP && L.tape != nullptr && lane == 0) bulk_wait_all();  // no copy outlives the staging smem
 }
 
 
