@@ -53,13 +53,23 @@ def flops_per_cell(N: int, d: int) -> int:
     return 2 * fma
 
 
-def bwd_flops_per_cell(N: int, d: int) -> int:
-    """Algorithmic FLOPs of one cell of the adjoint (2 per multiply-add): the forward cell whose
-    values it needs, its transpose (Toeplitz (N+1)(N+2), Hankel 2N(N+1), weights 2(N+1)), the
-    e_m adjoint with recomputed Hankel sums 3N^2 + 4N, and the two d-term contractions
-    dk/dx += Mbar dy, dk/dy += Mbar dx.  Checkpoint replays are not counted."""
-    adj = 2 * (N + 1) + (N + 1) * (N + 2) + 2 * N * (N + 1) + 3 * N * N + 4 * N + 2 * d
-    return flops_per_cell(N, d) + 2 * adj
+def adjoint_core_fma(N: int) -> int:
+    """Multiply-adds of one cell's adjoint map: weights 2(N+1), Toeplitz transposes (N+1)(N+2),
+    Hankel couplings 2N(N+1), and dk/dM with its recomputed Hankel sums 3N^2 + 4N."""
+    return 2 * (N + 1) + (N + 1) * (N + 2) + 2 * N * (N + 1) + 3 * N * N + 4 * N
+
+
+def tape_adjoint_flops_per_cell(N: int) -> int:
+    """Algorithmic FLOPs of one cell of the tape adjoint kernel (2 per multiply-add): the adjoint
+    map plus the N terms of e_m = M^m/m! rebuilt from the recorded M.  The forward cell is not
+    recomputed and the d-term contractions run in the separate contraction kernel."""
+    return 2 * (adjoint_core_fma(N) + N)
+
+
+def contract_bytes_per_cell(esize: int = 4) -> int:
+    """Algorithmic DRAM bytes per cell of the contraction kernel: one dk/dM element read (the
+    increments it multiplies are re-read from L1/L2 and counted per pair, not per cell)."""
+    return esize
 
 
 def parse():
@@ -71,6 +81,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--nx", type=int, default=NX,
                     help="paths per side (a smaller Gram of the same paths, for profiling runs)")
+    ap.add_argument("--len", type=int, default=L,
+                    help="points per path (shorter paths, for profiling runs that must hold only a few GB)")
     ap.add_argument("--parts", default=",".join(PARTS),
                     help="comma list: f32 (headline fwd+bwd step), fwd (forward only), f64 (FP64 forward), "
                          "e2e, cpu")
@@ -81,10 +93,10 @@ def parse():
     return args
 
 
-def workload(rank: int, n: int = NX):
+def workload(rank: int, n: int = NX, points: int = L):
     from paper_2502_08470_gb300 import workloads as W
-    X = W.brownian(NX, L, D, seed=3 + 1000 * rank)[:n]
-    Y = W.brownian(NY, L, D, seed=4 + 1000 * rank)[:n]
+    X = W.brownian(NX, points, D, seed=3 + 1000 * rank)[:n]
+    Y = W.brownian(NY, points, D, seed=4 + 1000 * rank)[:n]
     return X, Y
 
 
@@ -221,8 +233,9 @@ def main():
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     nx = args.nx
-    cells = nx * nx * CELLS_PER_PAIR
-    X, Y = workload(rank, nx)
+    npts = args.len
+    cells = nx * nx * (npts - 1) ** 2
+    X, Y = workload(rank, nx, npts)
     Xt = torch.tensor(X, device=dev)
     Yt = torch.tensor(Y, device=dev)
     G = torch.empty(nx, nx, dtype=torch.float64, device=dev)
@@ -246,30 +259,38 @@ def main():
                 sk.sigkernel_gram(Xt, Yt, compute=compute, workspace=ws, out=G, time_kernel=timed, **opts)
             kf = sk.last_kernel_ms() if timed else None
             kb = None
+            ev = None
             if backward:
+                if timed:
+                    ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                    ev[0].record()
                 if tape:
                     sk.sigkernel_backward_tape(tape_buf[0], Wt, Xt, Yt, compute=compute, time_kernel=timed, **opts)
                 else:
                     sk.sigkernel_backward(Wt, Xt, Yt, compute=compute, time_kernel=timed, **opts)
                 kb = sk.last_kernel_ms() if timed else None
-            return kf, kb
+                if timed:
+                    ev[1].record()
+            return kf, kb, ev
 
         for _ in range(warmup):
             step(False)
         torch.cuda.synchronize()
         if dist is not None:
             dist.barrier()
-        step_ms, kf_ms, kb_ms = [], [], []
+        step_ms, kf_ms, kb_ms, bc_ms = [], [], [], []
         t_wall = time.perf_counter()
         for _ in range(steps):
             flush.zero_()
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record()
-            kf, kb = step(True)
+            kf, kb, ev = step(True)
             e1.record()
             e1.synchronize()
             step_ms.append(e0.elapsed_time(e1))
+            if ev is not None:
+                bc_ms.append(ev[0].elapsed_time(ev[1]))
             kf_ms.append(kf)
             if kb is not None:
                 kb_ms.append(kb)
@@ -277,11 +298,12 @@ def main():
         wall = time.perf_counter() - t_wall
         if dist is not None:
             dist.barrier()
+        run.backward_call_ms = bc_ms
         return step_ms, kf_ms, kb_ms, wall
 
     line = {}
     fpc = flops_per_cell(DEGREE, D)
-    bpc = bwd_flops_per_cell(DEGREE, D)
+    bpc = tape_adjoint_flops_per_cell(DEGREE)
     peak = SM_COUNT * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
     import oracle
     rng = np.random.default_rng(0)
@@ -303,6 +325,7 @@ def main():
     status = sk.device_status()
     kf = statistics.mean(kf_ms)
     kb = statistics.mean(kb_ms)
+    bcall = statistics.mean(run.backward_call_ms) if run.backward_call_ms else None
     ach_b = bpc * cells / (kb / 1e3) / 1e12
     ach_f = fpc * cells / (kf / 1e3) / 1e12
     ref = oracle.pairs(list(X), list(Y), pa, pb, "approx", DEGREE)
@@ -313,7 +336,8 @@ def main():
         "value": value, "unit": "cell-updates/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32", "data": "synthetic",
-        "config": {"workload": f"gram{nx}: X, Y = {nx} Brownian paths each, 257 points, d=8, N(0,1/256) increments; "
+        "config": {"workload": f"gram{nx}: X, Y = {nx} Brownian paths each, {npts} points, d=8, N(0,1/{npts - 1}) "
+                               "increments; "
                                "step = forward Gram + adjoint for a seeded upstream gradient",
                    "scheme": "polynomial approximation", "degree": DEGREE, "dyadic": 0,
                    "cells_per_step": cells, "pairs_per_step": nx * nx,
@@ -321,7 +345,7 @@ def main():
                    "tape_gb": round(tape_buf[0].numel() / 1e9, 2),
                    "parallelism": f"weak scaling, one independent {nx}x{nx} Gram per GPU ({world} GPUs)"},
         "roofline": {"bound": "alu", "achieved": ach_b, "peak": peak, "unit": "TFLOP/s", "frac": ach_b / peak,
-                     "traffic": None, "kernel": "bwd_tape_kernel<float,6,8> (adjoint wavefront from the tape)",
+                     "traffic": None, "kernel": "bwd_tape_kernel<float,6> (adjoint wavefront from the tape)",
                      "kernel_ms": kb,
                      "flops_per_cell": bpc,
                      "peak_source": "152 SMs x 128 FP32 lanes x 2 FLOP x 2070 MHz (derived, nominal clocks)"},
@@ -329,7 +353,11 @@ def main():
                            "achieved_tflops": ach_f,
                            "frac": ach_f / peak, "flops_per_cell": fpc,
                            "cell_updates_per_s": cells / (kf / 1e3)},
-        "gpu_launches": 8 * args.steps,  # forward: 2 increments + wavefront; adjoint: 2 increments + adjoint + 2 gradient conversions
+        "backward_call": {"ms": bcall, "adjoint_kernel_ms": kb,
+                          "rest_ms": (bcall - kb) if bcall is not None else None,
+                          "rest": "increments, dk/dM contraction kernel, gradient conversions"},
+        # forward: 2 increments + wavefront; adjoint: 2 increments + adjoint + contraction + 2 gradient conversions
+        "gpu_launches": 9 * args.steps,
         "clocks": clocks, "device_status": status, "wall_s_timed_region": wall,
     })
 
@@ -361,8 +389,8 @@ def main():
         Yh = torch.tensor(Y).pin_memory()
         Wh = Wt.cpu().pin_memory()
         Gh = torch.empty(nx, nx, dtype=torch.float64).pin_memory()
-        gXh = torch.empty(nx * L, D, dtype=torch.float64).pin_memory()
-        gYh = torch.empty(nx * L, D, dtype=torch.float64).pin_memory()
+        gXh = torch.empty(nx * npts, D, dtype=torch.float64).pin_memory()
+        gYh = torch.empty(nx * npts, D, dtype=torch.float64).pin_memory()
         ws = sk.gram_workspace(Xt, Yt, scheme="approx", degree=DEGREE, compute="f32")
         Wd = torch.empty_like(Wt)
         e2e_ms = []

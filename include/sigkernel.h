@@ -179,15 +179,18 @@ int sigkernel_backward(const sk_paths* X, const sk_paths* Y, int32_t d, int32_t 
  * Forward tape (approximation scheme only).  sigkernel_forward_tape computes the same results as
  * sigkernel_pairs / sigkernel_gram (Gram mode when pair_a is NULL; `out` is then [X->count][Y->count]
  * and SK_FLAG_SYMMETRIC applies) and also records, in the caller's `tape`, every cell's inputs
- * (the two incoming edge coefficient vectors and their exponent) and the exponent of each k_hat.
- * sigkernel_backward_tape then runs the adjoint from the tape without recomputing the forward
- * sweep.  Both calls must use the same X, Y, pair list, options and path contents.
+ * (the two incoming edge coefficient vectors, their exponent and the cell's M) and the exponent
+ * of each k_hat.  sigkernel_backward_tape then runs the adjoint from the tape without recomputing
+ * the forward sweep; it writes every cell's dL/dM into its workspace and contracts that with the
+ * increments in a second kernel.  Both calls must use the same X, Y, pair list, options and path
+ * contents.
  *   tape        device buffer, 256-byte aligned, caller-owned, >= sigkernel_tape_size() bytes;
  *               the size grows as npairs x (max_len << lambda)^2 x ~64 B (FP32) or ~128 B (FP64):
  *               about 70 GB for 16,384 pairs of 257-point paths in FP32.
  *   sigkernel_tape_size: `npairs` = -1 for a Gram; writes the bytes and returns SK_OK or SK_ERR_*.
- * The backward's workspace is sized with SK_OP_BACKWARD_TAPE.  Other arguments and the gradient
- * semantics are those of sigkernel_backward.
+ * The backward's workspace is sized with SK_OP_BACKWARD_TAPE; it holds one element per cell (4 B
+ * in FP32, 8 B in FP64; about 4.4 GB for the Gram above).  Other arguments and the gradient
+ * semantics are those of sigkernel_backward; any d <= 64 is supported.
  */
 int sigkernel_tape_size(const sk_paths* X, const sk_paths* Y, int32_t d, int64_t npairs,
                         const sk_options* opt, size_t* bytes);

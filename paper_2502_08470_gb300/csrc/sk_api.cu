@@ -252,6 +252,7 @@ int launch_increments(const sk_paths* S, int32_t d, int32_t dtype, int inc_mode,
 // fixed-stride block per work item of nsteps_max x 32 lanes x tape_row<T>(N) elements.
 struct TapePlan {
     size_t ek_bytes, stride, total;
+    int64_t nsteps;  // warp steps of the longest item
 };
 
 int plan_tape(const sk_paths* X, const sk_paths* Y, const sk_options* o, int T, int64_t npairs, TapePlan& t) {
@@ -261,6 +262,7 @@ int plan_tape(const sk_paths* X, const sk_paths* Y, const sk_options* o, int T, 
     const int64_t nsteps = ((rows + 31) / 32 - 1) * std::max<int64_t>(cols, 32) + 31 + cols;
     const int row = T ? tape_row<float>(o->degree) : tape_row<double>(o->degree);
     const int esize = T ? 4 : 8;
+    t.nsteps = nsteps;
     t.ek_bytes = align256(static_cast<size_t>(npairs) * sizeof(int));
     t.stride = align256(static_cast<size_t>(nsteps) * 32 * row * esize);
     t.total = t.ek_bytes + static_cast<size_t>(npairs) * t.stride;
@@ -273,7 +275,7 @@ int run_forward(const sk_paths* X, const sk_paths* Y, int32_t d, int32_t dtype, 
     Plan p;
     int rc = plan_forward(X, Y, d, dtype, o, mode, npairs, p);
     if (rc != SK_OK) return rc;
-    TapePlan tp{0, 0, 0};
+    TapePlan tp{0, 0, 0, 0};
     if (tape) {
         if ((rc = plan_tape(X, Y, o, p.T, npairs, tp)) != SK_OK) return rc;
         if (tape_bytes < tp.total) return fail(SK_ERR_WORKSPACE, "tape %zu bytes < %zu required", tape_bytes, tp.total);
@@ -570,9 +572,10 @@ struct TapeBwdPlan {
     Plan f;
     TapePlan t;
     const void* kern;
-    int smem_bytes;
-    int64_t cols_max, off_rbuf, off_rexp, slot_bytes;
-    size_t off_gincx, off_gincy, off_scratch, total;
+    const void* ckern;
+    int smem_bytes, cblocks, csmem;
+    int64_t cols_max, off_rbuf, off_rexp, slot_bytes, mb_stride, acc_bytes;
+    size_t off_gincx, off_gincy, off_scratch, off_mbuf, total;
 };
 
 int plan_backward_tape(const sk_paths* X, const sk_paths* Y, int32_t d, int32_t dtype, const sk_options* o, int mode,
@@ -581,15 +584,11 @@ int plan_backward_tape(const sk_paths* X, const sk_paths* Y, int32_t d, int32_t 
     if (rc != SK_OK) return rc;
     const Plan& p = b.f;
     if ((rc = plan_tape(X, Y, o, p.T, npairs, b.t)) != SK_OK) return rc;
-    const int dmax = p.dpad <= 8 ? 8 : (p.dpad <= 32 ? 32 : 0);
-    if (!dmax) return fail(SK_ERR_UNSUPPORTED, "the adjoint supports d <= 32");
-    b.kern = p.T ? bwd_tape_ptr_f32(o->degree, dmax) : bwd_tape_ptr_f64(o->degree, dmax);
+    b.kern = p.T ? bwd_tape_ptr_f32(o->degree) : bwd_tape_ptr_f64(o->degree);
     if (!b.kern) return fail(SK_ERR_UNSUPPORTED, "no adjoint kernel for order %d", o->degree);
-    {
-        const int step_bytes = 32 * (p.T ? tape_row<float>(o->degree) * 4 : tape_row<double>(o->degree) * 8);
-        const int xacc = p.T ? bwd_xacc_bytes<float>(p.dpad) : bwd_xacc_bytes<double>(p.dpad);
-        b.smem_bytes = kFwdWarps * (kTapeRing * step_bytes + kTapeRing * 8 + xacc);
-    }
+    b.ckern = p.T ? bwd_contract_ptr_f32() : bwd_contract_ptr_f64();
+    const int step_bytes = 32 * (p.T ? tape_row<float>(o->degree) * 4 : tape_row<double>(o->degree) * 8);
+    b.smem_bytes = kFwdWarps * (kTapeRing * step_bytes + kTapeRing * 8);
     const int esize = p.T ? 4 : 8, N = o->degree;
     b.cols_max = std::max<int64_t>(Y->max_len << o->dyadic, 1);
     b.off_rbuf = 0;
@@ -597,12 +596,25 @@ int plan_backward_tape(const sk_paths* X, const sk_paths* Y, int32_t d, int32_t 
     b.off_rexp = off;
     off += static_cast<int64_t>(align256(b.cols_max * 4));
     b.slot_bytes = off;
-    int dev = 0, sms = 0, per_sm = 0;
+    // dk/dM buffer: the tape's [step][lane] grid of one element per cell
+    // (plus the rows past an item's last step that the contraction's tiles may read)
+    b.mb_stride = static_cast<int64_t>(align256(static_cast<size_t>(b.t.nsteps + kContractSlack) * 32 * esize));
+    // contraction accumulators: (lx + ly) increments x kContractC coordinates, when they fit
+    const int64_t acc_need = (std::max<int64_t>(X->max_len, 1) + std::max<int64_t>(Y->max_len, 1)) * kContractC * esize;
+    b.acc_bytes = acc_need <= (64 << 10) ? acc_need : 0;
+    b.csmem = kContractWarps * (p.T ? contract_warp_bytes<float>() : contract_warp_bytes<double>()) +
+              static_cast<int>(b.acc_bytes);
+    int dev = 0, sms = 0, per_sm = 0, cper_sm = 0;
     SK_CUDA(cudaGetDevice(&dev));
     SK_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     SK_CUDA(cudaFuncSetAttribute(b.kern, cudaFuncAttributeMaxDynamicSharedMemorySize, b.smem_bytes));
     SK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, b.kern, p.threads, b.smem_bytes));
     if (per_sm < 1) return fail(SK_ERR_UNSUPPORTED, "adjoint kernel does not fit an SM");
+    SK_CUDA(cudaFuncSetAttribute(b.ckern, cudaFuncAttributeMaxDynamicSharedMemorySize, b.csmem));
+    SK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&cper_sm, b.ckern, kContractWarps * 32,
+                                                          static_cast<size_t>(b.csmem)));
+    if (cper_sm < 1) return fail(SK_ERR_UNSUPPORTED, "contraction kernel does not fit an SM");
+    b.cblocks = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(npairs, static_cast<int64_t>(sms) * cper_sm)));
     const int64_t want = (npairs + kFwdWarps - 1) / kFwdWarps;
     b.f.blocks = static_cast<int>(std::max<int64_t>(1, std::min(want, static_cast<int64_t>(sms) * per_sm)));
     size_t o2 = p.off_scratch;
@@ -612,6 +624,9 @@ int plan_backward_tape(const sk_paths* X, const sk_paths* Y, int32_t d, int32_t 
     if (!p.same_xy) o2 += align256(static_cast<size_t>(Y->rows_total) * p.dpad * sizeof(double));
     b.off_scratch = o2;
     o2 += static_cast<size_t>(b.f.blocks) * kFwdWarps * static_cast<size_t>(b.slot_bytes);
+    o2 = align256(o2);
+    b.off_mbuf = o2;
+    o2 += static_cast<size_t>(npairs) * static_cast<size_t>(b.mb_stride);
     b.total = o2 + 256;
     return SK_OK;
 }
@@ -679,6 +694,9 @@ int run_backward_tape(const sk_paths* X, const sk_paths* Y, int32_t d, int32_t d
     B.cols_max = b.cols_max;
     B.off_rbuf = b.off_rbuf;
     B.off_rexp = b.off_rexp;
+    B.mbuf = base + b.off_mbuf;
+    B.mb_stride = b.mb_stride;
+    B.acc_bytes = b.acc_bytes;
     SK_CUDA(cudaMemsetAsync(base + p.off_queue, 0, 256, st));
     if (!(o->flags & SK_FLAG_NO_SORT) && npairs > 1) {
         unsigned int* hist = reinterpret_cast<unsigned int*>(base + p.off_hist);
@@ -703,6 +721,8 @@ int run_backward_tape(const sk_paths* X, const sk_paths* Y, int32_t d, int32_t d
         SK_CUDA(cudaEventRecord(t_ev1, st));
         t_timed = true;
     }
+    SK_CUDA(cudaLaunchKernel(b.ckern, dim3(b.cblocks), dim3(kContractWarps * 32), args,
+                             static_cast<size_t>(b.csmem), st));
     if ((rc = convert_grad(X, d, p.dpad, inc_mode, gincX, gX, st)) != SK_OK) return rc;
     if (!p.same_xy && (rc = convert_grad(Y, d, p.dpad, inc_mode, gincY, gY, st)) != SK_OK) return rc;
     if (own) SK_CUDA(cudaFreeAsync(ws, st));

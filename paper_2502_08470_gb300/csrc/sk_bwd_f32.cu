@@ -1,5 +1,5 @@
 // Instantiations of the approximation-scheme adjoint wavefronts (float cell updates): the
-// checkpointing form and the tape-driven form.
+// checkpointing form, the tape-driven form and the dk/dM contraction.
 #include "sk_bwd_poly.cuh"
 #include "sk_dispatch.h"
 
@@ -35,35 +35,23 @@ const void* bwd_approx_ptr_f32(int N, int dmax, int* stack_bytes) {
     return nullptr;
 }
 
-const void* bwd_tape_ptr_f32(int N, int dmax) {
-    if (dmax == 8) switch (N) {
-        case 2: return reinterpret_cast<const void*>(&bwd_tape_kernel<float, 2, 8>);
-        case 3: return reinterpret_cast<const void*>(&bwd_tape_kernel<float, 3, 8>);
-        case 4: return reinterpret_cast<const void*>(&bwd_tape_kernel<float, 4, 8>);
-        case 5: return reinterpret_cast<const void*>(&bwd_tape_kernel<float, 5, 8>);
-        case 6: return reinterpret_cast<const void*>(&bwd_tape_kernel<float, 6, 8>);
-        case 7: return reinterpret_cast<const void*>(&bwd_tape_kernel<float, 7, 8>);
-        case 8: return reinterpret_cast<const void*>(&bwd_tape_kernel<float, 8, 8>);
-        case 9: return reinterpret_cast<const void*>(&bwd_tape_kernel<float, 9, 8>);
-        case 10: return reinterpret_cast<const void*>(&bwd_tape_kernel<float, 10, 8>);
-        case 12: return reinterpret_cast<const void*>(&bwd_tape_kernel<float, 12, 8>);
-        default: break;
+const void* bwd_tape_ptr_f32(int N) {
+    switch (N) {
+        case 2: return reinterpret_cast<const void*>(&bwd_tape_kernel<float, 2>);
+        case 3: return reinterpret_cast<const void*>(&bwd_tape_kernel<float, 3>);
+        case 4: return reinterpret_cast<const void*>(&bwd_tape_kernel<float, 4>);
+        case 5: return reinterpret_cast<const void*>(&bwd_tape_kernel<float, 5>);
+        case 6: return reinterpret_cast<const void*>(&bwd_tape_kernel<float, 6>);
+        case 7: return reinterpret_cast<const void*>(&bwd_tape_kernel<float, 7>);
+        case 8: return reinterpret_cast<const void*>(&bwd_tape_kernel<float, 8>);
+        case 9: return reinterpret_cast<const void*>(&bwd_tape_kernel<float, 9>);
+        case 10: return reinterpret_cast<const void*>(&bwd_tape_kernel<float, 10>);
+        case 12: return reinterpret_cast<const void*>(&bwd_tape_kernel<float, 12>);
+        default: return nullptr;
     }
-    if (dmax == 32) switch (N) {
-        case 2: return reinterpret_cast<const void*>(&bwd_tape_kernel<float, 2, 32>);
-        case 3: return reinterpret_cast<const void*>(&bwd_tape_kernel<float, 3, 32>);
-        case 4: return reinterpret_cast<const void*>(&bwd_tape_kernel<float, 4, 32>);
-        case 5: return reinterpret_cast<const void*>(&bwd_tape_kernel<float, 5, 32>);
-        case 6: return reinterpret_cast<const void*>(&bwd_tape_kernel<float, 6, 32>);
-        case 7: return reinterpret_cast<const void*>(&bwd_tape_kernel<float, 7, 32>);
-        case 8: return reinterpret_cast<const void*>(&bwd_tape_kernel<float, 8, 32>);
-        case 9: return reinterpret_cast<const void*>(&bwd_tape_kernel<float, 9, 32>);
-        case 10: return reinterpret_cast<const void*>(&bwd_tape_kernel<float, 10, 32>);
-        case 12: return reinterpret_cast<const void*>(&bwd_tape_kernel<float, 12, 32>);
-        default: break;
-    }
-    return nullptr;
 }
+
+const void* bwd_contract_ptr_f32() { return reinterpret_cast<const void*>(&bwd_contract_kernel<float>); }
 
 int bwd_segment_f32() { return 8; }
 

@@ -1,5 +1,5 @@
 // Instantiations of the approximation-scheme adjoint wavefronts (double cell updates): the
-// checkpointing form and the tape-driven form.
+// checkpointing form, the tape-driven form and the dk/dM contraction.
 #include "sk_bwd_poly.cuh"
 #include "sk_dispatch.h"
 
@@ -35,35 +35,23 @@ const void* bwd_approx_ptr_f64(int N, int dmax, int* stack_bytes) {
     return nullptr;
 }
 
-const void* bwd_tape_ptr_f64(int N, int dmax) {
-    if (dmax == 8) switch (N) {
-        case 2: return reinterpret_cast<const void*>(&bwd_tape_kernel<double, 2, 8>);
-        case 3: return reinterpret_cast<const void*>(&bwd_tape_kernel<double, 3, 8>);
-        case 4: return reinterpret_cast<const void*>(&bwd_tape_kernel<double, 4, 8>);
-        case 5: return reinterpret_cast<const void*>(&bwd_tape_kernel<double, 5, 8>);
-        case 6: return reinterpret_cast<const void*>(&bwd_tape_kernel<double, 6, 8>);
-        case 7: return reinterpret_cast<const void*>(&bwd_tape_kernel<double, 7, 8>);
-        case 8: return reinterpret_cast<const void*>(&bwd_tape_kernel<double, 8, 8>);
-        case 9: return reinterpret_cast<const void*>(&bwd_tape_kernel<double, 9, 8>);
-        case 10: return reinterpret_cast<const void*>(&bwd_tape_kernel<double, 10, 8>);
-        case 12: return reinterpret_cast<const void*>(&bwd_tape_kernel<double, 12, 8>);
-        default: break;
+const void* bwd_tape_ptr_f64(int N) {
+    switch (N) {
+        case 2: return reinterpret_cast<const void*>(&bwd_tape_kernel<double, 2>);
+        case 3: return reinterpret_cast<const void*>(&bwd_tape_kernel<double, 3>);
+        case 4: return reinterpret_cast<const void*>(&bwd_tape_kernel<double, 4>);
+        case 5: return reinterpret_cast<const void*>(&bwd_tape_kernel<double, 5>);
+        case 6: return reinterpret_cast<const void*>(&bwd_tape_kernel<double, 6>);
+        case 7: return reinterpret_cast<const void*>(&bwd_tape_kernel<double, 7>);
+        case 8: return reinterpret_cast<const void*>(&bwd_tape_kernel<double, 8>);
+        case 9: return reinterpret_cast<const void*>(&bwd_tape_kernel<double, 9>);
+        case 10: return reinterpret_cast<const void*>(&bwd_tape_kernel<double, 10>);
+        case 12: return reinterpret_cast<const void*>(&bwd_tape_kernel<double, 12>);
+        default: return nullptr;
     }
-    if (dmax == 32) switch (N) {
-        case 2: return reinterpret_cast<const void*>(&bwd_tape_kernel<double, 2, 32>);
-        case 3: return reinterpret_cast<const void*>(&bwd_tape_kernel<double, 3, 32>);
-        case 4: return reinterpret_cast<const void*>(&bwd_tape_kernel<double, 4, 32>);
-        case 5: return reinterpret_cast<const void*>(&bwd_tape_kernel<double, 5, 32>);
-        case 6: return reinterpret_cast<const void*>(&bwd_tape_kernel<double, 6, 32>);
-        case 7: return reinterpret_cast<const void*>(&bwd_tape_kernel<double, 7, 32>);
-        case 8: return reinterpret_cast<const void*>(&bwd_tape_kernel<double, 8, 32>);
-        case 9: return reinterpret_cast<const void*>(&bwd_tape_kernel<double, 9, 32>);
-        case 10: return reinterpret_cast<const void*>(&bwd_tape_kernel<double, 10, 32>);
-        case 12: return reinterpret_cast<const void*>(&bwd_tape_kernel<double, 12, 32>);
-        default: break;
-    }
-    return nullptr;
 }
+
+const void* bwd_contract_ptr_f64() { return reinterpret_cast<const void*>(&bwd_contract_kernel<double>); }
 
 int bwd_segment_f64() { return 4; }
 

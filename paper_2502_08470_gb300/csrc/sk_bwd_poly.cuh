@@ -47,6 +47,9 @@ struct BwdParams {
     int64_t strips_max;       // strips of the longest x path
     int64_t seg_max;          // K-step segments of the longest pair
     int64_t off_fbuf, off_fexp, off_rbuf, off_rexp, off_ybar;  // byte offsets inside a warp slot
+    void* mbuf;               // tape adjoint: per-item dk/dM, [step][lane] of T
+    int64_t mb_stride;        // bytes per item of mbuf
+    int64_t acc_bytes;        // contraction: shared-memory accumulator bytes per block
 };
 
 template <typename T>
@@ -555,27 +558,39 @@ __global__ void __launch_bounds__(kFwdWarps * 32, (bwd_min_blocks<T, N, K>()))
 
 // ---------------------------------------------------------------------------------------------
 // Adjoint from a forward tape.  The forward kernel recorded, for every warp step, the 32 lanes'
-// cell inputs (a, b, exponent; laid out [vector][lane]) and the exponent of k_hat; this kernel
+// cell inputs (a, b, exponent, M; laid out [vector][lane]) and the exponent of k_hat; this kernel
 // walks the same steps backward (the reverse of the forward schedule, strips overlapping exactly
-// as there) and needs no forward recomputation.  The steps stream into a ring of kTapeRing
-// shared-memory slots per warp with bulk copies issued kTapeRing steps ahead by lane 0, each slot
-// completing on its own mbarrier.
+// as there) and needs neither forward recomputation nor the increments.  The steps stream into a
+// ring of kTapeRing shared-memory slots per warp with bulk copies issued kTapeRing steps ahead by
+// lane 0, each slot completing on its own mbarrier.  Each cell's dk/dM (relative to 2^ek, with
+// the 4^-lambda of the sub-cell M folded in) is written to a per-item buffer of 32-element rows,
+// one per step, lane r's value at position (r + step) mod 32 (zero where a lane is idle); the
+// skew lets bwd_contract_kernel read both rows and columns of a cell tile without bank
+// conflicts.  That kernel turns the buffer into dk/dx and dk/dy.
 // ---------------------------------------------------------------------------------------------
-constexpr int kTapeRing = 8;
+constexpr int kTapeRing = 4;
 
-template <typename T, int N, int DMAX>
-__host__ __device__ constexpr int bwd_tape_min_blocks() {
-    return sizeof(T) == 8 ? 1 : 3;
-}
-
-// Shared memory of one warp for the tape adjoint: the ring, its mbarriers, dk/dx accumulators.
 template <typename T, int N>
-__host__ __device__ constexpr int bwd_tape_warp_bytes(int dpad) {
-    return kTapeRing * fwd_tape_step_bytes<T, N>() + kTapeRing * 8 + bwd_xacc_bytes<T>(dpad);
+__host__ __device__ constexpr int bwd_tape_min_blocks() {
+    return sizeof(T) == 8 ? 2 : 4;
 }
 
-template <typename T, int N, int DMAX>
-__global__ void __launch_bounds__(kFwdWarps * 32, (bwd_tape_min_blocks<T, N, DMAX>()))
+// Shared memory of one warp for the tape adjoint: the ring and its mbarriers.
+template <typename T, int N>
+__host__ __device__ constexpr int bwd_tape_warp_bytes() {
+    return kTapeRing * fwd_tape_step_bytes<T, N>() + kTapeRing * 8;
+}
+
+// Gradient seed and exponent of k_hat for item `item` (shared by the adjoint and the contraction).
+__device__ __forceinline__ double item_gbar(const BwdParams& B, int64_t item, const PairDesc& P) {
+    const Launch& L = B.L;
+    if (L.mode == kPairsList) return B.gout[item];
+    if (L.mode == kGramFull) return B.gout[P.a * L.ldo + P.b];
+    return B.gout[P.a * L.ldo + P.b] + (P.a != P.b ? B.gout[P.b * L.ldo + P.a] : 0.0);
+}
+
+template <typename T, int N>
+__global__ void __launch_bounds__(kFwdWarps * 32, (bwd_tape_min_blocks<T, N>()))
     bwd_tape_kernel(BwdParams B) {
     constexpr bool kRescale = std::is_same<T, float>::value;
     using V = typename Vec<T>::type;
@@ -588,15 +603,10 @@ __global__ void __launch_bounds__(kFwdWarps * 32, (bwd_tape_min_blocks<T, N, DMA
     char* base = static_cast<char*>(L.scratch) + slot * L.scratch_stride;
     T* rbuf = reinterpret_cast<T*>(base + B.off_rbuf);          // [col][N+1]
     int* rexp = reinterpret_cast<int*>(base + B.off_rexp);      // [col]
-    const int dpad = L.dpad;
     constexpr int kStepBytes = fwd_tape_step_bytes<T, N>();
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    unsigned char* wsm = smem_raw + wib * bwd_tape_warp_bytes<T, N>(dpad);
-    unsigned char* ring = wsm;
-    uint64_t* bars = reinterpret_cast<uint64_t*>(wsm + kTapeRing * kStepBytes);
-    T* xacc = reinterpret_cast<T*>(wsm + kTapeRing * kStepBytes + kTapeRing * 8) + lane * (dpad + 1);
-    const T* __restrict__ incX = static_cast<const T*>(L.X.inc);
-    const T* __restrict__ incY = static_cast<const T*>(L.Y.inc);
+    unsigned char* ring = smem_raw + wib * bwd_tape_warp_bytes<T, N>();
+    uint64_t* bars = reinterpret_cast<uint64_t*>(ring + kTapeRing * kStepBytes);
     if (lane == 0) {
         for (int k = 0; k < kTapeRing; ++k) mbar_init(bars + k, 1);
         fence_mbar_init();
@@ -614,11 +624,7 @@ __global__ void __launch_bounds__(kFwdWarps * 32, (bwd_tape_min_blocks<T, N, DMA
             continue;
         }
         if (P.lx == 0 || P.ly == 0) continue;
-        double gbar;
-        if (L.mode == kPairsList) gbar = B.gout[item];
-        else if (L.mode == kGramFull) gbar = B.gout[P.a * L.ldo + P.b];
-        else gbar = B.gout[P.a * L.ldo + P.b] + (P.a != P.b ? B.gout[P.b * L.ldo + P.a] : 0.0);
-        if (gbar == 0.0) continue;
+        if (item_gbar(B, item, P) == 0.0) continue;  // bwd_contract_kernel skips it too
 
         const int lam = L.lam;
         const int rows = static_cast<int>(P.lx << lam);
@@ -627,20 +633,24 @@ __global__ void __launch_bounds__(kFwdWarps * 32, (bwd_tape_min_blocks<T, N, DMA
         const int nstrips = (rows + 31) >> 5;
         const int last_lane = (rows - 1) - ((nstrips - 1) << 5);
         const int nsteps = (nstrips - 1) * period + last_lane + cols;
-        const T* xbase = incX + P.xs * dpad;
-        const T* ybase = incY + P.ys * dpad;
         const int ek = L.tape_ek[item];
-        const double gscale = gbar * pow2d(ek);
         const char* tape = static_cast<const char*>(L.tape) + item * L.tape_stride;
+        T* mout = reinterpret_cast<T*>(static_cast<char*>(B.mbuf) + item * B.mb_stride);
 
+        // Edge conditions of the reverse sweep.  A lane's right-edge input (no cell to the right)
+        // is zero: gra starts at zero and is cleared whenever the lane moves down a strip.  The top
+        // row's upper input is zero: it comes from a lane beyond the last row, never active in
+        // this item, whose gbo stays zero (lane 31 is handled where it reads the hand-off).  The
+        // corner cell (rows-1, cols-1), run by lane last_lane at the first reverse step, is
+        // seeded from the endpoint average: both inputs are 1/(2 n!).
         T gra[N + 1], gbo[N + 1];
         int gea = kZeroExp, gbe = kZeroExp;
-        T ysum[DMAX];
 #pragma unroll
-        for (int n = 0; n <= N; ++n) { gra[n] = T(0); gbo[n] = T(0); }
-#pragma unroll
-        for (int c = 0; c < DMAX; ++c) ysum[c] = T(0);
-        for (int c = 0; c < dpad; ++c) xacc[c] = T(0);
+        for (int n = 0; n <= N; ++n) {
+            gra[n] = lane == last_lane ? static_cast<T>(0.5 * cx_rfact(n)) : T(0);
+            gbo[n] = T(0);
+        }
+        if (lane == last_lane) gea = 0;
 
         // fill the ring with the last kTapeRing steps (step t lives in slot t % kTapeRing)
         if (lane == 0) {
@@ -664,11 +674,28 @@ __global__ void __launch_bounds__(kFwdWarps * 32, (bwd_tape_min_blocks<T, N, DMA
                 break;
             }
             parity ^= 1u << sl;
-            T cur[TR];
+            T fa[N + 1], fb[N + 1];
+            int ef;
+            T M;
             {
                 const V* src = reinterpret_cast<const V*>(ring + sl * kStepBytes);
 #pragma unroll
-                for (int v = 0; v < TR / W; ++v) reinterpret_cast<V*>(cur)[v] = src[v * 32 + lane];
+                for (int v = 0; v < TR / W; ++v) {
+                    const V t = src[v * 32 + lane];
+                    const T* tp = reinterpret_cast<const T*>(&t);
+#pragma unroll
+                    for (int w = 0; w < W; ++w) {
+                        const int q = v * W + w;
+                        if (q <= N) fa[q] = tp[w];
+                        else if (q <= 2 * N + 1) fb[q - N - 1] = tp[w];
+                        else if (q == 2 * N + 2) {
+                            if constexpr (std::is_same<T, float>::value) ef = __float_as_int(tp[w]);
+                            else ef = static_cast<int>(__double_as_longlong(tp[w]));
+                        } else if (q == 2 * N + 3) {
+                            M = tp[w];
+                        }
+                    }
+                }
             }
             __syncwarp();  // every lane has its row: the slot can be refilled
             if (lane == 0 && step - kTapeRing >= 0) {
@@ -680,50 +707,34 @@ __global__ void __launch_bounds__(kFwdWarps * 32, (bwd_tape_min_blocks<T, N, DMA
 #pragma unroll
             for (int n = 0; n <= N; ++n) gb_in[n] = __shfl_down_sync(kFull, gbo[n], 1);
             int gbe_in = __shfl_down_sync(kFull, gbe, 1);
-#pragma unroll
-            for (int c = 0; c < DMAX; ++c) ysum[c] = __shfl_down_sync(kFull, ysum[c], 1);
             const int row = (s << 5) + lane;
             const bool active = s >= 0 && jj < cols && row < rows;
+            T mrel = T(0);
             if (active) {
-                if (row == rows - 1) {             // no row above: the top edge is final
+                if (lane == 31) {                  // from lane 0 of the strip above, if any
+                    if (row == rows - 1) {
 #pragma unroll
-                    for (int n = 0; n <= N; ++n) gb_in[n] = T(0);
-                    gbe_in = kZeroExp;
-                } else if (lane == 31) {           // from lane 0 of the strip above
-                    const T* src = rbuf + static_cast<int64_t>(jj) * (N + 1);
+                        for (int n = 0; n <= N; ++n) gb_in[n] = T(0);
+                        gbe_in = kZeroExp;
+                    } else {
+                        const T* src = rbuf + static_cast<int64_t>(jj) * (N + 1);
 #pragma unroll
-                    for (int n = 0; n <= N; ++n) gb_in[n] = src[n];
-                    gbe_in = kRescale ? rexp[jj] : 0;
-                }
-                if (row == rows - 1 || lane == 31) {
-#pragma unroll
-                    for (int c = 0; c < DMAX; ++c) ysum[c] = T(0);
-                }
-                T ga_in[N + 1];
-                int gae_in = gea;
-#pragma unroll
-                for (int n = 0; n <= N; ++n) ga_in[n] = gra[n];
-                if (jj == cols - 1) {              // right edge of the grid
-#pragma unroll
-                    for (int n = 0; n <= N; ++n) ga_in[n] = T(0);
-                    gae_in = kZeroExp;
-                }
-                if (row == rows - 1 && jj == cols - 1) {  // seed from the endpoint average
-#pragma unroll
-                    for (int n = 0; n <= N; ++n) {
-                        ga_in[n] = static_cast<T>(0.5 * cx_rfact(n));
-                        gb_in[n] = ga_in[n];
+                        for (int n = 0; n <= N; ++n) gb_in[n] = src[n];
+                        gbe_in = kRescale ? rexp[jj] : 0;
                     }
-                    gae_in = 0;
+                }
+                if (step == nsteps - 1) {          // warp-uniform: the corner cell's upper input
+#pragma unroll
+                    for (int n = 0; n <= N; ++n) gb_in[n] = static_cast<T>(0.5 * cx_rfact(n));
                     gbe_in = 0;
                 }
                 int eg = 0;
                 if (kRescale) {
-                    eg = max(gae_in, gbe_in);
-                    if (gae_in != eg) {
-                        const T f = pow2c<T>(gae_in - eg);
+                    eg = max(gea, gbe_in);
+                    if (gea != eg) {
+                        const T f = pow2c<T>(gea - eg);
 #pragma unroll
-                        for (int n = 0; n <= N; ++n) ga_in[n] *= f;
+                        for (int n = 0; n <= N; ++n) gra[n] *= f;
                     }
                     if (gbe_in != eg) {
                         const T f = pow2c<T>(gbe_in - eg);
@@ -731,50 +742,22 @@ __global__ void __launch_bounds__(kFwdWarps * 32, (bwd_tape_min_blocks<T, N, DMA
                         for (int n = 0; n <= N; ++n) gb_in[n] *= f;
                     }
                 }
-                T fa[N + 1], fb[N + 1], e[N + 1];
-                int ef;
-#pragma unroll
-                for (int n = 0; n <= N; ++n) {
-                    fa[n] = cur[n];
-                    fb[n] = cur[N + 1 + n];
-                }
-                if constexpr (std::is_same<T, float>::value) ef = __float_as_int(cur[2 * N + 2]);
-                else ef = static_cast<int>(__double_as_longlong(cur[2 * N + 2]));
                 unit_scale<T, N>(fa, fb, ef);
-                const T* xrow = xbase + static_cast<int64_t>(row >> lam) * dpad;
-                const T* yrow = ybase + static_cast<int64_t>(jj >> lam) * dpad;
-                const T M = row_dot<T>(xrow, yrow, L.nvec) * pow2t<T>(-2 * lam);
+                T e[N + 1];
                 build_exp_series<T, N>(M, L.tau, e);
                 T mbar;
+                T ga_in[N + 1];
+#pragma unroll
+                for (int n = 0; n <= N; ++n) ga_in[n] = gra[n];
                 cell_adjoint<T, N>(fa, fb, e, ga_in, gb_in, gra, gbo, mbar);
-                const T mrel = mbar * pow2c<T>(eg + ef - ek - 2 * lam);
-                {
-                    const V* yv = reinterpret_cast<const V*>(yrow);
-                    const V* xv = reinterpret_cast<const V*>(xrow);
-#pragma unroll
-                    for (int c4 = 0; c4 < DMAX / W; ++c4) {
-                        if (c4 * W < dpad) {
-                            const V yy = __ldg(yv + c4);
-                            const V xx = __ldg(xv + c4);
-                            const T* yp = reinterpret_cast<const T*>(&yy);
-                            const T* xp = reinterpret_cast<const T*>(&xx);
-#pragma unroll
-                            for (int w = 0; w < W; ++w) {
-                                xacc[c4 * W + w] = fma(mrel, yp[w], xacc[c4 * W + w]);
-                                ysum[c4 * W + w] = fma(mrel, xp[w], ysum[c4 * W + w]);
-                            }
-                        }
-                    }
-                }
+                mrel = mbar * pow2c<T>(eg + ef - ek - 2 * lam);
                 gea = eg;
-                if (kRescale) {
+                if (kRescale && (step & 3) == 0) {  // keep the adjoints within [2^-64, 2^64]
                     float mag = 0.f;
 #pragma unroll
                     for (int n = 0; n <= N; ++n)
                         mag = fmaxf(mag, fmaxf(fabsf(static_cast<float>(gra[n])), fabsf(static_cast<float>(gbo[n]))));
-                    if (mag == 0.f) {
-                        gea = kZeroExp;
-                    } else if (mag > 0x1p64f || mag < 0x1p-64f) {
+                    if (mag > 0x1p64f || (mag < 0x1p-64f && mag > 0.f)) {
                         const int sh = mag > 0x1p64f ? -64 : 64;
 #pragma unroll
                         for (int n = 0; n <= N; ++n) { gra[n] *= pow2t<T>(sh); gbo[n] *= pow2t<T>(sh); }
@@ -782,30 +765,21 @@ __global__ void __launch_bounds__(kFwdWarps * 32, (bwd_tape_min_blocks<T, N, DMA
                     }
                 }
                 gbe = gea;
-                if (lane == 0) {
-                    if (s > 0) {  // hand the left-edge adjoint to lane 31 of the strip below
-                        T* dst = rbuf + static_cast<int64_t>(jj) * (N + 1);
+                if (lane == 0 && s > 0) {  // hand the left-edge adjoint to lane 31 of the strip below
+                    T* dst = rbuf + static_cast<int64_t>(jj) * (N + 1);
 #pragma unroll
-                        for (int n = 0; n <= N; ++n) dst[n] = gbo[n];
-                        if (kRescale) rexp[jj] = gbe;
-                    }
-                    double* gy = B.gincY + (P.ys + (jj >> lam)) * dpad;
-#pragma unroll
-                    for (int c = 0; c < DMAX; ++c)
-                        if (c < dpad && ysum[c] != T(0)) atomicAdd(gy + c, static_cast<double>(ysum[c]) * gscale);
-                }
-                if (jj == 0) {  // the row is finished: flush dk/dx of its increment
-                    double* gx = B.gincX + (P.xs + (row >> lam)) * dpad;
-                    for (int c = 0; c < dpad; ++c) {
-                        if (xacc[c] != T(0)) atomicAdd(gx + c, static_cast<double>(xacc[c]) * gscale);
-                        xacc[c] = T(0);
-                    }
+                    for (int n = 0; n <= N; ++n) dst[n] = gbo[n];
+                    if (kRescale) rexp[jj] = gbe;
                 }
             }
+            mout[static_cast<int64_t>(step) * 32 + ((lane + step) & 31)] = mrel;  // skewed row
             __syncwarp();
-            if (s >= 0 && --jj < 0) {
+            if (s >= 0 && --jj < 0) {  // down one strip: the next row starts at the right edge
                 jj = period - 1;
                 --s;
+#pragma unroll
+                for (int n = 0; n <= N; ++n) gra[n] = T(0);
+                gea = kZeroExp;
             }
         }
         if (stuck) {
@@ -820,6 +794,218 @@ __global__ void __launch_bounds__(kFwdWarps * 32, (bwd_tape_min_blocks<T, N, DMA
             break;
         }
         __syncwarp();
+    }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Chain rule through M_ij = <dx_i, dy_j> / 4^lambda (M_ij is the increments' inner product that
+// drives the Goursat PDE of the kernel of piecewise linear paths):
+//   dk/d(dx_i) = sum_j dk/dM_ij dy_j,   dk/d(dy_j) = sum_i dk/dM_ij dx_i,
+// from the dk/dM buffer written by bwd_tape_kernel.  One block per work item (grid-stride), one
+// warp per strip of 32 rows.  A strip is cut into tiles of 32 columns; cell (r, j0 + q) of tile
+// j0 sits at step sP + j0 + r + q, so a tile spans 63 consecutive 32-element rows of the buffer.
+// The warp streams halves of 32 rows (4 KB in FP32) into a three-slot shared-memory ring with
+// cp.async.bulk, one half ahead, and with the buffer's skew (lane r of step t at (r + t) mod 32):
+//   * dk/dx: lane r walks its row (q = 0..31) against the broadcast dy_{j0+q};
+//   * dk/dy: lane q walks its column (r = 0..31) against the broadcast dx_r of the strip,
+// each with at most two-way bank conflicts.  Column sums are added to a shared per-increment
+// accumulator once per tile, row sums once per strip; the accumulators are added to the FP64
+// gradients once per item, scaled by gbar 2^ek (straight to FP64 atomics when they do not fit).
+// Coordinates are taken kContractC at a time.
+// ---------------------------------------------------------------------------------------------
+constexpr int kContractC = 8;
+constexpr int kContractWarps = 4;
+constexpr int kContractSlack = 64;  // buffer rows past an item's last step that a tile may read
+
+// Shared memory of one contraction warp, padded to 128 bytes so that every warp's ring (a bulk
+// copy destination) starts 128-byte aligned.
+template <typename T>
+__host__ __device__ constexpr int contract_warp_bytes() {
+    return (3 * 32 * 32 * static_cast<int>(sizeof(T))        // ring of three halves
+            + 32 * kContractC * static_cast<int>(sizeof(T))  // dx of the strip's rows
+            + 3 * 8                                          // mbarriers
+            + 127) / 128 * 128;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kContractWarps * 32) bwd_contract_kernel(BwdParams B) {
+    constexpr int C = kContractC;
+    constexpr int HB = 32 * 32 * static_cast<int>(sizeof(T));  // bytes of one half
+    using V = typename Vec<T>::type;
+    constexpr int W = Vec<T>::W;
+    const Launch& L = B.L;
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    const int dpad = L.dpad;
+    const int lam = L.lam;
+    const T* __restrict__ incX = static_cast<const T*>(L.X.inc);
+    const T* __restrict__ incY = static_cast<const T*>(L.Y.inc);
+    extern __shared__ __align__(16) unsigned char csm[];
+    unsigned char* wsm = csm + wib * contract_warp_bytes<T>();
+    T* ring = reinterpret_cast<T*>(wsm);                                   // [3][32 rows][32]
+    T* xs = reinterpret_cast<T*>(wsm + 3 * HB);                            // [32][C]
+    uint64_t* bars = reinterpret_cast<uint64_t*>(wsm + 3 * HB + 32 * C * sizeof(T));
+    T* acc = reinterpret_cast<T*>(csm + kContractWarps * contract_warp_bytes<T>());  // [lx + ly][C]
+    if (lane == 0) {
+        for (int k = 0; k < 3; ++k) mbar_init(bars + k, 1);
+        fence_mbar_init();
+    }
+    __syncwarp();
+    uint32_t parity = 0;   // bit k: phase of slot k's barrier awaited next (warp-uniform)
+    uint32_t pending = 0;  // bit k: a copy into slot k was issued and not yet awaited
+    bool stuck = false;
+
+    // Every warp visits every item of its block (a stuck warp skips its strips) so that the
+    // block-wide barriers below are reached by all warps.
+    for (int64_t item = blockIdx.x; item < L.npairs; item += gridDim.x) {
+        const PairDesc P = decode_pair(L, item);
+        if (P.lx <= 0 || P.ly <= 0) continue;
+        const double gbar = item_gbar(B, item, P);
+        if (gbar == 0.0) continue;
+        const double gscale = gbar * pow2d(L.tape_ek[item]);
+        const int rows = static_cast<int>(P.lx << lam);
+        const int cols = static_cast<int>(P.ly << lam);
+        const int period = cols > 32 ? cols : 32;
+        const int nstrips = (rows + 31) >> 5;
+        const int ntiles = (cols + 31) >> 5;
+        // Waits on slot k for the copy issued last into it; false when the wait ran out.
+        auto await_slot = [&](int k) -> bool {
+            if (!mbar_wait(bars + k, (parity >> k) & 1u)) return false;
+            parity ^= 1u << k;
+            pending &= ~(1u << k);
+            return true;
+        };
+        const char* mb = static_cast<const char*>(B.mbuf) + item * B.mb_stride;
+        const T* xbase = incX + P.xs * dpad;
+        const T* ybase = incY + P.ys * dpad;
+        double* gx = B.gincX + P.xs * dpad;
+        double* gy = B.gincY + P.ys * dpad;
+        const int nacc = static_cast<int>(P.lx + P.ly) * C;
+        const bool use_smem = static_cast<int64_t>(nacc) * static_cast<int64_t>(sizeof(T)) <= B.acc_bytes;
+        for (int c0 = 0; c0 < dpad; c0 += C) {
+            if (use_smem) {
+                for (int q = threadIdx.x; q < nacc; q += blockDim.x) acc[q] = T(0);
+                __syncthreads();
+            }
+            for (int s = wib; s < nstrips && !stuck; s += kContractWarps) {
+                const int t0 = s * period;
+                const int nr = min(32, rows - (s << 5));  // valid rows of the strip
+                // half h of the strip = buffer rows t0 + 32h .. t0 + 32h + 31, in slot h % 3
+                for (int h = 0; h < 3 && h <= ntiles; ++h) {
+                    if (lane == 0) {
+                        mbar_arrive_expect_tx(bars + h, HB);
+                        bulk_load(ring + h * 1024, mb + static_cast<int64_t>(t0 + 32 * h) * 32 * sizeof(T), HB,
+                                  bars + h);
+                    }
+                    pending |= 1u << h;
+                }
+                __syncwarp();  // the previous strip's readers of xs are done
+                {
+                    const int xi = min((s << 5) + lane, rows - 1) >> lam;
+                    const T* xr = xbase + static_cast<int64_t>(xi) * dpad + c0;
+#pragma unroll
+                    for (int c = 0; c < C; ++c) xs[lane * C + c] = (lane < nr && c0 + c < dpad) ? xr[c] : T(0);
+                }
+                __syncwarp();
+                T xa[C];
+#pragma unroll
+                for (int c = 0; c < C; ++c) xa[c] = T(0);
+                for (int b = 0; b < ntiles; ++b) {
+                    // half b (slot s0) was awaited as the upper half of tile b - 1, except for b = 0
+                    const int s0 = b % 3, s1 = (b + 1) % 3;
+                    if (b == 0 && !await_slot(s0)) { stuck = true; break; }
+                    if (!await_slot(s1)) { stuck = true; break; }
+                    const int j0 = b << 5;
+                    const int coff = (t0 + j0) & 31;
+                    const T* S0 = ring + s0 * 1024;
+                    const T* S1 = ring + s1 * 1024;
+                    const bool full = (nr == 32) && (j0 + 32 <= cols);
+                    // dk/dx: row `lane`, columns j0 .. j0 + 31
+#pragma unroll 8
+                    for (int q = 0; q < 32; ++q) {
+                        const int u = lane + q;
+                        const T* Sr = u < 32 ? S0 : S1;
+                        T m = Sr[((u & 31) << 5) + ((lane + u + coff) & 31)];
+                        if (!full) m = (lane < nr && j0 + q < cols) ? m : T(0);
+                        const int yi = min(j0 + q, cols - 1) >> lam;
+                        const V* yv = reinterpret_cast<const V*>(ybase + static_cast<int64_t>(yi) * dpad + c0);
+#pragma unroll
+                        for (int c4 = 0; c4 < C / W; ++c4) {
+                            if (c0 + c4 * W < dpad) {
+                                const V yy = __ldg(yv + c4);
+                                const T* yp = reinterpret_cast<const T*>(&yy);
+#pragma unroll
+                                for (int w = 0; w < W; ++w) xa[c4 * W + w] = fma(m, yp[w], xa[c4 * W + w]);
+                            }
+                        }
+                    }
+                    // dk/dy: column j0 + lane, rows 0 .. 31 of the strip
+                    T ys[C];
+#pragma unroll
+                    for (int c = 0; c < C; ++c) ys[c] = T(0);
+#pragma unroll 8
+                    for (int r = 0; r < 32; ++r) {
+                        const int u = r + lane;
+                        const T* Sr = u < 32 ? S0 : S1;
+                        T m = Sr[((u & 31) << 5) + ((r + u + coff) & 31)];
+                        if (!full) m = (r < nr && j0 + lane < cols) ? m : T(0);
+                        const V* xv = reinterpret_cast<const V*>(xs + r * C);
+#pragma unroll
+                        for (int c4 = 0; c4 < C / W; ++c4) {
+                            const V xx = xv[c4];
+                            const T* xp = reinterpret_cast<const T*>(&xx);
+#pragma unroll
+                            for (int w = 0; w < W; ++w) ys[c4 * W + w] = fma(m, xp[w], ys[c4 * W + w]);
+                        }
+                    }
+                    if (j0 + lane < cols) {
+                        const int yi = (j0 + lane) >> lam;
+#pragma unroll
+                        for (int c = 0; c < C; ++c) {
+                            if (c0 + c < dpad && ys[c] != T(0)) {
+                                if (use_smem) atomicAdd(acc + (P.lx + yi) * C + c, ys[c]);
+                                else atomicAdd(gy + static_cast<int64_t>(yi) * dpad + c0 + c,
+                                               static_cast<double>(ys[c]) * gscale);
+                            }
+                        }
+                    }
+                    __syncwarp();  // slot s0 is read by every lane: refill it with half b + 3
+                    if (b + 3 <= ntiles) {
+                        if (lane == 0) {
+                            mbar_arrive_expect_tx(bars + s0, HB);
+                            bulk_load(ring + s0 * 1024, mb + static_cast<int64_t>(t0 + 32 * (b + 3)) * 32 * sizeof(T),
+                                      HB, bars + s0);
+                        }
+                        pending |= 1u << s0;
+                    }
+                }
+                if (lane < nr) {
+                    const int xi = ((s << 5) + lane) >> lam;
+#pragma unroll
+                    for (int c = 0; c < C; ++c) {
+                        if (c0 + c < dpad && xa[c] != T(0)) {
+                            if (use_smem) atomicAdd(acc + xi * C + c, xa[c]);
+                            else atomicAdd(gx + static_cast<int64_t>(xi) * dpad + c0 + c,
+                                           static_cast<double>(xa[c]) * gscale);
+                        }
+                    }
+                }
+            }
+            if (use_smem) {
+                __syncthreads();
+                for (int q = threadIdx.x; q < nacc; q += blockDim.x) {
+                    const int r = q / C, c = q - r * C;
+                    if (c0 + c >= dpad || acc[q] == T(0)) continue;
+                    double* g = r < P.lx ? gx + static_cast<int64_t>(r) * dpad : gy + static_cast<int64_t>(r - P.lx) * dpad;
+                    atomicAdd(g + c0 + c, static_cast<double>(acc[q]) * gscale);
+                }
+                __syncthreads();
+            }
+        }
+    }
+    if (stuck) {  // the device error word is set; wait (bounded) for this warp's copies in flight
+        for (int k = 0; k < 3; ++k)
+            if (pending & (1u << k)) mbar_wait(bars + k, (parity >> k) & 1u);
     }
 }
 

@@ -127,17 +127,18 @@ struct Launch {
     int64_t scratch_stride;  // bytes per warp slot
     float tau;               // |M| above which an FP32 map is built in FP64
     // Optional tape of the forward pass (approximation scheme): per work item, per warp step, per
-    // lane, the cell's inputs (a[N+1], b[N+1], exponent) in a padded 16-byte-vector row; plus the
-    // exponent of k_hat per item.  NULL when not recorded.
+    // lane, the cell's inputs (a[N+1], b[N+1], exponent, M) in a padded 16-byte-vector row; plus
+    // the exponent of k_hat per item.  NULL when not recorded.
     void* tape;
     int64_t tape_stride;     // bytes per work item
     int* tape_ek;            // [npairs]
 };
 
-// Width, in elements of T, of one lane's tape row: a, b and the exponent, padded to 16 bytes.
+// Width, in elements of T, of one lane's tape row: a[0..N], b[0..N], the exponent (element
+// 2N+2) and the cell's M (element 2N+3), padded to 16 bytes.
 template <typename T>
 __host__ __device__ constexpr int tape_row(int N) {
-    return ((2 * (N + 1) + 1) * static_cast<int>(sizeof(T)) + 15) / 16 * 16 / static_cast<int>(sizeof(T));
+    return ((2 * (N + 1) + 2) * static_cast<int>(sizeof(T)) + 15) / 16 * 16 / static_cast<int>(sizeof(T));
 }
 
 __device__ __forceinline__ int64_t upper_row(int64_t p, int64_t n) {

@@ -25,7 +25,10 @@ int bwd_segment_f64();
 }  // namespace sk
 
 namespace sk {
-// Tape-driven adjoint of the approximation scheme (dmax = 8 or 32).  NULL when no kernel exists.
-const void* bwd_tape_ptr_f32(int N, int dmax);
-const void* bwd_tape_ptr_f64(int N, int dmax);
+// Tape-driven adjoint of the approximation scheme (NULL when no kernel exists for order N) and
+// the contraction of its dk/dM buffer into increment gradients.
+const void* bwd_tape_ptr_f32(int N);
+const void* bwd_tape_ptr_f64(int N);
+const void* bwd_contract_ptr_f32();
+const void* bwd_contract_ptr_f64();
 }  // namespace sk

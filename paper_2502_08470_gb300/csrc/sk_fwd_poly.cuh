@@ -223,9 +223,13 @@ __global__ void __launch_bounds__(kFwdWarps * 32, (fwd_poly_min_blocks<T, N, NE>
                     ea = eb;
                 }
             }
+            // Every lane runs the cell (inactive lanes on a clamped, in-bounds column); only
+            // the results of active lanes are ever consumed.
+            const int jc = min(max(jj, 0), cols - 1);
+            const T M = row_dot<T>(xrow, ybase + static_cast<int64_t>(jc >> lam) * dpad, L.nvec) * sub;
             if constexpr (!INTERP) {
                 if (L.tape != nullptr) {
-                    // Record the cell's inputs for the adjoint: each lane writes its row into a
+                    // Record the cell's inputs (a, b, exponent, M) for the adjoint: each lane writes its row into a
                     // shared-memory slot laid out [vector][lane], then one lane moves the whole step
                     // (32 rows) to the tape with a bulk copy.  Two slots alternate; a slot is
                     // rewritten only after the copy issued from it two steps ago has read it.
@@ -246,6 +250,7 @@ __global__ void __launch_bounds__(kFwdWarps * 32, (fwd_poly_min_blocks<T, N, NE>
                                 if constexpr (std::is_same<T, float>::value) tp[w] = __int_as_float(ea);
                                 else tp[w] = __longlong_as_double(static_cast<long long>(ea));
                             }
+                            if (q == 2 * N + 3) tp[w] = M;
                         }
                         slot_v[v * 32 + lane] = t;
                     }
@@ -258,10 +263,6 @@ __global__ void __launch_bounds__(kFwdWarps * 32, (fwd_poly_min_blocks<T, N, NE>
                     }
                 }
             }
-            // Every lane runs the cell (inactive lanes on a clamped, in-bounds column); only
-            // the results of active lanes are ever consumed.
-            const int jc = min(max(jj, 0), cols - 1);
-            const T M = row_dot<T>(xrow, ybase + static_cast<int64_t>(jc >> lam) * dpad, L.nvec) * sub;
             T e[NE + 1];
             build_exp_series<T, NE>(M, L.tau, e);
             T ct[NE + 1], cr[NE + 1];
