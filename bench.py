@@ -72,6 +72,29 @@ def contract_bytes_per_cell(esize: int = 4) -> int:
     return esize
 
 
+def tape_steps(points: int) -> int:
+    """Warp steps of one pair of `points`-point paths in the wavefront schedule (strips of 32 rows
+    overlapping with period max(cols, 32))."""
+    rows = cols = points - 1
+    nstrips = (rows + 31) // 32
+    return (nstrips - 1) * max(cols, 32) + (rows - 1 - 32 * (nstrips - 1)) + cols
+
+
+def tape_adjoint_bytes(pairs: int, points: int, N: int = DEGREE) -> int:
+    """Algorithmic DRAM bytes of one tape-adjoint launch: each warp step reads a 32-lane tape step
+    (a, b, exponent, M padded to 16 B per lane) and writes 32 dk/dM values."""
+    row = ((2 * (N + 1) + 2) * 4 + 15) // 16 * 16
+    return pairs * tape_steps(points) * 32 * (row + 4)
+
+
+# DRAM traffic of bwd_tape_kernel<float,6> per launch from one ncu capture on 64x64 pairs of
+# 129-point paths (read 4.603778 GB + write 0.333018 GB), as a multiple of that launch's
+# algorithmic bytes.  The traffic scales with the tape, so the bench launch's traffic is this ratio
+# times its own algorithmic bytes.  Valid only while the kernel is unchanged since that capture.
+NCU_TAPE_TRAFFIC_RATIO = (4.603778e9 + 0.333018e9) / tape_adjoint_bytes(64 * 64, 129)
+HBM_GBS = 6681.2  # measured copy bandwidth of this GB300 pool
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -345,7 +368,13 @@ def main():
                    "tape_gb": round(tape_buf[0].numel() / 1e9, 2),
                    "parallelism": f"weak scaling, one independent {nx}x{nx} Gram per GPU ({world} GPUs)"},
         "roofline": {"bound": "alu", "achieved": ach_b, "peak": peak, "unit": "TFLOP/s", "frac": ach_b / peak,
-                     "traffic": None, "kernel": "bwd_tape_kernel<float,6> (adjoint wavefront from the tape)",
+                     "traffic": NCU_TAPE_TRAFFIC_RATIO * tape_adjoint_bytes(nx * nx, npts),
+                     "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one 64x64x129-point "
+                                       "launch, scaled by algorithmic tape bytes to this launch",
+                     "algorithmic_bytes": tape_adjoint_bytes(nx * nx, npts),
+                     "hbm_gbs": tape_adjoint_bytes(nx * nx, npts) / (kb / 1e3) / 1e9,
+                     "hbm_frac_of_measured": tape_adjoint_bytes(nx * nx, npts) / (kb / 1e3) / 1e9 / HBM_GBS,
+                     "kernel": "bwd_tape_kernel<float,6> (adjoint wavefront from the tape)",
                      "kernel_ms": kb,
                      "flops_per_cell": bpc,
                      "peak_source": "152 SMs x 128 FP32 lanes x 2 FLOP x 2070 MHz (derived, nominal clocks)"},

@@ -845,7 +845,7 @@ __global__ void __launch_bounds__(kContractWarps * 32) bwd_contract_kernel(BwdPa
     T* ring = reinterpret_cast<T*>(wsm);                                   // [3][32 rows][32]
     T* xs = reinterpret_cast<T*>(wsm + 3 * HB);                            // [32][C]
     uint64_t* bars = reinterpret_cast<uint64_t*>(wsm + 3 * HB + 32 * C * sizeof(T));
-    T* acc = reinterpret_cast<T*>(csm + kContractWarps * contract_warp_bytes<T>());  // [lx + ly][C]
+    T* acc = reinterpret_cast<T*>(csm + kContractWarps * contract_warp_bytes<T>());  // [C][lx + ly]
     if (lane == 0) {
         for (int k = 0; k < 3; ++k) mbar_init(bars + k, 1);
         fence_mbar_init();
@@ -880,7 +880,8 @@ __global__ void __launch_bounds__(kContractWarps * 32) bwd_contract_kernel(BwdPa
         const T* ybase = incY + P.ys * dpad;
         double* gx = B.gincX + P.xs * dpad;
         double* gy = B.gincY + P.ys * dpad;
-        const int nacc = static_cast<int>(P.lx + P.ly) * C;
+        const int nrow = static_cast<int>(P.lx + P.ly);  // accumulator rows: X increments, then Y
+        const int nacc = nrow * C;                        // laid out [C][nrow]
         const bool use_smem = static_cast<int64_t>(nacc) * static_cast<int64_t>(sizeof(T)) <= B.acc_bytes;
         for (int c0 = 0; c0 < dpad; c0 += C) {
             if (use_smem) {
@@ -920,9 +921,11 @@ __global__ void __launch_bounds__(kContractWarps * 32) bwd_contract_kernel(BwdPa
                     const T* S0 = ring + s0 * 1024;
                     const T* S1 = ring + s1 * 1024;
                     const bool full = (nr == 32) && (j0 + 32 <= cols);
-                    // dk/dx: row `lane`, columns j0 .. j0 + 31
+                    // dk/dx: row `lane`, columns j0 .. j0 + 31.  The upper half-warp runs one column
+                    // ahead (cyclically) so that the two halves read banks of opposite parity.
 #pragma unroll 8
-                    for (int q = 0; q < 32; ++q) {
+                    for (int q0 = 0; q0 < 32; ++q0) {
+                        const int q = (q0 + (lane >> 4)) & 31;
                         const int u = lane + q;
                         const T* Sr = u < 32 ? S0 : S1;
                         T m = Sr[((u & 31) << 5) + ((lane + u + coff) & 31)];
@@ -963,7 +966,7 @@ __global__ void __launch_bounds__(kContractWarps * 32) bwd_contract_kernel(BwdPa
 #pragma unroll
                         for (int c = 0; c < C; ++c) {
                             if (c0 + c < dpad && ys[c] != T(0)) {
-                                if (use_smem) atomicAdd(acc + (P.lx + yi) * C + c, ys[c]);
+                                if (use_smem) atomicAdd(acc + c * nrow + P.lx + yi, ys[c]);
                                 else atomicAdd(gy + static_cast<int64_t>(yi) * dpad + c0 + c,
                                                static_cast<double>(ys[c]) * gscale);
                             }
@@ -984,7 +987,7 @@ __global__ void __launch_bounds__(kContractWarps * 32) bwd_contract_kernel(BwdPa
 #pragma unroll
                     for (int c = 0; c < C; ++c) {
                         if (c0 + c < dpad && xa[c] != T(0)) {
-                            if (use_smem) atomicAdd(acc + xi * C + c, xa[c]);
+                            if (use_smem) atomicAdd(acc + c * nrow + xi, xa[c]);
                             else atomicAdd(gx + static_cast<int64_t>(xi) * dpad + c0 + c,
                                            static_cast<double>(xa[c]) * gscale);
                         }
@@ -994,7 +997,7 @@ __global__ void __launch_bounds__(kContractWarps * 32) bwd_contract_kernel(BwdPa
             if (use_smem) {
                 __syncthreads();
                 for (int q = threadIdx.x; q < nacc; q += blockDim.x) {
-                    const int r = q / C, c = q - r * C;
+                    const int c = q / nrow, r = q - c * nrow;
                     if (c0 + c >= dpad || acc[q] == T(0)) continue;
                     double* g = r < P.lx ? gx + static_cast<int64_t>(r) * dpad : gy + static_cast<int64_t>(r - P.lx) * dpad;
                     atomicAdd(g + c0 + c, static_cast<double>(acc[q]) * gscale);

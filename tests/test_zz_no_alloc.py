@@ -8,6 +8,7 @@ refused before anything runs.  This file is collected last so that a run stoppin
 failure has already run every other test.
 """
 import ctypes
+import gc
 
 import numpy as np
 import pytest
@@ -43,11 +44,19 @@ def _noalloc(L, X, Y, pa, pb, scheme, degree, compute):
     pa_t = torch.as_tensor(pa, dtype=torch.int64, device="cuda")
     pb_t = torch.as_tensor(pb, dtype=torch.int64, device="cuda")
     out = torch.full((len(pa),), float("nan"), dtype=torch.float64, device="cuda")
-    before = torch.cuda.memory_allocated()
-    rc = L.sigkernel_pairs_noalloc(ctypes.byref(cX), ctypes.byref(cY), X.d, sk.DTYPES[X.rows.dtype],
-                                   pa_t.data_ptr(), pb_t.data_ptr(), len(pa), ctypes.byref(opt), out.data_ptr(),
-                                   torch.cuda.current_stream().cuda_stream)
-    assert torch.cuda.memory_allocated() == before  # nothing came from torch's allocator either
+    # Python's cycle collector could free earlier tensors during the call and move the count
+    # the other way; collect first and hold it off while measuring.
+    gc.collect()
+    gc.disable()
+    try:
+        before = torch.cuda.memory_allocated()
+        rc = L.sigkernel_pairs_noalloc(ctypes.byref(cX), ctypes.byref(cY), X.d, sk.DTYPES[X.rows.dtype],
+                                       pa_t.data_ptr(), pb_t.data_ptr(), len(pa), ctypes.byref(opt), out.data_ptr(),
+                                       torch.cuda.current_stream().cuda_stream)
+        after = torch.cuda.memory_allocated()
+    finally:
+        gc.enable()
+    assert after == before  # nothing came from torch's allocator either
     return rc, out
 
 
