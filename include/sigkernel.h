@@ -89,8 +89,14 @@ enum {
     SK_FLAG_INCREMENTS = 2,   /* rows hold increments, not points */
     SK_FLAG_UNBIASED = 4,     /* sigkernel_mmd2: U-statistic (diagonals of K_AA, K_BB left out) */
     SK_FLAG_NO_SORT = 8,      /* process pairs in the given order (no cell-count ordering) */
-    SK_FLAG_TIME_KERNEL = 16  /* record CUDA events around the wavefront kernel(s) of this call on
+    SK_FLAG_TIME_KERNEL = 16, /* record CUDA events around the wavefront kernel(s) of this call on
                                  `stream`; read the duration with sigkernel_last_kernel_ms() */
+    SK_FLAG_STRIP_PIPELINE = 32,    /* forward: sweep every pair of 2 or more strips (32 grid rows
+                                       each) with a block of warps, one strip per warp in a
+                                       pipeline, instead of one warp per pair */
+    SK_FLAG_NO_STRIP_PIPELINE = 64  /* forward: always one warp per pair.  With neither flag the
+                                       library pipelines long pairs when the batch is too small to
+                                       fill the GPU with one warp per pair (no effect with a tape) */
 };
 
 typedef struct {
@@ -167,7 +173,7 @@ int sigkernel_gram(const sk_paths* X, const sk_paths* Y, int32_t d, int32_t dtyp
  *           the existing contents (the caller zeroes it first for a plain gradient); NULL skips.
  *   grad_Y  likewise for Y.  When Y is X (same rows pointer) both accumulate into the same
  *           buffer correctly if grad_X == grad_Y.
- * Supported for SK_POLY_APPROX and the FD schemes; other schemes return SK_ERR_UNSUPPORTED.
+ * Supported for SK_POLY_APPROX with d <= 32; other schemes return SK_ERR_UNSUPPORTED.
  * Accumulation uses device atomics, so the last bits of the gradient can vary between runs.
  */
 int sigkernel_backward(const sk_paths* X, const sk_paths* Y, int32_t d, int32_t dtype,

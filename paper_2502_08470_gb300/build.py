@@ -30,7 +30,16 @@ def _nvcc() -> str:
 
 
 def _sources():
-    return sorted(glob.glob(os.path.join(CSRC, "*.cu")))
+    # Longest units first (adjoints, then the interpolation kernels of high order), so that the
+    # parallel build is not left waiting on one of them at the end.
+    def weight(path):
+        name = os.path.basename(path)
+        if name.startswith("sk_bwd"):
+            return 0
+        if "interp" in name:
+            return 1 + (10 - int(name[-4]) if name[-4].isdigit() else 0)
+        return 20
+    return sorted(glob.glob(os.path.join(CSRC, "*.cu")), key=lambda p: (weight(p), p))
 
 
 def _headers():

@@ -114,6 +114,8 @@ struct Plan {
     const void* kern;    // wavefront kernel
     int threads;         // threads per block
     int blocks;          // persistent grid
+    bool coop;           // cooperative-block kernel (strip pipeline for long pairs)
+    int coop_min_strips; // strips from which a pair is swept by a whole block
     int64_t slot_bytes;  // scratch per warp slot
     int64_t buf_cols;    // hand-off columns per warp slot
     // workspace layout (byte offsets)
@@ -154,13 +156,18 @@ int check_options(const sk_options* o, int32_t d, int32_t dtype) {
     }
     if (o->warps_per_block != 0 && o->warps_per_block != kFwdWarps)
         return fail(SK_ERR_UNSUPPORTED, "warps_per_block %d (this build: 0 or %d)", o->warps_per_block, kFwdWarps);
-    if (o->flags & ~(SK_FLAG_SYMMETRIC | SK_FLAG_INCREMENTS | SK_FLAG_UNBIASED | SK_FLAG_NO_SORT | SK_FLAG_TIME_KERNEL))
+    if (o->flags & ~(SK_FLAG_SYMMETRIC | SK_FLAG_INCREMENTS | SK_FLAG_UNBIASED | SK_FLAG_NO_SORT | SK_FLAG_TIME_KERNEL |
+                     SK_FLAG_STRIP_PIPELINE | SK_FLAG_NO_STRIP_PIPELINE))
         return fail(SK_ERR_INVALID_ARG, "unknown flag bits 0x%x", o->flags);
+    if ((o->flags & SK_FLAG_STRIP_PIPELINE) && (o->flags & SK_FLAG_NO_STRIP_PIPELINE))
+        return fail(SK_ERR_INVALID_ARG, "SK_FLAG_STRIP_PIPELINE and SK_FLAG_NO_STRIP_PIPELINE together");
     return SK_OK;
 }
 
+// allow_coop: the caller launches p.kern itself with p.threads (the plain forward); adjoint
+// plans reuse this layout with their own one-warp-per-pair kernels and pass false.
 int plan_forward(const sk_paths* X, const sk_paths* Y, int32_t d, int32_t dtype, const sk_options* o,
-                 int mode, int64_t npairs, Plan& p) {
+                 int mode, int64_t npairs, Plan& p, bool allow_coop = false) {
     int rc;
     if ((rc = check_options(o, d, dtype)) != SK_OK) return rc;
     if ((rc = check_paths(X, "X", d)) != SK_OK) return rc;
@@ -184,22 +191,47 @@ int plan_forward(const sk_paths* X, const sk_paths* Y, int32_t d, int32_t dtype,
 
     const bool poly = o->scheme == SK_POLY_APPROX || o->scheme == SK_POLY_INTERP;
     int width = 1;  // values handed from strip to strip per refined column
+    auto kernel_for = [&](bool coop) -> const void* {
+        return poly ? fwd_poly_kernel_ptr(p.T, o->scheme == SK_POLY_INTERP, o->degree, coop)
+                    : fwd_fd_kernel_ptr(p.T, o->scheme == SK_FD2 ? 2 : 1, lam, coop);
+    };
+    p.kern = kernel_for(false);
     if (poly) {
-        p.kern = fwd_poly_kernel_ptr(p.T, o->scheme == SK_POLY_INTERP, o->degree);
         const int hw = p.T ? 4 : 2;  // hand-off entries are padded to whole 16-byte vectors
         width = (o->degree + 1 + hw - 1) / hw * hw;
-    } else {
-        p.kern = fwd_fd_kernel_ptr(p.T, o->scheme == SK_FD2 ? 2 : 1, lam);
-        width = 1;
     }
     if (!p.kern) return fail(SK_ERR_UNSUPPORTED, "no kernel for scheme %d order %d compute %d", o->scheme, o->degree, o->compute);
     p.threads = kFwdWarps * 32;
+    p.coop = false;
+    p.coop_min_strips = 0;
     int dev = 0, sms = 0, per_sm = 0;
     SK_CUDA(cudaGetDevice(&dev));
     SK_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     SK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, p.kern, p.threads, 0));
     if (per_sm < 1) per_sm = 1;
-    int64_t want = (npairs + kFwdWarps - 1) / kFwdWarps;
+    // Strip pipeline: a pair of many strips swept by one warp is a serial chain of
+    // nstrips x cols steps; when the batch cannot fill the GPU with one warp per pair, long pairs
+    // are swept by blocks of kCoopWarps warps instead (one strip per warp, pipelined).
+    if (allow_coop && !(o->flags & SK_FLAG_NO_STRIP_PIPELINE)) {
+        const int rows_per_lane = poly ? 1 : (lam < 4 ? (1 << lam) : 16);
+        const int64_t max_strips = (((X->max_len << lam) / rows_per_lane) + 31) / 32;
+        const bool forced = (o->flags & SK_FLAG_STRIP_PIPELINE) != 0;
+        const int64_t resident = static_cast<int64_t>(sms) * per_sm * kFwdWarps;
+        if (max_strips >= 2 && (forced || (max_strips >= 2 * kCoopWarps && npairs < 4 * resident))) {
+            const void* ck = kernel_for(true);
+            int cper = 0;
+            if (ck) SK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&cper, ck, kCoopWarps * 32, 0));
+            if (ck && cper >= 1) {
+                p.kern = ck;
+                p.coop = true;
+                p.coop_min_strips = forced ? 2 : 2 * kCoopWarps;
+                p.threads = kCoopWarps * 32;
+                per_sm = cper;
+            }
+        }
+    }
+    const int wpb = p.threads / 32;
+    int64_t want = p.coop ? npairs : (npairs + wpb - 1) / wpb;
     int64_t cap = static_cast<int64_t>(sms) * per_sm;
     p.blocks = static_cast<int>(want < cap ? (want > 0 ? want : 1) : cap);
     p.buf_cols = (Y->max_len << lam) + 1;
@@ -218,7 +250,7 @@ int plan_forward(const sk_paths* X, const sk_paths* Y, int32_t d, int32_t dtype,
     p.off_order = off;
     off += align256(static_cast<size_t>(npairs) * sizeof(int32_t));
     p.off_scratch = off;
-    off += static_cast<size_t>(p.blocks) * kFwdWarps * static_cast<size_t>(p.slot_bytes);
+    off += static_cast<size_t>(p.blocks) * wpb * static_cast<size_t>(p.slot_bytes);
     p.total = off + 256;
     return SK_OK;
 }
@@ -273,7 +305,7 @@ int run_forward(const sk_paths* X, const sk_paths* Y, int32_t d, int32_t dtype, 
                 const int64_t* pa, const int64_t* pb, int64_t npairs, double* out, int64_t ldo, void* ws,
                 size_t ws_bytes, void* stream, void* tape = nullptr, size_t tape_bytes = 0) {
     Plan p;
-    int rc = plan_forward(X, Y, d, dtype, o, mode, npairs, p);
+    int rc = plan_forward(X, Y, d, dtype, o, mode, npairs, p, tape == nullptr);
     if (rc != SK_OK) return rc;
     TapePlan tp{0, 0, 0, 0};
     if (tape) {
@@ -323,6 +355,7 @@ int run_forward(const sk_paths* X, const sk_paths* Y, int32_t d, int32_t dtype, 
     L.tape = tape ? static_cast<char*>(tape) + tp.ek_bytes : nullptr;
     L.tape_stride = static_cast<int64_t>(tp.stride);
     L.tape_ek = tape ? static_cast<int*>(tape) : nullptr;
+    L.coop_min_strips = p.coop_min_strips;
     SK_CUDA(cudaMemsetAsync(base + p.off_queue, 0, 256 + align256(2 * 65 * sizeof(unsigned int)), st));
     if (!(o->flags & SK_FLAG_NO_SORT) && npairs > 1) {
         unsigned int* hist = reinterpret_cast<unsigned int*>(base + p.off_hist);
@@ -772,7 +805,7 @@ int run_mmd2(const sk_paths* A, const sk_paths* Bp, int32_t d, int32_t dtype, co
     const bool unb = (o->flags & SK_FLAG_UNBIASED) != 0;
     if (unb && (A->count < 2 || Bp->count < 2)) return fail(SK_ERR_INVALID_ARG, "unbiased MMD^2 needs >= 2 paths per set");
     sk_options os = *o;
-    os.flags = (o->flags & (SK_FLAG_INCREMENTS | SK_FLAG_NO_SORT | SK_FLAG_TIME_KERNEL)) | SK_FLAG_SYMMETRIC;
+    os.flags = (o->flags & (SK_FLAG_INCREMENTS | SK_FLAG_NO_SORT | SK_FLAG_TIME_KERNEL | SK_FLAG_STRIP_PIPELINE | SK_FLAG_NO_STRIP_PIPELINE)) | SK_FLAG_SYMMETRIC;
     sk_options of = os;
     of.flags &= ~SK_FLAG_SYMMETRIC;
     const bool grads = gA || gB;
@@ -780,9 +813,9 @@ int run_mmd2(const sk_paths* A, const sk_paths* Bp, int32_t d, int32_t dtype, co
     Plan paa, pbb, pab;
     BwdPlan baa, bbb, bab;
     int rc;
-    if ((rc = plan_forward(A, A, d, dtype, &os, kGramUpper, gram_items(A, A, true), paa)) != SK_OK) return rc;
-    if ((rc = plan_forward(Bp, Bp, d, dtype, &os, kGramUpper, gram_items(Bp, Bp, true), pbb)) != SK_OK) return rc;
-    if ((rc = plan_forward(A, Bp, d, dtype, &of, kGramFull, gram_items(A, Bp, false), pab)) != SK_OK) return rc;
+    if ((rc = plan_forward(A, A, d, dtype, &os, kGramUpper, gram_items(A, A, true), paa, true)) != SK_OK) return rc;
+    if ((rc = plan_forward(Bp, Bp, d, dtype, &os, kGramUpper, gram_items(Bp, Bp, true), pbb, true)) != SK_OK) return rc;
+    if ((rc = plan_forward(A, Bp, d, dtype, &of, kGramFull, gram_items(A, Bp, false), pab, true)) != SK_OK) return rc;
     size_t sub = std::max(paa.total, std::max(pbb.total, pab.total));
     if (grads) {
         if ((rc = plan_backward(A, A, d, dtype, &os, kGramUpper, gram_items(A, A, true), baa)) != SK_OK) return rc;
@@ -878,11 +911,11 @@ int sigkernel_workspace_size(int32_t op, const sk_paths* X, const sk_paths* Y, i
     const int dtype = SK_F64;  // sizes do not depend on the input element type
     switch (op) {
         case SK_OP_PAIRS:
-            rc = plan_forward(X, Y, d, dtype, opt, kPairsList, npairs, p);
+            rc = plan_forward(X, Y, d, dtype, opt, kPairsList, npairs, p, true);
             break;
         case SK_OP_GRAM: {
             bool sym = (opt->flags & SK_FLAG_SYMMETRIC) != 0;
-            rc = plan_forward(X, Y, d, dtype, opt, sym ? kGramUpper : kGramFull, gram_items(X, Y, sym), p);
+            rc = plan_forward(X, Y, d, dtype, opt, sym ? kGramUpper : kGramFull, gram_items(X, Y, sym), p, true);
             break;
         }
         case SK_OP_BACKWARD: {
@@ -908,12 +941,12 @@ int sigkernel_workspace_size(int32_t op, const sk_paths* X, const sk_paths* Y, i
             Plan pa, pb, pc;
             BwdPlan ba, bb, bc;
             sk_options os = *opt;
-            os.flags = (opt->flags & (SK_FLAG_INCREMENTS | SK_FLAG_NO_SORT | SK_FLAG_TIME_KERNEL)) | SK_FLAG_SYMMETRIC;
+            os.flags = (opt->flags & (SK_FLAG_INCREMENTS | SK_FLAG_NO_SORT | SK_FLAG_TIME_KERNEL | SK_FLAG_STRIP_PIPELINE | SK_FLAG_NO_STRIP_PIPELINE)) | SK_FLAG_SYMMETRIC;
             sk_options of = os;
             of.flags &= ~SK_FLAG_SYMMETRIC;
-            if ((rc = plan_forward(X, X, d, dtype, &os, kGramUpper, gram_items(X, X, true), pa)) != SK_OK) return rc;
-            if ((rc = plan_forward(Y, Y, d, dtype, &os, kGramUpper, gram_items(Y, Y, true), pb)) != SK_OK) return rc;
-            if ((rc = plan_forward(X, Y, d, dtype, &of, kGramFull, gram_items(X, Y, false), pc)) != SK_OK) return rc;
+            if ((rc = plan_forward(X, X, d, dtype, &os, kGramUpper, gram_items(X, X, true), pa, true)) != SK_OK) return rc;
+            if ((rc = plan_forward(Y, Y, d, dtype, &os, kGramUpper, gram_items(Y, Y, true), pb, true)) != SK_OK) return rc;
+            if ((rc = plan_forward(X, Y, d, dtype, &of, kGramFull, gram_items(X, Y, false), pc, true)) != SK_OK) return rc;
             size_t sub = std::max(pa.total, std::max(pb.total, pc.total));
             if (opt->scheme == SK_POLY_APPROX && d <= 32) {
                 if ((rc = plan_backward(X, X, d, dtype, &os, kGramUpper, gram_items(X, X, true), ba)) != SK_OK) return rc;

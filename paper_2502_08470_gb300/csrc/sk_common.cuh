@@ -132,6 +132,10 @@ struct Launch {
     void* tape;
     int64_t tape_stride;     // bytes per work item
     int* tape_ek;            // [npairs]
+    // Cooperative strip pipeline (kernels launched with several warps per pair): a pair with at
+    // least this many strips is swept by all warps of a block together; shorter pairs get one
+    // warp each.
+    int32_t coop_min_strips;
 };
 
 // Width, in elements of T, of one lane's tape row: a[0..N], b[0..N], the exponent (element
@@ -198,6 +202,44 @@ __device__ __forceinline__ void write_result(const Launch& L, int64_t item, cons
         L.out[P.a * L.ldo + P.b] = v;
         if (L.mode == kGramUpper) L.out[P.b * L.ldo + P.a] = v;
     }
+}
+
+// Pop the next work item for a whole block (call from one thread).
+__device__ __forceinline__ int64_t pop_item(const Launch& L) {
+    const unsigned int k = atomicAdd(L.queue, 1u);
+    if (static_cast<int64_t>(k) >= L.npairs) return -1;
+    return L.order ? static_cast<int64_t>(L.order[k]) : static_cast<int64_t>(k);
+}
+
+// Strip pipeline of a cooperative block: the warp that runs strip g publishes, after writing
+// the hand-off entry of column j, the monotonic count g * cols + j + 1 in its shared-memory
+// word; the warp that runs strip g + 1 waits for that count before reading the entry.  Release
+// and acquire at CTA scope order the hand-off's global-memory stores and loads around it.
+constexpr uint32_t kSpinLimit = 1u << 20;  // polls (with a short sleep) before a wait gives up
+
+__device__ __forceinline__ void publish_progress(int* p, int v) {
+    asm volatile("st.release.cta.shared::cta.b32 [%0], %1;" ::"r"(static_cast<uint32_t>(__cvta_generic_to_shared(p))),
+                 "r"(v)
+                 : "memory");
+}
+
+__device__ __forceinline__ int acquire_progress(const int* p) {
+    int v;
+    asm volatile("ld.acquire.cta.shared::cta.b32 %0, [%1];"
+                 : "=r"(v)
+                 : "r"(static_cast<uint32_t>(__cvta_generic_to_shared(p)))
+                 : "memory");
+    return v;
+}
+
+// Bounded wait for *p >= need; false (and the device error word set) when it runs out.
+__device__ __forceinline__ bool wait_progress(const int* p, int need) {
+    for (uint32_t it = 0; it < kSpinLimit; ++it) {
+        if (acquire_progress(p) >= need) return true;
+        __nanosleep(64);
+    }
+    record_error(SK_ERR_DEVICE_TIMEOUT);
+    return false;
 }
 
 // Pop the next work item for a warp (lane 0 takes it, all lanes receive it).

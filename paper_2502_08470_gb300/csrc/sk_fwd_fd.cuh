@@ -14,7 +14,8 @@
 // rounding in the long sweep direction is relative to |v| (small) rather than to |k|; in the
 // direct form every node's O(eps |k|) rounding reaches the whole quadrant above and to its right.
 //
-// Parallel layout.  One warp owns one pair.  Lane r owns R = min(2^lambda, 16) consecutive node
+// Parallel layout.  One warp owns one pair (or, for long pairs, a block of warps shares it with
+// one strip per warp in a pipeline, as in the polynomial wavefront).  Lane r owns R = min(2^lambda, 16) consecutive node
 // rows (a "row group"; all in one coarse row) and sweeps the refined columns; the top node of
 // its group moves one lane up per step by __shfl_up_sync, and lane 31's top nodes are handed to
 // lane 0 of the next strip through a per-warp buffer, as in the polynomial wavefront.  FP32 keeps
@@ -24,6 +25,7 @@
 #include <type_traits>
 
 #include "sk_common.cuh"
+#include "sk_fwd_poly.cuh"  // trivial_pair
 
 namespace sk {
 
@@ -33,126 +35,173 @@ __device__ __forceinline__ T fd_pow2(int e) {
     else return pow2d(e);
 }
 
-template <typename T, int ORDER, int R>
-__global__ void __launch_bounds__(kFwdWarps * 32) fwd_fd_kernel(Launch L, int64_t buf_cols) {
+// Sweep of one pair by one warp (CW = 1) or by warp w of a cooperative block of CW warps
+// (strips w, w + CW, ...; hand-off ordering as in sweep_poly).
+template <typename T, int ORDER, int R, int CW>
+__device__ __forceinline__ void sweep_fd(const Launch& L, int64_t item, const PairDesc& P, int w, char* own_buf,
+                                         const char* prev_buf, int* prog, int64_t buf_cols) {
     constexpr bool kRescale = std::is_same<T, float>::value;
     const int lane = threadIdx.x & 31;
-    const int64_t slot = static_cast<int64_t>(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    char* base = static_cast<char*>(L.scratch) + slot * L.scratch_stride;
-    T* hbuf = reinterpret_cast<T*>(base);                         // [buf_cols]
-    int* ebuf = reinterpret_cast<int*>(hbuf + buf_cols);          // [buf_cols]
+    T* hbuf = reinterpret_cast<T*>(own_buf);                          // [buf_cols]
+    int* ebuf = reinterpret_cast<int*>(hbuf + buf_cols);              // [buf_cols]
+    const T* hprev = reinterpret_cast<const T*>(prev_buf);
+    const int* eprev = reinterpret_cast<const int*>(hprev + buf_cols);
     const int dpad = L.dpad;
     const T* __restrict__ incX = static_cast<const T*>(L.X.inc);
     const T* __restrict__ incY = static_cast<const T*>(L.Y.inc);
 
+    const int lam = L.lam;
+    const int nI = static_cast<int>(P.lx << lam);   // refined node rows 0..nI
+    const int nJ = static_cast<int>(P.ly << lam);   // refined node columns 0..nJ
+    const int groups = nI / R;
+    // Period of a warp's strips.  Alone, a warp starts its next strip as soon as lane 0 is free
+    // (P = max(cols, 32)).  In a cooperative block that overlap can deadlock: a warp whose lane 0
+    // waits on the ring of other warps also holds back its lanes still publishing the previous
+    // strip, which those warps need.  A warp therefore starts strip k + 1 only after finishing
+    // strip k (P = cols + 31), unless the rows are longer than the ring's lag (cols > 31 CW),
+    // where the overlapped schedule keeps every wait pointed at finished work.  A model of this
+    // schedule (tests/test_pipeline_schedule.py) checks the rule and the deadlock it avoids.
+    const int period = CW == 1 ? (nJ > 32 ? nJ : 32) : (nJ > 31 * CW ? nJ : nJ + 31);
+    const int nstrips = (groups + 31) >> 5;
+    const int last_lane = (groups - 1) - ((nstrips - 1) << 5);
+    const int nloc = w < nstrips ? (nstrips - 1 - w) / CW + 1 : 0;
+    if (nloc == 0) return;
+    const bool has_last = (nstrips - 1) % CW == w;
+    const int nsteps = (nloc - 1) * period + (has_last ? last_lane : 31) + nJ;
+    const T sub = fd_pow2<T>(-2 * lam);
+    const T* xbase = incX + P.xs * dpad;
+    const T* ybase = incY + P.ys * dpad;
+
+    T v[R];     // k(gR + 1 + r, jj) - k(gR + r, jj) for the lane's group g at its column jj
+    T kb_prev = T(1), top = T(0);
+    int ea = 0, eo = 0;
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[r] = T(0);
+    int jj = -lane, sl = 0, gs = w;     // column, local strip, global strip
+    bool stuck = false;
+
+    for (int step = 0; step < nsteps; ++step) {
+        T kb = __shfl_up_sync(kFull, top, 1);            // k(gR, jj + 1) from the lane below
+        int eb = kRescale ? __shfl_up_sync(kFull, eo, 1) : 0;
+        const int g = (gs << 5) + lane;
+        const bool active = jj >= 0 && jj < nJ && g < groups && sl < nloc;
+        if (active) {
+            if (lane == 0) {
+                if (gs == 0) {
+                    kb = T(1);                               // row 0: k(s_0, .) = 1
+                    eb = 0;
+                } else {
+                    if constexpr (CW > 1) {
+                        if (!stuck && !wait_progress(prog + (w + CW - 1) % CW, (gs - 1) * nJ + jj + 1)) stuck = true;
+                    }
+                    kb = hprev[jj];
+                    if (kRescale) eb = eprev[jj];
+                }
+            }
+            if (jj == 0) {                               // column 0: k(., t_0) = 1, so v = 0
+#pragma unroll
+                for (int r = 0; r < R; ++r) v[r] = T(0);
+                kb_prev = T(1);
+                ea = 0;
+            }
+            if (kRescale && ea != eb) {
+                if (ea > eb) {
+                    kb *= (eb - ea < -126) ? T(0) : fd_pow2<T>(eb - ea);
+                } else {
+                    const T f = (ea - eb < -126) ? T(0) : fd_pow2<T>(ea - eb);
+#pragma unroll
+                    for (int r = 0; r < R; ++r) v[r] *= f;
+                    kb_prev *= f;
+                    ea = eb;
+                }
+            }
+            const T m = row_dot<T>(xbase + static_cast<int64_t>((g * R) >> lam) * dpad,
+                                   ybase + static_cast<int64_t>(jj >> lam) * dpad, L.nvec) * sub;
+            const T a1 = m * T(0.5);                     // alpha - 1
+            T m2 = T(0);                                 // (1 - beta) = alpha - 1 - m/2
+            if constexpr (ORDER == 2) m2 = m * m * T(1.0 / 12.0);
+            T k00 = kb_prev, k01 = kb;                   // k(I, J), k(I, J+1) for I = gR + r
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                const T k10 = k00 + v[r];                // k(I+1, J)
+                const T sum = k10 + k01;
+                T d2 = a1 * sum;
+                if constexpr (ORDER == 2) d2 = fma(m2, sum + k00, d2);
+                v[r] += d2;
+                const T k11 = k01 + v[r];                // k(I+1, J+1)
+                k00 = k10;
+                k01 = k11;
+            }
+            kb_prev = kb;
+            top = k01;
+            if (g == groups - 1 && jj == nJ - 1) {
+                double res = static_cast<double>(top);
+                if (kRescale) res = ldexp(res, ea);
+                if (!isfinite(res)) record_error(SK_ERR_NONFINITE);
+                write_result(L, item, P, res);
+            }
+            if (kRescale) {
+                const float mag = fmaxf(fabsf(static_cast<float>(kb_prev)), fabsf(static_cast<float>(top)));
+                if (mag > 0x1p64f || (mag < 0x1p-64f && mag > 0.f)) {
+                    const int sh = mag > 0x1p64f ? -64 : 64;
+                    const T f = fd_pow2<T>(sh);
+#pragma unroll
+                    for (int r = 0; r < R; ++r) v[r] *= f;
+                    kb_prev *= f;
+                    top *= f;
+                    ea -= sh;
+                }
+            }
+            eo = ea;
+            if (lane == 31 && gs + 1 < nstrips) {
+                hbuf[jj] = top;
+                if (kRescale) ebuf[jj] = eo;
+                if constexpr (CW > 1) publish_progress(prog + w, gs * nJ + jj + 1);
+            }
+        }
+        __syncwarp();
+        if (++jj == period) {
+            jj = 0;
+            ++sl;
+            gs += CW;
+        }
+    }
+}
+
+template <typename T, int ORDER, int R, int CW>
+__global__ void __launch_bounds__((CW > 1 ? CW : kFwdWarps) * 32) fwd_fd_kernel(Launch L, int64_t buf_cols) {
+    const int wib = threadIdx.x >> 5;
+    const int nw = blockDim.x >> 5;
+    char* block_base = static_cast<char*>(L.scratch) + static_cast<int64_t>(blockIdx.x) * nw * L.scratch_stride;
+    char* own = block_base + wib * L.scratch_stride;
+    if constexpr (CW > 1) {
+        __shared__ long long s_item;
+        __shared__ int s_prog[CW];
+        for (;;) {
+            if (threadIdx.x == 0) s_item = pop_item(L);
+            __syncthreads();
+            const int64_t item = s_item;
+            if (threadIdx.x < CW) s_prog[threadIdx.x] = 0;
+            __syncthreads();  // every warp has read s_item and sees the cleared progress words
+            if (item < 0) return;
+            const PairDesc P = decode_pair(L, item);
+            const int nstrips = P.lx > 0 ? static_cast<int>((((P.lx << L.lam) / R) + 31) >> 5) : 0;
+            if (nstrips < L.coop_min_strips) {  // short pairs from here on: one warp each
+                if (wib == 0 && !trivial_pair(L, item, P))
+                    sweep_fd<T, ORDER, R, 1>(L, item, P, 0, own, own, nullptr, buf_cols);
+                break;
+            }
+            if (!trivial_pair(L, item, P))
+                sweep_fd<T, ORDER, R, CW>(L, item, P, wib, own, block_base + ((wib + CW - 1) % CW) * L.scratch_stride,
+                                          s_prog, buf_cols);
+        }
+    }
     for (;;) {
         const int64_t item = next_item(L);
         if (item < 0) break;
         const PairDesc P = decode_pair(L, item);
-        if (P.lx < 0 || P.ly < 0) {
-            if (lane == 0) {
-                record_error(SK_ERR_BAD_LENGTH);
-                if (P.a >= 0 && P.a < L.X.count && P.b >= 0 && P.b < L.Y.count)
-                    write_result(L, item, P, __longlong_as_double(0x7ff8000000000000LL));
-            }
-            continue;
-        }
-        if (P.lx == 0 || P.ly == 0) {
-            if (lane == 0) write_result(L, item, P, 1.0);
-            continue;
-        }
-        const int lam = L.lam;
-        const int nI = static_cast<int>(P.lx << lam);   // refined node rows 0..nI
-        const int nJ = static_cast<int>(P.ly << lam);   // refined node columns 0..nJ
-        const int groups = nI / R;
-        const int period = nJ > 32 ? nJ : 32;
-        const int nstrips = (groups + 31) >> 5;
-        const int last_lane = (groups - 1) - ((nstrips - 1) << 5);
-        const int nsteps = (nstrips - 1) * period + last_lane + nJ;
-        const T sub = fd_pow2<T>(-2 * lam);
-        const T* xbase = incX + P.xs * dpad;
-        const T* ybase = incY + P.ys * dpad;
-
-        T v[R];     // k(gR + 1 + r, jj) - k(gR + r, jj) for the lane's group g at its column jj
-        T kb_prev = T(1), top = T(0);
-        int ea = 0, eo = 0;
-#pragma unroll
-        for (int r = 0; r < R; ++r) v[r] = T(0);
-        int jj = -lane, s = 0;
-
-        for (int step = 0; step < nsteps; ++step) {
-            T kb = __shfl_up_sync(kFull, top, 1);            // k(gR, jj + 1) from the lane below
-            int eb = kRescale ? __shfl_up_sync(kFull, eo, 1) : 0;
-            const int g = (s << 5) + lane;
-            const bool active = jj >= 0 && jj < nJ && g < groups;
-            if (active) {
-                if (lane == 0) {
-                    if (s == 0) { kb = T(1); eb = 0; }       // row 0: k(s_0, .) = 1
-                    else { kb = hbuf[jj]; if (kRescale) eb = ebuf[jj]; }
-                }
-                if (jj == 0) {                               // column 0: k(., t_0) = 1, so v = 0
-#pragma unroll
-                    for (int r = 0; r < R; ++r) v[r] = T(0);
-                    kb_prev = T(1);
-                    ea = 0;
-                }
-                if (kRescale && ea != eb) {
-                    if (ea > eb) {
-                        kb *= (eb - ea < -126) ? T(0) : fd_pow2<T>(eb - ea);
-                    } else {
-                        const T f = (ea - eb < -126) ? T(0) : fd_pow2<T>(ea - eb);
-#pragma unroll
-                        for (int r = 0; r < R; ++r) v[r] *= f;
-                        kb_prev *= f;
-                        ea = eb;
-                    }
-                }
-                const T m = row_dot<T>(xbase + static_cast<int64_t>((g * R) >> lam) * dpad,
-                                       ybase + static_cast<int64_t>(jj >> lam) * dpad, L.nvec) * sub;
-                const T a1 = m * T(0.5);                     // alpha - 1
-                T m2 = T(0);                                 // (1 - beta) = alpha - 1 - m/2
-                if constexpr (ORDER == 2) m2 = m * m * T(1.0 / 12.0);
-                T k00 = kb_prev, k01 = kb;                   // k(I, J), k(I, J+1) for I = gR + r
-#pragma unroll
-                for (int r = 0; r < R; ++r) {
-                    const T k10 = k00 + v[r];                // k(I+1, J)
-                    const T sum = k10 + k01;
-                    T d2 = a1 * sum;
-                    if constexpr (ORDER == 2) d2 = fma(m2, sum + k00, d2);
-                    v[r] += d2;
-                    const T k11 = k01 + v[r];                // k(I+1, J+1)
-                    k00 = k10;
-                    k01 = k11;
-                }
-                kb_prev = kb;
-                top = k01;
-                if (g == groups - 1 && jj == nJ - 1) {
-                    double res = static_cast<double>(top);
-                    if (kRescale) res = ldexp(res, ea);
-                    if (!isfinite(res)) record_error(SK_ERR_NONFINITE);
-                    write_result(L, item, P, res);
-                }
-                if (kRescale) {
-                    const float mag = fmaxf(fabsf(static_cast<float>(kb_prev)), fabsf(static_cast<float>(top)));
-                    if (mag > 0x1p64f || (mag < 0x1p-64f && mag > 0.f)) {
-                        const int sh = mag > 0x1p64f ? -64 : 64;
-                        const T f = fd_pow2<T>(sh);
-#pragma unroll
-                        for (int r = 0; r < R; ++r) v[r] *= f;
-                        kb_prev *= f;
-                        top *= f;
-                        ea -= sh;
-                    }
-                }
-                eo = ea;
-                if (lane == 31 && s + 1 < nstrips) {
-                    hbuf[jj] = top;
-                    if (kRescale) ebuf[jj] = eo;
-                }
-            }
-            __syncwarp();
-            if (++jj == period) { jj = 0; ++s; }
-        }
+        if (trivial_pair(L, item, P)) continue;
+        sweep_fd<T, ORDER, R, 1>(L, item, P, 0, own, own, nullptr, buf_cols);
     }
 }
 

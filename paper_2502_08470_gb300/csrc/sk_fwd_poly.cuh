@@ -129,211 +129,292 @@ constexpr int fwd_poly_min_blocks() {
     return b < 1 ? 1 : (b > 8 ? 8 : b);
 }
 
-template <typename T, int N, int NE, bool INTERP>
-__global__ void __launch_bounds__(kFwdWarps * 32, (fwd_poly_min_blocks<T, N, NE>()))
-    fwd_poly_kernel(Launch L, int64_t buf_cols) {
+// Warps of a block that sweep one long pair together (strip pipeline); see sweep_poly.
+constexpr int kCoopWarps = 8;
+
+template <typename T, int N, int NE>
+constexpr int fwd_poly_coop_min_blocks() {
+    constexpr int b = fwd_poly_min_blocks<T, N, NE>() * kFwdWarps / kCoopWarps;
+    return b < 1 ? 1 : b;
+}
+
+// Sweep of one pair by one warp (CW = 1), or by warp w of CW warps that share it: warp w runs
+// strips w, w + CW, w + 2 CW, ... in the same overlapped schedule a single warp uses for all of
+// them (local strip sigma starts at local step sigma * P).  Lane 31 of strip g writes its right
+// edges into this warp's hand-off buffer (own_buf); lane 0 of strip g + 1 reads them from the
+// buffer of the warp that ran strip g (prev_buf, the warp's own buffer when CW = 1).  With
+// CW > 1 the hand-off is ordered by the progress words prog[] (publish_progress /
+// wait_progress); a buffer entry of strip g is overwritten by strip g + CW only after strip
+// g + 1 has consumed it, because strip g + CW depends on strip g + 1 through the chain of
+// strips in between.
+template <typename T, int N, int NE, bool INTERP, int CW>
+__device__ __forceinline__ void sweep_poly(const Launch& L, int64_t item, const PairDesc& P, int w, char* own_buf,
+                                           const char* prev_buf, int* prog, int64_t buf_cols,
+                                           unsigned char* tape_stage) {
     constexpr bool kRescale = std::is_same<T, float>::value;
     using V = typename Vec<T>::type;
     constexpr int W = Vec<T>::W;
     constexpr int NB = (N + 1 + W - 1) / W * W;  // hand-off entry width, padded to whole vectors
     const int lane = threadIdx.x & 31;
-    const int64_t slot = static_cast<int64_t>(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    char* base = static_cast<char*>(L.scratch) + slot * L.scratch_stride;
-    V* hbuf = reinterpret_cast<V*>(base);                                         // [buf_cols][NB / W]
-    int* ebuf = reinterpret_cast<int*>(base + buf_cols * NB * static_cast<int64_t>(sizeof(T)));
+    V* hbuf = reinterpret_cast<V*>(own_buf);                                                // [buf_cols][NB / W]
+    int* ebuf = reinterpret_cast<int*>(own_buf + buf_cols * NB * static_cast<int64_t>(sizeof(T)));
+    const V* hprev = reinterpret_cast<const V*>(prev_buf);
+    const int* eprev = reinterpret_cast<const int*>(prev_buf + buf_cols * NB * static_cast<int64_t>(sizeof(T)));
     const int dpad = L.dpad;
     const T* __restrict__ incX = static_cast<const T*>(L.X.inc);
     const T* __restrict__ incY = static_cast<const T*>(L.Y.inc);
+
+    const int lam = L.lam;
+    const int rows = static_cast<int>(P.lx << lam);
+    const int cols = static_cast<int>(P.ly << lam);
+    // Period of a warp's strips.  Alone, a warp starts its next strip as soon as lane 0 is free
+    // (P = max(cols, 32)).  In a cooperative block that overlap can deadlock: a warp whose lane 0
+    // waits on the ring of other warps also holds back its lanes still publishing the previous
+    // strip, which those warps need.  A warp therefore starts strip k + 1 only after finishing
+    // strip k (P = cols + 31), unless the rows are longer than the ring's lag (cols > 31 CW),
+    // where the overlapped schedule keeps every wait pointed at finished work.  A model of this
+    // schedule (tests/test_pipeline_schedule.py) checks the rule and the deadlock it avoids.
+    const int period = CW == 1 ? (cols > 32 ? cols : 32) : (cols > 31 * CW ? cols : cols + 31);
+    const int nstrips = (rows + 31) >> 5;
+    const int last_lane = (rows - 1) - ((nstrips - 1) << 5);
+    // this warp's strips: w, w + CW, ...; the one holding the last row ends at lane last_lane
+    const int nloc = w < nstrips ? (nstrips - 1 - w) / CW + 1 : 0;
+    if (nloc == 0) return;
+    const bool has_last = (nstrips - 1) % CW == w;
+    const int nsteps = (nloc - 1) * period + (has_last ? last_lane : 31) + cols;
+    const T sub = pow2t<T>(-2 * lam);  // M of a sub-cell of P_lambda is M_ij / 4^lambda
+    const T* xbase = incX + P.xs * dpad;
+    const T* ybase = incY + P.ys * dpad;
+
+    T a[N + 1], bo[N + 1];
+#pragma unroll
+    for (int n = 0; n <= N; ++n) { a[n] = T(0); bo[n] = T(0); }
+    int ea = 0, eo = 0;
+    int jj = -lane, sl = 0;                 // column and local strip of this lane
+    int g = w, row = (w << 5) + lane;       // global strip and grid row
+    bool stuck = false;                     // a hand-off wait ran out (CW > 1 only)
+    const T* xrow = xbase + static_cast<int64_t>(min(row, rows - 1) >> lam) * dpad;
+
+    for (int step = 0; step < nsteps; ++step) {
+        T b[N + 1];
+#pragma unroll
+        for (int n = 0; n <= N; ++n) b[n] = __shfl_up_sync(kFull, bo[n], 1);
+        int eb = kRescale ? __shfl_up_sync(kFull, eo, 1) : 0;
+        const bool active = static_cast<unsigned>(jj) < static_cast<unsigned>(cols) && row < rows && sl < nloc;
+        if (active && lane == 0) {
+            if (g == 0) {  // q^{0,j} = e_0 (left boundary k(0, .) = 1)
+#pragma unroll
+                for (int n = 0; n <= N; ++n) b[n] = (n == 0) ? T(1) : T(0);
+                eb = 0;
+            } else {
+                if constexpr (CW > 1) {
+                    if (!stuck && !wait_progress(prog + (w + CW - 1) % CW, (g - 1) * cols + jj + 1)) stuck = true;
+                }
+                const V* src = hprev + static_cast<int64_t>(jj) * (NB / W);
+#pragma unroll
+                for (int v = 0; v < NB / W; ++v) {
+                    const V t = src[v];
+                    const T* tp = reinterpret_cast<const T*>(&t);
+#pragma unroll
+                    for (int q = 0; q < W; ++q)
+                        if (v * W + q <= N) b[v * W + q] = tp[q];
+                }
+                if (kRescale) eb = eprev[jj];
+            }
+        }
+        if (active && jj == 0) {  // p^{i,0} = e_0 (bottom boundary k(., 0) = 1)
+#pragma unroll
+            for (int n = 0; n <= N; ++n) a[n] = (n == 0) ? T(1) : T(0);
+            ea = 0;
+        }
+        if (kRescale && active && ea != eb) {  // bring both inputs to the larger exponent
+            if (ea > eb) {
+                const T f = (eb - ea < -126) ? T(0) : pow2t<T>(eb - ea);
+#pragma unroll
+                for (int n = 0; n <= N; ++n) b[n] *= f;
+            } else {
+                const T f = (ea - eb < -126) ? T(0) : pow2t<T>(ea - eb);
+#pragma unroll
+                for (int n = 0; n <= N; ++n) a[n] *= f;
+                ea = eb;
+            }
+        }
+        // Every lane runs the cell (inactive lanes on a clamped, in-bounds column); only
+        // the results of active lanes are ever consumed.
+        const int jc = min(max(jj, 0), cols - 1);
+        const T M = row_dot<T>(xrow, ybase + static_cast<int64_t>(jc >> lam) * dpad, L.nvec) * sub;
+        if constexpr (!INTERP && CW == 1) {
+            if (L.tape != nullptr) {
+                // Record the cell's inputs (a, b, exponent, M) for the adjoint: each lane writes
+                // its row into a shared-memory slot laid out [vector][lane], then one lane moves
+                // the whole step (32 rows) to the tape with a bulk copy.  Two slots alternate; a
+                // slot is rewritten only after the copy issued from it two steps ago has read it.
+                constexpr int TR = tape_row<T>(N);
+                constexpr int kStepBytes = 32 * TR * static_cast<int>(sizeof(T));
+                V* slot_v = reinterpret_cast<V*>(tape_stage + (step & 1) * kStepBytes);
+                if (lane == 0) bulk_wait_read<1>();
+                __syncwarp();
+#pragma unroll
+                for (int v = 0; v < TR / W; ++v) {
+                    V t;
+                    T* tp = reinterpret_cast<T*>(&t);
+#pragma unroll
+                    for (int q2 = 0; q2 < W; ++q2) {
+                        const int q = v * W + q2;
+                        tp[q2] = q <= N ? a[q] : (q <= 2 * N + 1 ? b[q - N - 1] : T(0));
+                        if (q == 2 * N + 2) {
+                            if constexpr (std::is_same<T, float>::value) tp[q2] = __int_as_float(ea);
+                            else tp[q2] = __longlong_as_double(static_cast<long long>(ea));
+                        }
+                        if (q == 2 * N + 3) tp[q2] = M;
+                    }
+                    slot_v[v * 32 + lane] = t;
+                }
+                fence_proxy_async_smem();
+                __syncwarp();
+                if (lane == 0) {
+                    bulk_store(static_cast<char*>(L.tape) + item * L.tape_stride + static_cast<int64_t>(step) * kStepBytes,
+                               slot_v, kStepBytes);
+                    bulk_commit();
+                }
+            }
+        }
+        T e[NE + 1];
+        build_exp_series<T, NE>(M, L.tau, e);
+        T ct[NE + 1], cr[NE + 1];
+        cell_series<T, N, NE, INTERP>(a, b, e, ct, cr);
+        if constexpr (INTERP) {
+            if (active && row == rows - 1 && jj == cols - 1) {
+                double v = 0.5 * (series_at_one<T, NE>(ct) + series_at_one<T, NE>(cr));
+                if (kRescale) v = ldexp(v, ea);
+                if (!isfinite(v)) record_error(SK_ERR_NONFINITE);
+                write_result(L, item, P, v);
+            }
+        }
+        project<T, N, NE, INTERP>(ct, a);
+        project<T, N, NE, INTERP>(cr, bo);
+        if (kRescale && (step & 3) == 0 && active) {
+            const float mag = fmaxf(fabsf(static_cast<float>(a[0])), fabsf(static_cast<float>(bo[0])));
+            if (mag > 0x1p64f) {
+#pragma unroll
+                for (int n = 0; n <= N; ++n) { a[n] *= pow2t<T>(-64); bo[n] *= pow2t<T>(-64); }
+                ea += 64;
+            } else if (mag < 0x1p-64f) {
+                float full = 0.f;
+#pragma unroll
+                for (int n = 0; n <= N; ++n)
+                    full = fmaxf(full, fmaxf(fabsf(static_cast<float>(a[n])), fabsf(static_cast<float>(bo[n]))));
+                if (full < 0x1p-64f && full > 0.f) {
+#pragma unroll
+                    for (int n = 0; n <= N; ++n) { a[n] *= pow2t<T>(64); bo[n] *= pow2t<T>(64); }
+                    ea -= 64;
+                }
+            }
+        }
+        eo = ea;
+        if (active && lane == 31 && g + 1 < nstrips) {  // hand the right edge to the next strip
+            V* dst = hbuf + static_cast<int64_t>(jj) * (NB / W);
+#pragma unroll
+            for (int v = 0; v < NB / W; ++v) {
+                V t;
+                T* tp = reinterpret_cast<T*>(&t);
+#pragma unroll
+                for (int q = 0; q < W; ++q) tp[q] = (v * W + q <= N) ? bo[v * W + q] : T(0);
+                dst[v] = t;
+            }
+            if (kRescale) ebuf[jj] = eo;
+            if constexpr (CW > 1) publish_progress(prog + w, g * cols + jj + 1);
+        }
+        __syncwarp();
+        if (++jj == period) {
+            jj = 0;
+            ++sl;
+            g += CW;
+            row += 32 * CW;
+            xrow = xbase + static_cast<int64_t>(min(row, rows - 1) >> lam) * dpad;
+        }
+    }
+    if constexpr (!INTERP) {
+        // The last cell was the final step of lane `last_lane` in the warp holding the last
+        // strip; for the approximation scheme its outputs are still in (a, bo):
+        // k_hat = 1/2 sum_n (a_n + b_n) / n!.
+        if (has_last && lane == last_lane) {
+            const double v0 = 0.5 * (series_at_one<T, N>(a) + series_at_one<T, N>(bo));
+            const double v = kRescale ? ldexp(v0, ea) : v0;
+            if (!isfinite(v)) record_error(SK_ERR_NONFINITE);
+            write_result(L, item, P, v);
+            if (L.tape_ek != nullptr) {
+                int e2 = 0;
+                if (v0 != 0.0) frexp(v0, &e2);
+                L.tape_ek[item] = (kRescale ? ea : 0) + e2;
+            }
+        }
+    }
+}
+
+// Result of a pair that has no cells (or bad lengths); false when the pair needs a sweep.
+__device__ __forceinline__ bool trivial_pair(const Launch& L, int64_t item, const PairDesc& P) {
+    if (P.lx < 0 || P.ly < 0) {
+        if ((threadIdx.x & 31) == 0) {
+            record_error(SK_ERR_BAD_LENGTH);
+            if (P.a >= 0 && P.a < L.X.count && P.b >= 0 && P.b < L.Y.count)
+                write_result(L, item, P, __longlong_as_double(0x7ff8000000000000LL));
+        }
+        return true;
+    }
+    if (P.lx == 0 || P.ly == 0) {
+        if ((threadIdx.x & 31) == 0) write_result(L, item, P, 1.0);
+        return true;
+    }
+    return false;
+}
+
+// Forward wavefront, persistent.  CW = 1: blocks of kFwdWarps independent warps, one pair per
+// warp.  CW > 1: blocks of CW warps; the block takes pairs of at least L.coop_min_strips strips
+// together (strip pipeline, sweep_poly<..., CW>), and at the first shorter pair (the queue is
+// ordered by cell count, longest first) its warps fall back to one pair each.
+template <typename T, int N, int NE, bool INTERP, int CW>
+__global__ void __launch_bounds__((CW > 1 ? CW : kFwdWarps) * 32,
+                                  (CW > 1 ? fwd_poly_coop_min_blocks<T, N, NE>() : fwd_poly_min_blocks<T, N, NE>()))
+    fwd_poly_kernel(Launch L, int64_t buf_cols) {
+    const int wib = threadIdx.x >> 5;
+    const int nw = blockDim.x >> 5;
+    char* block_base = static_cast<char*>(L.scratch) + static_cast<int64_t>(blockIdx.x) * nw * L.scratch_stride;
+    char* own = block_base + wib * L.scratch_stride;
     // tape staging (two step slots per warp) in dynamic shared memory, used only with a tape
     extern __shared__ __align__(128) unsigned char fwd_smem[];
-    unsigned char* tape_stage = fwd_smem + (threadIdx.x >> 5) * 2 * fwd_tape_step_bytes<T, N>();
+    unsigned char* tape_stage = fwd_smem + wib * 2 * fwd_tape_step_bytes<T, N>();
 
+    if constexpr (CW > 1) {
+        __shared__ long long s_item;
+        __shared__ int s_prog[CW];
+        for (;;) {
+            if (threadIdx.x == 0) s_item = pop_item(L);
+            __syncthreads();
+            const int64_t item = s_item;
+            if (threadIdx.x < CW) s_prog[threadIdx.x] = 0;
+            __syncthreads();  // every warp has read s_item and sees the cleared progress words
+            if (item < 0) return;
+            const PairDesc P = decode_pair(L, item);
+            const int nstrips = P.lx > 0 ? static_cast<int>(((P.lx << L.lam) + 31) >> 5) : 0;
+            if (nstrips < L.coop_min_strips) {  // short pairs from here on: one warp each
+                if (wib == 0 && !trivial_pair(L, item, P))
+                    sweep_poly<T, N, NE, INTERP, 1>(L, item, P, 0, own, own, nullptr, buf_cols, tape_stage);
+                break;
+            }
+            if (!trivial_pair(L, item, P))
+                sweep_poly<T, N, NE, INTERP, CW>(L, item, P, wib, own, block_base + ((wib + CW - 1) % CW) * L.scratch_stride,
+                                                 s_prog, buf_cols, tape_stage);
+        }
+    }
     for (;;) {
         const int64_t item = next_item(L);
         if (item < 0) break;
         const PairDesc P = decode_pair(L, item);
-        if (P.lx < 0 || P.ly < 0) {
-            if (lane == 0) {
-                record_error(SK_ERR_BAD_LENGTH);
-                if (P.a >= 0 && P.a < L.X.count && P.b >= 0 && P.b < L.Y.count)
-                    write_result(L, item, P, __longlong_as_double(0x7ff8000000000000LL));
-            }
-            continue;
-        }
-        if (P.lx == 0 || P.ly == 0) {
-            if (lane == 0) write_result(L, item, P, 1.0);
-            continue;
-        }
-        const int lam = L.lam;
-        const int rows = static_cast<int>(P.lx << lam);
-        const int cols = static_cast<int>(P.ly << lam);
-        const int period = cols > 32 ? cols : 32;
-        const int nstrips = (rows + 31) >> 5;
-        const int last_lane = (rows - 1) - ((nstrips - 1) << 5);
-        const int nsteps = (nstrips - 1) * period + last_lane + cols;
-        const T sub = pow2t<T>(-2 * lam);  // M of a sub-cell of P_lambda is M_ij / 4^lambda
-        const T* xbase = incX + P.xs * dpad;
-        const T* ybase = incY + P.ys * dpad;
-
-        T a[N + 1], bo[N + 1];
-#pragma unroll
-        for (int n = 0; n <= N; ++n) { a[n] = T(0); bo[n] = T(0); }
-        int ea = 0, eo = 0;
-        int jj = -lane, s = 0, row = lane;
-        const T* xrow = xbase + static_cast<int64_t>(min(row, rows - 1) >> lam) * dpad;
-
-        for (int step = 0; step < nsteps; ++step) {
-            T b[N + 1];
-#pragma unroll
-            for (int n = 0; n <= N; ++n) b[n] = __shfl_up_sync(kFull, bo[n], 1);
-            int eb = kRescale ? __shfl_up_sync(kFull, eo, 1) : 0;
-            const bool active = static_cast<unsigned>(jj) < static_cast<unsigned>(cols) && row < rows;
-            if (active && lane == 0) {
-                if (s == 0) {  // q^{0,j} = e_0 (left boundary k(0, .) = 1)
-#pragma unroll
-                    for (int n = 0; n <= N; ++n) b[n] = (n == 0) ? T(1) : T(0);
-                    eb = 0;
-                } else {
-                    const V* src = hbuf + static_cast<int64_t>(jj) * (NB / W);
-#pragma unroll
-                    for (int v = 0; v < NB / W; ++v) {
-                        const V t = src[v];
-                        const T* tp = reinterpret_cast<const T*>(&t);
-#pragma unroll
-                        for (int w = 0; w < W; ++w)
-                            if (v * W + w <= N) b[v * W + w] = tp[w];
-                    }
-                    if (kRescale) eb = ebuf[jj];
-                }
-            }
-            if (active && jj == 0) {  // p^{i,0} = e_0 (bottom boundary k(., 0) = 1)
-#pragma unroll
-                for (int n = 0; n <= N; ++n) a[n] = (n == 0) ? T(1) : T(0);
-                ea = 0;
-            }
-            if (kRescale && active && ea != eb) {  // bring both inputs to the larger exponent
-                if (ea > eb) {
-                    const T f = (eb - ea < -126) ? T(0) : pow2t<T>(eb - ea);
-#pragma unroll
-                    for (int n = 0; n <= N; ++n) b[n] *= f;
-                } else {
-                    const T f = (ea - eb < -126) ? T(0) : pow2t<T>(ea - eb);
-#pragma unroll
-                    for (int n = 0; n <= N; ++n) a[n] *= f;
-                    ea = eb;
-                }
-            }
-            // Every lane runs the cell (inactive lanes on a clamped, in-bounds column); only
-            // the results of active lanes are ever consumed.
-            const int jc = min(max(jj, 0), cols - 1);
-            const T M = row_dot<T>(xrow, ybase + static_cast<int64_t>(jc >> lam) * dpad, L.nvec) * sub;
-            if constexpr (!INTERP) {
-                if (L.tape != nullptr) {
-                    // Record the cell's inputs (a, b, exponent, M) for the adjoint: each lane writes its row into a
-                    // shared-memory slot laid out [vector][lane], then one lane moves the whole step
-                    // (32 rows) to the tape with a bulk copy.  Two slots alternate; a slot is
-                    // rewritten only after the copy issued from it two steps ago has read it.
-                    constexpr int TR = tape_row<T>(N);
-                    constexpr int kStepBytes = 32 * TR * static_cast<int>(sizeof(T));
-                    V* slot_v = reinterpret_cast<V*>(tape_stage + (step & 1) * kStepBytes);
-                    if (lane == 0) bulk_wait_read<1>();
-                    __syncwarp();
-#pragma unroll
-                    for (int v = 0; v < TR / W; ++v) {
-                        V t;
-                        T* tp = reinterpret_cast<T*>(&t);
-#pragma unroll
-                        for (int w = 0; w < W; ++w) {
-                            const int q = v * W + w;
-                            tp[w] = q <= N ? a[q] : (q <= 2 * N + 1 ? b[q - N - 1] : T(0));
-                            if (q == 2 * N + 2) {
-                                if constexpr (std::is_same<T, float>::value) tp[w] = __int_as_float(ea);
-                                else tp[w] = __longlong_as_double(static_cast<long long>(ea));
-                            }
-                            if (q == 2 * N + 3) tp[w] = M;
-                        }
-                        slot_v[v * 32 + lane] = t;
-                    }
-                    fence_proxy_async_smem();
-                    __syncwarp();
-                    if (lane == 0) {
-                        bulk_store(static_cast<char*>(L.tape) + item * L.tape_stride + static_cast<int64_t>(step) * kStepBytes,
-                                   slot_v, kStepBytes);
-                        bulk_commit();
-                    }
-                }
-            }
-            T e[NE + 1];
-            build_exp_series<T, NE>(M, L.tau, e);
-            T ct[NE + 1], cr[NE + 1];
-            cell_series<T, N, NE, INTERP>(a, b, e, ct, cr);
-            if constexpr (INTERP) {
-                if (active && row == rows - 1 && jj == cols - 1) {
-                    double v = 0.5 * (series_at_one<T, NE>(ct) + series_at_one<T, NE>(cr));
-                    if (kRescale) v = ldexp(v, ea);
-                    if (!isfinite(v)) record_error(SK_ERR_NONFINITE);
-                    write_result(L, item, P, v);
-                }
-            }
-            project<T, N, NE, INTERP>(ct, a);
-            project<T, N, NE, INTERP>(cr, bo);
-            if (kRescale && (step & 3) == 0 && active) {
-                const float mag = fmaxf(fabsf(static_cast<float>(a[0])), fabsf(static_cast<float>(bo[0])));
-                if (mag > 0x1p64f) {
-#pragma unroll
-                    for (int n = 0; n <= N; ++n) { a[n] *= pow2t<T>(-64); bo[n] *= pow2t<T>(-64); }
-                    ea += 64;
-                } else if (mag < 0x1p-64f) {
-                    float full = 0.f;
-#pragma unroll
-                    for (int n = 0; n <= N; ++n)
-                        full = fmaxf(full, fmaxf(fabsf(static_cast<float>(a[n])), fabsf(static_cast<float>(bo[n]))));
-                    if (full < 0x1p-64f && full > 0.f) {
-#pragma unroll
-                        for (int n = 0; n <= N; ++n) { a[n] *= pow2t<T>(64); bo[n] *= pow2t<T>(64); }
-                        ea -= 64;
-                    }
-                }
-            }
-            eo = ea;
-            if (active && lane == 31 && s + 1 < nstrips) {  // hand the right edge to the next strip
-                V* dst = hbuf + static_cast<int64_t>(jj) * (NB / W);
-#pragma unroll
-                for (int v = 0; v < NB / W; ++v) {
-                    V t;
-                    T* tp = reinterpret_cast<T*>(&t);
-#pragma unroll
-                    for (int w = 0; w < W; ++w) tp[w] = (v * W + w <= N) ? bo[v * W + w] : T(0);
-                    dst[v] = t;
-                }
-                if (kRescale) ebuf[jj] = eo;
-            }
-            __syncwarp();
-            if (++jj == period) {
-                jj = 0;
-                ++s;
-                row += 32;
-                xrow = xbase + static_cast<int64_t>(min(row, rows - 1) >> lam) * dpad;
-            }
-        }
-        if constexpr (!INTERP) {
-            // The last cell was the final step of lane `last_lane`; for the approximation scheme
-            // its outputs are still in (a, bo): k_hat = 1/2 sum_n (a_n + b_n) / n!.
-            if (lane == last_lane) {
-                const double v0 = 0.5 * (series_at_one<T, N>(a) + series_at_one<T, N>(bo));
-                const double v = kRescale ? ldexp(v0, ea) : v0;
-                if (!isfinite(v)) record_error(SK_ERR_NONFINITE);
-                write_result(L, item, P, v);
-                if (L.tape_ek != nullptr) {
-                    int e2 = 0;
-                    if (v0 != 0.0) frexp(v0, &e2);
-                    L.tape_ek[item] = (kRescale ? ea : 0) + e2;
-                }
-            }
-        }
+        if (trivial_pair(L, item, P)) continue;
+        sweep_poly<T, N, NE, INTERP, 1>(L, item, P, 0, own, own, nullptr, buf_cols, tape_stage);
     }
-    if (!INTERP && L.tape != nullptr && lane == 0) bulk_wait_all();  // no copy outlives the staging smem
+    if (!INTERP && L.tape != nullptr && (threadIdx.x & 31) == 0) bulk_wait_all();  // no copy outlives the staging smem
 }
-
 
 }  // namespace sk

@@ -26,6 +26,15 @@ SCHEMES = {"fd1": 0, "fd2": 1, "approx": 2, "interp": 3}
 COMPUTE = {"f64": 0, "f32": 1}
 DTYPES = {torch.float64: 0, torch.float32: 1, torch.bfloat16: 2}
 FLAG_SYMMETRIC, FLAG_INCREMENTS, FLAG_UNBIASED, FLAG_NO_SORT, FLAG_TIME_KERNEL = 1, 2, 4, 8, 16
+FLAG_STRIP_PIPELINE, FLAG_NO_STRIP_PIPELINE = 32, 64
+
+
+def _pipe_flags(strip_pipeline) -> int:
+    """None: the library decides; True: every pair of 2+ strips is swept by a block of warps;
+    False: one warp per pair."""
+    if strip_pipeline is None:
+        return 0
+    return FLAG_STRIP_PIPELINE if strip_pipeline else FLAG_NO_STRIP_PIPELINE
 OP_PAIRS, OP_GRAM, OP_BACKWARD, OP_MMD2, OP_BACKWARD_TAPE = 0, 1, 2, 3, 4
 
 
@@ -171,13 +180,15 @@ def _flags(X: Paths, extra=0) -> int:
 
 
 def sigkernel_pairs(X, Y, pair_a, pair_b, scheme="approx", degree=6, dyadic=0, compute="f64", sort=True,
-                    out: torch.Tensor | None = None) -> torch.Tensor:
+                    out: torch.Tensor | None = None, strip_pipeline=None, time_kernel: bool = False) -> torch.Tensor:
     """k_hat(X[pair_a[k]], Y[pair_b[k]]) for every k, as a float64 CUDA tensor."""
     X, Y = as_paths(X), as_paths(Y)
     pa = torch.as_tensor(pair_a, dtype=torch.int64, device="cuda").contiguous()
     pb = torch.as_tensor(pair_b, dtype=torch.int64, device="cuda").contiguous()
     n = pa.numel()
-    opt = _options(scheme, degree, dyadic, compute, _flags(X, 0 if sort else FLAG_NO_SORT))
+    opt = _options(scheme, degree, dyadic, compute,
+                   _flags(X, (0 if sort else FLAG_NO_SORT) | _pipe_flags(strip_pipeline)
+                          | (FLAG_TIME_KERNEL if time_kernel else 0)))
     cX, cY = _cpaths(X), _cpaths(Y)
     out = out if out is not None else torch.empty(n, dtype=torch.float64, device="cuda")
     ws = _workspace(OP_PAIRS, cX, cY, X.d, n, opt)
@@ -189,15 +200,17 @@ def sigkernel_pairs(X, Y, pair_a, pair_b, scheme="approx", degree=6, dyadic=0, c
 
 def sigkernel_gram(X, Y=None, scheme="approx", degree=6, dyadic=0, compute="f64", sort=True,
                    workspace: torch.Tensor | None = None, out: torch.Tensor | None = None,
-                   time_kernel: bool = False) -> torch.Tensor:
+                   time_kernel: bool = False, strip_pipeline=None) -> torch.Tensor:
     """G[a, b] = k_hat(X[a], Y[b]); with Y None (or Y is X) the symmetric Gram of X.
 
-    ``time_kernel`` records CUDA events around the wavefront kernel (see ``last_kernel_ms``)."""
+    ``time_kernel`` records CUDA events around the wavefront kernel (see ``last_kernel_ms``);
+    ``strip_pipeline`` (None / True / False) chooses how long pairs are swept (see the flags
+    SK_FLAG_STRIP_PIPELINE and SK_FLAG_NO_STRIP_PIPELINE)."""
     sym = Y is None or Y is X
     X = as_paths(X)
     Y = X if sym else as_paths(Y)
     flags = _flags(X, (FLAG_SYMMETRIC if sym else 0) | (0 if sort else FLAG_NO_SORT)
-                   | (FLAG_TIME_KERNEL if time_kernel else 0))
+                   | (FLAG_TIME_KERNEL if time_kernel else 0) | _pipe_flags(strip_pipeline))
     opt = _options(scheme, degree, dyadic, compute, flags)
     cX, cY = _cpaths(X), _cpaths(Y)
     G = out if out is not None else torch.empty(X.count, Y.count, dtype=torch.float64, device="cuda")
@@ -207,12 +220,14 @@ def sigkernel_gram(X, Y=None, scheme="approx", degree=6, dyadic=0, compute="f64"
     return G
 
 
-def gram_workspace(X, Y=None, scheme="approx", degree=6, dyadic=0, compute="f64") -> torch.Tensor:
+def gram_workspace(X, Y=None, scheme="approx", degree=6, dyadic=0, compute="f64",
+                   strip_pipeline=None) -> torch.Tensor:
     """A workspace tensor sized for ``sigkernel_gram`` with these shapes (reusable across calls)."""
     sym = Y is None or Y is X
     X = as_paths(X)
     Y = X if sym else as_paths(Y)
-    opt = _options(scheme, degree, dyadic, compute, _flags(X, FLAG_SYMMETRIC if sym else 0))
+    opt = _options(scheme, degree, dyadic, compute,
+                   _flags(X, (FLAG_SYMMETRIC if sym else 0) | _pipe_flags(strip_pipeline)))
     return _workspace(OP_GRAM, _cpaths(X), _cpaths(Y), X.d, -1, opt)
 
 

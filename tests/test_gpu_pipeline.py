@@ -1,0 +1,111 @@
+"""GPU tests of the strip pipeline: long pairs swept by a block of warps, one 32-row strip per warp,
+with the strip hand-off ordered by progress counters in shared memory.
+
+Each cell runs the same arithmetic on the same inputs in the pipelined and the one-warp sweep,
+so the two must agree bit for bit; the oracle pins both on sampled pairs.  The batches mix
+pairs of one strip (one warp each, inside the same launch) with pairs of up to ten strips, and
+the path lengths leave ragged last strips and tiles.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2502_08470_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+sk = pytest.importorskip("paper_2502_08470_gb300.sigkernel")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda_available():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+def _ragged(seed, lengths, d):
+    return [W.brownian(1, n, d, seed=seed + i)[0] for i, n in enumerate(lengths)]
+
+
+LX = [300, 20, 97, 257, 33, 161]   # 1 to 10 strips of 32 rows
+LY = [129, 300, 40, 7, 64]
+
+
+def _paths(seed, lengths, d=3):
+    return sk.Paths.from_list([torch.tensor(x) for x in _ragged(seed, lengths, d)])
+
+
+CASES = [
+    ("approx", 6, 0, "f32", 1e-4),
+    ("approx", 6, 0, "f64", 1e-11),
+    ("approx", 4, 1, "f32", 1e-4),
+    ("interp", 8, 0, "f32", 1e-4),
+    ("interp", 5, 0, "f64", 1e-11),
+    ("fd1", 0, 2, "f32", 1e-4),
+    ("fd2", 0, 3, "f64", 1e-11),
+]
+
+
+@pytest.mark.parametrize("scheme,N,lam,compute,tol", CASES)
+def test_pipelined_gram_is_bitwise_the_one_warp_gram(scheme, N, lam, compute, tol):
+    X = _paths(31, LX)
+    Y = _paths(61, LY)
+    kw = dict(scheme=scheme, degree=max(N, 2), dyadic=lam, compute=compute)
+    G1 = sk.sigkernel_gram(X, Y, strip_pipeline=False, **kw)
+    G2 = sk.sigkernel_gram(X, Y, strip_pipeline=True, **kw)
+    torch.cuda.synchronize()
+    assert sk.device_status() == 0
+    assert torch.equal(G1, G2)
+    # sampled pairs against the oracle, including the 10-strip one
+    Xs, Ys = _ragged(31, LX, 3), _ragged(61, LY, 3)
+    pa, pb = [0, 3, 5, 2], [1, 0, 4, 2]
+    ref = oracle.pairs([Xs[a] for a in pa], [Ys[b] for b in pb], list(range(4)), list(range(4)), scheme,
+                       max(N, 2), lam)
+    got = G2.cpu().numpy()[pa, pb]
+    assert np.max(np.abs(got - ref) / np.abs(ref)) < tol
+
+
+@pytest.mark.parametrize("compute", ["f32", "f64"])
+def test_pipelined_symmetric_gram(compute):
+    X = _paths(91, [200, 31, 130, 64, 300])
+    G1 = sk.sigkernel_gram(X, None, compute=compute, strip_pipeline=False)
+    G2 = sk.sigkernel_gram(X, None, compute=compute, strip_pipeline=True)
+    torch.cuda.synchronize()
+    assert sk.device_status() == 0
+    assert torch.equal(G1, G2)
+    assert torch.equal(G2, G2.T)
+
+
+def test_pipelined_pairs_list_with_repeats():
+    X = _paths(101, [400, 50])
+    Y = _paths(131, [380, 90, 33])
+    pa, pb = [0, 0, 1, 0, 0], [0, 1, 2, 0, 2]
+    o1 = sk.sigkernel_pairs(X, Y, pa, pb, compute="f32", strip_pipeline=False)
+    o2 = sk.sigkernel_pairs(X, Y, pa, pb, compute="f32", strip_pipeline=True)
+    torch.cuda.synchronize()
+    assert sk.device_status() == 0
+    assert torch.equal(o1, o2)
+    assert o2[0].item() == o2[3].item()
+
+
+def test_long_pairs_take_the_pipeline_by_default():
+    """Few pairs of 1025-point paths (32 strips each): the library pipelines them on its own
+    (the launch has 8-warp blocks) and the results equal the one-warp sweep (itself pinned to the
+    oracle in the forward tests)."""
+    rng = np.random.default_rng(5)
+    X = W.oscillatory(4, 1025, 4, seed=5)
+    Y = W.oscillatory(4, 1025, 4, seed=6)
+    Xt, Yt = torch.tensor(X, device="cuda"), torch.tensor(Y, device="cuda")
+    pa = rng.integers(0, 4, 6)
+    pb = rng.integers(0, 4, 6)
+    auto = sk.sigkernel_pairs(Xt, Yt, pa, pb, scheme="interp", degree=8, compute="f32", time_kernel=True)
+    torch.cuda.synchronize()
+    t_auto = sk.last_kernel_ms()
+    one = sk.sigkernel_pairs(Xt, Yt, pa, pb, scheme="interp", degree=8, compute="f32", strip_pipeline=False,
+                             time_kernel=True)
+    torch.cuda.synchronize()
+    t_one = sk.last_kernel_ms()
+    assert sk.device_status() == 0
+    assert torch.equal(auto, one)
+    assert t_auto < t_one  # 8 warps per pair instead of 1
