@@ -116,6 +116,22 @@ def parse():
     return args
 
 
+def max_over_ranks(ms: float, dist, device) -> float:
+    """The slowest rank's timed milliseconds (every rank gets it); `ms` itself with one rank."""
+    if dist is None:
+        return ms
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(cells_per_rank: int, world: int, steps: int, total_ms: float) -> float:
+    """Whole-job cell-updates/s: every rank solves its own Gram of `cells_per_rank` cells per step
+    (weak scaling), and the job takes the slowest rank's time."""
+    return cells_per_rank * world * steps / (total_ms / 1e3)
+
+
 def workload(rank: int, n: int = NX, points: int = L):
     from paper_2502_08470_gb300 import workloads as W
     X = W.brownian(NX, points, D, seed=3 + 1000 * rank)[:n]
@@ -337,13 +353,9 @@ def main():
     with ClockSampler(local) as clk:
         step_ms, kf_ms, kb_ms, wall = run("f32", args.steps, max(args.warmup, 3))
     clocks = clk.summary()
-    total_ms = float(sum(step_ms))
-    if dist is not None:
-        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(float(sum(step_ms)), dist, dev)
     ms_per_step = total_ms / args.steps
-    value = cells * world * args.steps / (total_ms / 1e3)
+    value = job_throughput(cells, world, args.steps, total_ms)
     g32 = G.cpu().numpy()[pa, pb]
     status = sk.device_status()
     kf = statistics.mean(kf_ms)

@@ -95,8 +95,10 @@ enum {
                                        each) with a block of warps, one strip per warp in a
                                        pipeline, instead of one warp per pair */
     SK_FLAG_NO_STRIP_PIPELINE = 64  /* forward: always one warp per pair.  With neither flag the
-                                       library pipelines long pairs when the batch is too small to
-                                       fill the GPU with one warp per pair (no effect with a tape) */
+                                       library pipelines every pair of 2 or more strips when some
+                                       pair has 32 or more strips and the batch is too small to
+                                       fill the GPU with one warp per pair.  Neither applies to the
+                                       tape forward or to the adjoints (one warp per pair) */
 };
 
 typedef struct {

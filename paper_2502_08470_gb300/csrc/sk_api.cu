@@ -224,7 +224,10 @@ int plan_forward(const sk_paths* X, const sk_paths* Y, int32_t d, int32_t dtype,
             if (ck && cper >= 1) {
                 p.kern = ck;
                 p.coop = true;
-                p.coop_min_strips = forced ? 2 : 2 * kCoopWarps;
+                // once a batch is pipelined at all, every pair of two or more strips is (measured on
+                // 4096 pairs of 64..4096-point paths: 101 ms against 197 ms with only pairs of
+                // 2 kCoopWarps strips or more)
+                p.coop_min_strips = 2;
                 p.threads = kCoopWarps * 32;
                 per_sm = cper;
             }

@@ -91,7 +91,7 @@ def test_pipelined_pairs_list_with_repeats():
 
 def test_long_pairs_take_the_pipeline_by_default():
     """Few pairs of 1025-point paths (32 strips each): the library pipelines them on its own
-    (the launch has 8-warp blocks) and the results equal the one-warp sweep (itself pinned to the
+    (the launch has 16-warp blocks) and the results equal the one-warp sweep (itself pinned to the
     oracle in the forward tests)."""
     rng = np.random.default_rng(5)
     X = W.oscillatory(4, 1025, 4, seed=5)
@@ -108,4 +108,4 @@ def test_long_pairs_take_the_pipeline_by_default():
     t_one = sk.last_kernel_ms()
     assert sk.device_status() == 0
     assert torch.equal(auto, one)
-    assert t_auto < t_one  # 8 warps per pair instead of 1
+    assert t_auto < t_one  # 16 warps per pair instead of 1
