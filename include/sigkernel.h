@@ -111,7 +111,9 @@ typedef struct {
                                  interpolation projection; 0 = the build's value for the compute
                                  mode (6 for FP32, 10 for FP64); any other value must equal it */
     int32_t flags;            /* SK_FLAG_* */
-    int32_t warps_per_block;  /* launch shape override: 0 = the autotuned choice */
+    int32_t warps_per_block;  /* forward launch shape: 1, 2 or 4 warps per block for one warp per
+                                 pair; 0 = the shape sigkernel_autotune chose for this shape of
+                                 call, else the default (4) */
     int32_t reserved;         /* must be 0 */
 } sk_options;
 
@@ -211,6 +213,29 @@ int sigkernel_backward_tape(const sk_paths* X, const sk_paths* Y, int32_t d, int
                             const sk_options* opt, const void* tape, size_t tape_bytes,
                             const double* grad_out, double* grad_X, double* grad_Y,
                             void* workspace, size_t workspace_bytes, void* stream);
+
+/*
+ * sigkernel_autotune -- choose the launch shape of a forward call (sigkernel_pairs when pair_a is
+ * non-NULL, else sigkernel_gram; same arguments) by timing the candidates on these inputs:
+ * one warp per pair in blocks of 1, 2 or 4 warps, and the strip pipeline (blocks of 16 warps
+ * sharing each pair of two or more strips) when some pair spans two strips.  Each candidate runs
+ * once to warm up, then `trials` (1..1000) timed times on `stream`; `out` is overwritten with the
+ * results.  The call allocates its own workspace (stream-ordered) and returns after the runs have
+ * finished on the device.
+ *   best     written with *opt except warps_per_block and the strip-pipeline flags, which name
+ *            the winner explicitly (pass it to later calls to reuse the choice anywhere).
+ *   best_ms  the winner's fastest call in milliseconds (NULL to skip).
+ * The winner is also remembered in this process for calls of the same shape (scheme, degree,
+ * lambda, compute mode, d, call kind, path counts, max_len, pair count, device) whose
+ * warps_per_block is 0 and that set no strip-pipeline flag.  Workspace sizes follow the chosen
+ * shape, so query sigkernel_workspace_size after tuning.  sigkernel_autotune_clear forgets every
+ * remembered choice.  The paper has no counterpart: this is a facility of the library.
+ */
+int sigkernel_autotune(const sk_paths* X, const sk_paths* Y, int32_t d, int32_t dtype,
+                       const int64_t* pair_a, const int64_t* pair_b, int64_t npairs,
+                       const sk_options* opt, double* out, int32_t trials, sk_options* best,
+                       float* best_ms, void* stream);
+void sigkernel_autotune_clear(void);
 
 /*
  * sigkernel_mmd2 -- squared maximum mean discrepancy between the path sets A and B with the

@@ -5,6 +5,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <string>
 
@@ -30,6 +31,33 @@ int fail(int code, const char* fmt, ...) {
     va_end(ap);
     t_last_error = buf;
     return code;
+}
+
+// Launch shapes chosen by sigkernel_autotune, per shape of call (used when a call leaves
+// warps_per_block at 0 and sets no strip-pipeline flag).
+struct TuneKey {
+    int dev, scheme, degree, dyadic, compute, dpad, mode;
+    int64_t xmax, ymax, xcount, ycount, npairs;
+    bool operator<(const TuneKey& o) const {
+        const int64_t a[] = {dev, scheme, degree, dyadic, compute, dpad, mode, xmax, ymax, xcount, ycount, npairs};
+        const int64_t b[] = {o.dev, o.scheme, o.degree, o.dyadic, o.compute, o.dpad, o.mode, o.xmax, o.ymax, o.xcount,
+                             o.ycount, o.npairs};
+        for (int i = 0; i < 12; ++i)
+            if (a[i] != b[i]) return a[i] < b[i];
+        return false;
+    }
+};
+struct TuneChoice {
+    int wpb;   // warps per block of the one-warp-per-pair kernel
+    int pipe;  // 1: strip pipeline, -1: none
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, TuneChoice> g_tune;
+
+TuneKey tune_key(int dev, const sk_paths* X, const sk_paths* Y, const sk_options* o, int dpad, int mode,
+                 int64_t npairs) {
+    return TuneKey{dev, o->scheme, o->degree, o->dyadic, o->compute, dpad, mode,
+                   X->max_len, Y->max_len, X->count, Y->count, npairs};
 }
 
 #define SK_CUDA(call)                                                                         \
@@ -154,8 +182,8 @@ int check_options(const sk_options* o, int32_t d, int32_t dtype) {
             return fail(SK_ERR_UNSUPPORTED, "interp_extra %d: this build keeps J = %d for this compute mode",
                         o->interp_extra, j);
     }
-    if (o->warps_per_block != 0 && o->warps_per_block != kFwdWarps)
-        return fail(SK_ERR_UNSUPPORTED, "warps_per_block %d (this build: 0 or %d)", o->warps_per_block, kFwdWarps);
+    if (o->warps_per_block != 0 && o->warps_per_block != 1 && o->warps_per_block != 2 && o->warps_per_block != 4)
+        return fail(SK_ERR_UNSUPPORTED, "warps_per_block %d (this build: 0, 1, 2 or 4)", o->warps_per_block);
     if (o->flags & ~(SK_FLAG_SYMMETRIC | SK_FLAG_INCREMENTS | SK_FLAG_UNBIASED | SK_FLAG_NO_SORT | SK_FLAG_TIME_KERNEL |
                      SK_FLAG_STRIP_PIPELINE | SK_FLAG_NO_STRIP_PIPELINE))
         return fail(SK_ERR_INVALID_ARG, "unknown flag bits 0x%x", o->flags);
@@ -201,22 +229,39 @@ int plan_forward(const sk_paths* X, const sk_paths* Y, int32_t d, int32_t dtype,
         width = (o->degree + 1 + hw - 1) / hw * hw;
     }
     if (!p.kern) return fail(SK_ERR_UNSUPPORTED, "no kernel for scheme %d order %d compute %d", o->scheme, o->degree, o->compute);
-    p.threads = kFwdWarps * 32;
-    p.coop = false;
-    p.coop_min_strips = 0;
+    // Launch shape.  Explicit requests (warps_per_block, the strip-pipeline flags) win; otherwise a
+    // shape that sigkernel_autotune measured for this shape of call; otherwise the defaults.
+    int wpb_req = 0, pipe_req = 0;  // pipe_req: 1 strip pipeline, -1 none, 0 the default rule
+    if (allow_coop) {
+        wpb_req = o->warps_per_block;
+        if (o->flags & SK_FLAG_STRIP_PIPELINE) pipe_req = 1;
+        if (o->flags & SK_FLAG_NO_STRIP_PIPELINE) pipe_req = -1;
+    }
     int dev = 0, sms = 0, per_sm = 0;
     SK_CUDA(cudaGetDevice(&dev));
+    if (allow_coop && wpb_req == 0 && pipe_req == 0) {
+        const TuneKey key = tune_key(dev, X, Y, o, p.dpad, mode, npairs);
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        auto it = g_tune.find(key);
+        if (it != g_tune.end()) {
+            wpb_req = it->second.wpb;
+            pipe_req = it->second.pipe;
+        }
+    }
+    p.threads = (wpb_req ? wpb_req : kFwdWarps) * 32;
+    p.coop = false;
+    p.coop_min_strips = 0;
     SK_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     SK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, p.kern, p.threads, 0));
     if (per_sm < 1) per_sm = 1;
     // Strip pipeline: a pair of many strips swept by one warp is a serial chain of
     // nstrips x cols steps; when the batch cannot fill the GPU with one warp per pair, long pairs
     // are swept by blocks of kCoopWarps warps instead (one strip per warp, pipelined).
-    if (allow_coop && !(o->flags & SK_FLAG_NO_STRIP_PIPELINE)) {
+    if (allow_coop && pipe_req >= 0) {
         const int rows_per_lane = poly ? 1 : (lam < 4 ? (1 << lam) : 16);
         const int64_t max_strips = (((X->max_len << lam) / rows_per_lane) + 31) / 32;
-        const bool forced = (o->flags & SK_FLAG_STRIP_PIPELINE) != 0;
-        const int64_t resident = static_cast<int64_t>(sms) * per_sm * kFwdWarps;
+        const bool forced = pipe_req > 0;
+        const int64_t resident = static_cast<int64_t>(sms) * per_sm * (p.threads / 32);
         if (max_strips >= 2 && (forced || (max_strips >= 2 * kCoopWarps && npairs < 4 * resident))) {
             const void* ck = kernel_for(true);
             int cper = 0;
@@ -890,6 +935,94 @@ int run_mmd2(const sk_paths* A, const sk_paths* Bp, int32_t d, int32_t dtype, co
 using namespace sk;
 
 extern "C" {
+
+int sigkernel_autotune(const sk_paths* X, const sk_paths* Y, int32_t d, int32_t dtype, const int64_t* pair_a,
+                       const int64_t* pair_b, int64_t npairs, const sk_options* opt, double* out, int32_t trials,
+                       sk_options* best, float* best_ms, void* stream) {
+    t_last_error.clear();
+    if (!opt || !X || !Y || !out || !best) return fail(SK_ERR_INVALID_ARG, "NULL argument");
+    if (trials < 1 || trials > 1000) return fail(SK_ERR_INVALID_ARG, "trials %d outside [1, 1000]", trials);
+    if (pair_a && (!pair_b || npairs < 0)) return fail(SK_ERR_INVALID_ARG, "bad pair list");
+    const bool gram = pair_a == nullptr;
+    const bool sym = gram && (opt->flags & SK_FLAG_SYMMETRIC);
+    const int mode = gram ? (sym ? kGramUpper : kGramFull) : kPairsList;
+    const int64_t n = gram ? gram_items(X, Y, sym) : npairs;
+    const int64_t ldo = gram ? Y->count : 0;
+    const int strip = SK_FLAG_STRIP_PIPELINE | SK_FLAG_NO_STRIP_PIPELINE | SK_FLAG_TIME_KERNEL;
+    struct Cand {
+        int wpb, pipe;
+    };
+    Cand cands[4] = {{1, -1}, {2, -1}, {4, -1}, {0, 1}};
+    int ncand = 3;
+    size_t ws_bytes = 0;
+    int rc;
+    for (int c = 0; c < 4; ++c) {
+        sk_options co = *opt;
+        co.flags = (opt->flags & ~strip) | (cands[c].pipe > 0 ? SK_FLAG_STRIP_PIPELINE : SK_FLAG_NO_STRIP_PIPELINE);
+        co.warps_per_block = cands[c].wpb;
+        Plan p;
+        if ((rc = plan_forward(X, Y, d, dtype, &co, mode, n, p, true)) != SK_OK) return rc;
+        if (c == 3 && p.coop) ncand = 4;  // the pipeline only where some pair spans two strips
+        if (c < 3 || p.coop) ws_bytes = std::max(ws_bytes, p.total);
+    }
+    if (n == 0) return fail(SK_ERR_INVALID_ARG, "nothing to tune: no pairs");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    void* ws = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    SK_CUDA(cudaMallocAsync(&ws, ws_bytes, st));
+    float best_t = -1.f;
+    int best_c = 0;
+    rc = SK_OK;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        rc = fail(SK_ERR_CUDA, "cudaEventCreate failed");
+    }
+    for (int c = 0; c < ncand && rc == SK_OK; ++c) {
+        sk_options co = *opt;
+        co.flags = (opt->flags & ~strip) | (cands[c].pipe > 0 ? SK_FLAG_STRIP_PIPELINE : SK_FLAG_NO_STRIP_PIPELINE);
+        co.warps_per_block = cands[c].wpb;
+        float t_min = -1.f;
+        for (int t = 0; t <= trials && rc == SK_OK; ++t) {  // t = 0 warms up
+            if (cudaEventRecord(e0, st) != cudaSuccess) { rc = fail(SK_ERR_CUDA, "cudaEventRecord failed"); break; }
+            rc = run_forward(X, Y, d, dtype, &co, mode, pair_a, pair_b, n, out, ldo, ws, ws_bytes, stream);
+            if (rc != SK_OK) break;
+            if (cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) {
+                rc = fail(SK_ERR_CUDA, "timing a candidate failed");
+                break;
+            }
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (t > 0 && (t_min < 0.f || ms < t_min)) t_min = ms;
+        }
+        if (rc == SK_OK && (best_t < 0.f || t_min < best_t)) {
+            best_t = t_min;
+            best_c = c;
+        }
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaFreeAsync(ws, st);
+    if (rc != SK_OK) return rc;
+    int dev = 0;
+    SK_CUDA(cudaGetDevice(&dev));
+    const int vw = opt->compute == SK_COMPUTE_F32 ? 4 : 2;
+    const int dpad = (d + vw - 1) / vw * vw;
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        g_tune[tune_key(dev, X, Y, opt, dpad, mode, n)] =
+            TuneChoice{cands[best_c].wpb ? cands[best_c].wpb : kFwdWarps, cands[best_c].pipe};
+    }
+    *best = *opt;
+    best->flags = (opt->flags & ~strip) |
+                  (cands[best_c].pipe > 0 ? SK_FLAG_STRIP_PIPELINE : SK_FLAG_NO_STRIP_PIPELINE);
+    best->warps_per_block = cands[best_c].wpb;
+    if (best_ms) *best_ms = best_t;
+    return SK_OK;
+}
+
+void sigkernel_autotune_clear(void) {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    g_tune.clear();
+}
 
 int sigkernel_version(void) { return 100; }
 

@@ -88,6 +88,9 @@ def load_library():
         lib.sigkernel_forward_tape.argtypes = [PP, PP, I32, I32, P, P, I64, PO, P, P, SZ, P, SZ, P]
         lib.sigkernel_backward_tape.restype = ctypes.c_int
         lib.sigkernel_backward_tape.argtypes = [PP, PP, I32, I32, P, P, I64, PO, P, SZ, P, P, P, P, SZ, P]
+        lib.sigkernel_autotune.restype = ctypes.c_int
+        lib.sigkernel_autotune.argtypes = [PP, PP, I32, I32, P, P, I64, PO, P, I32, PO, ctypes.POINTER(ctypes.c_float), P]
+        lib.sigkernel_autotune_clear.restype = None
         lib.sigkernel_last_kernel_ms.restype = ctypes.c_float
         lib.sigkernel_device_status.restype = ctypes.c_int
         lib.sigkernel_device_status.argtypes = [P]
@@ -229,6 +232,40 @@ def gram_workspace(X, Y=None, scheme="approx", degree=6, dyadic=0, compute="f64"
     opt = _options(scheme, degree, dyadic, compute,
                    _flags(X, (FLAG_SYMMETRIC if sym else 0) | _pipe_flags(strip_pipeline)))
     return _workspace(OP_GRAM, _cpaths(X), _cpaths(Y), X.d, -1, opt)
+
+
+def autotune(X, Y=None, pair_a=None, pair_b=None, scheme="approx", degree=6, dyadic=0, compute="f32",
+             trials=3, sort=True):
+    """Time the forward launch shapes on these inputs (``sigkernel_autotune``) and remember the
+    fastest for later calls of the same shape that leave the shape to the library.  Returns
+    ``(shape, ms)`` with ``shape = {"warps_per_block": w, "strip_pipeline": bool}``."""
+    pairs = pair_a is not None
+    sym = not pairs and (Y is None or Y is X)
+    X = as_paths(X)
+    Y = X if (Y is None or Y is X) else as_paths(Y)
+    cX, cY = _cpaths(X), _cpaths(Y)
+    if pairs:
+        pa = torch.as_tensor(pair_a, dtype=torch.int64, device="cuda").contiguous()
+        pb = torch.as_tensor(pair_b, dtype=torch.int64, device="cuda").contiguous()
+        n, pa_ptr, pb_ptr = pa.numel(), pa.data_ptr(), pb.data_ptr()
+        out = torch.empty(n, dtype=torch.float64, device="cuda")
+    else:
+        n, pa_ptr, pb_ptr = 0, None, None
+        out = torch.empty(X.count, Y.count, dtype=torch.float64, device="cuda")
+    opt = _options(scheme, degree, dyadic, compute,
+                   _flags(X, (FLAG_SYMMETRIC if sym else 0) | (0 if sort else FLAG_NO_SORT)))
+    best = _Options()
+    ms = ctypes.c_float(0)
+    _check(load_library().sigkernel_autotune(ctypes.byref(cX), ctypes.byref(cY), X.d, _dtype_code(X, Y), pa_ptr,
+                                             pb_ptr, n, ctypes.byref(opt), out.data_ptr(), int(trials),
+                                             ctypes.byref(best), ctypes.byref(ms), _stream_ptr()))
+    return {"warps_per_block": best.warps_per_block,
+            "strip_pipeline": bool(best.flags & FLAG_STRIP_PIPELINE)}, float(ms.value)
+
+
+def autotune_clear():
+    """Forget every launch shape chosen by ``autotune`` in this process."""
+    load_library().sigkernel_autotune_clear()
 
 
 def sigkernel_backward(grad_out, X, Y=None, pair_a=None, pair_b=None, scheme="approx", degree=6, dyadic=0,
