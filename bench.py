@@ -39,7 +39,7 @@ D = 8
 DEGREE = 6
 CELLS_PER_PAIR = (L - 1) * (L - 1)
 CELLS = NX * NY * CELLS_PER_PAIR
-PARTS = ("f32", "ckpt", "fwd", "f64", "e2e", "cpu")
+PARTS = ("f32", "ckpt", "fwd", "f64", "e2e", "osc", "uneven", "mmd", "cpu")
 SM_COUNT = 152
 FP32_LANES = 128
 SM_MAX_MHZ = 2070.0
@@ -107,8 +107,9 @@ def parse():
     ap.add_argument("--len", type=int, default=L,
                     help="points per path (shorter paths, for profiling runs that must hold only a few GB)")
     ap.add_argument("--parts", default=",".join(PARTS),
-                    help="comma list: f32 (headline fwd+bwd step), fwd (forward only), f64 (FP64 forward), "
-                         "e2e, cpu")
+                    help="comma list: f32 (headline fwd+bwd step), ckpt (checkpointing adjoint), fwd (forward "
+                         "only), f64 (FP64 forward), e2e, osc (oscillatory pairs), uneven (uneven batch), mmd "
+                         "(MMD^2 fwd+bwd), cpu")
     args = ap.parse_args()
     args.parts = set(args.parts.split(","))
     if args.no_cpu_baseline:
@@ -269,6 +270,7 @@ def main():
         return
 
     from paper_2502_08470_gb300 import sigkernel as sk
+    from paper_2502_08470_gb300 import workloads as W
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     nx = args.nx
@@ -458,6 +460,87 @@ def main():
                        "d2h_bytes_per_step": int((Gh.numel() + gXh.numel() + gYh.numel()) * 8),
                        "ms_per_step": statistics.mean(e2e_ms)}
         tape_buf[0] = None
+
+    tape_buf[0] = None
+    torch.cuda.empty_cache()
+
+    def timed_steps(fn, steps, warmup):
+        """Per-call milliseconds (CUDA events on the current stream, L2 flushed before each call)."""
+        for _ in range(warmup):
+            fn()
+        torch.cuda.synchronize()
+        ms = []
+        for _ in range(steps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            fn()
+            e1.record()
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        return statistics.mean(ms)
+
+    if "osc" in args.parts:  # 64 pairs of 1025-point oscillatory paths, d=4 (few long pairs: strip pipeline)
+        Xo = torch.tensor(W.oscillatory(64, 1025, 4, seed=5 + 1000 * rank), device=dev)
+        Yo = torch.tensor(W.oscillatory(64, 1025, 4, seed=6 + 1000 * rank), device=dev)
+        io = torch.arange(64, dtype=torch.int64, device=dev)
+        cells_o = 64 * 1024 * 1024
+        osc = {"workload": "64 pairs, 1025 points on [0,1], d=4, sin(w t + phi) + N(0,1e-3), w ~ U(10,200)"}
+        for scheme, N, lam, comp in (("interp", 8, 0, "f32"), ("interp", 8, 0, "f64"), ("fd1", 2, 0, "f32"),
+                                     ("fd1", 2, 2, "f32"), ("fd1", 2, 4, "f32"), ("fd1", 2, 6, "f32")):
+            o = torch.empty(64, dtype=torch.float64, device=dev)
+            f = lambda: sk.sigkernel_pairs(Xo, Yo, io, io, scheme=scheme, degree=N, dyadic=lam, compute=comp, out=o)
+            t = timed_steps(f, 1 if lam == 6 else 3, 1)
+            key = f"{scheme}{N if scheme == 'interp' else ''}_lam{lam}_{comp}"
+            osc[key] = {"ms": t, "cell_updates_per_s": cells_o / (t / 1e3),
+                        "sub_cell_updates_per_s": cells_o * 4 ** lam / (t / 1e3)}
+            if key == "interp8_lam0_f32":
+                o32 = o.clone()
+            if key == "interp8_lam0_f64":
+                osc["interp8_f32_mape_vs_fp64_gpu"] = float(((o32 - o).abs() / o.abs()).mean())
+        line["oscillatory"] = osc
+        del Xo, Yo
+
+    if "uneven" in args.parts:  # 4096 pairs, lengths log-uniform in [64, 4096], d=16, BF16: autotuned + graph
+        Xs = W.uneven(4096, 64, 4096, 16, seed=6 + 1000 * rank)
+        Ys = W.uneven(4096, 64, 4096, 16, seed=7 + 1000 * rank)
+        PX = sk.Paths.from_list(Xs, dtype=torch.bfloat16)
+        PY = sk.Paths.from_list(Ys, dtype=torch.bfloat16)
+        cells_u = float(sum((len(x) - 1) * (len(y) - 1) for x, y in zip(Xs, Ys)))
+        iu = torch.arange(4096, dtype=torch.int64, device=dev)
+        ou = torch.empty(4096, dtype=torch.float64, device=dev)
+        sk.autotune_clear()
+        shape, tuned_ms = sk.autotune(PX, PY, iu, iu, compute="f32", trials=1)
+        t_tuned = timed_steps(lambda: sk.sigkernel_pairs(PX, PY, iu, iu, compute="f32", out=ou), 3, 1)
+        t_one = timed_steps(lambda: sk.sigkernel_pairs(PX, PY, iu, iu, compute="f32", out=ou,
+                                                       strip_pipeline=False), 2, 1)
+        graph = torch.cuda.CUDAGraph()
+        gs = torch.cuda.Stream()
+        with torch.cuda.stream(gs):
+            with torch.cuda.graph(graph, stream=gs):
+                sk.sigkernel_pairs(PX, PY, iu, iu, compute="f32", out=ou)
+        t_graph = timed_steps(graph.replay, 3, 1)
+        line["uneven_batch"] = {
+            "workload": "4096 pairs, lengths log-uniform in [64,4096], d=16, BF16 points, approx N=6, FP32 cells",
+            "cells": cells_u, "autotuned_shape": shape, "ms": t_tuned,
+            "cell_updates_per_s": cells_u / (t_tuned / 1e3), "graph_replay_ms": t_graph,
+            "graph_cell_updates_per_s": cells_u / (t_graph / 1e3), "one_warp_per_pair_ms": t_one}
+        sk.autotune_clear()
+        del PX, PY, graph
+
+    if "mmd" in args.parts:  # MMD^2 fwd+bwd: 256 + 256 paths, 513 points, d=32, FP32, checkpointing adjoint
+        Am = torch.tensor(W.brownian(256, 513, 32, seed=7 + 1000 * rank), device=dev)
+        Bm = torch.tensor(W.brownian(256, 513, 32, seed=8 + 1000 * rank, drift=0.5, vol=1.2), device=dev)
+        cells_m = (256 * 257 // 2 * 2 + 256 * 256) * 512 * 512
+        t_f = timed_steps(lambda: sk.sigkernel_mmd2(Am, Bm, degree=6, compute="f32"), 2, 1)
+        t_fb = timed_steps(lambda: sk.sigkernel_mmd2(Am, Bm, degree=6, compute="f32", grads=True), 2, 1)
+        line["mmd2"] = {"workload": "256 + 256 paths, 513 points, d=32 (Brownian vs drift 0.5, vol 1.2), approx N=6, "
+                                    "FP32, symmetric K_AA/K_BB + K_AB, checkpointing adjoint",
+                        "cells": cells_m, "forward_ms": t_f, "fwd_bwd_ms": t_fb,
+                        "forward_cell_updates_per_s": cells_m / (t_f / 1e3),
+                        "fwd_bwd_cell_updates_per_s": cells_m / (t_fb / 1e3)}
+        del Am, Bm
 
     if rank == 0:
         if "cpu" in args.parts:
