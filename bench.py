@@ -536,7 +536,8 @@ def main():
         t_f = timed_steps(lambda: sk.sigkernel_mmd2(Am, Bm, degree=6, compute="f32"), 2, 1)
         t_fb = timed_steps(lambda: sk.sigkernel_mmd2(Am, Bm, degree=6, compute="f32", grads=True), 2, 1)
         line["mmd2"] = {"workload": "256 + 256 paths, 513 points, d=32 (Brownian vs drift 0.5, vol 1.2), approx N=6, "
-                                    "FP32, symmetric K_AA/K_BB + K_AB, checkpointing adjoint",
+                                    "FP32, symmetric K_AA/K_BB + K_AB, tiled M; gradients from forward tapes in "
+                                    "chunks of pairs (tape <= 48 GiB per chunk)",
                         "cells": cells_m, "forward_ms": t_f, "fwd_bwd_ms": t_fb,
                         "forward_cell_updates_per_s": cells_m / (t_f / 1e3),
                         "fwd_bwd_cell_updates_per_s": cells_m / (t_fb / 1e3)}

@@ -94,11 +94,15 @@ enum {
     SK_FLAG_STRIP_PIPELINE = 32,    /* forward: sweep every pair of 2 or more strips (32 grid rows
                                        each) with a block of warps, one strip per warp in a
                                        pipeline, instead of one warp per pair */
-    SK_FLAG_NO_STRIP_PIPELINE = 64  /* forward: always one warp per pair.  With neither flag the
+    SK_FLAG_NO_STRIP_PIPELINE = 64, /* forward: always one warp per pair.  With neither flag the
                                        library pipelines every pair of 2 or more strips when some
                                        pair has 32 or more strips and the batch is too small to
                                        fill the GPU with one warp per pair.  Neither applies to the
                                        tape forward or to the adjoints (one warp per pair) */
+    SK_FLAG_NO_TILED_M = 128        /* forward, polynomial schemes in FP32: form each cell's M from
+                                       its two increment rows.  By default, with d > 8, each warp
+                                       first computes a strip's M_ij for all columns at once (the
+                                       same values bit for bit) */
 };
 
 typedef struct {
@@ -132,8 +136,9 @@ enum { SK_OP_PAIRS = 0, SK_OP_GRAM = 1, SK_OP_BACKWARD = 2, SK_OP_MMD2 = 3, SK_O
  * sigkernel_workspace_size -- writes to *bytes the device workspace the call `op` needs for
  * these shapes and options and returns SK_OK, or returns the SK_ERR_* code the call itself would
  * return for these arguments (then *bytes = 0).  `npairs` is the pair count for SK_OP_PAIRS /
- * SK_OP_BACKWARD with a pair list, ignored otherwise (pass -1 for a Gram backward).  Queries
- * properties of the current device (SM count, occupancy); no memory traffic.
+ * SK_OP_BACKWARD / SK_OP_BACKWARD_TAPE with a pair list (pass -1 for a Gram); for SK_OP_MMD2 it
+ * is 0 for the value alone and nonzero for the value with gradients (X = A, Y = B); ignored
+ * otherwise.  Queries properties of the current device (SM count, occupancy); no memory traffic.
  */
 int sigkernel_workspace_size(int32_t op, const sk_paths* X, const sk_paths* Y, int32_t d,
                              int64_t npairs, const sk_options* opt, size_t* bytes);
@@ -217,13 +222,14 @@ int sigkernel_backward_tape(const sk_paths* X, const sk_paths* Y, int32_t d, int
 /*
  * sigkernel_autotune -- choose the launch shape of a forward call (sigkernel_pairs when pair_a is
  * non-NULL, else sigkernel_gram; same arguments) by timing the candidates on these inputs:
- * one warp per pair in blocks of 1, 2 or 4 warps, and the strip pipeline (blocks of 16 warps
- * sharing each pair of two or more strips) when some pair spans two strips.  Each candidate runs
+ * one warp per pair in blocks of 1, 2 or 4 warps (each with and without the tiled M where it
+ * applies), and the strip pipeline (blocks of 16 warps sharing each pair of two or more strips)
+ * when some pair spans two strips.  Each candidate runs
  * once to warm up, then `trials` (1..1000) timed times on `stream`; `out` is overwritten with the
  * results.  The call allocates its own workspace (stream-ordered) and returns after the runs have
  * finished on the device.
- *   best     written with *opt except warps_per_block and the strip-pipeline flags, which name
- *            the winner explicitly (pass it to later calls to reuse the choice anywhere).
+ *   best     written with *opt except warps_per_block and the strip-pipeline and tiled-M flags,
+ *            which name the winner explicitly (pass it to later calls to reuse the choice).
  *   best_ms  the winner's fastest call in milliseconds (NULL to skip).
  * The winner is also remembered in this process for calls of the same shape (scheme, degree,
  * lambda, compute mode, d, call kind, path counts, max_len, pair count, device) whose
@@ -245,6 +251,12 @@ void sigkernel_autotune_clear(void);
  *   out       device double [4]: MMD^2, mean K_AA, mean K_BB, mean K_AB (as used above)
  *   grad_A/B  device double with A's / B's row layout, or NULL: d MMD^2 / d rows, OVERWRITTEN.
  * K_AA and K_BB are solved as symmetric Grams; the reduction runs in FP64 on the device.
+ * Gradients (polynomial approximation only) run the adjoint from forward tapes: each Gram block is
+ * solved in chunks of pairs whose tape is at most 48 GiB, the chunk's forward recording the tape
+ * and the tape adjoint following at once with the block's constant weights.  A block whose paths
+ * are so long that a chunk cannot fill the GPU uses the checkpointing adjoint of
+ * sigkernel_backward instead (d <= 32).  The workspace (SK_OP_MMD2 with npairs != 0) includes the
+ * tape.
  */
 int sigkernel_mmd2(const sk_paths* A, const sk_paths* B, int32_t d, int32_t dtype,
                    const sk_options* opt, double* out, double* grad_A, double* grad_B,

@@ -50,6 +50,7 @@ struct TuneKey {
 struct TuneChoice {
     int wpb;   // warps per block of the one-warp-per-pair kernel
     int pipe;  // 1: strip pipeline, -1: none
+    int mt;    // 1: tiled M where eligible, -1: per-cell M
 };
 std::mutex g_tune_mu;
 std::map<TuneKey, TuneChoice> g_tune;
@@ -144,6 +145,10 @@ struct Plan {
     int blocks;          // persistent grid
     bool coop;           // cooperative-block kernel (strip pipeline for long pairs)
     int coop_min_strips; // strips from which a pair is swept by a whole block
+    bool mtile;          // tiled M (wide increments, polynomial schemes)
+    int64_t mtile_cols;  // columns of one warp's M strip buffer
+    int64_t mtile_off;   // byte offset of that buffer in a warp slot
+    int smem_x;          // dynamic shared memory of the tiled-M x rows per block
     int64_t slot_bytes;  // scratch per warp slot
     int64_t buf_cols;    // hand-off columns per warp slot
     // workspace layout (byte offsets)
@@ -185,7 +190,7 @@ int check_options(const sk_options* o, int32_t d, int32_t dtype) {
     if (o->warps_per_block != 0 && o->warps_per_block != 1 && o->warps_per_block != 2 && o->warps_per_block != 4)
         return fail(SK_ERR_UNSUPPORTED, "warps_per_block %d (this build: 0, 1, 2 or 4)", o->warps_per_block);
     if (o->flags & ~(SK_FLAG_SYMMETRIC | SK_FLAG_INCREMENTS | SK_FLAG_UNBIASED | SK_FLAG_NO_SORT | SK_FLAG_TIME_KERNEL |
-                     SK_FLAG_STRIP_PIPELINE | SK_FLAG_NO_STRIP_PIPELINE))
+                     SK_FLAG_STRIP_PIPELINE | SK_FLAG_NO_STRIP_PIPELINE | SK_FLAG_NO_TILED_M))
         return fail(SK_ERR_INVALID_ARG, "unknown flag bits 0x%x", o->flags);
     if ((o->flags & SK_FLAG_STRIP_PIPELINE) && (o->flags & SK_FLAG_NO_STRIP_PIPELINE))
         return fail(SK_ERR_INVALID_ARG, "SK_FLAG_STRIP_PIPELINE and SK_FLAG_NO_STRIP_PIPELINE together");
@@ -219,8 +224,13 @@ int plan_forward(const sk_paths* X, const sk_paths* Y, int32_t d, int32_t dtype,
 
     const bool poly = o->scheme == SK_POLY_APPROX || o->scheme == SK_POLY_INTERP;
     int width = 1;  // values handed from strip to strip per refined column
+    // Tiled M (FP32 polynomial schemes): with wide increments (padded d >= 12) a cell that forms M
+    // from two increment rows is bound by those loads; each warp builds a strip's M at once
+    // instead (produce_m_strip).
+    const bool mt_eligible = poly && p.T == 1 && p.dpad >= 12;
+    p.mtile = mt_eligible && !(o->flags & SK_FLAG_NO_TILED_M);
     auto kernel_for = [&](bool coop) -> const void* {
-        return poly ? fwd_poly_kernel_ptr(p.T, o->scheme == SK_POLY_INTERP, o->degree, coop)
+        return poly ? fwd_poly_kernel_ptr(p.T, o->scheme == SK_POLY_INTERP, o->degree, coop, p.mtile)
                     : fwd_fd_kernel_ptr(p.T, o->scheme == SK_FD2 ? 2 : 1, lam, coop);
     };
     p.kern = kernel_for(false);
@@ -239,20 +249,33 @@ int plan_forward(const sk_paths* X, const sk_paths* Y, int32_t d, int32_t dtype,
     }
     int dev = 0, sms = 0, per_sm = 0;
     SK_CUDA(cudaGetDevice(&dev));
-    if (allow_coop && wpb_req == 0 && pipe_req == 0) {
+    if (allow_coop && wpb_req == 0 && pipe_req == 0 && !(o->flags & SK_FLAG_NO_TILED_M)) {
         const TuneKey key = tune_key(dev, X, Y, o, p.dpad, mode, npairs);
         std::lock_guard<std::mutex> lock(g_tune_mu);
         auto it = g_tune.find(key);
         if (it != g_tune.end()) {
             wpb_req = it->second.wpb;
             pipe_req = it->second.pipe;
+            if (it->second.mt < 0 && p.mtile) {
+                p.mtile = false;
+                p.kern = kernel_for(false);
+            }
         }
     }
     p.threads = (wpb_req ? wpb_req : kFwdWarps) * 32;
     p.coop = false;
     p.coop_min_strips = 0;
+    const int esize = p.T ? 4 : 8;
+    p.smem_x = 0;
+    auto xsmem = [&](int threads) { return p.mtile ? (threads / 32) * 32 * p.dpad * esize : 0; };
+    auto occupancy = [&](const void* k, int threads, int* per) -> int {
+        const int sm = xsmem(threads);
+        if (sm > 48 * 1024) SK_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+        SK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(per, k, threads, sm));
+        return SK_OK;
+    };
     SK_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    SK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, p.kern, p.threads, 0));
+    if ((rc = occupancy(p.kern, p.threads, &per_sm)) != SK_OK) return rc;
     if (per_sm < 1) per_sm = 1;
     // Strip pipeline: a pair of many strips swept by one warp is a serial chain of
     // nstrips x cols steps; when the batch cannot fill the GPU with one warp per pair, long pairs
@@ -263,9 +286,15 @@ int plan_forward(const sk_paths* X, const sk_paths* Y, int32_t d, int32_t dtype,
         const bool forced = pipe_req > 0;
         const int64_t resident = static_cast<int64_t>(sms) * per_sm * (p.threads / 32);
         if (max_strips >= 2 && (forced || (max_strips >= 2 * kCoopWarps && npairs < 4 * resident))) {
+            // Pipelined warps are all on the pipeline's critical path, so a strip's tiled-M build
+            // delays the whole chain: per-cell M measured faster there (4096 pairs of 64..4096-point
+            // paths, d = 16: 101 against 118 ms).
+            const bool mt_one = p.mtile;
+            p.mtile = false;
             const void* ck = kernel_for(true);
             int cper = 0;
-            if (ck) SK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&cper, ck, kCoopWarps * 32, 0));
+            if (ck && (rc = occupancy(ck, kCoopWarps * 32, &cper)) != SK_OK) return rc;
+            if (!(ck && cper >= 1)) p.mtile = mt_one;
             if (ck && cper >= 1) {
                 p.kern = ck;
                 p.coop = true;
@@ -283,8 +312,11 @@ int plan_forward(const sk_paths* X, const sk_paths* Y, int32_t d, int32_t dtype,
     int64_t cap = static_cast<int64_t>(sms) * per_sm;
     p.blocks = static_cast<int>(want < cap ? (want > 0 ? want : 1) : cap);
     p.buf_cols = (Y->max_len << lam) + 1;
-    const int esize = p.T ? 4 : 8;
     p.slot_bytes = static_cast<int64_t>(align256(static_cast<size_t>(p.buf_cols * width * esize + p.buf_cols * 4)));
+    p.smem_x = xsmem(p.threads);
+    p.mtile_cols = std::max<int64_t>(Y->max_len << lam, 1);
+    p.mtile_off = p.slot_bytes;
+    if (p.mtile) p.slot_bytes += static_cast<int64_t>(align256(static_cast<size_t>(2 * 32 * p.mtile_cols * esize)));
 
     size_t off = 0;
     p.off_incx = off;
@@ -351,7 +383,7 @@ int plan_tape(const sk_paths* X, const sk_paths* Y, const sk_options* o, int T, 
 
 int run_forward(const sk_paths* X, const sk_paths* Y, int32_t d, int32_t dtype, const sk_options* o, int mode,
                 const int64_t* pa, const int64_t* pb, int64_t npairs, double* out, int64_t ldo, void* ws,
-                size_t ws_bytes, void* stream, void* tape = nullptr, size_t tape_bytes = 0) {
+                size_t ws_bytes, void* stream, void* tape = nullptr, size_t tape_bytes = 0, int64_t item_base = 0) {
     Plan p;
     int rc = plan_forward(X, Y, d, dtype, o, mode, npairs, p, tape == nullptr);
     if (rc != SK_OK) return rc;
@@ -383,6 +415,7 @@ int run_forward(const sk_paths* X, const sk_paths* Y, int32_t d, int32_t dtype, 
 
     Launch L;
     memset(&L, 0, sizeof(L));
+    L.item_base = item_base;
     L.X = PathSet{base + p.off_incx, X->offsets, X->count, X->max_len, X->rows_total};
     L.Y = PathSet{base + p.off_incy, Y->offsets, Y->count, Y->max_len, Y->rows_total};
     L.nvec = p.nvec;
@@ -404,6 +437,9 @@ int run_forward(const sk_paths* X, const sk_paths* Y, int32_t d, int32_t dtype, 
     L.tape_stride = static_cast<int64_t>(tp.stride);
     L.tape_ek = tape ? static_cast<int*>(tape) : nullptr;
     L.coop_min_strips = p.coop_min_strips;
+    L.mtile = p.mtile ? 1 : 0;
+    L.mtile_cols = static_cast<int32_t>(p.mtile_cols);
+    L.mtile_off = p.mtile_off;
     SK_CUDA(cudaMemsetAsync(base + p.off_queue, 0, 256 + align256(2 * 65 * sizeof(unsigned int)), st));
     if (!(o->flags & SK_FLAG_NO_SORT) && npairs > 1) {
         unsigned int* hist = reinterpret_cast<unsigned int*>(base + p.off_hist);
@@ -418,12 +454,12 @@ int run_forward(const sk_paths* X, const sk_paths* Y, int32_t d, int32_t dtype, 
     }
     int64_t buf_cols = p.buf_cols;
     void* args[] = {&L, &buf_cols};
-    int smem = 0;
+    int smem = p.smem_x;  // tiled-M x rows
     if (tape) {  // two staging slots per warp for the tape's bulk copies
         const int step_bytes = 32 * (p.T ? tape_row<float>(o->degree) * 4 : tape_row<double>(o->degree) * 8);
-        smem = kFwdWarps * 2 * step_bytes;
-        if (smem > 48 * 1024) SK_CUDA(cudaFuncSetAttribute(p.kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+        smem += (p.threads / 32) * 2 * step_bytes;
     }
+    if (smem > 48 * 1024) SK_CUDA(cudaFuncSetAttribute(p.kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     const bool timed = (o->flags & SK_FLAG_TIME_KERNEL) != 0;
     if (timed) {
         if (!t_ev0) SK_CUDA(cudaEventCreate(&t_ev0));
@@ -712,37 +748,17 @@ int plan_backward_tape(const sk_paths* X, const sk_paths* Y, int32_t d, int32_t 
     return SK_OK;
 }
 
-int run_backward_tape(const sk_paths* X, const sk_paths* Y, int32_t d, int32_t dtype, const sk_options* o,
-                      const int64_t* pa, const int64_t* pb, int64_t npairs, const void* tape, size_t tape_bytes,
-                      const double* gout, double* gX, double* gY, void* ws, size_t ws_bytes, void* stream) {
-    const bool gram = (pa == nullptr);
-    const bool sym = gram && (o->flags & SK_FLAG_SYMMETRIC);
-    const int mode = gram ? (sym ? kGramUpper : kGramFull) : kPairsList;
-    if (gram) npairs = gram_items(X, Y, sym);
-    TapeBwdPlan b;
-    int rc = plan_backward_tape(X, Y, d, dtype, o, mode, npairs, b);
-    if (rc != SK_OK) return rc;
-    if (b.f.same_xy && gY && gY != gX)
-        return fail(SK_ERR_INVALID_ARG, "X and Y are the same paths: pass grad_Y = NULL or grad_Y = grad_X");
-    if (!tape || tape_bytes < b.t.total) return fail(SK_ERR_WORKSPACE, "tape missing or smaller than %zu bytes", b.t.total);
-    if (npairs == 0) return SK_OK;
-    if (!gout) return fail(SK_ERR_INVALID_ARG, "grad_out is NULL");
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
-    bool own = false;
-    if (!ws) {
-        SK_CUDA(cudaMallocAsync(&ws, b.total, st));
-        own = true;
-    } else if (ws_bytes < b.total) {
-        return fail(SK_ERR_WORKSPACE, "workspace %zu bytes < %zu required", ws_bytes, b.total);
-    }
-    char* base = reinterpret_cast<char*>((reinterpret_cast<uintptr_t>(ws) + 255) / 256 * 256);
+// Adjoint from a tape over work items item_base .. item_base + npairs - 1 (Gram modes) or the
+// given pair list: increments, ordering, the tape adjoint and the contraction; gradients with
+// respect to increments are ADDED to gincX / gincY (which may alias).  `base` is the aligned
+// workspace laid out by plan_backward_tape for npairs items.
+int launch_backward_tape(const sk_paths* X, const sk_paths* Y, int32_t d, int32_t dtype, const sk_options* o,
+                         int mode, const int64_t* pa, const int64_t* pb, int64_t npairs, int64_t item_base,
+                         const void* tape, const double* gout, int64_t ldo, const TapeBwdPlan& b, char* base,
+                         double* gincX, double* gincY, cudaStream_t st) {
     const Plan& p = b.f;
     const int inc_mode = (o->flags & SK_FLAG_INCREMENTS) ? 1 : 0;
-    double* gincX = reinterpret_cast<double*>(base + b.off_gincx);
-    double* gincY = reinterpret_cast<double*>(base + b.off_gincy);
-    SK_CUDA(cudaMemsetAsync(gincX, 0, static_cast<size_t>(X->rows_total) * p.dpad * sizeof(double), st));
-    if (!p.same_xy) SK_CUDA(cudaMemsetAsync(gincY, 0, static_cast<size_t>(Y->rows_total) * p.dpad * sizeof(double), st));
-    rc = p.T ? launch_increments<float>(X, d, dtype, inc_mode, p.dpad, base + p.off_incx, st)
+    int rc = p.T ? launch_increments<float>(X, d, dtype, inc_mode, p.dpad, base + p.off_incx, st)
              : launch_increments<double>(X, d, dtype, inc_mode, p.dpad, base + p.off_incx, st);
     if (rc == SK_OK && !p.same_xy)
         rc = p.T ? launch_increments<float>(Y, d, dtype, inc_mode, p.dpad, base + p.off_incy, st)
@@ -759,15 +775,18 @@ int run_backward_tape(const sk_paths* X, const sk_paths* Y, int32_t d, int32_t d
     L.lam = o->dyadic;
     L.mode = mode;
     L.npairs = npairs;
+    L.item_base = item_base;
     L.pair_a = pa;
     L.pair_b = pb;
     L.queue = reinterpret_cast<unsigned int*>(base + p.off_queue);
-    L.ldo = Y->count;
+    L.ldo = ldo;
     L.scratch = base + b.off_scratch;
     L.scratch_stride = b.slot_bytes;
     L.tau = 1.0f;
-    L.tape = const_cast<char*>(static_cast<const char*>(tape)) + b.t.ek_bytes;
-    L.tape_stride = static_cast<int64_t>(b.t.stride);
+    TapePlan tp;  // the tape as the forward laid it out for these npairs items
+    if ((rc = plan_tape(X, Y, o, p.T, npairs, tp)) != SK_OK) return rc;
+    L.tape = const_cast<char*>(static_cast<const char*>(tape)) + tp.ek_bytes;
+    L.tape_stride = static_cast<int64_t>(tp.stride);
     L.tape_ek = const_cast<int*>(static_cast<const int*>(tape));
     B.gout = gout;
     B.gincX = gincX;
@@ -804,6 +823,42 @@ int run_backward_tape(const sk_paths* X, const sk_paths* Y, int32_t d, int32_t d
     }
     SK_CUDA(cudaLaunchKernel(b.ckern, dim3(b.cblocks), dim3(kContractWarps * 32), args,
                              static_cast<size_t>(b.csmem), st));
+    return SK_OK;
+}
+
+int run_backward_tape(const sk_paths* X, const sk_paths* Y, int32_t d, int32_t dtype, const sk_options* o,
+                      const int64_t* pa, const int64_t* pb, int64_t npairs, const void* tape, size_t tape_bytes,
+                      const double* gout, double* gX, double* gY, void* ws, size_t ws_bytes, void* stream) {
+    const bool gram = (pa == nullptr);
+    const bool sym = gram && (o->flags & SK_FLAG_SYMMETRIC);
+    const int mode = gram ? (sym ? kGramUpper : kGramFull) : kPairsList;
+    if (gram) npairs = gram_items(X, Y, sym);
+    TapeBwdPlan b;
+    int rc = plan_backward_tape(X, Y, d, dtype, o, mode, npairs, b);
+    if (rc != SK_OK) return rc;
+    if (b.f.same_xy && gY && gY != gX)
+        return fail(SK_ERR_INVALID_ARG, "X and Y are the same paths: pass grad_Y = NULL or grad_Y = grad_X");
+    if (!tape || tape_bytes < b.t.total) return fail(SK_ERR_WORKSPACE, "tape missing or smaller than %zu bytes", b.t.total);
+    if (npairs == 0) return SK_OK;
+    if (!gout) return fail(SK_ERR_INVALID_ARG, "grad_out is NULL");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    bool own = false;
+    if (!ws) {
+        SK_CUDA(cudaMallocAsync(&ws, b.total, st));
+        own = true;
+    } else if (ws_bytes < b.total) {
+        return fail(SK_ERR_WORKSPACE, "workspace %zu bytes < %zu required", ws_bytes, b.total);
+    }
+    char* base = reinterpret_cast<char*>((reinterpret_cast<uintptr_t>(ws) + 255) / 256 * 256);
+    const Plan& p = b.f;
+    const int inc_mode = (o->flags & SK_FLAG_INCREMENTS) ? 1 : 0;
+    double* gincX = reinterpret_cast<double*>(base + b.off_gincx);
+    double* gincY = reinterpret_cast<double*>(base + b.off_gincy);
+    SK_CUDA(cudaMemsetAsync(gincX, 0, static_cast<size_t>(X->rows_total) * p.dpad * sizeof(double), st));
+    if (!p.same_xy) SK_CUDA(cudaMemsetAsync(gincY, 0, static_cast<size_t>(Y->rows_total) * p.dpad * sizeof(double), st));
+    if ((rc = launch_backward_tape(X, Y, d, dtype, o, mode, pa, pb, npairs, 0, tape, gout, Y->count, b, base, gincX,
+                                   gincY, st)) != SK_OK)
+        return rc;
     if ((rc = convert_grad(X, d, p.dpad, inc_mode, gincX, gX, st)) != SK_OK) return rc;
     if (!p.same_xy && (rc = convert_grad(Y, d, p.dpad, inc_mode, gincY, gY, st)) != SK_OK) return rc;
     if (own) SK_CUDA(cudaFreeAsync(ws, st));
@@ -846,63 +901,133 @@ __global__ void fill_weights_kernel(double* W, int64_t n, int64_t m, double v, i
         W[i] = (zero_diag && (i / m) == (i % m)) ? 0.0 : v;
 }
 
-int run_mmd2(const sk_paths* A, const sk_paths* Bp, int32_t d, int32_t dtype, const sk_options* o, double* out,
-             double* gA, double* gB, void* ws, size_t ws_bytes, void* stream) {
-    if (!A || !Bp || !o || !out) return fail(SK_ERR_INVALID_ARG, "NULL argument");
+// MMD^2 planning, shared by sigkernel_mmd2 and sigkernel_workspace_size.  The three Gram blocks
+// (K_AA and K_BB symmetric, K_AB full) run one after another in one workspace.  With gradients
+// (polynomial approximation) each block runs in chunks of items: the forward records a tape of
+// the chunk and the tape adjoint runs from it at once, with the block's constant upstream weights
+// (MMD^2 is linear in the Gram entries).  A chunk's tape is at most kMmdTapeBudget bytes, and a
+// chunk smaller than a block is a whole number of the adjoint's resident warps.  When the budget
+// holds fewer items than half the adjoint's resident warps (very long paths), the block uses the
+// checkpointing adjoint instead, which keeps only antidiagonal checkpoints.
+constexpr size_t kMmdTapeBudget = size_t(48) << 30;
+
+struct MmdPlan {
+    bool grads;
+    sk_options os, of;     // options of the symmetric blocks and of the cross block
+    int64_t items[3];      // K_AA (upper), K_BB (upper), K_AB (full)
+    int64_t chunk[3];      // items per chunk (gradients)
+    bool tape[3];          // gradients from chunked tapes, else the checkpointing adjoint
+    Plan f[3];
+    TapeBwdPlan tb[3];
+    BwdPlan cb[3];
+    size_t gram_bytes, w_bytes, ginc_a, ginc_bytes, tape_bytes, sub, total;
+};
+
+int plan_mmd2(const sk_paths* A, const sk_paths* Bp, int32_t d, int32_t dtype, const sk_options* o, bool grads,
+              MmdPlan& m) {
+    if (!A || !Bp || !o) return fail(SK_ERR_INVALID_ARG, "NULL argument");
     if (A->count < 1 || Bp->count < 1) return fail(SK_ERR_INVALID_ARG, "MMD^2 needs non-empty path sets");
     const bool unb = (o->flags & SK_FLAG_UNBIASED) != 0;
     if (unb && (A->count < 2 || Bp->count < 2)) return fail(SK_ERR_INVALID_ARG, "unbiased MMD^2 needs >= 2 paths per set");
-    sk_options os = *o;
-    os.flags = (o->flags & (SK_FLAG_INCREMENTS | SK_FLAG_NO_SORT | SK_FLAG_TIME_KERNEL | SK_FLAG_STRIP_PIPELINE | SK_FLAG_NO_STRIP_PIPELINE)) | SK_FLAG_SYMMETRIC;
-    sk_options of = os;
-    of.flags &= ~SK_FLAG_SYMMETRIC;
-    const bool grads = gA || gB;
-    // size every sub-call; they run one after another on the same stream in one workspace
-    Plan paa, pbb, pab;
-    BwdPlan baa, bbb, bab;
+    if (grads && o->scheme != SK_POLY_APPROX)
+        return fail(SK_ERR_UNSUPPORTED, "MMD^2 gradients need the polynomial approximation scheme");
+    m.grads = grads;
+    m.os = *o;
+    m.os.flags = (o->flags & (SK_FLAG_INCREMENTS | SK_FLAG_NO_SORT | SK_FLAG_TIME_KERNEL | SK_FLAG_STRIP_PIPELINE |
+                              SK_FLAG_NO_STRIP_PIPELINE | SK_FLAG_NO_TILED_M)) | SK_FLAG_SYMMETRIC;
+    m.of = m.os;
+    m.of.flags &= ~SK_FLAG_SYMMETRIC;
+    const sk_paths* xs[3] = {A, Bp, A};
+    const sk_paths* ys[3] = {A, Bp, Bp};
+    const int modes[3] = {kGramUpper, kGramUpper, kGramFull};
+    m.items[0] = gram_items(A, A, true);
+    m.items[1] = gram_items(Bp, Bp, true);
+    m.items[2] = gram_items(A, Bp, false);
     int rc;
-    if ((rc = plan_forward(A, A, d, dtype, &os, kGramUpper, gram_items(A, A, true), paa, true)) != SK_OK) return rc;
-    if ((rc = plan_forward(Bp, Bp, d, dtype, &os, kGramUpper, gram_items(Bp, Bp, true), pbb, true)) != SK_OK) return rc;
-    if ((rc = plan_forward(A, Bp, d, dtype, &of, kGramFull, gram_items(A, Bp, false), pab, true)) != SK_OK) return rc;
-    size_t sub = std::max(paa.total, std::max(pbb.total, pab.total));
-    if (grads) {
-        if ((rc = plan_backward(A, A, d, dtype, &os, kGramUpper, gram_items(A, A, true), baa)) != SK_OK) return rc;
-        if ((rc = plan_backward(Bp, Bp, d, dtype, &os, kGramUpper, gram_items(Bp, Bp, true), bbb)) != SK_OK) return rc;
-        if ((rc = plan_backward(A, Bp, d, dtype, &of, kGramFull, gram_items(A, Bp, false), bab)) != SK_OK) return rc;
-        sub = std::max(sub, std::max(baa.total, std::max(bbb.total, bab.total)));
+    m.sub = 0;
+    m.tape_bytes = 0;
+    for (int k = 0; k < 3; ++k) {
+        const sk_options* ok = k < 2 ? &m.os : &m.of;
+        if (!grads) {
+            m.chunk[k] = m.items[k];
+            if ((rc = plan_forward(xs[k], ys[k], d, dtype, ok, modes[k], m.items[k], m.f[k], true)) != SK_OK) return rc;
+            m.sub = std::max(m.sub, m.f[k].total);
+            continue;
+        }
+        Plan p1;
+        if ((rc = plan_forward(xs[k], ys[k], d, dtype, ok, modes[k], 1, p1)) != SK_OK) return rc;
+        TapePlan t1;
+        if ((rc = plan_tape(xs[k], ys[k], ok, p1.T, 1, t1)) != SK_OK) return rc;
+        TapeBwdPlan whole;
+        if ((rc = plan_backward_tape(xs[k], ys[k], d, dtype, ok, modes[k], m.items[k], whole)) != SK_OK) return rc;
+        const int64_t resident = std::max<int64_t>(1, static_cast<int64_t>(whole.f.blocks) * kFwdWarps);
+        int64_t c = std::max<int64_t>(1, static_cast<int64_t>(kMmdTapeBudget / std::max<size_t>(t1.stride, 1)));
+        if (c < m.items[k] && c > resident) c -= c % resident;
+        m.chunk[k] = std::min(c, m.items[k]);
+        m.tape[k] = m.chunk[k] == m.items[k] || 2 * m.chunk[k] >= resident;
+        if (!m.tape[k]) {  // checkpointing adjoint over the whole block
+            m.chunk[k] = m.items[k];
+            if ((rc = plan_forward(xs[k], ys[k], d, dtype, ok, modes[k], m.items[k], m.f[k], true)) != SK_OK) return rc;
+            if ((rc = plan_backward(xs[k], ys[k], d, dtype, ok, modes[k], m.items[k], m.cb[k])) != SK_OK) return rc;
+            m.sub = std::max(m.sub, std::max(m.f[k].total, m.cb[k].total));
+            continue;
+        }
+        if ((rc = plan_forward(xs[k], ys[k], d, dtype, ok, modes[k], m.chunk[k], m.f[k])) != SK_OK) return rc;
+        if ((rc = plan_backward_tape(xs[k], ys[k], d, dtype, ok, modes[k], m.chunk[k], m.tb[k])) != SK_OK) return rc;
+        TapePlan tc;
+        if ((rc = plan_tape(xs[k], ys[k], ok, p1.T, m.chunk[k], tc)) != SK_OK) return rc;
+        m.tape_bytes = std::max(m.tape_bytes, tc.total);
+        m.sub = std::max(m.sub, std::max(m.f[k].total, m.tb[k].total));
     }
     const int64_t na = A->count, nb = Bp->count;
-    const size_t gram_bytes = align256((na * na + nb * nb + na * nb) * sizeof(double));
-    const size_t w_bytes = grads ? gram_bytes : 0;
-    const int dpad = paa.dpad;
-    const size_t ginc_bytes = grads ? align256(static_cast<size_t>(A->rows_total) * dpad * 8) +
-                                          align256(static_cast<size_t>(Bp->rows_total) * dpad * 8)
-                                    : 0;
-    const size_t total = gram_bytes + w_bytes + ginc_bytes + sub + 512;
+    const int dpad = m.f[0].dpad;
+    m.gram_bytes = align256((na * na + nb * nb + na * nb) * sizeof(double));
+    m.w_bytes = grads ? m.gram_bytes : 0;
+    m.ginc_a = grads ? align256(static_cast<size_t>(A->rows_total) * dpad * 8) : 0;
+    m.ginc_bytes = grads ? m.ginc_a + align256(static_cast<size_t>(Bp->rows_total) * dpad * 8) : 0;
+    m.total = m.gram_bytes + m.w_bytes + m.ginc_bytes + align256(m.tape_bytes) + m.sub + 512;
+    return SK_OK;
+}
+
+int run_mmd2(const sk_paths* A, const sk_paths* Bp, int32_t d, int32_t dtype, const sk_options* o, double* out,
+             double* gA, double* gB, void* ws, size_t ws_bytes, void* stream) {
+    if (!out) return fail(SK_ERR_INVALID_ARG, "NULL argument");
+    const bool grads = gA || gB;
+    MmdPlan m;
+    int rc = plan_mmd2(A, Bp, d, dtype, o, grads, m);
+    if (rc != SK_OK) return rc;
+    const bool unb = (o->flags & SK_FLAG_UNBIASED) != 0;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     bool own = false;
     if (!ws) {
-        SK_CUDA(cudaMallocAsync(&ws, total, st));
+        SK_CUDA(cudaMallocAsync(&ws, m.total, st));
         own = true;
-    } else if (ws_bytes < total) {
-        return fail(SK_ERR_WORKSPACE, "workspace %zu bytes < %zu required", ws_bytes, total);
+    } else if (ws_bytes < m.total) {
+        return fail(SK_ERR_WORKSPACE, "workspace %zu bytes < %zu required", ws_bytes, m.total);
     }
+    const int64_t na = A->count, nb = Bp->count;
     char* base = reinterpret_cast<char*>((reinterpret_cast<uintptr_t>(ws) + 255) / 256 * 256);
     double* Kaa = reinterpret_cast<double*>(base);
     double* Kbb = Kaa + na * na;
     double* Kab = Kbb + nb * nb;
-    double* Waa = reinterpret_cast<double*>(base + gram_bytes);
+    double* Waa = reinterpret_cast<double*>(base + m.gram_bytes);
     double* Wbb = Waa + na * na;
     double* Wab = Wbb + nb * nb;
-    double* gincA = reinterpret_cast<double*>(base + gram_bytes + w_bytes);
-    double* gincB = reinterpret_cast<double*>(base + gram_bytes + w_bytes + (grads ? align256(static_cast<size_t>(A->rows_total) * dpad * 8) : 0));
-    char* sub_ws = base + gram_bytes + w_bytes + ginc_bytes;
-    if ((rc = run_forward(A, A, d, dtype, &os, kGramUpper, nullptr, nullptr, gram_items(A, A, true), Kaa, na, sub_ws, sub, st)) != SK_OK) return rc;
-    if ((rc = run_forward(Bp, Bp, d, dtype, &os, kGramUpper, nullptr, nullptr, gram_items(Bp, Bp, true), Kbb, nb, sub_ws, sub, st)) != SK_OK) return rc;
-    if ((rc = run_forward(A, Bp, d, dtype, &of, kGramFull, nullptr, nullptr, gram_items(A, Bp, false), Kab, nb, sub_ws, sub, st)) != SK_OK) return rc;
-    mmd2_reduce_kernel<<<1, 256, 0, st>>>(Kaa, na, Kbb, nb, Kab, unb ? 1 : 0, out);
-    SK_CUDA(cudaGetLastError());
-    if (grads) {
+    double* gincA = reinterpret_cast<double*>(base + m.gram_bytes + m.w_bytes);
+    double* gincB = reinterpret_cast<double*>(base + m.gram_bytes + m.w_bytes + m.ginc_a);
+    char* tape = base + m.gram_bytes + m.w_bytes + m.ginc_bytes;
+    char* sub_ws = tape + align256(m.tape_bytes);
+    const sk_paths* xs[3] = {A, Bp, A};
+    const sk_paths* ys[3] = {A, Bp, Bp};
+    const int modes[3] = {kGramUpper, kGramUpper, kGramFull};
+    double* Ks[3] = {Kaa, Kbb, Kab};
+    const int64_t ldos[3] = {na, nb, nb};
+    if (!grads) {
+        for (int k = 0; k < 3; ++k)
+            if ((rc = run_forward(xs[k], ys[k], d, dtype, k < 2 ? &m.os : &m.of, modes[k], nullptr, nullptr, m.items[k],
+                                  Ks[k], ldos[k], sub_ws, m.sub, st)) != SK_OK)
+                return rc;
+    } else {
         const double waa = unb ? 1.0 / (static_cast<double>(na) * (na - 1)) : 1.0 / (static_cast<double>(na) * na);
         const double wbb = unb ? 1.0 / (static_cast<double>(nb) * (nb - 1)) : 1.0 / (static_cast<double>(nb) * nb);
         const double wab = -2.0 / (static_cast<double>(na) * nb);
@@ -910,12 +1035,34 @@ int run_mmd2(const sk_paths* A, const sk_paths* Bp, int32_t d, int32_t dtype, co
         fill_weights_kernel<<<64, 256, 0, st>>>(Wbb, nb, nb, wbb, unb ? 1 : 0);
         fill_weights_kernel<<<64, 256, 0, st>>>(Wab, na, nb, wab, 0);
         SK_CUDA(cudaGetLastError());
-        SK_CUDA(cudaMemsetAsync(gincA, 0, ginc_bytes, st));
+        SK_CUDA(cudaMemsetAsync(gincA, 0, m.ginc_bytes, st));
+        const double* Ws[3] = {Waa, Wbb, Wab};
+        double* gx[3] = {gincA, gincB, gincA};
+        double* gy[3] = {gincA, gincB, gincB};
         char* sb = reinterpret_cast<char*>((reinterpret_cast<uintptr_t>(sub_ws) + 255) / 256 * 256);
-        if ((rc = launch_backward(A, A, d, dtype, &os, kGramUpper, nullptr, nullptr, gram_items(A, A, true), Waa, na, baa, sb, gincA, gincA, st)) != SK_OK) return rc;
-        if ((rc = launch_backward(Bp, Bp, d, dtype, &os, kGramUpper, nullptr, nullptr, gram_items(Bp, Bp, true), Wbb, nb, bbb, sb, gincB, gincB, st)) != SK_OK) return rc;
-        if ((rc = launch_backward(A, Bp, d, dtype, &of, kGramFull, nullptr, nullptr, gram_items(A, Bp, false), Wab, nb, bab, sb, gincA, gincB, st)) != SK_OK) return rc;
+        for (int k = 0; k < 3; ++k) {
+            const sk_options* ok = k < 2 ? &m.os : &m.of;
+            if (!m.tape[k]) {
+                if ((rc = run_forward(xs[k], ys[k], d, dtype, ok, modes[k], nullptr, nullptr, m.items[k], Ks[k], ldos[k],
+                                      sub_ws, m.sub, st)) != SK_OK)
+                    return rc;
+                if ((rc = launch_backward(xs[k], ys[k], d, dtype, ok, modes[k], nullptr, nullptr, m.items[k], Ws[k],
+                                          ldos[k], m.cb[k], sb, gx[k], gy[k], st)) != SK_OK)
+                    return rc;
+                continue;
+            }
+            for (int64_t i0 = 0; i0 < m.items[k]; i0 += m.chunk[k]) {
+                const int64_t n = std::min(m.chunk[k], m.items[k] - i0);
+                if ((rc = run_forward(xs[k], ys[k], d, dtype, ok, modes[k], nullptr, nullptr, n, Ks[k], ldos[k], sub_ws,
+                                      m.sub, st, tape, m.tape_bytes, i0)) != SK_OK)
+                    return rc;
+                if ((rc = launch_backward_tape(xs[k], ys[k], d, dtype, ok, modes[k], nullptr, nullptr, n, i0, tape, Ws[k],
+                                               ldos[k], m.tb[k], sb, gx[k], gy[k], st)) != SK_OK)
+                    return rc;
+            }
+        }
         const int inc_mode = (o->flags & SK_FLAG_INCREMENTS) ? 1 : 0;
+        const int dpad = m.f[0].dpad;
         if (gA) {
             SK_CUDA(cudaMemsetAsync(gA, 0, static_cast<size_t>(A->rows_total) * d * sizeof(double), st));
             if ((rc = convert_grad(A, d, dpad, inc_mode, gincA, gA, st)) != SK_OK) return rc;
@@ -925,6 +1072,8 @@ int run_mmd2(const sk_paths* A, const sk_paths* Bp, int32_t d, int32_t dtype, co
             if ((rc = convert_grad(Bp, d, dpad, inc_mode, gincB, gB, st)) != SK_OK) return rc;
         }
     }
+    mmd2_reduce_kernel<<<1, 256, 0, st>>>(Kaa, na, Kbb, nb, Kab, unb ? 1 : 0, out);
+    SK_CUDA(cudaGetLastError());
     if (own) SK_CUDA(cudaFreeAsync(ws, st));
     return SK_OK;
 }
@@ -950,20 +1099,29 @@ int sigkernel_autotune(const sk_paths* X, const sk_paths* Y, int32_t d, int32_t 
     const int64_t ldo = gram ? Y->count : 0;
     const int strip = SK_FLAG_STRIP_PIPELINE | SK_FLAG_NO_STRIP_PIPELINE | SK_FLAG_TIME_KERNEL;
     struct Cand {
-        int wpb, pipe;
+        int wpb, pipe, mt;
     };
-    Cand cands[4] = {{1, -1}, {2, -1}, {4, -1}, {0, 1}};
-    int ncand = 3;
+    // one warp per pair with 1, 2, 4 warps per block, with and without tiled M; the pipeline
+    Cand all[7] = {{1, -1, 1}, {2, -1, 1}, {4, -1, 1}, {1, -1, -1}, {2, -1, -1}, {4, -1, -1}, {0, 1, -1}};
+    Cand cands[7];
+    int ncand = 0;
     size_t ws_bytes = 0;
     int rc;
-    for (int c = 0; c < 4; ++c) {
+    auto cand_options = [&](const Cand& c) {
         sk_options co = *opt;
-        co.flags = (opt->flags & ~strip) | (cands[c].pipe > 0 ? SK_FLAG_STRIP_PIPELINE : SK_FLAG_NO_STRIP_PIPELINE);
-        co.warps_per_block = cands[c].wpb;
+        co.flags = (opt->flags & ~(strip | SK_FLAG_NO_TILED_M)) |
+                   (c.pipe > 0 ? SK_FLAG_STRIP_PIPELINE : SK_FLAG_NO_STRIP_PIPELINE) | (c.mt < 0 ? SK_FLAG_NO_TILED_M : 0);
+        co.warps_per_block = c.wpb;
+        return co;
+    };
+    for (int c = 0; c < 7; ++c) {
+        sk_options co = cand_options(all[c]);
         Plan p;
         if ((rc = plan_forward(X, Y, d, dtype, &co, mode, n, p, true)) != SK_OK) return rc;
-        if (c == 3 && p.coop) ncand = 4;  // the pipeline only where some pair spans two strips
-        if (c < 3 || p.coop) ws_bytes = std::max(ws_bytes, p.total);
+        if (all[c].pipe > 0 && !p.coop) continue;            // no pair spans two strips
+        if (all[c].pipe < 0 && all[c].mt > 0 && !p.mtile) continue;  // tiled M not applicable
+        cands[ncand++] = all[c];
+        ws_bytes = std::max(ws_bytes, p.total);
     }
     if (n == 0) return fail(SK_ERR_INVALID_ARG, "nothing to tune: no pairs");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -977,9 +1135,7 @@ int sigkernel_autotune(const sk_paths* X, const sk_paths* Y, int32_t d, int32_t 
         rc = fail(SK_ERR_CUDA, "cudaEventCreate failed");
     }
     for (int c = 0; c < ncand && rc == SK_OK; ++c) {
-        sk_options co = *opt;
-        co.flags = (opt->flags & ~strip) | (cands[c].pipe > 0 ? SK_FLAG_STRIP_PIPELINE : SK_FLAG_NO_STRIP_PIPELINE);
-        co.warps_per_block = cands[c].wpb;
+        const sk_options co = cand_options(cands[c]);
         float t_min = -1.f;
         for (int t = 0; t <= trials && rc == SK_OK; ++t) {  // t = 0 warms up
             if (cudaEventRecord(e0, st) != cudaSuccess) { rc = fail(SK_ERR_CUDA, "cudaEventRecord failed"); break; }
@@ -1009,12 +1165,9 @@ int sigkernel_autotune(const sk_paths* X, const sk_paths* Y, int32_t d, int32_t 
     {
         std::lock_guard<std::mutex> lock(g_tune_mu);
         g_tune[tune_key(dev, X, Y, opt, dpad, mode, n)] =
-            TuneChoice{cands[best_c].wpb ? cands[best_c].wpb : kFwdWarps, cands[best_c].pipe};
+            TuneChoice{cands[best_c].wpb ? cands[best_c].wpb : kFwdWarps, cands[best_c].pipe, cands[best_c].mt};
     }
-    *best = *opt;
-    best->flags = (opt->flags & ~strip) |
-                  (cands[best_c].pipe > 0 ? SK_FLAG_STRIP_PIPELINE : SK_FLAG_NO_STRIP_PIPELINE);
-    best->warps_per_block = cands[best_c].wpb;
+    *best = cand_options(cands[best_c]);
     if (best_ms) *best_ms = best_t;
     return SK_OK;
 }
@@ -1073,29 +1226,12 @@ int sigkernel_workspace_size(int32_t op, const sk_paths* X, const sk_paths* Y, i
             return rc;
         }
         case SK_OP_MMD2: {
-            // sized by a dry run of the same planning as sigkernel_mmd2 (X = A, Y = B)
-            Plan pa, pb, pc;
-            BwdPlan ba, bb, bc;
-            sk_options os = *opt;
-            os.flags = (opt->flags & (SK_FLAG_INCREMENTS | SK_FLAG_NO_SORT | SK_FLAG_TIME_KERNEL | SK_FLAG_STRIP_PIPELINE | SK_FLAG_NO_STRIP_PIPELINE)) | SK_FLAG_SYMMETRIC;
-            sk_options of = os;
-            of.flags &= ~SK_FLAG_SYMMETRIC;
-            if ((rc = plan_forward(X, X, d, dtype, &os, kGramUpper, gram_items(X, X, true), pa, true)) != SK_OK) return rc;
-            if ((rc = plan_forward(Y, Y, d, dtype, &os, kGramUpper, gram_items(Y, Y, true), pb, true)) != SK_OK) return rc;
-            if ((rc = plan_forward(X, Y, d, dtype, &of, kGramFull, gram_items(X, Y, false), pc, true)) != SK_OK) return rc;
-            size_t sub = std::max(pa.total, std::max(pb.total, pc.total));
-            if (opt->scheme == SK_POLY_APPROX && d <= 32) {
-                if ((rc = plan_backward(X, X, d, dtype, &os, kGramUpper, gram_items(X, X, true), ba)) != SK_OK) return rc;
-                if ((rc = plan_backward(Y, Y, d, dtype, &os, kGramUpper, gram_items(Y, Y, true), bb)) != SK_OK) return rc;
-                if ((rc = plan_backward(X, Y, d, dtype, &of, kGramFull, gram_items(X, Y, false), bc)) != SK_OK) return rc;
-                sub = std::max(sub, std::max(ba.total, std::max(bb.total, bc.total)));
-            }
-            const int64_t na = X->count, nb = Y->count;
-            const size_t gram_bytes = align256((na * na + nb * nb + na * nb) * sizeof(double));
-            const size_t ginc = align256(static_cast<size_t>(X->rows_total) * pa.dpad * 8) +
-                                align256(static_cast<size_t>(Y->rows_total) * pa.dpad * 8);
-            *bytes = 2 * gram_bytes + ginc + sub + 512;
-            return SK_OK;
+            // sized by the same planning as sigkernel_mmd2 (X = A, Y = B); npairs = 1 asks for
+            // the gradient's workspace, 0 for the value alone
+            MmdPlan m;
+            rc = plan_mmd2(X, Y, d, dtype, opt, npairs != 0, m);
+            if (rc == SK_OK) *bytes = m.total;
+            return rc;
         }
         default:
             return fail(SK_ERR_UNSUPPORTED, "workspace for op %d", op);

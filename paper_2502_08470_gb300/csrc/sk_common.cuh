@@ -136,6 +136,16 @@ struct Launch {
     // least this many strips is swept by all warps of a block together; shorter pairs get one
     // warp each.
     int32_t coop_min_strips;
+    // Tiled M (polynomial schemes, wide increments): when nonzero, each warp builds the M_ij of
+    // a strip (32 rows x cols) in its scratch, at byte offset mtile_off of its slot, two strips
+    // deep ([2][32][mtile_cols]), before lane 0 enters the strip; the cells then read M there
+    // instead of forming the inner product from two increment rows each.
+    int32_t mtile;
+    int32_t mtile_cols;
+    int64_t mtile_off;
+    // Gram modes: work item k of this launch is item k + item_base of the whole Gram (a call can
+    // sweep a sub-range of a Gram's items; its tape and queue are indexed by k).
+    int64_t item_base;
 };
 
 // Width, in elements of T, of one lane's tape row: a[0..N], b[0..N], the exponent (element
@@ -177,12 +187,14 @@ __device__ __forceinline__ PairDesc decode_pair(const Launch& L, int64_t item) {
         P.a = L.pair_a[item];
         P.b = L.pair_b[item];
     } else if (L.mode == kGramFull) {
-        P.a = item / L.Y.count;
-        P.b = item - P.a * L.Y.count;
+        const int64_t gi = item + L.item_base;
+        P.a = gi / L.Y.count;
+        P.b = gi - P.a * L.Y.count;
     } else {
+        const int64_t gi = item + L.item_base;
         int64_t n = L.X.count;
-        P.a = upper_row(item, n);
-        P.b = P.a + (item - (P.a * n - P.a * (P.a - 1) / 2));
+        P.a = upper_row(gi, n);
+        P.b = P.a + (gi - (P.a * n - P.a * (P.a - 1) / 2));
     }
     bool okx = P.a >= 0 && P.a < L.X.count, oky = P.b >= 0 && P.b < L.Y.count;
     if (!okx || !oky) {

@@ -5,19 +5,23 @@
 namespace sk {
 
 // T: 0 = FP64 cell updates, 1 = FP32; coop: the cooperative-block (strip pipeline) variant,
-// launched with kCoopWarps warps per block.  NULL when no kernel exists for the request.
-const void* fwd_poly_kernel_ptr(int T, bool interp, int N, bool coop);
+// launched with kCoopWarps warps per block; mt: the tiled-M variant (FP32 only).  NULL when no
+// kernel exists for the request.
+const void* fwd_poly_kernel_ptr(int T, bool interp, int N, bool coop, bool mt);
 const void* fwd_fd_kernel_ptr(int T, int order, int lam, bool coop);
-
-const void* fwd_approx_ptr_f32(int N);
-const void* fwd_approx_ptr_f64(int N);
-const void* fwd_interp_ptr_f32(int N);
-const void* fwd_interp_ptr_f64(int N);
-const void* fwd_approx_coop_ptr_f32(int N);
-const void* fwd_approx_coop_ptr_f64(int N);
-const void* fwd_interp_coop_ptr_f32(int N);
-const void* fwd_interp_coop_ptr_f64(int N);
 const void* fwd_fd_coop_ptr(int T, int order, int lam);
+const void* fwd_approx_ptr_f32(int N);
+const void* fwd_interp_ptr_f32(int N);
+const void* fwd_approx_coop_ptr_f32(int N);
+const void* fwd_interp_coop_ptr_f32(int N);
+const void* fwd_approx_ptr_f64(int N);
+const void* fwd_interp_ptr_f64(int N);
+const void* fwd_approx_coop_ptr_f64(int N);
+const void* fwd_interp_coop_ptr_f64(int N);
+const void* fwd_approx_mt_ptr_f32(int N);
+const void* fwd_interp_mt_ptr_f32(int N);
+const void* fwd_approx_coop_mt_ptr_f32(int N);
+const void* fwd_interp_coop_mt_ptr_f32(int N);
 // interpolation orders are split over several units (chunk k of each family)
 const void* fwd_interp_ptr_f32_0(int N);
 const void* fwd_interp_ptr_f32_1(int N);
@@ -39,8 +43,16 @@ const void* fwd_interp_coop_ptr_f64_1(int N);
 const void* fwd_interp_coop_ptr_f64_2(int N);
 const void* fwd_interp_coop_ptr_f64_3(int N);
 const void* fwd_interp_coop_ptr_f64_4(int N);
-
-
+const void* fwd_interp_mt_ptr_f32_0(int N);
+const void* fwd_interp_mt_ptr_f32_1(int N);
+const void* fwd_interp_mt_ptr_f32_2(int N);
+const void* fwd_interp_mt_ptr_f32_3(int N);
+const void* fwd_interp_mt_ptr_f32_4(int N);
+const void* fwd_interp_coop_mt_ptr_f32_0(int N);
+const void* fwd_interp_coop_mt_ptr_f32_1(int N);
+const void* fwd_interp_coop_mt_ptr_f32_2(int N);
+const void* fwd_interp_coop_mt_ptr_f32_3(int N);
+const void* fwd_interp_coop_mt_ptr_f32_4(int N);
 }  // namespace sk
 
 namespace sk {

@@ -6,21 +6,21 @@ namespace sk {
 
 const void* fwd_approx_ptr_f32(int N) {
     switch (N) {
-        case 2: return reinterpret_cast<const void*>(&fwd_poly_kernel<float, 2, 2, false, 1>);
-        case 3: return reinterpret_cast<const void*>(&fwd_poly_kernel<float, 3, 3, false, 1>);
-        case 4: return reinterpret_cast<const void*>(&fwd_poly_kernel<float, 4, 4, false, 1>);
-        case 5: return reinterpret_cast<const void*>(&fwd_poly_kernel<float, 5, 5, false, 1>);
-        case 6: return reinterpret_cast<const void*>(&fwd_poly_kernel<float, 6, 6, false, 1>);
-        case 7: return reinterpret_cast<const void*>(&fwd_poly_kernel<float, 7, 7, false, 1>);
-        case 8: return reinterpret_cast<const void*>(&fwd_poly_kernel<float, 8, 8, false, 1>);
-        case 9: return reinterpret_cast<const void*>(&fwd_poly_kernel<float, 9, 9, false, 1>);
-        case 10: return reinterpret_cast<const void*>(&fwd_poly_kernel<float, 10, 10, false, 1>);
-        case 11: return reinterpret_cast<const void*>(&fwd_poly_kernel<float, 11, 11, false, 1>);
-        case 12: return reinterpret_cast<const void*>(&fwd_poly_kernel<float, 12, 12, false, 1>);
-        case 13: return reinterpret_cast<const void*>(&fwd_poly_kernel<float, 13, 13, false, 1>);
-        case 14: return reinterpret_cast<const void*>(&fwd_poly_kernel<float, 14, 14, false, 1>);
-        case 15: return reinterpret_cast<const void*>(&fwd_poly_kernel<float, 15, 15, false, 1>);
-        case 16: return reinterpret_cast<const void*>(&fwd_poly_kernel<float, 16, 16, false, 1>);
+        case 2: return reinterpret_cast<const void*>(&fwd_poly_kernel<float, 2, 2, false, 1, false>);
+        case 3: return reinterpret_cast<const void*>(&fwd_poly_kernel<float, 3, 3, false, 1, false>);
+        case 4: return reinterpret_cast<const void*>(&fwd_poly_kernel<float, 4, 4, false, 1, false>);
+        case 5: return reinterpret_cast<const void*>(&fwd_poly_kernel<float, 5, 5, false, 1, false>);
+        case 6: return reinterpret_cast<const void*>(&fwd_poly_kernel<float, 6, 6, false, 1, false>);
+        case 7: return reinterpret_cast<const void*>(&fwd_poly_kernel<float, 7, 7, false, 1, false>);
+        case 8: return reinterpret_cast<const void*>(&fwd_poly_kernel<float, 8, 8, false, 1, false>);
+        case 9: return reinterpret_cast<const void*>(&fwd_poly_kernel<float, 9, 9, false, 1, false>);
+        case 10: return reinterpret_cast<const void*>(&fwd_poly_kernel<float, 10, 10, false, 1, false>);
+        case 11: return reinterpret_cast<const void*>(&fwd_poly_kernel<float, 11, 11, false, 1, false>);
+        case 12: return reinterpret_cast<const void*>(&fwd_poly_kernel<float, 12, 12, false, 1, false>);
+        case 13: return reinterpret_cast<const void*>(&fwd_poly_kernel<float, 13, 13, false, 1, false>);
+        case 14: return reinterpret_cast<const void*>(&fwd_poly_kernel<float, 14, 14, false, 1, false>);
+        case 15: return reinterpret_cast<const void*>(&fwd_poly_kernel<float, 15, 15, false, 1, false>);
+        case 16: return reinterpret_cast<const void*>(&fwd_poly_kernel<float, 16, 16, false, 1, false>);
         default: return nullptr;
     }
 }

@@ -6,21 +6,21 @@ namespace sk {
 
 const void* fwd_approx_coop_ptr_f64(int N) {
     switch (N) {
-        case 2: return reinterpret_cast<const void*>(&fwd_poly_kernel<double, 2, 2, false, kCoopWarps>);
-        case 3: return reinterpret_cast<const void*>(&fwd_poly_kernel<double, 3, 3, false, kCoopWarps>);
-        case 4: return reinterpret_cast<const void*>(&fwd_poly_kernel<double, 4, 4, false, kCoopWarps>);
-        case 5: return reinterpret_cast<const void*>(&fwd_poly_kernel<double, 5, 5, false, kCoopWarps>);
-        case 6: return reinterpret_cast<const void*>(&fwd_poly_kernel<double, 6, 6, false, kCoopWarps>);
-        case 7: return reinterpret_cast<const void*>(&fwd_poly_kernel<double, 7, 7, false, kCoopWarps>);
-        case 8: return reinterpret_cast<const void*>(&fwd_poly_kernel<double, 8, 8, false, kCoopWarps>);
-        case 9: return reinterpret_cast<const void*>(&fwd_poly_kernel<double, 9, 9, false, kCoopWarps>);
-        case 10: return reinterpret_cast<const void*>(&fwd_poly_kernel<double, 10, 10, false, kCoopWarps>);
-        case 11: return reinterpret_cast<const void*>(&fwd_poly_kernel<double, 11, 11, false, kCoopWarps>);
-        case 12: return reinterpret_cast<const void*>(&fwd_poly_kernel<double, 12, 12, false, kCoopWarps>);
-        case 13: return reinterpret_cast<const void*>(&fwd_poly_kernel<double, 13, 13, false, kCoopWarps>);
-        case 14: return reinterpret_cast<const void*>(&fwd_poly_kernel<double, 14, 14, false, kCoopWarps>);
-        case 15: return reinterpret_cast<const void*>(&fwd_poly_kernel<double, 15, 15, false, kCoopWarps>);
-        case 16: return reinterpret_cast<const void*>(&fwd_poly_kernel<double, 16, 16, false, kCoopWarps>);
+        case 2: return reinterpret_cast<const void*>(&fwd_poly_kernel<double, 2, 2, false, kCoopWarps, false>);
+        case 3: return reinterpret_cast<const void*>(&fwd_poly_kernel<double, 3, 3, false, kCoopWarps, false>);
+        case 4: return reinterpret_cast<const void*>(&fwd_poly_kernel<double, 4, 4, false, kCoopWarps, false>);
+        case 5: return reinterpret_cast<const void*>(&fwd_poly_kernel<double, 5, 5, false, kCoopWarps, false>);
+        case 6: return reinterpret_cast<const void*>(&fwd_poly_kernel<double, 6, 6, false, kCoopWarps, false>);
+        case 7: return reinterpret_cast<const void*>(&fwd_poly_kernel<double, 7, 7, false, kCoopWarps, false>);
+        case 8: return reinterpret_cast<const void*>(&fwd_poly_kernel<double, 8, 8, false, kCoopWarps, false>);
+        case 9: return reinterpret_cast<const void*>(&fwd_poly_kernel<double, 9, 9, false, kCoopWarps, false>);
+        case 10: return reinterpret_cast<const void*>(&fwd_poly_kernel<double, 10, 10, false, kCoopWarps, false>);
+        case 11: return reinterpret_cast<const void*>(&fwd_poly_kernel<double, 11, 11, false, kCoopWarps, false>);
+        case 12: return reinterpret_cast<const void*>(&fwd_poly_kernel<double, 12, 12, false, kCoopWarps, false>);
+        case 13: return reinterpret_cast<const void*>(&fwd_poly_kernel<double, 13, 13, false, kCoopWarps, false>);
+        case 14: return reinterpret_cast<const void*>(&fwd_poly_kernel<double, 14, 14, false, kCoopWarps, false>);
+        case 15: return reinterpret_cast<const void*>(&fwd_poly_kernel<double, 15, 15, false, kCoopWarps, false>);
+        case 16: return reinterpret_cast<const void*>(&fwd_poly_kernel<double, 16, 16, false, kCoopWarps, false>);
         default: return nullptr;
     }
 }

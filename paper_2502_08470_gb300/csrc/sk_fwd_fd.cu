@@ -38,7 +38,22 @@ const void* fwd_interp_coop_ptr_f64(int N) {
     return nullptr;
 }
 
-const void* fwd_poly_kernel_ptr(int T, bool interp, int N, bool coop) {
+const void* fwd_interp_mt_ptr_f32(int N) {
+    if (const void* k = fwd_interp_mt_ptr_f32_0(N)) return k; if (const void* k = fwd_interp_mt_ptr_f32_1(N)) return k; if (const void* k = fwd_interp_mt_ptr_f32_2(N)) return k; if (const void* k = fwd_interp_mt_ptr_f32_3(N)) return k; if (const void* k = fwd_interp_mt_ptr_f32_4(N)) return k;
+    return nullptr;
+}
+
+const void* fwd_interp_coop_mt_ptr_f32(int N) {
+    if (const void* k = fwd_interp_coop_mt_ptr_f32_0(N)) return k; if (const void* k = fwd_interp_coop_mt_ptr_f32_1(N)) return k; if (const void* k = fwd_interp_coop_mt_ptr_f32_2(N)) return k; if (const void* k = fwd_interp_coop_mt_ptr_f32_3(N)) return k; if (const void* k = fwd_interp_coop_mt_ptr_f32_4(N)) return k;
+    return nullptr;
+}
+
+const void* fwd_poly_kernel_ptr(int T, bool interp, int N, bool coop, bool mt) {
+    if (mt) {
+        if (T != 1) return nullptr;
+        if (coop) return interp ? fwd_interp_coop_mt_ptr_f32(N) : fwd_approx_coop_mt_ptr_f32(N);
+        return interp ? fwd_interp_mt_ptr_f32(N) : fwd_approx_mt_ptr_f32(N);
+    }
     if (coop) {
         if (T == 1) return interp ? fwd_interp_coop_ptr_f32(N) : fwd_approx_coop_ptr_f32(N);
         return interp ? fwd_interp_coop_ptr_f64(N) : fwd_approx_coop_ptr_f64(N);

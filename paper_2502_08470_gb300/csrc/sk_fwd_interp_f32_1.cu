@@ -1,5 +1,4 @@
-// Instantiations of the polynomial-interpolation forward wavefront (float cell updates), orders 7..8
-// (one unit per group of orders so that the units compile in parallel).
+// Instantiations of the polynomial-interpolation forward wavefront (float cell updates), orders 7..8 (one unit per group of orders so that the units compile in parallel).
 #include "sk_fwd_poly.cuh"
 #include "sk_dispatch.h"
 
@@ -7,8 +6,8 @@ namespace sk {
 
 const void* fwd_interp_ptr_f32_1(int N) {
     switch (N) {
-        case 7: return reinterpret_cast<const void*>(&fwd_poly_kernel<float, 7, 7 + sk::kJF32, true, 1>);
-        case 8: return reinterpret_cast<const void*>(&fwd_poly_kernel<float, 8, 8 + sk::kJF32, true, 1>);
+        case 7: return reinterpret_cast<const void*>(&fwd_poly_kernel<float, 7, 7 + sk::kJF32, true, 1, false>);
+        case 8: return reinterpret_cast<const void*>(&fwd_poly_kernel<float, 8, 8 + sk::kJF32, true, 1, false>);
         default: return nullptr;
     }
 }

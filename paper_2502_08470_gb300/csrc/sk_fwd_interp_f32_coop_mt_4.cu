@@ -1,0 +1,14 @@
+// Instantiations of the cooperative-block (strip pipeline) tiled-M polynomial-interpolation forward wavefront (float cell updates), orders 12..12 (one unit per group of orders so that the units compile in parallel).
+#include "sk_fwd_poly.cuh"
+#include "sk_dispatch.h"
+
+namespace sk {
+
+const void* fwd_interp_coop_mt_ptr_f32_4(int N) {
+    switch (N) {
+        case 12: return reinterpret_cast<const void*>(&fwd_poly_kernel<float, 12, 12 + sk::kJF32, true, kCoopWarps, true>);
+        default: return nullptr;
+    }
+}
+
+}  // namespace sk

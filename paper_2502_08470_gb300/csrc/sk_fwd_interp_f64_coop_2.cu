@@ -1,5 +1,4 @@
-// Instantiations of the cooperative-block (strip pipeline) polynomial-interpolation forward wavefront (double cell updates), orders 9..10
-// (one unit per group of orders so that the units compile in parallel).
+// Instantiations of the cooperative-block (strip pipeline) polynomial-interpolation forward wavefront (double cell updates), orders 9..10 (one unit per group of orders so that the units compile in parallel).
 #include "sk_fwd_poly.cuh"
 #include "sk_dispatch.h"
 
@@ -7,8 +6,8 @@ namespace sk {
 
 const void* fwd_interp_coop_ptr_f64_2(int N) {
     switch (N) {
-        case 9: return reinterpret_cast<const void*>(&fwd_poly_kernel<double, 9, 9 + sk::kJF64, true, kCoopWarps>);
-        case 10: return reinterpret_cast<const void*>(&fwd_poly_kernel<double, 10, 10 + sk::kJF64, true, kCoopWarps>);
+        case 9: return reinterpret_cast<const void*>(&fwd_poly_kernel<double, 9, 9 + sk::kJF64, true, kCoopWarps, false>);
+        case 10: return reinterpret_cast<const void*>(&fwd_poly_kernel<double, 10, 10 + sk::kJF64, true, kCoopWarps, false>);
         default: return nullptr;
     }
 }

@@ -121,12 +121,57 @@ __host__ __device__ constexpr int fwd_tape_step_bytes() {
 }
 
 // Resident blocks per SM requested from the register allocator: the live state of a lane is
-// about 3 (N+1) edge values, 3 (NE+1) series values and ~24 addresses / counters.
-template <typename T, int N, int NE>
+// about 3 (N+1) edge values, 3 (NE+1) series values and ~24 addresses / counters (plus, with
+// tiled M, the producer's 16 accumulators, one 16-byte chunk and its buffer addresses).
+template <typename T, int N, int NE, bool MT = false>
 constexpr int fwd_poly_min_blocks() {
-    constexpr int words = (3 * (N + 1) + 3 * (NE + 1) + 24) * (sizeof(T) == 8 ? 2 : 1);
+    constexpr int words = (3 * (N + 1) + 3 * (NE + 1) + 24 + (MT ? 28 : 0)) * (sizeof(T) == 8 ? 2 : 1);
     constexpr int b = 65536 / (kFwdWarps * 32 * words);
     return b < 1 ? 1 : (b > 8 ? 8 : b);
+}
+
+// Tiled M for strip g: M[r][c] = <dx_{row}, dy_c> / 4^lambda for the strip's 32 rows and every
+// column, written to dst ([32][mcols], rows past the last grid row left unwritten).  Lane q owns
+// columns q, q + 32, ... and keeps that increment row in registers a 16-byte chunk at a time; the
+// strip's x rows sit in shared memory (xs, [32][dpad]) and are read as broadcasts, so 32 cells
+// share each operand load instead of each cell gathering two rows.  The inner products run in
+// row_dot's order, so M is bit for bit the value row_dot gives.
+template <typename T>
+__device__ __forceinline__ void produce_m_strip(const T* __restrict__ xbase, const T* __restrict__ ybase, int dpad,
+                                                int lam, int rows, int cols, int g, T sub, T* xs, T* dst, int mcols) {
+    using V = typename Vec<T>::type;
+    constexpr int W = Vec<T>::W;
+    constexpr int RH = 16;  // rows per pass (accumulators per lane)
+    const int lane = threadIdx.x & 31;
+    __syncwarp();  // earlier readers of xs are done
+    {
+        const T* xr = xbase + static_cast<int64_t>(min((g << 5) + lane, rows - 1) >> lam) * dpad;
+        for (int k = 0; k < dpad; k += W)
+            *reinterpret_cast<V*>(xs + lane * dpad + k) = __ldg(reinterpret_cast<const V*>(xr + k));
+    }
+    __syncwarp();
+    for (int c0 = 0; c0 < cols; c0 += 32) {
+        const int c = c0 + lane;
+        const V* yv = reinterpret_cast<const V*>(ybase + static_cast<int64_t>(min(c, cols - 1) >> lam) * dpad);
+#pragma unroll 1
+        for (int rh = 0; rh < 32; rh += RH) {
+            T acc[RH];
+#pragma unroll
+            for (int r = 0; r < RH; ++r) acc[r] = T(0);
+            for (int k = 0; k < dpad / W; ++k) {
+                const V y = __ldg(yv + k);
+#pragma unroll
+                for (int r = 0; r < RH; ++r)
+                    acc[r] = Vec<T>::dot(*reinterpret_cast<const V*>(xs + (rh + r) * dpad + k * W), y, acc[r]);
+            }
+            if (c < cols) {
+#pragma unroll
+                for (int r = 0; r < RH; ++r)
+                    if ((g << 5) + rh + r < rows) dst[static_cast<int64_t>(rh + r) * mcols + c] = acc[r] * sub;
+            }
+        }
+    }
+    __syncwarp();  // the strip's M is visible to every lane
 }
 
 // Warps of a block that sweep one long pair together (strip pipeline); see sweep_poly.  Sixteen
@@ -134,9 +179,9 @@ constexpr int fwd_poly_min_blocks() {
 // 5.8 ms) and on uneven batches (4096 pairs of 64..4096-point paths: 101 against 121 ms).
 constexpr int kCoopWarps = 16;
 
-template <typename T, int N, int NE>
+template <typename T, int N, int NE, bool MT = false>
 constexpr int fwd_poly_coop_min_blocks() {
-    constexpr int b = fwd_poly_min_blocks<T, N, NE>() * kFwdWarps / kCoopWarps;
+    constexpr int b = fwd_poly_min_blocks<T, N, NE, MT>() * kFwdWarps / kCoopWarps;
     return b < 1 ? 1 : b;
 }
 
@@ -149,10 +194,10 @@ constexpr int fwd_poly_coop_min_blocks() {
 // wait_progress); a buffer entry of strip g is overwritten by strip g + CW only after strip
 // g + 1 has consumed it, because strip g + CW depends on strip g + 1 through the chain of
 // strips in between.
-template <typename T, int N, int NE, bool INTERP, int CW>
+template <typename T, int N, int NE, bool INTERP, int CW, bool MT>
 __device__ __forceinline__ void sweep_poly(const Launch& L, int64_t item, const PairDesc& P, int w, char* own_buf,
                                            const char* prev_buf, int* prog, int64_t buf_cols,
-                                           unsigned char* tape_stage) {
+                                           unsigned char* tape_stage, T* xstage) {
     constexpr bool kRescale = std::is_same<T, float>::value;
     using V = typename Vec<T>::type;
     constexpr int W = Vec<T>::W;
@@ -196,8 +241,21 @@ __device__ __forceinline__ void sweep_poly(const Launch& L, int64_t item, const 
     int g = w, row = (w << 5) + lane;       // global strip and grid row
     bool stuck = false;                     // a hand-off wait ran out (CW > 1 only)
     const T* xrow = xbase + static_cast<int64_t>(min(row, rows - 1) >> lam) * dpad;
+    // tiled M (MT): this warp's [2][32][mcols] strip buffers; lane 0's column and local strip
+    const int mcols = MT ? L.mtile_cols : 0;
+    T* mbuf = MT ? reinterpret_cast<T*>(own_buf + L.mtile_off) : nullptr;
+    int jj0 = 0, sl0 = 0;
 
     for (int step = 0; step < nsteps; ++step) {
+        if constexpr (MT) {
+            if (jj0 == 0 && sl0 < nloc)  // lane 0 enters local strip sl0: build its M first
+                produce_m_strip<T>(xbase, ybase, dpad, lam, rows, cols, w + sl0 * CW, sub, xstage,
+                                   mbuf + (sl0 & 1) * 32 * static_cast<int64_t>(mcols), mcols);
+            if (++jj0 == period) {
+                jj0 = 0;
+                ++sl0;
+            }
+        }
         T b[N + 1];
 #pragma unroll
         for (int n = 0; n <= N; ++n) b[n] = __shfl_up_sync(kFull, bo[n], 1);
@@ -244,7 +302,9 @@ __device__ __forceinline__ void sweep_poly(const Launch& L, int64_t item, const 
         // Every lane runs the cell (inactive lanes on a clamped, in-bounds column); only
         // the results of active lanes are ever consumed.
         const int jc = min(max(jj, 0), cols - 1);
-        const T M = row_dot<T>(xrow, ybase + static_cast<int64_t>(jc >> lam) * dpad, L.nvec) * sub;
+        T M;
+        if constexpr (MT) M = active ? mbuf[((sl & 1) * 32 + lane) * static_cast<int64_t>(mcols) + jc] : T(0);
+        else M = row_dot<T>(xrow, ybase + static_cast<int64_t>(jc >> lam) * dpad, L.nvec) * sub;
         if constexpr (!INTERP && CW == 1) {
             if (L.tape != nullptr) {
                 // Record the cell's inputs (a, b, exponent, M) for the adjoint: each lane writes
@@ -371,21 +431,24 @@ __device__ __forceinline__ bool trivial_pair(const Launch& L, int64_t item, cons
     return false;
 }
 
-// Forward wavefront, persistent.  CW = 1: blocks of kFwdWarps independent warps, one pair per
-// warp.  CW > 1: blocks of CW warps; the block takes pairs of at least L.coop_min_strips strips
+// Forward wavefront, persistent.  MT: tiled M (produce_m_strip) instead of per-cell inner
+// products.  CW = 1: blocks of kFwdWarps independent warps, one pair per warp.  CW > 1: blocks of CW warps; the block takes pairs of at least L.coop_min_strips strips
 // together (strip pipeline, sweep_poly<..., CW>), and at the first shorter pair (the queue is
 // ordered by cell count, longest first) its warps fall back to one pair each.
-template <typename T, int N, int NE, bool INTERP, int CW>
+template <typename T, int N, int NE, bool INTERP, int CW, bool MT>
 __global__ void __launch_bounds__((CW > 1 ? CW : kFwdWarps) * 32,
-                                  (CW > 1 ? fwd_poly_coop_min_blocks<T, N, NE>() : fwd_poly_min_blocks<T, N, NE>()))
+                                  (CW > 1 ? fwd_poly_coop_min_blocks<T, N, NE, MT>() : fwd_poly_min_blocks<T, N, NE, MT>()))
     fwd_poly_kernel(Launch L, int64_t buf_cols) {
     const int wib = threadIdx.x >> 5;
     const int nw = blockDim.x >> 5;
     char* block_base = static_cast<char*>(L.scratch) + static_cast<int64_t>(blockIdx.x) * nw * L.scratch_stride;
     char* own = block_base + wib * L.scratch_stride;
-    // tape staging (two step slots per warp) in dynamic shared memory, used only with a tape
+    // dynamic shared memory: tape staging (two step slots per warp, with a tape), then the x rows
+    // of the tiled-M producer ([32][dpad] per warp, with L.mtile)
     extern __shared__ __align__(128) unsigned char fwd_smem[];
     unsigned char* tape_stage = fwd_smem + wib * 2 * fwd_tape_step_bytes<T, N>();
+    T* xstage = reinterpret_cast<T*>(fwd_smem + (L.tape != nullptr ? nw * 2 * fwd_tape_step_bytes<T, N>() : 0)) +
+                wib * 32 * L.dpad;
 
     if constexpr (CW > 1) {
         __shared__ long long s_item;
@@ -401,12 +464,12 @@ __global__ void __launch_bounds__((CW > 1 ? CW : kFwdWarps) * 32,
             const int nstrips = P.lx > 0 ? static_cast<int>(((P.lx << L.lam) + 31) >> 5) : 0;
             if (nstrips < L.coop_min_strips) {  // short pairs from here on: one warp each
                 if (wib == 0 && !trivial_pair(L, item, P))
-                    sweep_poly<T, N, NE, INTERP, 1>(L, item, P, 0, own, own, nullptr, buf_cols, tape_stage);
+                    sweep_poly<T, N, NE, INTERP, 1, MT>(L, item, P, 0, own, own, nullptr, buf_cols, tape_stage, xstage);
                 break;
             }
             if (!trivial_pair(L, item, P))
-                sweep_poly<T, N, NE, INTERP, CW>(L, item, P, wib, own, block_base + ((wib + CW - 1) % CW) * L.scratch_stride,
-                                                 s_prog, buf_cols, tape_stage);
+                sweep_poly<T, N, NE, INTERP, CW, MT>(L, item, P, wib, own, block_base + ((wib + CW - 1) % CW) * L.scratch_stride,
+                                                 s_prog, buf_cols, tape_stage, xstage);
         }
     }
     for (;;) {
@@ -414,7 +477,7 @@ __global__ void __launch_bounds__((CW > 1 ? CW : kFwdWarps) * 32,
         if (item < 0) break;
         const PairDesc P = decode_pair(L, item);
         if (trivial_pair(L, item, P)) continue;
-        sweep_poly<T, N, NE, INTERP, 1>(L, item, P, 0, own, own, nullptr, buf_cols, tape_stage);
+        sweep_poly<T, N, NE, INTERP, 1, MT>(L, item, P, 0, own, own, nullptr, buf_cols, tape_stage, xstage);
     }
     if (!INTERP && L.tape != nullptr && (threadIdx.x & 31) == 0) bulk_wait_all();  // no copy outlives the staging smem
 }

@@ -26,7 +26,7 @@ SCHEMES = {"fd1": 0, "fd2": 1, "approx": 2, "interp": 3}
 COMPUTE = {"f64": 0, "f32": 1}
 DTYPES = {torch.float64: 0, torch.float32: 1, torch.bfloat16: 2}
 FLAG_SYMMETRIC, FLAG_INCREMENTS, FLAG_UNBIASED, FLAG_NO_SORT, FLAG_TIME_KERNEL = 1, 2, 4, 8, 16
-FLAG_STRIP_PIPELINE, FLAG_NO_STRIP_PIPELINE = 32, 64
+FLAG_STRIP_PIPELINE, FLAG_NO_STRIP_PIPELINE, FLAG_NO_TILED_M = 32, 64, 128
 
 
 def _pipe_flags(strip_pipeline) -> int:
@@ -183,7 +183,8 @@ def _flags(X: Paths, extra=0) -> int:
 
 
 def sigkernel_pairs(X, Y, pair_a, pair_b, scheme="approx", degree=6, dyadic=0, compute="f64", sort=True,
-                    out: torch.Tensor | None = None, strip_pipeline=None, time_kernel: bool = False) -> torch.Tensor:
+                    out: torch.Tensor | None = None, strip_pipeline=None, time_kernel: bool = False,
+                    tiled_m: bool = True) -> torch.Tensor:
     """k_hat(X[pair_a[k]], Y[pair_b[k]]) for every k, as a float64 CUDA tensor."""
     X, Y = as_paths(X), as_paths(Y)
     pa = torch.as_tensor(pair_a, dtype=torch.int64, device="cuda").contiguous()
@@ -191,7 +192,7 @@ def sigkernel_pairs(X, Y, pair_a, pair_b, scheme="approx", degree=6, dyadic=0, c
     n = pa.numel()
     opt = _options(scheme, degree, dyadic, compute,
                    _flags(X, (0 if sort else FLAG_NO_SORT) | _pipe_flags(strip_pipeline)
-                          | (FLAG_TIME_KERNEL if time_kernel else 0)))
+                          | (FLAG_TIME_KERNEL if time_kernel else 0) | (0 if tiled_m else FLAG_NO_TILED_M)))
     cX, cY = _cpaths(X), _cpaths(Y)
     out = out if out is not None else torch.empty(n, dtype=torch.float64, device="cuda")
     ws = _workspace(OP_PAIRS, cX, cY, X.d, n, opt)
@@ -203,7 +204,7 @@ def sigkernel_pairs(X, Y, pair_a, pair_b, scheme="approx", degree=6, dyadic=0, c
 
 def sigkernel_gram(X, Y=None, scheme="approx", degree=6, dyadic=0, compute="f64", sort=True,
                    workspace: torch.Tensor | None = None, out: torch.Tensor | None = None,
-                   time_kernel: bool = False, strip_pipeline=None) -> torch.Tensor:
+                   time_kernel: bool = False, strip_pipeline=None, tiled_m: bool = True) -> torch.Tensor:
     """G[a, b] = k_hat(X[a], Y[b]); with Y None (or Y is X) the symmetric Gram of X.
 
     ``time_kernel`` records CUDA events around the wavefront kernel (see ``last_kernel_ms``);
@@ -213,7 +214,8 @@ def sigkernel_gram(X, Y=None, scheme="approx", degree=6, dyadic=0, compute="f64"
     X = as_paths(X)
     Y = X if sym else as_paths(Y)
     flags = _flags(X, (FLAG_SYMMETRIC if sym else 0) | (0 if sort else FLAG_NO_SORT)
-                   | (FLAG_TIME_KERNEL if time_kernel else 0) | _pipe_flags(strip_pipeline))
+                   | (FLAG_TIME_KERNEL if time_kernel else 0) | _pipe_flags(strip_pipeline)
+                   | (0 if tiled_m else FLAG_NO_TILED_M))
     opt = _options(scheme, degree, dyadic, compute, flags)
     cX, cY = _cpaths(X), _cpaths(Y)
     G = out if out is not None else torch.empty(X.count, Y.count, dtype=torch.float64, device="cuda")
@@ -366,7 +368,7 @@ def sigkernel_mmd2(A, B, scheme="approx", degree=6, dyadic=0, compute="f64", unb
     A, B = as_paths(A), as_paths(B)
     cA, cB = _cpaths(A), _cpaths(B)
     opt = _options(scheme, degree, dyadic, compute, _flags(A, FLAG_UNBIASED if unbiased else 0))
-    ws = _workspace(OP_MMD2, cA, cB, A.d, -1, opt)
+    ws = _workspace(OP_MMD2, cA, cB, A.d, 1 if grads else 0, opt)
     out = torch.empty(4, dtype=torch.float64, device="cuda")
     gA = torch.empty(A.rows.shape[0], A.d, dtype=torch.float64, device="cuda") if grads else None
     gB = torch.empty(B.rows.shape[0], B.d, dtype=torch.float64, device="cuda") if grads else None

@@ -149,3 +149,39 @@ def test_mmd2_gradient_central_differences(mmd_batches):
         xm[p, c] -= h
         fd = (path_terms(S, S, O, i, xp) - path_terms(S, S, O, i, xm)) / (2 * h)
         assert abs(g[i, p, c] - fd) < 1e-3 * scale, (side, i, p, c, g[i, p, c], fd)
+
+
+def test_mmd2_long_paths_take_the_checkpointing_adjoint():
+    """40 + 40 paths of 1025 points: one pair's tape is ~67 MB, so a 48 GiB chunk holds fewer pairs
+    than half the adjoint's resident warps and each Gram block takes the checkpointing adjoint.
+    Gradient entries against central differences of the FP64 GPU forward."""
+    A = W.brownian(40, 1025, 2, seed=11)
+    B = W.brownian(40, 1025, 2, seed=12, drift=0.5, vol=1.2)
+    At, Bt = torch.tensor(A, device="cuda"), torch.tensor(B, device="cuda")
+    _, _, gA, gB = sk.sigkernel_mmd2(At, Bt, degree=6, compute="f32", grads=True)
+    torch.cuda.synchronize()
+    assert sk.device_status() == 0
+    gA = gA.cpu().numpy().reshape(A.shape)
+    gB = gB.cpu().numpy().reshape(B.shape)
+    scale = max(np.abs(gA).max(), np.abs(gB).max())
+
+    def path_terms(S, O, i, path):
+        Ssame = S.copy()
+        Ssame[i] = path
+        same = sk.sigkernel_pairs(torch.tensor(Ssame, device="cuda"), torch.tensor(path[None], device="cuda"),
+                                  np.arange(len(S)), np.zeros(len(S), dtype=np.int64), compute="f64").cpu().numpy()
+        cross = sk.sigkernel_pairs(torch.tensor(path[None], device="cuda"), torch.tensor(O, device="cuda"),
+                                   np.zeros(len(O), dtype=np.int64), np.arange(len(O)), compute="f64").cpu().numpy()
+        return (2 * same.sum() - same[i]) / len(S) ** 2 - 2 * cross.sum() / (len(S) * len(O))
+
+    rng = np.random.default_rng(13)
+    h = 1e-4
+    for _ in range(6):
+        side = int(rng.integers(0, 2))
+        S, O, g = (A, B, gA) if side == 0 else (B, A, gB)
+        i, p, c = int(rng.integers(0, 40)), int(rng.integers(0, 1025)), int(rng.integers(0, 2))
+        xp, xm = S[i].copy(), S[i].copy()
+        xp[p, c] += h
+        xm[p, c] -= h
+        fd = (path_terms(S, O, i, xp) - path_terms(S, O, i, xm)) / (2 * h)
+        assert abs(g[i, p, c] - fd) < 1e-3 * scale, (side, i, p, c, g[i, p, c], fd)
