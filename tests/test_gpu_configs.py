@@ -7,7 +7,8 @@ outputs the FP64 oracle can compute one by one.
 * Uneven batch: 4096 pairs, lengths log-uniform in [64, 4096], d = 16, BF16 points, FP32 cells;
   the oracle gets the same BF16-rounded points in FP64.
 * MMD^2: 256 + 256 paths of 513 points, d = 32 (Brownian against Brownian with drift 0.5 and
-  volatility 1.2), FP32 with the checkpointing adjoint.  The value is checked against the three
+  volatility 1.2), FP32, gradients from forward tapes in chunks of pairs (and, for paths too long
+  for a chunk to fill the GPU, from the checkpointing adjoint).  The value is checked against the three
   Grams, Gram entries against the oracle, and the gradient on 16 random coordinates against
   central differences (h = 1e-4) of the FP64 GPU forward.  Perturbing one path changes only its
   own row and column of the Grams, so each difference needs only those pairs.
