@@ -191,7 +191,8 @@ int sigkernel_backward(const sk_paths* X, const sk_paths* Y, int32_t d, int32_t 
                        double* grad_Y, void* workspace, size_t workspace_bytes, void* stream);
 
 /*
- * Forward tape (approximation scheme only).  sigkernel_forward_tape computes the same results as
+ * Forward tape (polynomial schemes; the interpolation scheme for orders 2..12).  sigkernel_forward_tape
+ * computes the same results as
  * sigkernel_pairs / sigkernel_gram (Gram mode when pair_a is NULL; `out` is then [X->count][Y->count]
  * and SK_FLAG_SYMMETRIC applies) and also records, in the caller's `tape`, every cell's inputs
  * (the two incoming edge coefficient vectors, their exponent and the cell's M) and the exponent

@@ -368,7 +368,8 @@ struct TapePlan {
 };
 
 int plan_tape(const sk_paths* X, const sk_paths* Y, const sk_options* o, int T, int64_t npairs, TapePlan& t) {
-    if (o->scheme != SK_POLY_APPROX) return fail(SK_ERR_UNSUPPORTED, "a forward tape is recorded for the approximation scheme");
+    if (o->scheme != SK_POLY_APPROX && o->scheme != SK_POLY_INTERP)
+        return fail(SK_ERR_UNSUPPORTED, "a forward tape is recorded for the polynomial schemes");
     const int lam = o->dyadic;
     const int64_t rows = std::max<int64_t>(X->max_len << lam, 1), cols = std::max<int64_t>(Y->max_len << lam, 1);
     const int64_t nsteps = ((rows + 31) / 32 - 1) * std::max<int64_t>(cols, 32) + 31 + cols;
@@ -701,7 +702,8 @@ int plan_backward_tape(const sk_paths* X, const sk_paths* Y, int32_t d, int32_t 
     if (rc != SK_OK) return rc;
     const Plan& p = b.f;
     if ((rc = plan_tape(X, Y, o, p.T, npairs, b.t)) != SK_OK) return rc;
-    b.kern = p.T ? bwd_tape_ptr_f32(o->degree) : bwd_tape_ptr_f64(o->degree);
+    const bool interp = o->scheme == SK_POLY_INTERP;
+    b.kern = p.T ? bwd_tape_ptr_f32(o->degree, interp) : bwd_tape_ptr_f64(o->degree, interp);
     if (!b.kern) return fail(SK_ERR_UNSUPPORTED, "no adjoint kernel for order %d", o->degree);
     b.ckern = p.T ? bwd_contract_ptr_f32() : bwd_contract_ptr_f64();
     const int step_bytes = 32 * (p.T ? tape_row<float>(o->degree) * 4 : tape_row<double>(o->degree) * 8);

@@ -35,18 +35,19 @@ const void* bwd_approx_ptr_f32(int N, int dmax, int* stack_bytes) {
     return nullptr;
 }
 
-const void* bwd_tape_ptr_f32(int N) {
+const void* bwd_tape_ptr_f32(int N, bool interp) {
+    if (interp) return bwd_tape_interp_ptr_f32(N);
     switch (N) {
-        case 2: return reinterpret_cast<const void*>(&bwd_tape_kernel<float, 2>);
-        case 3: return reinterpret_cast<const void*>(&bwd_tape_kernel<float, 3>);
-        case 4: return reinterpret_cast<const void*>(&bwd_tape_kernel<float, 4>);
-        case 5: return reinterpret_cast<const void*>(&bwd_tape_kernel<float, 5>);
-        case 6: return reinterpret_cast<const void*>(&bwd_tape_kernel<float, 6>);
-        case 7: return reinterpret_cast<const void*>(&bwd_tape_kernel<float, 7>);
-        case 8: return reinterpret_cast<const void*>(&bwd_tape_kernel<float, 8>);
-        case 9: return reinterpret_cast<const void*>(&bwd_tape_kernel<float, 9>);
-        case 10: return reinterpret_cast<const void*>(&bwd_tape_kernel<float, 10>);
-        case 12: return reinterpret_cast<const void*>(&bwd_tape_kernel<float, 12>);
+        case 2: return reinterpret_cast<const void*>(&bwd_tape_kernel<float, 2, false>);
+        case 3: return reinterpret_cast<const void*>(&bwd_tape_kernel<float, 3, false>);
+        case 4: return reinterpret_cast<const void*>(&bwd_tape_kernel<float, 4, false>);
+        case 5: return reinterpret_cast<const void*>(&bwd_tape_kernel<float, 5, false>);
+        case 6: return reinterpret_cast<const void*>(&bwd_tape_kernel<float, 6, false>);
+        case 7: return reinterpret_cast<const void*>(&bwd_tape_kernel<float, 7, false>);
+        case 8: return reinterpret_cast<const void*>(&bwd_tape_kernel<float, 8, false>);
+        case 9: return reinterpret_cast<const void*>(&bwd_tape_kernel<float, 9, false>);
+        case 10: return reinterpret_cast<const void*>(&bwd_tape_kernel<float, 10, false>);
+        case 12: return reinterpret_cast<const void*>(&bwd_tape_kernel<float, 12, false>);
         default: return nullptr;
     }
 }

@@ -35,18 +35,19 @@ const void* bwd_approx_ptr_f64(int N, int dmax, int* stack_bytes) {
     return nullptr;
 }
 
-const void* bwd_tape_ptr_f64(int N) {
+const void* bwd_tape_ptr_f64(int N, bool interp) {
+    if (interp) return bwd_tape_interp_ptr_f64(N);
     switch (N) {
-        case 2: return reinterpret_cast<const void*>(&bwd_tape_kernel<double, 2>);
-        case 3: return reinterpret_cast<const void*>(&bwd_tape_kernel<double, 3>);
-        case 4: return reinterpret_cast<const void*>(&bwd_tape_kernel<double, 4>);
-        case 5: return reinterpret_cast<const void*>(&bwd_tape_kernel<double, 5>);
-        case 6: return reinterpret_cast<const void*>(&bwd_tape_kernel<double, 6>);
-        case 7: return reinterpret_cast<const void*>(&bwd_tape_kernel<double, 7>);
-        case 8: return reinterpret_cast<const void*>(&bwd_tape_kernel<double, 8>);
-        case 9: return reinterpret_cast<const void*>(&bwd_tape_kernel<double, 9>);
-        case 10: return reinterpret_cast<const void*>(&bwd_tape_kernel<double, 10>);
-        case 12: return reinterpret_cast<const void*>(&bwd_tape_kernel<double, 12>);
+        case 2: return reinterpret_cast<const void*>(&bwd_tape_kernel<double, 2, false>);
+        case 3: return reinterpret_cast<const void*>(&bwd_tape_kernel<double, 3, false>);
+        case 4: return reinterpret_cast<const void*>(&bwd_tape_kernel<double, 4, false>);
+        case 5: return reinterpret_cast<const void*>(&bwd_tape_kernel<double, 5, false>);
+        case 6: return reinterpret_cast<const void*>(&bwd_tape_kernel<double, 6, false>);
+        case 7: return reinterpret_cast<const void*>(&bwd_tape_kernel<double, 7, false>);
+        case 8: return reinterpret_cast<const void*>(&bwd_tape_kernel<double, 8, false>);
+        case 9: return reinterpret_cast<const void*>(&bwd_tape_kernel<double, 9, false>);
+        case 10: return reinterpret_cast<const void*>(&bwd_tape_kernel<double, 10, false>);
+        case 12: return reinterpret_cast<const void*>(&bwd_tape_kernel<double, 12, false>);
         default: return nullptr;
     }
 }

@@ -172,6 +172,77 @@ __device__ __forceinline__ void cell_adjoint(const T (&a)[N + 1], const T (&b)[N
     mbar = mb;
 }
 
+// Adjoint of one interpolation cell.  The forward (cell_series<INTERP>, then project) computes,
+// for n = 0..NE,
+//   ct_n = e_n ha_n + sum_{k <= min(n, N)} a_k  e_{n-k},   ha_n = sum_{k=1..N} b_k n!/(n+k)!
+//   cr_n = e_n hb_n + sum_{k <= min(n, N)} b'_k e_{n-k},   hb_n = sum_{k=1..N} a_k n!/(n+k)!
+// with b'_0 = a_0 (the printed corner term of eq. (interpformula)) and b'_k = b_k, and then
+// a' = P ct, b' = P cr.  Given the adjoints gt = ct_bar and gr = cr_bar (after the transpose of
+// P), it returns a_bar (ra), b_bar (rb; b_0 does not enter) and M_bar = sum_m e_bar_m e_{m-1}.
+template <typename T, int N, int NE>
+__device__ __forceinline__ void cell_adjoint_interp(const T (&a)[N + 1], const T (&b)[N + 1], const T (&e)[NE + 1],
+                                                    const T (&gt)[NE + 1], const T (&gr)[NE + 1], T (&ra)[N + 1],
+                                                    T (&rb)[N + 1], T& mbar) {
+    T al[NE + 1], be[NE + 1];  // gr_n e_n (weights of hb and of the corner), gt_n e_n (of ha)
+#pragma unroll
+    for (int n = 0; n <= NE; ++n) { al[n] = gr[n] * e[n]; be[n] = gt[n] * e[n]; }
+#pragma unroll
+    for (int k = 0; k <= N; ++k) {
+        T va = T(0), vb = T(0);
+        if (k >= 1) {
+#pragma unroll
+            for (int n = 0; n <= NE; ++n) {
+                va = fma(al[n], Tab<T>::hank(n, k), va);
+                vb = fma(be[n], Tab<T>::hank(n, k), vb);
+            }
+        } else {
+#pragma unroll
+            for (int n = 0; n <= NE; ++n) va += al[n];  // a_0 as the right edge's b'_0
+        }
+#pragma unroll
+        for (int n = k; n <= NE; ++n) {
+            va = fma(gt[n], e[n - k], va);
+            if (k >= 1) vb = fma(gr[n], e[n - k], vb);
+        }
+        ra[k] = va;
+        rb[k] = vb;
+    }
+    T mb = T(0);
+#pragma unroll
+    for (int m = 1; m <= NE; ++m) {
+        T ha = b[1] * Tab<T>::hank(m, 1);
+        T hb = a[1] * Tab<T>::hank(m, 1);
+#pragma unroll
+        for (int k = 2; k <= N; ++k) {
+            ha = fma(b[k], Tab<T>::hank(m, k), ha);
+            hb = fma(a[k], Tab<T>::hank(m, k), hb);
+        }
+        T eb = fma(gt[m], ha, gr[m] * hb);
+#pragma unroll
+        for (int k = 0; k <= N && m + k <= NE; ++k) {
+            eb = fma(gt[m + k], a[k], eb);
+            eb = fma(gr[m + k], k == 0 ? a[0] : b[k], eb);
+        }
+        mb = fma(eb, e[m - 1], mb);
+    }
+    mbar = mb;
+}
+
+// Transpose of the interpolation projection: c_bar_n = g_n (n <= N), c_bar_j = sum_n g_n P[n][j]
+// (j > N), for the adjoint g of a projected edge.
+template <typename T, int N, int NE>
+__device__ __forceinline__ void project_transpose(const T (&g)[N + 1], T (&c)[NE + 1]) {
+#pragma unroll
+    for (int n = 0; n <= N; ++n) c[n] = g[n];
+#pragma unroll
+    for (int j = N + 1; j <= NE; ++j) {
+        T v = T(0);
+#pragma unroll
+        for (int n = 0; n <= N; ++n) v = fma(g[n], Tab<T>::proj(N, n, j - N - 1), v);
+        c[j] = v;
+    }
+}
+
 // Shared memory of one warp: the K-step stack (a[N+1], b[N+1], M per lane, plus exponents),
 // then each lane's dk/dx accumulator of its row ([32][dpad + 1]; the odd stride puts the lanes'
 // scalar accesses in distinct banks).
@@ -570,9 +641,15 @@ __global__ void __launch_bounds__(kFwdWarps * 32, (bwd_min_blocks<T, N, K>()))
 // ---------------------------------------------------------------------------------------------
 constexpr int kTapeRing = 4;
 
-template <typename T, int N>
+template <typename T, int N, bool INTERP>
 __host__ __device__ constexpr int bwd_tape_min_blocks() {
-    return sizeof(T) == 8 ? 2 : 4;
+    return sizeof(T) == 8 ? (INTERP ? 1 : 2) : (INTERP ? 3 : 4);
+}
+
+// Series terms of a cell's adjoint: N + 1, or N + 1 + J for the interpolation scheme.
+template <typename T, int N, bool INTERP>
+__host__ __device__ constexpr int bwd_series_top() {
+    return INTERP ? N + (sizeof(T) == 8 ? kJF64 : kJF32) : N;
 }
 
 // Shared memory of one warp for the tape adjoint: the ring and its mbarriers.
@@ -589,9 +666,10 @@ __device__ __forceinline__ double item_gbar(const BwdParams& B, int64_t item, co
     return B.gout[P.a * L.ldo + P.b] + (P.a != P.b ? B.gout[P.b * L.ldo + P.a] : 0.0);
 }
 
-template <typename T, int N>
-__global__ void __launch_bounds__(kFwdWarps * 32, (bwd_tape_min_blocks<T, N>()))
+template <typename T, int N, bool INTERP>
+__global__ void __launch_bounds__(kFwdWarps * 32, (bwd_tape_min_blocks<T, N, INTERP>()))
     bwd_tape_kernel(BwdParams B) {
+    constexpr int NE = bwd_series_top<T, N, INTERP>();
     constexpr bool kRescale = std::is_same<T, float>::value;
     using V = typename Vec<T>::type;
     constexpr int W = Vec<T>::W;
@@ -642,15 +720,16 @@ __global__ void __launch_bounds__(kFwdWarps * 32, (bwd_tape_min_blocks<T, N>()))
         // row's upper input is zero: it comes from a lane beyond the last row, never active in
         // this item, whose gbo stays zero (lane 31 is handled where it reads the hand-off).  The
         // corner cell (rows-1, cols-1), run by lane last_lane at the first reverse step, is
-        // seeded from the endpoint average: both inputs are 1/(2 n!).
+        // seeded from the endpoint average: for the approximation scheme both output edges get
+        // 1/(2 n!); for the interpolation scheme the unprojected series do (n = 0..N+J).
         T gra[N + 1], gbo[N + 1];
         int gea = kZeroExp, gbe = kZeroExp;
 #pragma unroll
         for (int n = 0; n <= N; ++n) {
-            gra[n] = lane == last_lane ? static_cast<T>(0.5 * cx_rfact(n)) : T(0);
+            gra[n] = (!INTERP && lane == last_lane) ? static_cast<T>(0.5 * cx_rfact(n)) : T(0);
             gbo[n] = T(0);
         }
-        if (lane == last_lane) gea = 0;
+        if (!INTERP && lane == last_lane) gea = 0;
 
         // fill the ring with the last kTapeRing steps (step t lives in slot t % kTapeRing)
         if (lane == 0) {
@@ -723,7 +802,7 @@ __global__ void __launch_bounds__(kFwdWarps * 32, (bwd_tape_min_blocks<T, N>()))
                         gbe_in = kRescale ? rexp[jj] : 0;
                     }
                 }
-                if (step == nsteps - 1) {          // warp-uniform: the corner cell's upper input
+                if (!INTERP && step == nsteps - 1) {  // warp-uniform: the corner cell's upper input
 #pragma unroll
                     for (int n = 0; n <= N; ++n) gb_in[n] = static_cast<T>(0.5 * cx_rfact(n));
                     gbe_in = 0;
@@ -743,13 +822,28 @@ __global__ void __launch_bounds__(kFwdWarps * 32, (bwd_tape_min_blocks<T, N>()))
                     }
                 }
                 unit_scale<T, N>(fa, fb, ef);
-                T e[N + 1];
-                build_exp_series<T, N>(M, L.tau, e);
+                T e[NE + 1];
+                build_exp_series<T, NE>(M, L.tau, e);
                 T mbar;
                 T ga_in[N + 1];
 #pragma unroll
                 for (int n = 0; n <= N; ++n) ga_in[n] = gra[n];
-                cell_adjoint<T, N>(fa, fb, e, ga_in, gb_in, gra, gbo, mbar);
+                if constexpr (INTERP) {
+                    T gt[NE + 1], gr[NE + 1];
+                    project_transpose<T, N, NE>(ga_in, gt);
+                    project_transpose<T, N, NE>(gb_in, gr);
+                    if (step == nsteps - 1) {  // warp-uniform: the corner's endpoint seed
+#pragma unroll
+                        for (int n = 0; n <= NE; ++n) {
+                            gt[n] = static_cast<T>(0.5 * cx_rfact(n));
+                            gr[n] = gt[n];
+                        }
+                        eg = 0;
+                    }
+                    cell_adjoint_interp<T, N, NE>(fa, fb, e, gt, gr, gra, gbo, mbar);
+                } else {
+                    cell_adjoint<T, N>(fa, fb, e, ga_in, gb_in, gra, gbo, mbar);
+                }
                 mrel = mbar * pow2c<T>(eg + ef - ek - 2 * lam);
                 gea = eg;
                 if (kRescale && (step & 3) == 0) {  // keep the adjoints within [2^-64, 2^64]

@@ -126,7 +126,7 @@ struct Launch {
     void* scratch;           // per-warp-slot hand-off buffers
     int64_t scratch_stride;  // bytes per warp slot
     float tau;               // |M| above which an FP32 map is built in FP64
-    // Optional tape of the forward pass (approximation scheme): per work item, per warp step, per
+    // Optional tape of the forward pass (polynomial schemes): per work item, per warp step, per
     // lane, the cell's inputs (a[N+1], b[N+1], exponent, M) in a padded 16-byte-vector row; plus
     // the exponent of k_hat per item.  NULL when not recorded.
     void* tape;

@@ -65,10 +65,14 @@ int bwd_segment_f64();
 }  // namespace sk
 
 namespace sk {
-// Tape-driven adjoint of the approximation scheme (NULL when no kernel exists for order N) and
+// Tape-driven adjoint of the polynomial schemes (NULL when no kernel exists for order N) and
 // the contraction of its dk/dM buffer into increment gradients.
-const void* bwd_tape_ptr_f32(int N);
-const void* bwd_tape_ptr_f64(int N);
+const void* bwd_tape_ptr_f32(int N, bool interp);
+const void* bwd_tape_ptr_f64(int N, bool interp);
+const void* bwd_tape_interp_ptr_f32(int N);
+const void* bwd_tape_interp_ptr_f64(int N);
+const void* bwd_tape_interp_ptr_f64_0(int N);
+const void* bwd_tape_interp_ptr_f64_1(int N);
 const void* bwd_contract_ptr_f32();
 const void* bwd_contract_ptr_f64();
 }  // namespace sk

@@ -305,7 +305,7 @@ __device__ __forceinline__ void sweep_poly(const Launch& L, int64_t item, const 
         T M;
         if constexpr (MT) M = active ? mbuf[((sl & 1) * 32 + lane) * static_cast<int64_t>(mcols) + jc] : T(0);
         else M = row_dot<T>(xrow, ybase + static_cast<int64_t>(jc >> lam) * dpad, L.nvec) * sub;
-        if constexpr (!INTERP && CW == 1) {
+        if constexpr (CW == 1) {
             if (L.tape != nullptr) {
                 // Record the cell's inputs (a, b, exponent, M) for the adjoint: each lane writes
                 // its row into a shared-memory slot laid out [vector][lane], then one lane moves
@@ -347,10 +347,15 @@ __device__ __forceinline__ void sweep_poly(const Launch& L, int64_t item, const 
         cell_series<T, N, NE, INTERP>(a, b, e, ct, cr);
         if constexpr (INTERP) {
             if (active && row == rows - 1 && jj == cols - 1) {
-                double v = 0.5 * (series_at_one<T, NE>(ct) + series_at_one<T, NE>(cr));
-                if (kRescale) v = ldexp(v, ea);
+                const double v0 = 0.5 * (series_at_one<T, NE>(ct) + series_at_one<T, NE>(cr));
+                const double v = kRescale ? ldexp(v0, ea) : v0;
                 if (!isfinite(v)) record_error(SK_ERR_NONFINITE);
                 write_result(L, item, P, v);
+                if (L.tape_ek != nullptr) {
+                    int e2 = 0;
+                    if (v0 != 0.0) frexp(v0, &e2);
+                    L.tape_ek[item] = (kRescale ? ea : 0) + e2;
+                }
             }
         }
         project<T, N, NE, INTERP>(ct, a);
@@ -479,7 +484,7 @@ __global__ void __launch_bounds__((CW > 1 ? CW : kFwdWarps) * 32,
         if (trivial_pair(L, item, P)) continue;
         sweep_poly<T, N, NE, INTERP, 1, MT>(L, item, P, 0, own, own, nullptr, buf_cols, tape_stage, xstage);
     }
-    if (!INTERP && L.tape != nullptr && (threadIdx.x & 31) == 0) bulk_wait_all();  // no copy outlives the staging smem
+    if (L.tape != nullptr && (threadIdx.x & 31) == 0) bulk_wait_all();  // no copy outlives the staging smem
 }
 
 }  // namespace sk

@@ -30,7 +30,7 @@ def _scaled_err(g, ref):
     return float(np.max(np.abs(g - ref)) / max(np.max(np.abs(ref)), 1e-300))
 
 
-def _oracle_gram_grad(X, Y, Wt, N, lam, sym):
+def _oracle_gram_grad(X, Y, Wt, N, lam, sym, scheme="approx"):
     """d/dX, d/dY of sum_ab Wt[a,b] k(X_a, Y_b) from the oracle's complex-step gradients."""
     gX = np.zeros_like(X)
     gY = np.zeros_like(Y)
@@ -38,7 +38,7 @@ def _oracle_gram_grad(X, Y, Wt, N, lam, sym):
         for b in range(Y.shape[0]):
             if Wt[a, b] == 0.0:
                 continue
-            gx, gy = oracle.grad(X[a], Y[b], "approx", N, lam)
+            gx, gy = oracle.grad(X[a], Y[b], scheme, N, lam)
             gX[a] += Wt[a, b] * gx
             gY[b] += Wt[a, b] * gy
     if sym:
@@ -308,6 +308,42 @@ def test_tape_backward_long_paths_match_checkpoint_adjoint(compute, tol):
     assert np.all(np.isfinite(gX.cpu().numpy()))
     assert _scaled_err(gX.cpu().numpy(), cX.cpu().numpy()) < tol
     assert _scaled_err(gY.cpu().numpy(), cY.cpu().numpy()) < tol
+
+
+# ------------------------------------------------------------------------------------------
+# Adjoint of the interpolation scheme (tape path): projection transpose, the corner term and the
+# endpoint seed on the unprojected series
+# ------------------------------------------------------------------------------------------
+@pytest.mark.parametrize("compute,tol", [("f64", 1e-9), ("f32", 1e-4)])
+@pytest.mark.parametrize("N", [3, 6])
+def test_tape_backward_interp_matches_oracle(compute, tol, N):
+    X = W.brownian(2, 33, 2, seed=81)   # 32 rows: the top row is lane 31 of a full strip
+    Y = W.brownian(2, 25, 2, seed=82)
+    Wt = np.array([[0.9, -0.4], [1.7, 0.3]])
+    G, tape = sk.sigkernel_forward_tape(_cuda(X), _cuda(Y), scheme="interp", degree=N, compute=compute)
+    G0 = sk.sigkernel_gram(_cuda(X), _cuda(Y), scheme="interp", degree=N, compute=compute)
+    gX, gY = sk.sigkernel_backward_tape(tape, _cuda(Wt), _cuda(X), _cuda(Y), scheme="interp", degree=N,
+                                        compute=compute)
+    torch.cuda.synchronize()
+    assert sk.device_status() == 0
+    assert torch.equal(G, G0)
+    rX, rY = _oracle_gram_grad(X, Y, Wt, N, 0, False, scheme="interp")
+    assert _scaled_err(gX.cpu().numpy().reshape(X.shape), rX) < tol
+    assert _scaled_err(gY.cpu().numpy().reshape(Y.shape), rY) < tol
+
+
+def test_tape_backward_interp_symmetric_dyadic_rescaled():
+    X = 10.0 * W.brownian(3, 30, 2, seed=83)   # |k| far outside FP32 without the exponents
+    G, tape = sk.sigkernel_forward_tape(_cuda(X), None, scheme="interp", degree=5, dyadic=1, compute="f32")
+    Wt = np.random.default_rng(84).normal(size=(3, 3))
+    gX, _ = sk.sigkernel_backward_tape(tape, _cuda(Wt), _cuda(X), None, scheme="interp", degree=5, dyadic=1,
+                                       compute="f32")
+    torch.cuda.synchronize()
+    assert sk.device_status() == 0
+    got = gX.cpu().numpy().reshape(X.shape)
+    assert np.all(np.isfinite(got))
+    rX, _ = _oracle_gram_grad(X, X, Wt, 5, 1, True, scheme="interp")
+    assert _scaled_err(got, rX) < 1e-3
 
 
 def test_autograd_with_tape():
