@@ -130,6 +130,40 @@ template <typename T, int N>
 __device__ __forceinline__ void cell_adjoint(const T (&a)[N + 1], const T (&b)[N + 1], const T (&e)[N + 1],
                                              const T (&ga)[N + 1], const T (&gb)[N + 1], T (&ra)[N + 1],
                                              T (&rb)[N + 1], T& mbar) {
+    if constexpr (std::is_same<T, float>::value) {
+        // FP32: the a- and b-side adjoints run the same products on different data, so they go as
+        // packed pairs through the two-wide FP32 instructions; the dk/dM sum over n is split into
+        // its a- and b-side halves, added once per m.
+        float2 w[N + 1];  // (gb_n e_n, ga_n e_n): weights of the Hankel couplings
+#pragma unroll
+        for (int n = 0; n <= N; ++n) w[n] = __fmul2_rn(make_float2(gb[n], ga[n]), dup2(e[n]));
+#pragma unroll
+        for (int k = 0; k <= N; ++k) {
+            float2 v = make_float2(0.f, 0.f);  // (ra_k, rb_k)
+            if (k >= 1) {
+#pragma unroll
+                for (int n = 0; n <= N; ++n) v = __ffma2_rn(w[n], dup2(Tab<float>::hank(n, k)), v);
+            }
+#pragma unroll
+            for (int n = k; n <= N; ++n) v = __ffma2_rn(make_float2(ga[n], gb[n]), dup2(e[n - k]), v);
+            ra[k] = v.x;
+            rb[k] = v.y;
+        }
+        float mb = 0.f;
+#pragma unroll
+        for (int m = 1; m <= N; ++m) {
+            float2 h = __fmul2_rn(make_float2(b[1], a[1]), dup2(Tab<float>::hank(m, 1)));  // (ha, hb)
+#pragma unroll
+            for (int k = 2; k <= N; ++k) h = __ffma2_rn(make_float2(b[k], a[k]), dup2(Tab<float>::hank(m, k)), h);
+            float2 eb = __fmul2_rn(make_float2(ga[m], gb[m]), h);
+#pragma unroll
+            for (int n = m; n <= N; ++n)
+                eb = __ffma2_rn(make_float2(ga[n], gb[n]), make_float2(a[n - m], b[n - m]), eb);
+            mb = fma(eb.x + eb.y, e[m - 1], mb);
+        }
+        mbar = mb;
+        return;
+    }
     T al[N + 1], be[N + 1];
 #pragma unroll
     for (int n = 0; n <= N; ++n) { al[n] = ga[n] * e[n]; be[n] = gb[n] * e[n]; }
