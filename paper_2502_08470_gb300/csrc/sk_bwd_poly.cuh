@@ -217,6 +217,44 @@ template <typename T, int N, int NE>
 __device__ __forceinline__ void cell_adjoint_interp(const T (&a)[N + 1], const T (&b)[N + 1], const T (&e)[NE + 1],
                                                     const T (&gt)[NE + 1], const T (&gr)[NE + 1], T (&ra)[N + 1],
                                                     T (&rb)[N + 1], T& mbar) {
+    if constexpr (std::is_same<T, float>::value) {
+        // FP32: a- and b-sides as packed pairs through the two-wide FP32 instructions, as in
+        // cell_adjoint; the corner term and the dk/dM halves are summed once.
+        float2 w[NE + 1];  // (gr_n e_n, gt_n e_n)
+        float corner = 0.f;
+#pragma unroll
+        for (int n = 0; n <= NE; ++n) {
+            w[n] = __fmul2_rn(make_float2(gr[n], gt[n]), dup2(e[n]));
+            corner += w[n].x;  // a_0 as the right edge's b'_0
+        }
+#pragma unroll
+        for (int k = 0; k <= N; ++k) {
+            float2 v = make_float2(k == 0 ? corner : 0.f, 0.f);  // (ra_k, rb_k)
+            if (k >= 1) {
+#pragma unroll
+                for (int n = 0; n <= NE; ++n) v = __ffma2_rn(w[n], dup2(Tab<float>::hank(n, k)), v);
+            }
+#pragma unroll
+            for (int n = k; n <= NE; ++n)
+                v = __ffma2_rn(make_float2(gt[n], k >= 1 ? gr[n] : 0.f), dup2(e[n - k]), v);
+            ra[k] = v.x;
+            rb[k] = v.y;
+        }
+        float mb = 0.f;
+#pragma unroll
+        for (int m = 1; m <= NE; ++m) {
+            float2 h = __fmul2_rn(make_float2(b[1], a[1]), dup2(Tab<float>::hank(m, 1)));  // (ha, hb)
+#pragma unroll
+            for (int k = 2; k <= N; ++k) h = __ffma2_rn(make_float2(b[k], a[k]), dup2(Tab<float>::hank(m, k)), h);
+            float2 eb = __fmul2_rn(make_float2(gt[m], gr[m]), h);
+#pragma unroll
+            for (int k = 0; k <= N && m + k <= NE; ++k)
+                eb = __ffma2_rn(make_float2(gt[m + k], gr[m + k]), make_float2(a[k], k == 0 ? a[0] : b[k]), eb);
+            mb = fma(eb.x + eb.y, e[m - 1], mb);
+        }
+        mbar = mb;
+        return;
+    }
     T al[NE + 1], be[NE + 1];  // gr_n e_n (weights of hb and of the corner), gt_n e_n (of ha)
 #pragma unroll
     for (int n = 0; n <= NE; ++n) { al[n] = gr[n] * e[n]; be[n] = gt[n] * e[n]; }

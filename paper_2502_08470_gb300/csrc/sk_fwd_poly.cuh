@@ -67,24 +67,6 @@ __device__ __forceinline__ float2 dup2(float v) { return make_float2(v, v); }
 template <typename T, int N, int NE, bool INTERP>
 __device__ __forceinline__ void cell_series(const T (&a)[N + 1], const T (&b)[N + 1], const T (&e)[NE + 1],
                                             T (&ct)[NE + 1], T (&cr)[NE + 1]) {
-    if constexpr (std::is_same<T, float>::value) {
-        // FP32: the two edges run the same chain of products on different data, so they go as one
-        // packed pair through the two-wide FP32 instructions (__ffma2_rn / __fmul2_rn): half the
-        // issue slots, and each half rounds exactly as the scalar fmaf/fmul below.
-#pragma unroll
-        for (int n = 0; n <= NE; ++n) {
-            float2 h = __fmul2_rn(make_float2(b[1], a[1]), dup2(Tab<float>::hank(n, 1)));  // (ha, hb)
-#pragma unroll
-            for (int k = 2; k <= N; ++k) h = __ffma2_rn(make_float2(b[k], a[k]), dup2(Tab<float>::hank(n, k)), h);
-            float2 v = __fmul2_rn(dup2(e[n]), h);  // (vt, vr)
-#pragma unroll
-            for (int k = 0; k <= (n < N ? n : N); ++k)
-                v = __ffma2_rn(make_float2(a[k], (INTERP && k == 0) ? a[0] : b[k]), dup2(e[n - k]), v);
-            ct[n] = v.x;
-            cr[n] = v.y;
-        }
-        return;
-    }
 #pragma unroll
     for (int n = 0; n <= NE; ++n) {
         // coupling through the opposite edge: sum_{k>=1} (.)_k n!/(n+k)!
@@ -108,34 +90,24 @@ __device__ __forceinline__ void cell_series(const T (&a)[N + 1], const T (&b)[N 
     }
 }
 
-// Both edges through the interpolation projection (FP32: as packed pairs, same rounding as project).
+// Both edges through the interpolation projection.  (Pairing the two edges through the two-wide
+// FP32 instructions, as the adjoint does, measured slower here: building the pairs from the
+// separately held edges cost more instructions than it saved.)
 template <typename T, int N, int NE, bool INTERP>
 __device__ __forceinline__ void project_both(const T (&ct)[NE + 1], const T (&cr)[NE + 1], T (&a)[N + 1],
                                              T (&bo)[N + 1]) {
-    if constexpr (std::is_same<T, float>::value && INTERP) {
 #pragma unroll
-        for (int n = 0; n <= N; ++n) {
-            float2 v = make_float2(ct[n], cr[n]);
+    for (int n = 0; n <= N; ++n) {
+        T vt = ct[n], vr = cr[n];
+        if constexpr (INTERP) {
 #pragma unroll
-            for (int j = N + 1; j <= NE; ++j)
-                v = __ffma2_rn(dup2(Tab<float>::proj(N, n, j - N - 1)), make_float2(ct[j], cr[j]), v);
-            a[n] = v.x;
-            bo[n] = v.y;
-        }
-    } else {
-#pragma unroll
-        for (int n = 0; n <= N; ++n) {
-            T vt = ct[n], vr = cr[n];
-            if constexpr (INTERP) {
-#pragma unroll
-                for (int j = N + 1; j <= NE; ++j) {
-                    vt = fma(Tab<T>::proj(N, n, j - N - 1), ct[j], vt);
-                    vr = fma(Tab<T>::proj(N, n, j - N - 1), cr[j], vr);
-                }
+            for (int j = N + 1; j <= NE; ++j) {
+                vt = fma(Tab<T>::proj(N, n, j - N - 1), ct[j], vt);
+                vr = fma(Tab<T>::proj(N, n, j - N - 1), cr[j], vr);
             }
-            a[n] = vt;
-            bo[n] = vr;
         }
+        a[n] = vt;
+        bo[n] = vr;
     }
 }
 
