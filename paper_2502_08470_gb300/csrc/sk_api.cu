@@ -456,9 +456,9 @@ int run_forward(const sk_paths* X, const sk_paths* Y, int32_t d, int32_t dtype, 
     int64_t buf_cols = p.buf_cols;
     void* args[] = {&L, &buf_cols};
     int smem = p.smem_x;  // tiled-M x rows
-    if (tape) {  // two staging slots per warp for the tape's bulk copies
+    if (tape) {  // kTapeSlots staging slots per warp for the tape's bulk copies
         const int step_bytes = 32 * (p.T ? tape_row<float>(o->degree) * 4 : tape_row<double>(o->degree) * 8);
-        smem += (p.threads / 32) * 2 * step_bytes;
+        smem += (p.threads / 32) * kTapeSlots * step_bytes;
     }
     if (smem > 48 * 1024) SK_CUDA(cudaFuncSetAttribute(p.kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     const bool timed = (o->flags & SK_FLAG_TIME_KERNEL) != 0;

@@ -138,6 +138,13 @@ __device__ __forceinline__ T pow2t(int e) {
     else return pow2d(e);
 }
 
+// Staging slots per warp for the tape's bulk stores: a slot is refilled once the copy issued from
+// it kTapeSlots steps earlier has read it, so up to kTapeSlots steps are in flight per warp.  Two
+// measured fastest on the 128x128 Gram of 257-point paths (forward with tape: 14.9 ms; three
+// slots 15.5 ms, four 18.0 ms): the staging shared memory comes out of the L1 that serves the
+// increment rows.
+constexpr int kTapeSlots = 2;
+
 // Bytes of one warp step of the tape (32 lanes x one padded row of cell inputs).
 template <typename T, int N>
 __host__ __device__ constexpr int fwd_tape_step_bytes() {
@@ -333,12 +340,13 @@ __device__ __forceinline__ void sweep_poly(const Launch& L, int64_t item, const 
             if (L.tape != nullptr) {
                 // Record the cell's inputs (a, b, exponent, M) for the adjoint: each lane writes
                 // its row into a shared-memory slot laid out [vector][lane], then one lane moves
-                // the whole step (32 rows) to the tape with a bulk copy.  Two slots alternate; a
-                // slot is rewritten only after the copy issued from it two steps ago has read it.
+                // the whole step (32 rows) to the tape with a bulk copy.  kTapeSlots slots rotate;
+                // a slot is rewritten only after the copy issued from it kTapeSlots steps ago has
+                // read it.
                 constexpr int TR = tape_row<T>(N);
                 constexpr int kStepBytes = 32 * TR * static_cast<int>(sizeof(T));
-                V* slot_v = reinterpret_cast<V*>(tape_stage + (step & 1) * kStepBytes);
-                if (lane == 0) bulk_wait_read<1>();
+                V* slot_v = reinterpret_cast<V*>(tape_stage + (step % kTapeSlots) * kStepBytes);
+                if (lane == 0) bulk_wait_read<kTapeSlots - 1>();
                 __syncwarp();
 #pragma unroll
                 for (int v = 0; v < TR / W; ++v) {
@@ -474,8 +482,8 @@ __global__ void __launch_bounds__((CW > 1 ? CW : kFwdWarps) * 32,
     // dynamic shared memory: tape staging (two step slots per warp, with a tape), then the x rows
     // of the tiled-M producer ([32][dpad] per warp, with L.mtile)
     extern __shared__ __align__(128) unsigned char fwd_smem[];
-    unsigned char* tape_stage = fwd_smem + wib * 2 * fwd_tape_step_bytes<T, N>();
-    T* xstage = reinterpret_cast<T*>(fwd_smem + (L.tape != nullptr ? nw * 2 * fwd_tape_step_bytes<T, N>() : 0)) +
+    unsigned char* tape_stage = fwd_smem + wib * kTapeSlots * fwd_tape_step_bytes<T, N>();
+    T* xstage = reinterpret_cast<T*>(fwd_smem + (L.tape != nullptr ? nw * kTapeSlots * fwd_tape_step_bytes<T, N>() : 0)) +
                 wib * 32 * L.dpad;
 
     if constexpr (CW > 1) {
