@@ -88,10 +88,10 @@ def tape_adjoint_bytes(pairs: int, points: int, N: int = DEGREE) -> int:
 
 
 # DRAM traffic of bwd_tape_kernel<float,6> per launch from one ncu capture on 64x64 pairs of
-# 129-point paths (read 4.603778 GB + write 0.333018 GB), as a multiple of that launch's
+# 129-point paths (read 4.605319 GB + write 0.333258 GB), as a multiple of that launch's
 # algorithmic bytes.  The traffic scales with the tape, so the bench launch's traffic is this ratio
 # times its own algorithmic bytes.  Valid only while the kernel is unchanged since that capture.
-NCU_TAPE_TRAFFIC_RATIO = (4.603778e9 + 0.333018e9) / tape_adjoint_bytes(64 * 64, 129)
+NCU_TAPE_TRAFFIC_RATIO = (4.605319e9 + 0.333258e9) / tape_adjoint_bytes(64 * 64, 129)
 HBM_GBS = 6681.2  # measured copy bandwidth of this GB300 pool
 
 
