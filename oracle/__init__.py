@@ -10,6 +10,7 @@ Schemes (ids follow the C library's enum for convenience of the tests only):
   1 "fd2"     second-order explicit finite differences              (eq. secondexplicitscheme)
   2 "approx"  polynomial approximation scheme of order N            (Def. polyapproxscheme)
   3 "interp"  polynomial interpolation scheme of order N            (Def. polyinterpscheme)
+  4 "fd_implicit"  implicit finite differences, four-corner trapezoid rule (Remark higherfd)
 """
 from __future__ import annotations
 
@@ -27,7 +28,7 @@ _SO = os.path.join(_BUILD_DIR, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
 
-SCHEMES = {"fd1": 0, "fd2": 1, "approx": 2, "interp": 3}
+SCHEMES = {"fd1": 0, "fd2": 1, "approx": 2, "interp": 3, "fd_implicit": 4}
 
 
 def build(force: bool = False) -> str:

@@ -53,10 +53,20 @@ static double* FN(refine_grid)(const double* s, int64_t L, int lam) {
 
 /* ---------------------------------------------------------------------------------------------
  * Finite differences on the dyadic grid P_lambda (Definition "dyadic scheme", Section 2) with
- * the first-order explicit update, and the second-order explicit update of eq.
- * (secondexplicitscheme), Remark "higherfd".  The garbled arguments k(t_{i+1}, v_j) +
- * k(t_i, v_{j+1}) in the Definition are read as k(s_{i+1}, t_j) + k(s_i, t_{j+1}), the two
- * nodes of the trapezoid rule of Section 2.
+ * the first-order explicit update (order 1), the second-order explicit update of eq.
+ * (secondexplicitscheme), Remark "higherfd" (order 2), and the implicit update of Remark
+ * "higherfd" (order 3).  The garbled arguments k(t_{i+1}, v_j) + k(t_i, v_{j+1}) in the
+ * Definition are read as k(s_{i+1}, t_j) + k(s_i, t_{j+1}), the two nodes of the trapezoid rule
+ * of Section 2.
+ *
+ * Implicit update.  The double integral of eq. (integralpde) over one sub-cell is taken by the
+ * two-dimensional trapezoid rule on its four corners, (area/4) (k00 + k10 + k01 + k11), so with
+ * m = C (s - u)(t - v):
+ *     k11 = k10 + k01 - k00 + (m/4) (k00 + k10 + k01 + k11).
+ * The Remark prints the factor as 1/2; with 1/2 a single cell from k = 1 on its edges gives
+ * k11 = 1 + 2m + O(m^2) where the exact solution is 1 + m + m^2/4 + ..., so the factor is read
+ * as the trapezoid rule's 1/4.  The equation is linear in k11 and is solved for it below; it
+ * has no solution when m = 4 (the result is then inf or NaN).
  * ------------------------------------------------------------------------------------------- */
 static REAL FN(fd)(const REAL* x, int64_t Lx, const REAL* y, int64_t Ly, int d, int order, int lam) {
     if (Lx < 2 || Ly < 2) return 1.0;
@@ -75,8 +85,13 @@ static REAL FN(fd)(const REAL* x, int64_t Lx, const REAL* y, int64_t Ly, int d, 
             for (int c = 0; c < d; ++c) dy[c] = yr[(w + 1) * d + c] - yr[w * d + c];
             REAL m = FN(dot)(dx, dy, d); /* <x_{s_u+1} - x_{s_u}, y_{t_w+1} - y_{t_w}> */
             REAL k10 = cur[w], k01 = prev[w + 1], k00 = prev[w];
-            REAL v = k10 + k01 - k00 + 0.5 * m * (k10 + k01);
-            if (order == 2) v += (1.0 / 12.0) * m * m * (k10 + k01 + k00);
+            REAL v;
+            if (order == 3) {
+                v = (k10 + k01 - k00 + 0.25 * m * (k00 + k10 + k01)) / (1.0 - 0.25 * m);
+            } else {
+                v = k10 + k01 - k00 + 0.5 * m * (k10 + k01);
+                if (order == 2) v += (1.0 / 12.0) * m * m * (k10 + k01 + k00);
+            }
             cur[w + 1] = v;
         }
         REAL* tmp = prev; prev = cur; cur = tmp;
@@ -281,7 +296,8 @@ static REAL FN(poly_interp)(const REAL* x0, int64_t Lx0, const REAL* y0, int64_t
     return end;
 }
 
-/* Dispatch on the scheme id: 0 FD1, 1 FD2, 2 polynomial approximation, 3 interpolation. */
+/* Dispatch on the scheme id: 0 FD1, 1 FD2, 2 polynomial approximation, 3 interpolation,
+ * 4 implicit FD. */
 static REAL FN(scheme)(int scheme, const REAL* x, int64_t Lx, const REAL* y, int64_t Ly, int d,
                        int N, int lam, const double* s, const double* t) {
     switch (scheme) {
@@ -289,6 +305,7 @@ static REAL FN(scheme)(int scheme, const REAL* x, int64_t Lx, const REAL* y, int
         case 1: return FN(fd)(x, Lx, y, Ly, d, 2, lam);
         case 2: return FN(poly_approx)(x, Lx, y, Ly, d, N, lam, s, t);
         case 3: return FN(poly_interp)(x, Lx, y, Ly, d, N, lam, s, t);
+        case 4: return FN(fd)(x, Lx, y, Ly, d, 3, lam);
         default: return 0.0 / 0.0;
     }
 }

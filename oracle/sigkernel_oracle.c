@@ -9,7 +9,8 @@
  *   sko_scheme        one pair, any scheme: FD1 / FD2 (Definition "dyadic scheme" and eq.
  *                     (secondexplicitscheme), Section 2), polynomial approximation (Definition
  *                     "def:polyapproxscheme", Section 3.2), polynomial interpolation (Definition
- *                     "def:polyinterpscheme", Section 3.3); all with dyadic refinement.
+ *                     "def:polyinterpscheme", Section 3.3), implicit FD (Remark "higherfd");
+ *                     all with dyadic refinement.
  *   sko_pairs         many pairs over ragged concatenated paths, split over POSIX threads.
  *   sko_grad_entry    d k / d x[p][c] (or y) by the complex step on the same scheme code.
  *   sko_sig_trunc     the level-n truncated signature kernel sum_k <S_k(x), S_k(y)> by brute
@@ -55,7 +56,7 @@ static double* uniform_grid_(int64_t L) {
 
 /* ----------------------------------------------------------------------------------------- */
 /* One pair.  x: [Lx][d], y: [Ly][d] row-major points; s, t: optional partitions (NULL =       */
-/* uniform on [0, 1]).  scheme: 0 FD1, 1 FD2, 2 approximation, 3 interpolation.                */
+/* uniform on [0, 1]).  scheme: 0 FD1, 1 FD2, 2 approximation, 3 interpolation, 4 implicit FD. */
 /* ----------------------------------------------------------------------------------------- */
 double sko_scheme(int scheme, const double* x, int64_t Lx, const double* y, int64_t Ly, int d,
                   int N, int lam, const double* s, const double* t) {

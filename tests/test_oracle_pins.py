@@ -12,7 +12,7 @@ import scipy.special as sps
 import oracle
 from paper_2502_08470_gb300 import workloads as W
 
-SCHEMES = ["fd1", "fd2", "approx", "interp"]
+SCHEMES = ["fd1", "fd2", "approx", "interp", "fd_implicit"]
 
 
 def _seg(v0, v1):
@@ -168,7 +168,62 @@ def test_fd_single_cell_closed_forms(m):
     assert oracle.kernel(x, y, "fd2") == pytest.approx(1.0 + m + m * m / 4.0, rel=1e-15)
 
 
-@pytest.mark.parametrize("scheme", ["fd1", "fd2"])
+@pytest.mark.parametrize("m", [0.3, -0.7, 1.9, -3.1])
+def test_fd_implicit_single_cell_closed_form(m):
+    """Remark "higherfd", four-corner trapezoid rule: from three unit corners the cell equation
+    k11 = 1 + (m/4)(3 + k11) has the solution (1 + 3m/4)/(1 - m/4) = 1 + m + m^2/4 + m^3/16 + ...,
+    which agrees with the exact sum m^n/(n!)^2 up to the m^3 term."""
+    x = _seg([0.0], [1.0])
+    y = _seg([0.0], [m])
+    assert oracle.kernel(x, y, "fd_implicit") == pytest.approx((1.0 + 0.75 * m) / (1.0 - 0.25 * m), rel=1e-15)
+
+
+@pytest.mark.parametrize("lam", [0, 1])
+def test_fd_implicit_solves_the_global_linear_system(lam):
+    """The marching update against one dense solve of every cell equation at once: unknowns
+    k(i, j) for i, j >= 1, boundary k(0, .) = k(., 0) = 1, and for each (refined) cell
+    k11 - k10 - k01 + k00 - (m/4)(k00 + k10 + k01 + k11) = 0 with m = <dx_i, dy_j>.  The paths
+    differ in length and direction, so a transposed or shifted increment index changes the
+    answer.  For lambda = 1 the refined grid is built here by inserting midpoints."""
+    X = W.brownian(1, 4, 3, seed=71)[0]
+    Y = W.brownian(1, 6, 3, seed=72)[0] * 1.7
+    x, y = X, Y
+    for _ in range(lam):
+        x = np.concatenate([np.stack([x[:-1], 0.5 * (x[:-1] + x[1:])], 1).reshape(-1, 3), x[-1:]])
+        y = np.concatenate([np.stack([y[:-1], 0.5 * (y[:-1] + y[1:])], 1).reshape(-1, 3), y[-1:]])
+    dx, dy = np.diff(x, axis=0), np.diff(y, axis=0)
+    nI, nJ = len(dx), len(dy)
+    idx = lambda i, j: (i - 1) * nJ + (j - 1)
+    A = np.zeros((nI * nJ, nI * nJ))
+    b = np.zeros(nI * nJ)
+    for i in range(nI):
+        for j in range(nJ):
+            m = dx[i] @ dy[j]
+            row = idx(i + 1, j + 1)
+            for (a, c), coef in (((i + 1, j + 1), 1 - m / 4), ((i + 1, j), -1 - m / 4),
+                                 ((i, j + 1), -1 - m / 4), ((i, j), 1 - m / 4)):
+                if a == 0 or c == 0:
+                    b[row] -= coef  # boundary value 1 moved to the right-hand side
+                else:
+                    A[row, idx(a, c)] += coef
+    k = np.linalg.solve(A, b)
+    assert oracle.kernel(X, Y, "fd_implicit", lam=lam) == pytest.approx(k[-1], rel=1e-12)
+
+
+def test_fd_implicit_beats_the_two_corner_rule():
+    """The four-corner quadrature has a smaller error constant than the first-order explicit
+    update at equal refinement (same 4^-lambda rate); with the Remark's printed factor 1/2 the
+    implicit scheme would not converge at all."""
+    X = W.linear(2, 9, 2, seed=7)
+    U = W.linear_directions(2, 2, seed=7)
+    want = _i0_series(U[0] @ U[1])
+    for lam in (2, 3, 4):
+        e1 = abs(oracle.kernel(X[0], X[1], "fd1", lam=lam) - want)
+        ei = abs(oracle.kernel(X[0], X[1], "fd_implicit", lam=lam) - want)
+        assert ei < e1 / 10
+
+
+@pytest.mark.parametrize("scheme", ["fd1", "fd2", "fd_implicit"])
 def test_fd_convergence_rate(scheme):
     X = W.linear(2, 9, 2, seed=7)
     U = W.linear_directions(2, 2, seed=7)
