@@ -14,6 +14,12 @@
  *                   "def:polyapproxscheme" and the explicit update after it, Section 3.2)
  *   SK_POLY_INTERP  polynomial interpolation scheme of order N (Definition
  *                   "def:polyinterpscheme", Section 3.3)
+ *   SK_FD_IMPLICIT  implicit finite differences (Remark "higherfd", Section 2): each sub-cell
+ *                   solves k11 = k10 + k01 - k00 + (m/4)(k00 + k10 + k01 + k11) for k11, the
+ *                   two-dimensional trapezoid rule on the four corners (the Remark prints the
+ *                   factor as 1/2; 1/4 is the trapezoid weight and the only one that converges).
+ *                   A sub-cell with m = <dx, dy> = 4 has no solution: the call then reports
+ *                   SK_ERR_NONFINITE
  *
  * Every scheme accepts a dyadic order lambda >= 0: each cell is split into 2^lambda x 2^lambda
  * sub-cells by linear interpolation of the paths (Definition "dyadic scheme"); for the polynomial
@@ -69,7 +75,7 @@ enum {
 };
 
 /* Schemes. */
-enum { SK_FD1 = 0, SK_FD2 = 1, SK_POLY_APPROX = 2, SK_POLY_INTERP = 3 };
+enum { SK_FD1 = 0, SK_FD2 = 1, SK_POLY_APPROX = 2, SK_POLY_INTERP = 3, SK_FD_IMPLICIT = 4 };
 
 /* Element type of the input rows. */
 enum { SK_F64 = 0, SK_F32 = 1, SK_BF16 = 2 };
@@ -106,7 +112,7 @@ enum {
 };
 
 typedef struct {
-    int32_t scheme;           /* SK_FD1, SK_FD2, SK_POLY_APPROX, SK_POLY_INTERP */
+    int32_t scheme;           /* SK_FD1, SK_FD2, SK_POLY_APPROX, SK_POLY_INTERP, SK_FD_IMPLICIT */
     int32_t degree;           /* N: 2 <= N <= 16 (approximation), 2 <= N <= 12 (interpolation);
                                  ignored by FD (Definitions of Sections 3.2 and 3.3 take N >= 2) */
     int32_t dyadic;           /* lambda: 0 <= lambda <= 8 */

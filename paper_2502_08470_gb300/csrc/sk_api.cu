@@ -171,7 +171,7 @@ int check_paths(const sk_paths* P, const char* name, int d) {
 int check_options(const sk_options* o, int32_t d, int32_t dtype) {
     if (!o) return fail(SK_ERR_INVALID_ARG, "options is NULL");
     if (o->reserved != 0) return fail(SK_ERR_INVALID_ARG, "options.reserved must be 0");
-    if (o->scheme < SK_FD1 || o->scheme > SK_POLY_INTERP) return fail(SK_ERR_INVALID_ARG, "unknown scheme %d", o->scheme);
+    if (o->scheme < SK_FD1 || o->scheme > SK_FD_IMPLICIT) return fail(SK_ERR_INVALID_ARG, "unknown scheme %d", o->scheme);
     if (o->compute != SK_COMPUTE_F64 && o->compute != SK_COMPUTE_F32)
         return fail(SK_ERR_INVALID_ARG, "unknown compute mode %d", o->compute);
     if (dtype != SK_F64 && dtype != SK_F32 && dtype != SK_BF16) return fail(SK_ERR_INVALID_ARG, "unknown dtype %d", dtype);
@@ -231,7 +231,7 @@ int plan_forward(const sk_paths* X, const sk_paths* Y, int32_t d, int32_t dtype,
     p.mtile = mt_eligible && !(o->flags & SK_FLAG_NO_TILED_M);
     auto kernel_for = [&](bool coop) -> const void* {
         return poly ? fwd_poly_kernel_ptr(p.T, o->scheme == SK_POLY_INTERP, o->degree, coop, p.mtile)
-                    : fwd_fd_kernel_ptr(p.T, o->scheme == SK_FD2 ? 2 : 1, lam, coop);
+                    : fwd_fd_kernel_ptr(p.T, o->scheme == SK_FD2 ? 2 : o->scheme == SK_FD_IMPLICIT ? 3 : 1, lam, coop);
     };
     p.kern = kernel_for(false);
     if (poly) {

@@ -10,6 +10,7 @@ namespace sk {
 const void* fwd_poly_kernel_ptr(int T, bool interp, int N, bool coop, bool mt);
 const void* fwd_fd_kernel_ptr(int T, int order, int lam, bool coop);
 const void* fwd_fd_coop_ptr(int T, int order, int lam);
+const void* fwd_fd_implicit_ptr(int T, int lam, bool coop);  // order 3
 const void* fwd_approx_ptr_f32(int N);
 const void* fwd_interp_ptr_f32(int N);
 const void* fwd_approx_coop_ptr_f32(int N);

@@ -64,6 +64,7 @@ const void* fwd_poly_kernel_ptr(int T, bool interp, int N, bool coop, bool mt) {
 
 const void* fwd_fd_kernel_ptr(int T, int order, int lam, bool coop) {
     if (lam < 0 || lam > kLamMax) return nullptr;
+    if (order == 3) return fwd_fd_implicit_ptr(T, lam, coop);
     if (coop) return fwd_fd_coop_ptr(T, order, lam);
     if (T == 1) return order == 2 ? fd_rows<float, 2>(lam) : fd_rows<float, 1>(lam);
     return order == 2 ? fd_rows<double, 2>(lam) : fd_rows<double, 1>(lam);

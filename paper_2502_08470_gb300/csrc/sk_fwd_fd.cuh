@@ -1,11 +1,15 @@
 // Forward wavefront of the finite-difference schemes on the dyadic grid P_lambda (Definition
-// "dyadic scheme", Section 2; second-order explicit update eq. (secondexplicitscheme)) for sm_103a.
+// "dyadic scheme", Section 2; second-order explicit update eq. (secondexplicitscheme); implicit
+// update of Remark "higherfd") for sm_103a.
 //
 // On a sub-cell of P_lambda with m = <dx_I, dy_J> = M_ij / 4^lambda (the refined increments are
-// the coarse ones divided by 2^lambda), both explicit updates read
+// the coarse ones divided by 2^lambda), all three updates read
 //     k(I+1, J+1) = (k(I+1, J) + k(I, J+1)) alpha - k(I, J) beta
-// with alpha = 1 + m/2, beta = 1 (first order) or alpha = 1 + m/2 + m^2/12, beta = 1 - m^2/12
-// (second order).  All 4^lambda sub-cells of a cell share (alpha, beta).
+// with alpha = 1 + m/2, beta = 1 (ORDER 1, first order); alpha = 1 + m/2 + m^2/12,
+// beta = 1 - m^2/12 (ORDER 2, second order); alpha = (1 + m/4) / (1 - m/4), beta = 1 (ORDER 3,
+// implicit: the four-corner trapezoid equation k11 = k10 + k01 - k00 + (m/4)(k00 + k10 + k01 +
+// k11) solved for k11, which leaves the k00 terms cancelling to beta = 1).  All 4^lambda sub-cells
+// of a cell share (alpha, beta).
 //
 // Difference form.  Writing v(I+1, J) = k(I+1, J) - k(I, J), the same update is
 //     v(I+1, J+1) = v(I+1, J) + (alpha - 1)(k(I+1, J) + k(I, J+1)) - (beta - 1) k(I, J),
@@ -117,8 +121,9 @@ __device__ __forceinline__ void sweep_fd(const Launch& L, int64_t item, const Pa
             }
             const T m = row_dot<T>(xbase + static_cast<int64_t>((g * R) >> lam) * dpad,
                                    ybase + static_cast<int64_t>(jj >> lam) * dpad, L.nvec) * sub;
-            const T a1 = m * T(0.5);                     // alpha - 1
-            T m2 = T(0);                                 // (1 - beta) = alpha - 1 - m/2
+            T a1 = m * T(0.5);                           // alpha - 1
+            if constexpr (ORDER == 3) a1 = a1 / (T(1) - m * T(0.25));
+            T m2 = T(0);                                 // (1 - beta) = alpha - 1 - m/2 (ORDER 2)
             if constexpr (ORDER == 2) m2 = m * m * T(1.0 / 12.0);
             T k00 = kb_prev, k01 = kb;                   // k(I, J), k(I, J+1) for I = gR + r
 #pragma unroll

@@ -22,7 +22,7 @@ LIB_PATH = os.path.join(_HERE, "_lib", "libsigkernel.so")
 SK_OK = 0
 ERRORS = {-1: "SK_ERR_INVALID_ARG", -2: "SK_ERR_UNSUPPORTED", -3: "SK_ERR_CUDA", -4: "SK_ERR_WORKSPACE",
           -5: "SK_ERR_DEVICE_TIMEOUT", -6: "SK_ERR_NONFINITE", -7: "SK_ERR_BAD_LENGTH"}
-SCHEMES = {"fd1": 0, "fd2": 1, "approx": 2, "interp": 3}
+SCHEMES = {"fd1": 0, "fd2": 1, "approx": 2, "interp": 3, "fd_implicit": 4}
 COMPUTE = {"f64": 0, "f32": 1}
 DTYPES = {torch.float64: 0, torch.float32: 1, torch.bfloat16: 2}
 FLAG_SYMMETRIC, FLAG_INCREMENTS, FLAG_UNBIASED, FLAG_NO_SORT, FLAG_TIME_KERNEL = 1, 2, 4, 8, 16

@@ -69,6 +69,10 @@ def test_version_and_host_side_validation(lib):
     assert lib.sigkernel_workspace_size(1, ctypes.byref(X), ctypes.byref(X), 2, ctypes.c_int64(-1),
                                         ctypes.byref(bad), ctypes.byref(n)) == -1
     assert b"unknown flag" in lib.sigkernel_last_error()
+    bad = sk._options(max(sk.SCHEMES.values()) + 1, 6)
+    assert lib.sigkernel_workspace_size(1, ctypes.byref(X), ctypes.byref(X), 2, ctypes.c_int64(-1),
+                                        ctypes.byref(bad), ctypes.byref(n)) == -1
+    assert b"unknown scheme" in lib.sigkernel_last_error()
     # a call with invalid options returns before touching any device
     lib.sigkernel_gram.restype = ctypes.c_int
     bad = sk._options("interp", 20)

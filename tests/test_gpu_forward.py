@@ -64,7 +64,7 @@ def test_interp_f64_gram_matches_oracle(N):
     assert np.max(_rel(G, R)) < 1e-10
 
 
-@pytest.mark.parametrize("scheme", ["fd1", "fd2"])
+@pytest.mark.parametrize("scheme", ["fd1", "fd2", "fd_implicit"])
 @pytest.mark.parametrize("lam", [0, 1, 2, 3, 5])
 def test_fd_f64_gram_matches_oracle(scheme, lam):
     L = 20 if lam < 5 else 6
@@ -79,7 +79,8 @@ def test_fd_f64_gram_matches_oracle(scheme, lam):
 # FP32 cell updates with per-lane exponents
 # ------------------------------------------------------------------------------------------
 @pytest.mark.parametrize("scheme,N,lam", [("approx", 6, 0), ("approx", 4, 2), ("interp", 6, 0),
-                                          ("fd1", 0, 2), ("fd2", 0, 1)])
+                                          ("fd1", 0, 2), ("fd2", 0, 1), ("fd_implicit", 0, 0),
+                                          ("fd_implicit", 0, 3)])
 def test_f32_gram_mape(scheme, N, lam):
     X = W.brownian(6, 75, 4, seed=37)
     Y = W.brownian(5, 66, 4, seed=38)
@@ -124,7 +125,7 @@ def test_ragged_pairs_match_oracle(compute):
     pb = rng.integers(0, len(Ys), size=40)
     PX = sk.Paths.from_list([torch.tensor(x) for x in Xs])
     PY = sk.Paths.from_list([torch.tensor(y) for y in Ys])
-    for scheme, N in (("approx", 5), ("interp", 4), ("fd2", 0)):
+    for scheme, N in (("approx", 5), ("interp", 4), ("fd2", 0), ("fd_implicit", 0)):
         out = sk.sigkernel_pairs(PX, PY, pa, pb, scheme=scheme, degree=max(N, 2), compute=compute)
         torch.cuda.synchronize()
         assert sk.device_status() == 0
@@ -198,6 +199,22 @@ def test_single_pair_workload_approx4_and_fd2():
                                  dyadic=lam, compute="f64").cpu().numpy()
         ref = oracle.kernel(X[0], X[1], scheme, max(N, 2), lam)
         assert abs(got[0] - ref) <= 1e-12 * abs(ref)
+
+
+@pytest.mark.parametrize("compute", ["f64", "f32"])
+def test_fd_implicit_singular_cell_reports_nonfinite(compute):
+    """Remark "higherfd" read with the trapezoid weight 1/4: a cell with m = <dx, dy> = 4 makes
+    the implicit cell equation singular (1 - m/4 = 0); the call records SK_ERR_NONFINITE and the
+    other pairs of the batch are unaffected."""
+    x = np.array([[[0.0, 0.0], [2.0, 0.0]]])
+    y = np.array([[[0.0, 0.0], [2.0, 1.0]], [[0.0, 0.0], [0.5, 0.3]]])
+    out = sk.sigkernel_pairs(_cuda(x), _cuda(y), [0, 0], [0, 1], scheme="fd_implicit", compute=compute)
+    torch.cuda.synchronize()
+    assert sk.device_status() == -6
+    got = out.cpu().numpy()
+    assert not np.isfinite(got[0])
+    m = 2.0 * 0.5
+    assert got[1] == pytest.approx((1 + 0.75 * m) / (1 - 0.25 * m), rel=1e-6)
 
 
 # ------------------------------------------------------------------------------------------

@@ -44,6 +44,8 @@ CASES = [
     ("interp", 5, 0, "f64", 1e-11),
     ("fd1", 0, 2, "f32", 1e-4),
     ("fd2", 0, 3, "f64", 1e-11),
+    ("fd_implicit", 0, 2, "f32", 1e-4),
+    ("fd_implicit", 0, 1, "f64", 1e-11),
 ]
 
 
