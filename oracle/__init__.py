@@ -11,6 +11,9 @@ Schemes (ids follow the C library's enum for convenience of the tests only):
   2 "approx"  polynomial approximation scheme of order N            (Def. polyapproxscheme)
   3 "interp"  polynomial interpolation scheme of order N            (Def. polyinterpscheme)
   4 "fd_implicit"  implicit finite differences, four-corner trapezoid rule (Remark higherfd)
+
+Beyond the schemes: MMD^2 and its gradient (C), and the two-sample permutation test on MMD^2
+(``mmd2_permutation_test``, numpy over the oracle's Gram).
 """
 from __future__ import annotations
 
@@ -169,3 +172,40 @@ def mmd2_grad_entry(A, B, side, path, p, c, scheme="approx", N=6, lam=0, unbiase
     na, L, d = A.shape
     return _load().sko_mmd2_grad_entry(_sid(scheme), _ptr(A), na, _ptr(B), B.shape[0], L, d, N, lam,
                                        int(unbiased), side, path, p, c)
+
+
+def mmd2_permutation_test(A, B, labels, scheme="approx", N=6, lam=0, unbiased=False):
+    """Two-sample permutation test on MMD^2 (the paper names statistical hypothesis testing as a
+    use of the kernel, Sections 1 and 4, without defining it; this is the standard test).
+
+    The pooled sample Z = (A_0..A_{na-1}, B_0..B_{nb-1}) has Gram matrix K = gram(Z, Z).  A
+    relabelling marks na paths of Z as the first sample; its statistic is MMD^2 of the two marked
+    subsets, from the means of the blocks of K: biased  mean K_11 + mean K_00 - 2 mean K_10;
+    unbiased  the same with the diagonals of K_11 and K_00 left out of their sums and means over
+    na (na - 1) and nb (nb - 1).  The observed statistic is that of the given split (the first
+    na paths of Z).  p-value = (1 + #{p : stat_p >= observed}) / (1 + nperm).
+
+    labels: [nperm, na + nb], nonzero = first sample; every row must mark exactly na paths.
+    Returns (observed, p_value, stats[nperm])."""
+    A, B = list(A), list(B)
+    na, nb = len(A), len(B)
+    n = na + nb
+    K = gram(A + B, A + B, scheme, N, lam)
+    labels = np.asarray(labels)
+    assert labels.ndim == 2 and labels.shape[1] == n
+
+    def stat(first):
+        a, b = np.flatnonzero(first), np.flatnonzero(~first)
+        assert len(a) == na
+        Kaa, Kbb, Kab = K[np.ix_(a, a)], K[np.ix_(b, b)], K[np.ix_(a, b)]
+        if unbiased:
+            saa = (Kaa.sum() - np.trace(Kaa)) / (na * (na - 1))
+            sbb = (Kbb.sum() - np.trace(Kbb)) / (nb * (nb - 1))
+        else:
+            saa, sbb = Kaa.mean(), Kbb.mean()
+        return saa + sbb - 2.0 * Kab.mean()
+
+    observed = stat(np.arange(n) < na)
+    stats = np.array([stat(row != 0) for row in labels])
+    p_value = (1 + np.count_nonzero(stats >= observed)) / (1 + len(stats))
+    return observed, p_value, stats

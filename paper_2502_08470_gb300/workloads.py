@@ -15,6 +15,8 @@ Workloads
   * ``sinpath``      x_i = sin(U_i), U_i ~ N(0, I_2) i.i.d. (eq. (sinpath), Appendix B); ``cospath``
                      the matching y_i = cos(V_i).
   * ``uneven``       ragged batch: lengths floor(exp(U(ln Lmin, ln Lmax))), increments N(0, 1/L).
+  * ``split_labels`` random relabellings of a pooled sample of na + nb paths (uniform random
+                     permutations of the labels 1 x na, 0 x nb), the draws of a permutation test.
 """
 from __future__ import annotations
 
@@ -104,3 +106,14 @@ def round_bf16(a: np.ndarray) -> np.ndarray:
 def round_f32(a: np.ndarray) -> np.ndarray:
     """Round float64 values to float32 and return float64 (same purpose as ``round_bf16``)."""
     return np.asarray(a, dtype=np.float32).astype(np.float64)
+
+
+def split_labels(nperm: int, na: int, nb: int, seed: int) -> np.ndarray:
+    """[nperm, na + nb] uint8: row p marks with 1 the na pooled paths that relabelling p assigns to
+    the first sample (a uniformly random permutation of na ones and nb zeros)."""
+    rng = np.random.default_rng(seed)
+    base = np.concatenate([np.ones(na, dtype=np.uint8), np.zeros(nb, dtype=np.uint8)])
+    out = np.empty((nperm, na + nb), dtype=np.uint8)
+    for p in range(nperm):
+        out[p] = base[rng.permutation(na + nb)]
+    return out

@@ -384,3 +384,57 @@ def test_pairs_threads_agree_with_single_calls():
     out = oracle.pairs(X, Y, pa, pb, "approx", 6, threads=3)
     for k in range(4):
         assert out[k] == oracle.kernel(X[pa[k]], Y[pb[k]], "approx", 6)
+
+
+# --------------------------------------------------------------------------------------------
+# Two-sample permutation test on MMD^2 (Sections 1 and 4 name hypothesis testing; the standard
+# permutation test): statistics against the separately pinned MMD^2 code on relabelled sets
+# --------------------------------------------------------------------------------------------
+@pytest.mark.parametrize("unbiased", [False, True])
+def test_permutation_statistics_are_mmd2_of_the_relabelled_sets(unbiased):
+    A = W.brownian(5, 6, 2, seed=61)
+    B = W.brownian(4, 6, 2, seed=62, drift=0.4)
+    Z = np.concatenate([A, B])
+    labels = W.split_labels(6, 5, 4, seed=63)
+    obs, p, stats = oracle.mmd2_permutation_test(A, B, labels, "approx", 5, unbiased=unbiased)
+    assert obs == pytest.approx(oracle.mmd2(A, B, "approx", 5, unbiased=unbiased), rel=1e-12)
+    for row, s in zip(labels, stats):
+        first = row != 0
+        want = oracle.mmd2(Z[first], Z[~first], "approx", 5, unbiased=unbiased)
+        assert s == pytest.approx(want, rel=1e-11, abs=1e-13)
+    assert p == (1 + np.count_nonzero(stats >= obs)) / 7
+
+
+def test_permutation_test_invariances_and_extremes():
+    A = W.brownian(6, 5, 2, seed=64)
+    B = W.brownian(6, 5, 2, seed=65, drift=3.0)
+    n = 12
+    ident = (np.arange(n) < 6).astype(np.uint8)
+    swapped = 1 - ident  # the two samples exchanged: the biased MMD^2 is symmetric in them
+    within = ident.copy()
+    labels = np.stack([ident, swapped, within] + list(W.split_labels(20, 6, 6, seed=66)))
+    obs, p, stats = oracle.mmd2_permutation_test(A, B, labels, "approx", 4)
+    assert stats[0] == obs and stats[2] == obs
+    assert stats[1] == pytest.approx(obs, rel=1e-12)
+    # a drift of 3 separates the samples: every proper relabelling scores below the split itself
+    proper = [k for k in range(3, len(labels)) if not (np.array_equal(labels[k], ident)
+                                                       or np.array_equal(labels[k], swapped))]
+    assert np.all(stats[proper] < obs)
+    ties = np.count_nonzero(stats >= obs)
+    assert ties >= 2 and p == (1 + ties) / (1 + len(labels))
+
+
+def test_permutation_p_values_are_valid_under_the_null():
+    """Under H0 (both samples from one law) the permutation p-value is uniform on {1/40, ..., 1}
+    (39 relabellings): P(p <= a) <= a and E p = 0.5125.  100 independent tests at a = 0.1 expect
+    10 rejections (17 or more has probability about 0.02)."""
+    ps = []
+    for t in range(100):
+        A = W.brownian(6, 5, 2, seed=1000 + 2 * t)
+        B = W.brownian(6, 5, 2, seed=1001 + 2 * t)
+        _, p, _ = oracle.mmd2_permutation_test(A, B, W.split_labels(39, 6, 6, seed=3000 + t), "approx", 4)
+        assert 1 / 40 <= p <= 1
+        ps.append(p)
+    ps = np.array(ps)
+    assert np.count_nonzero(ps <= 0.1) <= 16
+    assert 0.42 < ps.mean() < 0.6
