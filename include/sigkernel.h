@@ -71,7 +71,9 @@ enum {
     SK_ERR_WORKSPACE = -4,     /* workspace smaller than sigkernel_workspace_size() */
     SK_ERR_DEVICE_TIMEOUT = -5,/* a bounded device-side wait ran out (device error word) */
     SK_ERR_NONFINITE = -6,     /* a result was NaN or infinite (device error word) */
-    SK_ERR_BAD_LENGTH = -7     /* a path had no rows or more than max_len rows (device word) */
+    SK_ERR_BAD_LENGTH = -7,    /* a path had no rows or more than max_len rows (device word) */
+    SK_ERR_BAD_LABELS = -8     /* a relabelling of sigkernel_mmd2_test did not mark exactly
+                                  A->count paths (device word) */
 };
 
 /* Schemes. */
@@ -136,15 +138,16 @@ typedef struct {
 } sk_paths;
 
 /* Which call a workspace is sized for. */
-enum { SK_OP_PAIRS = 0, SK_OP_GRAM = 1, SK_OP_BACKWARD = 2, SK_OP_MMD2 = 3, SK_OP_BACKWARD_TAPE = 4 };
+enum { SK_OP_PAIRS = 0, SK_OP_GRAM = 1, SK_OP_BACKWARD = 2, SK_OP_MMD2 = 3, SK_OP_BACKWARD_TAPE = 4,
+       SK_OP_MMD2_TEST = 5 };
 
 /*
  * sigkernel_workspace_size -- writes to *bytes the device workspace the call `op` needs for
  * these shapes and options and returns SK_OK, or returns the SK_ERR_* code the call itself would
  * return for these arguments (then *bytes = 0).  `npairs` is the pair count for SK_OP_PAIRS /
  * SK_OP_BACKWARD / SK_OP_BACKWARD_TAPE with a pair list (pass -1 for a Gram); for SK_OP_MMD2 it
- * is 0 for the value alone and nonzero for the value with gradients (X = A, Y = B); ignored
- * otherwise.  Queries properties of the current device (SM count, occupancy); no memory traffic.
+ * is 0 for the value alone and nonzero for the value with gradients (X = A, Y = B); for
+ * SK_OP_MMD2_TEST it is the number of relabellings (X = A, Y = B); ignored otherwise.  Queries properties of the current device (SM count, occupancy); no memory traffic.
  */
 int sigkernel_workspace_size(int32_t op, const sk_paths* X, const sk_paths* Y, int32_t d,
                              int64_t npairs, const sk_options* opt, size_t* bytes);
@@ -268,6 +271,27 @@ void sigkernel_autotune_clear(void);
 int sigkernel_mmd2(const sk_paths* A, const sk_paths* B, int32_t d, int32_t dtype,
                    const sk_options* opt, double* out, double* grad_A, double* grad_B,
                    void* workspace, size_t workspace_bytes, void* stream);
+
+/*
+ * sigkernel_mmd2_test -- two-sample permutation test on MMD^2 (the paper names statistical
+ * hypothesis testing among the library's uses, Sections 1 and 4, without defining it; this is the
+ * standard permutation test).  The pooled sample Z = (A_0..A_{na-1}, B_0..B_{nb-1}) is solved once
+ * as one symmetric Gram K (blocks K_AA, K_BB symmetric and K_AB full, as in sigkernel_mmd2, then
+ * K_BA = K_AB^T); each relabelling's statistic is then the MMD^2 (biased, or with SK_FLAG_UNBIASED
+ * the U-statistic) of the two subsets it marks, read from K in FP64 on the device.
+ *   labels   device uint8 [nperm][na + nb]: row p marks with a nonzero byte the pooled paths that
+ *            relabelling p assigns to the first sample.  A row that does not mark exactly na paths
+ *            gets a NaN statistic and sets SK_ERR_BAD_LABELS in the device error word.  The caller
+ *            draws the relabellings (uniformly random permutations of the split, usually).
+ *   nperm    0 <= nperm <= 2^24; na + nb <= 65536; na, nb >= 1 (>= 2 for the U-statistic)
+ *   out      device double [2 + nperm]: out[0] = MMD^2 of the given split (A, B); out[1] = p-value
+ *            (1 + #{p : out[2 + p] >= out[0]}) / (1 + nperm); out[2 + p] = MMD^2 under relabelling p.
+ * Workspace: SK_OP_MMD2_TEST with npairs = nperm; it holds K ((na + nb)^2 doubles).  A statistic
+ * depends only on K and its own relabelling (bitwise, for a given na + nb).
+ */
+int sigkernel_mmd2_test(const sk_paths* A, const sk_paths* B, int32_t d, int32_t dtype,
+                        const sk_options* opt, const uint8_t* labels, int64_t nperm, double* out,
+                        void* workspace, size_t workspace_bytes, void* stream);
 
 /*
  * sigkernel_pairs_noalloc -- sigkernel_pairs for callers that cannot allocate device memory

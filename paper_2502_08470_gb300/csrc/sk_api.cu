@@ -1080,6 +1080,64 @@ int run_mmd2(const sk_paths* A, const sk_paths* Bp, int32_t d, int32_t dtype, co
     return SK_OK;
 }
 
+// Permutation test on MMD^2: the pooled Gram K of Z = (A, B) from the three blocks of
+// sigkernel_mmd2 written in place (K_AA and K_BB symmetric, K_AB full; K_BA mirrored by the test's
+// own kernel), then the statistics of every relabelling (launch_mmd_perm).
+constexpr int64_t kMaxPooled = 65536;
+constexpr int64_t kMaxPerm = int64_t(1) << 24;
+
+struct MmdTestPlan {
+    MmdPlan m;
+    size_t k_bytes, scratch, total;
+};
+
+int plan_mmd2_test(const sk_paths* A, const sk_paths* Bp, int32_t d, int32_t dtype, const sk_options* o, int64_t nperm,
+                   MmdTestPlan& t) {
+    if (nperm < 0 || nperm > kMaxPerm) return fail(SK_ERR_INVALID_ARG, "nperm %lld outside [0, 2^24]", (long long)nperm);
+    int rc = plan_mmd2(A, Bp, d, dtype, o, false, t.m);
+    if (rc != SK_OK) return rc;
+    const int64_t n = A->count + Bp->count;
+    if (n > kMaxPooled) return fail(SK_ERR_UNSUPPORTED, "%lld pooled paths (this build: <= %lld)", (long long)n,
+                                    (long long)kMaxPooled);
+    t.k_bytes = align256(static_cast<size_t>(n) * n * sizeof(double));
+    t.scratch = mmd_perm_scratch_bytes(n, nperm);
+    t.total = t.k_bytes + t.scratch + t.m.sub + 512;
+    return SK_OK;
+}
+
+int run_mmd2_test(const sk_paths* A, const sk_paths* Bp, int32_t d, int32_t dtype, const sk_options* o,
+                  const uint8_t* labels, int64_t nperm, double* out, void* ws, size_t ws_bytes, void* stream) {
+    if (!out) return fail(SK_ERR_INVALID_ARG, "out is NULL");
+    if (nperm > 0 && !labels) return fail(SK_ERR_INVALID_ARG, "labels is NULL");
+    MmdTestPlan t;
+    int rc = plan_mmd2_test(A, Bp, d, dtype, o, nperm, t);
+    if (rc != SK_OK) return rc;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    bool own = false;
+    if (!ws) {
+        SK_CUDA(cudaMallocAsync(&ws, t.total, st));
+        own = true;
+    } else if (ws_bytes < t.total) {
+        return fail(SK_ERR_WORKSPACE, "workspace %zu bytes < %zu required", ws_bytes, t.total);
+    }
+    const int64_t na = A->count, n = A->count + Bp->count;
+    char* base = reinterpret_cast<char*>((reinterpret_cast<uintptr_t>(ws) + 255) / 256 * 256);
+    double* K = reinterpret_cast<double*>(base);
+    char* scratch = base + t.k_bytes;
+    char* sub_ws = scratch + t.scratch;
+    const sk_paths* xs[3] = {A, Bp, A};
+    const sk_paths* ys[3] = {A, Bp, Bp};
+    const int modes[3] = {kGramUpper, kGramUpper, kGramFull};
+    double* Ks[3] = {K, K + na * n + na, K + na};
+    for (int k = 0; k < 3; ++k)
+        if ((rc = run_forward(xs[k], ys[k], d, dtype, k < 2 ? &t.m.os : &t.m.of, modes[k], nullptr, nullptr, t.m.items[k],
+                              Ks[k], n, sub_ws, t.m.sub, st)) != SK_OK)
+            return rc;
+    SK_CUDA(launch_mmd_perm(K, n, na, labels, nperm, (o->flags & SK_FLAG_UNBIASED) ? 1 : 0, scratch, out, st));
+    if (own) SK_CUDA(cudaFreeAsync(ws, st));
+    return SK_OK;
+}
+
 }  // namespace
 }  // namespace sk
 
@@ -1235,6 +1293,12 @@ int sigkernel_workspace_size(int32_t op, const sk_paths* X, const sk_paths* Y, i
             if (rc == SK_OK) *bytes = m.total;
             return rc;
         }
+        case SK_OP_MMD2_TEST: {
+            MmdTestPlan t;
+            rc = plan_mmd2_test(X, Y, d, dtype, opt, npairs, t);
+            if (rc == SK_OK) *bytes = t.total;
+            return rc;
+        }
         default:
             return fail(SK_ERR_UNSUPPORTED, "workspace for op %d", op);
     }
@@ -1320,6 +1384,13 @@ int sigkernel_mmd2(const sk_paths* A, const sk_paths* B, int32_t d, int32_t dtyp
                    double* grad_A, double* grad_B, void* workspace, size_t workspace_bytes, void* stream) {
     t_last_error.clear();
     return run_mmd2(A, B, d, dtype, opt, out, grad_A, grad_B, workspace, workspace_bytes, stream);
+}
+
+int sigkernel_mmd2_test(const sk_paths* A, const sk_paths* B, int32_t d, int32_t dtype, const sk_options* opt,
+                        const uint8_t* labels, int64_t nperm, double* out, void* workspace, size_t workspace_bytes,
+                        void* stream) {
+    t_last_error.clear();
+    return run_mmd2_test(A, B, d, dtype, opt, labels, nperm, out, workspace, workspace_bytes, stream);
 }
 
 int sigkernel_device_status(void* stream) {

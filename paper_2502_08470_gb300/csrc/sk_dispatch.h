@@ -2,6 +2,11 @@
 // they compile in parallel).
 #pragma once
 
+#include <cstddef>
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
 namespace sk {
 
 // T: 0 = FP64 cell updates, 1 = FP32; coop: the cooperative-block (strip pipeline) variant,
@@ -76,4 +81,13 @@ const void* bwd_tape_interp_ptr_f64_0(int N);
 const void* bwd_tape_interp_ptr_f64_1(int N);
 const void* bwd_contract_ptr_f32();
 const void* bwd_contract_ptr_f64();
+}  // namespace sk
+
+namespace sk {
+// Two-sample permutation test on MMD^2 from the pooled Gram K [n][n] (the K_AB block filled, the
+// K_BA block written here): scratch of mmd_perm_scratch_bytes(n, nperm) bytes (256-byte aligned),
+// out [2 + nperm] as in sigkernel_mmd2_test.  Stream-ordered; returns the launch status.
+size_t mmd_perm_scratch_bytes(int64_t n, int64_t nperm);
+cudaError_t launch_mmd_perm(double* K, int64_t n, int64_t na, const uint8_t* labels, int64_t nperm, int unbiased,
+                            void* scratch, double* out, cudaStream_t st);
 }  // namespace sk

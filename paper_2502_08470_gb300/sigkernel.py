@@ -21,7 +21,7 @@ LIB_PATH = os.path.join(_HERE, "_lib", "libsigkernel.so")
 
 SK_OK = 0
 ERRORS = {-1: "SK_ERR_INVALID_ARG", -2: "SK_ERR_UNSUPPORTED", -3: "SK_ERR_CUDA", -4: "SK_ERR_WORKSPACE",
-          -5: "SK_ERR_DEVICE_TIMEOUT", -6: "SK_ERR_NONFINITE", -7: "SK_ERR_BAD_LENGTH"}
+          -5: "SK_ERR_DEVICE_TIMEOUT", -6: "SK_ERR_NONFINITE", -7: "SK_ERR_BAD_LENGTH", -8: "SK_ERR_BAD_LABELS"}
 SCHEMES = {"fd1": 0, "fd2": 1, "approx": 2, "interp": 3, "fd_implicit": 4}
 COMPUTE = {"f64": 0, "f32": 1}
 DTYPES = {torch.float64: 0, torch.float32: 1, torch.bfloat16: 2}
@@ -35,7 +35,7 @@ def _pipe_flags(strip_pipeline) -> int:
     if strip_pipeline is None:
         return 0
     return FLAG_STRIP_PIPELINE if strip_pipeline else FLAG_NO_STRIP_PIPELINE
-OP_PAIRS, OP_GRAM, OP_BACKWARD, OP_MMD2, OP_BACKWARD_TAPE = 0, 1, 2, 3, 4
+OP_PAIRS, OP_GRAM, OP_BACKWARD, OP_MMD2, OP_BACKWARD_TAPE, OP_MMD2_TEST = 0, 1, 2, 3, 4, 5
 
 
 class SigKernelError(RuntimeError):
@@ -82,6 +82,8 @@ def load_library():
         lib.sigkernel_backward.argtypes = [PP, PP, I32, I32, P, P, I64, PO, P, P, P, P, SZ, P]
         lib.sigkernel_mmd2.restype = ctypes.c_int
         lib.sigkernel_mmd2.argtypes = [PP, PP, I32, I32, PO, P, P, P, P, SZ, P]
+        lib.sigkernel_mmd2_test.restype = ctypes.c_int
+        lib.sigkernel_mmd2_test.argtypes = [PP, PP, I32, I32, PO, P, I64, P, P, SZ, P]
         lib.sigkernel_tape_size.restype = ctypes.c_int
         lib.sigkernel_tape_size.argtypes = [PP, PP, I32, I64, PO, ctypes.POINTER(SZ)]
         lib.sigkernel_forward_tape.restype = ctypes.c_int
@@ -378,6 +380,50 @@ def sigkernel_mmd2(A, B, scheme="approx", degree=6, dyadic=0, compute="f64", unb
     if grads:
         return out[0], out[1:], gA, gB
     return out[0], out[1:]
+
+
+def split_labels(nperm: int, na: int, nb: int, seed: int = 0) -> torch.Tensor:
+    """[nperm, na + nb] uint8 CUDA tensor: row p marks with 1 the na pooled paths that a uniformly
+    random relabelling assigns to the first sample (drawn on the host from a seeded generator)."""
+    g = torch.Generator().manual_seed(int(seed))
+    order = torch.argsort(torch.rand(int(nperm), na + nb, generator=g), dim=1)
+    return (order < na).to(torch.uint8).to("cuda")
+
+
+def sigkernel_mmd2_test(A, B, permutations=1000, labels=None, seed=0, scheme="approx", degree=6, dyadic=0,
+                        compute="f64", unbiased=False, workspace=None, out=None):
+    """Two-sample permutation test on MMD^2 between path sets A and B.
+
+    ``labels`` ([nperm, |A| + |B|] uint8 CUDA tensor, nonzero = first sample) gives the
+    relabellings of the pooled sample (A then B); without it ``permutations`` uniformly random
+    ones are drawn from ``seed``.  Returns (MMD^2 of the split, p-value, MMD^2 of every
+    relabelling) as float64 CUDA tensors; the p-value is (1 + #{stat >= observed}) / (1 + nperm).
+    ``workspace`` / ``out`` may be preallocated (``mmd2_test_workspace``; out of 2 + nperm)."""
+    A, B = as_paths(A), as_paths(B)
+    if labels is None:
+        labels = split_labels(permutations, A.count, B.count, seed)
+    if labels.dtype != torch.uint8 or not labels.is_cuda or labels.dim() != 2:
+        raise ValueError("labels must be a 2-d uint8 CUDA tensor")
+    if labels.shape[1] != A.count + B.count:
+        raise ValueError("labels must have |A| + |B| columns")
+    labels = labels.contiguous()
+    nperm = labels.shape[0]
+    cA, cB = _cpaths(A), _cpaths(B)
+    opt = _options(scheme, degree, dyadic, compute, _flags(A, FLAG_UNBIASED if unbiased else 0))
+    ws = workspace if workspace is not None else _workspace(OP_MMD2_TEST, cA, cB, A.d, nperm, opt)
+    if out is None:
+        out = torch.empty(2 + nperm, dtype=torch.float64, device="cuda")
+    _check(load_library().sigkernel_mmd2_test(ctypes.byref(cA), ctypes.byref(cB), A.d, _dtype_code(A, B),
+                                              ctypes.byref(opt), labels.data_ptr() if nperm else None, nperm,
+                                              out.data_ptr(), ws.data_ptr(), ws.numel(), _stream_ptr()))
+    return out[0], out[1], out[2:]
+
+
+def mmd2_test_workspace(A, B, nperm, scheme="approx", degree=6, dyadic=0, compute="f64", unbiased=False):
+    """Device workspace of ``sigkernel_mmd2_test`` for these sets and relabelling count."""
+    A, B = as_paths(A), as_paths(B)
+    opt = _options(scheme, degree, dyadic, compute, _flags(A, FLAG_UNBIASED if unbiased else 0))
+    return _workspace(OP_MMD2_TEST, _cpaths(A), _cpaths(B), A.d, int(nperm), opt)
 
 
 # ----------------------------------------------------------------------------------------------

@@ -25,7 +25,7 @@ def declared_functions():
 
 def test_header_declares_the_entry_points():
     names = declared_functions()
-    for required in ("sigkernel_pairs", "sigkernel_gram", "sigkernel_backward", "sigkernel_mmd2",
+    for required in ("sigkernel_pairs", "sigkernel_gram", "sigkernel_backward", "sigkernel_mmd2", "sigkernel_mmd2_test",
                      "sigkernel_workspace_size", "sigkernel_device_status", "sigkernel_last_error"):
         assert required in names
 
@@ -73,6 +73,10 @@ def test_version_and_host_side_validation(lib):
     assert lib.sigkernel_workspace_size(1, ctypes.byref(X), ctypes.byref(X), 2, ctypes.c_int64(-1),
                                         ctypes.byref(bad), ctypes.byref(n)) == -1
     assert b"unknown scheme" in lib.sigkernel_last_error()
+    ok = sk._options("approx", 6)
+    assert lib.sigkernel_workspace_size(sk.OP_MMD2_TEST, ctypes.byref(X), ctypes.byref(X), 2, ctypes.c_int64(-1),
+                                        ctypes.byref(ok), ctypes.byref(n)) == -1
+    assert b"nperm" in lib.sigkernel_last_error()
     # a call with invalid options returns before touching any device
     lib.sigkernel_gram.restype = ctypes.c_int
     bad = sk._options("interp", 20)
