@@ -535,13 +535,20 @@ def main():
         cells_m = (256 * 257 // 2 * 2 + 256 * 256) * 512 * 512
         t_f = timed_steps(lambda: sk.sigkernel_mmd2(Am, Bm, degree=6, compute="f32"), 2, 1)
         t_fb = timed_steps(lambda: sk.sigkernel_mmd2(Am, Bm, degree=6, compute="f32", grads=True), 2, 1)
+        labels = sk.split_labels(1000, 256, 256, seed=9 + rank)
+        ws_t = sk.mmd2_test_workspace(Am, Bm, 1000, compute="f32")
+        out_t = torch.empty(1002, dtype=torch.float64, device=dev)
+        t_test = timed_steps(lambda: sk.sigkernel_mmd2_test(Am, Bm, labels=labels, compute="f32", workspace=ws_t,
+                                                            out=out_t), 2, 1)
         line["mmd2"] = {"workload": "256 + 256 paths, 513 points, d=32 (Brownian vs drift 0.5, vol 1.2), approx N=6, "
                                     "FP32, symmetric K_AA/K_BB + K_AB, tiled M; gradients from forward tapes in "
                                     "chunks of pairs (tape <= 48 GiB per chunk)",
                         "cells": cells_m, "forward_ms": t_f, "fwd_bwd_ms": t_fb,
                         "forward_cell_updates_per_s": cells_m / (t_f / 1e3),
-                        "fwd_bwd_cell_updates_per_s": cells_m / (t_fb / 1e3)}
-        del Am, Bm
+                        "fwd_bwd_cell_updates_per_s": cells_m / (t_fb / 1e3),
+                        "permutation_test_1000_ms": t_test,
+                        "permutation_test_p_value": out_t[1].item()}
+        del Am, Bm, ws_t
 
     if rank == 0:
         if "cpu" in args.parts:
