@@ -39,7 +39,7 @@ D = 8
 DEGREE = 6
 CELLS_PER_PAIR = (L - 1) * (L - 1)
 CELLS = NX * NY * CELLS_PER_PAIR
-PARTS = ("f32", "ckpt", "fwd", "f64", "e2e", "osc", "uneven", "mmd", "cpu")
+PARTS = ("f32", "ckpt", "fwd", "f64", "e2e", "osc", "uneven", "mmd", "acc", "cpu")
 SM_COUNT = 152
 FP32_LANES = 128
 SM_MAX_MHZ = 2070.0
@@ -109,7 +109,7 @@ def parse():
     ap.add_argument("--parts", default=",".join(PARTS),
                     help="comma list: f32 (headline fwd+bwd step), ckpt (checkpointing adjoint), fwd (forward "
                          "only), f64 (FP64 forward), e2e, osc (oscillatory pairs), uneven (uneven batch), mmd "
-                         "(MMD^2 fwd+bwd), cpu")
+                         "(MMD^2 fwd+bwd, permutation test), acc (accuracy report: MAPE per order / refinement), cpu")
     args = ap.parse_args()
     args.parts = set(args.parts.split(","))
     if args.no_cpu_baseline:
@@ -549,6 +549,18 @@ def main():
                         "permutation_test_1000_ms": t_test,
                         "permutation_test_p_value": out_t[1].item()}
         del Am, Bm, ws_t
+
+    if "acc" in args.parts and rank == 0:  # MAPE per order / refinement against a converged FP64 solution
+        from paper_2502_08470_gb300 import accuracy
+
+        def sig3(rep):
+            return {L: {k: (round(v, 12) if k == "truth_check" else {o: float(f"{e:.3g}") for o, e in v.items()})
+                        for k, v in row.items()} for L, row in rep["lengths"].items()}
+        line["accuracy"] = {"truth": "interpolation N=12, lambda=3, FP64 (checked against approximation N=16)",
+                            "unit": "MAPE in percent; keys: order N (approx, interp) or dyadic lambda (fd*)"}
+        for kind, lengths in (("sin", (10, 50, 100, 200)), ("brownian", (10, 50, 200))):
+            line["accuracy"][kind] = {c: sig3(accuracy.report(kind, lengths=lengths, compute=c))
+                                      for c in ("f64", "f32")}
 
     if rank == 0:
         if "cpu" in args.parts:

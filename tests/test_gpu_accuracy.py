@@ -1,0 +1,94 @@
+"""The accuracy study on the GPU (Section 4 and Appendix "Additional Experiments": Figures
+"errorvslevel" and "errorvslevelsin", Tables 1-3): MAPE against a converged solution over the
+orders N = 2..17 (approximation), 2..12 (interpolation) and refinements lambda = 0..4 (FD), for
+the sin/cos paths of eq. (sinpath) and the tables' Brownian paths, at lengths 10 and 50.
+
+* The GPU truth (interpolation, N = 12, lambda = 3, FP64) is pinned to the oracle: to the level-21
+  truncated signature kernel at 10 points, and to the oracle's own converged solution at 50.
+* Every MAPE of the GPU report equals the oracle's MAPE for the same scheme and order wherever it
+  stands well above that scheme's rounding floor (100x the oracle's smallest MAPE of the scheme:
+  on the long sin/cos paths the approximation scheme's rounding is amplified to about 2e-4 %, and
+  there the two sides' roundings differ); at the floor the GPU's MAPE is within 10x the oracle's.
+* What the paper's tables and figures show holds on the GPU: each scheme improves with its order
+  until it reaches its rounding floor, interpolation is at least as accurate as approximation of
+  the same order, and the FD schemes approach the 4x-per-refinement rate of a second-order method.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+sk = pytest.importorskip("paper_2502_08470_gb300.sigkernel")
+acc = pytest.importorskip("paper_2502_08470_gb300.accuracy")
+
+PA, PB = np.repeat(np.arange(8), 8), np.tile(np.arange(8), 8)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda_available():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+@pytest.fixture(scope="module")
+def reports():
+    return {kind: acc.report(kind, lengths=(10, 50), fd_lambdas=range(0, 5)) for kind in ("sin", "brownian")}
+
+
+def test_gpu_truth_is_pinned_to_the_oracle():
+    for L in (10, 50):
+        Xn, Yn = acc.batch("sin", L)
+        truth = acc._gram(torch.tensor(Xn, device="cuda"), torch.tensor(Yn, device="cuda"), scheme="interp",
+                          degree=12, dyadic=3, compute="f64")
+        for a, b in ((0, 0), (3, 5)):
+            if L == 10:
+                ref = oracle.sig_trunc(Xn[a], Yn[b], 21)
+            else:
+                ref = oracle.kernel(Xn[a], Yn[b], "interp", 12, 2)
+            assert abs(truth[a, b] - ref) <= 1e-11 * abs(ref), (L, a, b)
+
+
+@pytest.mark.parametrize("kind", ["sin", "brownian"])
+@pytest.mark.parametrize("L", [10, 50])
+def test_report_equals_the_oracle_study(reports, kind, L):
+    row = reports[kind]["lengths"][L]
+    Xn, Yn = acc.batch(kind, L)
+    truth = oracle.pairs(list(Xn), list(Yn), PA, PB, "interp", 12, 2)
+    assert row["truth_check"] < 1e-9
+
+    def ref(scheme, N, lam):
+        v = oracle.pairs(list(Xn), list(Yn), PA, PB, scheme, N, lam)
+        return 100 * float(np.mean(np.abs(v - truth) / np.abs(truth)))
+
+    cases = {"approx": [(N, 0) for N in (2, 4, 6, 9, 13, 17)], "interp": [(N, 0) for N in (2, 3, 5, 8, 12)]}
+    for fd in ("fd1", "fd2", "fd_implicit"):
+        cases[fd] = [(2, lam) for lam in (0, 2, 4)]
+    for scheme, pts in cases.items():
+        want = {pt: ref(scheme, *pt) for pt in pts}
+        floor = min(want.values()) if scheme in ("approx", "interp") else 0.0  # FD: far above rounding
+        for (N, lam), w in want.items():
+            got = row[scheme][N] if scheme in ("approx", "interp") else row[scheme][lam]
+            if w > 100 * floor:
+                assert abs(got - w) <= 1e-3 * w, (scheme, N, lam, got, w)
+            else:
+                assert got <= 10 * w + 1e-10, (scheme, N, lam, got, w)
+
+
+@pytest.mark.parametrize("kind", ["sin", "brownian"])
+@pytest.mark.parametrize("L", [10, 50])
+def test_report_shows_the_papers_trends(reports, kind, L):
+    row = reports[kind]["lengths"][L]
+    for scheme in ("approx", "interp"):
+        curve = row[scheme]
+        floor = 10 * min(curve.values())
+        orders = sorted(curve)
+        for N in orders[:-3]:  # three orders more always help, until the rounding floor
+            assert curve[N + 3] < curve[N] or curve[N + 3] < floor, (scheme, N)
+    floor = 10 * min(row["approx"].values())
+    for N in row["interp"]:
+        assert row["interp"][N] <= row["approx"][N] or row["approx"][N] < floor, N
+    for fd in ("fd1", "fd2", "fd_implicit"):
+        assert row[fd][3] / row[fd][4] >= 3.0, fd
