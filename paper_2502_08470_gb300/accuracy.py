@@ -61,7 +61,9 @@ def mape_pct(G: np.ndarray, truth: np.ndarray) -> float:
 
 def report(kind: str = "sin", lengths=(10, 50, 100, 200), compute: str = "f64", truth_lambda: int = 3,
            approx_orders=range(2, 17), interp_orders=range(2, 13), fd_lambdas=range(0, 7), seed: int = 0) -> dict:
-    """MAPE (percent) per scheme and order / refinement for each length."""
+    """MAPE (percent) per scheme and order / refinement for each length: ``approx`` and ``interp``
+    by order N at lambda = 0, ``approx8_hybrid`` by lambda at N = 8, ``fd1`` / ``fd2`` /
+    ``fd_implicit`` by lambda."""
     out = {"workload": f"8 x 8 pairs of 2-d {kind} paths", "compute": compute, "truth": f"interp N=12, "
            f"lambda={truth_lambda}, FP64", "lengths": {}}
     for L in lengths:
@@ -74,6 +76,9 @@ def report(kind: str = "sin", lengths=(10, 50, 100, 200), compute: str = "f64", 
                          for N in approx_orders}
         row["interp"] = {N: mape_pct(_gram(X, Y, scheme="interp", degree=N, compute=compute), truth)
                          for N in interp_orders}
+        # the hybrid method of Section 3.2: the approximation scheme of order 8 on refined grids
+        row["approx8_hybrid"] = {lam: mape_pct(_gram(X, Y, scheme="approx", degree=8, dyadic=lam, compute=compute),
+                                               truth) for lam in (0, 1, 2, 3)}
         for fd in ("fd1", "fd2", "fd_implicit"):
             row[fd] = {lam: mape_pct(_gram(X, Y, scheme=fd, dyadic=lam, compute=compute), truth) for lam in fd_lambdas}
         out["lengths"][L] = row
