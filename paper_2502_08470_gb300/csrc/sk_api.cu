@@ -455,11 +455,7 @@ int run_forward(const sk_paths* X, const sk_paths* Y, int32_t d, int32_t dtype, 
     }
     int64_t buf_cols = p.buf_cols;
     void* args[] = {&L, &buf_cols};
-    int smem = p.smem_x;  // tiled-M x rows
-    if (tape) {  // kTapeSlots staging slots per warp for the tape's bulk copies
-        const int step_bytes = 32 * (p.T ? tape_row<float>(o->degree) * 4 : tape_row<double>(o->degree) * 8);
-        smem += (p.threads / 32) * kTapeSlots * step_bytes;
-    }
+    const int smem = p.smem_x;  // tiled-M x rows
     if (smem > 48 * 1024) SK_CUDA(cudaFuncSetAttribute(p.kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     const bool timed = (o->flags & SK_FLAG_TIME_KERNEL) != 0;
     if (timed) {

@@ -138,13 +138,6 @@ __device__ __forceinline__ T pow2t(int e) {
     else return pow2d(e);
 }
 
-// Staging slots per warp for the tape's bulk stores: a slot is refilled once the copy issued from
-// it kTapeSlots steps earlier has read it, so up to kTapeSlots steps are in flight per warp.  Two
-// measured fastest on the 128x128 Gram of 257-point paths (forward with tape: 14.9 ms; three
-// slots 15.5 ms, four 18.0 ms): the staging shared memory comes out of the L1 that serves the
-// increment rows.
-constexpr int kTapeSlots = 2;
-
 // Bytes of one warp step of the tape (32 lanes x one padded row of cell inputs).
 template <typename T, int N>
 __host__ __device__ constexpr int fwd_tape_step_bytes() {
@@ -227,8 +220,7 @@ constexpr int fwd_poly_coop_min_blocks() {
 // strips in between.
 template <typename T, int N, int NE, bool INTERP, int CW, bool MT>
 __device__ __forceinline__ void sweep_poly(const Launch& L, int64_t item, const PairDesc& P, int w, char* own_buf,
-                                           const char* prev_buf, int* prog, int64_t buf_cols,
-                                           unsigned char* tape_stage, T* xstage) {
+                                           const char* prev_buf, int* prog, int64_t buf_cols, T* xstage) {
     constexpr bool kRescale = std::is_same<T, float>::value;
     using V = typename Vec<T>::type;
     constexpr int W = Vec<T>::W;
@@ -338,16 +330,14 @@ __device__ __forceinline__ void sweep_poly(const Launch& L, int64_t item, const 
         else M = row_dot<T>(xrow, ybase + static_cast<int64_t>(jc >> lam) * dpad, L.nvec) * sub;
         if constexpr (CW == 1) {
             if (L.tape != nullptr) {
-                // Record the cell's inputs (a, b, exponent, M) for the adjoint: each lane writes
-                // its row into a shared-memory slot laid out [vector][lane], then one lane moves
-                // the whole step (32 rows) to the tape with a bulk copy.  kTapeSlots slots rotate;
-                // a slot is rewritten only after the copy issued from it kTapeSlots steps ago has
-                // read it.
+                // Record the cell's inputs (a, b, exponent, M) for the adjoint.  A step of the
+                // tape is laid out [vector][lane] (16-byte vectors), so each of the lane's vector
+                // stores fills 512 contiguous bytes with the warp's other lanes.  The stores are
+                // streaming (evict-first): the adjoint reads the tape only after the whole forward.
                 constexpr int TR = tape_row<T>(N);
                 constexpr int kStepBytes = 32 * TR * static_cast<int>(sizeof(T));
-                V* slot_v = reinterpret_cast<V*>(tape_stage + (step % kTapeSlots) * kStepBytes);
-                if (lane == 0) bulk_wait_read<kTapeSlots - 1>();
-                __syncwarp();
+                V* dst = reinterpret_cast<V*>(static_cast<char*>(L.tape) + item * L.tape_stride +
+                                              static_cast<int64_t>(step) * kStepBytes);
 #pragma unroll
                 for (int v = 0; v < TR / W; ++v) {
                     V t;
@@ -362,14 +352,7 @@ __device__ __forceinline__ void sweep_poly(const Launch& L, int64_t item, const 
                         }
                         if (q == 2 * N + 3) tp[q2] = M;
                     }
-                    slot_v[v * 32 + lane] = t;
-                }
-                fence_proxy_async_smem();
-                __syncwarp();
-                if (lane == 0) {
-                    bulk_store(static_cast<char*>(L.tape) + item * L.tape_stride + static_cast<int64_t>(step) * kStepBytes,
-                               slot_v, kStepBytes);
-                    bulk_commit();
+                    __stcs(dst + v * 32 + lane, t);
                 }
             }
         }
@@ -479,12 +462,9 @@ __global__ void __launch_bounds__((CW > 1 ? CW : kFwdWarps) * 32,
     const int nw = blockDim.x >> 5;
     char* block_base = static_cast<char*>(L.scratch) + static_cast<int64_t>(blockIdx.x) * nw * L.scratch_stride;
     char* own = block_base + wib * L.scratch_stride;
-    // dynamic shared memory: tape staging (two step slots per warp, with a tape), then the x rows
-    // of the tiled-M producer ([32][dpad] per warp, with L.mtile)
+    // dynamic shared memory: the x rows of the tiled-M producer ([32][dpad] per warp, with L.mtile)
     extern __shared__ __align__(128) unsigned char fwd_smem[];
-    unsigned char* tape_stage = fwd_smem + wib * kTapeSlots * fwd_tape_step_bytes<T, N>();
-    T* xstage = reinterpret_cast<T*>(fwd_smem + (L.tape != nullptr ? nw * kTapeSlots * fwd_tape_step_bytes<T, N>() : 0)) +
-                wib * 32 * L.dpad;
+    T* xstage = reinterpret_cast<T*>(fwd_smem) + wib * 32 * L.dpad;
 
     if constexpr (CW > 1) {
         __shared__ long long s_item;
@@ -500,12 +480,12 @@ __global__ void __launch_bounds__((CW > 1 ? CW : kFwdWarps) * 32,
             const int nstrips = P.lx > 0 ? static_cast<int>(((P.lx << L.lam) + 31) >> 5) : 0;
             if (nstrips < L.coop_min_strips) {  // short pairs from here on: one warp each
                 if (wib == 0 && !trivial_pair(L, item, P))
-                    sweep_poly<T, N, NE, INTERP, 1, MT>(L, item, P, 0, own, own, nullptr, buf_cols, tape_stage, xstage);
+                    sweep_poly<T, N, NE, INTERP, 1, MT>(L, item, P, 0, own, own, nullptr, buf_cols, xstage);
                 break;
             }
             if (!trivial_pair(L, item, P))
                 sweep_poly<T, N, NE, INTERP, CW, MT>(L, item, P, wib, own, block_base + ((wib + CW - 1) % CW) * L.scratch_stride,
-                                                 s_prog, buf_cols, tape_stage, xstage);
+                                                 s_prog, buf_cols, xstage);
         }
     }
     for (;;) {
@@ -513,9 +493,8 @@ __global__ void __launch_bounds__((CW > 1 ? CW : kFwdWarps) * 32,
         if (item < 0) break;
         const PairDesc P = decode_pair(L, item);
         if (trivial_pair(L, item, P)) continue;
-        sweep_poly<T, N, NE, INTERP, 1, MT>(L, item, P, 0, own, own, nullptr, buf_cols, tape_stage, xstage);
+        sweep_poly<T, N, NE, INTERP, 1, MT>(L, item, P, 0, own, own, nullptr, buf_cols, xstage);
     }
-    if (L.tape != nullptr && (threadIdx.x & 31) == 0) bulk_wait_all();  // no copy outlives the staging smem
 }
 
 }  // namespace sk
