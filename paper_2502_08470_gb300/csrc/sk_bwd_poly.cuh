@@ -856,13 +856,6 @@ __global__ void __launch_bounds__(kFwdWarps * 32, (bwd_tape_min_blocks<T, N, INT
                 bulk_load(ring + sl * kStepBytes, tape + static_cast<int64_t>(step - kTapeRing) * kStepBytes,
                           kStepBytes, bars + sl);
             }
-            if (lane == 31 && s >= 0) {  // lane 31 reads each column's hand-off first (sweep runs leftward)
-                const int jp = jj - kPrefetchSteps;
-                if (jp >= 0 && jp < cols) {
-                    prefetch_l1(rbuf + static_cast<int64_t>(jp) * (N + 1));
-                    if (kRescale) prefetch_l1(rexp + jp);
-                }
-            }
             T gb_in[N + 1];
 #pragma unroll
             for (int n = 0; n <= N; ++n) gb_in[n] = __shfl_down_sync(kFull, gbo[n], 1);

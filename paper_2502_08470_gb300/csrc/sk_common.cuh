@@ -27,14 +27,6 @@ extern __device__ int g_sk_error;
 
 __device__ __forceinline__ void record_error(int code) { atomicCAS(&g_sk_error, 0, code); }
 
-// Hint to bring the line holding p into this SM's L1 (no register, no effect on correctness: a
-// later store to the line from this SM updates it).  The sweeps use it for the one lane whose
-// operands change every step (the first touch of an increment row, the strip hand-off).
-__device__ __forceinline__ void prefetch_l1(const void* p) { asm volatile("prefetch.global.L1 [%0];" ::"l"(p)); }
-
-// Steps ahead at which that lane prefetches its next operands.
-constexpr int kPrefetchSteps = 2;
-
 // Coefficients that depend only on the (compile-time) indices of the unrolled cell loops are
 // constexpr, so they fold into instruction immediates instead of being fetched from the constant
 // bank every cell: 1/m, the Hankel coefficient n!/(n+k)!, and the interpolation projection

@@ -279,16 +279,6 @@ __device__ __forceinline__ void sweep_poly(const Launch& L, int64_t item, const 
                 ++sl0;
             }
         }
-        if (lane == 0) {  // lane 0 meets each column (its increment row, its hand-off) first
-            const int jp = jj + kPrefetchSteps;
-            if (jp >= 0 && jp < cols && sl < nloc) {
-                if constexpr (!MT) prefetch_l1(ybase + static_cast<int64_t>(jp >> lam) * dpad);
-                if (g > 0) {
-                    prefetch_l1(hprev + static_cast<int64_t>(jp) * (NB / W));
-                    if (kRescale) prefetch_l1(eprev + jp);
-                }
-            }
-        }
         T b[N + 1];
 #pragma unroll
         for (int n = 0; n <= N; ++n) b[n] = __shfl_up_sync(kFull, bo[n], 1);
