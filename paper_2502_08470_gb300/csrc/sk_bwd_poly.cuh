@@ -972,11 +972,13 @@ __global__ void __launch_bounds__(kFwdWarps * 32, (bwd_tape_min_blocks<T, N, INT
 // from the dk/dM buffer written by bwd_tape_kernel.  One block per work item (grid-stride), one
 // warp per strip of 32 rows.  A strip is cut into tiles of 32 columns; cell (r, j0 + q) of tile
 // j0 sits at step sP + j0 + r + q, so a tile spans 63 consecutive 32-element rows of the buffer.
-// The warp streams halves of 32 rows (4 KB in FP32) into a three-slot shared-memory ring with
-// cp.async.bulk, one half ahead, and with the buffer's skew (lane r of step t at (r + t) mod 32):
-//   * dk/dx: lane r walks its row (q = 0..31) against the broadcast dy_{j0+q};
-//   * dk/dy: lane q walks its column (r = 0..31) against the broadcast dx_r of the strip,
-// each with at most two-way bank conflicts.  Column sums are added to a shared per-increment
+// The warp streams halves of 32 rows (4 KB in FP32) into a circular ring of three halves (96 rows)
+// with cp.async.bulk, one half ahead.  Per tile it stages the 32 dy rows in shared memory next to
+// the strip's 32 dx rows, and with the buffer's skew (lane r of step t at (r + t) mod 32):
+//   * dk/dx: lane r walks its row (q = 0..31) against the dy rows;
+//   * dk/dy: lane q walks its column (r = 0..31) against the broadcast dx rows;
+// both conflict-free in FP32, every operand in shared memory, and the kContractC products of a
+// cell as two-wide FP32 instructions.  Column sums are added to a shared per-increment
 // accumulator once per tile, row sums once per strip; the accumulators are added to the FP64
 // gradients once per item, scaled by gbar 2^ek (straight to FP64 atomics when they do not fit).
 // Coordinates are taken kContractC at a time.
@@ -989,10 +991,80 @@ constexpr int kContractSlack = 64;  // buffer rows past an item's last step that
 // copy destination) starts 128-byte aligned.
 template <typename T>
 __host__ __device__ constexpr int contract_warp_bytes() {
-    return (3 * 32 * 32 * static_cast<int>(sizeof(T))        // ring of three halves
-            + 32 * kContractC * static_cast<int>(sizeof(T))  // dx of the strip's rows
-            + 3 * 8                                          // mbarriers
+    return (3 * 32 * 32 * static_cast<int>(sizeof(T))            // ring of three halves
+            + 2 * 32 * kContractC * static_cast<int>(sizeof(T))  // dx of the strip's rows, dy of the tile's columns
+            + 3 * 8                                              // mbarriers
             + 127) / 128 * 128;
+}
+
+// kContractC accumulators, acc += m v with v read from shared memory as 16-byte vectors (FP32:
+// two-wide FMAs on coordinate pairs).
+template <typename T> struct ContractAcc;
+template <> struct ContractAcc<float> {
+    float2 s[kContractC / 2];
+    __device__ __forceinline__ void zero() {
+#pragma unroll
+        for (int k = 0; k < kContractC / 2; ++k) s[k] = make_float2(0.f, 0.f);
+    }
+    __device__ __forceinline__ void axpy(float m, const float* v) {
+        const float2 m2 = make_float2(m, m);
+        const float4* vv = reinterpret_cast<const float4*>(v);
+#pragma unroll
+        for (int k = 0; k < kContractC / 4; ++k) {
+            const float4 y = vv[k];
+            s[2 * k] = __ffma2_rn(m2, make_float2(y.x, y.y), s[2 * k]);
+            s[2 * k + 1] = __ffma2_rn(m2, make_float2(y.z, y.w), s[2 * k + 1]);
+        }
+    }
+    __device__ __forceinline__ float get(int c) const { return (c & 1) ? s[c >> 1].y : s[c >> 1].x; }
+};
+template <> struct ContractAcc<double> {
+    double s[kContractC];
+    __device__ __forceinline__ void zero() {
+#pragma unroll
+        for (int c = 0; c < kContractC; ++c) s[c] = 0.0;
+    }
+    __device__ __forceinline__ void axpy(double m, const double* v) {
+        const double2* vv = reinterpret_cast<const double2*>(v);
+#pragma unroll
+        for (int k = 0; k < kContractC / 2; ++k) {
+            const double2 y = vv[k];
+            s[2 * k] = fma(m, y.x, s[2 * k]);
+            s[2 * k + 1] = fma(m, y.y, s[2 * k + 1]);
+        }
+    }
+    __device__ __forceinline__ double get(int c) const { return s[c]; }
+};
+
+// One tile: cell (r, j0 + q) is at ring row hb + r + q (mod 96), position (2r + q + coff) mod 32
+// with coff = (t0 + j0) mod 32.  nr, nc: valid rows and columns (FULL: 32 and 32; otherwise
+// cells outside them, whose buffer entries may hold anything, count as zero).
+template <typename T, bool FULL>
+__device__ __forceinline__ void contract_tile(const T* __restrict__ ring, int hb, int coff, const T* __restrict__ xs,
+                                              const T* __restrict__ ys, int nr, int nc, int lane, ContractAcc<T>& xa,
+                                              ContractAcc<T>& ya) {
+    // dk/dx: row `lane`.  The upper half-warp runs one column ahead (cyclically) so that the two
+    // halves read banks of opposite parity.
+#pragma unroll 8
+    for (int q0 = 0; q0 < 32; ++q0) {
+        const int q = (q0 + (lane >> 4)) & 31;
+        const int u = lane + q;
+        int row = hb + u;
+        row -= row >= 96 ? 96 : 0;
+        T m = ring[(row << 5) + ((lane + u + coff) & 31)];
+        if (!FULL) m = (lane < nr && q < nc) ? m : T(0);
+        xa.axpy(m, ys + q * kContractC);
+    }
+    // dk/dy: column `lane`, against the broadcast dx rows
+#pragma unroll 8
+    for (int r = 0; r < 32; ++r) {
+        const int u = r + lane;
+        int row = hb + u;
+        row -= row >= 96 ? 96 : 0;
+        T m = ring[(row << 5) + ((r + u + coff) & 31)];
+        if (!FULL) m = (r < nr && lane < nc) ? m : T(0);
+        ya.axpy(m, xs + r * kContractC);
+    }
 }
 
 template <typename T>
@@ -1010,9 +1082,10 @@ __global__ void __launch_bounds__(kContractWarps * 32) bwd_contract_kernel(BwdPa
     const T* __restrict__ incY = static_cast<const T*>(L.Y.inc);
     extern __shared__ __align__(16) unsigned char csm[];
     unsigned char* wsm = csm + wib * contract_warp_bytes<T>();
-    T* ring = reinterpret_cast<T*>(wsm);                                   // [3][32 rows][32]
+    T* ring = reinterpret_cast<T*>(wsm);                                   // [96 rows][32], circular
     T* xs = reinterpret_cast<T*>(wsm + 3 * HB);                            // [32][C]
-    uint64_t* bars = reinterpret_cast<uint64_t*>(wsm + 3 * HB + 32 * C * sizeof(T));
+    T* ys = xs + 32 * C;                                                   // [32][C]
+    uint64_t* bars = reinterpret_cast<uint64_t*>(wsm + 3 * HB + 2 * 32 * C * sizeof(T));
     T* acc = reinterpret_cast<T*>(csm + kContractWarps * contract_warp_bytes<T>());  // [C][lx + ly]
     if (lane == 0) {
         for (int k = 0; k < 3; ++k) mbar_init(bars + k, 1);
@@ -1071,72 +1144,50 @@ __global__ void __launch_bounds__(kContractWarps * 32) bwd_contract_kernel(BwdPa
                 __syncwarp();  // the previous strip's readers of xs are done
                 {
                     const int xi = min((s << 5) + lane, rows - 1) >> lam;
-                    const T* xr = xbase + static_cast<int64_t>(xi) * dpad + c0;
+                    const V* xr = reinterpret_cast<const V*>(xbase + static_cast<int64_t>(xi) * dpad + c0);
+                    V* xd = reinterpret_cast<V*>(xs + lane * C);
 #pragma unroll
-                    for (int c = 0; c < C; ++c) xs[lane * C + c] = (lane < nr && c0 + c < dpad) ? xr[c] : T(0);
+                    for (int k = 0; k < C / W; ++k) {
+                        V v = {};
+                        if (lane < nr && c0 + k * W < dpad) v = __ldg(xr + k);
+                        xd[k] = v;
+                    }
                 }
-                __syncwarp();
-                T xa[C];
-#pragma unroll
-                for (int c = 0; c < C; ++c) xa[c] = T(0);
+                ContractAcc<T> xa;
+                xa.zero();
                 for (int b = 0; b < ntiles; ++b) {
-                    // half b (slot s0) was awaited as the upper half of tile b - 1, except for b = 0
+                    // half b (slot b % 3) was awaited as the upper half of tile b - 1, except for b = 0
                     const int s0 = b % 3, s1 = (b + 1) % 3;
                     if (b == 0 && !await_slot(s0)) { stuck = true; break; }
                     if (!await_slot(s1)) { stuck = true; break; }
                     const int j0 = b << 5;
+                    const int nc = min(32, cols - j0);  // valid columns of the tile
+                    __syncwarp();  // the previous tile's readers of ys are done
+                    {
+                        const int yi = min(j0 + lane, cols - 1) >> lam;
+                        const V* yr = reinterpret_cast<const V*>(ybase + static_cast<int64_t>(yi) * dpad + c0);
+                        V* yd = reinterpret_cast<V*>(ys + lane * C);
+#pragma unroll
+                        for (int k = 0; k < C / W; ++k) {
+                            V v = {};
+                            if (lane < nc && c0 + k * W < dpad) v = __ldg(yr + k);
+                            yd[k] = v;
+                        }
+                    }
+                    __syncwarp();
+                    ContractAcc<T> ya;
+                    ya.zero();
                     const int coff = (t0 + j0) & 31;
-                    const T* S0 = ring + s0 * 1024;
-                    const T* S1 = ring + s1 * 1024;
-                    const bool full = (nr == 32) && (j0 + 32 <= cols);
-                    // dk/dx: row `lane`, columns j0 .. j0 + 31.  The upper half-warp runs one column
-                    // ahead (cyclically) so that the two halves read banks of opposite parity.
-#pragma unroll 8
-                    for (int q0 = 0; q0 < 32; ++q0) {
-                        const int q = (q0 + (lane >> 4)) & 31;
-                        const int u = lane + q;
-                        const T* Sr = u < 32 ? S0 : S1;
-                        T m = Sr[((u & 31) << 5) + ((lane + u + coff) & 31)];
-                        if (!full) m = (lane < nr && j0 + q < cols) ? m : T(0);
-                        const int yi = min(j0 + q, cols - 1) >> lam;
-                        const V* yv = reinterpret_cast<const V*>(ybase + static_cast<int64_t>(yi) * dpad + c0);
-#pragma unroll
-                        for (int c4 = 0; c4 < C / W; ++c4) {
-                            if (c0 + c4 * W < dpad) {
-                                const V yy = __ldg(yv + c4);
-                                const T* yp = reinterpret_cast<const T*>(&yy);
-#pragma unroll
-                                for (int w = 0; w < W; ++w) xa[c4 * W + w] = fma(m, yp[w], xa[c4 * W + w]);
-                            }
-                        }
-                    }
-                    // dk/dy: column j0 + lane, rows 0 .. 31 of the strip
-                    T ys[C];
-#pragma unroll
-                    for (int c = 0; c < C; ++c) ys[c] = T(0);
-#pragma unroll 8
-                    for (int r = 0; r < 32; ++r) {
-                        const int u = r + lane;
-                        const T* Sr = u < 32 ? S0 : S1;
-                        T m = Sr[((u & 31) << 5) + ((r + u + coff) & 31)];
-                        if (!full) m = (r < nr && j0 + lane < cols) ? m : T(0);
-                        const V* xv = reinterpret_cast<const V*>(xs + r * C);
-#pragma unroll
-                        for (int c4 = 0; c4 < C / W; ++c4) {
-                            const V xx = xv[c4];
-                            const T* xp = reinterpret_cast<const T*>(&xx);
-#pragma unroll
-                            for (int w = 0; w < W; ++w) ys[c4 * W + w] = fma(m, xp[w], ys[c4 * W + w]);
-                        }
-                    }
-                    if (j0 + lane < cols) {
+                    if (nr == 32 && nc == 32) contract_tile<T, true>(ring, s0 * 32, coff, xs, ys, nr, nc, lane, xa, ya);
+                    else contract_tile<T, false>(ring, s0 * 32, coff, xs, ys, nr, nc, lane, xa, ya);
+                    if (lane < nc) {
                         const int yi = (j0 + lane) >> lam;
 #pragma unroll
                         for (int c = 0; c < C; ++c) {
-                            if (c0 + c < dpad && ys[c] != T(0)) {
-                                if (use_smem) atomicAdd(acc + c * nrow + P.lx + yi, ys[c]);
-                                else atomicAdd(gy + static_cast<int64_t>(yi) * dpad + c0 + c,
-                                               static_cast<double>(ys[c]) * gscale);
+                            const T v = ya.get(c);
+                            if (c0 + c < dpad && v != T(0)) {
+                                if (use_smem) atomicAdd(acc + c * nrow + P.lx + yi, v);
+                                else atomicAdd(gy + static_cast<int64_t>(yi) * dpad + c0 + c, static_cast<double>(v) * gscale);
                             }
                         }
                     }
@@ -1154,10 +1205,10 @@ __global__ void __launch_bounds__(kContractWarps * 32) bwd_contract_kernel(BwdPa
                     const int xi = ((s << 5) + lane) >> lam;
 #pragma unroll
                     for (int c = 0; c < C; ++c) {
-                        if (c0 + c < dpad && xa[c] != T(0)) {
-                            if (use_smem) atomicAdd(acc + c * nrow + xi, xa[c]);
-                            else atomicAdd(gx + static_cast<int64_t>(xi) * dpad + c0 + c,
-                                           static_cast<double>(xa[c]) * gscale);
+                        const T v = xa.get(c);
+                        if (c0 + c < dpad && v != T(0)) {
+                            if (use_smem) atomicAdd(acc + c * nrow + xi, v);
+                            else atomicAdd(gx + static_cast<int64_t>(xi) * dpad + c0 + c, static_cast<double>(v) * gscale);
                         }
                     }
                 }
