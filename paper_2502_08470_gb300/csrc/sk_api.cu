@@ -706,10 +706,10 @@ int plan_backward_tape(const sk_paths* X, const sk_paths* Y, int32_t d, int32_t 
     b.smem_bytes = kFwdWarps * (kTapeRing * step_bytes + kTapeRing * 8);
     const int esize = p.T ? 4 : 8, N = o->degree;
     b.cols_max = std::max<int64_t>(Y->max_len << o->dyadic, 1);
-    b.off_rbuf = 0;  // strip hand-off rows: edge adjoints and their exponent, whole 16-byte vectors
-    const int rb = p.T ? bwd_handoff_row<float>(N) : bwd_handoff_row<double>(N);
-    int64_t off = static_cast<int64_t>(align256(b.cols_max * rb * esize));
-    b.off_rexp = 0;  // the exponent travels inside the hand-off row
+    b.off_rbuf = 0;
+    int64_t off = static_cast<int64_t>(align256(b.cols_max * (N + 1) * esize));
+    b.off_rexp = off;
+    off += static_cast<int64_t>(align256(b.cols_max * 4));
     b.slot_bytes = off;
     // dk/dM buffer: the tape's [step][lane] grid of one element per cell
     // (plus the rows past an item's last step that the contraction's tiles may read)

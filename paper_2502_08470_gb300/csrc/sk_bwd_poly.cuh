@@ -714,7 +714,6 @@ __global__ void __launch_bounds__(kFwdWarps * 32, (bwd_min_blocks<T, N, K>()))
 // Per-lane streaming loads of the tape one step ahead (no ring, no shared memory) measured slower
 // on the 128x128 Gram of 257-point paths: 18.9 ms against 15.6 ms for this ring.
 constexpr int kTapeRing = 4;
-static_assert((kTapeRing & (kTapeRing - 1)) == 0, "slots are indexed with a mask");
 
 template <typename T, int N, bool INTERP>
 __host__ __device__ constexpr int bwd_tape_min_blocks() {
@@ -731,13 +730,6 @@ __host__ __device__ constexpr int bwd_series_top() {
 template <typename T, int N>
 __host__ __device__ constexpr int bwd_tape_warp_bytes() {
     return kTapeRing * fwd_tape_step_bytes<T, N>() + kTapeRing * 8;
-}
-
-// Elements of one entry of the tape adjoint's strip hand-off: the N + 1 edge adjoints and their
-// exponent (as the element's bits), padded to whole 16-byte vectors.
-template <typename T>
-__host__ __device__ constexpr int bwd_handoff_row(int N) {
-    return (N + 2 + Vec<T>::W - 1) / Vec<T>::W * Vec<T>::W;
 }
 
 // Gradient seed and exponent of k_hat for item `item` (shared by the adjoint and the contraction).
@@ -761,8 +753,8 @@ __global__ void __launch_bounds__(kFwdWarps * 32, (bwd_tape_min_blocks<T, N, INT
     const int wib = threadIdx.x >> 5;
     const int64_t slot = static_cast<int64_t>(blockIdx.x) * (blockDim.x >> 5) + wib;
     char* base = static_cast<char*>(L.scratch) + slot * L.scratch_stride;
-    constexpr int RB = bwd_handoff_row<T>(N);
-    V* rbuf = reinterpret_cast<V*>(base + B.off_rbuf);          // [col][RB / W]: adjoints, exponent
+    T* rbuf = reinterpret_cast<T*>(base + B.off_rbuf);          // [col][N+1]
+    int* rexp = reinterpret_cast<int*>(base + B.off_rexp);      // [col]
     constexpr int kStepBytes = fwd_tape_step_bytes<T, N>();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     unsigned char* ring = smem_raw + wib * bwd_tape_warp_bytes<T, N>();
@@ -817,7 +809,7 @@ __global__ void __launch_bounds__(kFwdWarps * 32, (bwd_tape_min_blocks<T, N, INT
         if (lane == 0) {
             for (int k = 0; k < kTapeRing && nsteps - 1 - k >= 0; ++k) {
                 const int t = nsteps - 1 - k;
-                const int sl = t & (kTapeRing - 1);
+                const int sl = t % kTapeRing;
                 mbar_arrive_expect_tx(bars + sl, kStepBytes);
                 bulk_load(ring + sl * kStepBytes, tape + static_cast<int64_t>(t) * kStepBytes, kStepBytes, bars + sl);
             }
@@ -828,7 +820,7 @@ __global__ void __launch_bounds__(kFwdWarps * 32, (bwd_tape_min_blocks<T, N, INT
         int jj = tt >= 0 ? tt - s * period : -1;
         int stuck_step = -1;
         for (int step = nsteps - 1; step >= 0; --step) {
-            const int sl = step & (kTapeRing - 1);
+            const int sl = step % kTapeRing;
             if (!mbar_wait(bars + sl, (parity >> sl) & 1u)) {
                 stuck = true;  // the device error word is set; drain what is in flight and stop
                 stuck_step = step;
@@ -878,21 +870,10 @@ __global__ void __launch_bounds__(kFwdWarps * 32, (bwd_tape_min_blocks<T, N, INT
                         for (int n = 0; n <= N; ++n) gb_in[n] = T(0);
                         gbe_in = kZeroExp;
                     } else {
-                        const V* src = rbuf + static_cast<int64_t>(jj) * (RB / W);
+                        const T* src = rbuf + static_cast<int64_t>(jj) * (N + 1);
 #pragma unroll
-                        for (int v = 0; v < RB / W; ++v) {
-                            const V t = src[v];
-                            const T* tp = reinterpret_cast<const T*>(&t);
-#pragma unroll
-                            for (int w = 0; w < W; ++w) {
-                                const int q = v * W + w;
-                                if (q <= N) gb_in[q] = tp[w];
-                                else if (q == N + 1) {
-                                    if constexpr (kRescale) gbe_in = __float_as_int(tp[w]);
-                                    else gbe_in = 0;
-                                }
-                            }
-                        }
+                        for (int n = 0; n <= N; ++n) gb_in[n] = src[n];
+                        gbe_in = kRescale ? rexp[jj] : 0;
                     }
                 }
                 if (!INTERP && step == nsteps - 1) {  // warp-uniform: the corner cell's upper input
@@ -953,21 +934,10 @@ __global__ void __launch_bounds__(kFwdWarps * 32, (bwd_tape_min_blocks<T, N, INT
                 }
                 gbe = gea;
                 if (lane == 0 && s > 0) {  // hand the left-edge adjoint to lane 31 of the strip below
-                    V* dst = rbuf + static_cast<int64_t>(jj) * (RB / W);
+                    T* dst = rbuf + static_cast<int64_t>(jj) * (N + 1);
 #pragma unroll
-                    for (int v = 0; v < RB / W; ++v) {
-                        V t;
-                        T* tp = reinterpret_cast<T*>(&t);
-#pragma unroll
-                        for (int w = 0; w < W; ++w) {
-                            const int q = v * W + w;
-                            tp[w] = q <= N ? gbo[q] : T(0);
-                            if constexpr (kRescale) {
-                                if (q == N + 1) tp[w] = __int_as_float(gbe);
-                            }
-                        }
-                        dst[v] = t;
-                    }
+                    for (int n = 0; n <= N; ++n) dst[n] = gbo[n];
+                    if (kRescale) rexp[jj] = gbe;
                 }
             }
             mout[static_cast<int64_t>(step) * 32 + ((lane + step) & 31)] = mrel;  // skewed row
@@ -985,7 +955,7 @@ __global__ void __launch_bounds__(kFwdWarps * 32, (bwd_tape_min_blocks<T, N, INT
             // down to stuck_step - kTapeRing + 1) before leaving.
             if (lane == 0)
                 for (int k = 0; k < kTapeRing && stuck_step - k >= 0; ++k) {
-                    const int sl = (stuck_step - k) & (kTapeRing - 1);
+                    const int sl = (stuck_step - k) % kTapeRing;
                     mbar_wait(bars + sl, (parity >> sl) & 1u);
                 }
             __syncwarp();
