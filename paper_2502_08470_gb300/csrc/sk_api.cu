@@ -687,7 +687,7 @@ struct TapeBwdPlan {
     TapePlan t;
     const void* kern;
     const void* ckern;
-    int smem_bytes, cblocks, csmem;
+    int smem_bytes, cblocks, csmem, cC;
     int64_t cols_max, off_rbuf, off_rexp, slot_bytes, mb_stride, acc_bytes;
     size_t off_gincx, off_gincy, off_scratch, off_mbuf, total;
 };
@@ -701,7 +701,9 @@ int plan_backward_tape(const sk_paths* X, const sk_paths* Y, int32_t d, int32_t 
     const bool interp = o->scheme == SK_POLY_INTERP;
     b.kern = p.T ? bwd_tape_ptr_f32(o->degree, interp) : bwd_tape_ptr_f64(o->degree, interp);
     if (!b.kern) return fail(SK_ERR_UNSUPPORTED, "no adjoint kernel for order %d", o->degree);
-    b.ckern = p.T ? bwd_contract_ptr_f32() : bwd_contract_ptr_f64();
+    // contraction: every coordinate of a padded increment row in one pass up to 32 (8, 16 or 32)
+    b.cC = p.dpad <= 8 ? 8 : (p.dpad <= 16 ? 16 : 32);
+    b.ckern = p.T ? bwd_contract_ptr_f32(b.cC) : bwd_contract_ptr_f64(b.cC);
     const int step_bytes = 32 * (p.T ? tape_row<float>(o->degree) * 4 : tape_row<double>(o->degree) * 8);
     b.smem_bytes = kFwdWarps * (kTapeRing * step_bytes + kTapeRing * 8);
     const int esize = p.T ? 4 : 8, N = o->degree;
@@ -714,11 +716,14 @@ int plan_backward_tape(const sk_paths* X, const sk_paths* Y, int32_t d, int32_t 
     // dk/dM buffer: the tape's [step][lane] grid of one element per cell
     // (plus the rows past an item's last step that the contraction's tiles may read)
     b.mb_stride = static_cast<int64_t>(align256(static_cast<size_t>(b.t.nsteps + kContractSlack) * 32 * esize));
-    // contraction accumulators: (lx + ly) increments x kContractC coordinates, when they fit
-    const int64_t acc_need = (std::max<int64_t>(X->max_len, 1) + std::max<int64_t>(Y->max_len, 1)) * kContractC * esize;
-    b.acc_bytes = acc_need <= (64 << 10) ? acc_need : 0;
-    b.csmem = kContractWarps * (p.T ? contract_warp_bytes<float>() : contract_warp_bytes<double>()) +
-              static_cast<int>(b.acc_bytes);
+    // contraction: per-warp rings and staged rows, then the block's column accumulator
+    int cwarp = 0;
+    if (p.T) cwarp = b.cC == 8 ? contract_warp_bytes<float, 8>() : b.cC == 16 ? contract_warp_bytes<float, 16>()
+                                                                        : contract_warp_bytes<float, 32>();
+    else cwarp = b.cC == 8 ? contract_warp_bytes<double, 8>() : b.cC == 16 ? contract_warp_bytes<double, 16>()
+                                                                      : contract_warp_bytes<double, 32>();
+    b.acc_bytes = kContractAccBytes;
+    b.csmem = kContractWarps * cwarp + kContractAccBytes;
     int dev = 0, sms = 0, per_sm = 0, cper_sm = 0;
     SK_CUDA(cudaGetDevice(&dev));
     SK_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));

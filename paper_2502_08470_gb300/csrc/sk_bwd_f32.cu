@@ -52,7 +52,14 @@ const void* bwd_tape_ptr_f32(int N, bool interp) {
     }
 }
 
-const void* bwd_contract_ptr_f32() { return reinterpret_cast<const void*>(&bwd_contract_kernel<float>); }
+const void* bwd_contract_ptr_f32(int C) {
+    switch (C) {
+        case 8: return reinterpret_cast<const void*>(&bwd_contract_kernel<float, 8>);
+        case 16: return reinterpret_cast<const void*>(&bwd_contract_kernel<float, 16>);
+        case 32: return reinterpret_cast<const void*>(&bwd_contract_kernel<float, 32>);
+        default: return nullptr;
+    }
+}
 
 int bwd_segment_f32() { return 8; }
 

@@ -52,7 +52,14 @@ const void* bwd_tape_ptr_f64(int N, bool interp) {
     }
 }
 
-const void* bwd_contract_ptr_f64() { return reinterpret_cast<const void*>(&bwd_contract_kernel<double>); }
+const void* bwd_contract_ptr_f64(int C) {
+    switch (C) {
+        case 8: return reinterpret_cast<const void*>(&bwd_contract_kernel<double, 8>);
+        case 16: return reinterpret_cast<const void*>(&bwd_contract_kernel<double, 16>);
+        case 32: return reinterpret_cast<const void*>(&bwd_contract_kernel<double, 32>);
+        default: return nullptr;
+    }
+}
 
 int bwd_segment_f64() { return 4; }
 

@@ -49,7 +49,7 @@ struct BwdParams {
     int64_t off_fbuf, off_fexp, off_rbuf, off_rexp, off_ybar;  // byte offsets inside a warp slot
     void* mbuf;               // tape adjoint: per-item dk/dM, [step][lane] of T
     int64_t mb_stride;        // bytes per item of mbuf
-    int64_t acc_bytes;        // contraction: shared-memory accumulator bytes per block
+    int64_t acc_bytes;        // contraction: shared-memory column accumulator bytes per block
 };
 
 template <typename T>
@@ -974,43 +974,51 @@ __global__ void __launch_bounds__(kFwdWarps * 32, (bwd_tape_min_blocks<T, N, INT
 // j0 sits at step sP + j0 + r + q, so a tile spans 63 consecutive 32-element rows of the buffer.
 // The warp streams halves of 32 rows (4 KB in FP32) into a circular ring of three halves (96 rows)
 // with cp.async.bulk, one half ahead.  Per tile it stages the 32 dy rows in shared memory next to
-// the strip's 32 dx rows, and with the buffer's skew (lane r of step t at (r + t) mod 32):
+// the strip's 32 dx rows (C coordinates each), and with the buffer's skew (lane r of step t at
+// (r + t) mod 32):
 //   * dk/dx: lane r walks its row (q = 0..31) against the dy rows;
 //   * dk/dy: lane q walks its column (r = 0..31) against the broadcast dx rows;
-// both conflict-free in FP32, every operand in shared memory, and the kContractC products of a
-// cell as two-wide FP32 instructions.  Column sums are added to a shared per-increment
-// accumulator once per tile, row sums once per strip; the accumulators are added to the FP64
-// gradients once per item, scaled by gbar 2^ek (straight to FP64 atomics when they do not fit).
-// Coordinates are taken kContractC at a time.
+// both conflict-free in FP32, every operand in shared memory, each cell's dk/dM read once for all
+// C coordinates, and the products as two-wide FP32 instructions.  Row sums stay in registers
+// across a strip's tiles and go to the FP64 gradients once per strip (strips own disjoint rows).
+// Column sums are added to a shared per-column accumulator once per tile; the columns are taken a
+// window at a time (as many as the accumulator holds), and the accumulator goes to the FP64
+// gradients once per window, scaled by gbar 2^ek.  Coordinates beyond C are taken C at a time.
 // ---------------------------------------------------------------------------------------------
-constexpr int kContractC = 8;
 constexpr int kContractWarps = 4;
 constexpr int kContractSlack = 64;  // buffer rows past an item's last step that a tile may read
+constexpr int kContractAccBytes = 32 << 10;  // per-block column accumulator
 
 // Shared memory of one contraction warp, padded to 128 bytes so that every warp's ring (a bulk
 // copy destination) starts 128-byte aligned.
-template <typename T>
+template <typename T, int C>
 __host__ __device__ constexpr int contract_warp_bytes() {
-    return (3 * 32 * 32 * static_cast<int>(sizeof(T))            // ring of three halves
-            + 2 * 32 * kContractC * static_cast<int>(sizeof(T))  // dx of the strip's rows, dy of the tile's columns
-            + 3 * 8                                              // mbarriers
+    return (3 * 32 * 32 * static_cast<int>(sizeof(T))    // ring of three halves
+            + 2 * 32 * C * static_cast<int>(sizeof(T))   // dx of the strip's rows, dy of the tile's columns
+            + 3 * 8                                      // mbarriers
             + 127) / 128 * 128;
 }
 
-// kContractC accumulators, acc += m v with v read from shared memory as 16-byte vectors (FP32:
-// two-wide FMAs on coordinate pairs).
-template <typename T> struct ContractAcc;
-template <> struct ContractAcc<float> {
-    float2 s[kContractC / 2];
+// Columns of a window: the accumulator holds [C][window] elements.
+template <typename T, int C>
+__host__ __device__ constexpr int contract_window() {
+    return kContractAccBytes / (C * static_cast<int>(sizeof(T))) / 32 * 32;
+}
+
+// C accumulators, acc += m v with v read from shared memory as 16-byte vectors (FP32: two-wide
+// FMAs on coordinate pairs).
+template <typename T, int C> struct ContractAcc;
+template <int C> struct ContractAcc<float, C> {
+    float2 s[C / 2];
     __device__ __forceinline__ void zero() {
 #pragma unroll
-        for (int k = 0; k < kContractC / 2; ++k) s[k] = make_float2(0.f, 0.f);
+        for (int k = 0; k < C / 2; ++k) s[k] = make_float2(0.f, 0.f);
     }
     __device__ __forceinline__ void axpy(float m, const float* v) {
         const float2 m2 = make_float2(m, m);
         const float4* vv = reinterpret_cast<const float4*>(v);
 #pragma unroll
-        for (int k = 0; k < kContractC / 4; ++k) {
+        for (int k = 0; k < C / 4; ++k) {
             const float4 y = vv[k];
             s[2 * k] = __ffma2_rn(m2, make_float2(y.x, y.y), s[2 * k]);
             s[2 * k + 1] = __ffma2_rn(m2, make_float2(y.z, y.w), s[2 * k + 1]);
@@ -1018,16 +1026,16 @@ template <> struct ContractAcc<float> {
     }
     __device__ __forceinline__ float get(int c) const { return (c & 1) ? s[c >> 1].y : s[c >> 1].x; }
 };
-template <> struct ContractAcc<double> {
-    double s[kContractC];
+template <int C> struct ContractAcc<double, C> {
+    double s[C];
     __device__ __forceinline__ void zero() {
 #pragma unroll
-        for (int c = 0; c < kContractC; ++c) s[c] = 0.0;
+        for (int c = 0; c < C; ++c) s[c] = 0.0;
     }
     __device__ __forceinline__ void axpy(double m, const double* v) {
         const double2* vv = reinterpret_cast<const double2*>(v);
 #pragma unroll
-        for (int k = 0; k < kContractC / 2; ++k) {
+        for (int k = 0; k < C / 2; ++k) {
             const double2 y = vv[k];
             s[2 * k] = fma(m, y.x, s[2 * k]);
             s[2 * k + 1] = fma(m, y.y, s[2 * k + 1]);
@@ -1039,10 +1047,10 @@ template <> struct ContractAcc<double> {
 // One tile: cell (r, j0 + q) is at ring row hb + r + q (mod 96), position (2r + q + coff) mod 32
 // with coff = (t0 + j0) mod 32.  nr, nc: valid rows and columns (FULL: 32 and 32; otherwise
 // cells outside them, whose buffer entries may hold anything, count as zero).
-template <typename T, bool FULL>
+template <typename T, int C, bool FULL>
 __device__ __forceinline__ void contract_tile(const T* __restrict__ ring, int hb, int coff, const T* __restrict__ xs,
-                                              const T* __restrict__ ys, int nr, int nc, int lane, ContractAcc<T>& xa,
-                                              ContractAcc<T>& ya) {
+                                              const T* __restrict__ ys, int nr, int nc, int lane, ContractAcc<T, C>& xa,
+                                              ContractAcc<T, C>& ya) {
     // dk/dx: row `lane`.  The upper half-warp runs one column ahead (cyclically) so that the two
     // halves read banks of opposite parity.
 #pragma unroll 8
@@ -1053,7 +1061,7 @@ __device__ __forceinline__ void contract_tile(const T* __restrict__ ring, int hb
         row -= row >= 96 ? 96 : 0;
         T m = ring[(row << 5) + ((lane + u + coff) & 31)];
         if (!FULL) m = (lane < nr && q < nc) ? m : T(0);
-        xa.axpy(m, ys + q * kContractC);
+        xa.axpy(m, ys + q * C);
     }
     // dk/dy: column `lane`, against the broadcast dx rows
 #pragma unroll 8
@@ -1063,14 +1071,14 @@ __device__ __forceinline__ void contract_tile(const T* __restrict__ ring, int hb
         row -= row >= 96 ? 96 : 0;
         T m = ring[(row << 5) + ((r + u + coff) & 31)];
         if (!FULL) m = (r < nr && lane < nc) ? m : T(0);
-        ya.axpy(m, xs + r * kContractC);
+        ya.axpy(m, xs + r * C);
     }
 }
 
-template <typename T>
+template <typename T, int C>
 __global__ void __launch_bounds__(kContractWarps * 32) bwd_contract_kernel(BwdParams B) {
-    constexpr int C = kContractC;
     constexpr int HB = 32 * 32 * static_cast<int>(sizeof(T));  // bytes of one half
+    constexpr int WIN = contract_window<T, C>();
     using V = typename Vec<T>::type;
     constexpr int W = Vec<T>::W;
     const Launch& L = B.L;
@@ -1081,12 +1089,12 @@ __global__ void __launch_bounds__(kContractWarps * 32) bwd_contract_kernel(BwdPa
     const T* __restrict__ incX = static_cast<const T*>(L.X.inc);
     const T* __restrict__ incY = static_cast<const T*>(L.Y.inc);
     extern __shared__ __align__(16) unsigned char csm[];
-    unsigned char* wsm = csm + wib * contract_warp_bytes<T>();
+    unsigned char* wsm = csm + wib * contract_warp_bytes<T, C>();
     T* ring = reinterpret_cast<T*>(wsm);                                   // [96 rows][32], circular
     T* xs = reinterpret_cast<T*>(wsm + 3 * HB);                            // [32][C]
     T* ys = xs + 32 * C;                                                   // [32][C]
     uint64_t* bars = reinterpret_cast<uint64_t*>(wsm + 3 * HB + 2 * 32 * C * sizeof(T));
-    T* acc = reinterpret_cast<T*>(csm + kContractWarps * contract_warp_bytes<T>());  // [C][lx + ly]
+    T* acc = reinterpret_cast<T*>(csm + kContractWarps * contract_warp_bytes<T, C>());  // [C][WIN]
     if (lane == 0) {
         for (int k = 0; k < 3; ++k) mbar_init(bars + k, 1);
         fence_mbar_init();
@@ -1096,8 +1104,8 @@ __global__ void __launch_bounds__(kContractWarps * 32) bwd_contract_kernel(BwdPa
     uint32_t pending = 0;  // bit k: a copy into slot k was issued and not yet awaited
     bool stuck = false;
 
-    // Every warp visits every item of its block (a stuck warp skips its strips) so that the
-    // block-wide barriers below are reached by all warps.
+    // Every warp visits every item and window of its block (a stuck warp skips its strips) so
+    // that the block-wide barriers below are reached by all warps.
     for (int64_t item = blockIdx.x; item < L.npairs; item += gridDim.x) {
         const PairDesc P = decode_pair(L, item);
         if (P.lx <= 0 || P.ly <= 0) continue;
@@ -1108,7 +1116,6 @@ __global__ void __launch_bounds__(kContractWarps * 32) bwd_contract_kernel(BwdPa
         const int cols = static_cast<int>(P.ly << lam);
         const int period = cols > 32 ? cols : 32;
         const int nstrips = (rows + 31) >> 5;
-        const int ntiles = (cols + 31) >> 5;
         // Waits on slot k for the copy issued last into it; false when the wait ran out.
         auto await_slot = [&](int k) -> bool {
             if (!mbar_wait(bars + k, (parity >> k) & 1u)) return false;
@@ -1121,105 +1128,99 @@ __global__ void __launch_bounds__(kContractWarps * 32) bwd_contract_kernel(BwdPa
         const T* ybase = incY + P.ys * dpad;
         double* gx = B.gincX + P.xs * dpad;
         double* gy = B.gincY + P.ys * dpad;
-        const int nrow = static_cast<int>(P.lx + P.ly);  // accumulator rows: X increments, then Y
-        const int nacc = nrow * C;                        // laid out [C][nrow]
-        const bool use_smem = static_cast<int64_t>(nacc) * static_cast<int64_t>(sizeof(T)) <= B.acc_bytes;
         for (int c0 = 0; c0 < dpad; c0 += C) {
-            if (use_smem) {
-                for (int q = threadIdx.x; q < nacc; q += blockDim.x) acc[q] = T(0);
+            for (int w0 = 0; w0 < cols; w0 += WIN) {  // a window of columns [w0, w0 + WIN)
+                const int wcols = min(WIN, cols - w0);
+                const int ntiles = (wcols + 31) >> 5;
+                // coarse columns the window touches: (w0 >> lam) .. ((w0 + wcols - 1) >> lam)
+                const int ya0 = w0 >> lam;
+                const int nya = ((w0 + wcols - 1) >> lam) - ya0 + 1;
+                for (int q = threadIdx.x; q < C * nya; q += blockDim.x) acc[q] = T(0);
                 __syncthreads();
-            }
-            for (int s = wib; s < nstrips && !stuck; s += kContractWarps) {
-                const int t0 = s * period;
-                const int nr = min(32, rows - (s << 5));  // valid rows of the strip
-                // half h of the strip = buffer rows t0 + 32h .. t0 + 32h + 31, in slot h % 3
-                for (int h = 0; h < 3 && h <= ntiles; ++h) {
-                    if (lane == 0) {
-                        mbar_arrive_expect_tx(bars + h, HB);
-                        bulk_load(ring + h * 1024, mb + static_cast<int64_t>(t0 + 32 * h) * 32 * sizeof(T), HB,
-                                  bars + h);
+                for (int s = wib; s < nstrips && !stuck; s += kContractWarps) {
+                    const int t0 = s * period + w0;  // buffer row of the window's first tile
+                    const int nr = min(32, rows - (s << 5));  // valid rows of the strip
+                    // half h of the window = buffer rows t0 + 32h .. t0 + 32h + 31, in slot h % 3
+                    for (int h = 0; h < 3 && h <= ntiles; ++h) {
+                        if (lane == 0) {
+                            mbar_arrive_expect_tx(bars + h, HB);
+                            bulk_load(ring + h * 1024, mb + static_cast<int64_t>(t0 + 32 * h) * 32 * sizeof(T), HB,
+                                      bars + h);
+                        }
+                        pending |= 1u << h;
                     }
-                    pending |= 1u << h;
-                }
-                __syncwarp();  // the previous strip's readers of xs are done
-                {
-                    const int xi = min((s << 5) + lane, rows - 1) >> lam;
-                    const V* xr = reinterpret_cast<const V*>(xbase + static_cast<int64_t>(xi) * dpad + c0);
-                    V* xd = reinterpret_cast<V*>(xs + lane * C);
-#pragma unroll
-                    for (int k = 0; k < C / W; ++k) {
-                        V v = {};
-                        if (lane < nr && c0 + k * W < dpad) v = __ldg(xr + k);
-                        xd[k] = v;
-                    }
-                }
-                ContractAcc<T> xa;
-                xa.zero();
-                for (int b = 0; b < ntiles; ++b) {
-                    // half b (slot b % 3) was awaited as the upper half of tile b - 1, except for b = 0
-                    const int s0 = b % 3, s1 = (b + 1) % 3;
-                    if (b == 0 && !await_slot(s0)) { stuck = true; break; }
-                    if (!await_slot(s1)) { stuck = true; break; }
-                    const int j0 = b << 5;
-                    const int nc = min(32, cols - j0);  // valid columns of the tile
-                    __syncwarp();  // the previous tile's readers of ys are done
+                    __syncwarp();  // the previous strip's readers of xs are done
                     {
-                        const int yi = min(j0 + lane, cols - 1) >> lam;
-                        const V* yr = reinterpret_cast<const V*>(ybase + static_cast<int64_t>(yi) * dpad + c0);
-                        V* yd = reinterpret_cast<V*>(ys + lane * C);
+                        const int xi = min((s << 5) + lane, rows - 1) >> lam;
+                        const V* xr = reinterpret_cast<const V*>(xbase + static_cast<int64_t>(xi) * dpad + c0);
+                        V* xd = reinterpret_cast<V*>(xs + lane * C);
 #pragma unroll
                         for (int k = 0; k < C / W; ++k) {
                             V v = {};
-                            if (lane < nc && c0 + k * W < dpad) v = __ldg(yr + k);
-                            yd[k] = v;
+                            if (lane < nr && c0 + k * W < dpad) v = __ldg(xr + k);
+                            xd[k] = v;
                         }
                     }
-                    __syncwarp();
-                    ContractAcc<T> ya;
-                    ya.zero();
-                    const int coff = (t0 + j0) & 31;
-                    if (nr == 32 && nc == 32) contract_tile<T, true>(ring, s0 * 32, coff, xs, ys, nr, nc, lane, xa, ya);
-                    else contract_tile<T, false>(ring, s0 * 32, coff, xs, ys, nr, nc, lane, xa, ya);
-                    if (lane < nc) {
-                        const int yi = (j0 + lane) >> lam;
+                    ContractAcc<T, C> xa;
+                    xa.zero();
+                    for (int b = 0; b < ntiles; ++b) {
+                        // half b (slot b % 3) was awaited as the upper half of tile b - 1, except for b = 0
+                        const int s0 = b % 3, s1 = (b + 1) % 3;
+                        if (b == 0 && !await_slot(s0)) { stuck = true; break; }
+                        if (!await_slot(s1)) { stuck = true; break; }
+                        const int j0 = w0 + (b << 5);
+                        const int nc = min(32, cols - j0);  // valid columns of the tile
+                        __syncwarp();  // the previous tile's readers of ys are done
+                        {
+                            const int yi = min(j0 + lane, cols - 1) >> lam;
+                            const V* yr = reinterpret_cast<const V*>(ybase + static_cast<int64_t>(yi) * dpad + c0);
+                            V* yd = reinterpret_cast<V*>(ys + lane * C);
 #pragma unroll
-                        for (int c = 0; c < C; ++c) {
-                            const T v = ya.get(c);
-                            if (c0 + c < dpad && v != T(0)) {
-                                if (use_smem) atomicAdd(acc + c * nrow + P.lx + yi, v);
-                                else atomicAdd(gy + static_cast<int64_t>(yi) * dpad + c0 + c, static_cast<double>(v) * gscale);
+                            for (int k = 0; k < C / W; ++k) {
+                                V v = {};
+                                if (lane < nc && c0 + k * W < dpad) v = __ldg(yr + k);
+                                yd[k] = v;
                             }
                         }
-                    }
-                    __syncwarp();  // slot s0 is read by every lane: refill it with half b + 3
-                    if (b + 3 <= ntiles) {
-                        if (lane == 0) {
-                            mbar_arrive_expect_tx(bars + s0, HB);
-                            bulk_load(ring + s0 * 1024, mb + static_cast<int64_t>(t0 + 32 * (b + 3)) * 32 * sizeof(T),
-                                      HB, bars + s0);
-                        }
-                        pending |= 1u << s0;
-                    }
-                }
-                if (lane < nr) {
-                    const int xi = ((s << 5) + lane) >> lam;
+                        __syncwarp();
+                        ContractAcc<T, C> ya;
+                        ya.zero();
+                        const int coff = (s * period + j0) & 31;
+                        if (nr == 32 && nc == 32) contract_tile<T, C, true>(ring, s0 * 32, coff, xs, ys, nr, nc, lane, xa, ya);
+                        else contract_tile<T, C, false>(ring, s0 * 32, coff, xs, ys, nr, nc, lane, xa, ya);
+                        if (lane < nc) {
+                            const int yi = ((j0 + lane) >> lam) - ya0;
 #pragma unroll
-                    for (int c = 0; c < C; ++c) {
-                        const T v = xa.get(c);
-                        if (c0 + c < dpad && v != T(0)) {
-                            if (use_smem) atomicAdd(acc + c * nrow + xi, v);
-                            else atomicAdd(gx + static_cast<int64_t>(xi) * dpad + c0 + c, static_cast<double>(v) * gscale);
+                            for (int c = 0; c < C; ++c) {
+                                const T v = ya.get(c);
+                                if (c0 + c < dpad && v != T(0)) atomicAdd(acc + c * nya + yi, v);
+                            }
+                        }
+                        __syncwarp();  // slot s0 is read by every lane: refill it with half b + 3
+                        if (b + 3 <= ntiles) {
+                            if (lane == 0) {
+                                mbar_arrive_expect_tx(bars + s0, HB);
+                                bulk_load(ring + s0 * 1024, mb + static_cast<int64_t>(t0 + 32 * (b + 3)) * 32 * sizeof(T),
+                                          HB, bars + s0);
+                            }
+                            pending |= 1u << s0;
+                        }
+                    }
+                    if (lane < nr) {  // this strip's rows are its own: straight to the gradients
+                        const int xi = ((s << 5) + lane) >> lam;
+#pragma unroll
+                        for (int c = 0; c < C; ++c) {
+                            const T v = xa.get(c);
+                            if (c0 + c < dpad && v != T(0))
+                                atomicAdd(gx + static_cast<int64_t>(xi) * dpad + c0 + c, static_cast<double>(v) * gscale);
                         }
                     }
                 }
-            }
-            if (use_smem) {
                 __syncthreads();
-                for (int q = threadIdx.x; q < nacc; q += blockDim.x) {
-                    const int c = q / nrow, r = q - c * nrow;
+                for (int q = threadIdx.x; q < C * nya; q += blockDim.x) {
+                    const int c = q / nya, r = q - c * nya;
                     if (c0 + c >= dpad || acc[q] == T(0)) continue;
-                    double* g = r < P.lx ? gx + static_cast<int64_t>(r) * dpad : gy + static_cast<int64_t>(r - P.lx) * dpad;
-                    atomicAdd(g + c0 + c, static_cast<double>(acc[q]) * gscale);
+                    atomicAdd(gy + static_cast<int64_t>(ya0 + r) * dpad + c0 + c, static_cast<double>(acc[q]) * gscale);
                 }
                 __syncthreads();
             }

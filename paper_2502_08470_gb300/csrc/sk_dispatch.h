@@ -79,8 +79,9 @@ const void* bwd_tape_interp_ptr_f32(int N);
 const void* bwd_tape_interp_ptr_f64(int N);
 const void* bwd_tape_interp_ptr_f64_0(int N);
 const void* bwd_tape_interp_ptr_f64_1(int N);
-const void* bwd_contract_ptr_f32();
-const void* bwd_contract_ptr_f64();
+// C: coordinates per contraction pass (8, 16 or 32)
+const void* bwd_contract_ptr_f32(int C);
+const void* bwd_contract_ptr_f64(int C);
 }  // namespace sk
 
 namespace sk {

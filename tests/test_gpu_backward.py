@@ -277,7 +277,7 @@ def test_tape_backward_pairs_dyadic_and_rescaled():
 
 @pytest.mark.parametrize("compute,tol", [("f64", 1e-9), ("f32", 1e-4)])
 def test_tape_backward_wide_d_matches_oracle(compute, tol):
-    """d = 37: the contraction takes coordinates eight at a time, the last chunk partial."""
+    """d = 37 (40 padded): the contraction takes coordinates 32 at a time, the second pass partial."""
     X = W.brownian(2, 17, 37, seed=78)
     Y = W.brownian(2, 15, 37, seed=79)
     Wt = np.array([[0.7, -1.3], [0.4, 2.1]])
@@ -306,6 +306,23 @@ def test_tape_backward_long_paths_match_checkpoint_adjoint(compute, tol):
     torch.cuda.synchronize()
     assert sk.device_status() == 0
     assert np.all(np.isfinite(gX.cpu().numpy()))
+    assert _scaled_err(gX.cpu().numpy(), cX.cpu().numpy()) < tol
+    assert _scaled_err(gY.cpu().numpy(), cY.cpu().numpy()) < tol
+
+
+@pytest.mark.parametrize("compute,tol", [("f64", 1e-12), ("f32", 1e-5)])
+def test_tape_backward_column_windows_match_checkpoint_adjoint(compute, tol):
+    """d = 12 (16 coordinates per contraction pass) and 300-point paths at lambda = 1 (598 refined
+    columns): the contraction sweeps its column accumulator over 2 (FP32) or 3 (FP64) windows
+    whose edges split coarse increments' sub-columns.  The checkpointing adjoint is the reference."""
+    X = W.brownian(2, 300, 12, seed=82)
+    Y = W.brownian(2, 300, 12, seed=83)
+    Wt = _cuda([[0.9, -0.4], [1.3, 0.2]])
+    G, tape = sk.sigkernel_forward_tape(_cuda(X), _cuda(Y), degree=5, dyadic=1, compute=compute)
+    gX, gY = sk.sigkernel_backward_tape(tape, Wt, _cuda(X), _cuda(Y), degree=5, dyadic=1, compute=compute)
+    cX, cY = sk.sigkernel_backward(Wt, _cuda(X), _cuda(Y), degree=5, dyadic=1, compute=compute)
+    torch.cuda.synchronize()
+    assert sk.device_status() == 0
     assert _scaled_err(gX.cpu().numpy(), cX.cpu().numpy()) < tol
     assert _scaled_err(gY.cpu().numpy(), cY.cpu().numpy()) < tol
 
