@@ -717,13 +717,21 @@ int plan_backward_tape(const sk_paths* X, const sk_paths* Y, int32_t d, int32_t 
     // (plus the rows past an item's last step that the contraction's tiles may read)
     b.mb_stride = static_cast<int64_t>(align256(static_cast<size_t>(b.t.nsteps + kContractSlack) * 32 * esize));
     // contraction: per-warp rings and staged rows, then the block's column accumulator
-    int cwarp = 0;
-    if (p.T) cwarp = b.cC == 8 ? contract_warp_bytes<float, 8>() : b.cC == 16 ? contract_warp_bytes<float, 16>()
-                                                                        : contract_warp_bytes<float, 32>();
-    else cwarp = b.cC == 8 ? contract_warp_bytes<double, 8>() : b.cC == 16 ? contract_warp_bytes<double, 16>()
-                                                                      : contract_warp_bytes<double, 32>();
-    b.acc_bytes = kContractAccBytes;
-    b.csmem = kContractWarps * cwarp + kContractAccBytes;
+    int cwarp = 0, cwin = 0;
+    if (p.T) {
+        cwarp = b.cC == 8 ? contract_warp_bytes<float, 8>() : b.cC == 16 ? contract_warp_bytes<float, 16>()
+                                                                : contract_warp_bytes<float, 32>();
+        cwin = b.cC == 8 ? contract_window<float, 8>() : b.cC == 16 ? contract_window<float, 16>()
+                                                            : contract_window<float, 32>();
+    } else {
+        cwarp = b.cC == 8 ? contract_warp_bytes<double, 8>() : b.cC == 16 ? contract_warp_bytes<double, 16>()
+                                                                 : contract_warp_bytes<double, 32>();
+        cwin = b.cC == 8 ? contract_window<double, 8>() : b.cC == 16 ? contract_window<double, 16>()
+                                                             : contract_window<double, 32>();
+    }
+    // the accumulator holds a window of at most cwin columns (fewer when the paths are shorter)
+    b.acc_bytes = static_cast<int64_t>(b.cC) * esize * std::min<int64_t>(cwin, b.cols_max);
+    b.csmem = kContractWarps * cwarp + static_cast<int>(b.acc_bytes);
     int dev = 0, sms = 0, per_sm = 0, cper_sm = 0;
     SK_CUDA(cudaGetDevice(&dev));
     SK_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
