@@ -488,7 +488,8 @@ def main():
         cells_o = 64 * 1024 * 1024
         osc = {"workload": "64 pairs, 1025 points on [0,1], d=4, sin(w t + phi) + N(0,1e-3), w ~ U(10,200)"}
         for scheme, N, lam, comp in (("interp", 8, 0, "f32"), ("interp", 8, 0, "f64"), ("fd1", 2, 0, "f32"),
-                                     ("fd1", 2, 2, "f32"), ("fd1", 2, 4, "f32"), ("fd1", 2, 6, "f32")):
+                                     ("fd1", 2, 2, "f32"), ("fd1", 2, 4, "f32"), ("fd1", 2, 6, "f32"),
+                                     ("fd2", 2, 4, "f32"), ("fd_implicit", 2, 4, "f32")):
             o = torch.empty(64, dtype=torch.float64, device=dev)
             f = lambda: sk.sigkernel_pairs(Xo, Yo, io, io, scheme=scheme, degree=N, dyadic=lam, compute=comp, out=o)
             t = timed_steps(f, 1 if lam == 6 else 3, 1)
