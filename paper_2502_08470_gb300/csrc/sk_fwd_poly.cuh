@@ -205,6 +205,12 @@ constexpr int kCoopWarps = 16;
 
 template <typename T, int N, int NE, bool MT = false>
 constexpr int fwd_poly_coop_min_blocks() {
+    // Two 16-warp blocks per SM (64 registers) measured faster for the approximation scheme up to
+    // order 6 in FP32, despite a few spilled registers: 4096 pairs of 64..4096-point paths ran in
+    // 83.7 ms against 101.4 ms.  The interpolation scheme's longer series spill more, and it ran
+    // slower that way (64 pairs of 1025-point oscillatory paths: 5.47 against 4.76 ms), so it
+    // keeps one block.
+    if constexpr (std::is_same<T, float>::value && NE == N && N <= 6 && !MT) return 2;
     constexpr int b = fwd_poly_min_blocks<T, N, NE, MT>() * kFwdWarps / kCoopWarps;
     return b < 1 ? 1 : b;
 }
