@@ -173,8 +173,12 @@ __device__ __forceinline__ void sweep_fd(const Launch& L, int64_t item, const Pa
     }
 }
 
+// One-warp blocks are compiled for 8 blocks per SM (64 registers, no spills): FD Grams of
+// 128 x 128 pairs of 257-point paths ran 2.1x faster than at the 180-200 registers the
+// unconstrained build took (2 blocks per SM).  The pipelined blocks keep their budget: capped at
+// two blocks per SM they ran slower (64 oscillatory pairs at lambda = 4: 30.1 against 22.1 ms).
 template <typename T, int ORDER, int R, int CW>
-__global__ void __launch_bounds__((CW > 1 ? CW : kFwdWarps) * 32) fwd_fd_kernel(Launch L, int64_t buf_cols) {
+__global__ void __launch_bounds__((CW > 1 ? CW : kFwdWarps) * 32, (CW > 1 ? 1 : 8)) fwd_fd_kernel(Launch L, int64_t buf_cols) {
     const int wib = threadIdx.x >> 5;
     const int nw = blockDim.x >> 5;
     char* block_base = static_cast<char*>(L.scratch) + static_cast<int64_t>(blockIdx.x) * nw * L.scratch_stride;
