@@ -145,6 +145,8 @@ struct Plan {
     int blocks;          // persistent grid
     bool coop;           // cooperative-block kernel (strip pipeline for long pairs)
     int coop_min_strips; // strips from which a pair is swept by a whole block
+    int grid_bpp;        // grid strip pipeline: blocks sharing each pair (0 = off)
+    size_t off_gprog;    // its progress words [npairs][grid_bpp x kCoopWarps]
     bool mtile;          // tiled M (wide increments, polynomial schemes)
     int64_t mtile_cols;  // columns of one warp's M strip buffer
     int64_t mtile_off;   // byte offset of that buffer in a warp slot
@@ -265,6 +267,7 @@ int plan_forward(const sk_paths* X, const sk_paths* Y, int32_t d, int32_t dtype,
     p.threads = (wpb_req ? wpb_req : kFwdWarps) * 32;
     p.coop = false;
     p.coop_min_strips = 0;
+    p.grid_bpp = 0;
     const int esize = p.T ? 4 : 8;
     p.smem_x = 0;
     auto xsmem = [&](int threads) { return p.mtile ? (threads / 32) * 32 * p.dpad * esize : 0; };
@@ -304,11 +307,19 @@ int plan_forward(const sk_paths* X, const sk_paths* Y, int32_t d, int32_t dtype,
                 p.coop_min_strips = 2;
                 p.threads = kCoopWarps * 32;
                 per_sm = cper;
+                // Few long pairs: one block per pair would leave SMs idle, so each pair's ring of
+                // warps spans several co-resident blocks (at least two per pair, no more than its
+                // strips can use).
+                const int64_t rblocks = static_cast<int64_t>(sms) * cper;
+                if (poly && npairs > 0 && 2 * npairs <= rblocks && max_strips >= 2 * kCoopWarps) {
+                    const int64_t bpp = std::min<int64_t>(rblocks / npairs, (max_strips + kCoopWarps - 1) / kCoopWarps);
+                    if (bpp >= 2) p.grid_bpp = static_cast<int>(bpp);
+                }
             }
         }
     }
     const int wpb = p.threads / 32;
-    int64_t want = p.coop ? npairs : (npairs + wpb - 1) / wpb;
+    int64_t want = p.coop ? (p.grid_bpp > 0 ? npairs * p.grid_bpp : npairs) : (npairs + wpb - 1) / wpb;
     int64_t cap = static_cast<int64_t>(sms) * per_sm;
     p.blocks = static_cast<int>(want < cap ? (want > 0 ? want : 1) : cap);
     p.buf_cols = (Y->max_len << lam) + 1;
@@ -331,6 +342,8 @@ int plan_forward(const sk_paths* X, const sk_paths* Y, int32_t d, int32_t dtype,
     off += align256(static_cast<size_t>(npairs) * sizeof(int32_t));
     p.off_scratch = off;
     off += static_cast<size_t>(p.blocks) * wpb * static_cast<size_t>(p.slot_bytes);
+    p.off_gprog = off;
+    if (p.grid_bpp > 0) off += align256(static_cast<size_t>(p.blocks) * wpb * sizeof(int));
     p.total = off + 256;
     return SK_OK;
 }
@@ -438,6 +451,9 @@ int run_forward(const sk_paths* X, const sk_paths* Y, int32_t d, int32_t dtype, 
     L.tape_stride = static_cast<int64_t>(tp.stride);
     L.tape_ek = tape ? static_cast<int*>(tape) : nullptr;
     L.coop_min_strips = p.coop_min_strips;
+    L.grid_bpp = p.grid_bpp;
+    L.gprog = p.grid_bpp > 0 ? reinterpret_cast<int*>(base + p.off_gprog) : nullptr;
+    if (p.grid_bpp > 0) SK_CUDA(cudaMemsetAsync(L.gprog, 0, static_cast<size_t>(p.blocks) * (p.threads / 32) * sizeof(int), st));
     L.mtile = p.mtile ? 1 : 0;
     L.mtile_cols = static_cast<int32_t>(p.mtile_cols);
     L.mtile_off = p.mtile_off;
@@ -463,7 +479,22 @@ int run_forward(const sk_paths* X, const sk_paths* Y, int32_t d, int32_t dtype, 
         if (!t_ev1) SK_CUDA(cudaEventCreate(&t_ev1));
         SK_CUDA(cudaEventRecord(t_ev0, st));
     }
-    SK_CUDA(cudaLaunchKernel(p.kern, dim3(p.blocks), dim3(p.threads), args, smem, st));
+    if (p.grid_bpp > 0) {
+        // the blocks of a pair wait on one another: launch them co-resident
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(p.blocks);
+        cfg.blockDim = dim3(p.threads);
+        cfg.dynamicSmemBytes = static_cast<size_t>(smem);
+        cfg.stream = st;
+        cudaLaunchAttribute attr;
+        attr.id = cudaLaunchAttributeCooperative;
+        attr.val.cooperative = 1;
+        cfg.attrs = &attr;
+        cfg.numAttrs = 1;
+        SK_CUDA(cudaLaunchKernelExC(&cfg, p.kern, args));
+    } else {
+        SK_CUDA(cudaLaunchKernel(p.kern, dim3(p.blocks), dim3(p.threads), args, smem, st));
+    }
     if (timed) {
         SK_CUDA(cudaEventRecord(t_ev1, st));
         t_timed = true;

@@ -146,6 +146,12 @@ struct Launch {
     // Gram modes: work item k of this launch is item k + item_base of the whole Gram (a call can
     // sweep a sub-range of a Gram's items; its tape and queue are indexed by k).
     int64_t item_base;
+    // Grid strip pipeline (few long pairs): when nonzero, grid_bpp blocks of the pipelined kernel
+    // share each work item, all launched co-resident; block b takes slot b / grid_bpp of the queue
+    // order and is part b % grid_bpp of that item's ring of grid_bpp x CW warps.  The ring's
+    // progress words are gprog[slot][grid_bpp x CW] in global memory (zeroed before the launch).
+    int32_t grid_bpp;
+    int* gprog;
 };
 
 // Width, in elements of T, of one lane's tape row: a[0..N], b[0..N], the exponent (element
@@ -248,6 +254,24 @@ __device__ __forceinline__ int acquire_progress(const int* p) {
 __device__ __forceinline__ bool wait_progress(const int* p, int need) {
     for (uint32_t it = 0; it < kSpinLimit; ++it) {
         if (acquire_progress(p) >= need) return true;
+        __nanosleep(64);
+    }
+    record_error(SK_ERR_DEVICE_TIMEOUT);
+    return false;
+}
+
+// The same progress words in global memory, ordered at GPU scope, for a ring that spans blocks
+// (grid strip pipeline).  The release orders the hand-off entries stored before it; the acquire
+// orders the entry loads after it.
+__device__ __forceinline__ void publish_progress_gpu(int* p, int v) {
+    asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ bool wait_progress_gpu(const int* p, int need) {
+    for (uint32_t it = 0; it < kSpinLimit; ++it) {
+        int v;
+        asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+        if (v >= need) return true;
         __nanosleep(64);
     }
     record_error(SK_ERR_DEVICE_TIMEOUT);

@@ -224,9 +224,14 @@ constexpr int fwd_poly_coop_min_blocks() {
 // wait_progress); a buffer entry of strip g is overwritten by strip g + CW only after strip
 // g + 1 has consumed it, because strip g + CW depends on strip g + 1 through the chain of
 // strips in between.
-template <typename T, int N, int NE, bool INTERP, int CW, bool MT>
+//
+// The ring of warps is CW warps of one block (progress words in shared memory), or, with GS, ring
+// warps spread over co-resident blocks (progress words in global memory, GPU-scope ordering);
+// ring is the ring's width (CW, or blocks x CW with GS).
+template <typename T, int N, int NE, bool INTERP, int CW, bool MT, bool GS = false>
 __device__ __forceinline__ void sweep_poly(const Launch& L, int64_t item, const PairDesc& P, int w, char* own_buf,
-                                           const char* prev_buf, int* prog, int64_t buf_cols, T* xstage) {
+                                           const char* prev_buf, int* prog, int64_t buf_cols, T* xstage,
+                                           int ring = CW) {
     constexpr bool kRescale = std::is_same<T, float>::value;
     using V = typename Vec<T>::type;
     constexpr int W = Vec<T>::W;
@@ -250,13 +255,13 @@ __device__ __forceinline__ void sweep_poly(const Launch& L, int64_t item, const 
     // strip k (P = cols + 31), unless the rows are longer than the ring's lag (cols > 31 CW),
     // where the overlapped schedule keeps every wait pointed at finished work.  A model of this
     // schedule (tests/test_pipeline_schedule.py) checks the rule and the deadlock it avoids.
-    const int period = CW == 1 ? (cols > 32 ? cols : 32) : (cols > 31 * CW ? cols : cols + 31);
+    const int period = CW == 1 ? (cols > 32 ? cols : 32) : (cols > 31 * ring ? cols : cols + 31);
     const int nstrips = (rows + 31) >> 5;
     const int last_lane = (rows - 1) - ((nstrips - 1) << 5);
-    // this warp's strips: w, w + CW, ...; the one holding the last row ends at lane last_lane
-    const int nloc = w < nstrips ? (nstrips - 1 - w) / CW + 1 : 0;
+    // this warp's strips: w, w + ring, ...; the one holding the last row ends at lane last_lane
+    const int nloc = w < nstrips ? (nstrips - 1 - w) / ring + 1 : 0;
     if (nloc == 0) return;
-    const bool has_last = (nstrips - 1) % CW == w;
+    const bool has_last = (nstrips - 1) % ring == w;
     const int nsteps = (nloc - 1) * period + (has_last ? last_lane : 31) + cols;
     const T sub = pow2t<T>(-2 * lam);  // M of a sub-cell of P_lambda is M_ij / 4^lambda
     const T* xbase = incX + P.xs * dpad;
@@ -278,7 +283,7 @@ __device__ __forceinline__ void sweep_poly(const Launch& L, int64_t item, const 
     for (int step = 0; step < nsteps; ++step) {
         if constexpr (MT) {
             if (jj0 == 0 && sl0 < nloc)  // lane 0 enters local strip sl0: build its M first
-                produce_m_strip<T>(xbase, ybase, dpad, lam, rows, cols, w + sl0 * CW, sub, xstage,
+                produce_m_strip<T>(xbase, ybase, dpad, lam, rows, cols, w + sl0 * ring, sub, xstage,
                                    mbuf + (sl0 & 1) * 32 * static_cast<int64_t>(mcols), mcols);
             if (++jj0 == period) {
                 jj0 = 0;
@@ -297,7 +302,12 @@ __device__ __forceinline__ void sweep_poly(const Launch& L, int64_t item, const 
                 eb = 0;
             } else {
                 if constexpr (CW > 1) {
-                    if (!stuck && !wait_progress(prog + (w + CW - 1) % CW, (g - 1) * cols + jj + 1)) stuck = true;
+                    const int* pp = prog + (w + ring - 1) % ring;
+                    if constexpr (GS) {
+                        if (!stuck && !wait_progress_gpu(pp, (g - 1) * cols + jj + 1)) stuck = true;
+                    } else {
+                        if (!stuck && !wait_progress(pp, (g - 1) * cols + jj + 1)) stuck = true;
+                    }
                 }
                 const V* src = hprev + static_cast<int64_t>(jj) * (NB / W);
 #pragma unroll
@@ -410,14 +420,17 @@ __device__ __forceinline__ void sweep_poly(const Launch& L, int64_t item, const 
                 dst[v] = t;
             }
             if (kRescale) ebuf[jj] = eo;
-            if constexpr (CW > 1) publish_progress(prog + w, g * cols + jj + 1);
+            if constexpr (CW > 1) {
+                if constexpr (GS) publish_progress_gpu(prog + w, g * cols + jj + 1);
+                else publish_progress(prog + w, g * cols + jj + 1);
+            }
         }
         __syncwarp();
         if (++jj == period) {
             jj = 0;
             ++sl;
-            g += CW;
-            row += 32 * CW;
+            g += ring;
+            row += 32 * ring;
             xrow = xbase + static_cast<int64_t>(min(row, rows - 1) >> lam) * dpad;
         }
     }
@@ -473,6 +486,23 @@ __global__ void __launch_bounds__((CW > 1 ? CW : kFwdWarps) * 32,
     T* xstage = reinterpret_cast<T*>(fwd_smem) + wib * 32 * L.dpad;
 
     if constexpr (CW > 1) {
+        if (L.grid_bpp > 0) {  // grid strip pipeline: this block is part k of its slot's ring
+            const int bpp = L.grid_bpp;
+            const int64_t slot = blockIdx.x / bpp;
+            const int k = static_cast<int>(blockIdx.x - slot * bpp);
+            if (slot >= L.npairs) return;
+            const int64_t item = L.order ? static_cast<int64_t>(L.order[slot]) : slot;
+            const PairDesc P = decode_pair(L, item);
+            if (trivial_pair(L, item, P)) return;
+            const int ring = bpp * CW;
+            const int wr = k * CW + wib;                 // this warp's place in the ring
+            const int pw = (wr + ring - 1) % ring;       // the warp before it
+            const char* prev = static_cast<char*>(L.scratch) +
+                               ((slot * bpp + pw / CW) * nw + pw % CW) * L.scratch_stride;
+            sweep_poly<T, N, NE, INTERP, CW, MT, true>(L, item, P, wr, own, prev, L.gprog + slot * ring, buf_cols,
+                                                       xstage, ring);
+            return;
+        }
         __shared__ long long s_item;
         __shared__ int s_prog[CW];
         for (;;) {

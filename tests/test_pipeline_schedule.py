@@ -69,3 +69,12 @@ def test_plain_overlap_deadlocks_on_short_rows():
     assert not schedule_completes(3 * 32 - 5, 2, 2, 32)
     assert not schedule_completes(9 * 32 - 5, 200, 8, 200)   # cols <= 31 W
     assert schedule_completes(9 * 32 - 5, 260, 8, 260)       # cols > 31 W
+
+
+@pytest.mark.parametrize("W", [16, 32, 64])
+def test_kernel_period_rule_on_wide_rings(W):
+    """Rings as the kernels build them: one block of 16 warps, and rings of 2 or 4 such blocks
+    (the grid strip pipeline for few long pairs)."""
+    for cols in (1, 31, 33, 31 * W - 1, 31 * W, 31 * W + 1, 1024):
+        for nst in (W - 1, W + 1, 2 * W + 3):
+            assert schedule_completes(nst * 32 - 5, cols, W, kernel_period(cols, W)), (W, cols, nst)
