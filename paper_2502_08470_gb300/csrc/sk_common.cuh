@@ -267,16 +267,25 @@ __device__ __forceinline__ void publish_progress_gpu(int* p, int v) {
     asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
-__device__ __forceinline__ bool wait_progress_gpu(const int* p, int need) {
+// Bounded wait for *p >= need; *seen gets the value observed (the caller may then read every
+// entry up to it without another acquire).  False (and the device error word set) when it runs out.
+__device__ __forceinline__ bool wait_progress_gpu(const int* p, int need, int* seen) {
     for (uint32_t it = 0; it < kSpinLimit; ++it) {
         int v;
         asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-        if (v >= need) return true;
+        if (v >= need) {
+            *seen = v;
+            return true;
+        }
         __nanosleep(64);
     }
     record_error(SK_ERR_DEVICE_TIMEOUT);
     return false;
 }
+
+// Columns a ring spanning blocks publishes at once: a GPU-scope release every step stalls the
+// publishing lane (and so its warp) far longer than the step itself.
+constexpr int kGridPublish = 8;
 
 // Pop the next work item for a warp (lane 0 takes it, all lanes receive it).
 __device__ __forceinline__ int64_t next_item(const Launch& L) {

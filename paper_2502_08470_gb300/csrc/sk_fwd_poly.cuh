@@ -255,7 +255,10 @@ __device__ __forceinline__ void sweep_poly(const Launch& L, int64_t item, const 
     // strip k (P = cols + 31), unless the rows are longer than the ring's lag (cols > 31 CW),
     // where the overlapped schedule keeps every wait pointed at finished work.  A model of this
     // schedule (tests/test_pipeline_schedule.py) checks the rule and the deadlock it avoids.
-    const int period = CW == 1 ? (cols > 32 ? cols : 32) : (cols > 31 * ring ? cols : cols + 31);
+    // A ring spanning blocks publishes its progress every kGridPublish columns, which lengthens
+    // the lag the overlapped schedule must exceed (the schedule model checks this rule too).
+    constexpr int kLag = GS ? 31 + kGridPublish : 31;
+    const int period = CW == 1 ? (cols > 32 ? cols : 32) : (cols > kLag * ring ? cols : cols + 31);
     const int nstrips = (rows + 31) >> 5;
     const int last_lane = (rows - 1) - ((nstrips - 1) << 5);
     // this warp's strips: w, w + ring, ...; the one holding the last row ends at lane last_lane
@@ -274,6 +277,7 @@ __device__ __forceinline__ void sweep_poly(const Launch& L, int64_t item, const 
     int jj = -lane, sl = 0;                 // column and local strip of this lane
     int g = w, row = (w << 5) + lane;       // global strip and grid row
     bool stuck = false;                     // a hand-off wait ran out (CW > 1 only)
+    int seen = 0;                           // progress of the warp before, as last observed (GS)
     const T* xrow = xbase + static_cast<int64_t>(min(row, rows - 1) >> lam) * dpad;
     // tiled M (MT): this warp's [2][32][mcols] strip buffers; lane 0's column and local strip
     const int mcols = MT ? L.mtile_cols : 0;
@@ -304,7 +308,8 @@ __device__ __forceinline__ void sweep_poly(const Launch& L, int64_t item, const 
                 if constexpr (CW > 1) {
                     const int* pp = prog + (w + ring - 1) % ring;
                     if constexpr (GS) {
-                        if (!stuck && !wait_progress_gpu(pp, (g - 1) * cols + jj + 1)) stuck = true;
+                        const int need = (g - 1) * cols + jj + 1;
+                        if (!stuck && seen < need && !wait_progress_gpu(pp, need, &seen)) stuck = true;
                     } else {
                         if (!stuck && !wait_progress(pp, (g - 1) * cols + jj + 1)) stuck = true;
                     }
@@ -421,8 +426,11 @@ __device__ __forceinline__ void sweep_poly(const Launch& L, int64_t item, const 
             }
             if (kRescale) ebuf[jj] = eo;
             if constexpr (CW > 1) {
-                if constexpr (GS) publish_progress_gpu(prog + w, g * cols + jj + 1);
-                else publish_progress(prog + w, g * cols + jj + 1);
+                if constexpr (GS) {
+                    if ((jj + 1) % kGridPublish == 0 || jj == cols - 1) publish_progress_gpu(prog + w, g * cols + jj + 1);
+                } else {
+                    publish_progress(prog + w, g * cols + jj + 1);
+                }
             }
         }
         __syncwarp();

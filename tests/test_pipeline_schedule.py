@@ -13,7 +13,7 @@ show that plain overlap (P = max(cols, 32)) can deadlock when rows are short.
 import pytest
 
 
-def schedule_completes(rows, cols, W, P):
+def schedule_completes(rows, cols, W, P, K=1):
     nstrips = (rows + 31) // 32
     last_lane = rows - 1 - 32 * (nstrips - 1)
     done = [0] * nstrips
@@ -44,8 +44,8 @@ def schedule_completes(rows, cols, W, P):
             if c0 and c0[0] > 0 and done[c0[0] - 1] < c0[1] + 1:
                 continue
             c31 = cell(w, nloc, tau, 31)
-            if c31 and c31[0] + 1 < nstrips:
-                done[c31[0]] = c31[1] + 1
+            if c31 and c31[0] + 1 < nstrips and ((c31[1] + 1) % K == 0 or c31[1] + 1 == cols):
+                done[c31[0]] = c31[1] + 1  # published every K columns and at the row's end
             st[3] += 1
             moved = True
     return all(st[3] >= st[2] for st in warps)
@@ -78,3 +78,18 @@ def test_kernel_period_rule_on_wide_rings(W):
     for cols in (1, 31, 33, 31 * W - 1, 31 * W, 31 * W + 1, 1024):
         for nst in (W - 1, W + 1, 2 * W + 3):
             assert schedule_completes(nst * 32 - 5, cols, W, kernel_period(cols, W)), (W, cols, nst)
+
+
+@pytest.mark.parametrize("W", [32, 64])
+def test_batched_publishing_needs_the_longer_lag(W):
+    """Rings that span blocks publish their progress every 8 columns.  The overlapped schedule is
+    then safe only above cols > (31 + 8) W: just above 31 W it deadlocks."""
+    K = 8
+
+    def grid_period(cols):
+        return max(cols if cols > (31 + K) * W else cols + 31, 32)
+
+    for cols in (1, 8, 9, 33, 31 * W + 1, 31 * W + 32, (31 + K) * W, (31 + K) * W + 1, 4000):
+        for nst in (W - 1, W + 1, 2 * W + 3):
+            assert schedule_completes(nst * 32 - 5, cols, W, grid_period(cols), K), (cols, nst)
+    assert not schedule_completes((W + 1) * 32 - 5, 31 * W + 32, W, 31 * W + 32, K)
