@@ -159,6 +159,8 @@ struct Plan {
 
 size_t align256(size_t v) { return (v + 255) / 256 * 256; }
 
+constexpr int kGridMinBlocks = 8;  // fewest blocks a pair's ring may span in the grid strip pipeline
+
 int check_paths(const sk_paths* P, const char* name, int d) {
     if (!P) return fail(SK_ERR_INVALID_ARG, "%s is NULL", name);
     if (P->count < 0) return fail(SK_ERR_INVALID_ARG, "%s->count < 0", name);
@@ -308,12 +310,15 @@ int plan_forward(const sk_paths* X, const sk_paths* Y, int32_t d, int32_t dtype,
                 p.threads = kCoopWarps * 32;
                 per_sm = cper;
                 // Few long pairs: one block per pair would leave SMs idle, so each pair's ring of
-                // warps spans several co-resident blocks (at least two per pair, no more than its
-                // strips can use).
+                // warps spans several co-resident blocks (no more than its strips can use).  A
+                // step costs several times more there (GPU-scope hand-off), so the ring must
+                // spread over at least kGridMinBlocks blocks: 1 pair of 16385-point paths ran
+                // 5.5x faster, 8 pairs of 4097 points 1.4x, but 32 pairs of 2049 points (4 blocks
+                // each) 1.6x slower and 64 pairs of 1025 points (2 each) 2.8x slower.
                 const int64_t rblocks = static_cast<int64_t>(sms) * cper;
-                if (poly && npairs > 0 && 2 * npairs <= rblocks && max_strips >= 2 * kCoopWarps) {
+                if (poly && npairs > 0 && max_strips >= kGridMinBlocks * kCoopWarps) {
                     const int64_t bpp = std::min<int64_t>(rblocks / npairs, (max_strips + kCoopWarps - 1) / kCoopWarps);
-                    if (bpp >= 2) p.grid_bpp = static_cast<int>(bpp);
+                    if (bpp >= kGridMinBlocks) p.grid_bpp = static_cast<int>(bpp);
                 }
             }
         }

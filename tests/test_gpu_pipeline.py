@@ -135,3 +135,28 @@ def test_grid_pipeline_spreads_few_long_pairs_over_blocks(compute):
     tol = 1e-4 if compute == "f32" else 1e-11
     assert abs(auto[1].item() - ref) <= tol * abs(ref)
     assert t_auto < t_one / 4
+
+
+def test_grid_pipeline_captures_into_a_cuda_graph():
+    """One pair of 4097-point paths (a ring of eight 16-warp blocks, launched co-resident) replayed
+    from a CUDA graph on new inputs written into the same buffers."""
+    X = torch.tensor(W.brownian(1, 4097, 3, seed=161), device="cuda")
+    Y = torch.tensor(W.brownian(1, 4097, 3, seed=162), device="cuda")
+    idx = torch.zeros(1, dtype=torch.int64, device="cuda")
+    out = torch.empty(1, dtype=torch.float64, device="cuda")
+    sk.sigkernel_pairs(X, Y, idx, idx, compute="f32", out=out)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        with torch.cuda.graph(g, stream=s):
+            sk.sigkernel_pairs(X, Y, idx, idx, compute="f32", out=out)
+    torch.cuda.synchronize()
+    X.copy_(torch.tensor(W.brownian(1, 4097, 3, seed=163), device="cuda"))
+    out.fill_(float("nan"))
+    g.replay()
+    torch.cuda.synchronize()
+    ref = sk.sigkernel_pairs(X, Y, idx, idx, compute="f32", strip_pipeline=False)
+    torch.cuda.synchronize()
+    assert sk.device_status() == 0
+    assert torch.equal(out, ref)
