@@ -39,7 +39,7 @@ D = 8
 DEGREE = 6
 CELLS_PER_PAIR = (L - 1) * (L - 1)
 CELLS = NX * NY * CELLS_PER_PAIR
-PARTS = ("f32", "ckpt", "fwd", "f64", "e2e", "osc", "uneven", "mmd", "acc", "cpu")
+PARTS = ("f32", "ckpt", "fwd", "f64", "e2e", "osc", "long", "uneven", "mmd", "acc", "cpu")
 SM_COUNT = 152
 FP32_LANES = 128
 SM_MAX_MHZ = 2070.0
@@ -108,7 +108,8 @@ def parse():
                     help="points per path (shorter paths, for profiling runs that must hold only a few GB)")
     ap.add_argument("--parts", default=",".join(PARTS),
                     help="comma list: f32 (headline fwd+bwd step), ckpt (checkpointing adjoint), fwd (forward "
-                         "only), f64 (FP64 forward), e2e, osc (oscillatory pairs), uneven (uneven batch), mmd "
+                         "only), f64 (FP64 forward), e2e, osc (oscillatory pairs), long (one pair of 16385-point paths), "
+                         "uneven (uneven batch), mmd "
                          "(MMD^2 fwd+bwd, permutation test), acc (accuracy report: MAPE per order / refinement), cpu")
     args = ap.parse_args()
     args.parts = set(args.parts.split(","))
@@ -502,6 +503,18 @@ def main():
                 osc["interp8_f32_mape_vs_fp64_gpu"] = float(((o32 - o).abs() / o.abs()).mean())
         line["oscillatory"] = osc
         del Xo, Yo
+
+    if "long" in args.parts:  # one pair of 16385-point paths, d=4: parallelism inside a single pair
+        Xl = torch.tensor(W.brownian(1, 16385, 4, seed=11 + 1000 * rank), device=dev)
+        Yl = torch.tensor(W.brownian(1, 16385, 4, seed=12 + 1000 * rank), device=dev)
+        il = torch.zeros(1, dtype=torch.int64, device=dev)
+        ol = torch.empty(1, dtype=torch.float64, device=dev)
+        cells_l = 16384 * 16384
+        t_grid = timed_steps(lambda: sk.sigkernel_pairs(Xl, Yl, il, il, compute="f32", out=ol), 2, 1)
+        line["long_pair"] = {"workload": "1 pair of 16385-point Brownian paths, d=4, approx N=6, FP32: the pair's "
+                                         "512 strips swept by a ring of 32 co-resident 16-warp blocks",
+                             "cells": cells_l, "ms": t_grid, "cell_updates_per_s": cells_l / (t_grid / 1e3)}
+        del Xl, Yl
 
     if "uneven" in args.parts:  # 4096 pairs, lengths log-uniform in [64, 4096], d=16, BF16: autotuned + graph
         Xs = W.uneven(4096, 64, 4096, 16, seed=6 + 1000 * rank)
