@@ -215,19 +215,18 @@ constexpr int fwd_poly_coop_min_blocks() {
     return b < 1 ? 1 : b;
 }
 
-// Sweep of one pair by one warp (CW = 1), or by warp w of CW warps that share it: warp w runs
-// strips w, w + CW, w + 2 CW, ... in the same overlapped schedule a single warp uses for all of
-// them (local strip sigma starts at local step sigma * P).  Lane 31 of strip g writes its right
-// edges into this warp's hand-off buffer (own_buf); lane 0 of strip g + 1 reads them from the
-// buffer of the warp that ran strip g (prev_buf, the warp's own buffer when CW = 1).  With
-// CW > 1 the hand-off is ordered by the progress words prog[] (publish_progress /
-// wait_progress); a buffer entry of strip g is overwritten by strip g + CW only after strip
-// g + 1 has consumed it, because strip g + CW depends on strip g + 1 through the chain of
-// strips in between.
+// Sweep of one pair by one warp (CW = 1), or by warp w of a ring of `ring` warps that share it:
+// warp w runs strips w, w + ring, w + 2 ring, ... in the same overlapped schedule a single warp
+// uses for all of them (local strip sigma starts at local step sigma * P).  Lane 31 of strip g
+// writes its right edges into this warp's hand-off buffer (own_buf); lane 0 of strip g + 1 reads
+// them from the buffer of the warp that ran strip g (prev_buf, the warp's own buffer when
+// CW = 1).  In a ring the hand-off is ordered by the progress words prog[]; a buffer entry of
+// strip g is overwritten by strip g + ring only after strip g + 1 has consumed it, because strip
+// g + ring depends on strip g + 1 through the chain of strips in between.
 //
-// The ring of warps is CW warps of one block (progress words in shared memory), or, with GS, ring
-// warps spread over co-resident blocks (progress words in global memory, GPU-scope ordering);
-// ring is the ring's width (CW, or blocks x CW with GS).
+// The ring is the CW warps of one block (ring = CW, progress words in shared memory, CTA-scope
+// ordering), or, with GS, blocks x CW warps spread over co-resident blocks (progress words in
+// global memory, GPU-scope ordering, published every kGridPublish columns).
 template <typename T, int N, int NE, bool INTERP, int CW, bool MT, bool GS = false>
 __device__ __forceinline__ void sweep_poly(const Launch& L, int64_t item, const PairDesc& P, int w, char* own_buf,
                                            const char* prev_buf, int* prog, int64_t buf_cols, T* xstage,

@@ -113,8 +113,8 @@ def test_long_pairs_take_the_pipeline_by_default():
     assert t_auto < t_one  # 16 warps per pair instead of 1
 
 
-@pytest.mark.parametrize("compute", ["f32", "f64"])
-def test_grid_pipeline_spreads_few_long_pairs_over_blocks(compute):
+@pytest.mark.parametrize("scheme,N,compute", [("approx", 6, "f32"), ("approx", 6, "f64"), ("interp", 8, "f32")])
+def test_grid_pipeline_spreads_few_long_pairs_over_blocks(scheme, N, compute):
     """Four pairs with up to 128 strips: each pair's ring of warps spans several co-resident
     blocks (progress words in global memory).  Results equal the one-warp sweep bit for bit, the
     shortest pair is pinned to the oracle, and the spread sweep is faster."""
@@ -123,15 +123,16 @@ def test_grid_pipeline_spreads_few_long_pairs_over_blocks(compute):
     PX = sk.Paths.from_list([torch.tensor(x) for x in Xs])
     PY = sk.Paths.from_list([torch.tensor(y) for y in Ys])
     pa, pb = [0, 1, 2, 0], [0, 1, 0, 1]
-    auto = sk.sigkernel_pairs(PX, PY, pa, pb, compute=compute, time_kernel=True)
+    kw = dict(scheme=scheme, degree=N, compute=compute)
+    auto = sk.sigkernel_pairs(PX, PY, pa, pb, time_kernel=True, **kw)
     torch.cuda.synchronize()
     t_auto = sk.last_kernel_ms()
-    one = sk.sigkernel_pairs(PX, PY, pa, pb, compute=compute, strip_pipeline=False, time_kernel=True)
+    one = sk.sigkernel_pairs(PX, PY, pa, pb, strip_pipeline=False, time_kernel=True, **kw)
     torch.cuda.synchronize()
     t_one = sk.last_kernel_ms()
     assert sk.device_status() == 0
     assert torch.equal(auto, one)
-    ref = oracle.pairs([Xs[1]], [Ys[1]], [0], [0], "approx", 6, 0)[0]
+    ref = oracle.pairs([Xs[1]], [Ys[1]], [0], [0], scheme, N, 0)[0]
     tol = 1e-4 if compute == "f32" else 1e-11
     assert abs(auto[1].item() - ref) <= tol * abs(ref)
     assert t_auto < t_one / 4
