@@ -727,9 +727,14 @@ __host__ __device__ constexpr int bwd_series_top() {
 }
 
 // Shared memory of one warp for the tape adjoint: the ring and its mbarriers.
+// Each warp's region is padded to 128 bytes, so that every warp's ring (a bulk-copy destination,
+// which must be 16-byte aligned) starts aligned whatever the slot count.
+__host__ __device__ constexpr int bwd_tape_warp_bytes(int step_bytes) {
+    return (kTapeRing * step_bytes + kTapeRing * 8 + 127) / 128 * 128;
+}
 template <typename T, int N>
 __host__ __device__ constexpr int bwd_tape_warp_bytes() {
-    return kTapeRing * fwd_tape_step_bytes<T, N>() + kTapeRing * 8;
+    return bwd_tape_warp_bytes(fwd_tape_step_bytes<T, N>());
 }
 
 // Gradient seed and exponent of k_hat for item `item` (shared by the adjoint and the contraction).
