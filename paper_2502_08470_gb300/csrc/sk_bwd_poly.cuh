@@ -711,8 +711,9 @@ __global__ void __launch_bounds__(kFwdWarps * 32, (bwd_min_blocks<T, N, K>()))
 // skew lets bwd_contract_kernel read both rows and columns of a cell tile without bank
 // conflicts.  That kernel turns the buffer into dk/dx and dk/dy.
 // ---------------------------------------------------------------------------------------------
-// Per-lane streaming loads of the tape one step ahead (no ring, no shared memory) measured slower
-// on the 128x128 Gram of 257-point paths: 18.9 ms against 15.6 ms for this ring.
+// Four slots measured fastest on the 128x128 Gram of 257-point paths: 15.6 ms, against 16.3 ms
+// with three and 19.1 ms with eight.  Per-lane streaming loads of the tape one step ahead (no
+// ring, no shared memory) took 18.9 ms.
 constexpr int kTapeRing = 4;
 
 template <typename T, int N, bool INTERP>
