@@ -261,12 +261,12 @@ void sigkernel_autotune_clear(void);
  *   out       device double [4]: MMD^2, mean K_AA, mean K_BB, mean K_AB (as used above)
  *   grad_A/B  device double with A's / B's row layout, or NULL: d MMD^2 / d rows, OVERWRITTEN.
  * K_AA and K_BB are solved as symmetric Grams; the reduction runs in FP64 on the device.
- * Gradients (polynomial approximation only) run the adjoint from forward tapes: each Gram block is
+ * Gradients (polynomial schemes) run the adjoint from forward tapes: each Gram block is
  * solved in chunks of pairs whose tape is at most 48 GiB, the chunk's forward recording the tape
  * and the tape adjoint following at once with the block's constant weights.  A block whose paths
  * are so long that a chunk cannot fill the GPU uses the checkpointing adjoint of
- * sigkernel_backward instead (d <= 32).  The workspace (SK_OP_MMD2 with npairs != 0) includes the
- * tape.
+ * sigkernel_backward instead (d <= 32; approximation scheme only, else SK_ERR_UNSUPPORTED).
+ * The workspace (SK_OP_MMD2 with npairs != 0) includes the tape.
  */
 int sigkernel_mmd2(const sk_paths* A, const sk_paths* B, int32_t d, int32_t dtype,
                    const sk_options* opt, double* out, double* grad_A, double* grad_B,

@@ -976,8 +976,8 @@ int plan_mmd2(const sk_paths* A, const sk_paths* Bp, int32_t d, int32_t dtype, c
     if (A->count < 1 || Bp->count < 1) return fail(SK_ERR_INVALID_ARG, "MMD^2 needs non-empty path sets");
     const bool unb = (o->flags & SK_FLAG_UNBIASED) != 0;
     if (unb && (A->count < 2 || Bp->count < 2)) return fail(SK_ERR_INVALID_ARG, "unbiased MMD^2 needs >= 2 paths per set");
-    if (grads && o->scheme != SK_POLY_APPROX)
-        return fail(SK_ERR_UNSUPPORTED, "MMD^2 gradients need the polynomial approximation scheme");
+    if (grads && o->scheme != SK_POLY_APPROX && o->scheme != SK_POLY_INTERP)
+        return fail(SK_ERR_UNSUPPORTED, "MMD^2 gradients need a polynomial scheme");
     m.grads = grads;
     m.os = *o;
     m.os.flags = (o->flags & (SK_FLAG_INCREMENTS | SK_FLAG_NO_SORT | SK_FLAG_TIME_KERNEL | SK_FLAG_STRIP_PIPELINE |
@@ -1013,6 +1013,10 @@ int plan_mmd2(const sk_paths* A, const sk_paths* Bp, int32_t d, int32_t dtype, c
         m.chunk[k] = std::min(c, m.items[k]);
         m.tape[k] = m.chunk[k] == m.items[k] || 2 * m.chunk[k] >= resident;
         if (!m.tape[k]) {  // checkpointing adjoint over the whole block
+            if (o->scheme == SK_POLY_INTERP)
+                return fail(SK_ERR_UNSUPPORTED,
+                            "MMD^2 gradients of the interpolation scheme need forward tapes, and these paths are too "
+                            "long for a tape chunk to fill the GPU");
             m.chunk[k] = m.items[k];
             if ((rc = plan_forward(xs[k], ys[k], d, dtype, ok, modes[k], m.items[k], m.f[k], true)) != SK_OK) return rc;
             if ((rc = plan_backward(xs[k], ys[k], d, dtype, ok, modes[k], m.items[k], m.cb[k])) != SK_OK) return rc;

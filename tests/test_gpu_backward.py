@@ -178,6 +178,30 @@ def test_mmd2_matches_oracle(unbiased):
         assert abs(got - ref_g) < 1e-9 * max(1.0, np.max(np.abs(gA)))
 
 
+@pytest.mark.parametrize("compute,tol", [("f64", 1e-9), ("f32", 1e-4)])
+def test_mmd2_interpolation_gradient_matches_oracle(compute, tol):
+    """MMD^2 gradients of the interpolation scheme (N = 6) from the chunked tape adjoint, against
+    the oracle's complex-step derivative."""
+    A = W.brownian(4, 20, 2, seed=67)
+    B = W.brownian(3, 20, 2, seed=68, drift=0.5, vol=1.2)
+    m, means, gA, gB = sk.sigkernel_mmd2(_cuda(A), _cuda(B), scheme="interp", degree=6, compute=compute, grads=True)
+    torch.cuda.synchronize()
+    assert sk.device_status() == 0
+    ref = oracle.mmd2(A, B, "interp", 6)
+    assert abs(m.item() - ref) < tol * max(1.0, abs(ref))
+    gA = gA.cpu().numpy().reshape(A.shape)
+    gB = gB.cpu().numpy().reshape(B.shape)
+    scale = max(np.max(np.abs(gA)), np.max(np.abs(gB)))
+    rng = np.random.default_rng(69)
+    for _ in range(6):
+        side = int(rng.integers(0, 2))
+        S = A if side == 0 else B
+        path, p, c = rng.integers(0, S.shape[0]), rng.integers(0, 20), rng.integers(0, 2)
+        ref_g = oracle.mmd2_grad_entry(A, B, side, path, p, c, "interp", 6)
+        got = (gA if side == 0 else gB)[path, p, c]
+        assert abs(got - ref_g) < tol * scale, (side, path, p, c, got, ref_g)
+
+
 def test_mmd2_workload_gradient_central_differences_f32():
     """Two batches (Brownian vs Brownian with drift 0.5 and volatility 1.2), FP32 adjoint; 16 random
     coordinates checked against central differences (h = 1e-4) of the FP64 oracle."""
