@@ -191,7 +191,10 @@ int sigkernel_gram(const sk_paths* X, const sk_paths* Y, int32_t d, int32_t dtyp
  *           the existing contents (the caller zeroes it first for a plain gradient); NULL skips.
  *   grad_Y  likewise for Y.  When Y is X (same rows pointer) both accumulate into the same
  *           buffer correctly if grad_X == grad_Y.
- * Supported for SK_POLY_APPROX with d <= 32; other schemes return SK_ERR_UNSUPPORTED.
+ * SK_POLY_APPROX runs the checkpointing adjoint (d <= 32).  SK_POLY_INTERP, which has no
+ * checkpointing adjoint, records forward tapes in chunks of pairs (at most 48 GiB each, in the
+ * workspace) and runs the tape adjoint after each chunk; paths so long that a chunk cannot fill
+ * the GPU return SK_ERR_UNSUPPORTED.  The FD schemes return SK_ERR_UNSUPPORTED.
  * Accumulation uses device atomics, so the last bits of the gradient can vary between runs.
  */
 int sigkernel_backward(const sk_paths* X, const sk_paths* Y, int32_t d, int32_t dtype,

@@ -1129,6 +1129,100 @@ int run_mmd2(const sk_paths* A, const sk_paths* Bp, int32_t d, int32_t dtype, co
     return SK_OK;
 }
 
+// sigkernel_backward for the interpolation scheme, which has no checkpointing adjoint: the items
+// are taken in chunks whose forward records a tape (at most kMmdTapeBudget bytes) and whose tape
+// adjoint follows at once, as in sigkernel_mmd2.  Paths so long that a chunk holds fewer items
+// than half the adjoint's resident warps are refused (SK_ERR_UNSUPPORTED).
+struct ChunkBwdPlan {
+    int64_t items, chunk;
+    Plan f;           // forward of one chunk, recording its tape
+    TapeBwdPlan tb;   // tape adjoint of one chunk
+    size_t ginc_a, ginc_bytes, tape_bytes, out_bytes, sub, total;
+};
+
+int plan_backward_chunked(const sk_paths* X, const sk_paths* Y, int32_t d, int32_t dtype, const sk_options* o,
+                          int mode, int64_t items, ChunkBwdPlan& c) {
+    Plan p1;
+    int rc;
+    if ((rc = plan_forward(X, Y, d, dtype, o, mode, 1, p1)) != SK_OK) return rc;
+    TapePlan t1;
+    if ((rc = plan_tape(X, Y, o, p1.T, 1, t1)) != SK_OK) return rc;
+    TapeBwdPlan whole;
+    if ((rc = plan_backward_tape(X, Y, d, dtype, o, mode, std::max<int64_t>(items, 1), whole)) != SK_OK) return rc;
+    const int64_t resident = std::max<int64_t>(1, static_cast<int64_t>(whole.f.blocks) * kFwdWarps);
+    int64_t chunk = std::max<int64_t>(1, static_cast<int64_t>(kMmdTapeBudget / std::max<size_t>(t1.stride, 1)));
+    if (chunk < items && chunk > resident) chunk -= chunk % resident;
+    chunk = std::max<int64_t>(1, std::min(chunk, items));
+    if (chunk < items && 2 * chunk < resident)
+        return fail(SK_ERR_UNSUPPORTED, "sigkernel_backward of the interpolation scheme needs forward tapes, and these "
+                                        "paths are too long for a tape chunk to fill the GPU");
+    c.items = items;
+    c.chunk = chunk;
+    if ((rc = plan_forward(X, Y, d, dtype, o, mode, chunk, c.f)) != SK_OK) return rc;
+    if ((rc = plan_backward_tape(X, Y, d, dtype, o, mode, chunk, c.tb)) != SK_OK) return rc;
+    TapePlan tc;
+    if ((rc = plan_tape(X, Y, o, p1.T, chunk, tc)) != SK_OK) return rc;
+    c.tape_bytes = tc.total;
+    const int64_t nout = mode == kPairsList ? chunk : X->count * Y->count;
+    c.out_bytes = align256(static_cast<size_t>(std::max<int64_t>(nout, 1)) * sizeof(double));
+    c.ginc_a = align256(static_cast<size_t>(X->rows_total) * p1.dpad * sizeof(double));
+    c.ginc_bytes = c.ginc_a + (p1.same_xy ? 0 : align256(static_cast<size_t>(Y->rows_total) * p1.dpad * sizeof(double)));
+    c.sub = std::max(c.f.total, c.tb.total);
+    c.total = c.ginc_bytes + align256(c.tape_bytes) + c.out_bytes + c.sub + 512;
+    return SK_OK;
+}
+
+int run_backward_chunked(const sk_paths* X, const sk_paths* Y, int32_t d, int32_t dtype, const sk_options* o,
+                         const int64_t* pa, const int64_t* pb, int64_t npairs, const double* gout, double* gX,
+                         double* gY, void* ws, size_t ws_bytes, void* stream) {
+    const bool gram = (pa == nullptr);
+    const bool sym = gram && (o->flags & SK_FLAG_SYMMETRIC);
+    const int mode = gram ? (sym ? kGramUpper : kGramFull) : kPairsList;
+    if (gram) npairs = gram_items(X, Y, sym);
+    ChunkBwdPlan c;
+    int rc = plan_backward_chunked(X, Y, d, dtype, o, mode, npairs, c);
+    if (rc != SK_OK) return rc;
+    if (c.f.same_xy && gY && gY != gX)
+        return fail(SK_ERR_INVALID_ARG, "X and Y are the same paths: pass grad_Y = NULL or grad_Y = grad_X");
+    if (npairs == 0) return SK_OK;
+    if (!gout) return fail(SK_ERR_INVALID_ARG, "grad_out is NULL");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    bool own = false;
+    if (!ws) {
+        SK_CUDA(cudaMallocAsync(&ws, c.total, st));
+        own = true;
+    } else if (ws_bytes < c.total) {
+        return fail(SK_ERR_WORKSPACE, "workspace %zu bytes < %zu required", ws_bytes, c.total);
+    }
+    char* base = reinterpret_cast<char*>((reinterpret_cast<uintptr_t>(ws) + 255) / 256 * 256);
+    double* gincX = reinterpret_cast<double*>(base);
+    double* gincY = c.f.same_xy ? gincX : reinterpret_cast<double*>(base + c.ginc_a);
+    char* tape = base + c.ginc_bytes;
+    double* outbuf = reinterpret_cast<double*>(tape + align256(c.tape_bytes));
+    char* sub_ws = reinterpret_cast<char*>(outbuf) + c.out_bytes;
+    char* sb = reinterpret_cast<char*>((reinterpret_cast<uintptr_t>(sub_ws) + 255) / 256 * 256);
+    SK_CUDA(cudaMemsetAsync(gincX, 0, c.ginc_bytes, st));
+    const int64_t ldo = gram ? Y->count : 0;
+    for (int64_t i0 = 0; i0 < npairs; i0 += c.chunk) {
+        const int64_t n = std::min(c.chunk, npairs - i0);
+        const int64_t* pai = gram ? nullptr : pa + i0;
+        const int64_t* pbi = gram ? nullptr : pb + i0;
+        const double* gi = gram ? gout : gout + i0;
+        const int64_t base_item = gram ? i0 : 0;
+        if ((rc = run_forward(X, Y, d, dtype, o, mode, pai, pbi, n, outbuf, ldo, sub_ws, c.sub, st, tape, c.tape_bytes,
+                              base_item)) != SK_OK)
+            return rc;
+        if ((rc = launch_backward_tape(X, Y, d, dtype, o, mode, pai, pbi, n, base_item, tape, gi, ldo, c.tb, sb, gincX,
+                                       gincY, st)) != SK_OK)
+            return rc;
+    }
+    const int inc_mode = (o->flags & SK_FLAG_INCREMENTS) ? 1 : 0;
+    if ((rc = convert_grad(X, d, c.f.dpad, inc_mode, gincX, gX, st)) != SK_OK) return rc;
+    if (!c.f.same_xy && (rc = convert_grad(Y, d, c.f.dpad, inc_mode, gincY, gY, st)) != SK_OK) return rc;
+    if (own) SK_CUDA(cudaFreeAsync(ws, st));
+    return SK_OK;
+}
+
 // Permutation test on MMD^2: the pooled Gram K of Z = (A, B) from the three blocks of
 // sigkernel_mmd2 written in place (K_AA and K_BB symmetric, K_AB full; K_BA mirrored by the test's
 // own kernel), then the statistics of every relabelling (launch_mmd_perm).
@@ -1319,6 +1413,13 @@ int sigkernel_workspace_size(int32_t op, const sk_paths* X, const sk_paths* Y, i
         case SK_OP_BACKWARD: {
             const bool gram = npairs < 0;
             const bool sym = gram && (opt->flags & SK_FLAG_SYMMETRIC);
+            if (opt->scheme == SK_POLY_INTERP) {
+                ChunkBwdPlan c;
+                rc = plan_backward_chunked(X, Y, d, dtype, opt, gram ? (sym ? kGramUpper : kGramFull) : kPairsList,
+                                           gram ? gram_items(X, Y, sym) : npairs, c);
+                if (rc == SK_OK) *bytes = c.total;
+                return rc;
+            }
             BwdPlan b;
             rc = plan_backward(X, Y, d, dtype, opt, gram ? (sym ? kGramUpper : kGramFull) : kPairsList,
                                gram ? gram_items(X, Y, sym) : npairs, b);
@@ -1380,6 +1481,9 @@ int sigkernel_backward(const sk_paths* X, const sk_paths* Y, int32_t d, int32_t 
     t_last_error.clear();
     if (!opt || !X || !Y) return fail(SK_ERR_INVALID_ARG, "NULL argument");
     if (pair_a && (!pair_b || npairs < 0)) return fail(SK_ERR_INVALID_ARG, "bad pair list");
+    if (opt->scheme == SK_POLY_INTERP)
+        return run_backward_chunked(X, Y, d, dtype, opt, pair_a, pair_b, npairs, grad_out, grad_X, grad_Y, workspace,
+                                    workspace_bytes, stream);
     return run_backward(X, Y, d, dtype, opt, pair_a, pair_b, npairs, grad_out, grad_X, grad_Y, workspace,
                         workspace_bytes, stream);
 }
