@@ -416,9 +416,11 @@ def test_backward_interpolation_runs_chunked_tapes(compute, tol, sym):
     tX, tY = sk.sigkernel_backward_tape(tape, _cuda(Wt), Xt, Yt, scheme="interp", degree=5, compute=compute)
     torch.cuda.synchronize()
     assert sk.device_status() == 0
-    assert torch.allclose(gX, tX, rtol=1e-12, atol=1e-14)
+    same_tol = 1e-12 if compute == "f64" else 1e-5  # FP32 column sums meet in shared-memory atomics
+    scale = float(tX.abs().max())
+    assert float((gX - tX).abs().max()) <= same_tol * scale
     rX, rY = _oracle_gram_grad(X, Y, Wt, 5, 0, sym, scheme="interp")
     assert _scaled_err(gX.cpu().numpy().reshape(X.shape), rX) < tol
     if not sym:
-        assert torch.allclose(gY, tY, rtol=1e-12, atol=1e-14)
+        assert float((gY - tY).abs().max()) <= same_tol * float(tY.abs().max())
         assert _scaled_err(gY.cpu().numpy().reshape(Y.shape), rY) < tol
