@@ -1,10 +1,9 @@
 // Bulk-copy (TMA engine) and mbarrier helpers for sm_103a, as inline PTX.
 //
-// The tape of the forward pass streams through these: a warp stages one 2 KB step of cell inputs
-// in shared memory and one lane moves it with cp.async.bulk (global <- shared, bulk-group
-// completion), and the adjoint reads steps back into a shared-memory ring with
-// cp.async.bulk (shared <- global) completing on per-slot mbarriers.  Every wait is bounded; a
-// wait that runs out sets the device error word (SK_ERR_DEVICE_TIMEOUT) and reports failure.
+// The tape adjoint reads the forward tape's steps into a shared-memory ring, and the contraction
+// streams the dk/dM buffer the same way: cp.async.bulk (shared <- global) completing on per-slot
+// mbarriers.  Every wait is bounded; a wait that runs out sets the device error word
+// (SK_ERR_DEVICE_TIMEOUT) and reports failure.
 #pragma once
 
 #include <stdint.h>
@@ -60,29 +59,6 @@ __device__ __forceinline__ void bulk_load(void* smem_dst, const void* gsrc, uint
             smem_u32(smem_dst)),
         "l"(gsrc), "r"(bytes), "r"(smem_u32(bar))
         : "memory");
-}
-
-// shared -> global, tracked by the issuing thread's bulk groups.
-__device__ __forceinline__ void bulk_store(void* gdst, const void* smem_src, uint32_t bytes) {
-    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(gdst), "r"(smem_u32(smem_src)),
-                 "r"(bytes)
-                 : "memory");
-}
-
-__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
-
-// Wait until at most N committed bulk groups of this thread still read their shared source.
-template <int N>
-__device__ __forceinline__ void bulk_wait_read() {
-    asm volatile("cp.async.bulk.wait_group.read %0;" ::"n"(N) : "memory");
-}
-
-// Wait until all of this thread's bulk groups have completed (writes visible in global memory).
-__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
-
-// Orders this thread's generic-proxy shared-memory writes before later async-proxy reads.
-__device__ __forceinline__ void fence_proxy_async_smem() {
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 
 }  // namespace sk
