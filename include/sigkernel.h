@@ -106,7 +106,11 @@ enum {
                                        library pipelines every pair of 2 or more strips when some
                                        pair has 32 or more strips and the batch is too small to
                                        fill the GPU with one warp per pair.  Neither applies to the
-                                       tape forward or to the adjoints (one warp per pair) */
+                                       tape forward or to the adjoints (one warp per pair).  With
+                                       so few pairs that each pair's 16-warp ring can span 8 or
+                                       more blocks, the pipelined polynomial forward spreads each
+                                       ring over co-resident blocks (a cooperative launch; the
+                                       results are the same bit for bit) */
     SK_FLAG_NO_TILED_M = 128        /* forward, polynomial schemes in FP32: form each cell's M from
                                        its two increment rows.  By default, with d > 8, each warp
                                        first computes a strip's M_ij for all columns at once (the
