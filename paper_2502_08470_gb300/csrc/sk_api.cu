@@ -287,7 +287,9 @@ int plan_forward(const sk_paths* X, const sk_paths* Y, int32_t d, int32_t dtype,
     // are swept by blocks of kCoopWarps warps instead (one strip per warp, pipelined).
     if (allow_coop && pipe_req >= 0) {
         const int rows_per_lane = poly ? 1 : (lam < 4 ? (1 << lam) : 16);
-        const int64_t max_strips = (((X->max_len << lam) / rows_per_lane) + 31) / 32;
+        // rows of the longest X path: its increments (one fewer than its points in points mode)
+        const int64_t max_rows = std::max<int64_t>(X->max_len - ((o->flags & SK_FLAG_INCREMENTS) ? 0 : 1), 1) << lam;
+        const int64_t max_strips = ((max_rows / rows_per_lane) + 31) / 32;
         const bool forced = pipe_req > 0;
         const int64_t resident = static_cast<int64_t>(sms) * per_sm * (p.threads / 32);
         if (max_strips >= 2 && (forced || (max_strips >= 2 * kCoopWarps && npairs < 4 * resident))) {
