@@ -438,3 +438,37 @@ def test_permutation_p_values_are_valid_under_the_null():
     ps = np.array(ps)
     assert np.count_nonzero(ps <= 0.1) <= 16
     assert 0.42 < ps.mean() < 0.6
+
+
+@pytest.mark.parametrize("scheme", SCHEMES)
+@pytest.mark.parametrize("lam", [0, 1])
+def test_repeated_point_leaves_every_scheme_unchanged(scheme, lam):
+    """A repeated point adds a zero increment: its cells have M = 0, where the Goursat solution is
+    the bilinear k(s, v) + k(u, t) - k(u, v) of its edges, which every scheme carries exactly
+    (polynomial edges keep their degree; the FD update is exact).  The output is unchanged up to
+    rounding, with the repeat at the start or inside either path, and for the interpolation and
+    FD schemes also at the end.  The approximation scheme's top and right edges carry corner
+    values that differ by its truncation error (the Remark after Definition
+    "def:polyapproxscheme" takes p_0 on one and q_0 on the other), and its endpoint averages the
+    two, so a zero row appended at the end moves the average by half that difference."""
+    X = W.brownian(1, 9, 3, seed=101)[0]
+    Y = W.brownian(1, 7, 3, seed=102)[0]
+    k0 = oracle.kernel(X, Y, scheme, 5, lam=lam)
+    for where in ((0, 4) if scheme == "approx" else (0, 4, 8)):
+        Xr = np.insert(X, where, X[where], axis=0)
+        assert oracle.kernel(Xr, Y, scheme, 5, lam=lam) == pytest.approx(k0, rel=1e-12), where
+    Yr = np.insert(Y, 3, Y[3], axis=0)
+    assert oracle.kernel(X, Yr, scheme, 5, lam=lam) == pytest.approx(k0, rel=1e-12)
+
+
+def test_appended_zero_row_moves_the_approximation_endpoint_by_the_corner_mismatch():
+    """The exception above, quantified: with an appended zero row the approximation scheme's
+    output becomes a(1) + b(1) - (a(0) + b(0)) / 2, where a and b are the edges entering the final
+    (zero) cell, so it moves by half their corner mismatch.  That mismatch is truncation error and
+    shrinks fast with the order."""
+    X = W.brownian(1, 9, 3, seed=101)[0]
+    Y = W.brownian(1, 7, 3, seed=102)[0]
+    Xr = np.insert(X, 8, X[8], axis=0)
+    gaps = [abs(oracle.kernel(Xr, Y, "approx", N) - oracle.kernel(X, Y, "approx", N)) for N in (3, 5, 7, 9)]
+    assert gaps[0] > 1e-6
+    assert all(gaps[k + 1] < gaps[k] / 10 for k in range(3)), gaps
