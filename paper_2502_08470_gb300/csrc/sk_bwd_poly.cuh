@@ -1053,7 +1053,7 @@ template <int C> struct ContractAcc<double, C> {
 // One tile: cell (r, j0 + q) is at ring row hb + r + q (mod 96), position (2r + q + coff) mod 32
 // with coff = (t0 + j0) mod 32.  nr, nc: valid rows and columns (FULL: 32 and 32; otherwise
 // cells outside them, whose buffer entries may hold anything, count as zero).
-template <typename T, int C, bool FULL>
+template <typename T, int C, bool FULL, bool WRAP>
 __device__ __forceinline__ void contract_tile(const T* __restrict__ ring, int hb, int coff, const T* __restrict__ xs,
                                               const T* __restrict__ ys, int nr, int nc, int lane, ContractAcc<T, C>& xa,
                                               ContractAcc<T, C>& ya) {
@@ -1064,7 +1064,7 @@ __device__ __forceinline__ void contract_tile(const T* __restrict__ ring, int hb
         const int q = (q0 + (lane >> 4)) & 31;
         const int u = lane + q;
         int row = hb + u;
-        row -= row >= 96 ? 96 : 0;
+        if (WRAP) row -= row >= 96 ? 96 : 0;
         T m = ring[(row << 5) + ((lane + u + coff) & 31)];
         if (!FULL) m = (lane < nr && q < nc) ? m : T(0);
         xa.axpy(m, ys + q * C);
@@ -1074,7 +1074,7 @@ __device__ __forceinline__ void contract_tile(const T* __restrict__ ring, int hb
     for (int r = 0; r < 32; ++r) {
         const int u = r + lane;
         int row = hb + u;
-        row -= row >= 96 ? 96 : 0;
+        if (WRAP) row -= row >= 96 ? 96 : 0;
         T m = ring[(row << 5) + ((r + u + coff) & 31)];
         if (!FULL) m = (r < nr && lane < nc) ? m : T(0);
         ya.axpy(m, xs + r * C);
@@ -1192,8 +1192,13 @@ __global__ void __launch_bounds__(kContractWarps * 32) bwd_contract_kernel(BwdPa
                         ContractAcc<T, C> ya;
                         ya.zero();
                         const int coff = (s * period + j0) & 31;
-                        if (nr == 32 && nc == 32) contract_tile<T, C, true>(ring, s0 * 32, coff, xs, ys, nr, nc, lane, xa, ya);
-                        else contract_tile<T, C, false>(ring, s0 * 32, coff, xs, ys, nr, nc, lane, xa, ya);
+                        // slots 0-1 and 1-2 are contiguous in the ring; only slots 2-0 wrap
+                        if (nr == 32 && nc == 32) {
+                            if (s0 == 2) contract_tile<T, C, true, true>(ring, s0 * 32, coff, xs, ys, nr, nc, lane, xa, ya);
+                            else contract_tile<T, C, true, false>(ring, s0 * 32, coff, xs, ys, nr, nc, lane, xa, ya);
+                        } else {
+                            contract_tile<T, C, false, true>(ring, s0 * 32, coff, xs, ys, nr, nc, lane, xa, ya);
+                        }
                         if (lane < nc) {
                             const int yi = ((j0 + lane) >> lam) - ya0;
 #pragma unroll
