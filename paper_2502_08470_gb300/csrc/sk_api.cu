@@ -952,13 +952,14 @@ __global__ void fill_weights_kernel(double* W, int64_t n, int64_t m, double v, i
 
 // MMD^2 planning, shared by sigkernel_mmd2 and sigkernel_workspace_size.  The three Gram blocks
 // (K_AA and K_BB symmetric, K_AB full) run one after another in one workspace.  With gradients
-// (polynomial approximation) each block runs in chunks of items: the forward records a tape of
+// (polynomial schemes) each block runs in chunks of items: the forward records a tape of
 // the chunk and the tape adjoint runs from it at once, with the block's constant upstream weights
-// (MMD^2 is linear in the Gram entries).  A chunk's tape is at most kMmdTapeBudget bytes, and a
+// (MMD^2 is linear in the Gram entries).  A chunk's tape is at most kTapeChunkBudget bytes, and a
 // chunk smaller than a block is a whole number of the adjoint's resident warps.  When the budget
 // holds fewer items than half the adjoint's resident warps (very long paths), the block uses the
-// checkpointing adjoint instead, which keeps only antidiagonal checkpoints.
-constexpr size_t kMmdTapeBudget = size_t(48) << 30;
+// checkpointing adjoint instead, which keeps only antidiagonal checkpoints (approximation scheme
+// only).  The same budget bounds the chunks of sigkernel_backward for the interpolation scheme.
+constexpr size_t kTapeChunkBudget = size_t(48) << 30;
 
 struct MmdPlan {
     bool grads;
@@ -1010,7 +1011,7 @@ int plan_mmd2(const sk_paths* A, const sk_paths* Bp, int32_t d, int32_t dtype, c
         TapeBwdPlan whole;
         if ((rc = plan_backward_tape(xs[k], ys[k], d, dtype, ok, modes[k], m.items[k], whole)) != SK_OK) return rc;
         const int64_t resident = std::max<int64_t>(1, static_cast<int64_t>(whole.f.blocks) * kFwdWarps);
-        int64_t c = std::max<int64_t>(1, static_cast<int64_t>(kMmdTapeBudget / std::max<size_t>(t1.stride, 1)));
+        int64_t c = std::max<int64_t>(1, static_cast<int64_t>(kTapeChunkBudget / std::max<size_t>(t1.stride, 1)));
         if (c < m.items[k] && c > resident) c -= c % resident;
         m.chunk[k] = std::min(c, m.items[k]);
         m.tape[k] = m.chunk[k] == m.items[k] || 2 * m.chunk[k] >= resident;
@@ -1132,7 +1133,7 @@ int run_mmd2(const sk_paths* A, const sk_paths* Bp, int32_t d, int32_t dtype, co
 }
 
 // sigkernel_backward for the interpolation scheme, which has no checkpointing adjoint: the items
-// are taken in chunks whose forward records a tape (at most kMmdTapeBudget bytes) and whose tape
+// are taken in chunks whose forward records a tape (at most kTapeChunkBudget bytes) and whose tape
 // adjoint follows at once, as in sigkernel_mmd2.  Paths so long that a chunk holds fewer items
 // than half the adjoint's resident warps are refused (SK_ERR_UNSUPPORTED).
 struct ChunkBwdPlan {
@@ -1152,7 +1153,7 @@ int plan_backward_chunked(const sk_paths* X, const sk_paths* Y, int32_t d, int32
     TapeBwdPlan whole;
     if ((rc = plan_backward_tape(X, Y, d, dtype, o, mode, std::max<int64_t>(items, 1), whole)) != SK_OK) return rc;
     const int64_t resident = std::max<int64_t>(1, static_cast<int64_t>(whole.f.blocks) * kFwdWarps);
-    int64_t chunk = std::max<int64_t>(1, static_cast<int64_t>(kMmdTapeBudget / std::max<size_t>(t1.stride, 1)));
+    int64_t chunk = std::max<int64_t>(1, static_cast<int64_t>(kTapeChunkBudget / std::max<size_t>(t1.stride, 1)));
     if (chunk < items && chunk > resident) chunk -= chunk % resident;
     chunk = std::max<int64_t>(1, std::min(chunk, items));
     if (chunk < items && 2 * chunk < resident)
