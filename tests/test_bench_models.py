@@ -1,0 +1,51 @@
+"""CPU checks of the algorithmic work models that bench.py divides by measured times (the roofline
+numerators): warp steps of the wavefront schedule, tape bytes per adjoint launch, and FLOPs per
+cell of the forward and adjoint maps, against counts made independently here."""
+import importlib.util
+import os
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def bench():
+    spec = importlib.util.spec_from_file_location("bench_models", os.path.join(ROOT, "bench.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    return mod
+
+
+def _steps_by_simulation(points):
+    """Warp steps counted by walking the schedule: lane r works on local step t at column
+    (t - r) mod P of strip (t - r) // P; the sweep ends after the last lane's last cell."""
+    rows = cols = points - 1
+    P = max(cols, 32)
+    last = 0
+    for r in range(32):
+        for s in range((rows + 31) // 32):
+            if s * 32 + r < rows:
+                last = max(last, s * P + r + cols - 1)
+    return last + 1
+
+
+@pytest.mark.parametrize("points", [2, 20, 33, 34, 129, 257])
+def test_tape_steps_match_the_schedule(bench, points):
+    assert bench.tape_steps(points) == _steps_by_simulation(points)
+
+
+def test_tape_bytes_of_the_bench_launch(bench):
+    # 128 x 128 pairs of 257-point paths, N = 6: 16 floats of cell inputs per lane (64 B) and one
+    # dk/dM float per lane, per warp step
+    assert bench.tape_steps(257) == 2079
+    assert bench.tape_adjoint_bytes(128 * 128, 257) == 16384 * 2079 * 32 * (64 + 4)
+
+
+def test_flops_per_cell(bench):
+    N, d = 6, 8
+    toeplitz = 2 * sum(n + 1 for n in range(N + 1))      # both edges: sum_n (n + 1) terms
+    hankel = 2 * (N + 1) * N                             # both edges: N couplings per output
+    scale = 2 * (N + 1)                                  # e_n times each coupling sum
+    assert bench.flops_per_cell(N, d) == 2 * (toeplitz + hankel + scale + N + d) == 336
+    assert bench.tape_adjoint_flops_per_cell(N) == 584
