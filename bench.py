@@ -26,6 +26,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -151,7 +152,9 @@ class ClockSampler:
     def __init__(self, index: int):
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+        # SK_CLOCKS_CSV keeps the raw samples where the caller wants them; else a temporary file
+        self.path = os.environ.get("SK_CLOCKS_CSV") or os.path.join(tempfile.gettempdir(),
+                                                                     f"sk_clocks_{os.getpid()}.csv")
 
     def __enter__(self):
         try:
