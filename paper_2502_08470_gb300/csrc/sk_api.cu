@@ -67,6 +67,24 @@ TuneKey tune_key(int dev, const sk_paths* X, const sk_paths* Y, const sk_options
         if (e_ != cudaSuccess) return fail(SK_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
     } while (0)
 
+// A workspace that a call allocated for itself (the caller passed none).  It is freed in stream
+// order on every return path, so a call that fails after the allocation does not leak it.
+struct OwnedWorkspace {
+    void* p = nullptr;
+    cudaStream_t st = nullptr;
+    OwnedWorkspace() = default;
+    OwnedWorkspace(const OwnedWorkspace&) = delete;
+    OwnedWorkspace& operator=(const OwnedWorkspace&) = delete;
+    ~OwnedWorkspace() {
+        if (p) cudaFreeAsync(p, st);
+    }
+    cudaError_t release() {  // the success path's free, with its status
+        void* q = p;
+        p = nullptr;
+        return q ? cudaFreeAsync(q, st) : cudaSuccess;
+    }
+};
+
 // ------------------------------------------------------------------------------------------
 // Increments dx_i = x_{i+1} - x_i (or the caller's increments) in the compute type, rows
 // zero-padded to `dpad` elements.  One block per path (grid-stride over paths).
@@ -417,10 +435,11 @@ int run_forward(const sk_paths* X, const sk_paths* Y, int32_t d, int32_t dtype, 
     if (npairs == 0) return SK_OK;
     if (!out) return fail(SK_ERR_INVALID_ARG, "output pointer is NULL");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    bool own = false;
+    OwnedWorkspace owned;
     if (!ws) {
         SK_CUDA(cudaMallocAsync(&ws, p.total, st));
-        own = true;
+        owned.p = ws;
+        owned.st = st;
     } else if (ws_bytes < p.total) {
         return fail(SK_ERR_WORKSPACE, "workspace %zu bytes < %zu required", ws_bytes, p.total);
     }
@@ -506,7 +525,7 @@ int run_forward(const sk_paths* X, const sk_paths* Y, int32_t d, int32_t dtype, 
         SK_CUDA(cudaEventRecord(t_ev1, st));
         t_timed = true;
     }
-    if (own) SK_CUDA(cudaFreeAsync(ws, st));
+    SK_CUDA(owned.release());
     return SK_OK;
 }
 
@@ -694,10 +713,11 @@ int run_backward(const sk_paths* X, const sk_paths* Y, int32_t d, int32_t dtype,
     if (npairs == 0) return SK_OK;
     if (!gout) return fail(SK_ERR_INVALID_ARG, "grad_out is NULL");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    bool own = false;
+    OwnedWorkspace owned;
     if (!ws) {
         SK_CUDA(cudaMallocAsync(&ws, b.total, st));
-        own = true;
+        owned.p = ws;
+        owned.st = st;
     } else if (ws_bytes < b.total) {
         return fail(SK_ERR_WORKSPACE, "workspace %zu bytes < %zu required", ws_bytes, b.total);
     }
@@ -712,7 +732,7 @@ int run_backward(const sk_paths* X, const sk_paths* Y, int32_t d, int32_t dtype,
     const int inc_mode = (o->flags & SK_FLAG_INCREMENTS) ? 1 : 0;
     if ((rc = convert_grad(X, d, b.f.dpad, inc_mode, gincX, gX, st)) != SK_OK) return rc;
     if (!b.f.same_xy && (rc = convert_grad(Y, d, b.f.dpad, inc_mode, gincY, gY, st)) != SK_OK) return rc;
-    if (own) SK_CUDA(cudaFreeAsync(ws, st));
+    SK_CUDA(owned.release());
     return SK_OK;
 }
 
@@ -891,10 +911,11 @@ int run_backward_tape(const sk_paths* X, const sk_paths* Y, int32_t d, int32_t d
     if (npairs == 0) return SK_OK;
     if (!gout) return fail(SK_ERR_INVALID_ARG, "grad_out is NULL");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    bool own = false;
+    OwnedWorkspace owned;
     if (!ws) {
         SK_CUDA(cudaMallocAsync(&ws, b.total, st));
-        own = true;
+        owned.p = ws;
+        owned.st = st;
     } else if (ws_bytes < b.total) {
         return fail(SK_ERR_WORKSPACE, "workspace %zu bytes < %zu required", ws_bytes, b.total);
     }
@@ -910,7 +931,7 @@ int run_backward_tape(const sk_paths* X, const sk_paths* Y, int32_t d, int32_t d
         return rc;
     if ((rc = convert_grad(X, d, p.dpad, inc_mode, gincX, gX, st)) != SK_OK) return rc;
     if (!p.same_xy && (rc = convert_grad(Y, d, p.dpad, inc_mode, gincY, gY, st)) != SK_OK) return rc;
-    if (own) SK_CUDA(cudaFreeAsync(ws, st));
+    SK_CUDA(owned.release());
     return SK_OK;
 }
 
@@ -1052,10 +1073,11 @@ int run_mmd2(const sk_paths* A, const sk_paths* Bp, int32_t d, int32_t dtype, co
     if (rc != SK_OK) return rc;
     const bool unb = (o->flags & SK_FLAG_UNBIASED) != 0;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    bool own = false;
+    OwnedWorkspace owned;
     if (!ws) {
         SK_CUDA(cudaMallocAsync(&ws, m.total, st));
-        own = true;
+        owned.p = ws;
+        owned.st = st;
     } else if (ws_bytes < m.total) {
         return fail(SK_ERR_WORKSPACE, "workspace %zu bytes < %zu required", ws_bytes, m.total);
     }
@@ -1128,7 +1150,7 @@ int run_mmd2(const sk_paths* A, const sk_paths* Bp, int32_t d, int32_t dtype, co
     }
     mmd2_reduce_kernel<<<1, 256, 0, st>>>(Kaa, na, Kbb, nb, Kab, unb ? 1 : 0, out);
     SK_CUDA(cudaGetLastError());
-    if (own) SK_CUDA(cudaFreeAsync(ws, st));
+    SK_CUDA(owned.release());
     return SK_OK;
 }
 
@@ -1190,10 +1212,11 @@ int run_backward_chunked(const sk_paths* X, const sk_paths* Y, int32_t d, int32_
     if (npairs == 0) return SK_OK;
     if (!gout) return fail(SK_ERR_INVALID_ARG, "grad_out is NULL");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    bool own = false;
+    OwnedWorkspace owned;
     if (!ws) {
         SK_CUDA(cudaMallocAsync(&ws, c.total, st));
-        own = true;
+        owned.p = ws;
+        owned.st = st;
     } else if (ws_bytes < c.total) {
         return fail(SK_ERR_WORKSPACE, "workspace %zu bytes < %zu required", ws_bytes, c.total);
     }
@@ -1222,7 +1245,7 @@ int run_backward_chunked(const sk_paths* X, const sk_paths* Y, int32_t d, int32_
     const int inc_mode = (o->flags & SK_FLAG_INCREMENTS) ? 1 : 0;
     if ((rc = convert_grad(X, d, c.f.dpad, inc_mode, gincX, gX, st)) != SK_OK) return rc;
     if (!c.f.same_xy && (rc = convert_grad(Y, d, c.f.dpad, inc_mode, gincY, gY, st)) != SK_OK) return rc;
-    if (own) SK_CUDA(cudaFreeAsync(ws, st));
+    SK_CUDA(owned.release());
     return SK_OK;
 }
 
@@ -1259,10 +1282,11 @@ int run_mmd2_test(const sk_paths* A, const sk_paths* Bp, int32_t d, int32_t dtyp
     int rc = plan_mmd2_test(A, Bp, d, dtype, o, nperm, t);
     if (rc != SK_OK) return rc;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    bool own = false;
+    OwnedWorkspace owned;
     if (!ws) {
         SK_CUDA(cudaMallocAsync(&ws, t.total, st));
-        own = true;
+        owned.p = ws;
+        owned.st = st;
     } else if (ws_bytes < t.total) {
         return fail(SK_ERR_WORKSPACE, "workspace %zu bytes < %zu required", ws_bytes, t.total);
     }
@@ -1280,7 +1304,7 @@ int run_mmd2_test(const sk_paths* A, const sk_paths* Bp, int32_t d, int32_t dtyp
                               Ks[k], n, sub_ws, t.m.sub, st)) != SK_OK)
             return rc;
     SK_CUDA(launch_mmd_perm(K, n, na, labels, nperm, (o->flags & SK_FLAG_UNBIASED) ? 1 : 0, scratch, out, st));
-    if (own) SK_CUDA(cudaFreeAsync(ws, st));
+    SK_CUDA(owned.release());
     return SK_OK;
 }
 
