@@ -83,3 +83,36 @@ def test_version_and_host_side_validation(lib):
     rc = lib.sigkernel_gram(ctypes.byref(X), ctypes.byref(X), 2, 0, ctypes.byref(bad), None, None,
                             ctypes.c_size_t(0), None)
     assert rc == -1
+
+
+def _header_constants():
+    text = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
+    return {k: int(v) for k, v in re.findall(r"\b(SK_[A-Z0-9_]+)\s*=\s*(-?\d+)", text)}
+
+
+def _header_struct_fields(name):
+    text = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
+    body = re.search(r"typedef struct \{([^}]*)\}\s*" + name + r"\s*;", text).group(1)
+    return re.findall(r"(\w+)\s*;", body)
+
+
+def test_binding_constants_match_the_header():
+    """Every code, scheme, mode, flag and op the binding passes has the header's value."""
+    from paper_2502_08470_gb300 import sigkernel as sk
+    h = _header_constants()
+    assert {code: name for code, name in sk.ERRORS.items()} == {v: k for k, v in h.items() if k.startswith("SK_ERR_")}
+    schemes = {"fd1": "SK_FD1", "fd2": "SK_FD2", "approx": "SK_POLY_APPROX", "interp": "SK_POLY_INTERP",
+               "fd_implicit": "SK_FD_IMPLICIT"}
+    assert {k: h[v] for k, v in schemes.items()} == sk.SCHEMES
+    assert sk.COMPUTE == {"f64": h["SK_COMPUTE_F64"], "f32": h["SK_COMPUTE_F32"]}
+    assert sorted(sk.DTYPES.values()) == sorted(h[k] for k in ("SK_F64", "SK_F32", "SK_BF16"))
+    flags = {k[len("SK_FLAG_"):]: v for k, v in h.items() if k.startswith("SK_FLAG_")}
+    assert flags == {k[len("FLAG_"):]: getattr(sk, k) for k in dir(sk) if k.startswith("FLAG_")}
+    ops = {k[len("SK_OP_"):]: v for k, v in h.items() if k.startswith("SK_OP_")}
+    assert ops == {k[len("OP_"):]: getattr(sk, k) for k in dir(sk) if k.startswith("OP_")}
+
+
+def test_binding_structs_follow_the_header_field_order():
+    from paper_2502_08470_gb300 import sigkernel as sk
+    assert [f for f, _ in sk._Options._fields_] == _header_struct_fields("sk_options")
+    assert [f for f, _ in sk._Paths._fields_] == _header_struct_fields("sk_paths")
