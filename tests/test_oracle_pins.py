@@ -311,6 +311,27 @@ def test_global_truncation_error_bound(N):
     assert abs(truth - approx) <= bound
 
 
+@pytest.mark.parametrize("N", [2, 3, 4])
+def test_hybrid_scheme_converges_at_the_rate_of_the_bound(N):
+    """The hybrid method of Section 3.2 (the approximation scheme on the dyadically refined grid)
+    against the brute-force signature kernel.  Refining once halves Delta, keeps C and doubles
+    l_x + l_y, so the bound of Theorem "prop:globalte" scales by 4^-(N+1) 2^(N+2) = 2^-N: the
+    measured error ratio per refinement settles at 2^N (within [0.9, 1.5] x 2^N at lambda >= 2).
+    A refinement that mis-scaled the sub-cells (a dropped 2^-lambda on one side, say) would not
+    converge to the truth at all."""
+    X = W.brownian(2, 7, 2, seed=100)
+    Y = W.brownian(2, 6, 2, seed=200)
+    x, y = X[0], Y[0]
+    truth = oracle.sig_trunc(x, y, 18)
+    err = [abs(oracle.kernel(x, y, "approx", N, lam) - truth) / abs(truth) for lam in range(5)]
+    assert all(err[lam + 1] < err[lam] for lam in range(4))
+    for lam in (2, 3):
+        assert 0.9 * 2 ** N <= err[lam] / err[lam + 1] <= 1.5 * 2 ** N, (lam, err)
+    # the interpolation scheme on the same refined grids converges to the same truth
+    ierr = [abs(oracle.kernel(x, y, "interp", 2, lam) - truth) / abs(truth) for lam in range(5)]
+    assert ierr[4] < 1e-3 * ierr[0] and ierr[4] < 1e-9
+
+
 # --------------------------------------------------------------------------------------------
 # Complex-step gradients: central differences, and the single-cell closed form
 # --------------------------------------------------------------------------------------------
