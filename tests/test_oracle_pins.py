@@ -82,6 +82,41 @@ def test_interp_single_cell_bessel(N, M):
     assert got == pytest.approx(want, rel=1e-12, abs=1e-14)
 
 
+@pytest.mark.parametrize("N", [2, 3, 5])
+def test_interp_two_by_two_grid_from_library_routines(N):
+    """The interpolation scheme on a 2 x 2 grid assembled from library routines: each incoming
+    edge is interpolated at the N + 1 Chebyshev extrema of its interval (Def. "interpooperator")
+    by numpy.polyfit, and each cell's solution is eq. (interpformula) of Prop. "propinterp" with
+    scipy's 0F1, its first term weighted by the bottom interpolant's constant g_0 (reading 3).
+    Pins the node set, the corner term and the order of the 0F1 parameters where the single-cell
+    pin cannot: there both edges are constant."""
+    x = np.array([[0.0, 0.0], [0.7, -0.4], [1.1, 0.5]])
+    y = np.array([[0.0, 0.0], [-0.5, 0.9], [0.4, 1.3]])
+    s = t = np.array([0.0, 0.5, 1.0])
+
+    def omega(f, a, b):  # monomial coefficients in (r - a) of the interpolant at the extrema
+        nodes = 0.5 * (a + b) + 0.5 * (b - a) * np.cos(np.pi * np.arange(N + 1) / N)
+        return np.polyfit(nodes - a, [f(r) for r in nodes], N)[::-1]
+
+    def solve(i, j, g, h):  # closure of cell (i, j): k on [s_i, s_i+1] x [t_j, t_j+1]
+        C = (x[i + 1] - x[i]) @ (y[j + 1] - y[j]) / ((s[i + 1] - s[i]) * (t[j + 1] - t[j]))
+
+        def k(a, b):
+            u, v = a - s[i], b - t[j]
+            z = C * u * v
+            return g[0] * sps.hyp0f1(1, z) + sum((g[n] * u ** n + h[n] * v ** n) * sps.hyp0f1(n + 1, z)
+                                                 for n in range(1, N + 1))
+        return k
+
+    one = lambda r: 1.0  # noqa: E731  (the boundary k(s_0, .) = k(., t_0) = 1)
+    k00 = solve(0, 0, omega(one, s[0], s[1]), omega(one, t[0], t[1]))
+    k01 = solve(0, 1, omega(lambda r: k00(r, t[1]), s[0], s[1]), omega(one, t[1], t[2]))
+    k10 = solve(1, 0, omega(one, s[1], s[2]), omega(lambda r: k00(s[1], r), t[0], t[1]))
+    k11 = solve(1, 1, omega(lambda r: k10(r, t[1]), s[1], s[2]), omega(lambda r: k01(s[1], r), t[1], t[2]))
+    want = k11(s[2], t[2])
+    assert oracle.kernel(x, y, "interp", N) == pytest.approx(want, rel=1e-12)
+
+
 # --------------------------------------------------------------------------------------------
 # Linear paths x = s u, y = t v: exact kernel 0F1(;1;<u,v>)  (Remark "mbf")
 # --------------------------------------------------------------------------------------------
