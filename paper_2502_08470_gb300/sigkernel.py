@@ -169,6 +169,8 @@ def _stream_ptr() -> int:
 def _dtype_code(X: Paths, Y: Paths) -> int:
     if X.rows.dtype != Y.rows.dtype:
         raise ValueError("X and Y must have the same dtype")
+    if X.rows.dtype not in DTYPES:
+        raise ValueError(f"path dtype {X.rows.dtype} is not one of float64, float32, bfloat16")
     return DTYPES[X.rows.dtype]
 
 

@@ -1,0 +1,61 @@
+"""CPU checks of the Python binding's host-side marshalling (no library call, no GPU): ragged and
+dense path sets become the ABI's rows + int64 offsets + max_len, options become sk_options with
+the header's codes, and host tensors are refused before any pointer reaches the library."""
+import pytest
+import torch
+
+from paper_2502_08470_gb300 import sigkernel as sk
+
+
+def test_ragged_paths_become_rows_and_offsets():
+    lens = [5, 1, 12, 3]
+    paths = [torch.arange(L * 2, dtype=torch.float32).reshape(L, 2) + 100 * i for i, L in enumerate(lens)]
+    P = sk.Paths.from_list(paths, device="cpu")
+    assert P.count == 4 and P.d == 2 and P.max_len == 12
+    assert P.offsets.dtype == torch.int64 and P.offsets.tolist() == [0, 5, 6, 18, 21]
+    assert P.rows.dtype == torch.float32 and P.rows.shape == (21, 2) and P.rows.is_contiguous()
+    for i, p in enumerate(paths):
+        assert torch.equal(P.rows[P.offsets[i]:P.offsets[i + 1]], p)
+    # an explicit dtype converts every path; an empty list gives no paths
+    assert sk.Paths.from_list(paths, device="cpu", dtype=torch.float64).rows.dtype == torch.float64
+    E = sk.Paths.from_list([], device="cpu")
+    assert E.count == 0 and E.offsets.tolist() == [0] and E.max_len == 0
+
+
+def test_dense_paths_and_as_paths():
+    x = torch.randn(3, 7, 4, dtype=torch.float64)
+    P = sk.as_paths(x)
+    assert P.count == 3 and P.d == 4 and P.max_len == 7
+    assert P.offsets.tolist() == [0, 7, 14, 21]
+    assert torch.equal(P.rows.view(3, 7, 4), x)
+    assert sk.as_paths(P) is P
+    with pytest.raises(TypeError):
+        sk.as_paths(torch.randn(7, 4))
+    inc = sk.Paths.from_dense(x, increments=True)
+    assert sk._flags(inc, sk.FLAG_SYMMETRIC) == sk.FLAG_SYMMETRIC | sk.FLAG_INCREMENTS
+    assert sk._flags(P, sk.FLAG_NO_SORT) == sk.FLAG_NO_SORT
+
+
+def test_options_carry_the_header_codes():
+    o = sk._options("interp", 8, 2, "f32", flags=sk.FLAG_SYMMETRIC)
+    assert (o.scheme, o.degree, o.dyadic, o.compute, o.interp_extra, o.flags, o.warps_per_block, o.reserved) == (
+        sk.SCHEMES["interp"], 8, 2, sk.COMPUTE["f32"], 0, sk.FLAG_SYMMETRIC, 0, 0)
+    assert sk._options(4, 2).scheme == sk.SCHEMES["fd_implicit"]  # integer codes pass through
+    with pytest.raises(KeyError):
+        sk._options("fd3")
+    assert sk._pipe_flags(None) == 0
+    assert sk._pipe_flags(True) == sk.FLAG_STRIP_PIPELINE
+    assert sk._pipe_flags(False) == sk.FLAG_NO_STRIP_PIPELINE
+
+
+def test_host_tensors_and_mixed_dtypes_are_refused():
+    P = sk.Paths.from_list([torch.zeros(3, 2)], device="cpu")
+    with pytest.raises(ValueError, match="CUDA"):
+        sk._cpaths(P)
+    A = sk.Paths.from_list([torch.zeros(3, 2, dtype=torch.float32)], device="cpu")
+    B = sk.Paths.from_list([torch.zeros(3, 2, dtype=torch.float64)], device="cpu")
+    with pytest.raises(ValueError, match="same dtype"):
+        sk._dtype_code(A, B)
+    assert sk._dtype_code(A, A) == sk.DTYPES[torch.float32]
+    with pytest.raises(ValueError, match="float16"):
+        sk._dtype_code(*(2 * [sk.Paths.from_list([torch.zeros(3, 2, dtype=torch.float16)], device="cpu")]))
