@@ -152,7 +152,9 @@ class ClockSampler:
     def __init__(self, index: int):
         self.index = index
         self.proc = None
-        # SK_CLOCKS_CSV keeps the raw samples where the caller wants them; else a temporary file
+        # SK_CLOCKS_CSV keeps the raw samples where the caller wants them; else a temporary file,
+        # removed once summarised
+        self.keep = bool(os.environ.get("SK_CLOCKS_CSV"))
         self.path = os.environ.get("SK_CLOCKS_CSV") or os.path.join(tempfile.gettempdir(),
                                                                      f"sk_clocks_{os.getpid()}.csv")
 
@@ -177,11 +179,17 @@ class ClockSampler:
             self.f.close()
 
     def summary(self):
-        if self.proc is None or not os.path.exists(self.path):
+        lines = []
+        if os.path.exists(self.path):
+            with open(self.path) as f:
+                lines = f.readlines()
+            if not self.keep:
+                os.remove(self.path)
+        if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
         sms, maxs, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in open(self.path):
+        for line in lines:
             parts = [p.strip() for p in line.split(",")]
             if len(parts) < 9:
                 continue

@@ -49,3 +49,16 @@ def test_flops_per_cell(bench):
     scale = 2 * (N + 1)                                  # e_n times each coupling sum
     assert bench.flops_per_cell(N, d) == 2 * (toeplitz + hankel + scale + N + d) == 336
     assert bench.tape_adjoint_flops_per_cell(N) == 584
+
+
+def test_clock_samples_are_summarised_and_the_temporary_file_removed(bench, monkeypatch):
+    monkeypatch.delenv("SK_CLOCKS_CSV", raising=False)
+    c = bench.ClockSampler(0)
+    c.proc = object()  # as if nvidia-smi had run: summarise what it wrote
+    with open(c.path, "w") as f:
+        f.write("0, 1965, 2070, 900.1, 0x0000000000000004, Not Active, Not Active, Not Active, Active\n"
+                "0, 1980, 2070, 950.0, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active\n"
+                "0, [N/A], 2070, 950.0, 0x0, Not Active, Not Active, Not Active, Not Active\n")
+    s = c.summary()
+    assert s == {"sm_mhz": 1972.5, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"], "samples": 2}
+    assert not os.path.exists(c.path)
