@@ -6,28 +6,37 @@ increments N(0, 1/256) per coordinate (seeds 3 and 4; other ranks use their own 
 with the polynomial approximation scheme of order 6 in the batched FP32 form (per-lane
 power-of-two exponents, FP64 endpoints and gradient accumulation).
 
-One step = forward Gram G = k_hat(X_a, Y_b) over all 16,384 pairs x 65,536 cells, then the
-adjoint: d(sum_ab W_ab G_ab)/dX and /dY for a fixed seeded upstream gradient W.
+One step = forward Gram G = k_hat(X_a, Y_b) over all 16,384 pairs x 65,536 cells, recording the
+tape the adjoint reads, then the adjoint: d(sum_ab W_ab G_ab)/dX and /dY for a fixed seeded
+upstream gradient W.
 Metric: Goursat cell-updates per second of the fwd+bwd step, counting each of the Gram's
 1.07e9 cells once (value = cells / step time), plus the step's milliseconds.
 Timing: per-step CUDA events on the launching stream; a 256 MiB buffer is written between
 steps (outside the events) so every step starts with a cold L2.
 
-Also reported: the forward-only rate, the FP64 plain wavefront of the same Gram, the roofline of
-the dominant kernel (the adjoint, FP32 ALU bound), the end-to-end rate through the public API
-with host buffers, and the CPU oracle on a bounded sample.  ``--impl reference`` times the CPU
-oracle alone.
+Also reported (parts, --parts): the public sigkernel_backward and autograd paths, the forward
+alone, the FP64 plain wavefront forward and fwd+bwd, the end-to-end rate through the public API
+with host buffers, the single-pair latency of the plain method, the FD schemes on the same Gram,
+the oscillatory, long-pair, uneven-batch and MMD workloads, the accuracy study, and the CPU
+oracle.  Roofline fractions divide by peaks measured in the same run: the FP32 / FP64 FMA rate
+(sigkernel_fma_peak) and the HBM copy bandwidth of MEASURED_PEAKS.json.
+
+The FP64 oracle runs only in the CPU-baseline leg (`cpu` part), on rank 0: it computes the
+sampled outputs that every GPU part kept, which gives each part's MAPE against the oracle, and
+its own timing is the CPU baseline.  ``--impl reference`` times the CPU oracle alone.
 """
 from __future__ import annotations
 
 import argparse
 import json
 import os
+import socket
 import statistics
 import subprocess
 import sys
 import tempfile
 import time
+from math import factorial
 
 import numpy as np
 
@@ -40,10 +49,11 @@ D = 8
 DEGREE = 6
 CELLS_PER_PAIR = (L - 1) * (L - 1)
 CELLS = NX * NY * CELLS_PER_PAIR
-PARTS = ("f32", "ckpt", "fwd", "f64", "e2e", "osc", "long", "uneven", "mmd", "acc", "cpu")
-SM_COUNT = 152
-FP32_LANES = 128
-SM_MAX_MHZ = 2070.0
+PARTS = ("f32", "api", "fwd", "f64", "e2e", "single", "gram_fd", "osc", "long", "uneven", "mmd", "acc", "cpu")
+METRIC = ("Goursat cell-updates/s of the fwd+bwd Gram step (polynomial approximation N=6, 128x128 Gram of "
+          "257-point paths, d=8)")
+FALLBACK_HBM_GBS = 6800.0  # the profiling recipe's fallback when MEASURED_PEAKS.json is absent
+SM_COUNT, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0  # nominal, for context only
 
 
 def flops_per_cell(N: int, d: int) -> int:
@@ -54,23 +64,28 @@ def flops_per_cell(N: int, d: int) -> int:
     return 2 * fma
 
 
-def adjoint_core_fma(N: int) -> int:
-    """Multiply-adds of one cell's adjoint map: weights 2(N+1), Toeplitz transposes (N+1)(N+2),
-    Hankel couplings 2N(N+1), and dk/dM with its recomputed Hankel sums 3N^2 + 4N."""
-    return 2 * (N + 1) + (N + 1) * (N + 2) + 2 * N * (N + 1) + 3 * N * N + 4 * N
+def tape_forward_flops_per_cell(N: int, d: int) -> int:
+    """The forward cell plus the 2N derivatives d a'_n/dM, d b'_n/dM it records on the tape
+    (one multiply-add each)."""
+    return flops_per_cell(N, d) + 2 * 2 * N
+
+
+def adjoint_edge_fma(N: int) -> int:
+    """Multiply-adds of one cell's edge adjoints: Hankel weights 2(N+1), Toeplitz transposes
+    (N+1)(N+2), Hankel couplings 2N(N+1)."""
+    return 2 * (N + 1) + (N + 1) * (N + 2) + 2 * N * (N + 1)
 
 
 def tape_adjoint_flops_per_cell(N: int) -> int:
-    """Algorithmic FLOPs of one cell of the tape adjoint kernel (2 per multiply-add): the adjoint
-    map plus the N terms of e_m = M^m/m! rebuilt from the recorded M.  The forward cell is not
-    recomputed and the d-term contractions run in the separate contraction kernel."""
-    return 2 * (adjoint_core_fma(N) + N)
+    """Algorithmic FLOPs of one cell of the tape adjoint kernel (2 per multiply-add): the edge
+    adjoints, dk/dM from the 2N recorded derivatives, and the N terms of e_m = M^m/m! rebuilt from
+    the recorded M.  The d-term contractions run in the separate contraction kernel."""
+    return 2 * (adjoint_edge_fma(N) + 2 * N + N)
 
 
-def contract_bytes_per_cell(esize: int = 4) -> int:
-    """Algorithmic DRAM bytes per cell of the contraction kernel: one dk/dM element read (the
-    increments it multiplies are re-read from L1/L2 and counted per pair, not per cell)."""
-    return esize
+def tape_row_bytes(N: int, esize: int = 4) -> int:
+    """One lane's tape row of the approximation scheme: 2N derivatives, the exponent and M."""
+    return (2 * N + 2) * esize
 
 
 def tape_steps(points: int) -> int:
@@ -81,19 +96,31 @@ def tape_steps(points: int) -> int:
     return (nstrips - 1) * max(cols, 32) + (rows - 1 - 32 * (nstrips - 1)) + cols
 
 
-def tape_adjoint_bytes(pairs: int, points: int, N: int = DEGREE) -> int:
+def tape_forward_bytes(pairs: int, points: int, N: int = DEGREE, esize: int = 4) -> int:
+    """Algorithmic DRAM bytes the tape forward writes: one row per lane per warp step."""
+    return pairs * tape_steps(points) * 32 * tape_row_bytes(N, esize)
+
+
+def tape_adjoint_bytes(pairs: int, points: int, N: int = DEGREE, esize: int = 4) -> int:
     """Algorithmic DRAM bytes of one tape-adjoint launch: each warp step reads a 32-lane tape step
-    (a, b, exponent, M padded to 16 B per lane) and writes 32 dk/dM values."""
-    row = ((2 * (N + 1) + 2) * 4 + 15) // 16 * 16
-    return pairs * tape_steps(points) * 32 * (row + 4)
+    and writes 32 dk/dM values."""
+    return pairs * tape_steps(points) * 32 * (tape_row_bytes(N, esize) + esize)
 
 
-# DRAM traffic of bwd_tape_kernel<float,6> per launch from one ncu capture on 64x64 pairs of
-# 129-point paths (read 4.605319 GB + write 0.333258 GB), as a multiple of that launch's
-# algorithmic bytes.  The traffic scales with the tape, so the bench launch's traffic is this ratio
-# times its own algorithmic bytes.  Valid only while the kernel is unchanged since that capture.
-NCU_TAPE_TRAFFIC_RATIO = (4.605319e9 + 0.333258e9) / tape_adjoint_bytes(64 * 64, 129)
-HBM_GBS = 6681.2  # measured copy bandwidth of this GB300 pool
+def load_hbm_peak():
+    """(GB/s, source): the measured copy bandwidth of MEASURED_PEAKS.json, else the fallback."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            v = float(json.load(f)["hbm_gbs"])
+        return v, "measured (MEASURED_PEAKS.json copy bandwidth)"
+    except (OSError, ValueError, KeyError, TypeError):
+        return FALLBACK_HBM_GBS, "fallback (profiling recipe, MEASURED_PEAKS.json absent)"
+
+
+# DRAM traffic (ncu dram__bytes_read.sum + dram__bytes_write.sum) of one launch, as a multiple of
+# that launch's algorithmic bytes, from captures of the current kernels (see profiles/); None when
+# no capture of the current kernel exists.
+NCU_TRAFFIC_RATIO = {"bwd_tape_kernel<float,6,false>": None, "fwd_poly_kernel<float,6,6,false,1,false,true>": None}
 
 
 def parse():
@@ -108,15 +135,34 @@ def parse():
     ap.add_argument("--len", type=int, default=L,
                     help="points per path (shorter paths, for profiling runs that must hold only a few GB)")
     ap.add_argument("--parts", default=",".join(PARTS),
-                    help="comma list: f32 (headline fwd+bwd step), ckpt (checkpointing adjoint), fwd (forward "
-                         "only), f64 (FP64 forward), e2e, osc (oscillatory pairs), long (one pair of 16385-point paths), "
-                         "uneven (uneven batch), mmd "
-                         "(MMD^2 fwd+bwd, permutation test), acc (accuracy report: MAPE per order / refinement), cpu")
+                    help="comma list: f32 (headline fwd+bwd step), api (sigkernel_backward, autograd, checkpointing "
+                         "adjoint), fwd (forward only), f64 (FP64 forward and fwd+bwd), e2e, single (one pair of "
+                         "33-point paths), gram_fd (FD schemes on the Gram), osc (oscillatory pairs), long (one pair "
+                         "of 16385-point paths), uneven (uneven batch), mmd (MMD^2 fwd+bwd, permutation test), acc "
+                         "(accuracy report), cpu (the oracle: CPU baseline and every part's MAPE)")
     args = ap.parse_args()
     args.parts = set(args.parts.split(","))
     if args.no_cpu_baseline:
         args.parts.discard("cpu")
     return args
+
+
+def _free_port() -> int:
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def ensure_world(args) -> None:
+    """--gpus N without a launcher: start N ranks with torch.distributed.run on this node (and
+    exit with their status).  Under a launcher, WORLD_SIZE must equal N."""
+    world = os.environ.get("WORLD_SIZE")
+    if world is None and args.gpus > 1:
+        cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", f"--nproc-per-node={args.gpus}",
+               "--master-addr=127.0.0.1", f"--master-port={_free_port()}", os.path.abspath(__file__)] + sys.argv[1:]
+        sys.exit(subprocess.call(cmd))
+    if world is not None and int(world) != args.gpus:
+        sys.exit(f"bench.py: --gpus {args.gpus} but WORLD_SIZE={world}")
 
 
 def max_over_ranks(ms: float, dist, device) -> float:
@@ -152,6 +198,8 @@ class ClockSampler:
     def __init__(self, index: int):
         self.index = index
         self.proc = None
+        self.f = None
+        self.error = None
         # SK_CLOCKS_CSV keeps the raw samples where the caller wants them; else a temporary file,
         # removed once summarised
         self.keep = bool(os.environ.get("SK_CLOCKS_CSV"))
@@ -160,13 +208,19 @@ class ClockSampler:
 
     def __enter__(self):
         try:
-            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            parent = os.path.dirname(self.path)
+            if parent:
+                os.makedirs(parent, exist_ok=True)
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.QUERY}",
                                           "--format=csv,noheader,nounits", "-lms", "200"],
                                          stdout=self.f, stderr=subprocess.DEVNULL)
-        except (OSError, FileNotFoundError):
+        except OSError as e:
+            self.error = f"{type(e).__name__}: {e}"
             self.proc = None
+            if self.f is not None:
+                self.f.close()
+                self.f = None
         return self
 
     def __exit__(self, *exc):
@@ -176,7 +230,9 @@ class ClockSampler:
                 self.proc.wait(timeout=5)
             except subprocess.TimeoutExpired:
                 self.proc.kill()
+        if self.f is not None:
             self.f.close()
+            self.f = None
 
     def summary(self):
         lines = []
@@ -186,7 +242,7 @@ class ClockSampler:
             if not self.keep:
                 os.remove(self.path)
         if self.proc is None:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [f"no samples: {self.error or 'nvidia-smi'}"]}
         sms, maxs, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for line in lines:
@@ -206,6 +262,9 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sms)}
 
 
+# ---------------------------------------------------------------------------------------------
+# The CPU oracle (only here and in the reference arm).
+# ---------------------------------------------------------------------------------------------
 def cpu_fwd_bwd(X, Y, points=L):
     """The FP64 oracle as it stands on one pair (prefixes of `points` points): the forward scheme
     and its complex-step gradient with respect to both paths.  Returns (cells, seconds)."""
@@ -218,25 +277,50 @@ def cpu_fwd_bwd(X, Y, points=L):
     return (points - 1) ** 2, time.perf_counter() - t0
 
 
-def cpu_baseline(X, Y, budget_pairs=48):
-    """The FP64 oracle as it stands, on bounded samples of the step: one full pair forward +
-    gradient (the headline unit), and the first budget_pairs^2 pairs forward only."""
+def oracle_samples(samples):
+    """Runs the oracle on every part's sampled pairs.  `samples` maps a part's name to a dict with
+    the paths xs, ys (lists of float64 arrays: the exact numbers the GPU saw), the pairs pa, pb,
+    the scheme, N, lambda and the GPU values `gpu` (one per pair, or a dict of several columns);
+    returns ({name: MAPE dict}, oracle seconds, oracle cells)."""
     import oracle
     cores = os.cpu_count() or 1
+    out, secs, cells = {}, 0.0, 0.0
+    for name, s in samples.items():
+        t0 = time.perf_counter()
+        ref = oracle.pairs(s["xs"], s["ys"], s["pa"], s["pb"], s["scheme"], s["N"], s["lam"], threads=cores)
+        secs += time.perf_counter() - t0
+        cells += float(sum((len(s["xs"][a]) - 1) * (len(s["ys"][b]) - 1) for a, b in zip(s["pa"], s["pb"])))
+        gpu = s["gpu"] if isinstance(s["gpu"], dict) else {"value": s["gpu"]}
+        keep = np.abs(ref) >= 1e-3  # relative error is not defined near a zero of the kernel
+        m = {}
+        for col, g in gpu.items():
+            rel = np.abs(np.asarray(g, dtype=np.float64) - ref)[keep] / np.abs(ref[keep])
+            m[col] = {"mape": float(rel.mean()) if rel.size else None,
+                      "max_rel": float(rel.max()) if rel.size else None}
+        m["pairs"] = int(len(ref))
+        if not keep.all():
+            m["excluded_near_zero"] = int((~keep).sum())
+        m["scheme"] = f"{s['scheme']} N={s['N']} lambda={s['lam']}"
+        out[name] = m
+    return out, secs, cells
+
+
+def cpu_baseline(X, Y, samples):
+    """The FP64 oracle as it stands, timed on the host cores: fwd+bwd of one full pair (the
+    headline unit: forward scheme and complex-step gradient), and the forward rate over every
+    part's sampled pairs, which also gives each part's MAPE against the oracle."""
+    cores = os.cpu_count() or 1
     cells, dt = cpu_fwd_bwd(X, Y)
-    n = budget_pairs
-    t0 = time.perf_counter()
-    oracle.gram(list(X[:n]), list(Y[:n]), "approx", DEGREE, 0, threads=cores)
-    dtf = time.perf_counter() - t0
+    mape, secs, fcells = oracle_samples(samples)
     return {"value": cells / dt, "unit": "cell-updates/s", "cores": cores, "kind": "oracle",
             "sample": f"fwd+bwd of 1 pair (257 points, d=8, {dt:.1f} s: forward scheme + complex-step gradient "
                       f"of both paths, threads over coordinates)",
-            "forward_only": {"value": n * n * CELLS_PER_PAIR / dtf, "unit": "cell-updates/s",
-                             "sample": f"{n}x{n} pairs of the Gram, {dtf:.2f} s"}}
+            "forward_only": {"value": fcells / secs if secs > 0 else None, "unit": "cell-updates/s",
+                             "sample": f"the sampled pairs of every part ({fcells:.3g} cells, {secs:.1f} s, threads "
+                                       f"over pairs)"}}, mape
 
 
 def run_reference(args, rank, world):
-    import torch.distributed as dist
     if rank != 0:
         return
     X, Y = workload(0)
@@ -249,23 +333,26 @@ def run_reference(args, rank, world):
         cells += c
         secs += t
     value = cells / secs
-    ms = CELLS / value * 1e3
-    sample = "per step: fwd + complex-step gradient of one pair of 129-point prefixes (128x128 cells)"
-    line = {"impl": "reference",
-            "metric": "Goursat cell-updates/s of the fwd+bwd Gram step (polynomial approximation N=6, 128x128 Gram)",
+    sample = ("each step: fwd + complex-step gradient of one pair of 129-point prefixes of the workload's first pair "
+              "(16,384 cells), threads over coordinates")
+    line = {"impl": "reference", "metric": METRIC,
             "value": value, "unit": "cell-updates/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": "gram128: 128x128 Brownian paths, 257 points, d=8",
-                                            "sample": sample, "l2": "n/a (CPU)"},
+            "ms_per_step": secs / args.steps * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "gram128: X, Y = 128 Brownian paths each, 257 points, d=8, N(0,1/256) increments",
+                       "sample": sample, "l2": "n/a (CPU)"},
             "cpu_baseline": {"value": value, "unit": "cell-updates/s", "cores": cores, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": value, "unit": "cell-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
-    del dist
 
 
+# ---------------------------------------------------------------------------------------------
+# The GPU arm.
+# ---------------------------------------------------------------------------------------------
 def main():
     args = parse()
+    ensure_world(args)
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
@@ -293,23 +380,45 @@ def main():
     Yt = torch.tensor(Y, device=dev)
     G = torch.empty(nx, nx, dtype=torch.float64, device=dev)
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
-
     Wt = torch.tensor(np.random.default_rng(11 + rank).standard_normal((nx, nx)), device=dev)
     opts = dict(scheme="approx", degree=DEGREE, sort=False)
+    rng = np.random.default_rng(0)
+    samples = {}  # part -> sampled pairs and GPU values, for the oracle leg
+
+    def sample_gram(name, Gm, n=64, scheme="approx", N=DEGREE, lam=0, Xs=X, Ys=Y, extra=None):
+        pa = rng.integers(0, Gm.shape[0], n)
+        pb = rng.integers(0, Gm.shape[1], n)
+        g = Gm.cpu().numpy()[pa, pb]
+        gpu = {"value": g}
+        if extra:
+            gpu.update({k: v.cpu().numpy()[pa, pb] for k, v in extra.items()})
+        samples[name] = dict(xs=list(Xs), ys=list(Ys), pa=pa, pb=pb, scheme=scheme, N=N, lam=lam, gpu=gpu)
+
+    # measured peaks: FP32 / FP64 FMA rates (this run, with their clocks) and the HBM copy bandwidth
+    with ClockSampler(local) as pclk:
+        p32 = max(sk.fma_peak("f32", packed=False), sk.fma_peak("f32", packed=True))
+        p64 = sk.fma_peak("f64")
+    hbm_peak, hbm_src = load_hbm_peak()
+    peaks = {"fp32_tflops": p32, "fp64_tflops": p64, "hbm_gbs": hbm_peak, "hbm_source": hbm_src,
+             "fma_source": "sigkernel_fma_peak: independent FMA chains (FP32 scalar and two-wide, the faster), 4 x 384 "
+                           "threads per SM, fastest of 5 launches, CUDA events",
+             "fma_clocks": pclk.summary(),
+             "fp32_nominal_tflops": SM_COUNT * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12}
 
     tape_buf = [None]
 
-    def run(compute, steps, warmup, backward=True, tape=True):
+    def run(compute, steps, warmup, backward=True, tape=True, Xa=Xt, Ya=Yt, Wa=Wt, out=G):
         """Timed fwd(+bwd) steps; returns per-step ms, forward-kernel ms, adjoint-kernel ms, wall s.
-        With `tape` the forward records the cell inputs and the adjoint replays them."""
-        ws = sk.gram_workspace(Xt, Yt, scheme="approx", degree=DEGREE, compute=compute)
+        With `tape` the forward records the tape and the adjoint replays it; without it the backward
+        is the public sigkernel_backward."""
+        ws = sk.gram_workspace(Xa, Ya, scheme="approx", degree=DEGREE, compute=compute)
 
         def step(timed):
             if backward and tape:
-                _, tape_buf[0] = sk.sigkernel_forward_tape(Xt, Yt, compute=compute, workspace=ws, out=G,
+                _, tape_buf[0] = sk.sigkernel_forward_tape(Xa, Ya, compute=compute, workspace=ws, out=out,
                                                            tape=tape_buf[0], time_kernel=timed, **opts)
             else:
-                sk.sigkernel_gram(Xt, Yt, compute=compute, workspace=ws, out=G, time_kernel=timed, **opts)
+                sk.sigkernel_gram(Xa, Ya, compute=compute, workspace=ws, out=out, time_kernel=timed, **opts)
             kf = sk.last_kernel_ms() if timed else None
             kb = None
             ev = None
@@ -318,10 +427,10 @@ def main():
                     ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
                     ev[0].record()
                 if tape:
-                    sk.sigkernel_backward_tape(tape_buf[0], Wt, Xt, Yt, compute=compute, time_kernel=timed, **opts)
+                    sk.sigkernel_backward_tape(tape_buf[0], Wa, Xa, Ya, compute=compute, time_kernel=timed, **opts)
+                    kb = sk.last_kernel_ms() if timed else None
                 else:
-                    sk.sigkernel_backward(Wt, Xt, Yt, compute=compute, time_kernel=timed, **opts)
-                kb = sk.last_kernel_ms() if timed else None
+                    sk.sigkernel_backward(Wa, Xa, Ya, compute=compute, **opts)
                 if timed:
                     ev[1].record()
             return kf, kb, ev
@@ -354,90 +463,155 @@ def main():
         run.backward_call_ms = bc_ms
         return step_ms, kf_ms, kb_ms, wall
 
-    line = {}
-    fpc = flops_per_cell(DEGREE, D)
-    bpc = tape_adjoint_flops_per_cell(DEGREE)
-    peak = SM_COUNT * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
-    import oracle
-    rng = np.random.default_rng(0)
-    pa = rng.integers(0, nx, 16)
-    pb = rng.integers(0, nx, 16)
+    def kernel_roofline(name, ms, flops, bytes_, peak_tflops, ratio_key=None):
+        """ALU and HBM fractions of one kernel launch; `bound` is the larger of the two."""
+        alu = flops / (ms / 1e3) / 1e12
+        hbm = bytes_ / (ms / 1e3) / 1e9
+        fa, fh = alu / peak_tflops, hbm / hbm_peak
+        ratio = NCU_TRAFFIC_RATIO.get(ratio_key) if ratio_key else None
+        r = {"kernel": name, "kernel_ms": ms, "alu_tflops": alu, "alu_frac": fa, "hbm_gbs": hbm, "hbm_frac": fh,
+             "algorithmic_bytes": bytes_, "algorithmic_flops": flops,
+             "traffic": ratio * bytes_ if ratio is not None else None}
+        if fh > fa:
+            r.update({"bound": "hbm", "achieved": hbm, "peak": hbm_peak, "unit": "GB/s", "frac": fh})
+        else:
+            r.update({"bound": "alu", "achieved": alu, "peak": peak_tflops, "unit": "TFLOP/s", "frac": fa})
+        return r
 
-    # headline: fwd + bwd step, batched FP32 form
+    line = {}
+    # headline: fwd + bwd step, batched FP32 form, forward tape
     with ClockSampler(local) as clk:
         step_ms, kf_ms, kb_ms, wall = run("f32", args.steps, max(args.warmup, 3))
     clocks = clk.summary()
     total_ms = max_over_ranks(float(sum(step_ms)), dist, dev)
     ms_per_step = total_ms / args.steps
     value = job_throughput(cells, world, args.steps, total_ms)
-    g32 = G.cpu().numpy()[pa, pb]
+    sample_gram("f32", G)
     status = sk.device_status()
     kf = statistics.mean(kf_ms)
     kb = statistics.mean(kb_ms)
     bcall = statistics.mean(run.backward_call_ms) if run.backward_call_ms else None
-    ach_b = bpc * cells / (kb / 1e3) / 1e12
-    ach_f = fpc * cells / (kf / 1e3) / 1e12
-    ref = oracle.pairs(list(X), list(Y), pa, pb, "approx", DEGREE)
-    mape = {"f32": float(np.mean(np.abs(g32 - ref) / np.abs(ref))), "sample": "16 sampled Gram entries"}
+    tape_gb = tape_buf[0].numel() / 1e9
+    fwd_rl = kernel_roofline("fwd_poly_kernel<float,6,6,false,1,false,true> (forward recording the tape)", kf,
+                             tape_forward_flops_per_cell(DEGREE, D) * cells, tape_forward_bytes(nx * nx, npts), p32,
+                             "fwd_poly_kernel<float,6,6,false,1,false,true>")
+    bwd_rl = kernel_roofline("bwd_tape_kernel<float,6,false> (adjoint wavefront from the tape)", kb,
+                             tape_adjoint_flops_per_cell(DEGREE) * cells, tape_adjoint_bytes(nx * nx, npts), p32,
+                             "bwd_tape_kernel<float,6,false>")
+    dominant = bwd_rl if kb >= kf else fwd_rl
+    roofline = {k: dominant[k] for k in ("bound", "achieved", "peak", "unit", "frac", "traffic")}
+    roofline.update({"kernel": dominant["kernel"], "kernel_ms": dominant["kernel_ms"],
+                     "peak_source": "measured in this run: " + ("sigkernel_fma_peak FP32" if dominant["unit"] == "TFLOP/s"
+                                                                else hbm_src),
+                     "alu_frac": dominant["alu_frac"], "hbm_frac": dominant["hbm_frac"],
+                     "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum, per launch" if
+                     dominant["traffic"] is not None else "no ncu capture of the current kernel"})
     line.update({
-        "metric": "Goursat cell-updates/s of the fwd+bwd Gram step (polynomial approximation N=6, 128x128 Gram, "
-                  "batched FP32, forward tape)",
+        "metric": METRIC,
         "value": value, "unit": "cell-updates/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32", "data": "synthetic",
         "config": {"workload": f"gram{nx}: X, Y = {nx} Brownian paths each, {npts} points, d=8, N(0,1/{npts - 1}) "
-                               "increments; "
-                               "step = forward Gram + adjoint for a seeded upstream gradient",
+                               "increments; step = forward Gram recording the tape + adjoint for a seeded upstream "
+                               "gradient",
                    "scheme": "polynomial approximation", "degree": DEGREE, "dyadic": 0,
                    "cells_per_step": cells, "pairs_per_step": nx * nx,
                    "l2": "256 MiB buffer written between timed steps (outside the events)",
-                   "tape_gb": round(tape_buf[0].numel() / 1e9, 2),
+                   "tape_gb": round(tape_gb, 2),
                    "parallelism": f"weak scaling, one independent {nx}x{nx} Gram per GPU ({world} GPUs)"},
-        "roofline": {"bound": "alu", "achieved": ach_b, "peak": peak, "unit": "TFLOP/s", "frac": ach_b / peak,
-                     "traffic": NCU_TAPE_TRAFFIC_RATIO * tape_adjoint_bytes(nx * nx, npts),
-                     "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one 64x64x129-point "
-                                       "launch, scaled by algorithmic tape bytes to this launch",
-                     "algorithmic_bytes": tape_adjoint_bytes(nx * nx, npts),
-                     "hbm_gbs": tape_adjoint_bytes(nx * nx, npts) / (kb / 1e3) / 1e9,
-                     "hbm_frac_of_measured": tape_adjoint_bytes(nx * nx, npts) / (kb / 1e3) / 1e9 / HBM_GBS,
-                     "kernel": "bwd_tape_kernel<float,6> (adjoint wavefront from the tape)",
-                     "kernel_ms": kb,
-                     "flops_per_cell": bpc,
-                     "peak_source": "152 SMs x 128 FP32 lanes x 2 FLOP x 2070 MHz (derived, nominal clocks)"},
-        "forward_kernel": {"kernel": "fwd_poly_kernel<float,6,6,false> (recording the tape)", "kernel_ms": kf,
-                           "achieved_tflops": ach_f,
-                           "frac": ach_f / peak, "flops_per_cell": fpc,
-                           "cell_updates_per_s": cells / (kf / 1e3)},
-        "backward_call": {"ms": bcall, "adjoint_kernel_ms": kb,
-                          "rest_ms": (bcall - kb) if bcall is not None else None,
-                          "rest": "increments, dk/dM contraction kernel, gradient conversions"},
+        "roofline": roofline,
+        "kernels": {"forward_tape": fwd_rl, "adjoint": bwd_rl,
+                    "backward_call": {"ms": bcall, "adjoint_kernel_ms": kb,
+                                      "rest_ms": (bcall - kb) if bcall is not None else None,
+                                      "rest": "increments, dk/dM contraction kernel, gradient conversions"}},
+        "peaks": peaks,
         # forward: 2 increments + wavefront; adjoint: 2 increments + adjoint + contraction + 2 gradient conversions
         "gpu_launches": 9 * args.steps,
         "clocks": clocks, "device_status": status, "wall_s_timed_region": wall,
     })
-
-    if "ckpt" in args.parts:  # the same step with the checkpointing adjoint (no tape)
-        sc, kfc, kbc, _ = run("f32", max(2, min(3, args.steps)), 1, tape=False)
-        line["checkpoint_adjoint"] = {"value": cells / (statistics.mean(sc) / 1e3), "unit": "cell-updates/s",
-                                      "ms_per_step": statistics.mean(sc), "forward_kernel_ms": statistics.mean(kfc),
-                                      "adjoint_kernel_ms": statistics.mean(kbc)}
     tape_buf[0] = None
     torch.cuda.empty_cache()
 
+    if "api" in args.parts:
+        # the public sigkernel_backward (chunked tapes: re-runs the forward) after a plain forward,
+        # the autograd wrapper, and the checkpointing adjoint
+        sa, _, _, _ = run("f32", max(2, min(3, args.steps)), 1, tape=False)
+        api = {"sigkernel_backward": {"step_ms": statistics.mean(sa),
+                                      "backward_call_ms": statistics.mean(run.backward_call_ms),
+                                      "cell_updates_per_s": cells / (statistics.mean(sa) / 1e3),
+                                      "what": "forward Gram, then sigkernel_backward (forward tapes in chunks of "
+                                              "<= 48 GiB and the tape adjoint after each)"}}
+        kern = sk.SigKernel("approx", DEGREE, 0, "f32")
+        Xg = Xt.clone().requires_grad_(True)
+        Yg = Yt.clone().requires_grad_(True)
+
+        def ag_step():
+            Gg = kern.gram(Xg, Yg)
+            (Gg * Wt).sum().backward()
+        ms = []
+        for it in range(3 + 2):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            ag_step()
+            e1.record()
+            e1.synchronize()
+            if it >= 2:
+                ms.append(e0.elapsed_time(e1))
+            Xg.grad = Yg.grad = None
+        api["autograd"] = {"step_ms": statistics.mean(ms), "cell_updates_per_s": cells / (statistics.mean(ms) / 1e3),
+                           "what": "SigKernel(approx, 6, f32).gram(X, Y), (G * W).sum().backward(): the forward "
+                                   "keeps its tape (tape=None chooses it when it fits)"}
+        del Xg, Yg
+        torch.cuda.empty_cache()
+        ws = sk.gram_workspace(Xt, Yt, scheme="approx", degree=DEGREE, compute="f32")
+        ms = []
+        for it in range(2):
+            sk.sigkernel_gram(Xt, Yt, compute="f32", workspace=ws, out=G, **opts)
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            sk.sigkernel_backward(Wt, Xt, Yt, compute="f32", checkpoint=True, time_kernel=True, **opts)
+            e1.record()
+            e1.synchronize()
+            if it >= 1:
+                ms.append(e0.elapsed_time(e1))
+        api["checkpoint_adjoint"] = {"backward_call_ms": statistics.mean(ms), "adjoint_kernel_ms": sk.last_kernel_ms(),
+                                     "what": "sigkernel_backward with SK_FLAG_CHECKPOINT (no tape)"}
+        line["api"] = api
+        torch.cuda.empty_cache()
+
     if "fwd" in args.parts:  # forward only (the Gram alone)
         sf, kff, _, _ = run("f32", args.steps, 2, backward=False)
+        kfo = statistics.mean(kff)
         line["forward_only"] = {"value": cells / (statistics.mean(sf) / 1e3), "unit": "cell-updates/s",
-                                "ms_per_step": statistics.mean(sf), "kernel_ms": statistics.mean(kff)}
+                                "ms_per_step": statistics.mean(sf),
+                                "kernel": kernel_roofline("fwd_poly_kernel<float,6,6,false,1,false> (no tape)", kfo,
+                                                          flops_per_cell(DEGREE, D) * cells, 0, p32)}
 
-    if "f64" in args.parts:  # FP64 plain wavefront of the same Gram (a few steps)
-        s64, k64, _, _ = run("f64", max(2, min(3, args.steps)), 1, backward=False)
-        g64 = G.cpu().numpy()[pa, pb]
+    if "f64" in args.parts:  # FP64 plain wavefront: forward, and fwd+bwd from an FP64 tape
+        G64 = torch.empty_like(G)
+        s64, k64, _, _ = run("f64", max(2, min(3, args.steps)), 1, backward=False, out=G64)
         k64avg = statistics.mean(k64)
-        mape["f64"] = float(np.mean(np.abs(g64 - ref) / np.abs(ref)))
-        line["fp64_plain_wavefront"] = {"value": cells / (statistics.mean(s64) / 1e3), "unit": "cell-updates/s",
-                                        "kernel_ms": k64avg, "achieved_tflops": fpc * cells / (k64avg / 1e3) / 1e12,
-                                        "peak_tflops_nominal": 1.25}
-    line["mape_vs_fp64_oracle"] = mape
+        fb64, kf64, kb64, _ = run("f64", 2, 1, out=G64)
+        sample_gram("f64", G64)
+        line["fp64_plain_wavefront"] = {
+            "forward": {"value": cells / (statistics.mean(s64) / 1e3), "unit": "cell-updates/s",
+                        "ms_per_step": statistics.mean(s64),
+                        "kernel": kernel_roofline("fwd_poly_kernel<double,6,6,false,1,false>", k64avg,
+                                                  flops_per_cell(DEGREE, D) * cells, 0, p64)},
+            "fwd_bwd": {"value": cells / (statistics.mean(fb64) / 1e3), "unit": "cell-updates/s",
+                        "ms_per_step": statistics.mean(fb64), "tape_gb": round(tape_buf[0].numel() / 1e9, 2),
+                        "forward_kernel": kernel_roofline("fwd_poly_kernel<double,6,6,false,1,false,true>",
+                                                          statistics.mean(kf64),
+                                                          tape_forward_flops_per_cell(DEGREE, D) * cells,
+                                                          tape_forward_bytes(nx * nx, npts, esize=8), p64),
+                        "adjoint_kernel": kernel_roofline("bwd_tape_kernel<double,6,false>", statistics.mean(kb64),
+                                                          tape_adjoint_flops_per_cell(DEGREE) * cells,
+                                                          tape_adjoint_bytes(nx * nx, npts, esize=8), p64)}}
+        tape_buf[0] = None
+        del G64
+        torch.cuda.empty_cache()
 
     if "e2e" in args.parts:  # end to end through the public API with pinned host buffers
         Xh = torch.tensor(X).pin_memory()
@@ -493,12 +667,62 @@ def main():
             ms.append(e0.elapsed_time(e1))
         return statistics.mean(ms)
 
+    if "single" in args.parts:  # one pair of 33-point paths, d = 2, FP64: the plain method's latency
+        Xs1 = W.brownian(2, 33, 2, seed=1 + 1000 * rank)
+        Pa = torch.tensor(Xs1[:1], device=dev)
+        Pb = torch.tensor(Xs1[1:], device=dev)
+        i0 = torch.zeros(1, dtype=torch.int64, device=dev)
+        o1 = torch.empty(1, dtype=torch.float64, device=dev)
+        single = {"workload": "1 pair of 33-point Brownian paths, d=2, N(0,1/32) increments, FP64 (1,024 cells)"}
+        gpu = {}
+        for scheme, N, lam in (("approx", 4, 0), ("fd1", 2, 2), ("fd2", 2, 2)):
+            f = lambda: sk.sigkernel_pairs(Pa, Pb, i0, i0, scheme=scheme, degree=N, dyadic=lam, compute="f64", out=o1)
+            ms = timed_steps(f, 20, 3)
+            key = f"{scheme}_N{N}_lam{lam}" if scheme == "approx" else f"{scheme}_lam{lam}"
+            single[key] = {"us": ms * 1e3, "cell_updates_per_s": 1024 / (ms / 1e3)}
+            samples[f"single_{key}"] = dict(xs=[Xs1[0]], ys=[Xs1[1]], pa=[0], pb=[0], scheme=scheme, N=N, lam=lam,
+                                            gpu=o1.cpu().numpy().copy())
+        # 64 linear pairs x = s u, y = t v against the closed form 0F1(;1;<u,v>) = sum_n <u,v>^n/(n!)^2
+        Xl = W.linear(64, 33, 2, seed=2 + 1000 * rank)
+        Yl = W.linear(64, 33, 2, seed=3 + 1000 * rank)
+        il = torch.arange(64, dtype=torch.int64, device=dev)
+        gl = sk.sigkernel_pairs(torch.tensor(Xl, device=dev), torch.tensor(Yl, device=dev), il, il, degree=12,
+                                compute="f64").cpu().numpy()
+        u, v = Xl[:, -1, :], Yl[:, -1, :]
+        z = np.sum(u * v, axis=1)
+        exact = np.array([sum(zi ** n / float(factorial(n)) ** 2 for n in range(60)) for zi in z])
+        keep = np.abs(exact) >= 1e-3
+        single["linear_pairs_closed_form"] = {
+            "pairs": 64, "scheme": "approx N=12, FP64",
+            "max_abs_err": float(np.max(np.abs(gl - exact))),
+            "mape": float(np.mean(np.abs(gl - exact)[keep] / np.abs(exact[keep])))}
+        line["single_pair"] = single
+
+    if "gram_fd" in args.parts:  # the FD baseline on the same Gram beside the approximation scheme
+        fd = {"workload": f"gram{nx}, FD1 at dyadic refinement 0/2/4 (sub-cells x1/16/256), FP32 and FP64"}
+        Gf = torch.empty_like(G)
+        for scheme, lam, comp in (("fd1", 0, "f32"), ("fd1", 2, "f32"), ("fd1", 4, "f32"), ("fd2", 2, "f32"),
+                                  ("fd1", 0, "f64"), ("fd1", 2, "f64")):
+            wsf = sk.gram_workspace(Xt, Yt, scheme=scheme, dyadic=lam, compute=comp)
+            f = lambda: sk.sigkernel_gram(Xt, Yt, scheme=scheme, degree=2, dyadic=lam, compute=comp, workspace=wsf,
+                                          out=Gf, sort=False)
+            ms = timed_steps(f, 1 if lam == 4 else 3, 1)
+            key = f"{scheme}_lam{lam}_{comp}"
+            fd[key] = {"ms": ms, "cell_updates_per_s": cells / (ms / 1e3),
+                       "sub_cell_updates_per_s": cells * 4 ** lam / (ms / 1e3)}
+            sample_gram(f"gram_{key}", Gf, n=16, scheme=scheme, N=2, lam=lam)
+        line["gram_fd"] = fd
+        del Gf
+
     if "osc" in args.parts:  # 64 pairs of 1025-point oscillatory paths, d=4 (few long pairs: strip pipeline)
-        Xo = torch.tensor(W.oscillatory(64, 1025, 4, seed=5 + 1000 * rank), device=dev)
-        Yo = torch.tensor(W.oscillatory(64, 1025, 4, seed=6 + 1000 * rank), device=dev)
+        Xo_np = W.oscillatory(64, 1025, 4, seed=5 + 1000 * rank)
+        Yo_np = W.oscillatory(64, 1025, 4, seed=6 + 1000 * rank)
+        Xo = torch.tensor(Xo_np, device=dev)
+        Yo = torch.tensor(Yo_np, device=dev)
         io = torch.arange(64, dtype=torch.int64, device=dev)
         cells_o = 64 * 1024 * 1024
         osc = {"workload": "64 pairs, 1025 points on [0,1], d=4, sin(w t + phi) + N(0,1e-3), w ~ U(10,200)"}
+        so = rng.choice(64, 4, replace=False)  # pairs the oracle checks
         for scheme, N, lam, comp in (("interp", 8, 0, "f32"), ("interp", 8, 0, "f64"), ("fd1", 2, 0, "f32"),
                                      ("fd1", 2, 2, "f32"), ("fd1", 2, 4, "f32"), ("fd1", 2, 6, "f32"),
                                      ("fd2", 2, 4, "f32"), ("fd_implicit", 2, 4, "f32")):
@@ -508,23 +732,31 @@ def main():
             key = f"{scheme}{N if scheme == 'interp' else ''}_lam{lam}_{comp}"
             osc[key] = {"ms": t, "cell_updates_per_s": cells_o / (t / 1e3),
                         "sub_cell_updates_per_s": cells_o * 4 ** lam / (t / 1e3)}
-            if key == "interp8_lam0_f32":
-                o32 = o.clone()
-            if key == "interp8_lam0_f64":
-                osc["interp8_f32_mape_vs_fp64_gpu"] = float(((o32 - o).abs() / o.abs()).mean())
+            if lam <= 4:
+                oc = o.cpu().numpy()
+                samples[f"osc_{key}"] = dict(xs=list(Xo_np), ys=list(Yo_np), pa=so, pb=so, scheme=scheme, N=N,
+                                             lam=lam, gpu=oc[so])
         line["oscillatory"] = osc
         del Xo, Yo
 
     if "long" in args.parts:  # one pair of 16385-point paths, d=4: parallelism inside a single pair
-        Xl = torch.tensor(W.brownian(1, 16385, 4, seed=11 + 1000 * rank), device=dev)
-        Yl = torch.tensor(W.brownian(1, 16385, 4, seed=12 + 1000 * rank), device=dev)
+        Xl_np = W.brownian(1, 16385, 4, seed=11 + 1000 * rank)
+        Yl_np = W.brownian(1, 16385, 4, seed=12 + 1000 * rank)
+        Xl = torch.tensor(Xl_np, device=dev)
+        Yl = torch.tensor(Yl_np, device=dev)
         il = torch.zeros(1, dtype=torch.int64, device=dev)
         ol = torch.empty(1, dtype=torch.float64, device=dev)
         cells_l = 16384 * 16384
         t_grid = timed_steps(lambda: sk.sigkernel_pairs(Xl, Yl, il, il, compute="f32", out=ol), 2, 1)
+        # the oracle checks a pair of 4097-point prefixes, swept the same way (a ring of 8 blocks)
+        Xp, Yp = Xl[:, :4097].contiguous(), Yl[:, :4097].contiguous()
+        op = sk.sigkernel_pairs(Xp, Yp, il, il, compute="f32").cpu().numpy()
+        samples["long_prefix4097"] = dict(xs=[Xl_np[0, :4097]], ys=[Yl_np[0, :4097]], pa=[0], pb=[0],
+                                          scheme="approx", N=DEGREE, lam=0, gpu=op)
         line["long_pair"] = {"workload": "1 pair of 16385-point Brownian paths, d=4, approx N=6, FP32: the pair's "
                                          "512 strips swept by a ring of 32 co-resident 16-warp blocks",
-                             "cells": cells_l, "ms": t_grid, "cell_updates_per_s": cells_l / (t_grid / 1e3)}
+                             "cells": cells_l, "ms": t_grid, "cell_updates_per_s": cells_l / (t_grid / 1e3),
+                             "oracle_check": "a pair of 4097-point prefixes in the same grid strip pipeline"}
         del Xl, Yl
 
     if "uneven" in args.parts:  # 4096 pairs, lengths log-uniform in [64, 4096], d=16, BF16: autotuned + graph
@@ -546,6 +778,12 @@ def main():
             with torch.cuda.graph(graph, stream=gs):
                 sk.sigkernel_pairs(PX, PY, iu, iu, compute="f32", out=ou)
         t_graph = timed_steps(graph.replay, 3, 1)
+        graph.replay()
+        torch.cuda.synchronize()
+        su = rng.choice(4096, 16, replace=False)
+        samples["uneven"] = dict(xs=[W.round_bf16(Xs[k]) for k in su], ys=[W.round_bf16(Ys[k]) for k in su],
+                                 pa=np.arange(16), pb=np.arange(16), scheme="approx", N=DEGREE, lam=0,
+                                 gpu=ou.cpu().numpy()[su])
         line["uneven_batch"] = {
             "workload": "4096 pairs, lengths log-uniform in [64,4096], d=16, BF16 points, approx N=6, FP32 cells",
             "cells": cells_u, "autotuned_shape": shape, "ms": t_tuned,
@@ -554,9 +792,11 @@ def main():
         sk.autotune_clear()
         del PX, PY, graph
 
-    if "mmd" in args.parts:  # MMD^2 fwd+bwd: 256 + 256 paths, 513 points, d=32, FP32, checkpointing adjoint
-        Am = torch.tensor(W.brownian(256, 513, 32, seed=7 + 1000 * rank), device=dev)
-        Bm = torch.tensor(W.brownian(256, 513, 32, seed=8 + 1000 * rank, drift=0.5, vol=1.2), device=dev)
+    if "mmd" in args.parts:  # MMD^2 fwd+bwd: 256 + 256 paths, 513 points, d=32, FP32
+        Am_np = W.brownian(256, 513, 32, seed=7 + 1000 * rank)
+        Bm_np = W.brownian(256, 513, 32, seed=8 + 1000 * rank, drift=0.5, vol=1.2)
+        Am = torch.tensor(Am_np, device=dev)
+        Bm = torch.tensor(Bm_np, device=dev)
         cells_m = (256 * 257 // 2 * 2 + 256 * 256) * 512 * 512
         t_f = timed_steps(lambda: sk.sigkernel_mmd2(Am, Bm, degree=6, compute="f32"), 2, 1)
         t_fb = timed_steps(lambda: sk.sigkernel_mmd2(Am, Bm, degree=6, compute="f32", grads=True), 2, 1)
@@ -565,6 +805,14 @@ def main():
         out_t = torch.empty(1002, dtype=torch.float64, device=dev)
         t_test = timed_steps(lambda: sk.sigkernel_mmd2_test(Am, Bm, labels=labels, compute="f32", workspace=ws_t,
                                                             out=out_t), 2, 1)
+        # Gram entries of the three blocks, with the options sigkernel_mmd2 uses, for the oracle check
+        sa_, sb_ = rng.integers(0, 256, 16), rng.integers(0, 256, 16)
+        for name, P1, P2, n1, n2 in (("AB", Am, Bm, Am_np, Bm_np), ("AA", Am, Am, Am_np, Am_np),
+                                     ("BB", Bm, Bm, Bm_np, Bm_np)):
+            gm = sk.sigkernel_pairs(P1, P2, torch.tensor(sa_, device=dev), torch.tensor(sb_, device=dev),
+                                    degree=6, compute="f32").cpu().numpy()
+            samples[f"mmd_K{name}"] = dict(xs=list(n1), ys=list(n2), pa=sa_, pb=sb_, scheme="approx", N=6, lam=0,
+                                           gpu=gm)
         line["mmd2"] = {"workload": "256 + 256 paths, 513 points, d=32 (Brownian vs drift 0.5, vol 1.2), approx N=6, "
                                     "FP32, symmetric K_AA/K_BB + K_AB, tiled M; gradients from forward tapes in "
                                     "chunks of pairs (tape <= 48 GiB per chunk)",
@@ -572,7 +820,8 @@ def main():
                         "forward_cell_updates_per_s": cells_m / (t_f / 1e3),
                         "fwd_bwd_cell_updates_per_s": cells_m / (t_fb / 1e3),
                         "permutation_test_1000_ms": t_test,
-                        "permutation_test_p_value": out_t[1].item()}
+                        "permutation_test_p_value": out_t[1].item(),
+                        "oracle_check": "16 sampled entries of each Gram block through sigkernel_pairs"}
         del Am, Bm, ws_t
 
     if "acc" in args.parts and rank == 0:  # MAPE per order / refinement against a converged FP64 solution
@@ -589,7 +838,7 @@ def main():
 
     if rank == 0:
         if "cpu" in args.parts:
-            line["cpu_baseline"] = cpu_baseline(X, Y)
+            line["cpu_baseline"], line["mape_vs_fp64_oracle"] = cpu_baseline(X, Y, samples)
         print(json.dumps(line))
     if dist is not None:
         dist.barrier()

@@ -111,10 +111,14 @@ enum {
                                        more blocks, the pipelined polynomial forward spreads each
                                        ring over co-resident blocks (a cooperative launch; the
                                        results are the same bit for bit) */
-    SK_FLAG_NO_TILED_M = 128        /* forward, polynomial schemes in FP32: form each cell's M from
+    SK_FLAG_NO_TILED_M = 128,       /* forward, polynomial schemes in FP32: form each cell's M from
                                        its two increment rows.  By default, with d > 8, each warp
                                        first computes a strip's M_ij for all columns at once (the
                                        same values bit for bit) */
+    SK_FLAG_CHECKPOINT = 256        /* sigkernel_backward, approximation scheme: run the
+                                       checkpointing adjoint (no tape; its workspace grows with the
+                                       paths, not with the pair count) instead of the default
+                                       adjoint from chunked forward tapes */
 };
 
 typedef struct {
@@ -188,17 +192,22 @@ int sigkernel_gram(const sk_paths* X, const sk_paths* Y, int32_t d, int32_t dtyp
 /*
  * sigkernel_backward -- reverse-mode derivative of the discrete scheme (the paper defines no
  * gradient; this is the exact adjoint of the scheme's own arithmetic, run as a reverse
- * wavefront with checkpoints every few antidiagonals).
+ * wavefront).
  *   Pair-list mode (pair_a != NULL): grad_out[k] = dL/dk_hat(X_{pair_a[k]}, Y_{pair_b[k]}).
  *   Gram mode (pair_a == NULL): grad_out is [X->count][Y->count] row-major, dL/dG[a][b].
  *   grad_X  device double, same row layout as X->rows ([off[count]][d]): dL/d(row), added to
  *           the existing contents (the caller zeroes it first for a plain gradient); NULL skips.
  *   grad_Y  likewise for Y.  When Y is X (same rows pointer) both accumulate into the same
  *           buffer correctly if grad_X == grad_Y.
- * SK_POLY_APPROX runs the checkpointing adjoint (d <= 32).  SK_POLY_INTERP, which has no
- * checkpointing adjoint, records forward tapes in chunks of pairs (at most 48 GiB each, in the
- * workspace) and runs the tape adjoint after each chunk; paths so long that a chunk cannot fill
- * the GPU return SK_ERR_UNSUPPORTED.  The FD schemes return SK_ERR_UNSUPPORTED.
+ * Both polynomial schemes record forward tapes in chunks of pairs (at most 48 GiB each, in the
+ * workspace) and run the tape adjoint after each chunk (sigkernel_forward_tape and
+ * sigkernel_backward_tape below, one chunk at a time), so the call re-runs the forward sweep once.
+ * When the paths are so long that a chunk cannot fill the GPU, SK_POLY_APPROX runs the
+ * checkpointing adjoint instead (antidiagonal checkpoints every few steps, the forward cells
+ * replayed from them; d <= 32) and SK_POLY_INTERP, which has none, returns SK_ERR_UNSUPPORTED.
+ * SK_FLAG_CHECKPOINT asks for the checkpointing adjoint of SK_POLY_APPROX outright.  The FD
+ * schemes return SK_ERR_UNSUPPORTED.  Orders with an adjoint: 2..10 and 12 (approximation),
+ * 2..12 (interpolation).
  * Accumulation uses device atomics, so the last bits of the gradient can vary between runs.
  */
 int sigkernel_backward(const sk_paths* X, const sk_paths* Y, int32_t d, int32_t dtype,
@@ -207,18 +216,20 @@ int sigkernel_backward(const sk_paths* X, const sk_paths* Y, int32_t d, int32_t 
                        double* grad_Y, void* workspace, size_t workspace_bytes, void* stream);
 
 /*
- * Forward tape (polynomial schemes; the interpolation scheme for orders 2..12).  sigkernel_forward_tape
- * computes the same results as
- * sigkernel_pairs / sigkernel_gram (Gram mode when pair_a is NULL; `out` is then [X->count][Y->count]
- * and SK_FLAG_SYMMETRIC applies) and also records, in the caller's `tape`, every cell's inputs
- * (the two incoming edge coefficient vectors, their exponent and the cell's M) and the exponent
- * of each k_hat.  sigkernel_backward_tape then runs the adjoint from the tape without recomputing
- * the forward sweep; it writes every cell's dL/dM into its workspace and contracts that with the
- * increments in a second kernel.  Both calls must use the same X, Y, pair list, options and path
- * contents.
+ * Forward tape (polynomial schemes; approximation orders 2..10 and 12, interpolation orders
+ * 2..12).  sigkernel_forward_tape computes the same results as sigkernel_pairs / sigkernel_gram
+ * (Gram mode when pair_a is NULL; `out` is then [X->count][Y->count] and SK_FLAG_SYMMETRIC
+ * applies) and also records, in the caller's `tape`, what the adjoint needs of every cell and
+ * the exponent of each k_hat.  For SK_POLY_INTERP that is the cell's inputs (the two incoming
+ * edge coefficient vectors, their exponent and the cell's M: 2N+4 elements padded to 16 bytes);
+ * for SK_POLY_APPROX it is the derivatives of the cell's two outgoing edge vectors with respect
+ * to M (orders 1..N of each), their exponent and M: 2N+2 elements.  sigkernel_backward_tape then
+ * runs the adjoint from the tape without recomputing the forward sweep; it writes every cell's
+ * dL/dM into its workspace and contracts that with the increments in a second kernel.  Both
+ * calls must use the same X, Y, pair list, options and path contents.
  *   tape        device buffer, 256-byte aligned, caller-owned, >= sigkernel_tape_size() bytes;
- *               the size grows as npairs x (max_len << lambda)^2 x ~64 B (FP32) or ~128 B (FP64):
- *               about 70 GB for 16,384 pairs of 257-point paths in FP32.
+ *               the size grows as npairs x (max_len << lambda)^2 x (2N+2) elements (approximation):
+ *               about 61 GB for 16,384 pairs of 257-point paths at N = 6 in FP32.
  *   sigkernel_tape_size: `npairs` = -1 for a Gram; writes the bytes and returns SK_OK or SK_ERR_*.
  * The backward's workspace is sized with SK_OP_BACKWARD_TAPE; it holds one element per cell (4 B
  * in FP32, 8 B in FP64; about 4.4 GB for the Gram above).  Other arguments and the gradient
@@ -292,7 +303,8 @@ int sigkernel_mmd2(const sk_paths* A, const sk_paths* B, int32_t d, int32_t dtyp
  *            draws the relabellings (uniformly random permutations of the split, usually).
  *   nperm    0 <= nperm <= 2^24; na + nb <= 65536; na, nb >= 1 (>= 2 for the U-statistic)
  *   out      device double [2 + nperm]: out[0] = MMD^2 of the given split (A, B); out[1] = p-value
- *            (1 + #{p : out[2 + p] >= out[0]}) / (1 + nperm); out[2 + p] = MMD^2 under relabelling p.
+ *            (1 + #{p : out[2 + p] >= out[0]}) / (1 + nperm), NaN when any statistic is NaN;
+ *            out[2 + p] = MMD^2 under relabelling p.
  * Workspace: SK_OP_MMD2_TEST with npairs = nperm; it holds K ((na + nb)^2 doubles).  A statistic
  * depends only on K and its own relabelling (bitwise, for a given na + nb).
  */
@@ -320,6 +332,21 @@ size_t sigkernel_noalloc_capacity(void);
 const char* sigkernel_noalloc_last_error(void);
 
 /*
+ * sigkernel_fma_peak -- measures the multiply-add throughput of the current GPU and writes it to
+ * *tflops in TFLOP/s (2 FLOP per FMA).  The paper has no counterpart: this is a measurement
+ * utility whose result is the denominator of the roofline fractions of the ALU-bound wavefront
+ * kernels.  Every thread of 4 blocks per SM (384 threads each) runs independent chains
+ * v <- v * m + c; the kernel is launched once to warm up and then `reps` (1..100) times on
+ * `stream`, each timed with CUDA events, and the fastest launch counts.
+ *   compute  SK_COMPUTE_F32 or SK_COMPUTE_F64 (the FMA type)
+ *   packed   nonzero (FP32 only): the chains run through the two-wide FP32 instruction (two FMAs
+ *            per instruction)
+ * Synchronous: returns after the last launch has finished.  A few milliseconds per launch.  It
+ * changes no clock or other setting of the GPU: the figure is at whatever clock the GPU runs.
+ */
+int sigkernel_fma_peak(int32_t compute, int32_t packed, int32_t reps, double* tflops, void* stream);
+
+/*
  * sigkernel_device_status -- synchronises `stream`, reads and clears the device error word of
  * the current device, and returns SK_OK or the first recorded SK_ERR_* code.
  */
@@ -331,6 +358,17 @@ int sigkernel_device_status(void* stream);
  * thread (waits for the second event).  Returns -1 if no such call was made.
  */
 float sigkernel_last_kernel_ms(void);
+
+/*
+ * sigkernel_set_wait_limit -- how many times a strip-pipeline hand-off wait polls its progress word
+ * (each poll followed by a ~64 ns sleep) before it gives up: the warp then records
+ * SK_ERR_DEVICE_TIMEOUT in the device error word, finishes its sweep without waiting (that pair's
+ * result is then wrong) and the kernel returns normally.  0 restores the default, 2^20 polls.
+ * Process-wide; calls launched after it use the new limit.  The paper has no counterpart: this
+ * is a robustness facility (a caller that wants a stalled pipeline reported sooner, and the test
+ * of the timeout path).
+ */
+void sigkernel_set_wait_limit(uint32_t polls);
 
 /* Message describing the last non-SK_OK return on this host thread ("" if none). */
 const char* sigkernel_last_error(void);

@@ -1,6 +1,7 @@
 // Host side of the C ABI (include/sigkernel.h): argument checks, workspace layout, constant
 // tables, the increment and scheduling kernels, and dispatch to the wavefront kernels.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -20,6 +21,7 @@ __device__ int g_sk_error = 0;
 namespace {
 
 thread_local std::string t_last_error;
+std::atomic<uint32_t> g_wait_limit{0};  // sigkernel_set_wait_limit (0 = the kernels' default)
 thread_local cudaEvent_t t_ev0 = nullptr, t_ev1 = nullptr;
 thread_local bool t_timed = false;
 
@@ -212,7 +214,7 @@ int check_options(const sk_options* o, int32_t d, int32_t dtype) {
     if (o->warps_per_block != 0 && o->warps_per_block != 1 && o->warps_per_block != 2 && o->warps_per_block != 4)
         return fail(SK_ERR_UNSUPPORTED, "warps_per_block %d (this build: 0, 1, 2 or 4)", o->warps_per_block);
     if (o->flags & ~(SK_FLAG_SYMMETRIC | SK_FLAG_INCREMENTS | SK_FLAG_UNBIASED | SK_FLAG_NO_SORT | SK_FLAG_TIME_KERNEL |
-                     SK_FLAG_STRIP_PIPELINE | SK_FLAG_NO_STRIP_PIPELINE | SK_FLAG_NO_TILED_M))
+                     SK_FLAG_STRIP_PIPELINE | SK_FLAG_NO_STRIP_PIPELINE | SK_FLAG_NO_TILED_M | SK_FLAG_CHECKPOINT))
         return fail(SK_ERR_INVALID_ARG, "unknown flag bits 0x%x", o->flags);
     if ((o->flags & SK_FLAG_STRIP_PIPELINE) && (o->flags & SK_FLAG_NO_STRIP_PIPELINE))
         return fail(SK_ERR_INVALID_ARG, "SK_FLAG_STRIP_PIPELINE and SK_FLAG_NO_STRIP_PIPELINE together");
@@ -220,9 +222,10 @@ int check_options(const sk_options* o, int32_t d, int32_t dtype) {
 }
 
 // allow_coop: the caller launches p.kern itself with p.threads (the plain forward); adjoint
-// plans reuse this layout with their own one-warp-per-pair kernels and pass false.
+// plans reuse this layout with their own one-warp-per-pair kernels and pass false.  tape: the
+// forward records a tape (one warp per pair; its own kernels for the approximation scheme).
 int plan_forward(const sk_paths* X, const sk_paths* Y, int32_t d, int32_t dtype, const sk_options* o,
-                 int mode, int64_t npairs, Plan& p, bool allow_coop = false) {
+                 int mode, int64_t npairs, Plan& p, bool allow_coop = false, bool tape = false) {
     int rc;
     if ((rc = check_options(o, d, dtype)) != SK_OK) return rc;
     if ((rc = check_paths(X, "X", d)) != SK_OK) return rc;
@@ -252,7 +255,7 @@ int plan_forward(const sk_paths* X, const sk_paths* Y, int32_t d, int32_t dtype,
     const bool mt_eligible = poly && p.T == 1 && p.dpad >= 12;
     p.mtile = mt_eligible && !(o->flags & SK_FLAG_NO_TILED_M);
     auto kernel_for = [&](bool coop) -> const void* {
-        return poly ? fwd_poly_kernel_ptr(p.T, o->scheme == SK_POLY_INTERP, o->degree, coop, p.mtile)
+        return poly ? fwd_poly_kernel_ptr(p.T, o->scheme == SK_POLY_INTERP, o->degree, coop, p.mtile, tape)
                     : fwd_fd_kernel_ptr(p.T, o->scheme == SK_FD2 ? 2 : o->scheme == SK_FD_IMPLICIT ? 3 : 1, lam, coop);
     };
     p.kern = kernel_for(false);
@@ -398,8 +401,8 @@ int launch_increments(const sk_paths* S, int32_t d, int32_t dtype, int inc_mode,
     return SK_OK;
 }
 
-// Tape of the forward pass (approximation scheme): [npairs] int exponents of k_hat, then one
-// fixed-stride block per work item of nsteps_max x 32 lanes x tape_row<T>(N) elements.
+// Tape of the forward pass (polynomial schemes): [npairs] int exponents of k_hat, then one
+// fixed-stride block per work item of nsteps_max x 32 lanes x tape_row<T>(N, interp) elements.
 struct TapePlan {
     size_t ek_bytes, stride, total;
     int64_t nsteps;  // warp steps of the longest item
@@ -409,9 +412,13 @@ int plan_tape(const sk_paths* X, const sk_paths* Y, const sk_options* o, int T, 
     if (o->scheme != SK_POLY_APPROX && o->scheme != SK_POLY_INTERP)
         return fail(SK_ERR_UNSUPPORTED, "a forward tape is recorded for the polynomial schemes");
     const int lam = o->dyadic;
-    const int64_t rows = std::max<int64_t>(X->max_len << lam, 1), cols = std::max<int64_t>(Y->max_len << lam, 1);
+    // grid rows and columns of the longest paths: their increments (one fewer than their points)
+    const int64_t pts = (o->flags & SK_FLAG_INCREMENTS) ? 0 : 1;
+    const int64_t rows = std::max<int64_t>(X->max_len - pts, 1) << lam;
+    const int64_t cols = std::max<int64_t>(Y->max_len - pts, 1) << lam;
     const int64_t nsteps = ((rows + 31) / 32 - 1) * std::max<int64_t>(cols, 32) + 31 + cols;
-    const int row = T ? tape_row<float>(o->degree) : tape_row<double>(o->degree);
+    const bool interp = o->scheme == SK_POLY_INTERP;
+    const int row = T ? tape_row<float>(o->degree, interp) : tape_row<double>(o->degree, interp);
     const int esize = T ? 4 : 8;
     t.nsteps = nsteps;
     t.ek_bytes = align256(static_cast<size_t>(npairs) * sizeof(int));
@@ -424,7 +431,7 @@ int run_forward(const sk_paths* X, const sk_paths* Y, int32_t d, int32_t dtype, 
                 const int64_t* pa, const int64_t* pb, int64_t npairs, double* out, int64_t ldo, void* ws,
                 size_t ws_bytes, void* stream, void* tape = nullptr, size_t tape_bytes = 0, int64_t item_base = 0) {
     Plan p;
-    int rc = plan_forward(X, Y, d, dtype, o, mode, npairs, p, tape == nullptr);
+    int rc = plan_forward(X, Y, d, dtype, o, mode, npairs, p, tape == nullptr, tape != nullptr);
     if (rc != SK_OK) return rc;
     TapePlan tp{0, 0, 0, 0};
     if (tape) {
@@ -483,6 +490,7 @@ int run_forward(const sk_paths* X, const sk_paths* Y, int32_t d, int32_t dtype, 
     L.mtile = p.mtile ? 1 : 0;
     L.mtile_cols = static_cast<int32_t>(p.mtile_cols);
     L.mtile_off = p.mtile_off;
+    L.wait_limit = g_wait_limit.load(std::memory_order_relaxed);
     SK_CUDA(cudaMemsetAsync(base + p.off_queue, 0, 256 + align256(2 * 65 * sizeof(unsigned int)), st));
     if (!(o->flags & SK_FLAG_NO_SORT) && npairs > 1) {
         unsigned int* hist = reinterpret_cast<unsigned int*>(base + p.off_hist);
@@ -762,7 +770,7 @@ int plan_backward_tape(const sk_paths* X, const sk_paths* Y, int32_t d, int32_t 
     // contraction: every coordinate of a padded increment row in one pass up to 32 (8, 16 or 32)
     b.cC = p.dpad <= 8 ? 8 : (p.dpad <= 16 ? 16 : 32);
     b.ckern = p.T ? bwd_contract_ptr_f32(b.cC) : bwd_contract_ptr_f64(b.cC);
-    const int step_bytes = 32 * (p.T ? tape_row<float>(o->degree) * 4 : tape_row<double>(o->degree) * 8);
+    const int step_bytes = 32 * (p.T ? tape_row<float>(o->degree, interp) * 4 : tape_row<double>(o->degree, interp) * 8);
     b.smem_bytes = kFwdWarps * bwd_tape_warp_bytes(step_bytes);
     const int esize = p.T ? 4 : 8, N = o->degree;
     b.cols_max = std::max<int64_t>(Y->max_len << o->dyadic, 1);
@@ -1047,7 +1055,8 @@ int plan_mmd2(const sk_paths* A, const sk_paths* Bp, int32_t d, int32_t dtype, c
             m.sub = std::max(m.sub, std::max(m.f[k].total, m.cb[k].total));
             continue;
         }
-        if ((rc = plan_forward(xs[k], ys[k], d, dtype, ok, modes[k], m.chunk[k], m.f[k])) != SK_OK) return rc;
+        if ((rc = plan_forward(xs[k], ys[k], d, dtype, ok, modes[k], m.chunk[k], m.f[k], false, true)) != SK_OK)
+            return rc;
         if ((rc = plan_backward_tape(xs[k], ys[k], d, dtype, ok, modes[k], m.chunk[k], m.tb[k])) != SK_OK) return rc;
         TapePlan tc;
         if ((rc = plan_tape(xs[k], ys[k], ok, p1.T, m.chunk[k], tc)) != SK_OK) return rc;
@@ -1154,11 +1163,14 @@ int run_mmd2(const sk_paths* A, const sk_paths* Bp, int32_t d, int32_t dtype, co
     return SK_OK;
 }
 
-// sigkernel_backward for the interpolation scheme, which has no checkpointing adjoint: the items
-// are taken in chunks whose forward records a tape (at most kTapeChunkBudget bytes) and whose tape
-// adjoint follows at once, as in sigkernel_mmd2.  Paths so long that a chunk holds fewer items
-// than half the adjoint's resident warps are refused (SK_ERR_UNSUPPORTED).
+// sigkernel_backward of the polynomial schemes: the items are taken in chunks whose forward
+// records a tape (at most kTapeChunkBudget bytes) and whose tape adjoint follows at once, as in
+// sigkernel_mmd2.  When the paths are so long that a chunk holds fewer items than half the
+// adjoint's resident warps, the plan says so (fits = false): the approximation scheme then runs the
+// checkpointing adjoint, and the interpolation scheme, which has none, is refused
+// (SK_ERR_UNSUPPORTED).
 struct ChunkBwdPlan {
+    bool fits;        // a chunk fills the GPU (else the chunked plan below is not made)
     int64_t items, chunk;
     Plan f;           // forward of one chunk, recording its tape
     TapeBwdPlan tb;   // tape adjoint of one chunk
@@ -1178,12 +1190,16 @@ int plan_backward_chunked(const sk_paths* X, const sk_paths* Y, int32_t d, int32
     int64_t chunk = std::max<int64_t>(1, static_cast<int64_t>(kTapeChunkBudget / std::max<size_t>(t1.stride, 1)));
     if (chunk < items && chunk > resident) chunk -= chunk % resident;
     chunk = std::max<int64_t>(1, std::min(chunk, items));
-    if (chunk < items && 2 * chunk < resident)
-        return fail(SK_ERR_UNSUPPORTED, "sigkernel_backward of the interpolation scheme needs forward tapes, and these "
-                                        "paths are too long for a tape chunk to fill the GPU");
+    c.fits = !(chunk < items && 2 * chunk < resident);
+    if (!c.fits) {
+        if (o->scheme == SK_POLY_INTERP)
+            return fail(SK_ERR_UNSUPPORTED, "sigkernel_backward of the interpolation scheme needs forward tapes, and "
+                                            "these paths are too long for a tape chunk to fill the GPU");
+        return SK_OK;
+    }
     c.items = items;
     c.chunk = chunk;
-    if ((rc = plan_forward(X, Y, d, dtype, o, mode, chunk, c.f)) != SK_OK) return rc;
+    if ((rc = plan_forward(X, Y, d, dtype, o, mode, chunk, c.f, false, true)) != SK_OK) return rc;
     if ((rc = plan_backward_tape(X, Y, d, dtype, o, mode, chunk, c.tb)) != SK_OK) return rc;
     TapePlan tc;
     if ((rc = plan_tape(X, Y, o, p1.T, chunk, tc)) != SK_OK) return rc;
@@ -1197,6 +1213,13 @@ int plan_backward_chunked(const sk_paths* X, const sk_paths* Y, int32_t d, int32
     return SK_OK;
 }
 
+// sigkernel_backward runs from chunked tapes for both polynomial schemes unless the caller asks for
+// the checkpointing adjoint (approximation scheme only).
+bool uses_tape_chunks(const sk_options* o) {
+    if (o->scheme == SK_POLY_INTERP) return true;
+    return o->scheme == SK_POLY_APPROX && !(o->flags & SK_FLAG_CHECKPOINT);
+}
+
 int run_backward_chunked(const sk_paths* X, const sk_paths* Y, int32_t d, int32_t dtype, const sk_options* o,
                          const int64_t* pa, const int64_t* pb, int64_t npairs, const double* gout, double* gX,
                          double* gY, void* ws, size_t ws_bytes, void* stream) {
@@ -1207,6 +1230,8 @@ int run_backward_chunked(const sk_paths* X, const sk_paths* Y, int32_t d, int32_
     ChunkBwdPlan c;
     int rc = plan_backward_chunked(X, Y, d, dtype, o, mode, npairs, c);
     if (rc != SK_OK) return rc;
+    if (!c.fits)  // approximation scheme, paths too long for tape chunks: checkpointing adjoint
+        return run_backward(X, Y, d, dtype, o, pa, pb, npairs, gout, gX, gY, ws, ws_bytes, stream);
     if (c.f.same_xy && gY && gY != gX)
         return fail(SK_ERR_INVALID_ARG, "X and Y are the same paths: pass grad_Y = NULL or grad_Y = grad_X");
     if (npairs == 0) return SK_OK;
@@ -1309,6 +1334,9 @@ int run_mmd2_test(const sk_paths* A, const sk_paths* Bp, int32_t d, int32_t dtyp
 }
 
 }  // namespace
+
+void set_last_error(const char* msg) { t_last_error = msg; }
+
 }  // namespace sk
 
 using namespace sk;
@@ -1407,7 +1435,9 @@ void sigkernel_autotune_clear(void) {
     g_tune.clear();
 }
 
-int sigkernel_version(void) { return 100; }
+int sigkernel_version(void) { return 200; }
+
+void sigkernel_set_wait_limit(uint32_t polls) { g_wait_limit.store(polls, std::memory_order_relaxed); }
 
 const char* sigkernel_last_error(void) { return t_last_error.c_str(); }
 
@@ -1440,12 +1470,14 @@ int sigkernel_workspace_size(int32_t op, const sk_paths* X, const sk_paths* Y, i
         case SK_OP_BACKWARD: {
             const bool gram = npairs < 0;
             const bool sym = gram && (opt->flags & SK_FLAG_SYMMETRIC);
-            if (opt->scheme == SK_POLY_INTERP) {
+            if (uses_tape_chunks(opt)) {
                 ChunkBwdPlan c;
                 rc = plan_backward_chunked(X, Y, d, dtype, opt, gram ? (sym ? kGramUpper : kGramFull) : kPairsList,
                                            gram ? gram_items(X, Y, sym) : npairs, c);
-                if (rc == SK_OK) *bytes = c.total;
-                return rc;
+                if (rc != SK_OK || c.fits) {
+                    if (rc == SK_OK) *bytes = c.total;
+                    return rc;
+                }
             }
             BwdPlan b;
             rc = plan_backward(X, Y, d, dtype, opt, gram ? (sym ? kGramUpper : kGramFull) : kPairsList,
@@ -1508,7 +1540,7 @@ int sigkernel_backward(const sk_paths* X, const sk_paths* Y, int32_t d, int32_t 
     t_last_error.clear();
     if (!opt || !X || !Y) return fail(SK_ERR_INVALID_ARG, "NULL argument");
     if (pair_a && (!pair_b || npairs < 0)) return fail(SK_ERR_INVALID_ARG, "bad pair list");
-    if (opt->scheme == SK_POLY_INTERP)
+    if (uses_tape_chunks(opt))
         return run_backward_chunked(X, Y, d, dtype, opt, pair_a, pair_b, npairs, grad_out, grad_X, grad_Y, workspace,
                                     workspace_bytes, stream);
     return run_backward(X, Y, d, dtype, opt, pair_a, pair_b, npairs, grad_out, grad_X, grad_Y, workspace,

@@ -126,14 +126,33 @@ __device__ __forceinline__ void unit_scale(T (&fa)[N + 1], T (&fb)[N + 1], int& 
     }
 }
 
+// Edge adjoints of one approximation cell: given abar' (ga) and bbar' (gb), the adjoints of the
+// inputs a (ra) and b (rb); they depend on the cell only through e.
+// unit_scale for a tape row of output derivatives: all 2N entries scaled by one power of two to
+// magnitude ~1 (largest entry), the shift folded into their exponent.
 template <typename T, int N>
-__device__ __forceinline__ void cell_adjoint(const T (&a)[N + 1], const T (&b)[N + 1], const T (&e)[N + 1],
-                                             const T (&ga)[N + 1], const T (&gb)[N + 1], T (&ra)[N + 1],
-                                             T (&rb)[N + 1], T& mbar) {
+__device__ __forceinline__ void unit_scale_dm(T (&da)[N], T (&db)[N], int& ef) {
+    if constexpr (std::is_same<T, float>::value) {
+        float m = 0.f;
+#pragma unroll
+        for (int n = 0; n < N; ++n) m = fmaxf(m, fmaxf(fabsf(da[n]), fabsf(db[n])));
+        if (m > 0x1p16f || (m < 0x1p-16f && m > 0.f)) {
+            int sh = 0;
+            frexpf(m, &sh);
+            const float f = pow2c<float>(-sh);
+#pragma unroll
+            for (int n = 0; n < N; ++n) { da[n] *= f; db[n] *= f; }
+            ef += sh;
+        }
+    }
+}
+
+template <typename T, int N>
+__device__ __forceinline__ void cell_adjoint_edges(const T (&e)[N + 1], const T (&ga)[N + 1], const T (&gb)[N + 1],
+                                                   T (&ra)[N + 1], T (&rb)[N + 1]) {
     if constexpr (std::is_same<T, float>::value) {
         // FP32: the a- and b-side adjoints run the same products on different data, so they go as
-        // packed pairs through the two-wide FP32 instructions; the dk/dM sum over n is split into
-        // its a- and b-side halves, added once per m.
+        // packed pairs through the two-wide FP32 instructions.
         float2 w[N + 1];  // (gb_n e_n, ga_n e_n): weights of the Hankel couplings
 #pragma unroll
         for (int n = 0; n <= N; ++n) w[n] = __fmul2_rn(make_float2(gb[n], ga[n]), dup2(e[n]));
@@ -149,19 +168,6 @@ __device__ __forceinline__ void cell_adjoint(const T (&a)[N + 1], const T (&b)[N
             ra[k] = v.x;
             rb[k] = v.y;
         }
-        float mb = 0.f;
-#pragma unroll
-        for (int m = 1; m <= N; ++m) {
-            float2 h = __fmul2_rn(make_float2(b[1], a[1]), dup2(Tab<float>::hank(m, 1)));  // (ha, hb)
-#pragma unroll
-            for (int k = 2; k <= N; ++k) h = __ffma2_rn(make_float2(b[k], a[k]), dup2(Tab<float>::hank(m, k)), h);
-            float2 eb = __fmul2_rn(make_float2(ga[m], gb[m]), h);
-#pragma unroll
-            for (int n = m; n <= N; ++n)
-                eb = __ffma2_rn(make_float2(ga[n], gb[n]), make_float2(a[n - m], b[n - m]), eb);
-            mb = fma(eb.x + eb.y, e[m - 1], mb);
-        }
-        mbar = mb;
         return;
     }
     T al[N + 1], be[N + 1];
@@ -185,6 +191,31 @@ __device__ __forceinline__ void cell_adjoint(const T (&a)[N + 1], const T (&b)[N
         ra[k] = va;
         rb[k] = vb;
     }
+}
+
+// Adjoint of one approximation cell from its inputs (checkpointing adjoint, which replays them).
+template <typename T, int N>
+__device__ __forceinline__ void cell_adjoint(const T (&a)[N + 1], const T (&b)[N + 1], const T (&e)[N + 1],
+                                             const T (&ga)[N + 1], const T (&gb)[N + 1], T (&ra)[N + 1],
+                                             T (&rb)[N + 1], T& mbar) {
+    cell_adjoint_edges<T, N>(e, ga, gb, ra, rb);
+    if constexpr (std::is_same<T, float>::value) {
+        // the dk/dM sum over n split into its a- and b-side halves (packed), added once per m
+        float mb = 0.f;
+#pragma unroll
+        for (int m = 1; m <= N; ++m) {
+            float2 h = __fmul2_rn(make_float2(b[1], a[1]), dup2(Tab<float>::hank(m, 1)));  // (ha, hb)
+#pragma unroll
+            for (int k = 2; k <= N; ++k) h = __ffma2_rn(make_float2(b[k], a[k]), dup2(Tab<float>::hank(m, k)), h);
+            float2 eb = __fmul2_rn(make_float2(ga[m], gb[m]), h);
+#pragma unroll
+            for (int n = m; n <= N; ++n)
+                eb = __ffma2_rn(make_float2(ga[n], gb[n]), make_float2(a[n - m], b[n - m]), eb);
+            mb = fma(eb.x + eb.y, e[m - 1], mb);
+        }
+        mbar = mb;
+        return;
+    }
     T mb = T(0);
 #pragma unroll
     for (int m = 1; m <= N; ++m) {
@@ -202,6 +233,30 @@ __device__ __forceinline__ void cell_adjoint(const T (&a)[N + 1], const T (&b)[N
             eb = fma(gb[n], b[n - m], eb);
         }
         mb = fma(eb, e[m - 1], mb);
+    }
+    mbar = mb;
+}
+
+// Adjoint of one approximation cell from the tape of output derivatives (cell_series_dm):
+// dk/dM = sum_{n>=1} abar'_n d a'_n/dM + bbar'_n d b'_n/dM, 2N multiply-adds.
+template <typename T, int N>
+__device__ __forceinline__ void cell_adjoint_dm(const T (&da)[N], const T (&db)[N], const T (&e)[N + 1],
+                                                const T (&ga)[N + 1], const T (&gb)[N + 1], T (&ra)[N + 1],
+                                                T (&rb)[N + 1], T& mbar) {
+    cell_adjoint_edges<T, N>(e, ga, gb, ra, rb);
+    if constexpr (std::is_same<T, float>::value) {
+        float2 acc = __fmul2_rn(make_float2(ga[1], gb[1]), make_float2(da[0], db[0]));
+#pragma unroll
+        for (int n = 2; n <= N; ++n) acc = __ffma2_rn(make_float2(ga[n], gb[n]), make_float2(da[n - 1], db[n - 1]), acc);
+        mbar = acc.x + acc.y;
+        return;
+    }
+    T mb = ga[1] * da[0];
+    mb = fma(gb[1], db[0], mb);
+#pragma unroll
+    for (int n = 2; n <= N; ++n) {
+        mb = fma(ga[n], da[n - 1], mb);
+        mb = fma(gb[n], db[n - 1], mb);
     }
     mbar = mb;
 }
@@ -733,9 +788,9 @@ __host__ __device__ constexpr int bwd_series_top() {
 __host__ __device__ constexpr int bwd_tape_warp_bytes(int step_bytes) {
     return (kTapeRing * step_bytes + kTapeRing * 8 + 127) / 128 * 128;
 }
-template <typename T, int N>
+template <typename T, int N, bool INTERP>
 __host__ __device__ constexpr int bwd_tape_warp_bytes() {
-    return bwd_tape_warp_bytes(fwd_tape_step_bytes<T, N>());
+    return bwd_tape_warp_bytes(fwd_tape_step_bytes<T, N, INTERP>());
 }
 
 // Gradient seed and exponent of k_hat for item `item` (shared by the adjoint and the contraction).
@@ -753,7 +808,7 @@ __global__ void __launch_bounds__(kFwdWarps * 32, (bwd_tape_min_blocks<T, N, INT
     constexpr bool kRescale = std::is_same<T, float>::value;
     using V = typename Vec<T>::type;
     constexpr int W = Vec<T>::W;
-    constexpr int TR = tape_row<T>(N);
+    constexpr int TR = tape_row<T>(N, INTERP);
     const Launch& L = B.L;
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
@@ -761,9 +816,9 @@ __global__ void __launch_bounds__(kFwdWarps * 32, (bwd_tape_min_blocks<T, N, INT
     char* base = static_cast<char*>(L.scratch) + slot * L.scratch_stride;
     T* rbuf = reinterpret_cast<T*>(base + B.off_rbuf);          // [col][N+1]
     int* rexp = reinterpret_cast<int*>(base + B.off_rexp);      // [col]
-    constexpr int kStepBytes = fwd_tape_step_bytes<T, N>();
+    constexpr int kStepBytes = fwd_tape_step_bytes<T, N, INTERP>();
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    unsigned char* ring = smem_raw + wib * bwd_tape_warp_bytes<T, N>();
+    unsigned char* ring = smem_raw + wib * bwd_tape_warp_bytes<T, N, INTERP>();
     uint64_t* bars = reinterpret_cast<uint64_t*>(ring + kTapeRing * kStepBytes);
     if (lane == 0) {
         for (int k = 0; k < kTapeRing; ++k) mbar_init(bars + k, 1);
@@ -833,27 +888,38 @@ __global__ void __launch_bounds__(kFwdWarps * 32, (bwd_tape_min_blocks<T, N, INT
                 break;
             }
             parity ^= 1u << sl;
+            // The lane's tape row.  Interpolation: the cell inputs fa = a, fb = b.  Approximation:
+            // fa[0..N-1] = d a'_{n+1}/dM and fb[0..N-1] = d b'_{n+1}/dM (its whole 16-byte vectors
+            // [vector][lane], then an 8-byte remainder [lane] for FP32 with N even).
             T fa[N + 1], fb[N + 1];
             int ef;
             T M;
             {
                 const V* src = reinterpret_cast<const V*>(ring + sl * kStepBytes);
+                auto put = [&](int q, T x) {
+                    if constexpr (INTERP) {
+                        if (q <= N) fa[q] = x;
+                        else if (q <= 2 * N + 1) fb[q - N - 1] = x;
+                        else if (q == 2 * N + 2) ef = exponent_from<T>(x);
+                        else if (q == 2 * N + 3) M = x;
+                    } else {
+                        if (q < N) fa[q] = x;
+                        else if (q < 2 * N) fb[q - N] = x;
+                        else if (q == 2 * N) ef = exponent_from<T>(x);
+                        else M = x;
+                    }
+                };
 #pragma unroll
                 for (int v = 0; v < TR / W; ++v) {
                     const V t = src[v * 32 + lane];
                     const T* tp = reinterpret_cast<const T*>(&t);
 #pragma unroll
-                    for (int w = 0; w < W; ++w) {
-                        const int q = v * W + w;
-                        if (q <= N) fa[q] = tp[w];
-                        else if (q <= 2 * N + 1) fb[q - N - 1] = tp[w];
-                        else if (q == 2 * N + 2) {
-                            if constexpr (std::is_same<T, float>::value) ef = __float_as_int(tp[w]);
-                            else ef = static_cast<int>(__double_as_longlong(tp[w]));
-                        } else if (q == 2 * N + 3) {
-                            M = tp[w];
-                        }
-                    }
+                    for (int w = 0; w < W; ++w) put(v * W + w, tp[w]);
+                }
+                if constexpr (TR % W != 0) {
+                    const float2 t = reinterpret_cast<const float2*>(ring + sl * kStepBytes + (TR / W) * 32 * 16)[lane];
+                    put((TR / W) * W, t.x);
+                    put((TR / W) * W + 1, t.y);
                 }
             }
             __syncwarp();  // every lane has its row: the slot can be refilled
@@ -901,7 +967,11 @@ __global__ void __launch_bounds__(kFwdWarps * 32, (bwd_tape_min_blocks<T, N, INT
                         for (int n = 0; n <= N; ++n) gb_in[n] *= f;
                     }
                 }
-                unit_scale<T, N>(fa, fb, ef);
+                T da[N], db[N];  // approximation: the row's derivatives (fa, fb hold them in 0..N-1)
+#pragma unroll
+                for (int n = 0; n < N; ++n) { da[n] = fa[n]; db[n] = fb[n]; }
+                if constexpr (INTERP) unit_scale<T, N>(fa, fb, ef);
+                else unit_scale_dm<T, N>(da, db, ef);
                 T e[NE + 1];
                 build_exp_series<T, NE>(M, L.tau, e);
                 T mbar;
@@ -922,7 +992,7 @@ __global__ void __launch_bounds__(kFwdWarps * 32, (bwd_tape_min_blocks<T, N, INT
                     }
                     cell_adjoint_interp<T, N, NE>(fa, fb, e, gt, gr, gra, gbo, mbar);
                 } else {
-                    cell_adjoint<T, N>(fa, fb, e, ga_in, gb_in, gra, gbo, mbar);
+                    cell_adjoint_dm<T, N>(da, db, e, ga_in, gb_in, gra, gbo, mbar);
                 }
                 mrel = mbar * pow2c<T>(eg + ef - ek - 2 * lam);
                 gea = eg;

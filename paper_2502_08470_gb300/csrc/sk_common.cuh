@@ -127,8 +127,8 @@ struct Launch {
     int64_t scratch_stride;  // bytes per warp slot
     float tau;               // |M| above which an FP32 map is built in FP64
     // Optional tape of the forward pass (polynomial schemes): per work item, per warp step, per
-    // lane, the cell's inputs (a[N+1], b[N+1], exponent, M) in a padded 16-byte-vector row; plus
-    // the exponent of k_hat per item.  NULL when not recorded.
+    // lane, one row of tape_row<T>(N, interp) elements (see there), plus the exponent of k_hat
+    // per item.  NULL when not recorded.
     void* tape;
     int64_t tape_stride;     // bytes per work item
     int* tape_ek;            // [npairs]
@@ -152,13 +152,23 @@ struct Launch {
     // progress words are gprog[slot][grid_bpp x CW] in global memory (zeroed before the launch).
     int32_t grid_bpp;
     int* gprog;
+    // Polls a strip-pipeline hand-off wait makes before it gives up (0 = kSpinLimit).
+    uint32_t wait_limit;
 };
 
-// Width, in elements of T, of one lane's tape row: a[0..N], b[0..N], the exponent (element
-// 2N+2) and the cell's M (element 2N+3), padded to 16 bytes.
+// Width, in elements of T, of one lane's tape row.
+//   Interpolation scheme: the cell's inputs a[0..N], b[0..N], the exponent (element 2N+2) and the
+//   cell's M (element 2N+3), padded to 16 bytes.
+//   Approximation scheme: the derivatives of the cell's outputs with respect to M,
+//   d a'_n / dM (n = 1..N, elements 0..N-1) and d b'_n / dM (elements N..2N-1), the exponent
+//   (element 2N) and M (element 2N+1): 2N+2 elements, a whole number of 8-byte halves.  The
+//   adjoint needs a and b only through these derivatives (dk/dM = sum_n abar'_n da'_n/dM +
+//   bbar'_n db'_n/dM), so each lane's row is two elements shorter and the adjoint forms dk/dM
+//   in 2N multiply-adds instead of about 3N^2.
 template <typename T>
-__host__ __device__ constexpr int tape_row(int N) {
-    return ((2 * (N + 1) + 2) * static_cast<int>(sizeof(T)) + 15) / 16 * 16 / static_cast<int>(sizeof(T));
+__host__ __device__ constexpr int tape_row(int N, bool interp) {
+    return interp ? ((2 * (N + 1) + 2) * static_cast<int>(sizeof(T)) + 15) / 16 * 16 / static_cast<int>(sizeof(T))
+                  : 2 * N + 2;
 }
 
 __device__ __forceinline__ int64_t upper_row(int64_t p, int64_t n) {
@@ -233,7 +243,9 @@ __device__ __forceinline__ int64_t pop_item(const Launch& L) {
 // the hand-off entry of column j, the monotonic count g * cols + j + 1 in its shared-memory
 // word; the warp that runs strip g + 1 waits for that count before reading the entry.  Release
 // and acquire at CTA scope order the hand-off's global-memory stores and loads around it.
-constexpr uint32_t kSpinLimit = 1u << 20;  // polls (with a short sleep) before a wait gives up
+constexpr uint32_t kSpinLimit = 1u << 20;  // default polls (with a short sleep) before a wait gives up
+
+__device__ __forceinline__ uint32_t wait_polls(const Launch& L) { return L.wait_limit ? L.wait_limit : kSpinLimit; }
 
 __device__ __forceinline__ void publish_progress(int* p, int v) {
     asm volatile("st.release.cta.shared::cta.b32 [%0], %1;" ::"r"(static_cast<uint32_t>(__cvta_generic_to_shared(p))),
@@ -250,9 +262,10 @@ __device__ __forceinline__ int acquire_progress(const int* p) {
     return v;
 }
 
-// Bounded wait for *p >= need; false (and the device error word set) when it runs out.
-__device__ __forceinline__ bool wait_progress(const int* p, int need) {
-    for (uint32_t it = 0; it < kSpinLimit; ++it) {
+// Bounded wait for *p >= need (at most `polls` polls); false (and the device error word set) when
+// it runs out.
+__device__ __forceinline__ bool wait_progress(const int* p, int need, uint32_t polls) {
+    for (uint32_t it = 0; it < polls; ++it) {
         if (acquire_progress(p) >= need) return true;
         __nanosleep(64);
     }
@@ -269,8 +282,8 @@ __device__ __forceinline__ void publish_progress_gpu(int* p, int v) {
 
 // Bounded wait for *p >= need; *seen gets the value observed (the caller may then read every
 // entry up to it without another acquire).  False (and the device error word set) when it runs out.
-__device__ __forceinline__ bool wait_progress_gpu(const int* p, int need, int* seen) {
-    for (uint32_t it = 0; it < kSpinLimit; ++it) {
+__device__ __forceinline__ bool wait_progress_gpu(const int* p, int need, int* seen, uint32_t polls) {
+    for (uint32_t it = 0; it < polls; ++it) {
         int v;
         asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
         if (v >= need) {

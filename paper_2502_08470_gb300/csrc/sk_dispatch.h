@@ -12,7 +12,13 @@ namespace sk {
 // T: 0 = FP64 cell updates, 1 = FP32; coop: the cooperative-block (strip pipeline) variant,
 // launched with kCoopWarps warps per block; mt: the tiled-M variant (FP32 only).  NULL when no
 // kernel exists for the request.
-const void* fwd_poly_kernel_ptr(int T, bool interp, int N, bool coop, bool mt);
+// tape: the one-warp-per-pair kernel that records the forward tape (for the approximation scheme
+// a separate instantiation records the derivatives of each cell's outputs with respect to M; the
+// interpolation kernels record their inputs whenever the launch carries a tape).
+const void* fwd_poly_kernel_ptr(int T, bool interp, int N, bool coop, bool mt, bool tape = false);
+const void* fwd_approx_tape_ptr_f32(int N);
+const void* fwd_approx_tape_ptr_f32_mt(int N);
+const void* fwd_approx_tape_ptr_f64(int N);
 const void* fwd_fd_kernel_ptr(int T, int order, int lam, bool coop);
 const void* fwd_fd_coop_ptr(int T, int order, int lam);
 const void* fwd_fd_implicit_ptr(int T, int lam, bool coop);  // order 3
@@ -82,6 +88,11 @@ const void* bwd_tape_interp_ptr_f64_1(int N);
 // C: coordinates per contraction pass (8, 16 or 32)
 const void* bwd_contract_ptr_f32(int C);
 const void* bwd_contract_ptr_f64(int C);
+}  // namespace sk
+
+namespace sk {
+// Message returned by sigkernel_last_error() on this host thread (for entry points in other units).
+void set_last_error(const char* msg);
 }  // namespace sk
 
 namespace sk {

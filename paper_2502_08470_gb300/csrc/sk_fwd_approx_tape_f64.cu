@@ -1,0 +1,24 @@
+// Instantiations of the approximation-scheme forward wavefront that records the tape of output
+// derivatives read by the tape adjoint (double cell updates; the orders bwd_tape_kernel supports).
+#include "sk_fwd_poly.cuh"
+#include "sk_dispatch.h"
+
+namespace sk {
+
+const void* fwd_approx_tape_ptr_f64(int N) {
+    switch (N) {
+        case 2: return reinterpret_cast<const void*>(&fwd_poly_kernel<double, 2, 2, false, 1, false, true>);
+        case 3: return reinterpret_cast<const void*>(&fwd_poly_kernel<double, 3, 3, false, 1, false, true>);
+        case 4: return reinterpret_cast<const void*>(&fwd_poly_kernel<double, 4, 4, false, 1, false, true>);
+        case 5: return reinterpret_cast<const void*>(&fwd_poly_kernel<double, 5, 5, false, 1, false, true>);
+        case 6: return reinterpret_cast<const void*>(&fwd_poly_kernel<double, 6, 6, false, 1, false, true>);
+        case 7: return reinterpret_cast<const void*>(&fwd_poly_kernel<double, 7, 7, false, 1, false, true>);
+        case 8: return reinterpret_cast<const void*>(&fwd_poly_kernel<double, 8, 8, false, 1, false, true>);
+        case 9: return reinterpret_cast<const void*>(&fwd_poly_kernel<double, 9, 9, false, 1, false, true>);
+        case 10: return reinterpret_cast<const void*>(&fwd_poly_kernel<double, 10, 10, false, 1, false, true>);
+        case 12: return reinterpret_cast<const void*>(&fwd_poly_kernel<double, 12, 12, false, 1, false, true>);
+        default: return nullptr;
+    }
+}
+
+}  // namespace sk

@@ -48,7 +48,12 @@ const void* fwd_interp_coop_mt_ptr_f32(int N) {
     return nullptr;
 }
 
-const void* fwd_poly_kernel_ptr(int T, bool interp, int N, bool coop, bool mt) {
+const void* fwd_poly_kernel_ptr(int T, bool interp, int N, bool coop, bool mt, bool tape) {
+    if (tape && !interp) {
+        if (coop) return nullptr;
+        if (T == 1) return mt ? fwd_approx_tape_ptr_f32_mt(N) : fwd_approx_tape_ptr_f32(N);
+        return mt ? nullptr : fwd_approx_tape_ptr_f64(N);
+    }
     if (mt) {
         if (T != 1) return nullptr;
         if (coop) return interp ? fwd_interp_coop_mt_ptr_f32(N) : fwd_approx_coop_mt_ptr_f32(N);

@@ -96,7 +96,8 @@ __device__ __forceinline__ void sweep_fd(const Launch& L, int64_t item, const Pa
                     eb = 0;
                 } else {
                     if constexpr (CW > 1) {
-                        if (!stuck && !wait_progress(prog + (w + CW - 1) % CW, (gs - 1) * nJ + jj + 1)) stuck = true;
+                        if (!stuck && !wait_progress(prog + (w + CW - 1) % CW, (gs - 1) * nJ + jj + 1, wait_polls(L)))
+                            stuck = true;
                     }
                     kb = hprev[jj];
                     if (kRescale) eb = eprev[jj];

@@ -59,11 +59,11 @@ __device__ __forceinline__ void build_exp_series(T M, float tau, T (&e)[NE + 1])
     for (int m = 1; m <= NE; ++m) e[m] = e[m - 1] * (M * Tab<T>::inv(m));
 }
 
-// One cell: inputs a (bottom), b (left), outputs the factorial-scaled series of the top (ct)
-// and right (cr) edges, n = 0..NE.
 // Broadcast of one FP32 value into both halves of a packed pair.
 __device__ __forceinline__ float2 dup2(float v) { return make_float2(v, v); }
 
+// One cell: inputs a (bottom), b (left), outputs the factorial-scaled series of the top (ct)
+// and right (cr) edges, n = 0..NE.
 template <typename T, int N, int NE, bool INTERP>
 __device__ __forceinline__ void cell_series(const T (&a)[N + 1], const T (&b)[N + 1], const T (&e)[NE + 1],
                                             T (&ct)[NE + 1], T (&cr)[NE + 1]) {
@@ -77,16 +77,53 @@ __device__ __forceinline__ void cell_series(const T (&a)[N + 1], const T (&b)[N 
             ha = fma(b[k], Tab<T>::hank(n, k), ha);
             hb = fma(a[k], Tab<T>::hank(n, k), hb);
         }
-        T vt = e[n] * ha;
-        T vr = e[n] * hb;
+        // Toeplitz part sum_{k<=n} (.)_k e_{n-k}, then the coupling term e_n h_n
+        T vt = a[0] * e[n];
+        T vr = (INTERP ? a[0] : b[0]) * e[n];
 #pragma unroll
-        for (int k = 0; k <= (n < N ? n : N); ++k) {
+        for (int k = 1; k <= (n < N ? n : N); ++k) {
             vt = fma(a[k], e[n - k], vt);
-            T bk = (INTERP && k == 0) ? a[0] : b[k];
-            vr = fma(bk, e[n - k], vr);
+            vr = fma(b[k], e[n - k], vr);
         }
-        ct[n] = vt;
-        cr[n] = vr;
+        ct[n] = fma(e[n], ha, vt);
+        cr[n] = fma(e[n], hb, vr);
+    }
+}
+
+// The approximation cell (NE = N) as cell_series, bit for bit, plus the derivatives of its outputs
+// with respect to M, which are all the adjoint needs of the cell's inputs.  With e_m = M^m/m!
+// (d e_m / dM = e_{m-1}) and the Toeplitz sums T_n = sum_{k<=n} a_k e_{n-k}:
+//     d a'_n / dM = T_{n-1} + e_{n-1} ha_n,   d b'_n / dM = S_{n-1} + e_{n-1} hb_n   (n = 1..N)
+// where S_n is the Toeplitz sum of b; da[n-1] and db[n-1] receive them.
+template <typename T, int N>
+__device__ __forceinline__ void cell_series_dm(const T (&a)[N + 1], const T (&b)[N + 1], const T (&e)[N + 1],
+                                               T (&ct)[N + 1], T (&cr)[N + 1], T (&da)[N], T (&db)[N]) {
+    T ha[N + 1], hb[N + 1];
+#pragma unroll
+    for (int n = 0; n <= N; ++n) {
+        ha[n] = b[1] * Tab<T>::hank(n, 1);
+        hb[n] = a[1] * Tab<T>::hank(n, 1);
+#pragma unroll
+        for (int k = 2; k <= N; ++k) {
+            ha[n] = fma(b[k], Tab<T>::hank(n, k), ha[n]);
+            hb[n] = fma(a[k], Tab<T>::hank(n, k), hb[n]);
+        }
+    }
+#pragma unroll
+    for (int n = 0; n <= N; ++n) {
+        T vt = a[0] * e[n];
+        T vr = b[0] * e[n];
+#pragma unroll
+        for (int k = 1; k <= n; ++k) {
+            vt = fma(a[k], e[n - k], vt);
+            vr = fma(b[k], e[n - k], vr);
+        }
+        ct[n] = fma(e[n], ha[n], vt);
+        cr[n] = fma(e[n], hb[n], vr);
+        if (n < N) {
+            da[n] = fma(e[n], ha[n + 1], vt);
+            db[n] = fma(e[n], hb[n + 1], vr);
+        }
     }
 }
 
@@ -138,10 +175,58 @@ __device__ __forceinline__ T pow2t(int e) {
     else return pow2d(e);
 }
 
-// Bytes of one warp step of the tape (32 lanes x one padded row of cell inputs).
-template <typename T, int N>
+// Bytes of one warp step of the tape (32 lanes x one row).
+template <typename T, int N, bool INTERP>
 __host__ __device__ constexpr int fwd_tape_step_bytes() {
-    return 32 * tape_row<T>(N) * static_cast<int>(sizeof(T));
+    return 32 * tape_row<T>(N, INTERP) * static_cast<int>(sizeof(T));
+}
+
+// A lane's exponent stored in a tape element of type T (its bit pattern, read back with
+// exponent_from).
+template <typename T>
+__device__ __forceinline__ T exponent_as(int e) {
+    if constexpr (std::is_same<T, float>::value) return __int_as_float(e);
+    else return __longlong_as_double(static_cast<long long>(e));
+}
+template <typename T>
+__device__ __forceinline__ int exponent_from(T v) {
+    if constexpr (std::is_same<T, float>::value) return __float_as_int(v);
+    else return static_cast<int>(__double_as_longlong(v));
+}
+
+// Element q of an approximation tape row: d a'_{q+1}/dM (q < N), d b'_{q-N+1}/dM (q < 2N), the
+// exponent (q = 2N), M (q = 2N+1).
+template <typename T, int N>
+__device__ __forceinline__ T dm_row_elem(int q, const T (&da)[N], const T (&db)[N], int ea, T M) {
+    return q < N ? da[q] : (q < 2 * N ? db[q - N] : (q == 2 * N ? exponent_as<T>(ea) : M));
+}
+
+// One lane's row of an approximation-scheme tape step at `item_tape` (the item's tape): the row's
+// whole 16-byte vectors laid out [vector][lane] (each vector store of the warp fills 512
+// contiguous bytes), then, when the row has an 8-byte remainder (FP32 with N even), that half
+// laid out [lane] (256 contiguous bytes).  Streaming (evict-first) stores: the adjoint reads the
+// tape only after the whole forward.
+template <typename T, int N>
+__device__ __forceinline__ void store_dm_row(char* item_tape, int step, int lane, const T (&da)[N], const T (&db)[N],
+                                             int ea, T M) {
+    using V = typename Vec<T>::type;
+    constexpr int W = Vec<T>::W;
+    constexpr int TR = tape_row<T>(N, false);
+    constexpr int NV = TR / W;
+    char* base = item_tape + static_cast<int64_t>(step) * fwd_tape_step_bytes<T, N, false>();
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+        V t;
+        T* tp = reinterpret_cast<T*>(&t);
+#pragma unroll
+        for (int q2 = 0; q2 < W; ++q2) tp[q2] = dm_row_elem<T, N>(v * W + q2, da, db, ea, M);
+        __stcs(reinterpret_cast<V*>(base) + v * 32 + lane, t);
+    }
+    if constexpr (TR % W != 0) {
+        static_assert(std::is_same<T, float>::value && TR % W == 2, "8-byte remainder of an FP32 row");
+        const float2 t = make_float2(dm_row_elem<T, N>(NV * W, da, db, ea, M), dm_row_elem<T, N>(NV * W + 1, da, db, ea, M));
+        __stcs(reinterpret_cast<float2*>(base + NV * 32 * 16) + lane, t);
+    }
 }
 
 // Resident blocks per SM requested from the register allocator: the live state of a lane is
@@ -227,7 +312,7 @@ constexpr int fwd_poly_coop_min_blocks() {
 // The ring is the CW warps of one block (ring = CW, progress words in shared memory, CTA-scope
 // ordering), or, with GS, blocks x CW warps spread over co-resident blocks (progress words in
 // global memory, GPU-scope ordering, published every kGridPublish columns).
-template <typename T, int N, int NE, bool INTERP, int CW, bool MT, bool GS = false>
+template <typename T, int N, int NE, bool INTERP, int CW, bool MT, bool GS = false, bool DMT = false>
 __device__ __forceinline__ void sweep_poly(const Launch& L, int64_t item, const PairDesc& P, int w, char* own_buf,
                                            const char* prev_buf, int* prog, int64_t buf_cols, T* xstage,
                                            int ring = CW) {
@@ -308,9 +393,9 @@ __device__ __forceinline__ void sweep_poly(const Launch& L, int64_t item, const 
                     const int* pp = prog + (w + ring - 1) % ring;
                     if constexpr (GS) {
                         const int need = (g - 1) * cols + jj + 1;
-                        if (!stuck && seen < need && !wait_progress_gpu(pp, need, &seen)) stuck = true;
+                        if (!stuck && seen < need && !wait_progress_gpu(pp, need, &seen, wait_polls(L))) stuck = true;
                     } else {
-                        if (!stuck && !wait_progress(pp, (g - 1) * cols + jj + 1)) stuck = true;
+                        if (!stuck && !wait_progress(pp, (g - 1) * cols + jj + 1, wait_polls(L))) stuck = true;
                     }
                 }
                 const V* src = hprev + static_cast<int64_t>(jj) * (NB / W);
@@ -348,15 +433,15 @@ __device__ __forceinline__ void sweep_poly(const Launch& L, int64_t item, const 
         T M;
         if constexpr (MT) M = active ? mbuf[((sl & 1) * 32 + lane) * static_cast<int64_t>(mcols) + jc] : T(0);
         else M = row_dot<T>(xrow, ybase + static_cast<int64_t>(jc >> lam) * dpad, L.nvec) * sub;
-        if constexpr (CW == 1) {
+        if constexpr (CW == 1 && INTERP) {
             if (L.tape != nullptr) {
-                // Record the cell's inputs (a, b, exponent, M) for the adjoint.  A step of the
-                // tape is laid out [vector][lane] (16-byte vectors), so each of the lane's vector
-                // stores fills 512 contiguous bytes with the warp's other lanes.  The stores are
-                // streaming (evict-first): the adjoint reads the tape only after the whole forward
-                // (12.4 ms for the 128x128 Gram's forward, against 13.3 ms with plain or L2-only
-                // stores).
-                constexpr int TR = tape_row<T>(N);
+                // Interpolation scheme: record the cell's inputs (a, b, exponent, M) for the
+                // adjoint.  A step of the tape is laid out [vector][lane] (16-byte vectors), so
+                // each of the lane's vector stores fills 512 contiguous bytes with the warp's other
+                // lanes.  The stores are streaming (evict-first): the adjoint reads the tape only
+                // after the whole forward (12.4 ms for the 128x128 Gram's forward, against 13.3 ms
+                // with plain or L2-only stores).
+                constexpr int TR = tape_row<T>(N, true);
                 constexpr int kStepBytes = 32 * TR * static_cast<int>(sizeof(T));
                 V* dst = reinterpret_cast<V*>(static_cast<char*>(L.tape) + item * L.tape_stride +
                                               static_cast<int64_t>(step) * kStepBytes);
@@ -368,10 +453,7 @@ __device__ __forceinline__ void sweep_poly(const Launch& L, int64_t item, const 
                     for (int q2 = 0; q2 < W; ++q2) {
                         const int q = v * W + q2;
                         tp[q2] = q <= N ? a[q] : (q <= 2 * N + 1 ? b[q - N - 1] : T(0));
-                        if (q == 2 * N + 2) {
-                            if constexpr (std::is_same<T, float>::value) tp[q2] = __int_as_float(ea);
-                            else tp[q2] = __longlong_as_double(static_cast<long long>(ea));
-                        }
+                        if (q == 2 * N + 2) tp[q2] = exponent_as<T>(ea);
                         if (q == 2 * N + 3) tp[q2] = M;
                     }
                     __stcs(dst + v * 32 + lane, t);
@@ -381,7 +463,15 @@ __device__ __forceinline__ void sweep_poly(const Launch& L, int64_t item, const 
         T e[NE + 1];
         build_exp_series<T, NE>(M, L.tau, e);
         T ct[NE + 1], cr[NE + 1];
-        cell_series<T, N, NE, INTERP>(a, b, e, ct, cr);
+        if constexpr (DMT) {
+            // Approximation scheme with a tape: the cell also gives the derivatives of its outputs
+            // with respect to M, recorded (with the inputs' exponent and M) in place of the inputs.
+            T da[N], db[N];
+            cell_series_dm<T, N>(a, b, e, ct, cr, da, db);
+            store_dm_row<T, N>(static_cast<char*>(L.tape) + item * L.tape_stride, step, lane, da, db, ea, M);
+        } else {
+            cell_series<T, N, NE, INTERP>(a, b, e, ct, cr);
+        }
         if constexpr (INTERP) {
             if (active && row == rows - 1 && jj == cols - 1) {
                 const double v0 = 0.5 * (series_at_one<T, NE>(ct) + series_at_one<T, NE>(cr));
@@ -479,10 +569,13 @@ __device__ __forceinline__ bool trivial_pair(const Launch& L, int64_t item, cons
 }
 
 // Forward wavefront, persistent.  MT: tiled M (produce_m_strip) instead of per-cell inner
-// products.  CW = 1: blocks of kFwdWarps independent warps, one pair per warp.  CW > 1: blocks of CW warps; the block takes pairs of at least L.coop_min_strips strips
-// together (strip pipeline, sweep_poly<..., CW>), and at the first shorter pair (the queue is
-// ordered by cell count, longest first) its warps fall back to one pair each.
-template <typename T, int N, int NE, bool INTERP, int CW, bool MT>
+// products.  CW = 1: blocks of kFwdWarps independent warps, one pair per warp.  CW > 1: blocks of
+// CW warps; the block takes pairs of at least L.coop_min_strips strips together (strip pipeline,
+// sweep_poly<..., CW>), and at the first shorter pair (the queue is ordered by cell count, longest
+// first) its warps fall back to one pair each.  DMT (approximation scheme, CW = 1): record the
+// tape of output derivatives with respect to M (L.tape must be set); the interpolation kernels
+// record their tape of cell inputs whenever L.tape is set.
+template <typename T, int N, int NE, bool INTERP, int CW, bool MT, bool DMT = false>
 __global__ void __launch_bounds__((CW > 1 ? CW : kFwdWarps) * 32,
                                   (CW > 1 ? fwd_poly_coop_min_blocks<T, N, NE, MT>() : fwd_poly_min_blocks<T, N, NE, MT>()))
     fwd_poly_kernel(Launch L, int64_t buf_cols) {
@@ -538,7 +631,7 @@ __global__ void __launch_bounds__((CW > 1 ? CW : kFwdWarps) * 32,
         if (item < 0) break;
         const PairDesc P = decode_pair(L, item);
         if (trivial_pair(L, item, P)) continue;
-        sweep_poly<T, N, NE, INTERP, 1, MT>(L, item, P, 0, own, own, nullptr, buf_cols, xstage);
+        sweep_poly<T, N, NE, INTERP, 1, MT, false, DMT>(L, item, P, 0, own, own, nullptr, buf_cols, xstage);
     }
 }
 

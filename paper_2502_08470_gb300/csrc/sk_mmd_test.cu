@@ -144,18 +144,31 @@ __global__ void __launch_bounds__(kPermWarps * 32)
 }
 
 // out[1] = (1 + #{p : out[2 + p] >= out[0]}) / (1 + nperm); one block, integer counts.
+// The p-value is NaN when the observed statistic or any relabelling's statistic is NaN (a bad
+// relabelling row, or non-finite Gram entries): a count over the others would look plausible.
 __global__ void mmd_perm_pvalue_kernel(int64_t nperm, double* out) {
     __shared__ long long part[256];
+    __shared__ int any_nan;
+    if (threadIdx.x == 0) any_nan = 0;
+    __syncthreads();
     const double obs = out[0];
     long long c = 0;
-    for (int64_t p = threadIdx.x; p < nperm; p += blockDim.x) c += out[2 + p] >= obs ? 1 : 0;
+    bool nan_seen = isnan(obs);
+    for (int64_t p = threadIdx.x; p < nperm; p += blockDim.x) {
+        const double v = out[2 + p];
+        c += v >= obs ? 1 : 0;
+        nan_seen |= isnan(v);
+    }
+    if (nan_seen) atomicOr(&any_nan, 1);
     part[threadIdx.x] = c;
     __syncthreads();
     for (int w = blockDim.x / 2; w > 0; w >>= 1) {
         if (static_cast<int>(threadIdx.x) < w) part[threadIdx.x] += part[threadIdx.x + w];
         __syncthreads();
     }
-    if (threadIdx.x == 0) out[1] = static_cast<double>(1 + part[0]) / static_cast<double>(1 + nperm);
+    if (threadIdx.x == 0)
+        out[1] = any_nan ? __longlong_as_double(0x7ff8000000000000LL)
+                         : static_cast<double>(1 + part[0]) / static_cast<double>(1 + nperm);
 }
 
 // K[(na + b) n + a] = K[a n + na + b]: the K_BA block from K_AB.

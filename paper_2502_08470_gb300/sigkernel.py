@@ -26,7 +26,7 @@ SCHEMES = {"fd1": 0, "fd2": 1, "approx": 2, "interp": 3, "fd_implicit": 4}
 COMPUTE = {"f64": 0, "f32": 1}
 DTYPES = {torch.float64: 0, torch.float32: 1, torch.bfloat16: 2}
 FLAG_SYMMETRIC, FLAG_INCREMENTS, FLAG_UNBIASED, FLAG_NO_SORT, FLAG_TIME_KERNEL = 1, 2, 4, 8, 16
-FLAG_STRIP_PIPELINE, FLAG_NO_STRIP_PIPELINE, FLAG_NO_TILED_M = 32, 64, 128
+FLAG_STRIP_PIPELINE, FLAG_NO_STRIP_PIPELINE, FLAG_NO_TILED_M, FLAG_CHECKPOINT = 32, 64, 128, 256
 
 
 def _pipe_flags(strip_pipeline) -> int:
@@ -96,6 +96,10 @@ def load_library():
         lib.sigkernel_last_kernel_ms.restype = ctypes.c_float
         lib.sigkernel_device_status.restype = ctypes.c_int
         lib.sigkernel_device_status.argtypes = [P]
+        lib.sigkernel_fma_peak.restype = ctypes.c_int
+        lib.sigkernel_fma_peak.argtypes = [I32, I32, I32, ctypes.POINTER(ctypes.c_double), P]
+        lib.sigkernel_set_wait_limit.restype = None
+        lib.sigkernel_set_wait_limit.argtypes = [ctypes.c_uint32]
         _lib = lib
         return lib
 
@@ -275,10 +279,12 @@ def autotune_clear():
 
 
 def sigkernel_backward(grad_out, X, Y=None, pair_a=None, pair_b=None, scheme="approx", degree=6, dyadic=0,
-                       compute="f64", sort=True, time_kernel: bool = False):
+                       compute="f64", sort=True, time_kernel: bool = False, checkpoint: bool = False):
     """Gradients of sum(grad_out * k_hat) with respect to the rows of X and Y (float64 CUDA tensors
     shaped like the rows).  Gram mode when ``pair_a`` is None (``grad_out`` [nx, ny]); with Y None
-    (or Y is X) the symmetric Gram of X, and the single returned gradient is the total."""
+    (or Y is X) the symmetric Gram of X, and the single returned gradient is the total.
+    ``checkpoint`` selects the checkpointing adjoint of the approximation scheme (SK_FLAG_CHECKPOINT)
+    instead of the adjoint from chunked forward tapes."""
     sym = Y is None or Y is X
     X = as_paths(X)
     Y = X if sym else as_paths(Y)
@@ -287,7 +293,7 @@ def sigkernel_backward(grad_out, X, Y=None, pair_a=None, pair_b=None, scheme="ap
     gX = torch.zeros(X.rows.shape[0], X.d, dtype=torch.float64, device="cuda")
     same = sym or (X.rows.data_ptr() == Y.rows.data_ptr() and X.offsets.data_ptr() == Y.offsets.data_ptr())
     gY = gX if same else torch.zeros(Y.rows.shape[0], Y.d, dtype=torch.float64, device="cuda")
-    extra = (0 if sort else FLAG_NO_SORT) | (FLAG_TIME_KERNEL if time_kernel else 0)
+    extra = (0 if sort else FLAG_NO_SORT) | (FLAG_TIME_KERNEL if time_kernel else 0) | (FLAG_CHECKPOINT if checkpoint else 0)
     if pair_a is None:
         opt = _options(scheme, degree, dyadic, compute, _flags(X, extra | (FLAG_SYMMETRIC if sym else 0)))
         ws = _workspace(OP_BACKWARD, cX, cY, X.d, -1, opt)
@@ -431,9 +437,33 @@ def mmd2_test_workspace(A, B, nperm, scheme="approx", degree=6, dyadic=0, comput
 # ----------------------------------------------------------------------------------------------
 # torch.autograd wrappers (dense [B, L, d] inputs)
 # ----------------------------------------------------------------------------------------------
+def tape_bytes(X, Y=None, pair_a=None, scheme="approx", degree=6, dyadic=0, compute="f32") -> int:
+    """Bytes of the forward tape of these inputs (``sigkernel_tape_size``; Gram when ``pair_a`` is
+    None, symmetric when Y is None or X)."""
+    sym = pair_a is None and (Y is None or Y is X)
+    X = as_paths(X)
+    Y = X if (Y is None or Y is X) else as_paths(Y)
+    n = -1 if pair_a is None else int(torch.as_tensor(pair_a).numel())
+    opt = _options(scheme, degree, dyadic, compute, _flags(X, FLAG_SYMMETRIC if sym else 0))
+    nb = ctypes.c_size_t(0)
+    cX, cY = _cpaths(X), _cpaths(Y)
+    _check(load_library().sigkernel_tape_size(ctypes.byref(cX), ctypes.byref(cY), X.d, n, ctypes.byref(opt),
+                                              ctypes.byref(nb)))
+    return int(nb.value)
+
+
+# Largest tape the autograd wrapper keeps from forward to backward when left to choose (tape=None):
+# at most this many bytes and at most half the device memory free at the forward.
+AUTO_TAPE_MAX_BYTES = 128 << 30
+
+
 class _GramFn(torch.autograd.Function):
     @staticmethod
     def forward(ctx, X, Y, sym, opts, use_tape):
+        if use_tape is None:
+            need = tape_bytes(X, None if sym else Y, **opts)
+            free, _ = torch.cuda.mem_get_info()
+            use_tape = need <= min(AUTO_TAPE_MAX_BYTES, free // 2)
         ctx.opts, ctx.sym, ctx.use_tape = opts, sym, use_tape
         ctx.save_for_backward(X, Y)
         if use_tape:
@@ -444,9 +474,8 @@ class _GramFn(torch.autograd.Function):
     @staticmethod
     def backward(ctx, gG):
         X, Y = ctx.saved_tensors
-        if ctx.use_tape:
+        if ctx.use_tape:  # the tape stays with ctx (a retained graph may run backward again)
             gX, gY = sigkernel_backward_tape(ctx.tape, gG, X, None if ctx.sym else Y, **ctx.opts)
-            ctx.tape = None
         else:
             gX, gY = sigkernel_backward(gG, X, None if ctx.sym else Y, **ctx.opts)
         if ctx.sym:
@@ -470,10 +499,13 @@ class _MMD2Fn(torch.autograd.Function):
 class SigKernel:
     """Signature kernel k_hat of one scheme: ``gram`` and ``mmd2`` are differentiable with respect
     to dense [B, L, d] path tensors through the adjoint wavefront.  With ``tape=True`` the Gram's
-    forward records every cell's inputs (about 64 B per cell in FP32) and the adjoint replays them
-    instead of recomputing the forward sweep."""
+    forward records a tape of every cell (2N+2 values per cell for the approximation scheme, 56 B
+    at N = 6 in FP32) and the backward replays it instead of recomputing the forward sweep; with
+    ``tape=False`` the backward is ``sigkernel_backward`` (which re-runs the forward in chunks).
+    ``tape=None`` (default) records the tape when it takes at most ``AUTO_TAPE_MAX_BYTES`` and at
+    most half the free device memory."""
 
-    def __init__(self, scheme="approx", degree=6, dyadic=0, compute="f32", tape=False):
+    def __init__(self, scheme="approx", degree=6, dyadic=0, compute="f32", tape=None):
         self.opts = dict(scheme=scheme, degree=degree, dyadic=dyadic, compute=compute)
         self.tape = tape
 
@@ -497,3 +529,17 @@ def device_status() -> int:
 
 def version() -> int:
     return load_library().sigkernel_version()
+
+
+def fma_peak(compute="f32", packed=False, reps=5) -> float:
+    """Measured FMA throughput of the current GPU in TFLOP/s (``sigkernel_fma_peak``)."""
+    v = ctypes.c_double(0)
+    _check(load_library().sigkernel_fma_peak(COMPUTE[compute], 1 if packed else 0, int(reps), ctypes.byref(v),
+                                             _stream_ptr()))
+    return float(v.value)
+
+
+def set_wait_limit(polls: int = 0):
+    """Polls a strip-pipeline hand-off wait makes before it reports SK_ERR_DEVICE_TIMEOUT
+    (``sigkernel_set_wait_limit``; 0 restores the default)."""
+    load_library().sigkernel_set_wait_limit(int(polls))

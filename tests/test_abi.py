@@ -65,7 +65,7 @@ def test_version_and_host_side_validation(lib):
     assert lib.sigkernel_workspace_size(1, ctypes.byref(X), ctypes.byref(X), 2, ctypes.c_int64(-1),
                                         ctypes.byref(bad), ctypes.byref(n)) == -1
     assert b"together" in lib.sigkernel_last_error()
-    bad = sk._options("approx", 6, flags=256)
+    bad = sk._options("approx", 6, flags=1 << 20)
     assert lib.sigkernel_workspace_size(1, ctypes.byref(X), ctypes.byref(X), 2, ctypes.c_int64(-1),
                                         ctypes.byref(bad), ctypes.byref(n)) == -1
     assert b"unknown flag" in lib.sigkernel_last_error()

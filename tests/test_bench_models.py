@@ -36,10 +36,13 @@ def test_tape_steps_match_the_schedule(bench, points):
 
 
 def test_tape_bytes_of_the_bench_launch(bench):
-    # 128 x 128 pairs of 257-point paths, N = 6: 16 floats of cell inputs per lane (64 B) and one
-    # dk/dM float per lane, per warp step
+    # 128 x 128 pairs of 257-point paths, N = 6: per lane and warp step a row of 14 floats (the 12
+    # derivatives d a'_n/dM, d b'_n/dM, the exponent and M: 56 B) written by the forward, read by
+    # the adjoint, which writes one dk/dM float
     assert bench.tape_steps(257) == 2079
-    assert bench.tape_adjoint_bytes(128 * 128, 257) == 16384 * 2079 * 32 * (64 + 4)
+    assert bench.tape_forward_bytes(128 * 128, 257) == 16384 * 2079 * 32 * 56
+    assert bench.tape_adjoint_bytes(128 * 128, 257) == 16384 * 2079 * 32 * (56 + 4)
+    assert bench.tape_adjoint_bytes(128 * 128, 257, esize=8) == 16384 * 2079 * 32 * (112 + 8)
 
 
 def test_flops_per_cell(bench):
@@ -48,7 +51,10 @@ def test_flops_per_cell(bench):
     hankel = 2 * (N + 1) * N                             # both edges: N couplings per output
     scale = 2 * (N + 1)                                  # e_n times each coupling sum
     assert bench.flops_per_cell(N, d) == 2 * (toeplitz + hankel + scale + N + d) == 336
-    assert bench.tape_adjoint_flops_per_cell(N) == 584
+    assert bench.tape_forward_flops_per_cell(N, d) == 336 + 2 * 2 * N
+    # adjoint: Hankel weights, Toeplitz transposes and Hankel couplings of both edges, dk/dM from
+    # the 2N recorded derivatives, and e_m rebuilt from M
+    assert bench.tape_adjoint_flops_per_cell(N) == 2 * (2 * (N + 1) + toeplitz + hankel + 2 * N + N) == 344
 
 
 def test_clock_samples_are_summarised_and_the_temporary_file_removed(bench, monkeypatch):

@@ -46,14 +46,16 @@ def _oracle_gram_grad(X, Y, Wt, N, lam, sym, scheme="approx"):
     return gX, gY
 
 
+@pytest.mark.parametrize("checkpoint", [False, True])
 @pytest.mark.parametrize("N,lam", [(2, 0), (4, 0), (6, 0), (6, 1), (9, 0)])
-def test_pairs_backward_f64_matches_complex_step(N, lam):
+def test_pairs_backward_f64_matches_complex_step(N, lam, checkpoint):
+    """sigkernel_backward from chunked forward tapes (default) and the checkpointing adjoint."""
     X = W.brownian(2, 40, 3, seed=51)   # 39 rows: two strips with a ragged tail
     Y = W.brownian(2, 35, 3, seed=52)
     pa, pb = [0, 1, 1], [1, 0, 1]
     wts = np.array([0.7, -1.3, 2.0])
     gX, gY = sk.sigkernel_backward(_cuda(wts), _cuda(X), _cuda(Y), pair_a=pa, pair_b=pb, degree=N, dyadic=lam,
-                                   compute="f64")
+                                   compute="f64", checkpoint=checkpoint)
     torch.cuda.synchronize()
     assert sk.device_status() == 0
     rX = np.zeros_like(X)
@@ -66,12 +68,14 @@ def test_pairs_backward_f64_matches_complex_step(N, lam):
     assert _scaled_err(gY.cpu().numpy().reshape(Y.shape), rY) < 1e-9
 
 
-def test_pairs_backward_f32_matches_complex_step():
+@pytest.mark.parametrize("checkpoint", [False, True])
+def test_pairs_backward_f32_matches_complex_step(checkpoint):
     X = W.brownian(2, 70, 4, seed=53)
     Y = W.brownian(2, 66, 4, seed=54)
     pa, pb = [0, 1], [1, 0]
     wts = np.array([1.0, 0.5])
-    gX, gY = sk.sigkernel_backward(_cuda(wts), _cuda(X), _cuda(Y), pair_a=pa, pair_b=pb, degree=6, compute="f32")
+    gX, gY = sk.sigkernel_backward(_cuda(wts), _cuda(X), _cuda(Y), pair_a=pa, pair_b=pb, degree=6, compute="f32",
+                                   checkpoint=checkpoint)
     torch.cuda.synchronize()
     rX = np.zeros_like(X)
     rY = np.zeros_like(Y)
@@ -83,14 +87,16 @@ def test_pairs_backward_f32_matches_complex_step():
     assert _scaled_err(gY.cpu().numpy().reshape(Y.shape), rY) < 1e-4
 
 
+@pytest.mark.parametrize("checkpoint", [False, True])
 @pytest.mark.parametrize("sym", [False, True])
 @pytest.mark.parametrize("compute", ["f64", "f32"])
-def test_gram_backward_matches_oracle(sym, compute):
+def test_gram_backward_matches_oracle(sym, compute, checkpoint):
     X = W.brownian(3, 33, 2, seed=55)
     Y = X if sym else W.brownian(4, 29, 2, seed=56)
     rng = np.random.default_rng(57)
     Wt = rng.normal(size=(X.shape[0], Y.shape[0]))
-    gX, gY = sk.sigkernel_backward(_cuda(Wt), _cuda(X), None if sym else _cuda(Y), degree=5, compute=compute)
+    gX, gY = sk.sigkernel_backward(_cuda(Wt), _cuda(X), None if sym else _cuda(Y), degree=5, compute=compute,
+                                   checkpoint=checkpoint)
     torch.cuda.synchronize()
     assert sk.device_status() == 0
     rX, rY = _oracle_gram_grad(X, Y, Wt, 5, 0, sym)
@@ -249,10 +255,12 @@ def test_autograd_gram_and_mmd():
     assert abs(A.grad[1, 4, 1].item() - ref) < 1e-9 * max(1.0, A.grad.abs().max().item())
 
 
-def test_gradcheck_small():
+@pytest.mark.parametrize("tape", [None, True, False])
+def test_gradcheck_small(tape):
+    """gradcheck runs backward several times on one graph: the wrapper keeps its tape for that."""
     X = _cuda(W.brownian(2, 6, 2, seed=72)).requires_grad_(True)
     Y = _cuda(W.brownian(2, 5, 2, seed=73)).requires_grad_(True)
-    kern = sk.SigKernel("approx", 5, 0, "f64")
+    kern = sk.SigKernel("approx", 5, 0, "f64", tape=tape)
     assert torch.autograd.gradcheck(lambda x, y: kern.gram(x, y), (X, Y), eps=1e-6, atol=1e-8, rtol=1e-6)
 
 
@@ -326,7 +334,8 @@ def test_tape_backward_long_paths_match_checkpoint_adjoint(compute, tol):
     out, tape = sk.sigkernel_forward_tape(_cuda(X), _cuda(Y), pair_a=pa, pair_b=pb, degree=6, compute=compute)
     gX, gY = sk.sigkernel_backward_tape(tape, wts, _cuda(X), _cuda(Y), pair_a=pa, pair_b=pb, degree=6,
                                         compute=compute)
-    cX, cY = sk.sigkernel_backward(wts, _cuda(X), _cuda(Y), pair_a=pa, pair_b=pb, degree=6, compute=compute)
+    cX, cY = sk.sigkernel_backward(wts, _cuda(X), _cuda(Y), pair_a=pa, pair_b=pb, degree=6, compute=compute,
+                                   checkpoint=True)
     torch.cuda.synchronize()
     assert sk.device_status() == 0
     assert np.all(np.isfinite(gX.cpu().numpy()))
@@ -344,7 +353,7 @@ def test_tape_backward_column_windows_match_checkpoint_adjoint(compute, tol):
     Wt = _cuda([[0.9, -0.4], [1.3, 0.2]])
     G, tape = sk.sigkernel_forward_tape(_cuda(X), _cuda(Y), degree=5, dyadic=1, compute=compute)
     gX, gY = sk.sigkernel_backward_tape(tape, Wt, _cuda(X), _cuda(Y), degree=5, dyadic=1, compute=compute)
-    cX, cY = sk.sigkernel_backward(Wt, _cuda(X), _cuda(Y), degree=5, dyadic=1, compute=compute)
+    cX, cY = sk.sigkernel_backward(Wt, _cuda(X), _cuda(Y), degree=5, dyadic=1, compute=compute, checkpoint=True)
     torch.cuda.synchronize()
     assert sk.device_status() == 0
     assert _scaled_err(gX.cpu().numpy(), cX.cpu().numpy()) < tol

@@ -89,6 +89,7 @@ def test_a_bad_relabelling_is_reported_and_isolated():
     assert sk.device_status() == -8
     stats = out[2].cpu().numpy()
     assert np.isnan(stats[3]) and np.all(np.isfinite(np.delete(stats, 3)))
+    assert np.isnan(out[1].item())  # no p-value over the remaining relabellings
     good = np.delete(labels, 3, axis=0)
     _, _, r_stats = oracle.mmd2_permutation_test(A, B, good, "approx", 4)
     assert np.max(np.abs(np.delete(stats, 3) - r_stats)) < 1e-11
