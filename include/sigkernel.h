@@ -115,10 +115,17 @@ enum {
                                        its two increment rows.  By default, with d > 8, each warp
                                        first computes a strip's M_ij for all columns at once (the
                                        same values bit for bit) */
-    SK_FLAG_CHECKPOINT = 256        /* sigkernel_backward, approximation scheme: run the
+    SK_FLAG_CHECKPOINT = 256,       /* sigkernel_backward, approximation scheme: run the
                                        checkpointing adjoint (no tape; its workspace grows with the
                                        paths, not with the pair count) instead of the default
                                        adjoint from chunked forward tapes */
+    SK_FLAG_NO_TC = 512             /* adjoints from a tape in FP32: contract dk/dM with the
+                                       increments on the FMA pipe.  By default, with 8 < d <= 32,
+                                       that contraction runs on the tensor cores (BF16 high and low
+                                       parts of dk/dM and of the increments, three products each,
+                                       FP32 accumulation: about 2^-17 relative per product) when
+                                       the refined grid of the longest pair fits its tensor memory
+                                       ((ceil(rows / 128) + ceil(cols / 128)) x (16 or 32) <= 256) */
 };
 
 typedef struct {

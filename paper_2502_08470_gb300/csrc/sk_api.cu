@@ -214,7 +214,8 @@ int check_options(const sk_options* o, int32_t d, int32_t dtype) {
     if (o->warps_per_block != 0 && o->warps_per_block != 1 && o->warps_per_block != 2 && o->warps_per_block != 4)
         return fail(SK_ERR_UNSUPPORTED, "warps_per_block %d (this build: 0, 1, 2 or 4)", o->warps_per_block);
     if (o->flags & ~(SK_FLAG_SYMMETRIC | SK_FLAG_INCREMENTS | SK_FLAG_UNBIASED | SK_FLAG_NO_SORT | SK_FLAG_TIME_KERNEL |
-                     SK_FLAG_STRIP_PIPELINE | SK_FLAG_NO_STRIP_PIPELINE | SK_FLAG_NO_TILED_M | SK_FLAG_CHECKPOINT))
+                     SK_FLAG_STRIP_PIPELINE | SK_FLAG_NO_STRIP_PIPELINE | SK_FLAG_NO_TILED_M | SK_FLAG_CHECKPOINT |
+                     SK_FLAG_NO_TC))
         return fail(SK_ERR_INVALID_ARG, "unknown flag bits 0x%x", o->flags);
     if ((o->flags & SK_FLAG_STRIP_PIPELINE) && (o->flags & SK_FLAG_NO_STRIP_PIPELINE))
         return fail(SK_ERR_INVALID_ARG, "SK_FLAG_STRIP_PIPELINE and SK_FLAG_NO_STRIP_PIPELINE together");
@@ -755,6 +756,11 @@ struct TapeBwdPlan {
     const void* ckern;
     int smem_bytes, cblocks, csmem, cC;
     int64_t cols_max, off_rbuf, off_rexp, slot_bytes, mb_stride, acc_bytes;
+    // tensor-core contraction: operand coordinates (16 or 32), 128-row blocks of the longest X and
+    // Y paths, operand tiles in the workspace, CTAs
+    bool tc;
+    int tcN, nrb, ncb, tc_sms;
+    size_t off_xt, off_yt;
     size_t off_gincx, off_gincy, off_scratch, off_mbuf, total;
 };
 
@@ -782,6 +788,19 @@ int plan_backward_tape(const sk_paths* X, const sk_paths* Y, int32_t d, int32_t 
     // dk/dM buffer: the tape's [step][lane] grid of one element per cell
     // (plus the rows past an item's last step that the contraction's tiles may read)
     b.mb_stride = static_cast<int64_t>(align256(static_cast<size_t>(b.t.nsteps + kContractSlack) * 32 * esize));
+    // Tensor-core contraction (FP32, 8 < d <= 32): dk/dM as BF16 hi/lo tiles of 128 x 128 cells
+    // instead, when the longest pair's sums fit one half of the tensor memory.
+    {
+        const int64_t pts = (o->flags & SK_FLAG_INCREMENTS) ? 0 : 1;
+        const int64_t rmax = std::max<int64_t>(X->max_len - pts, 1) << o->dyadic;
+        const int64_t cmax = std::max<int64_t>(Y->max_len - pts, 1) << o->dyadic;
+        b.tcN = p.dpad <= 16 ? 16 : 32;
+        b.nrb = static_cast<int>((rmax + 127) / 128);
+        b.ncb = static_cast<int>((cmax + 127) / 128);
+        b.tc = p.T == 1 && !(o->flags & SK_FLAG_NO_TC) && p.dpad > 8 && p.dpad <= 32 &&
+               static_cast<int64_t>(b.nrb + b.ncb) * b.tcN <= 256;
+        if (b.tc) b.mb_stride = static_cast<int64_t>(b.nrb) * b.ncb * 65536;
+    }
     // contraction: per-warp rings and staged rows, then the block's column accumulator
     int cwarp = 0, cwin = 0;
     if (p.T) {
@@ -808,6 +827,7 @@ int plan_backward_tape(const sk_paths* X, const sk_paths* Y, int32_t d, int32_t 
     SK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&cper_sm, b.ckern, kContractWarps * 32,
                                                           static_cast<size_t>(b.csmem)));
     if (cper_sm < 1) return fail(SK_ERR_UNSUPPORTED, "contraction kernel does not fit an SM");
+    b.tc_sms = sms;
     b.cblocks = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(npairs, static_cast<int64_t>(sms) * cper_sm)));
     const int64_t want = (npairs + kFwdWarps - 1) / kFwdWarps;
     b.f.blocks = static_cast<int>(std::max<int64_t>(1, std::min(want, static_cast<int64_t>(sms) * per_sm)));
@@ -821,6 +841,13 @@ int plan_backward_tape(const sk_paths* X, const sk_paths* Y, int32_t d, int32_t 
     o2 = align256(o2);
     b.off_mbuf = o2;
     o2 += static_cast<size_t>(npairs) * static_cast<size_t>(b.mb_stride);
+    o2 = align256(o2);
+    b.off_xt = b.off_yt = o2;
+    if (b.tc) {
+        o2 += align256(tc_operand_bytes(b.tcN, X->count, b.nrb));
+        b.off_yt = p.same_xy ? b.off_xt : o2;
+        if (!p.same_xy) o2 += align256(tc_operand_bytes(b.tcN, Y->count, b.ncb));
+    }
     b.total = o2 + 256;
     return SK_OK;
 }
@@ -874,6 +901,16 @@ int launch_backward_tape(const sk_paths* X, const sk_paths* Y, int32_t d, int32_
     B.mbuf = base + b.off_mbuf;
     B.mb_stride = b.mb_stride;
     B.acc_bytes = b.acc_bytes;
+    if (b.tc) {  // dk/dM tiles for the tensor cores, and the transposed split increments
+        B.gtile = 1;
+        B.gt_ncb = b.ncb;
+        B.xt = base + b.off_xt;
+        B.yt = base + b.off_yt;
+        B.xt_nblk = b.nrb;
+        B.yt_nblk = p.same_xy ? b.nrb : b.ncb;
+        SK_CUDA(launch_tc_operands(b.tcN, L.X, inc_mode, L.lam, p.dpad, b.nrb, base + b.off_xt, st));
+        if (!p.same_xy) SK_CUDA(launch_tc_operands(b.tcN, L.Y, inc_mode, L.lam, p.dpad, b.ncb, base + b.off_yt, st));
+    }
     SK_CUDA(cudaMemsetAsync(base + p.off_queue, 0, 256, st));
     if (!(o->flags & SK_FLAG_NO_SORT) && npairs > 1) {
         unsigned int* hist = reinterpret_cast<unsigned int*>(base + p.off_hist);
@@ -898,8 +935,9 @@ int launch_backward_tape(const sk_paths* X, const sk_paths* Y, int32_t d, int32_
         SK_CUDA(cudaEventRecord(t_ev1, st));
         t_timed = true;
     }
-    SK_CUDA(cudaLaunchKernel(b.ckern, dim3(b.cblocks), dim3(kContractWarps * 32), args,
-                             static_cast<size_t>(b.csmem), st));
+    if (b.tc) SK_CUDA(launch_tc_contraction(b.tcN, B, b.nrb, b.tc_sms, st));
+    else SK_CUDA(cudaLaunchKernel(b.ckern, dim3(b.cblocks), dim3(kContractWarps * 32), args,
+                                  static_cast<size_t>(b.csmem), st));
     return SK_OK;
 }
 
@@ -1013,7 +1051,7 @@ int plan_mmd2(const sk_paths* A, const sk_paths* Bp, int32_t d, int32_t dtype, c
     m.grads = grads;
     m.os = *o;
     m.os.flags = (o->flags & (SK_FLAG_INCREMENTS | SK_FLAG_NO_SORT | SK_FLAG_TIME_KERNEL | SK_FLAG_STRIP_PIPELINE |
-                              SK_FLAG_NO_STRIP_PIPELINE | SK_FLAG_NO_TILED_M)) | SK_FLAG_SYMMETRIC;
+                              SK_FLAG_NO_STRIP_PIPELINE | SK_FLAG_NO_TILED_M | SK_FLAG_NO_TC)) | SK_FLAG_SYMMETRIC;
     m.of = m.os;
     m.of.flags &= ~SK_FLAG_SYMMETRIC;
     const sk_paths* xs[3] = {A, Bp, A};

@@ -33,6 +33,7 @@
 
 #include "sk_fwd_poly.cuh"
 #include "sk_tma.cuh"
+#include "sk_umma.cuh"
 
 namespace sk {
 
@@ -47,10 +48,31 @@ struct BwdParams {
     int64_t strips_max;       // strips of the longest x path
     int64_t seg_max;          // K-step segments of the longest pair
     int64_t off_fbuf, off_fexp, off_rbuf, off_rexp, off_ybar;  // byte offsets inside a warp slot
-    void* mbuf;               // tape adjoint: per-item dk/dM, [step][lane] of T
+    void* mbuf;               // tape adjoint: per-item dk/dM, [step][lane] of T (or tiles, gtile)
     int64_t mb_stride;        // bytes per item of mbuf
     int64_t acc_bytes;        // contraction: shared-memory column accumulator bytes per block
+    // Tensor-core contraction (FP32): the adjoint writes dk/dM as BF16 hi/lo tiles (gtile_index)
+    // of gt_ncb column blocks per row block, and the contraction reads them with bulk copies.
+    int32_t gtile;
+    int32_t gt_ncb;
+    const void* xt;           // transposed, split increments of X / Y (tc_operand_offset), or NULL
+    const void* yt;
+    int32_t xt_nblk, yt_nblk; // 128-row blocks per path in xt / yt
 };
+
+// dk/dM tiles for the tensor-core contraction.  An item's buffer holds 128 x 128 blocks of the
+// refined cell grid (row block i / 128, column block j / 128; gt_ncb column blocks per row block),
+// 64 KB each: the BF16 high parts of the 128 x 128 values, then their BF16 low parts
+// (value - high, rounded).  Within a plane, the values sit in 8 x 8 "core matrices" of 128
+// contiguous bytes, core matrix ((i % 128) / 8, (j % 128) / 8) at index ((i % 128) / 8) * 16 +
+// (j % 128) / 8, element (i % 8, j % 8) at (i % 8) * 8 + (j % 8).  That is the layout the tensor
+// core reads without swizzling, both as a row-major (K = j) operand and as its transpose (K = i).
+__device__ __forceinline__ int64_t gtile_index(int i, int j, int ncb) {
+    const int64_t blk = static_cast<int64_t>(i >> 7) * ncb + (j >> 7);
+    const int ii = i & 127, jj = j & 127;
+    return blk * 32768 + ((ii >> 3) * 16 + (jj >> 3)) * 64 + (ii & 7) * 8 + (jj & 7);
+}
+constexpr int kGtilePlane = 16384;  // BF16 elements of one plane of a block
 
 template <typename T>
 __device__ __forceinline__ T pow2c(int e) {  // 2^e, or 0 below the normal range
@@ -849,6 +871,25 @@ __global__ void __launch_bounds__(kFwdWarps * 32, (bwd_tape_min_blocks<T, N, INT
         const int ek = L.tape_ek[item];
         const char* tape = static_cast<const char*>(L.tape) + item * L.tape_stride;
         T* mout = reinterpret_cast<T*>(static_cast<char*>(B.mbuf) + item * B.mb_stride);
+        if constexpr (std::is_same<T, float>::value) {
+            if (B.gtile) {  // cells of the padded tile grid outside the pair's grid hold zero
+                __nv_bfloat16* gt = reinterpret_cast<__nv_bfloat16*>(mout);
+                const int rpad = (rows + 127) & ~127, cpad = (cols + 127) & ~127;
+                const __nv_bfloat16 z = __float2bfloat16_rn(0.f);
+                for (int i = rows; i < rpad; ++i)
+                    for (int j = lane; j < cpad; j += 32) {
+                        const int64_t q = gtile_index(i, j, B.gt_ncb);
+                        gt[q] = z;
+                        gt[q + kGtilePlane] = z;
+                    }
+                for (int i = 0; i < rows; ++i)
+                    for (int j = cols + lane; j < cpad; j += 32) {
+                        const int64_t q = gtile_index(i, j, B.gt_ncb);
+                        gt[q] = z;
+                        gt[q + kGtilePlane] = z;
+                    }
+            }
+        }
 
         // Edge conditions of the reverse sweep.  A lane's right-edge input (no cell to the right)
         // is zero: gra starts at zero and is cleared whenever the lane moves down a strip.  The top
@@ -1016,7 +1057,21 @@ __global__ void __launch_bounds__(kFwdWarps * 32, (bwd_tape_min_blocks<T, N, INT
                     if (kRescale) rexp[jj] = gbe;
                 }
             }
-            mout[static_cast<int64_t>(step) * 32 + ((lane + step) & 31)] = mrel;  // skewed row
+            bool tiled = false;
+            if constexpr (std::is_same<T, float>::value) {
+                if (B.gtile) {  // BF16 hi/lo tiles for the tensor-core contraction
+                    tiled = true;
+                    if (active) {
+                        __nv_bfloat16 h, l;
+                        split_bf16(mrel, h, l);
+                        __nv_bfloat16* gt = reinterpret_cast<__nv_bfloat16*>(mout);
+                        const int64_t q = gtile_index(row, jj, B.gt_ncb);
+                        gt[q] = h;
+                        gt[q + kGtilePlane] = l;
+                    }
+                }
+            }
+            if (!tiled) mout[static_cast<int64_t>(step) * 32 + ((lane + step) & 31)] = mrel;  // skewed row
             __syncwarp();
             if (s >= 0 && --jj < 0) {  // down one strip: the next row starts at the right edge
                 jj = period - 1;

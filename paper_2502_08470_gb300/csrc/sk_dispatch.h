@@ -91,6 +91,18 @@ const void* bwd_contract_ptr_f64(int C);
 }  // namespace sk
 
 namespace sk {
+struct PathSet;
+struct BwdParams;
+// Tensor-core contraction of the tape adjoint's dk/dM tiles (FP32 compute; N = 16 or 32 operand
+// coordinates): operand tiles of a path set (nblk 128-row blocks per path, tc_operand_bytes
+// bytes), and the contraction itself on `sms` CTAs (nrb_max: row blocks of the longest X path).
+size_t tc_operand_bytes(int N, int64_t paths, int nblk);
+cudaError_t launch_tc_operands(int N, const PathSet& S, int inc_mode, int lam, int dpad, int nblk, void* out,
+                               cudaStream_t st);
+cudaError_t launch_tc_contraction(int N, const BwdParams& B, int nrb_max, int sms, cudaStream_t st);
+}  // namespace sk
+
+namespace sk {
 // Message returned by sigkernel_last_error() on this host thread (for entry points in other units).
 void set_last_error(const char* msg);
 }  // namespace sk

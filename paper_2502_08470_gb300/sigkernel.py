@@ -26,7 +26,7 @@ SCHEMES = {"fd1": 0, "fd2": 1, "approx": 2, "interp": 3, "fd_implicit": 4}
 COMPUTE = {"f64": 0, "f32": 1}
 DTYPES = {torch.float64: 0, torch.float32: 1, torch.bfloat16: 2}
 FLAG_SYMMETRIC, FLAG_INCREMENTS, FLAG_UNBIASED, FLAG_NO_SORT, FLAG_TIME_KERNEL = 1, 2, 4, 8, 16
-FLAG_STRIP_PIPELINE, FLAG_NO_STRIP_PIPELINE, FLAG_NO_TILED_M, FLAG_CHECKPOINT = 32, 64, 128, 256
+FLAG_STRIP_PIPELINE, FLAG_NO_STRIP_PIPELINE, FLAG_NO_TILED_M, FLAG_CHECKPOINT, FLAG_NO_TC = 32, 64, 128, 256, 512
 
 
 def _pipe_flags(strip_pipeline) -> int:
@@ -279,12 +279,14 @@ def autotune_clear():
 
 
 def sigkernel_backward(grad_out, X, Y=None, pair_a=None, pair_b=None, scheme="approx", degree=6, dyadic=0,
-                       compute="f64", sort=True, time_kernel: bool = False, checkpoint: bool = False):
+                       compute="f64", sort=True, time_kernel: bool = False, checkpoint: bool = False,
+                       tensor_cores: bool = True):
     """Gradients of sum(grad_out * k_hat) with respect to the rows of X and Y (float64 CUDA tensors
     shaped like the rows).  Gram mode when ``pair_a`` is None (``grad_out`` [nx, ny]); with Y None
     (or Y is X) the symmetric Gram of X, and the single returned gradient is the total.
     ``checkpoint`` selects the checkpointing adjoint of the approximation scheme (SK_FLAG_CHECKPOINT)
-    instead of the adjoint from chunked forward tapes."""
+    instead of the adjoint from chunked forward tapes; ``tensor_cores=False`` keeps the dk/dM
+    contraction on the FMA pipe (SK_FLAG_NO_TC)."""
     sym = Y is None or Y is X
     X = as_paths(X)
     Y = X if sym else as_paths(Y)
@@ -293,7 +295,8 @@ def sigkernel_backward(grad_out, X, Y=None, pair_a=None, pair_b=None, scheme="ap
     gX = torch.zeros(X.rows.shape[0], X.d, dtype=torch.float64, device="cuda")
     same = sym or (X.rows.data_ptr() == Y.rows.data_ptr() and X.offsets.data_ptr() == Y.offsets.data_ptr())
     gY = gX if same else torch.zeros(Y.rows.shape[0], Y.d, dtype=torch.float64, device="cuda")
-    extra = (0 if sort else FLAG_NO_SORT) | (FLAG_TIME_KERNEL if time_kernel else 0) | (FLAG_CHECKPOINT if checkpoint else 0)
+    extra = ((0 if sort else FLAG_NO_SORT) | (FLAG_TIME_KERNEL if time_kernel else 0) | (FLAG_CHECKPOINT if checkpoint else 0)
+             | (0 if tensor_cores else FLAG_NO_TC))
     if pair_a is None:
         opt = _options(scheme, degree, dyadic, compute, _flags(X, extra | (FLAG_SYMMETRIC if sym else 0)))
         ws = _workspace(OP_BACKWARD, cX, cY, X.d, -1, opt)
@@ -350,15 +353,16 @@ def sigkernel_forward_tape(X, Y=None, pair_a=None, pair_b=None, scheme="approx",
 
 
 def sigkernel_backward_tape(tape, grad_out, X, Y=None, pair_a=None, pair_b=None, scheme="approx", degree=6, dyadic=0,
-                            compute="f32", sort=True, time_kernel=False):
-    """Gradients from a tape recorded by ``sigkernel_forward_tape`` with the same arguments."""
+                            compute="f32", sort=True, time_kernel=False, tensor_cores: bool = True):
+    """Gradients from a tape recorded by ``sigkernel_forward_tape`` with the same arguments
+    (``tensor_cores=False``: the dk/dM contraction on the FMA pipe, SK_FLAG_NO_TC)."""
     sym = pair_a is None and (Y is None or Y is X)
     X = as_paths(X)
     Y = X if (Y is None or Y is X) else as_paths(Y)
     cX, cY = _cpaths(X), _cpaths(Y)
     pa_ptr, pb_ptr, n, keep = _pair_args(X, pair_a, pair_b, sym)
     flags = _flags(X, (FLAG_SYMMETRIC if sym else 0) | (0 if sort else FLAG_NO_SORT)
-                   | (FLAG_TIME_KERNEL if time_kernel else 0))
+                   | (FLAG_TIME_KERNEL if time_kernel else 0) | (0 if tensor_cores else FLAG_NO_TC))
     opt = _options(scheme, degree, dyadic, compute, flags)
     g = torch.as_tensor(grad_out, dtype=torch.float64, device="cuda").contiguous()
     gX = torch.zeros(X.rows.shape[0], X.d, dtype=torch.float64, device="cuda")
@@ -372,12 +376,14 @@ def sigkernel_backward_tape(tape, grad_out, X, Y=None, pair_a=None, pair_b=None,
     return gX, gY
 
 
-def sigkernel_mmd2(A, B, scheme="approx", degree=6, dyadic=0, compute="f64", unbiased=False, grads=False):
+def sigkernel_mmd2(A, B, scheme="approx", degree=6, dyadic=0, compute="f64", unbiased=False, grads=False,
+                   tensor_cores: bool = True):
     """MMD^2 between path sets A and B; returns (mmd2, [mean K_AA, mean K_BB, mean K_AB]) or, with
     ``grads``, also (dMMD2/dA rows, dMMD2/dB rows) as float64 CUDA tensors."""
     A, B = as_paths(A), as_paths(B)
     cA, cB = _cpaths(A), _cpaths(B)
-    opt = _options(scheme, degree, dyadic, compute, _flags(A, FLAG_UNBIASED if unbiased else 0))
+    opt = _options(scheme, degree, dyadic, compute, _flags(A, (FLAG_UNBIASED if unbiased else 0)
+                                                           | (0 if tensor_cores else FLAG_NO_TC)))
     ws = _workspace(OP_MMD2, cA, cB, A.d, 1 if grads else 0, opt)
     out = torch.empty(4, dtype=torch.float64, device="cuda")
     gA = torch.empty(A.rows.shape[0], A.d, dtype=torch.float64, device="cuda") if grads else None
