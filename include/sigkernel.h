@@ -206,15 +206,14 @@ int sigkernel_gram(const sk_paths* X, const sk_paths* Y, int32_t d, int32_t dtyp
  *           the existing contents (the caller zeroes it first for a plain gradient); NULL skips.
  *   grad_Y  likewise for Y.  When Y is X (same rows pointer) both accumulate into the same
  *           buffer correctly if grad_X == grad_Y.
- * Both polynomial schemes record forward tapes in chunks of pairs (at most 48 GiB each, in the
- * workspace) and run the tape adjoint after each chunk (sigkernel_forward_tape and
- * sigkernel_backward_tape below, one chunk at a time), so the call re-runs the forward sweep once.
- * When the paths are so long that a chunk cannot fill the GPU, SK_POLY_APPROX runs the
- * checkpointing adjoint instead (antidiagonal checkpoints every few steps, the forward cells
- * replayed from them; d <= 32) and SK_POLY_INTERP, which has none, returns SK_ERR_UNSUPPORTED.
- * SK_FLAG_CHECKPOINT asks for the checkpointing adjoint of SK_POLY_APPROX outright.  The FD
- * schemes return SK_ERR_UNSUPPORTED.  Orders with an adjoint: 2..10 and 12 (approximation),
- * 2..12 (interpolation).
+ * Every scheme records forward tapes in chunks of pairs (at most 48 GiB each, in the workspace)
+ * and runs the tape adjoint after each chunk (sigkernel_forward_tape and sigkernel_backward_tape
+ * below, one chunk at a time), so the call re-runs the forward sweep once.  When the paths are so
+ * long that a chunk cannot fill the GPU, SK_POLY_APPROX runs the checkpointing adjoint instead
+ * (antidiagonal checkpoints every few steps, the forward cells replayed from them; d <= 32) and
+ * the other schemes, which have none, return SK_ERR_UNSUPPORTED.  SK_FLAG_CHECKPOINT asks for the
+ * checkpointing adjoint of SK_POLY_APPROX outright.  Orders with an adjoint: 2..10 and 12
+ * (approximation), 2..12 (interpolation); the FD schemes for dyadic orders 0..4.
  * Accumulation uses device atomics, so the last bits of the gradient can vary between runs.
  */
 int sigkernel_backward(const sk_paths* X, const sk_paths* Y, int32_t d, int32_t dtype,
@@ -223,14 +222,16 @@ int sigkernel_backward(const sk_paths* X, const sk_paths* Y, int32_t d, int32_t 
                        double* grad_Y, void* workspace, size_t workspace_bytes, void* stream);
 
 /*
- * Forward tape (polynomial schemes; approximation orders 2..10 and 12, interpolation orders
- * 2..12).  sigkernel_forward_tape computes the same results as sigkernel_pairs / sigkernel_gram
- * (Gram mode when pair_a is NULL; `out` is then [X->count][Y->count] and SK_FLAG_SYMMETRIC
- * applies) and also records, in the caller's `tape`, what the adjoint needs of every cell and
- * the exponent of each k_hat.  For SK_POLY_INTERP that is the cell's inputs (the two incoming
- * edge coefficient vectors, their exponent and the cell's M: 2N+4 elements padded to 16 bytes);
- * for SK_POLY_APPROX it is the derivatives of the cell's two outgoing edge vectors with respect
- * to M (orders 1..N of each), their exponent and M: 2N+2 elements.  sigkernel_backward_tape then
+ * Forward tape (approximation orders 2..10 and 12, interpolation orders 2..12, the FD schemes at
+ * dyadic orders 0..4).  sigkernel_forward_tape computes the same results as sigkernel_pairs /
+ * sigkernel_gram (Gram mode when pair_a is NULL; `out` is then [X->count][Y->count] and
+ * SK_FLAG_SYMMETRIC applies) and also records, in the caller's `tape`, what the adjoint needs of
+ * every cell and the exponent of each k_hat.  For SK_POLY_INTERP that is the cell's inputs (the
+ * two incoming edge coefficient vectors, their exponent and the cell's M: 2N+4 elements padded to
+ * 16 bytes); for SK_POLY_APPROX it is the derivatives of the cell's two outgoing edge vectors
+ * with respect to M (orders 1..N of each), their exponent and M: 2N+2 elements; for the FD
+ * schemes, per refined column, a lane's 2^lambda node differences, the two bottom nodes, the
+ * sub-cell m and the exponent (2^lambda + 4 elements padded to 16 bytes).  sigkernel_backward_tape then
  * runs the adjoint from the tape without recomputing the forward sweep; it writes every cell's
  * dL/dM into its workspace and contracts that with the increments in a second kernel.  Both
  * calls must use the same X, Y, pair list, options and path contents.
@@ -286,11 +287,12 @@ void sigkernel_autotune_clear(void);
  *   out       device double [4]: MMD^2, mean K_AA, mean K_BB, mean K_AB (as used above)
  *   grad_A/B  device double with A's / B's row layout, or NULL: d MMD^2 / d rows, OVERWRITTEN.
  * K_AA and K_BB are solved as symmetric Grams; the reduction runs in FP64 on the device.
- * Gradients (polynomial schemes) run the adjoint from forward tapes: each Gram block is
- * solved in chunks of pairs whose tape is at most 48 GiB, the chunk's forward recording the tape
- * and the tape adjoint following at once with the block's constant weights.  A block whose paths
- * are so long that a chunk cannot fill the GPU uses the checkpointing adjoint of
- * sigkernel_backward instead (d <= 32; approximation scheme only, else SK_ERR_UNSUPPORTED).
+ * Gradients (every scheme with an adjoint, see sigkernel_backward) run the adjoint from forward
+ * tapes: each Gram block is solved in chunks of pairs whose tape is at most 48 GiB, the chunk's
+ * forward recording the tape and the tape adjoint following at once with the block's constant
+ * weights.  A block whose paths are so long that a chunk cannot fill the GPU uses the
+ * checkpointing adjoint of sigkernel_backward instead (d <= 32; approximation scheme only, else
+ * SK_ERR_UNSUPPORTED).
  * The workspace (SK_OP_MMD2 with npairs != 0) includes the tape.
  */
 int sigkernel_mmd2(const sk_paths* A, const sk_paths* B, int32_t d, int32_t dtype,

@@ -257,7 +257,7 @@ int plan_forward(const sk_paths* X, const sk_paths* Y, int32_t d, int32_t dtype,
     p.mtile = mt_eligible && !(o->flags & SK_FLAG_NO_TILED_M);
     auto kernel_for = [&](bool coop) -> const void* {
         return poly ? fwd_poly_kernel_ptr(p.T, o->scheme == SK_POLY_INTERP, o->degree, coop, p.mtile, tape)
-                    : fwd_fd_kernel_ptr(p.T, o->scheme == SK_FD2 ? 2 : o->scheme == SK_FD_IMPLICIT ? 3 : 1, lam, coop);
+                    : fwd_fd_kernel_ptr(p.T, o->scheme == SK_FD2 ? 2 : o->scheme == SK_FD_IMPLICIT ? 3 : 1, lam, coop, tape);
     };
     p.kern = kernel_for(false);
     if (poly) {
@@ -407,19 +407,33 @@ int launch_increments(const sk_paths* S, int32_t d, int32_t dtype, int inc_mode,
 struct TapePlan {
     size_t ek_bytes, stride, total;
     int64_t nsteps;  // warp steps of the longest item
+    int64_t nsteps_c;  // FD: steps of the coarse-grid schedule of the dk/dM buffer
 };
 
+bool is_fd(const sk_options* o) {
+    return o->scheme == SK_FD1 || o->scheme == SK_FD2 || o->scheme == SK_FD_IMPLICIT;
+}
+int fd_order(const sk_options* o) { return o->scheme == SK_FD2 ? 2 : o->scheme == SK_FD_IMPLICIT ? 3 : 1; }
+
 int plan_tape(const sk_paths* X, const sk_paths* Y, const sk_options* o, int T, int64_t npairs, TapePlan& t) {
-    if (o->scheme != SK_POLY_APPROX && o->scheme != SK_POLY_INTERP)
-        return fail(SK_ERR_UNSUPPORTED, "a forward tape is recorded for the polynomial schemes");
     const int lam = o->dyadic;
     // grid rows and columns of the longest paths: their increments (one fewer than their points)
     const int64_t pts = (o->flags & SK_FLAG_INCREMENTS) ? 0 : 1;
-    const int64_t rows = std::max<int64_t>(X->max_len - pts, 1) << lam;
-    const int64_t cols = std::max<int64_t>(Y->max_len - pts, 1) << lam;
+    const int64_t lx = std::max<int64_t>(X->max_len - pts, 1), ly = std::max<int64_t>(Y->max_len - pts, 1);
+    int64_t rows = lx << lam;
+    const int64_t cols = ly << lam;
+    int row;
+    if (is_fd(o)) {
+        // FD: each lane sweeps 2^lambda node rows (one coarse row) over the refined columns
+        if (lam > 4) return fail(SK_ERR_UNSUPPORTED, "the FD adjoint supports dyadic orders 0..4");
+        rows = lx;
+        row = fd_tape_row_elems(T, lam);
+    } else {
+        const bool interp = o->scheme == SK_POLY_INTERP;
+        row = T ? tape_row<float>(o->degree, interp) : tape_row<double>(o->degree, interp);
+    }
     const int64_t nsteps = ((rows + 31) / 32 - 1) * std::max<int64_t>(cols, 32) + 31 + cols;
-    const bool interp = o->scheme == SK_POLY_INTERP;
-    const int row = T ? tape_row<float>(o->degree, interp) : tape_row<double>(o->degree, interp);
+    t.nsteps_c = ((lx + 31) / 32 - 1) * std::max<int64_t>(ly, 32) + 31 + ly;
     const int esize = T ? 4 : 8;
     t.nsteps = nsteps;
     t.ek_bytes = align256(static_cast<size_t>(npairs) * sizeof(int));
@@ -771,14 +785,16 @@ int plan_backward_tape(const sk_paths* X, const sk_paths* Y, int32_t d, int32_t 
     const Plan& p = b.f;
     if ((rc = plan_tape(X, Y, o, p.T, npairs, b.t)) != SK_OK) return rc;
     const bool interp = o->scheme == SK_POLY_INTERP;
-    b.kern = p.T ? bwd_tape_ptr_f32(o->degree, interp) : bwd_tape_ptr_f64(o->degree, interp);
+    const bool fd = is_fd(o);
+    b.kern = fd ? bwd_fd_tape_ptr(p.T, fd_order(o), o->dyadic)
+                : (p.T ? bwd_tape_ptr_f32(o->degree, interp) : bwd_tape_ptr_f64(o->degree, interp));
     if (!b.kern) return fail(SK_ERR_UNSUPPORTED, "no adjoint kernel for order %d", o->degree);
     // contraction: every coordinate of a padded increment row in one pass up to 32 (8, 16 or 32)
     b.cC = p.dpad <= 8 ? 8 : (p.dpad <= 16 ? 16 : 32);
     b.ckern = p.T ? bwd_contract_ptr_f32(b.cC) : bwd_contract_ptr_f64(b.cC);
     const int step_bytes = 32 * (p.T ? tape_row<float>(o->degree, interp) * 4 : tape_row<double>(o->degree, interp) * 8);
-    b.smem_bytes = kFwdWarps * bwd_tape_warp_bytes(step_bytes);
-    const int esize = p.T ? 4 : 8, N = o->degree;
+    b.smem_bytes = fd ? 0 : kFwdWarps * bwd_tape_warp_bytes(step_bytes);
+    const int esize = p.T ? 4 : 8, N = fd ? 0 : o->degree;  // FD hands one value per column down
     b.cols_max = std::max<int64_t>(Y->max_len << o->dyadic, 1);
     b.off_rbuf = 0;
     int64_t off = static_cast<int64_t>(align256(b.cols_max * (N + 1) * esize));
@@ -787,13 +803,16 @@ int plan_backward_tape(const sk_paths* X, const sk_paths* Y, int32_t d, int32_t 
     b.slot_bytes = off;
     // dk/dM buffer: the tape's [step][lane] grid of one element per cell
     // (plus the rows past an item's last step that the contraction's tiles may read)
-    b.mb_stride = static_cast<int64_t>(align256(static_cast<size_t>(b.t.nsteps + kContractSlack) * 32 * esize));
+    b.mb_stride = static_cast<int64_t>(align256(static_cast<size_t>((fd ? b.t.nsteps_c : b.t.nsteps) + kContractSlack) *
+                                                32 * esize));
     // Tensor-core contraction (FP32, 8 < d <= 32): dk/dM as BF16 hi/lo tiles of 128 x 128 cells
     // instead, when the longest pair's sums fit one half of the tensor memory.
     {
         const int64_t pts = (o->flags & SK_FLAG_INCREMENTS) ? 0 : 1;
-        const int64_t rmax = std::max<int64_t>(X->max_len - pts, 1) << o->dyadic;
-        const int64_t cmax = std::max<int64_t>(Y->max_len - pts, 1) << o->dyadic;
+        // the FD adjoint writes dk/dM on the coarse grid (the contraction then runs at lambda = 0)
+        const int clam = fd ? 0 : o->dyadic;
+        const int64_t rmax = std::max<int64_t>(X->max_len - pts, 1) << clam;
+        const int64_t cmax = std::max<int64_t>(Y->max_len - pts, 1) << clam;
         b.tcN = p.dpad <= 16 ? 16 : 32;
         b.nrb = static_cast<int>((rmax + 127) / 128);
         b.ncb = static_cast<int>((cmax + 127) / 128);
@@ -908,8 +927,9 @@ int launch_backward_tape(const sk_paths* X, const sk_paths* Y, int32_t d, int32_
         B.yt = base + b.off_yt;
         B.xt_nblk = b.nrb;
         B.yt_nblk = p.same_xy ? b.nrb : b.ncb;
-        SK_CUDA(launch_tc_operands(b.tcN, L.X, inc_mode, L.lam, p.dpad, b.nrb, base + b.off_xt, st));
-        if (!p.same_xy) SK_CUDA(launch_tc_operands(b.tcN, L.Y, inc_mode, L.lam, p.dpad, b.ncb, base + b.off_yt, st));
+        const int clam = is_fd(o) ? 0 : L.lam;
+        SK_CUDA(launch_tc_operands(b.tcN, L.X, inc_mode, clam, p.dpad, b.nrb, base + b.off_xt, st));
+        if (!p.same_xy) SK_CUDA(launch_tc_operands(b.tcN, L.Y, inc_mode, clam, p.dpad, b.ncb, base + b.off_yt, st));
     }
     SK_CUDA(cudaMemsetAsync(base + p.off_queue, 0, 256, st));
     if (!(o->flags & SK_FLAG_NO_SORT) && npairs > 1) {
@@ -935,6 +955,7 @@ int launch_backward_tape(const sk_paths* X, const sk_paths* Y, int32_t d, int32_
         SK_CUDA(cudaEventRecord(t_ev1, st));
         t_timed = true;
     }
+    if (is_fd(o)) B.L.lam = 0;  // the FD adjoint wrote dk/dM for the coarse cells
     if (b.tc) SK_CUDA(launch_tc_contraction(b.tcN, B, b.nrb, b.tc_sms, st));
     else SK_CUDA(cudaLaunchKernel(b.ckern, dim3(b.cblocks), dim3(kContractWarps * 32), args,
                                   static_cast<size_t>(b.csmem), st));
@@ -1046,8 +1067,8 @@ int plan_mmd2(const sk_paths* A, const sk_paths* Bp, int32_t d, int32_t dtype, c
     if (A->count < 1 || Bp->count < 1) return fail(SK_ERR_INVALID_ARG, "MMD^2 needs non-empty path sets");
     const bool unb = (o->flags & SK_FLAG_UNBIASED) != 0;
     if (unb && (A->count < 2 || Bp->count < 2)) return fail(SK_ERR_INVALID_ARG, "unbiased MMD^2 needs >= 2 paths per set");
-    if (grads && o->scheme != SK_POLY_APPROX && o->scheme != SK_POLY_INTERP)
-        return fail(SK_ERR_UNSUPPORTED, "MMD^2 gradients need a polynomial scheme");
+    if (grads && is_fd(o) && o->dyadic > 4)
+        return fail(SK_ERR_UNSUPPORTED, "MMD^2 gradients of the FD schemes support dyadic orders 0..4");
     m.grads = grads;
     m.os = *o;
     m.os.flags = (o->flags & (SK_FLAG_INCREMENTS | SK_FLAG_NO_SORT | SK_FLAG_TIME_KERNEL | SK_FLAG_STRIP_PIPELINE |
@@ -1083,10 +1104,10 @@ int plan_mmd2(const sk_paths* A, const sk_paths* Bp, int32_t d, int32_t dtype, c
         m.chunk[k] = std::min(c, m.items[k]);
         m.tape[k] = m.chunk[k] == m.items[k] || 2 * m.chunk[k] >= resident;
         if (!m.tape[k]) {  // checkpointing adjoint over the whole block
-            if (o->scheme == SK_POLY_INTERP)
+            if (o->scheme != SK_POLY_APPROX)
                 return fail(SK_ERR_UNSUPPORTED,
-                            "MMD^2 gradients of the interpolation scheme need forward tapes, and these paths are too "
-                            "long for a tape chunk to fill the GPU");
+                            "MMD^2 gradients of this scheme need forward tapes, and these paths are too long for a "
+                            "tape chunk to fill the GPU");
             m.chunk[k] = m.items[k];
             if ((rc = plan_forward(xs[k], ys[k], d, dtype, ok, modes[k], m.items[k], m.f[k], true)) != SK_OK) return rc;
             if ((rc = plan_backward(xs[k], ys[k], d, dtype, ok, modes[k], m.items[k], m.cb[k])) != SK_OK) return rc;
@@ -1230,9 +1251,9 @@ int plan_backward_chunked(const sk_paths* X, const sk_paths* Y, int32_t d, int32
     chunk = std::max<int64_t>(1, std::min(chunk, items));
     c.fits = !(chunk < items && 2 * chunk < resident);
     if (!c.fits) {
-        if (o->scheme == SK_POLY_INTERP)
-            return fail(SK_ERR_UNSUPPORTED, "sigkernel_backward of the interpolation scheme needs forward tapes, and "
-                                            "these paths are too long for a tape chunk to fill the GPU");
+        if (o->scheme != SK_POLY_APPROX)
+            return fail(SK_ERR_UNSUPPORTED, "sigkernel_backward of this scheme needs forward tapes, and these paths "
+                                            "are too long for a tape chunk to fill the GPU");
         return SK_OK;
     }
     c.items = items;
@@ -1254,7 +1275,7 @@ int plan_backward_chunked(const sk_paths* X, const sk_paths* Y, int32_t d, int32
 // sigkernel_backward runs from chunked tapes for both polynomial schemes unless the caller asks for
 // the checkpointing adjoint (approximation scheme only).
 bool uses_tape_chunks(const sk_options* o) {
-    if (o->scheme == SK_POLY_INTERP) return true;
+    if (o->scheme == SK_POLY_INTERP || is_fd(o)) return true;
     return o->scheme == SK_POLY_APPROX && !(o->flags & SK_FLAG_CHECKPOINT);
 }
 

@@ -74,6 +74,27 @@ __device__ __forceinline__ int64_t gtile_index(int i, int j, int ncb) {
 }
 constexpr int kGtilePlane = 16384;  // BF16 elements of one plane of a block
 
+// Zero both planes of the cells of an item's padded tile grid that lie outside its rows x cols
+// (the tensor-core contraction sums over whole 128-cell blocks).  One warp.
+__device__ __forceinline__ void gtile_zero_padding(void* item_tiles, int rows, int cols, int ncb) {
+    const int lane = threadIdx.x & 31;
+    __nv_bfloat16* gt = static_cast<__nv_bfloat16*>(item_tiles);
+    const int rpad = (rows + 127) & ~127, cpad = (cols + 127) & ~127;
+    const __nv_bfloat16 z = __float2bfloat16_rn(0.f);
+    for (int i = rows; i < rpad; ++i)
+        for (int j = lane; j < cpad; j += 32) {
+            const int64_t q = gtile_index(i, j, ncb);
+            gt[q] = z;
+            gt[q + kGtilePlane] = z;
+        }
+    for (int i = 0; i < rows; ++i)
+        for (int j = cols + lane; j < cpad; j += 32) {
+            const int64_t q = gtile_index(i, j, ncb);
+            gt[q] = z;
+            gt[q + kGtilePlane] = z;
+        }
+}
+
 template <typename T>
 __device__ __forceinline__ T pow2c(int e) {  // 2^e, or 0 below the normal range
     if constexpr (std::is_same<T, float>::value) return e < -126 ? 0.f : pow2f(e > 127 ? 127 : e);
@@ -872,23 +893,7 @@ __global__ void __launch_bounds__(kFwdWarps * 32, (bwd_tape_min_blocks<T, N, INT
         const char* tape = static_cast<const char*>(L.tape) + item * L.tape_stride;
         T* mout = reinterpret_cast<T*>(static_cast<char*>(B.mbuf) + item * B.mb_stride);
         if constexpr (std::is_same<T, float>::value) {
-            if (B.gtile) {  // cells of the padded tile grid outside the pair's grid hold zero
-                __nv_bfloat16* gt = reinterpret_cast<__nv_bfloat16*>(mout);
-                const int rpad = (rows + 127) & ~127, cpad = (cols + 127) & ~127;
-                const __nv_bfloat16 z = __float2bfloat16_rn(0.f);
-                for (int i = rows; i < rpad; ++i)
-                    for (int j = lane; j < cpad; j += 32) {
-                        const int64_t q = gtile_index(i, j, B.gt_ncb);
-                        gt[q] = z;
-                        gt[q + kGtilePlane] = z;
-                    }
-                for (int i = 0; i < rows; ++i)
-                    for (int j = cols + lane; j < cpad; j += 32) {
-                        const int64_t q = gtile_index(i, j, B.gt_ncb);
-                        gt[q] = z;
-                        gt[q + kGtilePlane] = z;
-                    }
-            }
+            if (B.gtile) gtile_zero_padding(mout, rows, cols, B.gt_ncb);  // cells outside the grid hold zero
         }
 
         // Edge conditions of the reverse sweep.  A lane's right-edge input (no cell to the right)

@@ -19,7 +19,12 @@ const void* fwd_poly_kernel_ptr(int T, bool interp, int N, bool coop, bool mt, b
 const void* fwd_approx_tape_ptr_f32(int N);
 const void* fwd_approx_tape_ptr_f32_mt(int N);
 const void* fwd_approx_tape_ptr_f64(int N);
-const void* fwd_fd_kernel_ptr(int T, int order, int lam, bool coop);
+const void* fwd_fd_kernel_ptr(int T, int order, int lam, bool coop, bool tape = false);
+// The FD forward that records the adjoint's tape, the FD adjoint from it (dyadic orders 0..4; NULL
+// otherwise), and the elements of one lane's tape row.
+const void* fwd_fd_tape_ptr(int T, int order, int lam);
+const void* bwd_fd_tape_ptr(int T, int order, int lam);
+int fd_tape_row_elems(int T, int lam);
 const void* fwd_fd_coop_ptr(int T, int order, int lam);
 const void* fwd_fd_implicit_ptr(int T, int lam, bool coop);  // order 3
 const void* fwd_approx_ptr_f32(int N);

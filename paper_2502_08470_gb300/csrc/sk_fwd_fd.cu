@@ -67,8 +67,9 @@ const void* fwd_poly_kernel_ptr(int T, bool interp, int N, bool coop, bool mt, b
     return interp ? fwd_interp_ptr_f64(N) : fwd_approx_ptr_f64(N);
 }
 
-const void* fwd_fd_kernel_ptr(int T, int order, int lam, bool coop) {
+const void* fwd_fd_kernel_ptr(int T, int order, int lam, bool coop, bool tape) {
     if (lam < 0 || lam > kLamMax) return nullptr;
+    if (tape) return coop ? nullptr : fwd_fd_tape_ptr(T, order, lam);
     if (order == 3) return fwd_fd_implicit_ptr(T, lam, coop);
     if (coop) return fwd_fd_coop_ptr(T, order, lam);
     if (T == 1) return order == 2 ? fd_rows<float, 2>(lam) : fd_rows<float, 1>(lam);

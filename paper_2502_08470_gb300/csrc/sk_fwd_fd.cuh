@@ -33,6 +33,15 @@
 
 namespace sk {
 
+// One lane's row of the FD forward tape: its R node differences v (before the column's update),
+// k0 = k(gR, J), k1 = k(gR, J+1), the sub-cell m and the exponent, padded to 16 bytes.  From it the
+// adjoint rebuilds the lane's R sub-cells of column J (fd_tape_row elements per lane and step,
+// laid out [vector][lane] like the polynomial tapes).
+template <typename T>
+__host__ __device__ constexpr int fd_tape_row(int R) {
+    return ((R + 4) * static_cast<int>(sizeof(T)) + 15) / 16 * 16 / static_cast<int>(sizeof(T));
+}
+
 template <typename T>
 __device__ __forceinline__ T fd_pow2(int e) {
     if constexpr (std::is_same<T, float>::value) return pow2f(e);
@@ -41,7 +50,7 @@ __device__ __forceinline__ T fd_pow2(int e) {
 
 // Sweep of one pair by one warp (CW = 1) or by warp w of a cooperative block of CW warps
 // (strips w, w + CW, ...; hand-off ordering as in sweep_poly).
-template <typename T, int ORDER, int R, int CW>
+template <typename T, int ORDER, int R, int CW, bool TAPE = false>
 __device__ __forceinline__ void sweep_fd(const Launch& L, int64_t item, const PairDesc& P, int w, char* own_buf,
                                          const char* prev_buf, int* prog, int64_t buf_cols) {
     constexpr bool kRescale = std::is_same<T, float>::value;
@@ -122,6 +131,25 @@ __device__ __forceinline__ void sweep_fd(const Launch& L, int64_t item, const Pa
             }
             const T m = row_dot<T>(xbase + static_cast<int64_t>((g * R) >> lam) * dpad,
                                    ybase + static_cast<int64_t>(jj >> lam) * dpad, L.nvec) * sub;
+            if constexpr (TAPE) {  // the column's inputs for the adjoint (fd_tape_row)
+                using V = typename Vec<T>::type;
+                constexpr int W = Vec<T>::W;
+                constexpr int TR = fd_tape_row<T>(R);
+                V* dst = reinterpret_cast<V*>(static_cast<char*>(L.tape) + item * L.tape_stride +
+                                              static_cast<int64_t>(step) * (32 * TR * static_cast<int>(sizeof(T))));
+#pragma unroll
+                for (int vv = 0; vv < TR / W; ++vv) {
+                    V t;
+                    T* tp = reinterpret_cast<T*>(&t);
+#pragma unroll
+                    for (int q2 = 0; q2 < W; ++q2) {
+                        const int q = vv * W + q2;
+                        tp[q2] = q < R ? v[q < R ? q : 0] : (q == R ? kb_prev : (q == R + 1 ? kb : (q == R + 2 ? m : T(0))));
+                        if (q == R + 3) tp[q2] = exponent_as<T>(kRescale ? ea : 0);
+                    }
+                    __stcs(dst + vv * 32 + lane, t);
+                }
+            }
             T a1 = m * T(0.5);                           // alpha - 1
             if constexpr (ORDER == 3) a1 = a1 / (T(1) - m * T(0.25));
             T m2 = T(0);                                 // (1 - beta) = alpha - 1 - m/2 (ORDER 2)
@@ -145,6 +173,12 @@ __device__ __forceinline__ void sweep_fd(const Launch& L, int64_t item, const Pa
                 if (kRescale) res = ldexp(res, ea);
                 if (!isfinite(res)) record_error(SK_ERR_NONFINITE);
                 write_result(L, item, P, res);
+                if (TAPE && L.tape_ek != nullptr) {  // exponent of k_hat for the adjoint's scaling
+                    int e2 = 0;
+                    const double t0 = static_cast<double>(top);
+                    if (t0 != 0.0) frexp(t0, &e2);
+                    L.tape_ek[item] = (kRescale ? ea : 0) + e2;
+                }
             }
             if (kRescale) {
                 const float mag = fmaxf(fabsf(static_cast<float>(kb_prev)), fabsf(static_cast<float>(top)));
@@ -178,8 +212,10 @@ __device__ __forceinline__ void sweep_fd(const Launch& L, int64_t item, const Pa
 // 128 x 128 pairs of 257-point paths ran 2.1x faster than at the 180-200 registers the
 // unconstrained build took (2 blocks per SM).  The pipelined blocks keep their budget: capped at
 // two blocks per SM they ran slower (64 oscillatory pairs at lambda = 4: 30.1 against 22.1 ms).
-template <typename T, int ORDER, int R, int CW>
-__global__ void __launch_bounds__((CW > 1 ? CW : kFwdWarps) * 32, (CW > 1 ? 1 : 8)) fwd_fd_kernel(Launch L, int64_t buf_cols) {
+// TAPE (CW = 1): also record the forward tape of the FD adjoint (fd_tape_row, L.tape must be set).
+template <typename T, int ORDER, int R, int CW, bool TAPE = false>
+__global__ void __launch_bounds__((CW > 1 ? CW : kFwdWarps) * 32, (CW > 1 ? 1 : (TAPE ? 4 : 8)))
+    fwd_fd_kernel(Launch L, int64_t buf_cols) {
     const int wib = threadIdx.x >> 5;
     const int nw = blockDim.x >> 5;
     char* block_base = static_cast<char*>(L.scratch) + static_cast<int64_t>(blockIdx.x) * nw * L.scratch_stride;
@@ -211,7 +247,7 @@ __global__ void __launch_bounds__((CW > 1 ? CW : kFwdWarps) * 32, (CW > 1 ? 1 : 
         if (item < 0) break;
         const PairDesc P = decode_pair(L, item);
         if (trivial_pair(L, item, P)) continue;
-        sweep_fd<T, ORDER, R, 1>(L, item, P, 0, own, own, nullptr, buf_cols);
+        sweep_fd<T, ORDER, R, 1, TAPE>(L, item, P, 0, own, own, nullptr, buf_cols);
     }
 }
 
