@@ -170,6 +170,14 @@ struct Plan {
     bool mtile;          // tiled M (wide increments, polynomial schemes)
     int64_t mtile_cols;  // columns of one warp's M strip buffer
     int64_t mtile_off;   // byte offset of that buffer in a warp slot
+    // tensor-core M (FP32 approximation scheme, 8 < d <= 32, one warp per pair): the forward is
+    // swept in chunks of mx_chunk items, each preceded by the M kernel writing the chunk's M
+    bool mx;
+    int kp;              // padded coordinates of the M operand tiles (16 or 32)
+    int xt_nblk, yt_nblk;// 128-row blocks per path of the operand tiles
+    int64_t mx_stride;   // bytes of M per item
+    int64_t mx_chunk;    // items per chunk (npairs when MX is off)
+    size_t off_xt, off_yt, off_mx;
     int smem_x;          // dynamic shared memory of the tiled-M x rows per block
     int64_t slot_bytes;  // scratch per warp slot
     int64_t buf_cols;    // hand-off columns per warp slot
@@ -180,6 +188,9 @@ struct Plan {
 size_t align256(size_t v) { return (v + 255) / 256 * 256; }
 
 constexpr int kGridMinBlocks = 8;  // fewest blocks a pair's ring may span in the grid strip pipeline
+// Bytes of precomputed M a forward holds at once (the chunk of items whose M the tensor cores
+// wrote before the chunk's sweep); a chunk is a whole number of the sweep's resident warps.
+constexpr size_t kMxBudget = size_t(8) << 30;
 
 int check_paths(const sk_paths* P, const char* name, int d) {
     if (!P) return fail(SK_ERR_INVALID_ARG, "%s is NULL", name);
@@ -347,6 +358,48 @@ int plan_forward(const sk_paths* X, const sk_paths* Y, int32_t d, int32_t dtype,
             }
         }
     }
+    // Tensor-core M: in place of the tiled-M build, the FP32 approximation scheme's one-warp-per-pair
+    // sweep reads each cell's M from a buffer that a tcgen05 GEMM fills per chunk of items
+    // (sk_m_tc.cu).  Off with SK_FLAG_NO_TC, for the interpolation scheme, for the strip pipeline,
+    // and when even one wave of resident warps would need more than twice kMxBudget.
+    p.mx = false;
+    p.kp = p.dpad <= 16 ? 16 : 32;
+    p.xt_nblk = static_cast<int>(((X->max_len << lam) + 127) / 128);
+    p.yt_nblk = static_cast<int>(((Y->max_len << lam) + 127) / 128);
+    p.mx_stride = 0;
+    p.mx_chunk = npairs;
+    if (p.mtile && !p.coop && o->scheme == SK_POLY_APPROX && p.dpad <= 32 && !(o->flags & SK_FLAG_NO_TC)) {
+        const void* km = fwd_poly_kernel_ptr(p.T, false, o->degree, false, false, tape, true);
+        if (km) {
+            const int64_t pts = (o->flags & SK_FLAG_INCREMENTS) ? 0 : 1;
+            const int64_t rmax = std::max<int64_t>(X->max_len - pts, 1) << lam;
+            const int64_t cmax = std::max<int64_t>(Y->max_len - pts, 1) << lam;
+            const int64_t nsteps = ((rmax + 31) / 32 - 1) * std::max<int64_t>(cmax, 32) + 31 + cmax;
+            // groups of four warp steps, 32 lanes x float4 each
+            const int64_t stride = static_cast<int64_t>(align256(static_cast<size_t>((nsteps + 3) / 4) * 32 * 16));
+            int mper = 0;
+            p.mtile = false;  // no x-row staging for this kernel
+            if ((rc = occupancy(km, p.threads, &mper)) != SK_OK) return rc;
+            if (mper < 1) mper = 1;
+            const int64_t resident = static_cast<int64_t>(sms) * mper * (p.threads / 32);
+            int64_t chunk = npairs;
+            if (static_cast<size_t>(npairs) * stride > kMxBudget) {
+                chunk = static_cast<int64_t>(kMxBudget / static_cast<size_t>(stride));
+                if (chunk >= resident) chunk -= chunk % resident;
+                else if (static_cast<size_t>(resident) * stride <= 2 * kMxBudget) chunk = resident;
+                else chunk = 0;
+            }
+            if (chunk > 0) {
+                p.mx = true;
+                p.kern = km;
+                per_sm = mper;
+                p.mx_stride = stride;
+                p.mx_chunk = std::max<int64_t>(std::min(chunk, npairs), 1);
+            } else {
+                p.mtile = true;
+            }
+        }
+    }
     const int wpb = p.threads / 32;
     int64_t want = p.coop ? (p.grid_bpp > 0 ? npairs * p.grid_bpp : npairs) : (npairs + wpb - 1) / wpb;
     int64_t cap = static_cast<int64_t>(sms) * per_sm;
@@ -373,6 +426,15 @@ int plan_forward(const sk_paths* X, const sk_paths* Y, int32_t d, int32_t dtype,
     off += static_cast<size_t>(p.blocks) * wpb * static_cast<size_t>(p.slot_bytes);
     p.off_gprog = off;
     if (p.grid_bpp > 0) off += align256(static_cast<size_t>(p.blocks) * wpb * sizeof(int));
+    p.off_xt = p.off_yt = p.off_mx = off;
+    if (p.mx) {
+        p.off_xt = off;
+        off += align256(m_operand_bytes(p.kp, X->count, p.xt_nblk));
+        p.off_yt = p.same_xy ? p.off_xt : off;
+        if (!p.same_xy) off += align256(m_operand_bytes(p.kp, Y->count, p.yt_nblk));
+        p.off_mx = off;
+        off += static_cast<size_t>(p.mx_chunk) * static_cast<size_t>(p.mx_stride);
+    }
     p.total = off + 256;
     return SK_OK;
 }
@@ -506,43 +568,82 @@ int run_forward(const sk_paths* X, const sk_paths* Y, int32_t d, int32_t dtype, 
     L.mtile_cols = static_cast<int32_t>(p.mtile_cols);
     L.mtile_off = p.mtile_off;
     L.wait_limit = g_wait_limit.load(std::memory_order_relaxed);
-    SK_CUDA(cudaMemsetAsync(base + p.off_queue, 0, 256 + align256(2 * 65 * sizeof(unsigned int)), st));
-    if (!(o->flags & SK_FLAG_NO_SORT) && npairs > 1) {
-        unsigned int* hist = reinterpret_cast<unsigned int*>(base + p.off_hist);
-        int32_t* order = reinterpret_cast<int32_t*>(base + p.off_order);
-        int sb = static_cast<int>((npairs + 255) / 256);
-        if (sb > 4096) sb = 4096;
-        sched_hist_kernel<<<sb, 256, 0, st>>>(L, hist);
-        sched_scan_kernel<<<1, 32, 0, st>>>(hist, hist + 65);
-        sched_scatter_kernel<<<sb, 256, 0, st>>>(L, hist + 65, order);
-        SK_CUDA(cudaGetLastError());
-        L.order = order;
+    L.mx = nullptr;
+    L.mx_stride = 0;
+    int sms = 0;
+    if (p.mx) {
+        int dev = 0;
+        SK_CUDA(cudaGetDevice(&dev));
+        SK_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        SK_CUDA(launch_m_operands(p.kp, L.X, inc_mode, L.lam, p.dpad, p.xt_nblk, base + p.off_xt, st));
+        if (!p.same_xy) SK_CUDA(launch_m_operands(p.kp, L.Y, inc_mode, L.lam, p.dpad, p.yt_nblk, base + p.off_yt, st));
+        L.mx = reinterpret_cast<const float*>(base + p.off_mx);
+        L.mx_stride = p.mx_stride;
     }
     int64_t buf_cols = p.buf_cols;
-    void* args[] = {&L, &buf_cols};
     const int smem = p.smem_x;  // tiled-M x rows
     if (smem > 48 * 1024) SK_CUDA(cudaFuncSetAttribute(p.kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     const bool timed = (o->flags & SK_FLAG_TIME_KERNEL) != 0;
     if (timed) {
         if (!t_ev0) SK_CUDA(cudaEventCreate(&t_ev0));
         if (!t_ev1) SK_CUDA(cudaEventCreate(&t_ev1));
-        SK_CUDA(cudaEventRecord(t_ev0, st));
     }
-    if (p.grid_bpp > 0) {
-        // the blocks of a pair wait on one another: launch them co-resident
-        cudaLaunchConfig_t cfg = {};
-        cfg.gridDim = dim3(p.blocks);
-        cfg.blockDim = dim3(p.threads);
-        cfg.dynamicSmemBytes = static_cast<size_t>(smem);
-        cfg.stream = st;
-        cudaLaunchAttribute attr;
-        attr.id = cudaLaunchAttributeCooperative;
-        attr.val.cooperative = 1;
-        cfg.attrs = &attr;
-        cfg.numAttrs = 1;
-        SK_CUDA(cudaLaunchKernelExC(&cfg, p.kern, args));
-    } else {
-        SK_CUDA(cudaLaunchKernel(p.kern, dim3(p.blocks), dim3(p.threads), args, smem, st));
+    // Items in chunks of p.mx_chunk (one chunk unless M is precomputed): each chunk is a launch of
+    // its own over items c0 .. c0 + n - 1 (pair lists, outputs and tape offset by c0; a Gram's
+    // items by item_base), with its own queue and order.
+    const int wpb = p.threads / 32;
+    for (int64_t c0 = 0; c0 < npairs; c0 += p.mx_chunk) {
+        const int64_t n = std::min(p.mx_chunk, npairs - c0);
+        Launch C = L;
+        C.npairs = n;
+        if (c0 > 0) {
+            if (mode == kPairsList) {
+                C.pair_a = pa + c0;
+                C.pair_b = pb + c0;
+                C.out = out + c0;
+            } else {
+                C.item_base = item_base + c0;
+            }
+            if (tape) {
+                C.tape = static_cast<char*>(L.tape) + c0 * L.tape_stride;
+                C.tape_ek = L.tape_ek + c0;
+            }
+        }
+        SK_CUDA(cudaMemsetAsync(base + p.off_queue, 0, 256 + align256(2 * 65 * sizeof(unsigned int)), st));
+        if (!(o->flags & SK_FLAG_NO_SORT) && n > 1) {
+            unsigned int* hist = reinterpret_cast<unsigned int*>(base + p.off_hist);
+            int32_t* order = reinterpret_cast<int32_t*>(base + p.off_order);
+            int sb = static_cast<int>((n + 255) / 256);
+            if (sb > 4096) sb = 4096;
+            sched_hist_kernel<<<sb, 256, 0, st>>>(C, hist);
+            sched_scan_kernel<<<1, 32, 0, st>>>(hist, hist + 65);
+            sched_scatter_kernel<<<sb, 256, 0, st>>>(C, hist + 65, order);
+            SK_CUDA(cudaGetLastError());
+            C.order = order;
+        }
+        if (timed && c0 == 0) SK_CUDA(cudaEventRecord(t_ev0, st));
+        if (p.mx)
+            SK_CUDA(launch_m_tc(p.kp, C, base + p.off_xt, base + p.off_yt, p.xt_nblk, p.yt_nblk,
+                                reinterpret_cast<float*>(base + p.off_mx), p.mx_stride, sms, st));
+        void* args[] = {&C, &buf_cols};
+        if (p.grid_bpp > 0) {
+            // the blocks of a pair wait on one another: launch them co-resident
+            cudaLaunchConfig_t cfg = {};
+            cfg.gridDim = dim3(p.blocks);
+            cfg.blockDim = dim3(p.threads);
+            cfg.dynamicSmemBytes = static_cast<size_t>(smem);
+            cfg.stream = st;
+            cudaLaunchAttribute attr;
+            attr.id = cudaLaunchAttributeCooperative;
+            attr.val.cooperative = 1;
+            cfg.attrs = &attr;
+            cfg.numAttrs = 1;
+            SK_CUDA(cudaLaunchKernelExC(&cfg, p.kern, args));
+        } else {
+            const int64_t want = p.coop ? n : (n + wpb - 1) / wpb;
+            const int blocks = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(want, p.blocks)));
+            SK_CUDA(cudaLaunchKernel(p.kern, dim3(blocks), dim3(p.threads), args, smem, st));
+        }
     }
     if (timed) {
         SK_CUDA(cudaEventRecord(t_ev1, st));

@@ -154,6 +154,12 @@ struct Launch {
     int* gprog;
     // Polls a strip-pipeline hand-off wait makes before it gives up (0 = kSpinLimit).
     uint32_t wait_limit;
+    // Precomputed M (FP32 approximation scheme, one warp per pair): per work item k of the launch,
+    // at byte offset k * mx_stride, the cells' M_ij / 4^lambda in the warp's schedule, in groups of
+    // four warp steps: lane r's M of steps 4G .. 4G + 3 is the float4 at index 32 G + r.  NULL when
+    // the cells form M themselves.
+    const float* mx;
+    int64_t mx_stride;
 };
 
 // Width, in elements of T, of one lane's tape row.

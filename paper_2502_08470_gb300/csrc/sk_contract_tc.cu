@@ -69,20 +69,6 @@ __global__ void tc_operand_kernel(PathSet S, int inc_mode, int lam, int dpad, in
     }
 }
 
-// Non-swizzled shared-memory matrix descriptor (layout 0): start address, the byte offset between
-// core matrices along K (lbo) and along M / N (sbo), version 1.
-__device__ __forceinline__ uint64_t desc_cm(uint32_t addr, uint32_t lbo, uint32_t sbo) {
-    uint64_t d = static_cast<uint64_t>((addr >> 4) & 0x3FFFu);
-    d |= static_cast<uint64_t>((lbo >> 4) & 0x3FFFu) << 16;
-    d |= static_cast<uint64_t>((sbo >> 4) & 0x3FFFu) << 32;
-    d |= static_cast<uint64_t>(1) << 46;
-    return d;
-}
-
-__device__ __forceinline__ void mbar_arrive_one(uint64_t* bar) {
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
-}
-
 struct TcItem {
     PairDesc P;
     int rows, cols, nrb, ncb;

@@ -15,7 +15,11 @@ namespace sk {
 // tape: the one-warp-per-pair kernel that records the forward tape (for the approximation scheme
 // a separate instantiation records the derivatives of each cell's outputs with respect to M; the
 // interpolation kernels record their inputs whenever the launch carries a tape).
-const void* fwd_poly_kernel_ptr(int T, bool interp, int N, bool coop, bool mt, bool tape = false);
+// mx: the FP32 approximation-scheme variant whose cells read M from the buffer the tensor-core M
+// kernel writes (one warp per pair; with tape, recording the tape of output derivatives).
+const void* fwd_poly_kernel_ptr(int T, bool interp, int N, bool coop, bool mt, bool tape = false, bool mx = false);
+const void* fwd_approx_mx_ptr_f32(int N);
+const void* fwd_approx_tape_mx_ptr_f32(int N);
 const void* fwd_approx_tape_ptr_f32(int N);
 const void* fwd_approx_tape_ptr_f32_mt(int N);
 const void* fwd_approx_tape_ptr_f64(int N);
@@ -105,6 +109,17 @@ size_t tc_operand_bytes(int N, int64_t paths, int nblk);
 cudaError_t launch_tc_operands(int N, const PathSet& S, int inc_mode, int lam, int dpad, int nblk, void* out,
                                cudaStream_t st);
 cudaError_t launch_tc_contraction(int N, const BwdParams& B, int nrb_max, int sms, cudaStream_t st);
+
+struct Launch;
+// Tensor-core M of the forward (FP32 approximation scheme, 8 < d <= 32; KP = 16 or 32 padded
+// coordinates): operand tiles of a path set (nblk 128-row blocks per path, m_operand_bytes bytes),
+// and the M of work items 0 .. L.npairs - 1 of a launch into mx (mx_stride bytes per item, the
+// layout of Launch::mx) on `sms` CTAs.
+size_t m_operand_bytes(int KP, int64_t paths, int nblk);
+cudaError_t launch_m_operands(int KP, const PathSet& S, int inc_mode, int lam, int dpad, int nblk, void* out,
+                              cudaStream_t st);
+cudaError_t launch_m_tc(int KP, const Launch& L, const void* xt, const void* yt, int xt_nblk, int yt_nblk, float* mx,
+                        int64_t mx_stride, int sms, cudaStream_t st);
 }  // namespace sk
 
 namespace sk {

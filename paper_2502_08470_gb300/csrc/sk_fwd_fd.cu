@@ -48,7 +48,11 @@ const void* fwd_interp_coop_mt_ptr_f32(int N) {
     return nullptr;
 }
 
-const void* fwd_poly_kernel_ptr(int T, bool interp, int N, bool coop, bool mt, bool tape) {
+const void* fwd_poly_kernel_ptr(int T, bool interp, int N, bool coop, bool mt, bool tape, bool mx) {
+    if (mx) {
+        if (T != 1 || interp || coop) return nullptr;
+        return tape ? fwd_approx_tape_mx_ptr_f32(N) : fwd_approx_mx_ptr_f32(N);
+    }
     if (tape && !interp) {
         if (coop) return nullptr;
         if (T == 1) return mt ? fwd_approx_tape_ptr_f32_mt(N) : fwd_approx_tape_ptr_f32(N);

@@ -312,11 +312,12 @@ constexpr int fwd_poly_coop_min_blocks() {
 // The ring is the CW warps of one block (ring = CW, progress words in shared memory, CTA-scope
 // ordering), or, with GS, blocks x CW warps spread over co-resident blocks (progress words in
 // global memory, GPU-scope ordering, published every kGridPublish columns).
-template <typename T, int N, int NE, bool INTERP, int CW, bool MT, bool GS = false, bool DMT = false>
+template <typename T, int N, int NE, bool INTERP, int CW, bool MT, bool GS = false, bool DMT = false, bool MX = false>
 __device__ __forceinline__ void sweep_poly(const Launch& L, int64_t item, const PairDesc& P, int w, char* own_buf,
                                            const char* prev_buf, int* prog, int64_t buf_cols, T* xstage,
                                            int ring = CW) {
     constexpr bool kRescale = std::is_same<T, float>::value;
+    static_assert(!MX || (CW == 1 && !MT && std::is_same<T, float>::value), "precomputed M: FP32, one warp per pair");
     using V = typename Vec<T>::type;
     constexpr int W = Vec<T>::W;
     constexpr int NB = (N + 1 + W - 1) / W * W;  // hand-off entry width, padded to whole vectors
@@ -367,6 +368,15 @@ __device__ __forceinline__ void sweep_poly(const Launch& L, int64_t item, const 
     const int mcols = MT ? L.mtile_cols : 0;
     T* mbuf = MT ? reinterpret_cast<T*>(own_buf + L.mtile_off) : nullptr;
     int jj0 = 0, sl0 = 0;
+    // precomputed M (MX): this item's groups of four warp steps (lane r's M of steps 4G .. 4G + 3 in
+    // the float4 32 G + r).  Group G + 1 is loaded on entering group G, four to seven steps ahead of
+    // its use: the groups come from HBM, and a step's cell arithmetic alone does not cover the load
+    // latency (measured: the sweep of 256 x 256 / 2 pairs of 513-point paths took 112 ms reading M
+    // at its step and 77 ms reading ahead).
+    const float4* mxi = MX ? reinterpret_cast<const float4*>(reinterpret_cast<const char*>(L.mx) + item * L.mx_stride)
+                           : nullptr;
+    float4 mcur = make_float4(0.f, 0.f, 0.f, 0.f), mnxt = mcur;
+    if constexpr (MX) mnxt = __ldcs(mxi + lane);  // group 0
 
     for (int step = 0; step < nsteps; ++step) {
         if constexpr (MT) {
@@ -432,6 +442,15 @@ __device__ __forceinline__ void sweep_poly(const Launch& L, int64_t item, const 
         const int jc = min(max(jj, 0), cols - 1);
         T M;
         if constexpr (MT) M = active ? mbuf[((sl & 1) * 32 + lane) * static_cast<int64_t>(mcols) + jc] : T(0);
+        else if constexpr (MX) {
+            if ((step & 3) == 0) {  // entering group step / 4: its M was read a group ago
+                mcur = mnxt;
+                const int gn = (step >> 2) + 1;
+                if (4 * gn < nsteps) mnxt = __ldcs(mxi + static_cast<int64_t>(gn) * 32 + lane);
+            }
+            M = active ? mcur.x : T(0);
+            mcur = make_float4(mcur.y, mcur.z, mcur.w, 0.f);
+        }
         else M = row_dot<T>(xrow, ybase + static_cast<int64_t>(jc >> lam) * dpad, L.nvec) * sub;
         if constexpr (CW == 1 && INTERP) {
             if (L.tape != nullptr) {
@@ -574,8 +593,9 @@ __device__ __forceinline__ bool trivial_pair(const Launch& L, int64_t item, cons
 // sweep_poly<..., CW>), and at the first shorter pair (the queue is ordered by cell count, longest
 // first) its warps fall back to one pair each.  DMT (approximation scheme, CW = 1): record the
 // tape of output derivatives with respect to M (L.tape must be set); the interpolation kernels
-// record their tape of cell inputs whenever L.tape is set.
-template <typename T, int N, int NE, bool INTERP, int CW, bool MT, bool DMT = false>
+// record their tape of cell inputs whenever L.tape is set.  MX (FP32 approximation scheme,
+// CW = 1): the cells read M from the buffer L.mx that the tensor-core M kernel wrote.
+template <typename T, int N, int NE, bool INTERP, int CW, bool MT, bool DMT = false, bool MX = false>
 __global__ void __launch_bounds__((CW > 1 ? CW : kFwdWarps) * 32,
                                   (CW > 1 ? fwd_poly_coop_min_blocks<T, N, NE, MT>() : fwd_poly_min_blocks<T, N, NE, MT>()))
     fwd_poly_kernel(Launch L, int64_t buf_cols) {
@@ -631,7 +651,7 @@ __global__ void __launch_bounds__((CW > 1 ? CW : kFwdWarps) * 32,
         if (item < 0) break;
         const PairDesc P = decode_pair(L, item);
         if (trivial_pair(L, item, P)) continue;
-        sweep_poly<T, N, NE, INTERP, 1, MT, false, DMT>(L, item, P, 0, own, own, nullptr, buf_cols, xstage);
+        sweep_poly<T, N, NE, INTERP, 1, MT, false, DMT, MX>(L, item, P, 0, own, own, nullptr, buf_cols, xstage);
     }
 }
 

@@ -40,6 +40,22 @@ __device__ __forceinline__ uint64_t umma_desc_sw128(uint32_t addr) {
     return d;
 }
 
+// Non-swizzled shared-memory matrix descriptor (layout 0) of a tile of 8 x 8 core matrices (each
+// 128 contiguous bytes, row r of a core matrix at 16 r): start address, the byte offset between
+// core matrices adjacent along K (lbo) and along M / N (sbo), version 1.  For a K-major operand a
+// K-slice of 16 elements is two core matrices along K, so slice k starts at addr + 2 k lbo.
+__device__ __forceinline__ uint64_t desc_cm(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+    uint64_t d = static_cast<uint64_t>((addr >> 4) & 0x3FFFu);
+    d |= static_cast<uint64_t>((lbo >> 4) & 0x3FFFu) << 16;
+    d |= static_cast<uint64_t>((sbo >> 4) & 0x3FFFu) << 32;
+    d |= static_cast<uint64_t>(1) << 46;
+    return d;
+}
+
+__device__ __forceinline__ void mbar_arrive_one(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
 // Instruction descriptor of kind::f16 with BF16 A and B (both K-major), FP32 accumulator, dense:
 // D format F32 (bits 4-5 = 1), A format BF16 (bits 7-9 = 1), B format BF16 (bits 10-12 = 1),
 // N >> 3 (bits 17-22), M >> 4 (bits 24-28).

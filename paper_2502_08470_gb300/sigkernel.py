@@ -192,15 +192,19 @@ def _flags(X: Paths, extra=0) -> int:
 
 def sigkernel_pairs(X, Y, pair_a, pair_b, scheme="approx", degree=6, dyadic=0, compute="f64", sort=True,
                     out: torch.Tensor | None = None, strip_pipeline=None, time_kernel: bool = False,
-                    tiled_m: bool = True) -> torch.Tensor:
-    """k_hat(X[pair_a[k]], Y[pair_b[k]]) for every k, as a float64 CUDA tensor."""
+                    tiled_m: bool = True, tensor_cores: bool = True) -> torch.Tensor:
+    """k_hat(X[pair_a[k]], Y[pair_b[k]]) for every k, as a float64 CUDA tensor.
+
+    ``tensor_cores=False`` (SK_FLAG_NO_TC) keeps the FP32 approximation scheme's M on the FMA pipe
+    (tiled, or per cell with ``tiled_m=False``) instead of the tcgen05 M kernel (8 < d <= 32)."""
     X, Y = as_paths(X), as_paths(Y)
     pa = torch.as_tensor(pair_a, dtype=torch.int64, device="cuda").contiguous()
     pb = torch.as_tensor(pair_b, dtype=torch.int64, device="cuda").contiguous()
     n = pa.numel()
     opt = _options(scheme, degree, dyadic, compute,
                    _flags(X, (0 if sort else FLAG_NO_SORT) | _pipe_flags(strip_pipeline)
-                          | (FLAG_TIME_KERNEL if time_kernel else 0) | (0 if tiled_m else FLAG_NO_TILED_M)))
+                          | (FLAG_TIME_KERNEL if time_kernel else 0) | (0 if tiled_m else FLAG_NO_TILED_M)
+                          | (0 if tensor_cores else FLAG_NO_TC)))
     cX, cY = _cpaths(X), _cpaths(Y)
     out = out if out is not None else torch.empty(n, dtype=torch.float64, device="cuda")
     ws = _workspace(OP_PAIRS, cX, cY, X.d, n, opt)
@@ -212,18 +216,21 @@ def sigkernel_pairs(X, Y, pair_a, pair_b, scheme="approx", degree=6, dyadic=0, c
 
 def sigkernel_gram(X, Y=None, scheme="approx", degree=6, dyadic=0, compute="f64", sort=True,
                    workspace: torch.Tensor | None = None, out: torch.Tensor | None = None,
-                   time_kernel: bool = False, strip_pipeline=None, tiled_m: bool = True) -> torch.Tensor:
+                   time_kernel: bool = False, strip_pipeline=None, tiled_m: bool = True,
+                   tensor_cores: bool = True) -> torch.Tensor:
     """G[a, b] = k_hat(X[a], Y[b]); with Y None (or Y is X) the symmetric Gram of X.
 
-    ``time_kernel`` records CUDA events around the wavefront kernel (see ``last_kernel_ms``);
-    ``strip_pipeline`` (None / True / False) chooses how long pairs are swept (see the flags
-    SK_FLAG_STRIP_PIPELINE and SK_FLAG_NO_STRIP_PIPELINE)."""
+    ``time_kernel`` records CUDA events around the wavefront kernel (see ``last_kernel_ms``; with
+    the tcgen05 M kernel, from its first launch to the last sweep); ``strip_pipeline`` (None / True
+    / False) chooses how long pairs are swept (see the flags SK_FLAG_STRIP_PIPELINE and
+    SK_FLAG_NO_STRIP_PIPELINE); ``tensor_cores=False`` (SK_FLAG_NO_TC) keeps the FP32
+    approximation scheme's M on the FMA pipe instead of the tcgen05 M kernel (8 < d <= 32)."""
     sym = Y is None or Y is X
     X = as_paths(X)
     Y = X if sym else as_paths(Y)
     flags = _flags(X, (FLAG_SYMMETRIC if sym else 0) | (0 if sort else FLAG_NO_SORT)
                    | (FLAG_TIME_KERNEL if time_kernel else 0) | _pipe_flags(strip_pipeline)
-                   | (0 if tiled_m else FLAG_NO_TILED_M))
+                   | (0 if tiled_m else FLAG_NO_TILED_M) | (0 if tensor_cores else FLAG_NO_TC))
     opt = _options(scheme, degree, dyadic, compute, flags)
     cX, cY = _cpaths(X), _cpaths(Y)
     G = out if out is not None else torch.empty(X.count, Y.count, dtype=torch.float64, device="cuda")
@@ -326,16 +333,17 @@ def _pair_args(X, pair_a, pair_b, sym):
 
 def sigkernel_forward_tape(X, Y=None, pair_a=None, pair_b=None, scheme="approx", degree=6, dyadic=0, compute="f32",
                            sort=True, time_kernel=False, tape: torch.Tensor | None = None,
-                           workspace: torch.Tensor | None = None, out: torch.Tensor | None = None):
+                           workspace: torch.Tensor | None = None, out: torch.Tensor | None = None,
+                           tensor_cores: bool = True):
     """Forward values (Gram when ``pair_a`` is None) plus the tape the adjoint replays from.
-    Returns (values, tape)."""
+    Returns (values, tape).  ``tensor_cores=False``: M on the FMA pipe (SK_FLAG_NO_TC)."""
     sym = pair_a is None and (Y is None or Y is X)
     X = as_paths(X)
     Y = X if (Y is None or Y is X) else as_paths(Y)
     cX, cY = _cpaths(X), _cpaths(Y)
     pa_ptr, pb_ptr, n, keep = _pair_args(X, pair_a, pair_b, sym)
     flags = _flags(X, (FLAG_SYMMETRIC if sym else 0) | (0 if sort else FLAG_NO_SORT)
-                   | (FLAG_TIME_KERNEL if time_kernel else 0))
+                   | (FLAG_TIME_KERNEL if time_kernel else 0) | (0 if tensor_cores else FLAG_NO_TC))
     opt = _options(scheme, degree, dyadic, compute, flags)
     lib = load_library()
     nb = ctypes.c_size_t(0)

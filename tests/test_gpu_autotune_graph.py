@@ -1,9 +1,10 @@
 """GPU tests of the launch-shape autotuner and of CUDA-graph capture of the forward calls.
 
 Every launch shape runs the same per-cell arithmetic, so a tuned call must return bit for bit
-what the default shape returns.  A call given its workspace allocates and synchronises nothing,
-so it can be captured in a CUDA graph and replayed on new input values written into the same
-buffers.
+what the default shape returns (with M on the FMA pipe: the tensor-core M of the one-warp-per-pair
+shape rounds differently, so these calls pass tensor_cores=False).  A call given its workspace
+allocates and synchronises nothing, so it can be captured in a CUDA graph and replayed on new
+input values written into the same buffers.
 """
 import numpy as np
 import pytest
@@ -32,12 +33,12 @@ def test_autotune_uneven_batch_chooses_the_pipeline_and_keeps_results():
     sk.autotune_clear()
     X, Y = _uneven_batch(192, 40)
     idx = torch.arange(192, dtype=torch.int64, device="cuda")
-    ref = sk.sigkernel_pairs(X, Y, idx, idx, compute="f32", strip_pipeline=False)
+    ref = sk.sigkernel_pairs(X, Y, idx, idx, compute="f32", strip_pipeline=False, tensor_cores=False)
     shape, ms = sk.autotune(X, Y, idx, idx, compute="f32", trials=2)
     assert ms > 0
     # 192 pairs of up to 2047 x 2047 cells cannot fill the GPU one warp per pair
     assert shape["strip_pipeline"] is True
-    tuned = sk.sigkernel_pairs(X, Y, idx, idx, compute="f32")  # takes the remembered shape
+    tuned = sk.sigkernel_pairs(X, Y, idx, idx, compute="f32", tensor_cores=False)  # the remembered shape
     torch.cuda.synchronize()
     assert sk.device_status() == 0
     assert torch.equal(tuned, ref)
@@ -87,20 +88,21 @@ def test_autotuned_uneven_batch_captures_into_a_cuda_graph():
     idx = torch.arange(128, dtype=torch.int64, device="cuda")
     shape, _ = sk.autotune(X, Y, idx, idx, compute="f32", trials=1)
     out = torch.empty(128, dtype=torch.float64, device="cuda")
-    sk.sigkernel_pairs(X, Y, idx, idx, compute="f32", out=out)
+    sk.sigkernel_pairs(X, Y, idx, idx, compute="f32", out=out, tensor_cores=False)
     torch.cuda.synchronize()
     g = torch.cuda.CUDAGraph()
     s = torch.cuda.Stream()
     with torch.cuda.stream(s):
         with torch.cuda.graph(g, stream=s):
-            sk.sigkernel_pairs(X, Y, idx, idx, compute="f32", out=out)
+            sk.sigkernel_pairs(X, Y, idx, idx, compute="f32", out=out, tensor_cores=False)
     torch.cuda.synchronize()
     rng = np.random.default_rng(51)
     X.rows.mul_(torch.tensor(rng.uniform(0.5, 1.5, size=(1, 16)), dtype=X.rows.dtype, device="cuda"))
     out.fill_(float("nan"))
     g.replay()
     torch.cuda.synchronize()
-    ref = sk.sigkernel_pairs(X, Y, idx, idx, compute="f32", strip_pipeline=not shape["strip_pipeline"])
+    ref = sk.sigkernel_pairs(X, Y, idx, idx, compute="f32", strip_pipeline=not shape["strip_pipeline"],
+                             tensor_cores=False)
     torch.cuda.synchronize()
     assert sk.device_status() == 0
     assert torch.equal(out, ref)

@@ -96,10 +96,12 @@ def test_tc_contraction_symmetric_gram_and_pairs():
 def test_mmd2_gradient_with_and_without_tensor_cores():
     A = torch.tensor(W.brownian(24, 129, 32, seed=560), device="cuda")
     B = torch.tensor(W.brownian(20, 129, 32, seed=561, drift=0.5, vol=1.2), device="cuda")
-    m1, _, gA1, gB1 = sk.sigkernel_mmd2(A, B, compute="f32", grads=True)
+    m1, means, gA1, gB1 = sk.sigkernel_mmd2(A, B, compute="f32", grads=True)
     m2, _, gA2, gB2 = sk.sigkernel_mmd2(A, B, compute="f32", grads=True, tensor_cores=False)
     torch.cuda.synchronize()
     assert sk.device_status() == 0
-    assert m1.item() == m2.item()
+    # the forward's M also comes from the tensor cores (about 2^-22 relative per product): the
+    # value agrees to FP32 rounding on the scale of the kernel means
+    assert abs(m1.item() - m2.item()) < 2e-5 * means.abs().sum().item()
     assert _scaled_err(gA1.cpu().numpy(), gA2.cpu().numpy()) < 5e-5
     assert _scaled_err(gB1.cpu().numpy(), gB2.cpu().numpy()) < 5e-5

@@ -2,7 +2,8 @@
 M_ij = <dx_i, dy_j> / 4^lambda for all columns at once, with every operand row loaded once for 32
 cells, instead of each cell reading two increment rows.  The inner products run in the same order
 as the per-cell form, so every result must agree bit for bit with SK_FLAG_NO_TILED_M; the oracle
-pins both on sampled pairs.
+pins both on sampled pairs.  (The approximation scheme computes M on the tensor cores by default
+for 8 < d <= 32; these tests turn that off to compare the two FMA-pipe forms.)
 """
 import numpy as np
 import pytest
@@ -34,7 +35,7 @@ def test_tiled_m_is_bitwise_the_per_cell_m(d, scheme, N, lam, pipeline):
     Ys = _paths(301, [100, 33, 260], d)
     X = sk.Paths.from_list([torch.tensor(x) for x in Xs])
     Y = sk.Paths.from_list([torch.tensor(y) for y in Ys])
-    kw = dict(scheme=scheme, degree=N, dyadic=lam, compute="f32", strip_pipeline=pipeline)
+    kw = dict(scheme=scheme, degree=N, dyadic=lam, compute="f32", strip_pipeline=pipeline, tensor_cores=False)
     G = sk.sigkernel_gram(X, Y, **kw)
     G0 = sk.sigkernel_gram(X, Y, tiled_m=False, **kw)
     torch.cuda.synchronize()
@@ -48,8 +49,8 @@ def test_tiled_m_is_bitwise_the_per_cell_m(d, scheme, N, lam, pipeline):
 def test_tiled_m_with_the_forward_tape():
     X = torch.tensor(W.brownian(3, 70, 24, seed=401), device="cuda")
     Y = torch.tensor(W.brownian(2, 90, 24, seed=402), device="cuda")
-    G, tape = sk.sigkernel_forward_tape(X, Y, degree=6, compute="f32")
-    G0 = sk.sigkernel_gram(X, Y, degree=6, compute="f32", tiled_m=False)
+    G, tape = sk.sigkernel_forward_tape(X, Y, degree=6, compute="f32", tensor_cores=False)
+    G0 = sk.sigkernel_gram(X, Y, degree=6, compute="f32", tiled_m=False, tensor_cores=False)
     torch.cuda.synchronize()
     assert sk.device_status() == 0
     assert torch.equal(G, G0)
