@@ -134,6 +134,10 @@ def parse():
                     help="paths per side (a smaller Gram of the same paths, for profiling runs)")
     ap.add_argument("--len", type=int, default=L,
                     help="points per path (shorter paths, for profiling runs that must hold only a few GB)")
+    ap.add_argument("--mmd-n", type=int, default=256,
+                    help="paths per sample of the mmd part (fewer, for profiling runs that must hold only a few GB)")
+    ap.add_argument("--mmd-forward-only", action="store_true",
+                    help="mmd part: the forward alone (profiling runs that must not hold a gradient tape)")
     ap.add_argument("--parts", default=",".join(PARTS),
                     help="comma list: f32 (headline fwd+bwd step), api (sigkernel_backward, autograd, checkpointing "
                          "adjoint), fwd (forward only), f64 (FP64 forward and fwd+bwd), e2e, single (one pair of "
@@ -793,32 +797,45 @@ def main():
         del PX, PY, graph
 
     if "mmd" in args.parts:  # MMD^2 fwd+bwd: 256 + 256 paths, 513 points, d=32, FP32
-        Am_np = W.brownian(256, 513, 32, seed=7 + 1000 * rank)
-        Bm_np = W.brownian(256, 513, 32, seed=8 + 1000 * rank, drift=0.5, vol=1.2)
+        nm = args.mmd_n
+        Am_np = W.brownian(nm, 513, 32, seed=7 + 1000 * rank)
+        Bm_np = W.brownian(nm, 513, 32, seed=8 + 1000 * rank, drift=0.5, vol=1.2)
         Am = torch.tensor(Am_np, device=dev)
         Bm = torch.tensor(Bm_np, device=dev)
-        cells_m = (256 * 257 // 2 * 2 + 256 * 256) * 512 * 512
+        cells_m = (nm * (nm + 1) // 2 * 2 + nm * nm) * 512 * 512
         t_f = timed_steps(lambda: sk.sigkernel_mmd2(Am, Bm, degree=6, compute="f32"), 2, 1)
+    if "mmd" in args.parts and args.mmd_forward_only:
+        line["mmd2_forward_only"] = {"workload": f"{nm} + {nm} paths, 513 points, d=32, approx N=6, FP32",
+                                     "cells": cells_m, "forward_ms": t_f}
+        del Am, Bm
+    elif "mmd" in args.parts:
         t_fb = timed_steps(lambda: sk.sigkernel_mmd2(Am, Bm, degree=6, compute="f32", grads=True), 2, 1)
-        labels = sk.split_labels(1000, 256, 256, seed=9 + rank)
+        # the same with every contraction on the FMA pipe (tiled M forward, FMA dk/dM contraction)
+        t_f0 = timed_steps(lambda: sk.sigkernel_mmd2(Am, Bm, degree=6, compute="f32", tensor_cores=False), 1, 1)
+        t_fb0 = timed_steps(lambda: sk.sigkernel_mmd2(Am, Bm, degree=6, compute="f32", grads=True,
+                                                      tensor_cores=False), 1, 1)
+        labels = sk.split_labels(1000, nm, nm, seed=9 + rank)
         ws_t = sk.mmd2_test_workspace(Am, Bm, 1000, compute="f32")
         out_t = torch.empty(1002, dtype=torch.float64, device=dev)
         t_test = timed_steps(lambda: sk.sigkernel_mmd2_test(Am, Bm, labels=labels, compute="f32", workspace=ws_t,
                                                             out=out_t), 2, 1)
         # Gram entries of the three blocks, with the options sigkernel_mmd2 uses, for the oracle check
-        sa_, sb_ = rng.integers(0, 256, 16), rng.integers(0, 256, 16)
+        sa_, sb_ = rng.integers(0, nm, 16), rng.integers(0, nm, 16)
         for name, P1, P2, n1, n2 in (("AB", Am, Bm, Am_np, Bm_np), ("AA", Am, Am, Am_np, Am_np),
                                      ("BB", Bm, Bm, Bm_np, Bm_np)):
             gm = sk.sigkernel_pairs(P1, P2, torch.tensor(sa_, device=dev), torch.tensor(sb_, device=dev),
                                     degree=6, compute="f32").cpu().numpy()
             samples[f"mmd_K{name}"] = dict(xs=list(n1), ys=list(n2), pa=sa_, pb=sb_, scheme="approx", N=6, lam=0,
                                            gpu=gm)
-        line["mmd2"] = {"workload": "256 + 256 paths, 513 points, d=32 (Brownian vs drift 0.5, vol 1.2), approx N=6, "
-                                    "FP32, symmetric K_AA/K_BB + K_AB, tiled M; gradients from forward tapes in "
-                                    "chunks of pairs (tape <= 48 GiB per chunk)",
+        line["mmd2"] = {"workload": f"{nm} + {nm} paths, 513 points, d=32 (Brownian vs drift 0.5, vol 1.2), approx "
+                                    "N=6, FP32, symmetric K_AA/K_BB + K_AB; M_ij from a tcgen05 GEMM per chunk of "
+                                    "pairs (three BF16 parts, FP32 accumulation); gradients from forward tapes in "
+                                    "chunks of pairs (tape <= 48 GiB per chunk), dk/dM contracted on the tensor cores",
                         "cells": cells_m, "forward_ms": t_f, "fwd_bwd_ms": t_fb,
                         "forward_cell_updates_per_s": cells_m / (t_f / 1e3),
                         "fwd_bwd_cell_updates_per_s": cells_m / (t_fb / 1e3),
+                        "fma_pipe_only": {"forward_ms": t_f0, "fwd_bwd_ms": t_fb0,
+                                          "note": "SK_FLAG_NO_TC: tiled M on the FMA pipe, FMA dk/dM contraction"},
                         "permutation_test_1000_ms": t_test,
                         "permutation_test_p_value": out_t[1].item(),
                         "oracle_check": "16 sampled entries of each Gram block through sigkernel_pairs"}
