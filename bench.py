@@ -118,9 +118,12 @@ def load_hbm_peak():
 
 
 # DRAM traffic (ncu dram__bytes_read.sum + dram__bytes_write.sum) of one launch, as a multiple of
-# that launch's algorithmic bytes, from captures of the current kernels (see profiles/); None when
-# no capture of the current kernel exists.
-NCU_TRAFFIC_RATIO = {"bwd_tape_kernel<float,6,false>": None, "fwd_poly_kernel<float,6,6,false,1,false,true>": None}
+# that launch's algorithmic bytes, from captures of the current kernels on 48 x 48 pairs of
+# 129-point paths (profiles/fwd_poly_kernel_tape_gram48x129.md, bwd_tape_kernel_gram48x129.md):
+# both kernels' traffic is per warp step, so it scales with the steps of the bench's Gram.  None
+# when no capture of the current kernel exists.
+NCU_TRAFFIC_RATIO = {"bwd_tape_kernel<float,6,false>": 2.455 / 2.402,
+                     "fwd_poly_kernel<float,6,6,false,1,false,true>": 2.206 / 2.242}
 
 
 def parse():
@@ -508,7 +511,9 @@ def main():
                      "peak_source": "measured in this run: " + ("sigkernel_fma_peak FP32" if dominant["unit"] == "TFLOP/s"
                                                                 else hbm_src),
                      "alu_frac": dominant["alu_frac"], "hbm_frac": dominant["hbm_frac"],
-                     "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum, per launch" if
+                     "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch on 48 x 48 "
+                                       "pairs of 129-point paths, as a multiple of its algorithmic bytes, times this "
+                                       "launch's algorithmic bytes" if
                      dominant["traffic"] is not None else "no ncu capture of the current kernel"})
     line.update({
         "metric": METRIC,

@@ -18,8 +18,8 @@
 // one coalesced 512-byte load gives the warp four steps of M.
 //
 // One CTA per SM over a contiguous range of pairs, warp-specialised as the tensor-core contraction
-// (sk_contract_tc.cu): warp 0 bulk-copies each tile's two operand tiles into a three-stage ring,
-// warp 1 allocates the tensor memory (three 128-column accumulators) and issues the MMAs, warps 2..9
+// (sk_contract_tc.cu): warp 0 bulk-copies each tile's two operand tiles into a two-stage ring,
+// warp 1 allocates the tensor memory (two 128-column accumulators) and issues the MMAs, warps 2..9
 // move each accumulator through shared memory to the M buffer (two warps per 32-row strip of the
 // tile, 64 columns each), one float4 per lane and store.  Every mbarrier wait is bounded.
 #include <cuda_runtime.h>
@@ -34,8 +34,9 @@ namespace sk {
 
 constexpr int kMtEpiWarps = 8;
 constexpr int kMtThreads = 64 + 32 * kMtEpiWarps;
-constexpr int kMtStage = 32 * 64 * 4;  // staging bytes per epilogue warp
-constexpr int kMtStages = 3;
+constexpr int kMtRow = 100;                 // staging floats per lane (64 + 31 + 3 steps, 16-byte rows)
+constexpr int kMtStage = 32 * kMtRow * 4;  // staging bytes per epilogue warp
+constexpr int kMtStages = 2;
 constexpr int kMtParts = 3;  // BF16 parts per FP32 operand
 
 // Byte offset of element (r, k) of one (hi or lo) plane of an operand tile: 128 rows x KP
@@ -46,10 +47,13 @@ __device__ __forceinline__ uint32_t m_operand_offset(int r, int k) {
     return static_cast<uint32_t>(((r >> 3) * (KP / 8) + (k >> 3)) * 128 + (r & 7) * 16 + (k & 7) * 2);
 }
 
+// Operand tiles of a path set: for path p and 128-row block k, the h, m and l parts of the refined
+// rows' increments scaled by 2^-lambda (exact), so that the products are M_ij / 4^lambda.
 template <int KP>
 __global__ void m_operand_kernel(PathSet S, int inc_mode, int lam, int dpad, int nblk, unsigned char* out) {
     constexpr int kPlane = 128 * KP * 2;  // one part of a tile
     const float* __restrict__ inc = static_cast<const float*>(S.inc);
+    const float scale = pow2f(-lam);
     for (int64_t pb = blockIdx.x; pb < S.count * nblk; pb += gridDim.x) {
         const int64_t p = pb / nblk;
         const int k = static_cast<int>(pb - p * nblk);
@@ -61,7 +65,7 @@ __global__ void m_operand_kernel(PathSet S, int inc_mode, int lam, int dpad, int
             const int r = e / KP, c = e - r * KP;
             const int64_t i = static_cast<int64_t>(k) * 128 + r;
             float v = 0.f;
-            if (i < rows && c < dpad) v = inc[(start + (i >> lam)) * dpad + c];
+            if (i < rows && c < dpad) v = inc[(start + (i >> lam)) * dpad + c] * scale;
             const __nv_bfloat16 h = __float2bfloat16_rn(v);
             const float r1 = v - __bfloat162float(h);
             const __nv_bfloat16 m = __float2bfloat16_rn(r1);
@@ -118,7 +122,7 @@ __global__ void __launch_bounds__(kMtThreads, 1) m_tc_kernel(Launch L, MtParams 
         mbar_init(drain, 1);
         fence_mbar_init();
     }
-    if (warp == 1) tmem_alloc(slot, 512);
+    if (warp == 1) tmem_alloc(slot, 256);  // two 128-column accumulators
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
@@ -189,10 +193,12 @@ __global__ void __launch_bounds__(kMtThreads, 1) m_tc_kernel(Launch L, MtParams 
     } else {  // epilogue warps 2..9: tensor-memory lanes 32 (warp % 4) .. (one strip of the tile)
         const int q = warp & 3;
         const int half = (warp - 2) >> 2;  // columns 64 half .. 64 half + 63 of the tile
-        // The warp's 32 x 64 block goes through shared memory: lane r's value of column c at float
-        // r * 64 + ((c + 4 r) mod 64), so that both the row-wise float4 writes from tensor memory
-        // and the reads along antidiagonals (lane r reading column x - r) are free of bank conflicts.
-        float* stg = reinterpret_cast<float*>(sm + kMtStages * kStage + (warp - 2) * kMtStage);
+        // The warp's 32 x 64 block goes through shared memory indexed by warp step: lane r's cell
+        // of column c, in warp step T0 + c + r, at float r * kMtRow + (c + r + (T0 mod 4)).  Lane r's
+        // M of a group of four steps is then one aligned float4, read conflict-free (kMtRow / 4 is
+        // odd), and the scalar writes from tensor memory are conflict-free as well (kMtRow + 1 is
+        // odd modulo 32).
+        float* stg = reinterpret_cast<float*>(sm + kMtStages * kStage + (warp - 2) * kMtStage) + lane * kMtRow;
         uint32_t it = 0;
         for (int64_t item = i0; item < i1; ++item) {
             PairDesc P;
@@ -200,7 +206,6 @@ __global__ void __launch_bounds__(kMtThreads, 1) m_tc_kernel(Launch L, MtParams 
             if (!m_item(L, item, P, rows, cols)) continue;
             const int nrb = (rows + 127) >> 7, ncb = (cols + 127) >> 7;
             const int period = cols > 32 ? cols : 32;
-            const float sub = pow2f(-2 * L.lam);
             float4* mx = reinterpret_cast<float4*>(reinterpret_cast<char*>(M.mx) + item * M.mx_stride);
             bool stuck = false;
             for (int rb = 0; rb < nrb && !stuck; ++rb)
@@ -209,46 +214,43 @@ __global__ void __launch_bounds__(kMtThreads, 1) m_tc_kernel(Launch L, MtParams 
                     const uint32_t u = it / kMtStages;
                     if (!mbar_wait(tfull + s, u & 1u)) { stuck = true; break; }
                     tc_fence_after();
+                    const int sg = rb * 4 + q;                   // the strip's index in the pair
+                    const int jb = cb * 128 + 64 * half;         // the block's first column
+                    const int64_t T0 = static_cast<int64_t>(sg) * period + jb;  // step of cell (32 sg, jb)
+                    const int a = static_cast<int>(T0 & 3);
 #pragma unroll
                     for (int c0 = 0; c0 < 64; c0 += 16) {
                         float v[16];
                         tmem_ld16(taddr + ((32u * q) << 16) + s * 128 + 64 * half + c0, v);
                         tmem_ld_wait();
 #pragma unroll
-                        for (int k = 0; k < 4; ++k)
-                            *reinterpret_cast<float4*>(stg + lane * 64 + ((c0 + 4 * k + 4 * lane) & 63)) =
-                                make_float4(v[4 * k] * sub, v[4 * k + 1] * sub, v[4 * k + 2] * sub, v[4 * k + 3] * sub);
+                        for (int k = 0; k < 16; ++k) stg[c0 + k + lane + a] = v[k];
                     }
                     tc_fence_before();
                     __syncwarp();
                     if (lane == 0) mbar_arrive_one(tempty + s);  // the accumulator is free again
-                    const int sg = rb * 4 + q;                   // the strip's index in the pair
-                    const int jb = cb * 128 + 64 * half;         // the block's first column
-                    const int ncol = min(64, cols - jb);         // its columns in the grid
+                    const int ncol = min(64, cols - jb);         // the block's columns in the grid
                     if ((sg << 5) < rows && ncol > 0) {
+                        const bool rows_full = (sg << 5) + 32 <= rows;
                         const bool row_ok = (sg << 5) + lane < rows;
-                        // cell (32 sg + r, jb + c) sits in warp step t = T0 + c + r
-                        const int64_t T0 = static_cast<int64_t>(sg) * period + jb;
-                        const int64_t g0 = T0 >> 2, g1 = (T0 + ncol + 30) >> 2;
-#pragma unroll 2
-                        for (int64_t G = g0; G <= g1; ++G) {
-                            const int cfirst = static_cast<int>(4 * G - T0) - lane;  // column of step 4G
-                            float w[4];
-                            bool ok[4];
+                        const int ng = (ncol + 30 + a) / 4 + 1;  // groups of steps the block touches
+                        float4* dst = mx + (T0 >> 2) * 32 + lane;
+                        // group g holds cells c = 4 g + k - lane - a; all are in the block when
+                        // 4 g >= 31 + a and 4 g + 3 - a < ncol
+                        const int gin0 = (31 + a + 3) / 4, gin1 = (ncol - 4 + a) / 4;  // interior groups
+#pragma unroll 4
+                        for (int g = 0; g < ng; ++g) {
+                            const float4 w = *reinterpret_cast<const float4*>(stg + 4 * g);
+                            if (rows_full && g >= gin0 && g <= gin1) {
+                                dst[static_cast<int64_t>(g) * 32] = w;
+                            } else if (row_ok) {
+                                float* d1 = reinterpret_cast<float*>(dst + static_cast<int64_t>(g) * 32);
+                                const float wk[4] = {w.x, w.y, w.z, w.w};
 #pragma unroll
-                            for (int k = 0; k < 4; ++k) {
-                                const int c = cfirst + k;
-                                ok[k] = row_ok && c >= 0 && c < ncol;
-                                w[k] = stg[lane * 64 + ((c + 4 * lane) & 63)];
-                            }
-                            float4* dst = mx + G * 32 + lane;
-                            if (ok[0] && ok[1] && ok[2] && ok[3]) {
-                                *dst = make_float4(w[0], w[1], w[2], w[3]);
-                            } else {
-                                float* d1 = reinterpret_cast<float*>(dst);
-#pragma unroll
-                                for (int k = 0; k < 4; ++k)
-                                    if (ok[k]) d1[k] = w[k];
+                                for (int k = 0; k < 4; ++k) {
+                                    const int c = 4 * g + k - lane - a;
+                                    if (c >= 0 && c < ncol) d1[k] = wk[k];
+                                }
                             }
                         }
                     }
@@ -261,7 +263,7 @@ __global__ void __launch_bounds__(kMtThreads, 1) m_tc_kernel(Launch L, MtParams 
     __syncthreads();
     if (warp == 1) {
         tc_fence_after();
-        tmem_dealloc(taddr, 512);
+        tmem_dealloc(taddr, 256);
     }
 }
 
