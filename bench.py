@@ -720,6 +720,13 @@ def main():
             fd[key] = {"ms": ms, "cell_updates_per_s": cells / (ms / 1e3),
                        "sub_cell_updates_per_s": cells * 4 ** lam / (ms / 1e3)}
             sample_gram(f"gram_{key}", Gf, n=16, scheme=scheme, N=2, lam=lam)
+        # gradients of the FD schemes: sigkernel_backward (forward recording per-column tapes in
+        # chunks of pairs, the FD adjoint, the dk/dM contraction)
+        for scheme, lam in (("fd1", 0), ("fd2", 2)):
+            ms = timed_steps(lambda: sk.sigkernel_backward(Wt, Xt, Yt, scheme=scheme, degree=2, dyadic=lam,
+                                                           compute="f32"), 2, 1)
+            fd[f"{scheme}_lam{lam}_f32_fwd_bwd"] = {"ms": ms, "cell_updates_per_s": cells / (ms / 1e3),
+                                                    "sub_cell_updates_per_s": cells * 4 ** lam / (ms / 1e3)}
         line["gram_fd"] = fd
         del Gf
 

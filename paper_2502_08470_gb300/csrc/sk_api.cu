@@ -1,5 +1,6 @@
 // Host side of the C ABI (include/sigkernel.h): argument checks, workspace layout, constant
 // tables, the increment and scheduling kernels, and dispatch to the wavefront kernels.
+#include <nvtx3/nvToolsExt.h>
 #include <algorithm>
 #include <atomic>
 #include <cmath>
@@ -1501,11 +1502,21 @@ void set_last_error(const char* msg) { t_last_error = msg; }
 
 using namespace sk;
 
+// An NVTX range over an entry point, for timelines of profilers that attach to the process (a
+// no-op otherwise).
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
+
 extern "C" {
 
 int sigkernel_autotune(const sk_paths* X, const sk_paths* Y, int32_t d, int32_t dtype, const int64_t* pair_a,
                        const int64_t* pair_b, int64_t npairs, const sk_options* opt, double* out, int32_t trials,
                        sk_options* best, float* best_ms, void* stream) {
+    NvtxRange nvtx_range("sigkernel_autotune");
     t_last_error.clear();
     if (!opt || !X || !Y || !out || !best) return fail(SK_ERR_INVALID_ARG, "NULL argument");
     if (trials < 1 || trials > 1000) return fail(SK_ERR_INVALID_ARG, "trials %d outside [1, 1000]", trials);
@@ -1678,6 +1689,7 @@ int sigkernel_workspace_size(int32_t op, const sk_paths* X, const sk_paths* Y, i
 int sigkernel_pairs(const sk_paths* X, const sk_paths* Y, int32_t d, int32_t dtype, const int64_t* pair_a,
                     const int64_t* pair_b, int64_t npairs, const sk_options* opt, double* out, void* workspace,
                     size_t workspace_bytes, void* stream) {
+    NvtxRange nvtx_range("sigkernel_pairs");
     t_last_error.clear();
     if (npairs < 0) return fail(SK_ERR_INVALID_ARG, "npairs < 0");
     if (npairs > 0 && (!pair_a || !pair_b)) return fail(SK_ERR_INVALID_ARG, "pair index arrays are NULL");
@@ -1687,6 +1699,7 @@ int sigkernel_pairs(const sk_paths* X, const sk_paths* Y, int32_t d, int32_t dty
 
 int sigkernel_gram(const sk_paths* X, const sk_paths* Y, int32_t d, int32_t dtype, const sk_options* opt, double* G,
                    void* workspace, size_t workspace_bytes, void* stream) {
+    NvtxRange nvtx_range("sigkernel_gram");
     t_last_error.clear();
     if (!opt || !X || !Y) return fail(SK_ERR_INVALID_ARG, "NULL argument");
     bool sym = (opt->flags & SK_FLAG_SYMMETRIC) != 0;
@@ -1697,6 +1710,7 @@ int sigkernel_gram(const sk_paths* X, const sk_paths* Y, int32_t d, int32_t dtyp
 int sigkernel_backward(const sk_paths* X, const sk_paths* Y, int32_t d, int32_t dtype, const int64_t* pair_a,
                        const int64_t* pair_b, int64_t npairs, const sk_options* opt, const double* grad_out,
                        double* grad_X, double* grad_Y, void* workspace, size_t workspace_bytes, void* stream) {
+    NvtxRange nvtx_range("sigkernel_backward");
     t_last_error.clear();
     if (!opt || !X || !Y) return fail(SK_ERR_INVALID_ARG, "NULL argument");
     if (pair_a && (!pair_b || npairs < 0)) return fail(SK_ERR_INVALID_ARG, "bad pair list");
@@ -1728,6 +1742,7 @@ int sigkernel_tape_size(const sk_paths* X, const sk_paths* Y, int32_t d, int64_t
 int sigkernel_forward_tape(const sk_paths* X, const sk_paths* Y, int32_t d, int32_t dtype, const int64_t* pair_a,
                            const int64_t* pair_b, int64_t npairs, const sk_options* opt, double* out, void* tape,
                            size_t tape_bytes, void* workspace, size_t workspace_bytes, void* stream) {
+    NvtxRange nvtx_range("sigkernel_forward_tape");
     t_last_error.clear();
     if (!opt || !X || !Y) return fail(SK_ERR_INVALID_ARG, "NULL argument");
     if (!tape) return fail(SK_ERR_INVALID_ARG, "tape is NULL");
@@ -1745,6 +1760,7 @@ int sigkernel_backward_tape(const sk_paths* X, const sk_paths* Y, int32_t d, int
                             const int64_t* pair_b, int64_t npairs, const sk_options* opt, const void* tape,
                             size_t tape_bytes, const double* grad_out, double* grad_X, double* grad_Y, void* workspace,
                             size_t workspace_bytes, void* stream) {
+    NvtxRange nvtx_range("sigkernel_backward_tape");
     t_last_error.clear();
     if (!opt || !X || !Y) return fail(SK_ERR_INVALID_ARG, "NULL argument");
     if (pair_a && (!pair_b || npairs < 0)) return fail(SK_ERR_INVALID_ARG, "bad pair list");
@@ -1754,6 +1770,7 @@ int sigkernel_backward_tape(const sk_paths* X, const sk_paths* Y, int32_t d, int
 
 int sigkernel_mmd2(const sk_paths* A, const sk_paths* B, int32_t d, int32_t dtype, const sk_options* opt, double* out,
                    double* grad_A, double* grad_B, void* workspace, size_t workspace_bytes, void* stream) {
+    NvtxRange nvtx_range("sigkernel_mmd2");
     t_last_error.clear();
     return run_mmd2(A, B, d, dtype, opt, out, grad_A, grad_B, workspace, workspace_bytes, stream);
 }
@@ -1761,6 +1778,7 @@ int sigkernel_mmd2(const sk_paths* A, const sk_paths* B, int32_t d, int32_t dtyp
 int sigkernel_mmd2_test(const sk_paths* A, const sk_paths* B, int32_t d, int32_t dtype, const sk_options* opt,
                         const uint8_t* labels, int64_t nperm, double* out, void* workspace, size_t workspace_bytes,
                         void* stream) {
+    NvtxRange nvtx_range("sigkernel_mmd2_test");
     t_last_error.clear();
     return run_mmd2_test(A, B, d, dtype, opt, labels, nperm, out, workspace, workspace_bytes, stream);
 }

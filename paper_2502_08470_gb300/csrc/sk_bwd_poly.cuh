@@ -196,29 +196,34 @@ __device__ __forceinline__ void cell_adjoint_edges(const T (&e)[N + 1], const T 
     if constexpr (std::is_same<T, float>::value) {
         // FP32: the a- and b-side adjoints run the same products on different data, so they go as
         // packed pairs through the two-wide FP32 instructions.
+        // e_0 = 1: the n = 0 weights and the n = k Toeplitz terms need no product, so every sum
+        // starts from its n = k term.
         float2 w[N + 1];  // (gb_n e_n, ga_n e_n): weights of the Hankel couplings
+        w[0] = make_float2(gb[0], ga[0]);
 #pragma unroll
-        for (int n = 0; n <= N; ++n) w[n] = __fmul2_rn(make_float2(gb[n], ga[n]), dup2(e[n]));
+        for (int n = 1; n <= N; ++n) w[n] = __fmul2_rn(make_float2(gb[n], ga[n]), dup2(e[n]));
 #pragma unroll
         for (int k = 0; k <= N; ++k) {
-            float2 v = make_float2(0.f, 0.f);  // (ra_k, rb_k)
+            float2 v = make_float2(ga[k], gb[k]);  // (ra_k, rb_k), from the n = k Toeplitz term
             if (k >= 1) {
 #pragma unroll
                 for (int n = 0; n <= N; ++n) v = __ffma2_rn(w[n], dup2(Tab<float>::hank(n, k)), v);
             }
 #pragma unroll
-            for (int n = k; n <= N; ++n) v = __ffma2_rn(make_float2(ga[n], gb[n]), dup2(e[n - k]), v);
+            for (int n = k + 1; n <= N; ++n) v = __ffma2_rn(make_float2(ga[n], gb[n]), dup2(e[n - k]), v);
             ra[k] = v.x;
             rb[k] = v.y;
         }
         return;
     }
     T al[N + 1], be[N + 1];
+    al[0] = ga[0];
+    be[0] = gb[0];
 #pragma unroll
-    for (int n = 0; n <= N; ++n) { al[n] = ga[n] * e[n]; be[n] = gb[n] * e[n]; }
+    for (int n = 1; n <= N; ++n) { al[n] = ga[n] * e[n]; be[n] = gb[n] * e[n]; }
 #pragma unroll
     for (int k = 0; k <= N; ++k) {
-        T va = T(0), vb = T(0);
+        T va = ga[k], vb = gb[k];  // the n = k Toeplitz term (e_0 = 1)
         if (k >= 1) {
 #pragma unroll
             for (int n = 0; n <= N; ++n) {
@@ -227,7 +232,7 @@ __device__ __forceinline__ void cell_adjoint_edges(const T (&e)[N + 1], const T 
             }
         }
 #pragma unroll
-        for (int n = k; n <= N; ++n) {
+        for (int n = k + 1; n <= N; ++n) {
             va = fma(ga[n], e[n - k], va);
             vb = fma(gb[n], e[n - k], vb);
         }

@@ -63,30 +63,46 @@ __device__ __forceinline__ void build_exp_series(T M, float tau, T (&e)[NE + 1])
 __device__ __forceinline__ float2 dup2(float v) { return make_float2(v, v); }
 
 // One cell: inputs a (bottom), b (left), outputs the factorial-scaled series of the top (ct)
-// and right (cr) edges, n = 0..NE.
+// and right (cr) edges, n = 0..NE:
+//     ct_n = sum_{k<=n} a_k e_{n-k} + e_n sum_{k>=1} b_k n!/(n+k)!     (cr_n likewise with a, b
+// exchanged; the interpolation scheme's corner term k = 0 is a_0 on both edges).  Since e_0 = 1,
+// the k = 0 term joins the coupling, ct_n = e_n (a_0 + H_n(b)) + sum_{1<=k<=n} a_k e_{n-k}, and the
+// k = n term is a_n itself: every sum starts from a value it already has, so the cell is all
+// fused multiply-adds (28 fewer instructions per cell at N = 6 than starting each sum with a
+// product).
 template <typename T, int N, int NE, bool INTERP>
 __device__ __forceinline__ void cell_series(const T (&a)[N + 1], const T (&b)[N + 1], const T (&e)[NE + 1],
                                             T (&ct)[NE + 1], T (&cr)[NE + 1]) {
 #pragma unroll
     for (int n = 0; n <= NE; ++n) {
-        // coupling through the opposite edge: sum_{k>=1} (.)_k n!/(n+k)!
-        T ha = b[1] * Tab<T>::hank(n, 1);
-        T hb = a[1] * Tab<T>::hank(n, 1);
+        // corner term plus the coupling through the opposite edge: c_0 + sum_{k>=1} (.)_k n!/(n+k)!
+        T ta = a[0], tb = INTERP ? a[0] : b[0];
 #pragma unroll
-        for (int k = 2; k <= N; ++k) {
-            ha = fma(b[k], Tab<T>::hank(n, k), ha);
-            hb = fma(a[k], Tab<T>::hank(n, k), hb);
+        for (int k = 1; k <= N; ++k) {
+            ta = fma(b[k], Tab<T>::hank(n, k), ta);
+            tb = fma(a[k], Tab<T>::hank(n, k), tb);
         }
-        // Toeplitz part sum_{k<=n} (.)_k e_{n-k}, then the coupling term e_n h_n
-        T vt = a[0] * e[n];
-        T vr = (INTERP ? a[0] : b[0]) * e[n];
+        if (n == 0) {
+            ct[0] = ta;
+            cr[0] = tb;
+            continue;
+        }
+        // Toeplitz part without its k = 0 term: sum_{1<=k<=min(n,N)} (.)_k e_{n-k}
+        T vt, vr;
+        if (n <= N) {
+            vt = a[n];
+            vr = b[n];
+        } else {
+            vt = a[N] * e[n - N];
+            vr = b[N] * e[n - N];
+        }
 #pragma unroll
-        for (int k = 1; k <= (n < N ? n : N); ++k) {
+        for (int k = (n <= N ? n : N) - 1; k >= 1; --k) {
             vt = fma(a[k], e[n - k], vt);
             vr = fma(b[k], e[n - k], vr);
         }
-        ct[n] = fma(e[n], ha, vt);
-        cr[n] = fma(e[n], hb, vr);
+        ct[n] = fma(e[n], ta, vt);
+        cr[n] = fma(e[n], tb, vr);
     }
 }
 
@@ -94,35 +110,39 @@ __device__ __forceinline__ void cell_series(const T (&a)[N + 1], const T (&b)[N 
 // with respect to M, which are all the adjoint needs of the cell's inputs.  With e_m = M^m/m!
 // (d e_m / dM = e_{m-1}) and the Toeplitz sums T_n = sum_{k<=n} a_k e_{n-k}:
 //     d a'_n / dM = T_{n-1} + e_{n-1} ha_n,   d b'_n / dM = S_{n-1} + e_{n-1} hb_n   (n = 1..N)
-// where S_n is the Toeplitz sum of b; da[n-1] and db[n-1] receive them.
+// where S_n is the Toeplitz sum of b; da[n-1] and db[n-1] receive them.  As in cell_series the
+// k = 0 term joins the coupling: d a'_{n+1} / dM = e_n (a_0 + ha_{n+1}) + sum_{1<=k<=n} a_k e_{n-k}.
 template <typename T, int N>
 __device__ __forceinline__ void cell_series_dm(const T (&a)[N + 1], const T (&b)[N + 1], const T (&e)[N + 1],
                                                T (&ct)[N + 1], T (&cr)[N + 1], T (&da)[N], T (&db)[N]) {
-    T ha[N + 1], hb[N + 1];
+    T ta[N + 1], tb[N + 1];  // a_0 + ha_n, b_0 + hb_n
 #pragma unroll
     for (int n = 0; n <= N; ++n) {
-        ha[n] = b[1] * Tab<T>::hank(n, 1);
-        hb[n] = a[1] * Tab<T>::hank(n, 1);
+        ta[n] = a[0];
+        tb[n] = b[0];
 #pragma unroll
-        for (int k = 2; k <= N; ++k) {
-            ha[n] = fma(b[k], Tab<T>::hank(n, k), ha[n]);
-            hb[n] = fma(a[k], Tab<T>::hank(n, k), hb[n]);
+        for (int k = 1; k <= N; ++k) {
+            ta[n] = fma(b[k], Tab<T>::hank(n, k), ta[n]);
+            tb[n] = fma(a[k], Tab<T>::hank(n, k), tb[n]);
         }
     }
+    ct[0] = ta[0];
+    cr[0] = tb[0];
+    da[0] = ta[1];
+    db[0] = tb[1];
 #pragma unroll
-    for (int n = 0; n <= N; ++n) {
-        T vt = a[0] * e[n];
-        T vr = b[0] * e[n];
+    for (int n = 1; n <= N; ++n) {
+        T vt = a[n], vr = b[n];
 #pragma unroll
-        for (int k = 1; k <= n; ++k) {
+        for (int k = n - 1; k >= 1; --k) {
             vt = fma(a[k], e[n - k], vt);
             vr = fma(b[k], e[n - k], vr);
         }
-        ct[n] = fma(e[n], ha[n], vt);
-        cr[n] = fma(e[n], hb[n], vr);
+        ct[n] = fma(e[n], ta[n], vt);
+        cr[n] = fma(e[n], tb[n], vr);
         if (n < N) {
-            da[n] = fma(e[n], ha[n + 1], vt);
-            db[n] = fma(e[n], hb[n + 1], vr);
+            da[n] = fma(e[n], ta[n + 1], vt);
+            db[n] = fma(e[n], tb[n + 1], vr);
         }
     }
 }
