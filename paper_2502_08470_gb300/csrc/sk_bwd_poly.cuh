@@ -917,8 +917,10 @@ __global__ void __launch_bounds__(kFwdWarps * 32, (bwd_tape_min_blocks<T, N, INT
         }
         if (!INTERP && lane == last_lane) gea = 0;
 
-        // fill the ring with the last kTapeRing steps (step t lives in slot t % kTapeRing)
+        // fill the ring with the last kTapeRing steps (step t lives in slot t % kTapeRing); the
+        // slots were read by the previous item's steps
         if (lane == 0) {
+            fence_proxy_async_smem();
             for (int k = 0; k < kTapeRing && nsteps - 1 - k >= 0; ++k) {
                 const int t = nsteps - 1 - k;
                 const int sl = t % kTapeRing;
@@ -975,6 +977,7 @@ __global__ void __launch_bounds__(kFwdWarps * 32, (bwd_tape_min_blocks<T, N, INT
             }
             __syncwarp();  // every lane has its row: the slot can be refilled
             if (lane == 0 && step - kTapeRing >= 0) {
+                fence_proxy_async_smem();
                 mbar_arrive_expect_tx(bars + sl, kStepBytes);
                 bulk_load(ring + sl * kStepBytes, tape + static_cast<int64_t>(step - kTapeRing) * kStepBytes,
                           kStepBytes, bars + sl);
@@ -1282,6 +1285,7 @@ __global__ void __launch_bounds__(kContractWarps * 32) bwd_contract_kernel(BwdPa
                     const int t0 = s * period + w0;  // buffer row of the window's first tile
                     const int nr = min(32, rows - (s << 5));  // valid rows of the strip
                     // half h of the window = buffer rows t0 + 32h .. t0 + 32h + 31, in slot h % 3
+                    if (lane == 0) fence_proxy_async_smem();  // the previous strip read these slots
                     for (int h = 0; h < 3 && h <= ntiles; ++h) {
                         if (lane == 0) {
                             mbar_arrive_expect_tx(bars + h, HB);
@@ -1345,6 +1349,7 @@ __global__ void __launch_bounds__(kContractWarps * 32) bwd_contract_kernel(BwdPa
                         __syncwarp();  // slot s0 is read by every lane: refill it with half b + 3
                         if (b + 3 <= ntiles) {
                             if (lane == 0) {
+                                fence_proxy_async_smem();
                                 mbar_arrive_expect_tx(bars + s0, HB);
                                 bulk_load(ring + s0 * 1024, mb + static_cast<int64_t>(t0 + 32 * (b + 3)) * 32 * sizeof(T),
                                           HB, bars + s0);

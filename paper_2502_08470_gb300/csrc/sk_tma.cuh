@@ -52,6 +52,16 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
     return false;
 }
 
+// Orders this thread's shared-memory accesses in the generic proxy (ordinary loads and stores,
+// and those of the threads it synchronised with) before its later async-proxy operations (bulk
+// copies, tensor-core reads), and the other way round.  A ring slot that the warp has read must
+// be fenced so before a bulk copy refills it: without the fence the copy may land before a
+// pending shared-memory load of the slot has read it (seen as corrupted adjoints when another
+// kernel's stores kept the load/store units busy).
+__device__ __forceinline__ void fence_proxy_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
 // global -> shared, `bytes` (multiple of 16, both addresses 16-byte aligned), completing on `bar`.
 __device__ __forceinline__ void bulk_load(void* smem_dst, const void* gsrc, uint32_t bytes, uint64_t* bar) {
     asm volatile(

@@ -97,11 +97,6 @@ __device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
-// Makes this thread's ordinary shared-memory writes visible to the tensor core (async proxy).
-__device__ __forceinline__ void fence_proxy_async_smem() {
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-
 // 16 consecutive accumulator columns of the warp's 32 tensor-memory lanes (lane = thread): warp
 // w % 4 may address lanes 32 (w % 4) .. 32 (w % 4) + 31 only.  Complete with tmem_ld_wait().
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {

@@ -1,0 +1,98 @@
+"""GPU tests of the two-stream chunk pipeline of sigkernel_backward and sigkernel_mmd2: each
+chunk's tape adjoint runs on a second stream beside the next chunk's forward, and the call joins
+that stream back into the caller's stream.  The results must be the caller-stream-ordered ones
+(read right after the call on the caller's stream, no device-wide synchronisation in between),
+and the whole fork/join must capture into a CUDA graph and replay on new inputs.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2502_08470_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+sk = pytest.importorskip("paper_2502_08470_gb300.sigkernel")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda_available():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+def _scaled(a, b):
+    a, b = np.asarray(a), np.asarray(b)
+    return np.max(np.abs(a - b)) / np.max(np.abs(b))
+
+
+@pytest.mark.parametrize("scheme,lam", [("approx", 0), ("fd1", 1)])
+def test_backward_on_a_side_stream_is_ordered_for_the_caller(scheme, lam):
+    X = torch.tensor(W.brownian(6, 80, 3, seed=71), device="cuda")
+    Y = torch.tensor(W.brownian(5, 70, 3, seed=72), device="cuda")
+    g = torch.tensor(np.random.default_rng(73).standard_normal((6, 5)), device="cuda")
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        gx, gy = sk.sigkernel_backward(g, X, Y, scheme=scheme, degree=6, dyadic=lam, compute="f64")
+        # consumed on the caller's stream right away: the call must have joined its second stream
+        tot_x, tot_y = gx.sum(), gy.sum()
+    s.synchronize()
+    assert sk.device_status() == 0
+    Xn, Yn = X.cpu().numpy(), Y.cpu().numpy()
+    ref = np.zeros(Xn.shape)
+    gn = g.cpu().numpy()
+    for a in range(6):
+        for b in range(5):
+            gxa, _ = oracle.grad(Xn[a], Yn[b], scheme, 6 if scheme == "approx" else 2, lam)
+            ref[a] += gn[a, b] * gxa
+    assert _scaled(gx.cpu().numpy(), ref.reshape(-1, 3)) < 1e-9  # gradients come in the rows layout
+    assert abs(tot_x.item() - gx.sum().item()) <= 1e-12 * gx.abs().sum().item()
+    assert abs(tot_y.item() - gy.sum().item()) <= 1e-12 * gy.abs().sum().item()
+
+
+def test_backward_captures_into_a_cuda_graph():
+    X = torch.tensor(W.brownian(8, 65, 4, seed=81), device="cuda")
+    Y = torch.tensor(W.brownian(8, 65, 4, seed=82), device="cuda")
+    g = torch.tensor(np.random.default_rng(83).standard_normal((8, 8)), device="cuda")
+    gx0, _ = sk.sigkernel_backward(g, X, Y, compute="f32")  # eager first: creates the second stream
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        with torch.cuda.graph(graph, stream=s):
+            gx, gy = sk.sigkernel_backward(g, X, Y, compute="f32")
+    torch.cuda.synchronize()
+    for seed in (84, 85):
+        X.copy_(torch.tensor(W.brownian(8, 65, 4, seed=seed), device="cuda"))
+        gx.fill_(float("nan"))
+        graph.replay()
+        torch.cuda.synchronize()
+        ref, _ = sk.sigkernel_backward(g, X, Y, compute="f32")
+        torch.cuda.synchronize()
+        assert sk.device_status() == 0
+        assert _scaled(gx.cpu().numpy(), ref.cpu().numpy()) < 1e-12
+
+
+def test_mmd2_gradient_across_many_chunks_matches_the_backward_of_each_block():
+    # 80 + 80 paths of 513 points (14.7 MB of tape per pair at N = 6): with 32 GiB per tape a chunk
+    # holds 2331 pairs, so K_AA and K_BB run in 2 chunks each and K_AB in 3, and the second
+    # stream's adjoints overlap the next chunks' forwards across the blocks
+    n = 80
+    A = torch.tensor(W.brownian(n, 513, 3, seed=91), device="cuda")
+    B = torch.tensor(W.brownian(n, 513, 3, seed=92, drift=0.5, vol=1.2), device="cuda")
+    m, means, gA, gB = sk.sigkernel_mmd2(A, B, compute="f32", grads=True)
+    torch.cuda.synchronize()
+    assert sk.device_status() == 0
+    w = 1.0 / (n * n)
+    full = lambda v: torch.full((n, n), v, device="cuda", dtype=torch.float64)
+    gaa, _ = sk.sigkernel_backward(full(w), A, None, compute="f32")
+    gbb, _ = sk.sigkernel_backward(full(w), B, None, compute="f32")
+    gab, gba = sk.sigkernel_backward(full(-2 * w), A, B, compute="f32")
+    torch.cuda.synchronize()
+    assert sk.device_status() == 0
+    # The FP32 contraction sums columns with shared-memory atomics, whose order varies from run to
+    # run, and the MMD gradient is a difference of the blocks' gradients (the two samples are
+    # alike), so the error is measured against the size of the parts, not of their sum.
+    for g, p1, p2 in ((gA, gaa, gab), (gB, gbb, gba)):
+        scale = (p1.abs() + p2.abs()).max().item()
+        assert (g - (p1 + p2)).abs().max().item() < 1e-5 * scale
