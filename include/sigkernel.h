@@ -216,11 +216,9 @@ int sigkernel_gram(const sk_paths* X, const sk_paths* Y, int32_t d, int32_t dtyp
  *           the existing contents (the caller zeroes it first for a plain gradient); NULL skips.
  *   grad_Y  likewise for Y.  When Y is X (same rows pointer) both accumulate into the same
  *           buffer correctly if grad_X == grad_Y.
- * Every scheme records forward tapes in chunks of pairs (at most 32 GiB each, two tape buffers in
- * the workspace) and runs the tape adjoint of each chunk (sigkernel_forward_tape and
- * sigkernel_backward_tape below, one chunk at a time) on a second stream, beside the next chunk's
- * forward; the call joins that stream back into `stream` before it returns, and re-runs the
- * forward sweep once.  When the paths are so
+ * Every scheme records forward tapes in chunks of pairs (at most 48 GiB each, in the workspace)
+ * and runs the tape adjoint after each chunk (sigkernel_forward_tape and sigkernel_backward_tape
+ * below, one chunk at a time), so the call re-runs the forward sweep once.  When the paths are so
  * long that a chunk cannot fill the GPU, SK_POLY_APPROX runs the checkpointing adjoint instead
  * (antidiagonal checkpoints every few steps, the forward cells replayed from them; d <= 32) and
  * the other schemes, which have none, return SK_ERR_UNSUPPORTED.  SK_FLAG_CHECKPOINT asks for the
@@ -300,9 +298,9 @@ void sigkernel_autotune_clear(void);
  *   grad_A/B  device double with A's / B's row layout, or NULL: d MMD^2 / d rows, OVERWRITTEN.
  * K_AA and K_BB are solved as symmetric Grams; the reduction runs in FP64 on the device.
  * Gradients (every scheme with an adjoint, see sigkernel_backward) run the adjoint from forward
- * tapes: each Gram block is solved in chunks of pairs whose tape is at most 32 GiB, the chunk's
- * forward recording the tape and the tape adjoint following on a second stream (beside the next
- * chunk's forward, joined back into `stream`) with the block's constant weights.  A block whose paths are so long that a chunk cannot fill the GPU uses the
+ * tapes: each Gram block is solved in chunks of pairs whose tape is at most 48 GiB, the chunk's
+ * forward recording the tape and the tape adjoint following at once with the block's constant
+ * weights.  A block whose paths are so long that a chunk cannot fill the GPU uses the
  * checkpointing adjoint of sigkernel_backward instead (d <= 32; approximation scheme only, else
  * SK_ERR_UNSUPPORTED).
  * The workspace (SK_OP_MMD2 with npairs != 0) includes the tape.

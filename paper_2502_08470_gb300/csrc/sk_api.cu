@@ -70,53 +70,6 @@ TuneKey tune_key(int dev, const sk_paths* X, const sk_paths* Y, const sk_options
         if (e_ != cudaSuccess) return fail(SK_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
     } while (0)
 
-// Chunked tape work (sigkernel_backward, sigkernel_mmd2 with gradients) runs each chunk's forward
-// on the caller's stream and its adjoint on a second stream, so that the next chunk's forward
-// fills the SMs the adjoint's tail leaves idle and the other way round (the two kernels have
-// different resident warp counts, so neither fills whole waves with the other's chunk size).  The
-// second stream and the events that order the two belong to the host thread and the device; they
-// are created on first use and kept.  Dependencies: adjoint j after forward j (event fwd[j % 2]),
-// forward j + 2 after adjoint j (event adj[j % 2]: the tape buffer j % 2 is free again), and the
-// caller's stream after the last adjoint (event join).
-struct Overlap {
-    cudaStream_t aux = nullptr;
-    cudaEvent_t fwd[2] = {nullptr, nullptr}, adj[2] = {nullptr, nullptr}, fork = nullptr, join = nullptr;
-};
-thread_local std::map<int, Overlap> t_overlap;
-
-// Joins the second stream back into the caller's stream when it goes out of scope (every return
-// path after the fork, so that a workspace freed in the caller's stream order outlives the work
-// of both streams), or earlier through join().
-struct OverlapJoin {
-    Overlap* ov;
-    cudaStream_t st;
-    bool armed = true;
-    OverlapJoin(Overlap* o, cudaStream_t s) : ov(o), st(s) {}
-    cudaError_t join() {
-        if (!armed) return cudaSuccess;
-        armed = false;
-        cudaError_t e = cudaEventRecord(ov->join, ov->aux);
-        if (e == cudaSuccess) e = cudaStreamWaitEvent(st, ov->join, 0);
-        return e;
-    }
-    ~OverlapJoin() { join(); }
-    OverlapJoin(const OverlapJoin&) = delete;
-    OverlapJoin& operator=(const OverlapJoin&) = delete;
-};
-
-int get_overlap(Overlap*& out) {
-    int dev = 0;
-    SK_CUDA(cudaGetDevice(&dev));
-    Overlap& ov = t_overlap[dev];
-    if (!ov.aux) {
-        SK_CUDA(cudaStreamCreateWithFlags(&ov.aux, cudaStreamNonBlocking));
-        cudaEvent_t* evs[6] = {&ov.fwd[0], &ov.fwd[1], &ov.adj[0], &ov.adj[1], &ov.fork, &ov.join};
-        for (cudaEvent_t* e : evs) SK_CUDA(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
-    }
-    out = &ov;
-    return SK_OK;
-}
-
 // A workspace that a call allocated for itself (the caller passed none).  It is freed in stream
 // order on every return path, so a call that fails after the allocation does not leak it.
 struct OwnedWorkspace {
@@ -1191,13 +1144,12 @@ __global__ void fill_weights_kernel(double* W, int64_t n, int64_t m, double v, i
 // (K_AA and K_BB symmetric, K_AB full) run one after another in one workspace.  With gradients
 // (polynomial schemes) each block runs in chunks of items: the forward records a tape of
 // the chunk and the tape adjoint runs from it at once, with the block's constant upstream weights
-// (MMD^2 is linear in the Gram entries).  A chunk's tape is at most kTapeChunkBudget bytes (two
-// tape buffers: a chunk's adjoint runs on a second stream beside the next chunk's forward, see
-// Overlap), and a chunk larger than the adjoint's resident warps is a whole number of them.  When
-// the budget holds fewer items than half the adjoint's resident warps (very long paths), the block
-// uses the checkpointing adjoint instead, which keeps only antidiagonal checkpoints (approximation
-// scheme only).  The same budget bounds the chunks of sigkernel_backward.
-constexpr size_t kTapeChunkBudget = size_t(32) << 30;
+// (MMD^2 is linear in the Gram entries).  A chunk's tape is at most kTapeChunkBudget bytes, and a
+// chunk smaller than a block is a whole number of the adjoint's resident warps.  When the budget
+// holds fewer items than half the adjoint's resident warps (very long paths), the block uses the
+// checkpointing adjoint instead, which keeps only antidiagonal checkpoints (approximation scheme
+// only).  The same budget bounds the chunks of sigkernel_backward for the interpolation scheme.
+constexpr size_t kTapeChunkBudget = size_t(48) << 30;
 
 struct MmdPlan {
     bool grads;
@@ -1208,9 +1160,7 @@ struct MmdPlan {
     Plan f[3];
     TapeBwdPlan tb[3];
     BwdPlan cb[3];
-    // sub: the forwards' workspace (and the checkpointing fallback's); sub_b: the tape adjoints',
-    // which run on the second stream beside the next chunk's forward
-    size_t gram_bytes, w_bytes, ginc_a, ginc_bytes, tape_bytes, sub, sub_b, total;
+    size_t gram_bytes, w_bytes, ginc_a, ginc_bytes, tape_bytes, sub, total;
 };
 
 int plan_mmd2(const sk_paths* A, const sk_paths* Bp, int32_t d, int32_t dtype, const sk_options* o, bool grads,
@@ -1235,7 +1185,6 @@ int plan_mmd2(const sk_paths* A, const sk_paths* Bp, int32_t d, int32_t dtype, c
     m.items[2] = gram_items(A, Bp, false);
     int rc;
     m.sub = 0;
-    m.sub_b = 0;
     m.tape_bytes = 0;
     for (int k = 0; k < 3; ++k) {
         const sk_options* ok = k < 2 ? &m.os : &m.of;
@@ -1273,8 +1222,7 @@ int plan_mmd2(const sk_paths* A, const sk_paths* Bp, int32_t d, int32_t dtype, c
         TapePlan tc;
         if ((rc = plan_tape(xs[k], ys[k], ok, p1.T, m.chunk[k], tc)) != SK_OK) return rc;
         m.tape_bytes = std::max(m.tape_bytes, tc.total);
-        m.sub = std::max(m.sub, m.f[k].total);
-        m.sub_b = std::max(m.sub_b, m.tb[k].total);
+        m.sub = std::max(m.sub, std::max(m.f[k].total, m.tb[k].total));
     }
     const int64_t na = A->count, nb = Bp->count;
     const int dpad = m.f[0].dpad;
@@ -1282,8 +1230,7 @@ int plan_mmd2(const sk_paths* A, const sk_paths* Bp, int32_t d, int32_t dtype, c
     m.w_bytes = grads ? m.gram_bytes : 0;
     m.ginc_a = grads ? align256(static_cast<size_t>(A->rows_total) * dpad * 8) : 0;
     m.ginc_bytes = grads ? m.ginc_a + align256(static_cast<size_t>(Bp->rows_total) * dpad * 8) : 0;
-    m.total = m.gram_bytes + m.w_bytes + m.ginc_bytes + 2 * align256(m.tape_bytes) + align256(m.sub) +
-              align256(m.sub_b) + 512;
+    m.total = m.gram_bytes + m.w_bytes + m.ginc_bytes + align256(m.tape_bytes) + m.sub + 512;
     return SK_OK;
 }
 
@@ -1315,9 +1262,7 @@ int run_mmd2(const sk_paths* A, const sk_paths* Bp, int32_t d, int32_t dtype, co
     double* gincA = reinterpret_cast<double*>(base + m.gram_bytes + m.w_bytes);
     double* gincB = reinterpret_cast<double*>(base + m.gram_bytes + m.w_bytes + m.ginc_a);
     char* tape = base + m.gram_bytes + m.w_bytes + m.ginc_bytes;
-    char* tapes[2] = {tape, tape + align256(m.tape_bytes)};
-    char* sub_ws = tape + 2 * align256(m.tape_bytes);
-    char* sub_b = sub_ws + align256(m.sub);
+    char* sub_ws = tape + align256(m.tape_bytes);
     const sk_paths* xs[3] = {A, Bp, A};
     const sk_paths* ys[3] = {A, Bp, Bp};
     const int modes[3] = {kGramUpper, kGramUpper, kGramFull};
@@ -1341,45 +1286,27 @@ int run_mmd2(const sk_paths* A, const sk_paths* Bp, int32_t d, int32_t dtype, co
         double* gx[3] = {gincA, gincB, gincA};
         double* gy[3] = {gincA, gincB, gincB};
         char* sb = reinterpret_cast<char*>((reinterpret_cast<uintptr_t>(sub_ws) + 255) / 256 * 256);
-        // chunk j's forward on st, its tape adjoint on the second stream (see Overlap)
-        Overlap* ov = nullptr;
-        if ((rc = get_overlap(ov)) != SK_OK) return rc;
-        cudaStream_t sa = ov->aux;
-        SK_CUDA(cudaEventRecord(ov->fork, st));
-        SK_CUDA(cudaStreamWaitEvent(sa, ov->fork, 0));
-        OverlapJoin joiner(ov, st);
-        int64_t j = 0;
         for (int k = 0; k < 3; ++k) {
             const sk_options* ok = k < 2 ? &m.os : &m.of;
-            if (!m.tape[k]) {  // checkpointing adjoint on st, after the second stream's work
-                SK_CUDA(joiner.join());
+            if (!m.tape[k]) {
                 if ((rc = run_forward(xs[k], ys[k], d, dtype, ok, modes[k], nullptr, nullptr, m.items[k], Ks[k], ldos[k],
                                       sub_ws, m.sub, st)) != SK_OK)
                     return rc;
                 if ((rc = launch_backward(xs[k], ys[k], d, dtype, ok, modes[k], nullptr, nullptr, m.items[k], Ws[k],
                                           ldos[k], m.cb[k], sb, gx[k], gy[k], st)) != SK_OK)
                     return rc;
-                SK_CUDA(cudaEventRecord(ov->fork, st));
-                SK_CUDA(cudaStreamWaitEvent(sa, ov->fork, 0));
-                joiner.armed = true;
                 continue;
             }
-            for (int64_t i0 = 0; i0 < m.items[k]; i0 += m.chunk[k], ++j) {
+            for (int64_t i0 = 0; i0 < m.items[k]; i0 += m.chunk[k]) {
                 const int64_t n = std::min(m.chunk[k], m.items[k] - i0);
-                const int t = static_cast<int>(j & 1);
-                if (j >= 2) SK_CUDA(cudaStreamWaitEvent(st, ov->adj[t], 0));  // adjoint j - 2 has read this tape
                 if ((rc = run_forward(xs[k], ys[k], d, dtype, ok, modes[k], nullptr, nullptr, n, Ks[k], ldos[k], sub_ws,
-                                      m.sub, st, tapes[t], m.tape_bytes, i0)) != SK_OK)
+                                      m.sub, st, tape, m.tape_bytes, i0)) != SK_OK)
                     return rc;
-                SK_CUDA(cudaEventRecord(ov->fwd[t], st));
-                SK_CUDA(cudaStreamWaitEvent(sa, ov->fwd[t], 0));
-                if ((rc = launch_backward_tape(xs[k], ys[k], d, dtype, ok, modes[k], nullptr, nullptr, n, i0, tapes[t],
-                                               Ws[k], ldos[k], m.tb[k], sub_b, gx[k], gy[k], sa)) != SK_OK)
+                if ((rc = launch_backward_tape(xs[k], ys[k], d, dtype, ok, modes[k], nullptr, nullptr, n, i0, tape, Ws[k],
+                                               ldos[k], m.tb[k], sb, gx[k], gy[k], st)) != SK_OK)
                     return rc;
-                SK_CUDA(cudaEventRecord(ov->adj[t], sa));
             }
         }
-        SK_CUDA(joiner.join());
         const int inc_mode = (o->flags & SK_FLAG_INCREMENTS) ? 1 : 0;
         const int dpad = m.f[0].dpad;
         if (gA) {
@@ -1397,9 +1324,9 @@ int run_mmd2(const sk_paths* A, const sk_paths* Bp, int32_t d, int32_t dtype, co
     return SK_OK;
 }
 
-// sigkernel_backward: the items are taken in chunks whose forward records a tape (at most
-// kTapeChunkBudget bytes, two tape buffers) and whose tape adjoint follows on the second stream,
-// as in sigkernel_mmd2.  When the paths are so long that a chunk holds fewer items than half the
+// sigkernel_backward of the polynomial schemes: the items are taken in chunks whose forward
+// records a tape (at most kTapeChunkBudget bytes) and whose tape adjoint follows at once, as in
+// sigkernel_mmd2.  When the paths are so long that a chunk holds fewer items than half the
 // adjoint's resident warps, the plan says so (fits = false): the approximation scheme then runs the
 // checkpointing adjoint, and the interpolation scheme, which has none, is refused
 // (SK_ERR_UNSUPPORTED).
@@ -1408,7 +1335,7 @@ struct ChunkBwdPlan {
     int64_t items, chunk;
     Plan f;           // forward of one chunk, recording its tape
     TapeBwdPlan tb;   // tape adjoint of one chunk
-    size_t ginc_a, ginc_bytes, tape_bytes, out_bytes, sub_f, sub_b, total;
+    size_t ginc_a, ginc_bytes, tape_bytes, out_bytes, sub, total;
 };
 
 int plan_backward_chunked(const sk_paths* X, const sk_paths* Y, int32_t d, int32_t dtype, const sk_options* o,
@@ -1442,9 +1369,8 @@ int plan_backward_chunked(const sk_paths* X, const sk_paths* Y, int32_t d, int32
     c.out_bytes = align256(static_cast<size_t>(std::max<int64_t>(nout, 1)) * sizeof(double));
     c.ginc_a = align256(static_cast<size_t>(X->rows_total) * p1.dpad * sizeof(double));
     c.ginc_bytes = c.ginc_a + (p1.same_xy ? 0 : align256(static_cast<size_t>(Y->rows_total) * p1.dpad * sizeof(double)));
-    c.sub_f = align256(c.f.total);
-    c.sub_b = align256(c.tb.total);
-    c.total = c.ginc_bytes + 2 * align256(c.tape_bytes) + c.out_bytes + c.sub_f + c.sub_b + 512;
+    c.sub = std::max(c.f.total, c.tb.total);
+    c.total = c.ginc_bytes + align256(c.tape_bytes) + c.out_bytes + c.sub + 512;
     return SK_OK;
 }
 
@@ -1483,38 +1409,25 @@ int run_backward_chunked(const sk_paths* X, const sk_paths* Y, int32_t d, int32_
     char* base = reinterpret_cast<char*>((reinterpret_cast<uintptr_t>(ws) + 255) / 256 * 256);
     double* gincX = reinterpret_cast<double*>(base);
     double* gincY = c.f.same_xy ? gincX : reinterpret_cast<double*>(base + c.ginc_a);
-    char* tapes[2] = {base + c.ginc_bytes, base + c.ginc_bytes + align256(c.tape_bytes)};
-    double* outbuf = reinterpret_cast<double*>(tapes[1] + align256(c.tape_bytes));
-    char* sub_f = reinterpret_cast<char*>(outbuf) + c.out_bytes;
-    char* sub_b = sub_f + c.sub_f;
-    Overlap* ov = nullptr;
-    if ((rc = get_overlap(ov)) != SK_OK) return rc;
-    cudaStream_t sa = ov->aux;
+    char* tape = base + c.ginc_bytes;
+    double* outbuf = reinterpret_cast<double*>(tape + align256(c.tape_bytes));
+    char* sub_ws = reinterpret_cast<char*>(outbuf) + c.out_bytes;
+    char* sb = reinterpret_cast<char*>((reinterpret_cast<uintptr_t>(sub_ws) + 255) / 256 * 256);
     SK_CUDA(cudaMemsetAsync(gincX, 0, c.ginc_bytes, st));
-    SK_CUDA(cudaEventRecord(ov->fork, st));
-    SK_CUDA(cudaStreamWaitEvent(sa, ov->fork, 0));
-    OverlapJoin joiner(ov, st);
     const int64_t ldo = gram ? Y->count : 0;
-    int64_t j = 0;
-    for (int64_t i0 = 0; i0 < npairs; i0 += c.chunk, ++j) {
+    for (int64_t i0 = 0; i0 < npairs; i0 += c.chunk) {
         const int64_t n = std::min(c.chunk, npairs - i0);
         const int64_t* pai = gram ? nullptr : pa + i0;
         const int64_t* pbi = gram ? nullptr : pb + i0;
         const double* gi = gram ? gout : gout + i0;
         const int64_t base_item = gram ? i0 : 0;
-        const int t = static_cast<int>(j & 1);
-        if (j >= 2) SK_CUDA(cudaStreamWaitEvent(st, ov->adj[t], 0));  // adjoint j - 2 has read this tape
-        if ((rc = run_forward(X, Y, d, dtype, o, mode, pai, pbi, n, outbuf, ldo, sub_f, c.sub_f, st, tapes[t],
-                              c.tape_bytes, base_item)) != SK_OK)
+        if ((rc = run_forward(X, Y, d, dtype, o, mode, pai, pbi, n, outbuf, ldo, sub_ws, c.sub, st, tape, c.tape_bytes,
+                              base_item)) != SK_OK)
             return rc;
-        SK_CUDA(cudaEventRecord(ov->fwd[t], st));
-        SK_CUDA(cudaStreamWaitEvent(sa, ov->fwd[t], 0));
-        if ((rc = launch_backward_tape(X, Y, d, dtype, o, mode, pai, pbi, n, base_item, tapes[t], gi, ldo, c.tb, sub_b,
-                                       gincX, gincY, sa)) != SK_OK)
+        if ((rc = launch_backward_tape(X, Y, d, dtype, o, mode, pai, pbi, n, base_item, tape, gi, ldo, c.tb, sb, gincX,
+                                       gincY, st)) != SK_OK)
             return rc;
-        SK_CUDA(cudaEventRecord(ov->adj[t], sa));
     }
-    SK_CUDA(joiner.join());
     const int inc_mode = (o->flags & SK_FLAG_INCREMENTS) ? 1 : 0;
     if ((rc = convert_grad(X, d, c.f.dpad, inc_mode, gincX, gX, st)) != SK_OK) return rc;
     if (!c.f.same_xy && (rc = convert_grad(Y, d, c.f.dpad, inc_mode, gincY, gY, st)) != SK_OK) return rc;

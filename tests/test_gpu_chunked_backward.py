@@ -1,8 +1,14 @@
-"""GPU tests of the two-stream chunk pipeline of sigkernel_backward and sigkernel_mmd2: each
-chunk's tape adjoint runs on a second stream beside the next chunk's forward, and the call joins
-that stream back into the caller's stream.  The results must be the caller-stream-ordered ones
-(read right after the call on the caller's stream, no device-wide synchronisation in between),
-and the whole fork/join must capture into a CUDA graph and replay on new inputs.
+"""GPU tests of the chunked tape adjoints of sigkernel_backward and sigkernel_mmd2: the results
+must be ordered on the caller's stream (read right after the call on that stream, with no
+device-wide synchronisation in between), the whole call must capture into a CUDA graph and replay
+on new inputs, and the MMD^2 gradient solved in several chunks per Gram block must match the
+backward of each block.
+
+These runs also guard the shared-memory rings of the tape adjoint and the FMA contraction: a ring
+slot that the warp has read is fenced (fence.proxy.async) before a bulk copy refills it.  Without
+the fence the refill could overtake a pending load of the slot when other kernels kept the
+load/store units busy (seen as intermittent FP32 gradient errors up to 1e-3 of scale while a
+forward kernel ran beside the adjoint).
 """
 import numpy as np
 import pytest
@@ -28,13 +34,15 @@ def _scaled(a, b):
 
 @pytest.mark.parametrize("scheme,lam", [("approx", 0), ("fd1", 1)])
 def test_backward_on_a_side_stream_is_ordered_for_the_caller(scheme, lam):
+    """The call on a non-default torch stream: its gradients are complete for the next kernel on
+    that stream."""
     X = torch.tensor(W.brownian(6, 80, 3, seed=71), device="cuda")
     Y = torch.tensor(W.brownian(5, 70, 3, seed=72), device="cuda")
     g = torch.tensor(np.random.default_rng(73).standard_normal((6, 5)), device="cuda")
     s = torch.cuda.Stream()
     with torch.cuda.stream(s):
         gx, gy = sk.sigkernel_backward(g, X, Y, scheme=scheme, degree=6, dyadic=lam, compute="f64")
-        # consumed on the caller's stream right away: the call must have joined its second stream
+        # consumed on the caller's stream right away, without a device-wide synchronisation
         tot_x, tot_y = gx.sum(), gy.sum()
     s.synchronize()
     assert sk.device_status() == 0
@@ -54,7 +62,7 @@ def test_backward_captures_into_a_cuda_graph():
     X = torch.tensor(W.brownian(8, 65, 4, seed=81), device="cuda")
     Y = torch.tensor(W.brownian(8, 65, 4, seed=82), device="cuda")
     g = torch.tensor(np.random.default_rng(83).standard_normal((8, 8)), device="cuda")
-    gx0, _ = sk.sigkernel_backward(g, X, Y, compute="f32")  # eager first: creates the second stream
+    gx0, _ = sk.sigkernel_backward(g, X, Y, compute="f32")  # an eager call before the capture
     torch.cuda.synchronize()
     graph = torch.cuda.CUDAGraph()
     s = torch.cuda.Stream()
@@ -74,10 +82,9 @@ def test_backward_captures_into_a_cuda_graph():
 
 
 def test_mmd2_gradient_across_many_chunks_matches_the_backward_of_each_block():
-    # 80 + 80 paths of 513 points (14.7 MB of tape per pair at N = 6): with 32 GiB per tape a chunk
-    # holds 2331 pairs, so K_AA and K_BB run in 2 chunks each and K_AB in 3, and the second
-    # stream's adjoints overlap the next chunks' forwards across the blocks
-    n = 80
+    # 120 + 120 paths of 513 points (14.7 MB of tape per pair at N = 6): with 48 GiB of tape a chunk
+    # holds 3497 pairs, so K_AA and K_BB (7260 pairs) run in 3 chunks each and K_AB (14400) in 5
+    n = 120
     A = torch.tensor(W.brownian(n, 513, 3, seed=91), device="cuda")
     B = torch.tensor(W.brownian(n, 513, 3, seed=92, drift=0.5, vol=1.2), device="cuda")
     m, means, gA, gB = sk.sigkernel_mmd2(A, B, compute="f32", grads=True)
