@@ -57,23 +57,27 @@ SM_COUNT, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0  # nominal, for context only
 
 
 def flops_per_cell(N: int, d: int) -> int:
-    """Algorithmic FLOPs of one polynomial-approximation cell update (2 per multiply-add):
-    both edges' Toeplitz convolutions (N+1)(N+2), Hankel couplings 2N(N+1) and their e_n
-    scalings 2(N+1), the N terms of e_m = M^m/m!, and the d-term inner product M_ij."""
-    fma = (N + 1) * (N + 2) + 2 * N * (N + 1) + 2 * (N + 1) + N + d
+    """Algorithmic FLOPs of one polynomial-approximation cell update (2 per multiply-add), as the
+    kernels compute it: with e_0 = 1 every output c_n = e_n (c_0 + H_n) + sum_{1<=k<n} c_k e_{n-k}
+    + c_n costs N multiply-adds for the corner term plus Hankel coupling (n = 0..N), n - 1 for the
+    rest of the Toeplitz convolution and one for the scaling (n >= 1), on both edges; then the N
+    terms of e_m = M^m/m! and the d-term inner product M_ij.  (Counting the products with e_0 and
+    each sum's first product, as a literal reading of the update does, gives 336 instead of 280
+    at N = 6, d = 8.)"""
+    fma = 2 * N * (N + 1) + N * (N - 1) + 2 * N + N + d
     return 2 * fma
 
 
 def tape_forward_flops_per_cell(N: int, d: int) -> int:
-    """The forward cell plus the 2N derivatives d a'_n/dM, d b'_n/dM it records on the tape
-    (one multiply-add each)."""
-    return flops_per_cell(N, d) + 2 * 2 * N
+    """The forward cell plus the 2N derivatives d a'_n/dM, d b'_n/dM it records on the tape (one
+    multiply-add each but the first of each edge, which is the n = 1 coupling sum itself)."""
+    return flops_per_cell(N, d) + 2 * 2 * (N - 1)
 
 
 def adjoint_edge_fma(N: int) -> int:
-    """Multiply-adds of one cell's edge adjoints: Hankel weights 2(N+1), Toeplitz transposes
-    (N+1)(N+2), Hankel couplings 2N(N+1)."""
-    return 2 * (N + 1) + (N + 1) * (N + 2) + 2 * N * (N + 1)
+    """Multiply-adds of one cell's edge adjoints: Hankel weights g_n e_n (n >= 1) on both edges 2N,
+    Toeplitz transposes N(N+1) (each sum starts from its e_0 term), Hankel couplings 2N(N+1)."""
+    return 2 * N + N * (N + 1) + 2 * N * (N + 1)
 
 
 def tape_adjoint_flops_per_cell(N: int) -> int:

@@ -47,14 +47,17 @@ def test_tape_bytes_of_the_bench_launch(bench):
 
 def test_flops_per_cell(bench):
     N, d = 6, 8
-    toeplitz = 2 * sum(n + 1 for n in range(N + 1))      # both edges: sum_n (n + 1) terms
-    hankel = 2 * (N + 1) * N                             # both edges: N couplings per output
-    scale = 2 * (N + 1)                                  # e_n times each coupling sum
-    assert bench.flops_per_cell(N, d) == 2 * (toeplitz + hankel + scale + N + d) == 336
-    assert bench.tape_forward_flops_per_cell(N, d) == 336 + 2 * 2 * N
-    # adjoint: Hankel weights, Toeplitz transposes and Hankel couplings of both edges, dk/dM from
-    # the 2N recorded derivatives, and e_m rebuilt from M
-    assert bench.tape_adjoint_flops_per_cell(N) == 2 * (2 * (N + 1) + toeplitz + hankel + 2 * N + N) == 344
+    # per edge and output n: N multiply-adds for the corner term plus Hankel coupling; for n >= 1
+    # the Toeplitz terms 1 <= k < n (the k = n term is a_n e_0 = a_n) and the e_n scaling
+    corner_hankel = 2 * (N + 1) * N
+    toeplitz = 2 * sum(n - 1 for n in range(1, N + 1))
+    scale = 2 * N
+    assert bench.flops_per_cell(N, d) == 2 * (corner_hankel + toeplitz + scale + N + d) == 280
+    assert bench.tape_forward_flops_per_cell(N, d) == 280 + 2 * 2 * (N - 1)
+    # adjoint: Hankel weights (n >= 1), Toeplitz transposes (each from its e_0 term) and Hankel
+    # couplings of both edges, dk/dM from the 2N recorded derivatives, and e_m rebuilt from M
+    transposes = 2 * sum(N - k for k in range(N + 1))
+    assert bench.tape_adjoint_flops_per_cell(N) == 2 * (2 * N + transposes + corner_hankel + 2 * N + N) == 312
 
 
 def test_clock_samples_are_summarised_and_the_temporary_file_removed(bench, monkeypatch):
