@@ -123,11 +123,10 @@ def load_hbm_peak():
 
 # DRAM traffic (ncu dram__bytes_read.sum + dram__bytes_write.sum) of one launch, as a multiple of
 # that launch's algorithmic bytes, from captures of the current kernels on 48 x 48 pairs of
-# 129-point paths (profiles/fwd_poly_kernel_tape_gram48x129.md, bwd_tape_kernel_gram48x129.md):
-# both kernels' traffic is per warp step, so it scales with the steps of the bench's Gram.  None
-# when no capture of the current kernel exists.
-NCU_TRAFFIC_RATIO = {"bwd_tape_kernel<float,6,false>": (2.270 + 0.186) / 2.402,
-                     "fwd_poly_kernel<float,6,6,false,1,false,true>": (2.205 + 0.001) / 2.242}
+# 129-point paths (profiles/*_gram48x129.md): both kernels' traffic is per warp step, so it
+# scales with the steps of the bench's Gram.  None when no capture of the current kernel exists.
+NCU_TRAFFIC_RATIO = {"bwd_tape_kernel<float,6,false>": (2.270 + 0.185) / 2.402,
+                     "fwd_poly_kernel<float,6,6,false,1,false,true,true>": (2.207 + 0.161) / 2.242}
 
 
 def parse():
@@ -503,9 +502,10 @@ def main():
     kb = statistics.mean(kb_ms)
     bcall = statistics.mean(run.backward_call_ms) if run.backward_call_ms else None
     tape_gb = tape_buf[0].numel() / 1e9
-    fwd_rl = kernel_roofline("fwd_poly_kernel<float,6,6,false,1,false,true> (forward recording the tape)", kf,
+    fwd_rl = kernel_roofline("m_tc_kernel<16> + fwd_poly_kernel<float,6,6,false,1,false,true,true> (forward "
+                             "recording the tape, M from the tensor cores; algorithmic bytes: the tape)", kf,
                              tape_forward_flops_per_cell(DEGREE, D) * cells, tape_forward_bytes(nx * nx, npts), p32,
-                             "fwd_poly_kernel<float,6,6,false,1,false,true>")
+                             "fwd_poly_kernel<float,6,6,false,1,false,true,true>")
     bwd_rl = kernel_roofline("bwd_tape_kernel<float,6,false> (adjoint wavefront from the tape)", kb,
                              tape_adjoint_flops_per_cell(DEGREE) * cells, tape_adjoint_bytes(nx * nx, npts), p32,
                              "bwd_tape_kernel<float,6,false>")
@@ -538,8 +538,10 @@ def main():
                                       "rest_ms": (bcall - kb) if bcall is not None else None,
                                       "rest": "increments, dk/dM contraction kernel, gradient conversions"}},
         "peaks": peaks,
-        # forward: 2 increments + wavefront; adjoint: 2 increments + adjoint + contraction + 2 gradient conversions
-        "gpu_launches": 9 * args.steps,
+        # forward: 2 increments + 2 BF16 operand splits + tensor-core M + wavefront; adjoint: 2
+        # increments + adjoint + contraction + 2 gradient conversions (the ncu launch list of the
+        # same command, profiles/launches_gram128.md, counts the same 12 per step)
+        "gpu_launches": 12 * args.steps,
         "clocks": clocks, "device_status": status, "wall_s_timed_region": wall,
     })
     tape_buf[0] = None
@@ -599,7 +601,8 @@ def main():
         kfo = statistics.mean(kff)
         line["forward_only"] = {"value": cells / (statistics.mean(sf) / 1e3), "unit": "cell-updates/s",
                                 "ms_per_step": statistics.mean(sf),
-                                "kernel": kernel_roofline("fwd_poly_kernel<float,6,6,false,1,false> (no tape)", kfo,
+                                "kernel": kernel_roofline("m_tc_kernel<16> + fwd_poly_kernel<float,6,6,false,1,false,"
+                                                          "false,true> (no tape, M from the tensor cores)", kfo,
                                                           flops_per_cell(DEGREE, D) * cells, 0, p32)}
 
     if "f64" in args.parts:  # FP64 plain wavefront: forward, and fwd+bwd from an FP64 tape

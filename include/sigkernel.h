@@ -120,22 +120,23 @@ enum {
                                        checkpointing adjoint (no tape; its workspace grows with the
                                        paths, not with the pair count) instead of the default
                                        adjoint from chunked forward tapes */
-    SK_FLAG_NO_TC = 512             /* FP32, 8 < d <= 32: keep the tensor cores out.  By default
-                                       (1) the approximation scheme's forward with one warp per
-                                       pair (plain or recording a tape; not the strip pipeline)
-                                       takes each cell's M_ij = <dx_i, dy_j> / 4^lambda from a
-                                       tcgen05 GEMM of the increments, run per chunk of pairs
-                                       before the chunk's sweep (flag set: tiled or per-cell M on
-                                       the FMA pipe, see SK_FLAG_NO_TILED_M), and (2) an adjoint
-                                       from a tape contracts dk/dM with the increments on the
-                                       tensor cores when the refined grid of the longest pair fits
-                                       its tensor memory ((ceil(rows / 128) + ceil(cols / 128)) x
-                                       (16 or 32) <= 256; flag set: on the FMA pipe).  The M
-                                       kernel splits each FP32 increment into three BF16 parts and
-                                       keeps six of the nine part products (about 2^-22 relative
-                                       per product); the contraction splits dk/dM and the
-                                       increments into two parts and keeps three products (about
-                                       2^-16); both accumulate in FP32 */
+    SK_FLAG_NO_TC = 512             /* FP32: keep the tensor cores out.  By default (1) the
+                                       approximation scheme's forward with one warp per pair
+                                       (plain or recording a tape; not the strip pipeline) with
+                                       4 < d <= 32 takes each cell's M_ij = <dx_i, dy_j> /
+                                       4^lambda from a tcgen05 GEMM of the increments, run per
+                                       chunk of pairs before the chunk's sweep (flag set: tiled
+                                       or per-cell M on the FMA pipe, see SK_FLAG_NO_TILED_M),
+                                       and (2) with 8 < d <= 32 an adjoint from a tape contracts
+                                       dk/dM with the increments on the tensor cores when the
+                                       refined grid of the longest pair fits its tensor memory
+                                       ((ceil(rows / 128) + ceil(cols / 128)) x (16 or 32) <=
+                                       256; flag set: on the FMA pipe).  The M kernel splits each
+                                       FP32 increment into three BF16 parts and keeps six of the
+                                       nine part products (about 2^-22 relative per product);
+                                       the contraction splits dk/dM and the increments into two
+                                       parts and keeps three products (about 2^-16); both
+                                       accumulate in FP32 */
 };
 
 typedef struct {

@@ -359,17 +359,22 @@ int plan_forward(const sk_paths* X, const sk_paths* Y, int32_t d, int32_t dtype,
             }
         }
     }
-    // Tensor-core M: in place of the tiled-M build, the FP32 approximation scheme's one-warp-per-pair
-    // sweep reads each cell's M from a buffer that a tcgen05 GEMM fills per chunk of items
-    // (sk_m_tc.cu).  Off with SK_FLAG_NO_TC, for the interpolation scheme, for the strip pipeline,
-    // and when even one wave of resident warps would need more than twice kMxBudget.
+    // Tensor-core M: in place of the per-cell or tiled M, the FP32 approximation scheme's
+    // one-warp-per-pair sweep reads each cell's M from a buffer that a tcgen05 GEMM fills per chunk
+    // of items (sk_m_tc.cu), for padded widths 8..32 (d from 5 to 32).  At d = 8 it took the
+    // 128 x 128 Gram's plain forward from 10.62 to 9.02 ms (the M kernel included) and its tape
+    // forward from 12.31 to 12.18 ms.  Off with SK_FLAG_NO_TC, for the interpolation scheme, for
+    // the strip pipeline, and when even one wave of resident warps would need more than twice
+    // kMxBudget.
     p.mx = false;
     p.kp = p.dpad <= 16 ? 16 : 32;
     p.xt_nblk = static_cast<int>(((X->max_len << lam) + 127) / 128);
     p.yt_nblk = static_cast<int>(((Y->max_len << lam) + 127) / 128);
     p.mx_stride = 0;
     p.mx_chunk = npairs;
-    if (p.mtile && !p.coop && o->scheme == SK_POLY_APPROX && p.dpad <= 32 && !(o->flags & SK_FLAG_NO_TC)) {
+    const bool mt_chosen = p.mtile;
+    if ((p.mtile || (p.T == 1 && p.dpad == 8)) && !p.coop && o->scheme == SK_POLY_APPROX && p.dpad <= 32 &&
+        !(o->flags & SK_FLAG_NO_TC)) {
         const void* km = fwd_poly_kernel_ptr(p.T, false, o->degree, false, false, tape, true);
         if (km) {
             const int64_t pts = (o->flags & SK_FLAG_INCREMENTS) ? 0 : 1;
@@ -397,7 +402,7 @@ int plan_forward(const sk_paths* X, const sk_paths* Y, int32_t d, int32_t dtype,
                 p.mx_stride = stride;
                 p.mx_chunk = std::max<int64_t>(std::min(chunk, npairs), 1);
             } else {
-                p.mtile = true;
+                p.mtile = mt_chosen;
             }
         }
     }

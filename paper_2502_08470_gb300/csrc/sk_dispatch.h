@@ -111,7 +111,7 @@ cudaError_t launch_tc_operands(int N, const PathSet& S, int inc_mode, int lam, i
 cudaError_t launch_tc_contraction(int N, const BwdParams& B, int nrb_max, int sms, cudaStream_t st);
 
 struct Launch;
-// Tensor-core M of the forward (FP32 approximation scheme, 8 < d <= 32; KP = 16 or 32 padded
+// Tensor-core M of the forward (FP32 approximation scheme, 4 < d <= 32; KP = 16 or 32 padded
 // coordinates): operand tiles of a path set (nblk 128-row blocks per path, m_operand_bytes bytes),
 // and the M of work items 0 .. L.npairs - 1 of a launch into mx (mx_stride bytes per item, the
 // layout of Launch::mx) on `sms` CTAs.

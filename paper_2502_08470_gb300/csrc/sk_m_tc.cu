@@ -1,5 +1,5 @@
 // The increment inner products M_ij = <dx_i, dy_j> / 4^lambda of every cell of a batch of pairs on
-// the tensor cores (tcgen05, FP32 compute mode with 8 < d <= 32), for the wavefront to read.
+// the tensor cores (tcgen05, FP32 compute mode with 4 < d <= 32), for the wavefront to read.
 //
 // For a pair (a, b) the cells' M is the product of the pair's increment rows, DX_a (rows x d) times
 // DY_b^T (d x cols), with refined row i using increment i >> lambda.  Each FP32 increment is split

@@ -196,7 +196,7 @@ def sigkernel_pairs(X, Y, pair_a, pair_b, scheme="approx", degree=6, dyadic=0, c
     """k_hat(X[pair_a[k]], Y[pair_b[k]]) for every k, as a float64 CUDA tensor.
 
     ``tensor_cores=False`` (SK_FLAG_NO_TC) keeps the FP32 approximation scheme's M on the FMA pipe
-    (tiled, or per cell with ``tiled_m=False``) instead of the tcgen05 M kernel (8 < d <= 32)."""
+    (tiled, or per cell with ``tiled_m=False``) instead of the tcgen05 M kernel (4 < d <= 32)."""
     X, Y = as_paths(X), as_paths(Y)
     pa = torch.as_tensor(pair_a, dtype=torch.int64, device="cuda").contiguous()
     pb = torch.as_tensor(pair_b, dtype=torch.int64, device="cuda").contiguous()
@@ -224,7 +224,7 @@ def sigkernel_gram(X, Y=None, scheme="approx", degree=6, dyadic=0, compute="f64"
     the tcgen05 M kernel, from its first launch to the last sweep); ``strip_pipeline`` (None / True
     / False) chooses how long pairs are swept (see the flags SK_FLAG_STRIP_PIPELINE and
     SK_FLAG_NO_STRIP_PIPELINE); ``tensor_cores=False`` (SK_FLAG_NO_TC) keeps the FP32
-    approximation scheme's M on the FMA pipe instead of the tcgen05 M kernel (8 < d <= 32)."""
+    approximation scheme's M on the FMA pipe instead of the tcgen05 M kernel (4 < d <= 32)."""
     sym = Y is None or Y is X
     X = as_paths(X)
     Y = X if sym else as_paths(Y)
