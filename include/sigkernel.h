@@ -111,11 +111,11 @@ enum {
                                        more blocks, the pipelined polynomial forward spreads each
                                        ring over co-resident blocks (a cooperative launch; the
                                        results are the same bit for bit) */
-    SK_FLAG_NO_TILED_M = 128,       /* forward, polynomial schemes in FP32: form each cell's M from
-                                       its two increment rows.  By default, with d > 8, each warp
-                                       first computes a strip's M_ij for all columns at once (the
-                                       same values bit for bit), unless the tensor cores compute M
-                                       (see SK_FLAG_NO_TC) */
+    SK_FLAG_NO_TILED_M = 128,       /* forward, polynomial schemes in FP32, where the tensor cores
+                                       do not compute M (see SK_FLAG_NO_TC): form each cell's M
+                                       from its two increment rows.  By default, with d > 8, each
+                                       warp first computes a strip's M_ij for all columns at once
+                                       (the same values bit for bit) */
     SK_FLAG_CHECKPOINT = 256,       /* sigkernel_backward, approximation scheme: run the
                                        checkpointing adjoint (no tape; its workspace grows with the
                                        paths, not with the pair count) instead of the default

@@ -373,7 +373,7 @@ int plan_forward(const sk_paths* X, const sk_paths* Y, int32_t d, int32_t dtype,
     p.mx_stride = 0;
     p.mx_chunk = npairs;
     const bool mt_chosen = p.mtile;
-    if ((p.mtile || (p.T == 1 && p.dpad == 8)) && !p.coop && o->scheme == SK_POLY_APPROX && p.dpad <= 32 &&
+    if (p.T == 1 && o->scheme == SK_POLY_APPROX && p.dpad >= 8 && p.dpad <= 32 && !p.coop &&
         !(o->flags & SK_FLAG_NO_TC)) {
         const void* km = fwd_poly_kernel_ptr(p.T, false, o->degree, false, false, tape, true);
         if (km) {
