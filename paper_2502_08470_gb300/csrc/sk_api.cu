@@ -900,7 +900,7 @@ int plan_backward_tape(const sk_paths* X, const sk_paths* Y, int32_t d, int32_t 
     b.cC = p.dpad <= 8 ? 8 : (p.dpad <= 16 ? 16 : 32);
     b.ckern = p.T ? bwd_contract_ptr_f32(b.cC) : bwd_contract_ptr_f64(b.cC);
     const int step_bytes = 32 * (p.T ? tape_row<float>(o->degree, interp) * 4 : tape_row<double>(o->degree, interp) * 8);
-    b.smem_bytes = fd ? 0 : kFwdWarps * bwd_tape_warp_bytes(step_bytes);
+    b.smem_bytes = kFwdWarps * (fd ? bwd_fd_ring_bytes(p.T, o->dyadic) : bwd_tape_warp_bytes(step_bytes));
     const int esize = p.T ? 4 : 8, N = fd ? 0 : o->degree;  // FD hands one value per column down
     b.cols_max = std::max<int64_t>(Y->max_len << o->dyadic, 1);
     b.off_rbuf = 0;

@@ -25,4 +25,15 @@ const void* bwd_fd_tape_ptr(int T, int order, int lam) {
 
 int fd_tape_row_elems(int T, int lam) { return T ? fd_tape_row<float>(1 << lam) : fd_tape_row<double>(1 << lam); }
 
+int bwd_fd_ring_bytes(int T, int lam) {
+    switch (lam) {
+        case 0: return T ? fd_ring_warp_bytes<float, 1>() : fd_ring_warp_bytes<double, 1>();
+        case 1: return T ? fd_ring_warp_bytes<float, 2>() : fd_ring_warp_bytes<double, 2>();
+        case 2: return T ? fd_ring_warp_bytes<float, 4>() : fd_ring_warp_bytes<double, 4>();
+        case 3: return T ? fd_ring_warp_bytes<float, 8>() : fd_ring_warp_bytes<double, 8>();
+        case 4: return T ? fd_ring_warp_bytes<float, 16>() : fd_ring_warp_bytes<double, 16>();
+        default: return 0;
+    }
+}
+
 }  // namespace sk

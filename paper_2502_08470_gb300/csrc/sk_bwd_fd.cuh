@@ -18,6 +18,13 @@
 // writes the sum, relative to 2^ek, into the contraction's dk/dM buffer for the coarse grid (the
 // skewed [step][lane] rows of bwd_contract_kernel, or the tiles of the tensor-core contraction).
 // FP32 carries power-of-two exponents for the adjoints as the polynomial adjoint does.
+//
+// The tape rows stream through a per-warp ring in shared memory, kFdRing<R> steps ahead: each
+// lane copies its own 16-byte vectors of a step with cp.async (one commit group per step) and
+// waits for the oldest group only when it needs that step, so the row loads no longer stall
+// every step (measured: the FD1 adjoint at lambda = 0 spent most cycles waiting on its per-step
+// loads, issue 30%).  A lane reads only the vectors it copied itself, so cp.async.wait_group
+// orders the copy before the read without any warp-wide barrier.
 #pragma once
 
 #include <type_traits>
@@ -26,6 +33,26 @@
 #include "sk_fwd_fd.cuh"
 
 namespace sk {
+
+// Steps of tape rows in flight per warp: deeper for the short rows of few node rows per lane.
+template <int R>
+__host__ __device__ constexpr int kFdRing() {
+    return R <= 1 ? 8 : (R <= 2 ? 6 : 4);
+}
+// Shared-memory bytes of one warp's ring.
+template <typename T, int R>
+__host__ __device__ constexpr int fd_ring_warp_bytes() {
+    return kFdRing<R>() * 32 * fd_tape_row<T>(R) * static_cast<int>(sizeof(T));
+}
+
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gsrc) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(smem_dst)), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
 
 template <typename T, int ORDER, int R>
 __global__ void __launch_bounds__(kFwdWarps * 32) bwd_fd_tape_kernel(BwdParams B) {
@@ -40,6 +67,10 @@ __global__ void __launch_bounds__(kFwdWarps * 32) bwd_fd_tape_kernel(BwdParams B
     char* base = static_cast<char*>(L.scratch) + slot * L.scratch_stride;
     T* rbuf = reinterpret_cast<T*>(base + B.off_rbuf);       // [col]: adjoint of lane 0's k1
     int* rexp = reinterpret_cast<int*>(base + B.off_rexp);   // [col]
+    constexpr int D = kFdRing<R>();
+    constexpr int kStepBytes = 32 * TR * static_cast<int>(sizeof(T));
+    extern __shared__ __align__(16) unsigned char fd_smem[];
+    unsigned char* ring = fd_smem + wib * fd_ring_warp_bytes<T, R>();  // [D][vector][lane]
 
     for (;;) {
         const int64_t item = next_item(L);
@@ -78,10 +109,26 @@ __global__ void __launch_bounds__(kFwdWarps * 32) bwd_fd_tape_kernel(BwdParams B
 #pragma unroll
         for (int r = 0; r < R; ++r) vbar[r] = T(0);
 
+        // this lane's vectors of steps nsteps - 1 .. nsteps - D, one commit group per step (step t
+        // in slot t % D; empty groups past step 0 keep the count uniform)
+        auto fetch = [&](int t) {
+            if (t >= 0) {
+                const V* src = reinterpret_cast<const V*>(tape + static_cast<int64_t>(t) * kStepBytes);
+                V* dst = reinterpret_cast<V*>(ring + (t % D) * kStepBytes);
+#pragma unroll
+                for (int vv = 0; vv < TR / W; ++vv) cp_async16(dst + vv * 32 + lane, src + vv * 32 + lane);
+            }
+            cp_async_commit();
+        };
+#pragma unroll
+        for (int k = 0; k < D; ++k) fetch(nsteps - 1 - k);
+
         int tt = nsteps - 1 - lane;
         int s = tt >= 0 ? tt / period : -1;
         int jj = tt >= 0 ? tt - s * period : -1;
         for (int step = nsteps - 1; step >= 0; --step) {
+            cp_async_wait<D - 1>();  // this step's group has landed (the D - 1 after it may not)
+            const V* trow = reinterpret_cast<const V*>(ring + (step % D) * kStepBytes);
             T tb = __shfl_down_sync(kFull, k1out, 1);
             int tbe = __shfl_down_sync(kFull, k1e, 1);
             const int g = (s << 5) + lane;
@@ -102,10 +149,9 @@ __global__ void __launch_bounds__(kFwdWarps * 32) bwd_fd_tape_kernel(BwdParams B
                 T v[R], k0, k1, m;
                 int ea = 0;
                 {
-                    const V* src = reinterpret_cast<const V*>(tape + static_cast<int64_t>(step) * (32 * TR * sizeof(T)));
 #pragma unroll
                     for (int vv = 0; vv < TR / W; ++vv) {
-                        const V t = __ldcs(src + vv * 32 + lane);
+                        const V t = trow[vv * 32 + lane];
                         const T* tp = reinterpret_cast<const T*>(&t);
 #pragma unroll
                         for (int q2 = 0; q2 < W; ++q2) {
@@ -236,6 +282,7 @@ __global__ void __launch_bounds__(kFwdWarps * 32) bwd_fd_tape_kernel(BwdParams B
                     mcell = T(0);
                 }
             }
+            fetch(step - D);  // into the slot this step's row came from
             __syncwarp();
             if (s >= 0 && --jj < 0) {  // down one strip
                 jj = period - 1;

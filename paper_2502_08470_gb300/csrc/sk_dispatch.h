@@ -29,6 +29,8 @@ const void* fwd_fd_kernel_ptr(int T, int order, int lam, bool coop, bool tape = 
 const void* fwd_fd_tape_ptr(int T, int order, int lam);
 const void* bwd_fd_tape_ptr(int T, int order, int lam);
 int fd_tape_row_elems(int T, int lam);
+// Shared memory of one warp of bwd_fd_tape_kernel (its ring of tape rows).
+int bwd_fd_ring_bytes(int T, int lam);
 const void* fwd_fd_coop_ptr(int T, int order, int lam);
 const void* fwd_fd_implicit_ptr(int T, int lam, bool coop);  // order 3
 const void* fwd_approx_ptr_f32(int N);
