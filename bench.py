@@ -759,6 +759,13 @@ def main():
                 oc = o.cpu().numpy()
                 samples[f"osc_{key}"] = dict(xs=list(Xo_np), ys=list(Yo_np), pa=so, pb=so, scheme=scheme, N=N,
                                              lam=lam, gpu=oc[so])
+        # gradients of the interpolation scheme (tape of cell inputs, one warp per pair: 64 warps)
+        go = torch.ones(64, dtype=torch.float64, device=dev)
+        t = timed_steps(lambda: sk.sigkernel_backward(go, Xo, Yo, io, io, scheme="interp", degree=8,
+                                                      compute="f32"), 2, 1)
+        osc["interp8_lam0_f32_fwd_bwd"] = {"ms": t, "cell_updates_per_s": cells_o / (t / 1e3),
+                                           "note": "sigkernel_backward: forward recording the tape of cell inputs "
+                                                   "(one warp per pair), the adjoint, the contraction"}
         line["oscillatory"] = osc
         del Xo, Yo
 
