@@ -555,7 +555,7 @@ def main():
                                       "backward_call_ms": statistics.mean(run.backward_call_ms),
                                       "cell_updates_per_s": cells / (statistics.mean(sa) / 1e3),
                                       "what": "forward Gram, then sigkernel_backward (forward tapes in chunks of "
-                                              "<= 48 GiB and the tape adjoint after each)"}}
+                                              "<= 64 GiB and the tape adjoint after each)"}}
         kern = sk.SigKernel("approx", DEGREE, 0, "f32")
         Xg = Xt.clone().requires_grad_(True)
         Yg = Yt.clone().requires_grad_(True)
@@ -856,7 +856,7 @@ def main():
         line["mmd2"] = {"workload": f"{nm} + {nm} paths, 513 points, d=32 (Brownian vs drift 0.5, vol 1.2), approx "
                                     "N=6, FP32, symmetric K_AA/K_BB + K_AB; M_ij from a tcgen05 GEMM per chunk of "
                                     "pairs (three BF16 parts, FP32 accumulation); gradients from forward tapes in "
-                                    "chunks of pairs (tape <= 48 GiB per chunk), dk/dM contracted on the tensor cores",
+                                    "chunks of pairs (tape <= 64 GiB per chunk), dk/dM contracted on the tensor cores",
                         "cells": cells_m, "forward_ms": t_f, "fwd_bwd_ms": t_fb,
                         "forward_cell_updates_per_s": cells_m / (t_f / 1e3),
                         "fwd_bwd_cell_updates_per_s": cells_m / (t_fb / 1e3),

@@ -217,7 +217,7 @@ int sigkernel_gram(const sk_paths* X, const sk_paths* Y, int32_t d, int32_t dtyp
  *           the existing contents (the caller zeroes it first for a plain gradient); NULL skips.
  *   grad_Y  likewise for Y.  When Y is X (same rows pointer) both accumulate into the same
  *           buffer correctly if grad_X == grad_Y.
- * Every scheme records forward tapes in chunks of pairs (at most 48 GiB each, in the workspace)
+ * Every scheme records forward tapes in chunks of pairs (at most 64 GiB each, in the workspace)
  * and runs the tape adjoint after each chunk (sigkernel_forward_tape and sigkernel_backward_tape
  * below, one chunk at a time), so the call re-runs the forward sweep once.  When the paths are so
  * long that a chunk cannot fill the GPU, SK_POLY_APPROX runs the checkpointing adjoint instead
@@ -299,7 +299,7 @@ void sigkernel_autotune_clear(void);
  *   grad_A/B  device double with A's / B's row layout, or NULL: d MMD^2 / d rows, OVERWRITTEN.
  * K_AA and K_BB are solved as symmetric Grams; the reduction runs in FP64 on the device.
  * Gradients (every scheme with an adjoint, see sigkernel_backward) run the adjoint from forward
- * tapes: each Gram block is solved in chunks of pairs whose tape is at most 48 GiB, the chunk's
+ * tapes: each Gram block is solved in chunks of pairs whose tape is at most 64 GiB, the chunk's
  * forward recording the tape and the tape adjoint following at once with the block's constant
  * weights.  A block whose paths are so long that a chunk cannot fill the GPU uses the
  * checkpointing adjoint of sigkernel_backward instead (d <= 32; approximation scheme only, else

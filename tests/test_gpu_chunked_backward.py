@@ -82,8 +82,9 @@ def test_backward_captures_into_a_cuda_graph():
 
 
 def test_mmd2_gradient_across_many_chunks_matches_the_backward_of_each_block():
-    # 120 + 120 paths of 513 points (14.7 MB of tape per pair at N = 6): with 48 GiB of tape a chunk
-    # holds 3497 pairs, so K_AA and K_BB (7260 pairs) run in 3 chunks each and K_AB (14400) in 5
+    # 120 + 120 paths of 513 points (14.7 MB of tape per pair at N = 6): 64 GiB of tape hold 4663
+    # pairs, rounded down to the adjoint's 3648 resident warps, so K_AA and K_BB (7260 pairs) run in
+    # 2 chunks each and K_AB (14400) in 4
     n = 120
     A = torch.tensor(W.brownian(n, 513, 3, seed=91), device="cuda")
     B = torch.tensor(W.brownian(n, 513, 3, seed=92, drift=0.5, vol=1.2), device="cuda")

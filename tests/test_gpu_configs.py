@@ -153,7 +153,7 @@ def test_mmd2_gradient_central_differences(mmd_batches):
 
 
 def test_mmd2_long_paths_take_the_checkpointing_adjoint():
-    """40 + 40 paths of 1025 points: one pair's tape is ~67 MB, so a 48 GiB chunk holds fewer pairs
+    """40 + 40 paths of 1025 points: one pair's tape is ~67 MB, so a 64 GiB chunk holds fewer pairs
     than half the adjoint's resident warps and each Gram block takes the checkpointing adjoint.
     Gradient entries against central differences of the FP64 GPU forward."""
     A = W.brownian(40, 1025, 2, seed=11)
