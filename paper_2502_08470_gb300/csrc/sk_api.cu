@@ -725,7 +725,8 @@ int plan_backward(const sk_paths* X, const sk_paths* Y, int32_t d, int32_t dtype
     off += static_cast<int64_t>(align256(b.cols_max * (N + 1) * esize));
     b.off_rexp = off;
     off += static_cast<int64_t>(align256(b.cols_max * 4));
-    b.off_ybar = off;
+    b.off_ybar = off;  // the pair's dk/dy column sums in T, [coarse column][dpad]
+    off += static_cast<int64_t>(align256(std::max<int64_t>(Y->max_len, 1) * p.dpad * esize));
     b.slot_bytes = off;
     int dev = 0, sms = 0, per_sm = 0;
     SK_CUDA(cudaGetDevice(&dev));

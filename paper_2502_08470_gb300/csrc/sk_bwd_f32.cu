@@ -7,29 +7,29 @@ namespace sk {
 
 const void* bwd_approx_ptr_f32(int N, int dmax, int* stack_bytes) {
     if (dmax == 8) switch (N) {
-        case 2: *stack_bytes = bwd_stack_bytes<float, 2, 8>(); return reinterpret_cast<const void*>(&bwd_approx_kernel<float, 2, 8, 8>);
-        case 3: *stack_bytes = bwd_stack_bytes<float, 3, 8>(); return reinterpret_cast<const void*>(&bwd_approx_kernel<float, 3, 8, 8>);
-        case 4: *stack_bytes = bwd_stack_bytes<float, 4, 8>(); return reinterpret_cast<const void*>(&bwd_approx_kernel<float, 4, 8, 8>);
-        case 5: *stack_bytes = bwd_stack_bytes<float, 5, 8>(); return reinterpret_cast<const void*>(&bwd_approx_kernel<float, 5, 8, 8>);
-        case 6: *stack_bytes = bwd_stack_bytes<float, 6, 8>(); return reinterpret_cast<const void*>(&bwd_approx_kernel<float, 6, 8, 8>);
-        case 7: *stack_bytes = bwd_stack_bytes<float, 7, 8>(); return reinterpret_cast<const void*>(&bwd_approx_kernel<float, 7, 8, 8>);
-        case 8: *stack_bytes = bwd_stack_bytes<float, 8, 8>(); return reinterpret_cast<const void*>(&bwd_approx_kernel<float, 8, 8, 8>);
-        case 9: *stack_bytes = bwd_stack_bytes<float, 9, 8>(); return reinterpret_cast<const void*>(&bwd_approx_kernel<float, 9, 8, 8>);
-        case 10: *stack_bytes = bwd_stack_bytes<float, 10, 8>(); return reinterpret_cast<const void*>(&bwd_approx_kernel<float, 10, 8, 8>);
-        case 12: *stack_bytes = bwd_stack_bytes<float, 12, 8>(); return reinterpret_cast<const void*>(&bwd_approx_kernel<float, 12, 8, 8>);
+        case 2: *stack_bytes = bwd_stack_bytes<float, 2, 4>(); return reinterpret_cast<const void*>(&bwd_approx_kernel<float, 2, 4, 8>);
+        case 3: *stack_bytes = bwd_stack_bytes<float, 3, 4>(); return reinterpret_cast<const void*>(&bwd_approx_kernel<float, 3, 4, 8>);
+        case 4: *stack_bytes = bwd_stack_bytes<float, 4, 4>(); return reinterpret_cast<const void*>(&bwd_approx_kernel<float, 4, 4, 8>);
+        case 5: *stack_bytes = bwd_stack_bytes<float, 5, 4>(); return reinterpret_cast<const void*>(&bwd_approx_kernel<float, 5, 4, 8>);
+        case 6: *stack_bytes = bwd_stack_bytes<float, 6, 4>(); return reinterpret_cast<const void*>(&bwd_approx_kernel<float, 6, 4, 8>);
+        case 7: *stack_bytes = bwd_stack_bytes<float, 7, 4>(); return reinterpret_cast<const void*>(&bwd_approx_kernel<float, 7, 4, 8>);
+        case 8: *stack_bytes = bwd_stack_bytes<float, 8, 4>(); return reinterpret_cast<const void*>(&bwd_approx_kernel<float, 8, 4, 8>);
+        case 9: *stack_bytes = bwd_stack_bytes<float, 9, 4>(); return reinterpret_cast<const void*>(&bwd_approx_kernel<float, 9, 4, 8>);
+        case 10: *stack_bytes = bwd_stack_bytes<float, 10, 4>(); return reinterpret_cast<const void*>(&bwd_approx_kernel<float, 10, 4, 8>);
+        case 12: *stack_bytes = bwd_stack_bytes<float, 12, 4>(); return reinterpret_cast<const void*>(&bwd_approx_kernel<float, 12, 4, 8>);
         default: break;
     }
     if (dmax == 32) switch (N) {
-        case 2: *stack_bytes = bwd_stack_bytes<float, 2, 8>(); return reinterpret_cast<const void*>(&bwd_approx_kernel<float, 2, 8, 32>);
-        case 3: *stack_bytes = bwd_stack_bytes<float, 3, 8>(); return reinterpret_cast<const void*>(&bwd_approx_kernel<float, 3, 8, 32>);
-        case 4: *stack_bytes = bwd_stack_bytes<float, 4, 8>(); return reinterpret_cast<const void*>(&bwd_approx_kernel<float, 4, 8, 32>);
-        case 5: *stack_bytes = bwd_stack_bytes<float, 5, 8>(); return reinterpret_cast<const void*>(&bwd_approx_kernel<float, 5, 8, 32>);
-        case 6: *stack_bytes = bwd_stack_bytes<float, 6, 8>(); return reinterpret_cast<const void*>(&bwd_approx_kernel<float, 6, 8, 32>);
-        case 7: *stack_bytes = bwd_stack_bytes<float, 7, 8>(); return reinterpret_cast<const void*>(&bwd_approx_kernel<float, 7, 8, 32>);
-        case 8: *stack_bytes = bwd_stack_bytes<float, 8, 8>(); return reinterpret_cast<const void*>(&bwd_approx_kernel<float, 8, 8, 32>);
-        case 9: *stack_bytes = bwd_stack_bytes<float, 9, 8>(); return reinterpret_cast<const void*>(&bwd_approx_kernel<float, 9, 8, 32>);
-        case 10: *stack_bytes = bwd_stack_bytes<float, 10, 8>(); return reinterpret_cast<const void*>(&bwd_approx_kernel<float, 10, 8, 32>);
-        case 12: *stack_bytes = bwd_stack_bytes<float, 12, 8>(); return reinterpret_cast<const void*>(&bwd_approx_kernel<float, 12, 8, 32>);
+        case 2: *stack_bytes = bwd_stack_bytes<float, 2, 4>(); return reinterpret_cast<const void*>(&bwd_approx_kernel<float, 2, 4, 32>);
+        case 3: *stack_bytes = bwd_stack_bytes<float, 3, 4>(); return reinterpret_cast<const void*>(&bwd_approx_kernel<float, 3, 4, 32>);
+        case 4: *stack_bytes = bwd_stack_bytes<float, 4, 4>(); return reinterpret_cast<const void*>(&bwd_approx_kernel<float, 4, 4, 32>);
+        case 5: *stack_bytes = bwd_stack_bytes<float, 5, 4>(); return reinterpret_cast<const void*>(&bwd_approx_kernel<float, 5, 4, 32>);
+        case 6: *stack_bytes = bwd_stack_bytes<float, 6, 4>(); return reinterpret_cast<const void*>(&bwd_approx_kernel<float, 6, 4, 32>);
+        case 7: *stack_bytes = bwd_stack_bytes<float, 7, 4>(); return reinterpret_cast<const void*>(&bwd_approx_kernel<float, 7, 4, 32>);
+        case 8: *stack_bytes = bwd_stack_bytes<float, 8, 4>(); return reinterpret_cast<const void*>(&bwd_approx_kernel<float, 8, 4, 32>);
+        case 9: *stack_bytes = bwd_stack_bytes<float, 9, 4>(); return reinterpret_cast<const void*>(&bwd_approx_kernel<float, 9, 4, 32>);
+        case 10: *stack_bytes = bwd_stack_bytes<float, 10, 4>(); return reinterpret_cast<const void*>(&bwd_approx_kernel<float, 10, 4, 32>);
+        case 12: *stack_bytes = bwd_stack_bytes<float, 12, 4>(); return reinterpret_cast<const void*>(&bwd_approx_kernel<float, 12, 4, 32>);
         default: break;
     }
     return nullptr;
@@ -61,6 +61,6 @@ const void* bwd_contract_ptr_f32(int C) {
     }
 }
 
-int bwd_segment_f32() { return 8; }
+int bwd_segment_f32() { return 4; }
 
 }  // namespace sk

@@ -428,13 +428,13 @@ __host__ __device__ constexpr int bwd_stack_bytes() {
 template <typename T>
 __host__ __device__ constexpr int bwd_xacc_bytes(int dpad) { return 32 * (dpad + 1) * static_cast<int>(sizeof(T)); }
 
-template <typename T, int N, int K>
+template <typename T, int N, int K, int DMAX>
 constexpr int bwd_min_blocks() {
-    return sizeof(T) == 8 ? 1 : 3;
+    return sizeof(T) == 8 ? 1 : (DMAX <= 8 ? 5 : 3);
 }
 
 template <typename T, int N, int K, int DMAX>
-__global__ void __launch_bounds__(kFwdWarps * 32, (bwd_min_blocks<T, N, K>()))
+__global__ void __launch_bounds__(kFwdWarps * 32, (bwd_min_blocks<T, N, K, DMAX>()))
     bwd_approx_kernel(BwdParams B) {
     constexpr bool kRescale = std::is_same<T, float>::value;
     using V = typename Vec<T>::type;
@@ -451,6 +451,7 @@ __global__ void __launch_bounds__(kFwdWarps * 32, (bwd_min_blocks<T, N, K>()))
     int* fexp = reinterpret_cast<int*>(base + B.off_fexp);      // [strip][col]
     T* rbuf = reinterpret_cast<T*>(base + B.off_rbuf);          // [col][N+1]
     int* rexp = reinterpret_cast<int*>(base + B.off_rexp);      // [col]
+    T* ybar = reinterpret_cast<T*>(base + B.off_ybar);          // [coarse col][dpad]
     const int dpad = L.dpad;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     unsigned char* wsm = smem_raw + wib * (bwd_stack_bytes<T, N, K>() + bwd_xacc_bytes<T>(dpad));
@@ -551,6 +552,10 @@ __global__ void __launch_bounds__(kFwdWarps * 32, (bwd_min_blocks<T, N, K>()))
 #pragma unroll
         for (int c = 0; c < DMAX; ++c) ysum[c] = T(0);
         for (int c = 0; c < dpad; ++c) xacc[c] = T(0);
+        // dk/dy of the pair's columns, summed over its strips in T (lane 0 adds each strip's
+        // column sum as the adjoint leaves the column) and added to the gradient once at the end
+        for (int q = lane; q < P.ly * dpad; q += 32) ybar[q] = T(0);
+        __syncwarp();
 
         for (int s = nstrips - 1; s >= 0; --s) {
             const int row = (s << 5) + lane;
@@ -779,11 +784,10 @@ __global__ void __launch_bounds__(kFwdWarps * 32, (bwd_min_blocks<T, N, K>()))
                                 if (kRescale) rexp[jj] = gbe;
                             }
                             // the column's partial dk/dy over this strip is complete
-                            double* gy = B.gincY + (P.ys + (jj >> lam)) * dpad;
+                            T* yb = ybar + static_cast<int64_t>(jj >> lam) * dpad;
 #pragma unroll
                             for (int c = 0; c < DMAX; ++c)
-                                if (c < dpad && ysum[c] != T(0))
-                                    atomicAdd(gy + c, static_cast<double>(ysum[c]) * gscale);
+                                if (c < dpad) yb[c] += ysum[c];
                         }
                         if (jj == 0) {  // the row is finished: flush dk/dx of its increment
                             double* gx = B.gincX + (P.xs + (row >> lam)) * dpad;
@@ -796,6 +800,12 @@ __global__ void __launch_bounds__(kFwdWarps * 32, (bwd_min_blocks<T, N, K>()))
                     __syncwarp();
                 }
             }
+        }
+        __syncwarp();  // lane 0's column sums are visible to the warp
+        {
+            double* gy = B.gincY + P.ys * dpad;
+            for (int q = lane; q < P.ly * dpad; q += 32)
+                if (ybar[q] != T(0)) atomicAdd(gy + q, static_cast<double>(ybar[q]) * gscale);
         }
         __syncwarp();
     }
