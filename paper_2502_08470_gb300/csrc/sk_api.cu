@@ -690,7 +690,7 @@ struct BwdPlan {
     Plan f;                    // forward plan (increments, queue, order offsets)
     const void* kern;
     int K, dmax, stack_bytes, smem_bytes;
-    int64_t cols_max, strips_max, seg_max;
+    int64_t cols_max, strips_max, strip_steps;
     int64_t off_fbuf, off_fexp, off_rbuf, off_rexp, off_ybar, slot_bytes;
     size_t off_gincx, off_gincy, off_scratch, total;
 };
@@ -713,9 +713,9 @@ int plan_backward(const sk_paths* X, const sk_paths* Y, int32_t d, int32_t dtype
     const int64_t rows_max = std::max<int64_t>(X->max_len << lam, 1);
     b.cols_max = std::max<int64_t>(Y->max_len << lam, 1);
     b.strips_max = (rows_max + 31) / 32;
-    b.seg_max = (b.cols_max + 31 + b.K - 1) / b.K;  // checkpoints of one strip
-    int64_t off = 0;
-    off += b.seg_max * (2 * N + 2) * 32 * esize + b.seg_max * 32 * 4;
+    b.strip_steps = b.cols_max + 31;  // warp steps of one strip
+    int64_t off = 0;                  // the strip tape: one tape step per warp step of a strip
+    off += b.strip_steps * 32 * static_cast<int64_t>(p.T ? tape_row<float>(N, false) * 4 : tape_row<double>(N, false) * 8);
     off = static_cast<int64_t>(align256(off));
     b.off_fbuf = off;
     off += static_cast<int64_t>(align256(std::max<int64_t>(b.strips_max - 1, 1) * b.cols_max * (N + 1) * esize));
@@ -787,7 +787,6 @@ int launch_backward(const sk_paths* X, const sk_paths* Y, int32_t d, int32_t dty
     B.gincY = gincY;
     B.cols_max = b.cols_max;
     B.strips_max = b.strips_max;
-    B.seg_max = b.seg_max;
     B.off_fbuf = b.off_fbuf;
     B.off_fexp = b.off_fexp;
     B.off_rbuf = b.off_rbuf;

@@ -45,15 +45,6 @@ __host__ __device__ constexpr int fd_ring_warp_bytes() {
     return kFdRing<R>() * 32 * fd_tape_row<T>(R) * static_cast<int>(sizeof(T));
 }
 
-__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gsrc) {
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(smem_dst)), "l"(gsrc) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() {
-    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
-}
-
 template <typename T, int ORDER, int R>
 __global__ void __launch_bounds__(kFwdWarps * 32) bwd_fd_tape_kernel(BwdParams B) {
     constexpr bool kRescale = std::is_same<T, float>::value;

@@ -13,18 +13,20 @@
 // of P_lambda has M = M_ij / 4^lambda, so dk/dM_ij sums the sub-cell Mbar / 4^lambda, and
 // d k / d dx_i = sum_j (dk/dM_ij) dy_j, d k / d dy_j = sum_i (dk/dM_ij) dx_i.
 //
-// Schedule (one warp per pair, same lane/strip layout as the forward kernel):
-//   F  forward replay of the whole pair; every strip's hand-off column goes to per-warp scratch
-//      and the exponent of k_hat is kept.
+// Schedule of the checkpointing adjoint (one warp per pair, same lane/strip layout as the forward
+// kernel; memory per warp slot: the pair's strip hand-offs and one strip's tape):
+//   F  forward replay of the whole pair; every strip's hand-off column (the checkpoints) goes to
+//      per-warp scratch and the exponent of k_hat is kept.
 //   for each 32-row strip, from the top one down:
-//   R1 re-run the strip's forward from its hand-off column, storing every K steps each lane's
-//      cell inputs (an antidiagonal checkpoint) in a per-warp buffer small enough for L2;
-//   R2 for each K-step segment from the last to the first: re-run its K forward steps from the
-//      checkpoint into a shared-memory stack, then walk them backward applying the adjoint.  The
-//      right-edge adjoint moves one lane down per step (__shfl_down_sync) together with the column
-//      partial sums of dk/dy (lane 0 adds them to the y gradient with atomics), lane 0 hands the
-//      adjoint to lane 31 of the strip below through a per-warp buffer, and each lane keeps dk/dx
-//      of its row in shared memory.
+//   R1 re-run the strip's forward from its hand-off column, recording each cell's output
+//      derivatives with respect to M, exponent and M (the forward tape's rows) in a per-warp
+//      strip tape;
+//   R2 walk the strip's steps backward from that tape (each lane copies its rows into a
+//      shared-memory ring K steps ahead) applying the adjoint.  The right-edge adjoint moves one
+//      lane down per step (__shfl_down_sync) together with the column partial sums of dk/dy
+//      (lane 0 adds them into a per-warp row of the pair's columns, added to the y gradient once
+//      per pair), lane 0 hands the adjoint to lane 31 of the strip below through a per-warp
+//      buffer, and each lane keeps dk/dx of its row in shared memory.
 // FP32 keeps power-of-two exponents per lane for the forward values (as in the forward kernel)
 // and, separately, for the adjoints; dk/dM is accumulated relative to 2^E(k) of the pair.
 #pragma once
@@ -46,7 +48,6 @@ struct BwdParams {
     double* gincY;            // same for Y (may alias gincX)
     int64_t cols_max;         // refined columns a hand-off buffer holds
     int64_t strips_max;       // strips of the longest x path
-    int64_t seg_max;          // K-step segments of the longest pair
     int64_t off_fbuf, off_fexp, off_rbuf, off_rexp, off_ybar;  // byte offsets inside a warp slot
     void* mbuf;               // tape adjoint: per-item dk/dM, [step][lane] of T (or tiles, gtile)
     int64_t mb_stride;        // bytes per item of mbuf
@@ -123,16 +124,9 @@ __device__ __forceinline__ void align_inputs(T (&a)[N + 1], int& ea, T (&b)[N + 
     }
 }
 
-// One forward cell of the approximation scheme with the forward kernel's renormalisation:
-// (a, b) -> (a, bo) in place, exponent ea.
+// The replays' renormalisation of a cell's outputs (a, bo) by 2^-+64 into exponent ea (FP32).
 template <typename T, int N>
-__device__ __forceinline__ void fwd_cell(T (&a)[N + 1], const T (&b)[N + 1], T M, float tau, T (&bo)[N + 1],
-                                         int& ea) {
-    T e[N + 1], ct[N + 1], cr[N + 1];
-    build_exp_series<T, N>(M, tau, e);
-    cell_series<T, N, N, false>(a, b, e, ct, cr);
-#pragma unroll
-    for (int n = 0; n <= N; ++n) { a[n] = ct[n]; bo[n] = cr[n]; }
+__device__ __forceinline__ void rescale_edges(T (&a)[N + 1], T (&bo)[N + 1], int& ea) {
     if constexpr (std::is_same<T, float>::value) {
         const float mag = fmaxf(fabsf(a[0]), fabsf(bo[0]));
         if (mag > 0x1p64f) {
@@ -150,6 +144,19 @@ __device__ __forceinline__ void fwd_cell(T (&a)[N + 1], const T (&b)[N + 1], T M
             }
         }
     }
+}
+
+// One forward cell of the approximation scheme with the replays' renormalisation:
+// (a, b) -> (a, bo) in place, exponent ea.
+template <typename T, int N>
+__device__ __forceinline__ void fwd_cell(T (&a)[N + 1], const T (&b)[N + 1], T M, float tau, T (&bo)[N + 1],
+                                         int& ea) {
+    T e[N + 1], ct[N + 1], cr[N + 1];
+    build_exp_series<T, N>(M, tau, e);
+    cell_series<T, N, N, false>(a, b, e, ct, cr);
+#pragma unroll
+    for (int n = 0; n <= N; ++n) { a[n] = ct[n]; bo[n] = cr[n]; }
+    rescale_edges<T, N>(a, bo, ea);
 }
 
 // Scale a cell's forward inputs to magnitude ~1 by an exact power of two (FP32), folding the shift
@@ -418,12 +425,12 @@ __device__ __forceinline__ void project_transpose(const T (&g)[N + 1], T (&c)[NE
     }
 }
 
-// Shared memory of one warp: the K-step stack (a[N+1], b[N+1], M per lane, plus exponents),
-// then each lane's dk/dx accumulator of its row ([32][dpad + 1]; the odd stride puts the lanes'
-// scalar accesses in distinct banks).
+// Shared memory of one warp: a ring of K steps of the strip tape (each lane copies its own row
+// of a step ahead of the reverse walk), then each lane's dk/dx accumulator of its row
+// ([32][dpad + 1]; the odd stride puts the lanes' scalar accesses in distinct banks).
 template <typename T, int N, int K>
 __host__ __device__ constexpr int bwd_stack_bytes() {
-    return K * (2 * N + 3) * 32 * static_cast<int>(sizeof(T)) + K * 32 * 4;
+    return K * fwd_tape_step_bytes<T, N, false>();
 }
 template <typename T>
 __host__ __device__ constexpr int bwd_xacc_bytes(int dpad) { return 32 * (dpad + 1) * static_cast<int>(sizeof(T)); }
@@ -444,9 +451,11 @@ __global__ void __launch_bounds__(kFwdWarps * 32, (bwd_min_blocks<T, N, K, DMAX>
     const int wib = threadIdx.x >> 5;
     const int64_t slot = static_cast<int64_t>(blockIdx.x) * (blockDim.x >> 5) + wib;
     char* base = static_cast<char*>(L.scratch) + slot * L.scratch_stride;
-    // strip checkpoints: [seg][2N+2][32] T then [seg][32] int
-    T* ckpt = reinterpret_cast<T*>(base);
-    int* ckpt_e = reinterpret_cast<int*>(ckpt + B.seg_max * (2 * N + 2) * 32);
+    // the strip tape: per step of the current strip, the 32 lanes' rows of output derivatives,
+    // exponent and M (the layout of the forward tape, store_dm_row)
+    char* stape = base;
+    constexpr int kStep = fwd_tape_step_bytes<T, N, false>();
+    constexpr int TR = tape_row<T>(N, false);
     T* fbuf = reinterpret_cast<T*>(base + B.off_fbuf);          // [strip][col][N+1]
     int* fexp = reinterpret_cast<int*>(base + B.off_fexp);      // [strip][col]
     T* rbuf = reinterpret_cast<T*>(base + B.off_rbuf);          // [col][N+1]
@@ -455,8 +464,7 @@ __global__ void __launch_bounds__(kFwdWarps * 32, (bwd_min_blocks<T, N, K, DMAX>
     const int dpad = L.dpad;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     unsigned char* wsm = smem_raw + wib * (bwd_stack_bytes<T, N, K>() + bwd_xacc_bytes<T>(dpad));
-    T* stk = reinterpret_cast<T*>(wsm);
-    int* stk_e = reinterpret_cast<int*>(stk + K * (2 * N + 3) * 32);
+    unsigned char* ring = wsm;  // K slots of kStep bytes: step t of the strip in slot t % K
     T* xacc = reinterpret_cast<T*>(wsm + bwd_stack_bytes<T, N, K>()) + lane * (dpad + 1);
     const T* __restrict__ incX = static_cast<const T*>(L.X.inc);
     const T* __restrict__ incY = static_cast<const T*>(L.Y.inc);
@@ -560,9 +568,10 @@ __global__ void __launch_bounds__(kFwdWarps * 32, (bwd_min_blocks<T, N, K, DMAX>
         for (int s = nstrips - 1; s >= 0; --s) {
             const int row = (s << 5) + lane;
             const int ts = (s == nstrips - 1 ? last_lane : 31) + cols;  // steps of this strip
-            const int nseg = (ts + K - 1) / K;
             const T* xrow = xbase + static_cast<int64_t>(min(row, rows - 1) >> lam) * dpad;
             // -------------------------------------------------------------- R1
+            // the strip's forward from its hand-off column, each active cell's row of output
+            // derivatives, exponent and M to the strip tape
             {
                 T a[N + 1], bo[N + 1];
 #pragma unroll
@@ -592,213 +601,181 @@ __global__ void __launch_bounds__(kFwdWarps * 32, (bwd_min_blocks<T, N, K, DMAX>
                             ea = 0;
                         }
                         if (kRescale) align_inputs<T, N>(a, ea, b, eb);
-                    }
-                    if (tt % K == 0) {  // antidiagonal checkpoint: this step's cell inputs
-                        T* cp = ckpt + static_cast<int64_t>(tt / K) * (2 * N + 2) * 32;
-#pragma unroll
-                        for (int n = 0; n <= N; ++n) {
-                            cp[n * 32 + lane] = a[n];
-                            cp[(N + 1 + n) * 32 + lane] = b[n];
-                        }
-                        ckpt_e[static_cast<int64_t>(tt / K) * 32 + lane] = ea;
-                    }
-                    if (active) {
                         const T M = row_dot<T>(xrow, ybase + static_cast<int64_t>(jj >> lam) * dpad, L.nvec) * sub;
-                        fwd_cell<T, N>(a, b, M, L.tau, bo, ea);
+                        T e[N + 1], ct[N + 1], cr[N + 1], da[N], db[N];
+                        build_exp_series<T, N>(M, L.tau, e);
+                        cell_series_dm<T, N>(a, b, e, ct, cr, da, db);  // ct, cr: fwd_cell's outputs
+                        store_dm_row<T, N>(stape, tt, lane, da, db, ea, M);
+#pragma unroll
+                        for (int n = 0; n <= N; ++n) { a[n] = ct[n]; bo[n] = cr[n]; }
+                        rescale_edges<T, N>(a, bo, ea);
                         eo = ea;
                     }
                 }
             }
             __syncwarp();
+            __threadfence_block();  // each lane's stores of its rows before its copies of them
             // -------------------------------------------------------------- R2
-            for (int g = nseg - 1; g >= 0; --g) {
-                const int t0 = g * K;
-                const int tn = min(K, ts - t0);
-                {   // re-run the segment's forward steps into the stack
-                    const T* cp = ckpt + static_cast<int64_t>(g) * (2 * N + 2) * 32;
-                    T ra[N + 1], rb[N + 1], rbo[N + 1];
+            // the strip's steps backward; each lane copies its own row of step t into ring slot
+            // t % K, K steps ahead of its use (one commit group per step, empty past step 0)
+            auto fetch = [&](int t) {
+                if (t >= 0) {
+                    const char* src = stape + static_cast<int64_t>(t) * kStep;
+                    unsigned char* dst = ring + (t % K) * kStep;
 #pragma unroll
-                    for (int n = 0; n <= N; ++n) {
-                        ra[n] = cp[n * 32 + lane];
-                        rb[n] = cp[(N + 1 + n) * 32 + lane];
-                        rbo[n] = T(0);
-                    }
-                    int rea = ckpt_e[static_cast<int64_t>(g) * 32 + lane], reo = 0;
+                    for (int v = 0; v < TR / W; ++v) cp_async16(dst + (v * 32 + lane) * 16, src + (v * 32 + lane) * 16);
+                    if constexpr (TR % W != 0)
+                        cp_async8(dst + (TR / W) * 512 + lane * 8, src + (TR / W) * 512 + lane * 8);
+                }
+                cp_async_commit();
+            };
+#pragma unroll
+            for (int k = 0; k < K; ++k) fetch(ts - 1 - k);
 #pragma unroll 1
-                    for (int k = 0; k < tn; ++k) {
-                        const int jj = t0 + k - lane;
-                        const bool active = jj >= 0 && jj < cols && row < rows;
-                        if (k > 0) {
-                            int eb = kRescale ? __shfl_up_sync(kFull, reo, 1) : 0;
+            for (int tt = ts - 1; tt >= 0; --tt) {
+                cp_async_wait<K - 1>();  // step tt's group has landed
+                T da[N], db[N], M = T(0);
+                int ef = 0;
+                {
+                    const unsigned char* r = ring + (tt % K) * kStep;
+                    auto put = [&](int q, T x) {
+                        if (q < N) da[q] = x;
+                        else if (q < 2 * N) db[q - N] = x;
+                        else if (q == 2 * N) ef = exponent_from<T>(x);
+                        else M = x;
+                    };
 #pragma unroll
-                            for (int n = 0; n <= N; ++n) rb[n] = __shfl_up_sync(kFull, rbo[n], 1);
-                            if (active) {
-                                if (lane == 0) {
-                                    if (s == 0) {
-                                        set_unit<T, N>(rb);
-                                        eb = 0;
-                                    } else {
-                                        const T* src = fbuf + (static_cast<int64_t>(s - 1) * B.cols_max + jj) * (N + 1);
+                    for (int v = 0; v < TR / W; ++v) {
+                        const V t = reinterpret_cast<const V*>(r)[v * 32 + lane];
+                        const T* tp = reinterpret_cast<const T*>(&t);
 #pragma unroll
-                                        for (int n = 0; n <= N; ++n) rb[n] = src[n];
-                                        if (kRescale) eb = fexp[static_cast<int64_t>(s - 1) * B.cols_max + jj];
-                                    }
-                                }
-                                if (jj == 0) {
-                                    set_unit<T, N>(ra);
-                                    rea = 0;
-                                }
-                                if (kRescale) align_inputs<T, N>(ra, rea, rb, eb);
-                            }
-                        }
-                        T M = T(0);
-                        if (active)
-                            M = row_dot<T>(xrow, ybase + static_cast<int64_t>(jj >> lam) * dpad, L.nvec) * sub;
-                        T* sk_ = stk + k * (2 * N + 3) * 32;
+                        for (int w = 0; w < W; ++w) put(v * W + w, tp[w]);
+                    }
+                    if constexpr (TR % W != 0) {
+                        const float2 t = reinterpret_cast<const float2*>(r + (TR / W) * 512)[lane];
+                        put((TR / W) * W, t.x);
+                        put((TR / W) * W + 1, t.y);
+                    }
+                }
+                const int jj = tt - lane;
+                const bool active = jj >= 0 && jj < cols && row < rows;
+                T gb_in[N + 1];
+#pragma unroll
+                for (int n = 0; n <= N; ++n) gb_in[n] = __shfl_down_sync(kFull, gbo[n], 1);
+                int gbe_in = __shfl_down_sync(kFull, gbe, 1);
+#pragma unroll
+                for (int c = 0; c < DMAX; ++c) ysum[c] = __shfl_down_sync(kFull, ysum[c], 1);
+                if (active) {
+                    if (row == rows - 1) {             // no row above: the top edge is final
+#pragma unroll
+                        for (int n = 0; n <= N; ++n) gb_in[n] = T(0);
+                        gbe_in = kZeroExp;
+                    } else if (lane == 31) {           // from lane 0 of the strip above
+                        const T* src = rbuf + static_cast<int64_t>(jj) * (N + 1);
+#pragma unroll
+                        for (int n = 0; n <= N; ++n) gb_in[n] = src[n];
+                        gbe_in = kRescale ? rexp[jj] : 0;
+                    }
+                    if (row == rows - 1 || lane == 31) {
+#pragma unroll
+                        for (int c = 0; c < DMAX; ++c) ysum[c] = T(0);
+                    }
+                    T ga_in[N + 1];
+                    int gae_in = gea;
+#pragma unroll
+                    for (int n = 0; n <= N; ++n) ga_in[n] = gra[n];
+                    if (jj == cols - 1) {              // right edge of the grid
+#pragma unroll
+                        for (int n = 0; n <= N; ++n) ga_in[n] = T(0);
+                        gae_in = kZeroExp;
+                    }
+                    if (row == rows - 1 && jj == cols - 1) {  // seed from the endpoint average
 #pragma unroll
                         for (int n = 0; n <= N; ++n) {
-                            sk_[n * 32 + lane] = ra[n];
-                            sk_[(N + 1 + n) * 32 + lane] = rb[n];
+                            ga_in[n] = static_cast<T>(0.5 * cx_rfact(n));
+                            gb_in[n] = ga_in[n];
                         }
-                        sk_[(2 * N + 2) * 32 + lane] = M;
-                        stk_e[k * 32 + lane] = rea;
-                        if (active) {
-                            fwd_cell<T, N>(ra, rb, M, L.tau, rbo, rea);
-                            reo = rea;
+                        gae_in = 0;
+                        gbe_in = 0;
+                    }
+                    int eg = 0;
+                    if (kRescale) {
+                        eg = max(gae_in, gbe_in);
+                        if (gae_in != eg) {
+                            const T f = pow2c<T>(gae_in - eg);
+#pragma unroll
+                            for (int n = 0; n <= N; ++n) ga_in[n] *= f;
+                        }
+                        if (gbe_in != eg) {
+                            const T f = pow2c<T>(gbe_in - eg);
+#pragma unroll
+                            for (int n = 0; n <= N; ++n) gb_in[n] *= f;
+                        }
+                    }
+                    unit_scale_dm<T, N>(da, db, ef);
+                    T e[N + 1];
+                    build_exp_series<T, N>(M, L.tau, e);
+                    T mbar;
+                    cell_adjoint_dm<T, N>(da, db, e, ga_in, gb_in, gra, gbo, mbar);
+                    // dk/dM of the coarse cell, relative to 2^ek
+                    const T mrel = mbar * pow2c<T>(eg + ef - ek - 2 * lam);
+                    {
+                        const V* yv = reinterpret_cast<const V*>(ybase + static_cast<int64_t>(jj >> lam) * dpad);
+                        const V* xv = reinterpret_cast<const V*>(xrow);
+#pragma unroll
+                        for (int c4 = 0; c4 < DMAX / W; ++c4) {
+                            if (c4 * W < dpad) {
+                                const V yy = __ldg(yv + c4);
+                                const V xx = __ldg(xv + c4);
+                                const T* yp = reinterpret_cast<const T*>(&yy);
+                                const T* xp = reinterpret_cast<const T*>(&xx);
+#pragma unroll
+                                for (int w = 0; w < W; ++w) {
+                                    xacc[c4 * W + w] = fma(mrel, yp[w], xacc[c4 * W + w]);
+                                    ysum[c4 * W + w] = fma(mrel, xp[w], ysum[c4 * W + w]);
+                                }
+                            }
+                        }
+                    }
+                    gea = eg;
+                    if (kRescale) {
+                        float mag = 0.f;
+#pragma unroll
+                        for (int n = 0; n <= N; ++n)
+                            mag = fmaxf(mag, fmaxf(fabsf(static_cast<float>(gra[n])), fabsf(static_cast<float>(gbo[n]))));
+                        if (mag == 0.f) {
+                            gea = kZeroExp;
+                        } else if (mag > 0x1p64f || mag < 0x1p-64f) {
+                            const int sh = mag > 0x1p64f ? -64 : 64;
+#pragma unroll
+                            for (int n = 0; n <= N; ++n) { gra[n] *= pow2t<T>(sh); gbo[n] *= pow2t<T>(sh); }
+                            gea -= sh;
+                        }
+                    }
+                    gbe = gea;
+                    if (lane == 0) {
+                        if (s > 0) {  // hand the left-edge adjoint to lane 31 of the strip below
+                            T* dst = rbuf + static_cast<int64_t>(jj) * (N + 1);
+#pragma unroll
+                            for (int n = 0; n <= N; ++n) dst[n] = gbo[n];
+                            if (kRescale) rexp[jj] = gbe;
+                        }
+                        // the column's partial dk/dy over this strip is complete
+                        T* yb = ybar + static_cast<int64_t>(jj >> lam) * dpad;
+#pragma unroll
+                        for (int c = 0; c < DMAX; ++c)
+                            if (c < dpad) yb[c] += ysum[c];
+                    }
+                    if (jj == 0) {  // the row is finished: flush dk/dx of its increment
+                        double* gx = B.gincX + (P.xs + (row >> lam)) * dpad;
+                        for (int c = 0; c < dpad; ++c) {
+                            if (xacc[c] != T(0)) atomicAdd(gx + c, static_cast<double>(xacc[c]) * gscale);
+                            xacc[c] = T(0);
                         }
                     }
                 }
+                fetch(tt - K);  // into the slot this step's row came from
                 __syncwarp();
-                // walk the segment backward
-#pragma unroll 1
-                for (int k = tn - 1; k >= 0; --k) {
-                    const int jj = t0 + k - lane;
-                    const bool active = jj >= 0 && jj < cols && row < rows;
-                    T gb_in[N + 1];
-#pragma unroll
-                    for (int n = 0; n <= N; ++n) gb_in[n] = __shfl_down_sync(kFull, gbo[n], 1);
-                    int gbe_in = __shfl_down_sync(kFull, gbe, 1);
-#pragma unroll
-                    for (int c = 0; c < DMAX; ++c) ysum[c] = __shfl_down_sync(kFull, ysum[c], 1);
-                    if (active) {
-                        if (row == rows - 1) {             // no row above: the top edge is final
-#pragma unroll
-                            for (int n = 0; n <= N; ++n) gb_in[n] = T(0);
-                            gbe_in = kZeroExp;
-                        } else if (lane == 31) {           // from lane 0 of the strip above
-                            const T* src = rbuf + static_cast<int64_t>(jj) * (N + 1);
-#pragma unroll
-                            for (int n = 0; n <= N; ++n) gb_in[n] = src[n];
-                            gbe_in = kRescale ? rexp[jj] : 0;
-                        }
-                        if (row == rows - 1 || lane == 31) {
-#pragma unroll
-                            for (int c = 0; c < DMAX; ++c) ysum[c] = T(0);
-                        }
-                        T ga_in[N + 1];
-                        int gae_in = gea;
-#pragma unroll
-                        for (int n = 0; n <= N; ++n) ga_in[n] = gra[n];
-                        if (jj == cols - 1) {              // right edge of the grid
-#pragma unroll
-                            for (int n = 0; n <= N; ++n) ga_in[n] = T(0);
-                            gae_in = kZeroExp;
-                        }
-                        if (row == rows - 1 && jj == cols - 1) {  // seed from the endpoint average
-#pragma unroll
-                            for (int n = 0; n <= N; ++n) {
-                                ga_in[n] = static_cast<T>(0.5 * cx_rfact(n));
-                                gb_in[n] = ga_in[n];
-                            }
-                            gae_in = 0;
-                            gbe_in = 0;
-                        }
-                        int eg = 0;
-                        if (kRescale) {
-                            eg = max(gae_in, gbe_in);
-                            if (gae_in != eg) {
-                                const T f = pow2c<T>(gae_in - eg);
-#pragma unroll
-                                for (int n = 0; n <= N; ++n) ga_in[n] *= f;
-                            }
-                            if (gbe_in != eg) {
-                                const T f = pow2c<T>(gbe_in - eg);
-#pragma unroll
-                                for (int n = 0; n <= N; ++n) gb_in[n] *= f;
-                            }
-                        }
-                        const T* sk_ = stk + k * (2 * N + 3) * 32;
-                        T fa[N + 1], fb[N + 1], e[N + 1];
-#pragma unroll
-                        for (int n = 0; n <= N; ++n) {
-                            fa[n] = sk_[n * 32 + lane];
-                            fb[n] = sk_[(N + 1 + n) * 32 + lane];
-                        }
-                        const T M = sk_[(2 * N + 2) * 32 + lane];
-                        int ef = stk_e[k * 32 + lane];
-                        unit_scale<T, N>(fa, fb, ef);
-                        build_exp_series<T, N>(M, L.tau, e);
-                        T mbar;
-                        cell_adjoint<T, N>(fa, fb, e, ga_in, gb_in, gra, gbo, mbar);
-                        // dk/dM of the coarse cell, relative to 2^ek
-                        const T mrel = mbar * pow2c<T>(eg + ef - ek - 2 * lam);
-                        {
-                            const V* yv = reinterpret_cast<const V*>(ybase + static_cast<int64_t>(jj >> lam) * dpad);
-                            const V* xv = reinterpret_cast<const V*>(xrow);
-#pragma unroll
-                            for (int c4 = 0; c4 < DMAX / W; ++c4) {
-                                if (c4 * W < dpad) {
-                                    const V yy = __ldg(yv + c4);
-                                    const V xx = __ldg(xv + c4);
-                                    const T* yp = reinterpret_cast<const T*>(&yy);
-                                    const T* xp = reinterpret_cast<const T*>(&xx);
-#pragma unroll
-                                    for (int w = 0; w < W; ++w) {
-                                        xacc[c4 * W + w] = fma(mrel, yp[w], xacc[c4 * W + w]);
-                                        ysum[c4 * W + w] = fma(mrel, xp[w], ysum[c4 * W + w]);
-                                    }
-                                }
-                            }
-                        }
-                        gea = eg;
-                        if (kRescale) {
-                            float mag = 0.f;
-#pragma unroll
-                            for (int n = 0; n <= N; ++n)
-                                mag = fmaxf(mag, fmaxf(fabsf(static_cast<float>(gra[n])), fabsf(static_cast<float>(gbo[n]))));
-                            if (mag == 0.f) {
-                                gea = kZeroExp;
-                            } else if (mag > 0x1p64f || mag < 0x1p-64f) {
-                                const int sh = mag > 0x1p64f ? -64 : 64;
-#pragma unroll
-                                for (int n = 0; n <= N; ++n) { gra[n] *= pow2t<T>(sh); gbo[n] *= pow2t<T>(sh); }
-                                gea -= sh;
-                            }
-                        }
-                        gbe = gea;
-                        if (lane == 0) {
-                            if (s > 0) {  // hand the left-edge adjoint to lane 31 of the strip below
-                                T* dst = rbuf + static_cast<int64_t>(jj) * (N + 1);
-#pragma unroll
-                                for (int n = 0; n <= N; ++n) dst[n] = gbo[n];
-                                if (kRescale) rexp[jj] = gbe;
-                            }
-                            // the column's partial dk/dy over this strip is complete
-                            T* yb = ybar + static_cast<int64_t>(jj >> lam) * dpad;
-#pragma unroll
-                            for (int c = 0; c < DMAX; ++c)
-                                if (c < dpad) yb[c] += ysum[c];
-                        }
-                        if (jj == 0) {  // the row is finished: flush dk/dx of its increment
-                            double* gx = B.gincX + (P.xs + (row >> lam)) * dpad;
-                            for (int c = 0; c < dpad; ++c) {
-                                if (xacc[c] != T(0)) atomicAdd(gx + c, static_cast<double>(xacc[c]) * gscale);
-                                xacc[c] = T(0);
-                            }
-                        }
-                    }
-                    __syncwarp();
-                }
             }
         }
         __syncwarp();  // lane 0's column sums are visible to the warp

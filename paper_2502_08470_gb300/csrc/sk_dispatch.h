@@ -83,7 +83,7 @@ namespace sk {
 // writes the per-warp shared-memory stack size.  NULL when no kernel exists.
 const void* bwd_approx_ptr_f32(int N, int dmax, int* stack_bytes);
 const void* bwd_approx_ptr_f64(int N, int dmax, int* stack_bytes);
-int bwd_segment_f32();  // antidiagonal checkpoint interval K
+int bwd_segment_f32();  // steps of the checkpointing adjoint's strip tape held in its shared-memory ring
 int bwd_segment_f64();
 }  // namespace sk
 
