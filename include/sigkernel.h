@@ -221,8 +221,9 @@ int sigkernel_gram(const sk_paths* X, const sk_paths* Y, int32_t d, int32_t dtyp
  * and runs the tape adjoint after each chunk (sigkernel_forward_tape and sigkernel_backward_tape
  * below, one chunk at a time), so the call re-runs the forward sweep once.  When the paths are so
  * long that a chunk cannot fill the GPU, SK_POLY_APPROX runs the checkpointing adjoint instead
- * (antidiagonal checkpoints every few steps, the forward cells replayed from them; d <= 32) and
- * the other schemes, which have none, return SK_ERR_UNSUPPORTED.  SK_FLAG_CHECKPOINT asks for the
+ * (the strip hand-offs as checkpoints, one strip's tape re-recorded from them at a time;
+ * d <= 32) and the other schemes, which have none, return SK_ERR_UNSUPPORTED.
+ * SK_FLAG_CHECKPOINT asks for the
  * checkpointing adjoint of SK_POLY_APPROX outright.  Orders with an adjoint: 2..10 and 12
  * (approximation), 2..12 (interpolation); the FD schemes for dyadic orders 0..4.
  * Accumulation uses device atomics, so the last bits of the gradient can vary between runs.
