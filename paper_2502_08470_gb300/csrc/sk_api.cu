@@ -171,7 +171,7 @@ struct Plan {
     bool mtile;          // tiled M (wide increments, polynomial schemes)
     int64_t mtile_cols;  // columns of one warp's M strip buffer
     int64_t mtile_off;   // byte offset of that buffer in a warp slot
-    // tensor-core M (FP32 approximation scheme, 8 < d <= 32, one warp per pair): the forward is
+    // tensor-core M (FP32 approximation scheme, 4 < d <= 32, one warp per pair): the forward is
     // swept in chunks of mx_chunk items, each preceded by the M kernel writing the chunk's M
     bool mx;
     int kp;              // padded coordinates of the M operand tiles (16 or 32)
@@ -244,7 +244,8 @@ int plan_forward(const sk_paths* X, const sk_paths* Y, int32_t d, int32_t dtype,
     if ((rc = check_paths(X, "X", d)) != SK_OK) return rc;
     if ((rc = check_paths(Y, "Y", d)) != SK_OK) return rc;
     const int lam = o->dyadic;
-    if ((X->max_len << lam) > kMaxRefined || (Y->max_len << lam) > kMaxRefined)
+    // (max_len << lam) > kMaxRefined, written so that no shift can overflow for any max_len
+    if (X->max_len > (kMaxRefined >> lam) || Y->max_len > (kMaxRefined >> lam))
         return fail(SK_ERR_UNSUPPORTED, "max_len << dyadic exceeds %d", kMaxRefined);
     if (mode == kGramUpper) {
         if (X->rows != Y->rows || X->offsets != Y->offsets || X->count != Y->count)

@@ -85,6 +85,24 @@ def test_version_and_host_side_validation(lib):
     assert rc == -1
 
 
+def test_path_lengths_beyond_the_refined_bound_are_refused(lib):
+    """(max_len << dyadic) above the bound is refused before any device call, also for a max_len
+    so large that the shift itself would overflow."""
+    from paper_2502_08470_gb300 import sigkernel as sk
+    lib.sigkernel_workspace_size.restype = ctypes.c_int
+    lib.sigkernel_last_error.restype = ctypes.c_char_p
+    n = ctypes.c_size_t(1)
+    ok = sk._Paths(0, 0, 0, 10, 0)
+    for max_len, lam in ((131073, 0), (65537, 1), (513, 8), (1 << 62, 8), ((1 << 63) - 1, 1)):
+        big = sk._Paths(0, 0, 0, max_len, 0)
+        opt = sk._options("approx", 6, dyadic=lam)
+        for X, Y in ((big, ok), (ok, big)):
+            rc = lib.sigkernel_workspace_size(sk.OP_PAIRS, ctypes.byref(X), ctypes.byref(Y), 2, ctypes.c_int64(1),
+                                              ctypes.byref(opt), ctypes.byref(n))
+            assert rc == -2 and n.value == 0
+            assert b"max_len" in lib.sigkernel_last_error()
+
+
 def _header_constants():
     text = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
     return {k: int(v) for k, v in re.findall(r"\b(SK_[A-Z0-9_]+)\s*=\s*(-?\d+)", text)}
