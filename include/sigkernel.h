@@ -133,9 +133,10 @@ enum {
                                        ((ceil(rows / 128) + ceil(cols / 128)) x (16 or 32) <=
                                        256; flag set: on the FMA pipe).  The M kernel splits each
                                        FP32 increment into three BF16 parts and keeps six of the
-                                       nine part products (about 2^-22 relative per product);
-                                       the contraction splits dk/dM and the increments into two
-                                       parts and keeps three products (about 2^-16); both
+                                       nine part products (at most about 2^-23 relative per
+                                       product); the contraction splits dk/dM and the increments
+                                       into two parts and keeps three products (at most about
+                                       3 x 2^-16); both
                                        accumulate in FP32 */
 };
 

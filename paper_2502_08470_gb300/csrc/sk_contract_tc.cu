@@ -7,7 +7,8 @@
 // of 8 x 8 core matrices (gtile_index), which the tensor core reads as the K-major operand of D1
 // and as the M-major (transposed) operand of D2 without any reshuffling; the increments come
 // transposed and split the same way (tc_operand_offset), one 128-row block per operand tile.  Each
-// product is hi*hi + hi*lo + lo*hi (relative error about 2^-17 per product), accumulated in FP32
+// product is hi*hi + hi*lo + lo*hi (relative error at most about 3 x 2^-16 per product: the
+// rounding of each lo and the dropped lo*lo, each up to 2^-16), accumulated in FP32
 // in tensor memory, and the sums go to the FP64 gradients with gbar 2^ek, as in the FMA
 // contraction (bwd_contract_kernel).
 //

@@ -3,12 +3,13 @@
 //
 // For a pair (a, b) the cells' M is the product of the pair's increment rows, DX_a (rows x d) times
 // DY_b^T (d x cols), with refined row i using increment i >> lambda.  Each FP32 increment is split
-// into three BF16 parts, x = h + m + l + e with h = bf16(x), m = bf16(x - h), l = bf16(x - h - m)
-// (both differences exact) and |e| <= 2^-24 |x|, and each 128 x 128 tile of M accumulates, in FP32
-// in tensor memory, the six products whose parts carry at least 2^-16 of the value, smallest first:
-// mm', hl', lh', hm', mh', hh'.  The dropped ml', lm', ll' and the split's remainder leave about
-// 2^-22 relative per product, the order of the FP32 inner product's own rounding (a two-part split
-// left about 2^-16, which moved Gram entries by 1e-4 relative).  The operand tiles are prepared
+// into three BF16 parts, x = h + m + l with h = bf16(x), m = bf16(x - h), l = bf16(x - h - m): both
+// differences are exact in FP32 and the last has at most 8 significant bits, so the split is exact
+// for |x| >= 2^-110.  Each 128 x 128 tile of M accumulates, in FP32 in tensor memory, the six
+// products whose parts carry at least 2^-16 of the value, smallest first: mm', hl', lh', hm', mh',
+// hh'.  The dropped ml', lm', ll' are at most 2 x 2^-24 + 2^-32 (about 2^-23) of each product, the
+// order of the FP32 inner product's own rounding (a two-part split left about 2^-16, which moved
+// Gram entries by 1e-4 relative).  The operand tiles are prepared
 // once per call: per path and 128-row block, the h, m and l planes of 128 rows x KP coordinates
 // (KP = d rounded up to 16 or 32, zero padded) in K-major 8 x 8 core matrices.
 //

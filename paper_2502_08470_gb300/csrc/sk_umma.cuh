@@ -115,7 +115,8 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
 __device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
 // BF16 split of an FP32 value: hi = bf16(x), lo = bf16(x - hi); hi*y_hi + hi*y_lo + lo*y_hi
-// reproduces x*y to about 2^-17 relative (the dropped lo*lo term and the rounding of lo).
+// reproduces x*y to within about 3 x 2^-16 relative: BF16 keeps 8 significant bits, so the
+// rounding of each lo and the dropped lo*lo term are each up to 2^-16 of the product.
 __device__ __forceinline__ void split_bf16(float x, __nv_bfloat16& hi, __nv_bfloat16& lo) {
     hi = __float2bfloat16_rn(x);
     lo = __float2bfloat16_rn(x - __bfloat162float(hi));
