@@ -154,10 +154,18 @@ def as_paths(x) -> Paths:
 
 
 def _cpaths(p: Paths) -> _Paths:
+    # the library reads rows as [R][d] and offsets as [B + 1] from their first elements
+    if p.rows.dim() != 2 or p.offsets.dim() != 1:
+        raise ValueError("path rows must be [R, d] and offsets [B + 1]")
+    if not p.rows.is_contiguous() or not p.offsets.is_contiguous():
+        raise ValueError("path rows and offsets must be contiguous")
     if not p.rows.is_cuda or not p.offsets.is_cuda:
         raise ValueError("path rows and offsets must be CUDA tensors")
     if p.offsets.dtype != torch.int64:
         raise ValueError("offsets must be int64")
+    dev = torch.cuda.current_device()
+    if p.rows.device.index != dev or p.offsets.device.index != dev:
+        raise ValueError(f"path rows and offsets must be on the current CUDA device (cuda:{dev})")
     return _Paths(p.rows.data_ptr(), p.offsets.data_ptr(), p.count, int(p.max_len), p.rows.shape[0])
 
 

@@ -59,3 +59,23 @@ def test_host_tensors_and_mixed_dtypes_are_refused():
     assert sk._dtype_code(A, A) == sk.DTYPES[torch.float32]
     with pytest.raises(ValueError, match="float16"):
         sk._dtype_code(*(2 * [sk.Paths.from_list([torch.zeros(3, 2, dtype=torch.float16)], device="cpu")]))
+
+
+def test_strided_or_misshapen_paths_are_refused():
+    """The library reads rows [R][d] and offsets [B + 1] as dense arrays: a transposed or sliced
+    view, or a tensor of the wrong rank, is refused before any pointer is taken."""
+    rows = torch.zeros(2, 5, dtype=torch.float64)
+    off = torch.tensor([0, 3, 5], dtype=torch.int64)
+    with pytest.raises(ValueError, match="contiguous"):
+        sk._cpaths(sk.Paths(rows.t(), off, 3))
+    with pytest.raises(ValueError, match="contiguous"):
+        sk._cpaths(sk.Paths(torch.zeros(5, 4)[:, ::2], off, 3))
+    with pytest.raises(ValueError, match="contiguous"):
+        sk._cpaths(sk.Paths(torch.zeros(5, 2), torch.arange(6, dtype=torch.int64)[::2], 3))
+    with pytest.raises(ValueError, match=r"\[R, d\]"):
+        sk._cpaths(sk.Paths(torch.zeros(5), off, 3))
+    with pytest.raises(ValueError, match=r"\[R, d\]"):
+        sk._cpaths(sk.Paths(torch.zeros(5, 2), off.reshape(1, 3), 3))
+    # dense host tensors pass these checks and stop at the device check
+    with pytest.raises(ValueError, match="CUDA"):
+        sk._cpaths(sk.Paths(torch.zeros(5, 2), off, 3))
