@@ -169,6 +169,46 @@ def _cpaths(p: Paths) -> _Paths:
     return _Paths(p.rows.data_ptr(), p.offsets.data_ptr(), p.count, int(p.max_len), p.rows.shape[0])
 
 
+def _device_buffer(t: torch.Tensor, name: str, dtype=None, numel=None) -> torch.Tensor:
+    """A tensor the library reads or writes through a raw pointer: contiguous, on the current CUDA
+    device, of `dtype` and with `numel` elements when given.  The library cannot see the size of a
+    device buffer, so a short one would be read or written past its end."""
+    if dtype is not None and t.dtype != dtype:
+        raise ValueError(f"{name} must be {dtype}, not {t.dtype}")
+    if numel is not None and t.numel() != numel:
+        raise ValueError(f"{name} has {t.numel()} elements where the call needs {numel}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if not t.is_cuda or t.device.index != torch.cuda.current_device():
+        raise ValueError(f"{name} must be on the current CUDA device")
+    return t
+
+
+def _nbytes(t: torch.Tensor) -> int:
+    return t.numel() * t.element_size()
+
+
+def _pair_tensors(pair_a, pair_b):
+    """The pair lists as int64 CUDA tensors of equal length (the library reads npairs of each)."""
+    pa = torch.as_tensor(pair_a, dtype=torch.int64)
+    pb = torch.as_tensor(pair_b, dtype=torch.int64)
+    if pa.dim() != 1 or pb.dim() != 1 or pa.numel() != pb.numel():
+        raise ValueError(f"pair_a and pair_b must be 1-d of one length (got {tuple(pa.shape)} and {tuple(pb.shape)})")
+    return pa.to("cuda").contiguous(), pb.to("cuda").contiguous()
+
+
+def _grad_out(grad_out, nx: int, ny: int, npairs: int) -> torch.Tensor:
+    """The upstream gradient as float64 on the device: [nx, ny] in Gram mode (npairs < 0), else
+    npairs values."""
+    g = torch.as_tensor(grad_out, dtype=torch.float64)
+    if npairs < 0:
+        if g.numel() != nx * ny or (g.dim() == 2 and tuple(g.shape) != (nx, ny)):
+            raise ValueError(f"grad_out must be [{nx}, {ny}] (got {tuple(g.shape)})")
+    elif g.numel() != npairs:
+        raise ValueError(f"grad_out must hold {npairs} values, one per pair (got {g.numel()})")
+    return g.to("cuda").contiguous()
+
+
 def _options(scheme="approx", degree=6, dyadic=0, compute="f64", flags=0, interp_extra=0) -> _Options:
     return _Options(SCHEMES[scheme] if isinstance(scheme, str) else int(scheme), int(degree), int(dyadic),
                     COMPUTE[compute] if isinstance(compute, str) else int(compute), int(interp_extra), int(flags), 0, 0)
@@ -206,15 +246,15 @@ def sigkernel_pairs(X, Y, pair_a, pair_b, scheme="approx", degree=6, dyadic=0, c
     ``tensor_cores=False`` (SK_FLAG_NO_TC) keeps the FP32 approximation scheme's M on the FMA pipe
     (tiled, or per cell with ``tiled_m=False``) instead of the tcgen05 M kernel (4 < d <= 32)."""
     X, Y = as_paths(X), as_paths(Y)
-    pa = torch.as_tensor(pair_a, dtype=torch.int64, device="cuda").contiguous()
-    pb = torch.as_tensor(pair_b, dtype=torch.int64, device="cuda").contiguous()
+    pa, pb = _pair_tensors(pair_a, pair_b)
     n = pa.numel()
     opt = _options(scheme, degree, dyadic, compute,
                    _flags(X, (0 if sort else FLAG_NO_SORT) | _pipe_flags(strip_pipeline)
                           | (FLAG_TIME_KERNEL if time_kernel else 0) | (0 if tiled_m else FLAG_NO_TILED_M)
                           | (0 if tensor_cores else FLAG_NO_TC)))
     cX, cY = _cpaths(X), _cpaths(Y)
-    out = out if out is not None else torch.empty(n, dtype=torch.float64, device="cuda")
+    out = _device_buffer(out, "out", torch.float64, n) if out is not None else \
+        torch.empty(n, dtype=torch.float64, device="cuda")
     ws = _workspace(OP_PAIRS, cX, cY, X.d, n, opt)
     _check(load_library().sigkernel_pairs(ctypes.byref(cX), ctypes.byref(cY), X.d, _dtype_code(X, Y), pa.data_ptr(),
                                           pb.data_ptr(), n, ctypes.byref(opt), out.data_ptr(), ws.data_ptr(),
@@ -241,10 +281,12 @@ def sigkernel_gram(X, Y=None, scheme="approx", degree=6, dyadic=0, compute="f64"
                    | (0 if tiled_m else FLAG_NO_TILED_M) | (0 if tensor_cores else FLAG_NO_TC))
     opt = _options(scheme, degree, dyadic, compute, flags)
     cX, cY = _cpaths(X), _cpaths(Y)
-    G = out if out is not None else torch.empty(X.count, Y.count, dtype=torch.float64, device="cuda")
-    ws = workspace if workspace is not None else _workspace(OP_GRAM, cX, cY, X.d, -1, opt)
+    G = _device_buffer(out, "out", torch.float64, X.count * Y.count) if out is not None else \
+        torch.empty(X.count, Y.count, dtype=torch.float64, device="cuda")
+    ws = _device_buffer(workspace, "workspace") if workspace is not None else \
+        _workspace(OP_GRAM, cX, cY, X.d, -1, opt)
     _check(load_library().sigkernel_gram(ctypes.byref(cX), ctypes.byref(cY), X.d, _dtype_code(X, Y),
-                                         ctypes.byref(opt), G.data_ptr(), ws.data_ptr(), ws.numel(), _stream_ptr()))
+                                         ctypes.byref(opt), G.data_ptr(), ws.data_ptr(), _nbytes(ws), _stream_ptr()))
     return G
 
 
@@ -270,8 +312,7 @@ def autotune(X, Y=None, pair_a=None, pair_b=None, scheme="approx", degree=6, dya
     Y = X if (Y is None or Y is X) else as_paths(Y)
     cX, cY = _cpaths(X), _cpaths(Y)
     if pairs:
-        pa = torch.as_tensor(pair_a, dtype=torch.int64, device="cuda").contiguous()
-        pb = torch.as_tensor(pair_b, dtype=torch.int64, device="cuda").contiguous()
+        pa, pb = _pair_tensors(pair_a, pair_b)
         n, pa_ptr, pb_ptr = pa.numel(), pa.data_ptr(), pb.data_ptr()
         out = torch.empty(n, dtype=torch.float64, device="cuda")
     else:
@@ -306,7 +347,9 @@ def sigkernel_backward(grad_out, X, Y=None, pair_a=None, pair_b=None, scheme="ap
     X = as_paths(X)
     Y = X if sym else as_paths(Y)
     cX, cY = _cpaths(X), _cpaths(Y)
-    g = torch.as_tensor(grad_out, dtype=torch.float64, device="cuda").contiguous()
+    if pair_a is not None:
+        pa, pb = _pair_tensors(pair_a, pair_b)
+    g = _grad_out(grad_out, X.count, Y.count, -1 if pair_a is None else pa.numel())
     gX = torch.zeros(X.rows.shape[0], X.d, dtype=torch.float64, device="cuda")
     same = sym or (X.rows.data_ptr() == Y.rows.data_ptr() and X.offsets.data_ptr() == Y.offsets.data_ptr())
     gY = gX if same else torch.zeros(Y.rows.shape[0], Y.d, dtype=torch.float64, device="cuda")
@@ -318,8 +361,6 @@ def sigkernel_backward(grad_out, X, Y=None, pair_a=None, pair_b=None, scheme="ap
         pa_ptr = pb_ptr = None
         n = -1
     else:
-        pa = torch.as_tensor(pair_a, dtype=torch.int64, device="cuda").contiguous()
-        pb = torch.as_tensor(pair_b, dtype=torch.int64, device="cuda").contiguous()
         n = pa.numel()
         opt = _options(scheme, degree, dyadic, compute, _flags(X, extra))
         ws = _workspace(OP_BACKWARD, cX, cY, X.d, n, opt)
@@ -334,8 +375,7 @@ def sigkernel_backward(grad_out, X, Y=None, pair_a=None, pair_b=None, scheme="ap
 def _pair_args(X, pair_a, pair_b, sym):
     if pair_a is None:
         return None, None, -1, None
-    pa = torch.as_tensor(pair_a, dtype=torch.int64, device="cuda").contiguous()
-    pb = torch.as_tensor(pair_b, dtype=torch.int64, device="cuda").contiguous()
+    pa, pb = _pair_tensors(pair_a, pair_b)
     return pa.data_ptr(), pb.data_ptr(), pa.numel(), (pa, pb)
 
 
@@ -356,15 +396,17 @@ def sigkernel_forward_tape(X, Y=None, pair_a=None, pair_b=None, scheme="approx",
     lib = load_library()
     nb = ctypes.c_size_t(0)
     _check(lib.sigkernel_tape_size(ctypes.byref(cX), ctypes.byref(cY), X.d, n, ctypes.byref(opt), ctypes.byref(nb)))
-    if tape is None or tape.numel() < nb.value:
+    if tape is None or _nbytes(tape) < nb.value:
         tape = torch.empty(int(nb.value), dtype=torch.uint8, device="cuda")
+    _device_buffer(tape, "tape")
     if out is None:
         out = torch.empty((X.count, Y.count) if pair_a is None else (n,), dtype=torch.float64, device="cuda")
-    ws = workspace if workspace is not None else _workspace(OP_GRAM if pair_a is None else OP_PAIRS, cX, cY, X.d,
-                                                            n, opt)
+    _device_buffer(out, "out", torch.float64, X.count * Y.count if pair_a is None else n)
+    ws = _device_buffer(workspace, "workspace") if workspace is not None else \
+        _workspace(OP_GRAM if pair_a is None else OP_PAIRS, cX, cY, X.d, n, opt)
     _check(lib.sigkernel_forward_tape(ctypes.byref(cX), ctypes.byref(cY), X.d, _dtype_code(X, Y), pa_ptr, pb_ptr, n,
-                                      ctypes.byref(opt), out.data_ptr(), tape.data_ptr(), tape.numel(), ws.data_ptr(),
-                                      ws.numel(), _stream_ptr()))
+                                      ctypes.byref(opt), out.data_ptr(), tape.data_ptr(), _nbytes(tape), ws.data_ptr(),
+                                      _nbytes(ws), _stream_ptr()))
     return out, tape
 
 
@@ -380,13 +422,14 @@ def sigkernel_backward_tape(tape, grad_out, X, Y=None, pair_a=None, pair_b=None,
     flags = _flags(X, (FLAG_SYMMETRIC if sym else 0) | (0 if sort else FLAG_NO_SORT)
                    | (FLAG_TIME_KERNEL if time_kernel else 0) | (0 if tensor_cores else FLAG_NO_TC))
     opt = _options(scheme, degree, dyadic, compute, flags)
-    g = torch.as_tensor(grad_out, dtype=torch.float64, device="cuda").contiguous()
+    g = _grad_out(grad_out, X.count, Y.count, n)
+    _device_buffer(tape, "tape")
     gX = torch.zeros(X.rows.shape[0], X.d, dtype=torch.float64, device="cuda")
     same = X is Y or (X.rows.data_ptr() == Y.rows.data_ptr() and X.offsets.data_ptr() == Y.offsets.data_ptr())
     gY = gX if same else torch.zeros(Y.rows.shape[0], Y.d, dtype=torch.float64, device="cuda")
     ws = _workspace(OP_BACKWARD_TAPE, cX, cY, X.d, n, opt)
     _check(load_library().sigkernel_backward_tape(ctypes.byref(cX), ctypes.byref(cY), X.d, _dtype_code(X, Y), pa_ptr,
-                                                  pb_ptr, n, ctypes.byref(opt), tape.data_ptr(), tape.numel(),
+                                                  pb_ptr, n, ctypes.byref(opt), tape.data_ptr(), _nbytes(tape),
                                                   g.data_ptr(), gX.data_ptr(), None if same else gY.data_ptr(),
                                                   ws.data_ptr(), ws.numel(), _stream_ptr()))
     return gX, gY
@@ -440,12 +483,14 @@ def sigkernel_mmd2_test(A, B, permutations=1000, labels=None, seed=0, scheme="ap
     nperm = labels.shape[0]
     cA, cB = _cpaths(A), _cpaths(B)
     opt = _options(scheme, degree, dyadic, compute, _flags(A, FLAG_UNBIASED if unbiased else 0))
-    ws = workspace if workspace is not None else _workspace(OP_MMD2_TEST, cA, cB, A.d, nperm, opt)
+    ws = _device_buffer(workspace, "workspace") if workspace is not None else \
+        _workspace(OP_MMD2_TEST, cA, cB, A.d, nperm, opt)
     if out is None:
         out = torch.empty(2 + nperm, dtype=torch.float64, device="cuda")
+    _device_buffer(out, "out", torch.float64, 2 + nperm)
     _check(load_library().sigkernel_mmd2_test(ctypes.byref(cA), ctypes.byref(cB), A.d, _dtype_code(A, B),
                                               ctypes.byref(opt), labels.data_ptr() if nperm else None, nperm,
-                                              out.data_ptr(), ws.data_ptr(), ws.numel(), _stream_ptr()))
+                                              out.data_ptr(), ws.data_ptr(), _nbytes(ws), _stream_ptr()))
     return out[0], out[1], out[2:]
 
 

@@ -79,3 +79,29 @@ def test_strided_or_misshapen_paths_are_refused():
     # dense host tensors pass these checks and stop at the device check
     with pytest.raises(ValueError, match="CUDA"):
         sk._cpaths(sk.Paths(torch.zeros(5, 2), off, 3))
+
+
+def test_buffers_passed_as_pointers_are_checked_before_use():
+    """Outputs, workspaces, tapes, upstream gradients and pair lists reach the library as raw
+    pointers whose sizes it cannot see: a wrong dtype, a wrong element count, a strided view, a
+    short pair list or a mis-shaped upstream gradient is refused on the host."""
+    out = torch.zeros(6, dtype=torch.float64)
+    with pytest.raises(ValueError, match="float64"):
+        sk._device_buffer(out.float(), "out", torch.float64, 6)
+    with pytest.raises(ValueError, match="5 elements"):
+        sk._device_buffer(out[:5], "out", torch.float64, 6)
+    with pytest.raises(ValueError, match="contiguous"):
+        sk._device_buffer(torch.zeros(12, dtype=torch.float64)[::2], "out", torch.float64, 6)
+    with pytest.raises(ValueError, match="CUDA"):
+        sk._device_buffer(out, "out", torch.float64, 6)
+    assert sk._nbytes(torch.zeros(3, dtype=torch.float64)) == 24
+    with pytest.raises(ValueError, match="one length"):
+        sk._pair_tensors([0, 1, 2], [0, 1])
+    with pytest.raises(ValueError, match="one length"):
+        sk._pair_tensors([[0, 1]], [[0, 1]])
+    with pytest.raises(ValueError, match=r"\[3, 2\]"):
+        sk._grad_out(torch.zeros(2, 3), 3, 2, -1)       # transposed Gram weights
+    with pytest.raises(ValueError, match=r"\[3, 2\]"):
+        sk._grad_out(torch.zeros(5), 3, 2, -1)
+    with pytest.raises(ValueError, match="one per pair"):
+        sk._grad_out([1.0, 2.0], 3, 2, 3)
