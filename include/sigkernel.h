@@ -40,6 +40,11 @@
  *     update of Section 3.2 depends on C_ij (s_{i+1}-s_i)(t_{j+1}-t_j) only), so no time
  *     partition is passed.
  *   * Outputs are FP64, device memory, caller-owned.
+ *   * Alignment.  Device pointers must be aligned to their elements: path rows to the input
+ *     element (8, 4 or 2 bytes), offsets, pair lists, outputs and gradients to 8 bytes, and tapes
+ *     to 256 bytes.  A misaligned pointer is refused with SK_ERR_INVALID_ARG before anything is
+ *     launched.  Sizes of device buffers cannot be checked: each must hold what its entry point
+ *     states.
  *   * Calls are asynchronous on `stream` (a cudaStream_t; NULL = the legacy default stream) and
  *     make no host-device synchronisation.  Argument errors are reported by the return code
  *     before anything is launched; errors that need device data (bad lengths, an exhausted

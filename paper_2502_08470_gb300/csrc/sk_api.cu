@@ -7,9 +7,11 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <initializer_list>
 #include <map>
 #include <mutex>
 #include <string>
+#include <utility>
 
 #include "sk_bwd_poly.cuh"
 #include "sk_common.cuh"
@@ -201,6 +203,29 @@ int check_paths(const sk_paths* P, const char* name, int d) {
     if (P->rows_total > 0 && !P->rows) return fail(SK_ERR_INVALID_ARG, "%s->rows is NULL", name);
     if (P->count > (int64_t(1) << 30)) return fail(SK_ERR_UNSUPPORTED, "%s: more than 2^30 paths", name);
     (void)d;
+    return SK_OK;
+}
+
+// The kernels read path rows as elements of the input type, and offsets, pair lists, outputs and
+// gradients as 8-byte elements; a pointer misaligned for its elements would fault on the device,
+// so the compute entry points refuse it before anything runs (NULL passes here: the callers check
+// for NULL where a pointer is required).
+int check_path_ptrs(const sk_paths* P, int32_t dtype, const char* name) {
+    if (!P) return SK_OK;
+    const size_t es = dtype == SK_F64 ? 8 : dtype == SK_F32 ? 4 : dtype == SK_BF16 ? 2 : 1;
+    if (reinterpret_cast<uintptr_t>(P->rows) % es)
+        return fail(SK_ERR_INVALID_ARG, "%s->rows is not %zu-byte aligned", name, es);
+    if (reinterpret_cast<uintptr_t>(P->offsets) % 8) return fail(SK_ERR_INVALID_ARG, "%s->offsets is not 8-byte aligned", name);
+    return SK_OK;
+}
+
+int check_call_ptrs(const sk_paths* X, const char* xn, const sk_paths* Y, const char* yn, int32_t dtype,
+                    std::initializer_list<std::pair<const void*, const char*>> ptrs8) {
+    int rc;
+    if ((rc = check_path_ptrs(X, dtype, xn)) != SK_OK) return rc;
+    if ((rc = check_path_ptrs(Y, dtype, yn)) != SK_OK) return rc;
+    for (const auto& q : ptrs8)
+        if (reinterpret_cast<uintptr_t>(q.first) % 8) return fail(SK_ERR_INVALID_ARG, "%s is not 8-byte aligned", q.second);
     return SK_OK;
 }
 
@@ -1527,6 +1552,8 @@ int sigkernel_autotune(const sk_paths* X, const sk_paths* Y, int32_t d, int32_t 
                        sk_options* best, float* best_ms, void* stream) {
     NvtxRange nvtx_range("sigkernel_autotune");
     t_last_error.clear();
+    int prc = check_call_ptrs(X, "X", Y, "Y", dtype, {{pair_a, "pair_a"}, {pair_b, "pair_b"}, {out, "out"}});
+    if (prc != SK_OK) return prc;
     if (!opt || !X || !Y || !out || !best) return fail(SK_ERR_INVALID_ARG, "NULL argument");
     if (trials < 1 || trials > 1000) return fail(SK_ERR_INVALID_ARG, "trials %d outside [1, 1000]", trials);
     if (pair_a && (!pair_b || npairs < 0)) return fail(SK_ERR_INVALID_ARG, "bad pair list");
@@ -1700,6 +1727,8 @@ int sigkernel_pairs(const sk_paths* X, const sk_paths* Y, int32_t d, int32_t dty
                     size_t workspace_bytes, void* stream) {
     NvtxRange nvtx_range("sigkernel_pairs");
     t_last_error.clear();
+    int prc = check_call_ptrs(X, "X", Y, "Y", dtype, {{pair_a, "pair_a"}, {pair_b, "pair_b"}, {out, "out"}});
+    if (prc != SK_OK) return prc;
     if (npairs < 0) return fail(SK_ERR_INVALID_ARG, "npairs < 0");
     if (npairs > 0 && (!pair_a || !pair_b)) return fail(SK_ERR_INVALID_ARG, "pair index arrays are NULL");
     return run_forward(X, Y, d, dtype, opt, kPairsList, pair_a, pair_b, npairs, out, 0, workspace, workspace_bytes,
@@ -1710,6 +1739,8 @@ int sigkernel_gram(const sk_paths* X, const sk_paths* Y, int32_t d, int32_t dtyp
                    void* workspace, size_t workspace_bytes, void* stream) {
     NvtxRange nvtx_range("sigkernel_gram");
     t_last_error.clear();
+    int prc = check_call_ptrs(X, "X", Y, "Y", dtype, {{G, "G"}});
+    if (prc != SK_OK) return prc;
     if (!opt || !X || !Y) return fail(SK_ERR_INVALID_ARG, "NULL argument");
     bool sym = (opt->flags & SK_FLAG_SYMMETRIC) != 0;
     return run_forward(X, Y, d, dtype, opt, sym ? kGramUpper : kGramFull, nullptr, nullptr, gram_items(X, Y, sym), G,
@@ -1721,6 +1752,9 @@ int sigkernel_backward(const sk_paths* X, const sk_paths* Y, int32_t d, int32_t 
                        double* grad_X, double* grad_Y, void* workspace, size_t workspace_bytes, void* stream) {
     NvtxRange nvtx_range("sigkernel_backward");
     t_last_error.clear();
+    int prc = check_call_ptrs(X, "X", Y, "Y", dtype, {{pair_a, "pair_a"}, {pair_b, "pair_b"}, {grad_out, "grad_out"},
+                                                      {grad_X, "grad_X"}, {grad_Y, "grad_Y"}});
+    if (prc != SK_OK) return prc;
     if (!opt || !X || !Y) return fail(SK_ERR_INVALID_ARG, "NULL argument");
     if (pair_a && (!pair_b || npairs < 0)) return fail(SK_ERR_INVALID_ARG, "bad pair list");
     if (uses_tape_chunks(opt))
@@ -1753,8 +1787,11 @@ int sigkernel_forward_tape(const sk_paths* X, const sk_paths* Y, int32_t d, int3
                            size_t tape_bytes, void* workspace, size_t workspace_bytes, void* stream) {
     NvtxRange nvtx_range("sigkernel_forward_tape");
     t_last_error.clear();
+    int prc = check_call_ptrs(X, "X", Y, "Y", dtype, {{pair_a, "pair_a"}, {pair_b, "pair_b"}, {out, "out"}});
+    if (prc != SK_OK) return prc;
     if (!opt || !X || !Y) return fail(SK_ERR_INVALID_ARG, "NULL argument");
     if (!tape) return fail(SK_ERR_INVALID_ARG, "tape is NULL");
+    if (reinterpret_cast<uintptr_t>(tape) % 256) return fail(SK_ERR_INVALID_ARG, "tape must be 256-byte aligned");
     if (pair_a == nullptr) {
         const bool sym = (opt->flags & SK_FLAG_SYMMETRIC) != 0;
         return run_forward(X, Y, d, dtype, opt, sym ? kGramUpper : kGramFull, nullptr, nullptr, gram_items(X, Y, sym),
@@ -1771,6 +1808,12 @@ int sigkernel_backward_tape(const sk_paths* X, const sk_paths* Y, int32_t d, int
                             size_t workspace_bytes, void* stream) {
     NvtxRange nvtx_range("sigkernel_backward_tape");
     t_last_error.clear();
+    int prc = check_call_ptrs(X, "X", Y, "Y", dtype, {{pair_a, "pair_a"}, {pair_b, "pair_b"}, {grad_out, "grad_out"},
+                                                      {grad_X, "grad_X"}, {grad_Y, "grad_Y"}});
+    if (prc != SK_OK) return prc;
+    // the adjoint streams tape steps with bulk copies, which need 16-byte aligned sources; the
+    // forward lays the tape out from a 256-byte aligned base
+    if (reinterpret_cast<uintptr_t>(tape) % 256) return fail(SK_ERR_INVALID_ARG, "tape must be 256-byte aligned");
     if (!opt || !X || !Y) return fail(SK_ERR_INVALID_ARG, "NULL argument");
     if (pair_a && (!pair_b || npairs < 0)) return fail(SK_ERR_INVALID_ARG, "bad pair list");
     return run_backward_tape(X, Y, d, dtype, opt, pair_a, pair_b, npairs, tape, tape_bytes, grad_out, grad_X, grad_Y,
@@ -1781,6 +1824,8 @@ int sigkernel_mmd2(const sk_paths* A, const sk_paths* B, int32_t d, int32_t dtyp
                    double* grad_A, double* grad_B, void* workspace, size_t workspace_bytes, void* stream) {
     NvtxRange nvtx_range("sigkernel_mmd2");
     t_last_error.clear();
+    int prc = check_call_ptrs(A, "A", B, "B", dtype, {{out, "out"}, {grad_A, "grad_A"}, {grad_B, "grad_B"}});
+    if (prc != SK_OK) return prc;
     return run_mmd2(A, B, d, dtype, opt, out, grad_A, grad_B, workspace, workspace_bytes, stream);
 }
 
@@ -1789,6 +1834,8 @@ int sigkernel_mmd2_test(const sk_paths* A, const sk_paths* B, int32_t d, int32_t
                         void* stream) {
     NvtxRange nvtx_range("sigkernel_mmd2_test");
     t_last_error.clear();
+    int prc = check_call_ptrs(A, "A", B, "B", dtype, {{out, "out"}});
+    if (prc != SK_OK) return prc;
     return run_mmd2_test(A, B, d, dtype, opt, labels, nperm, out, workspace, workspace_bytes, stream);
 }
 

@@ -5,6 +5,7 @@ import os
 import re
 
 import pytest
+import torch
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 HEADER = os.path.join(ROOT, "include", "sigkernel.h")
@@ -101,6 +102,40 @@ def test_path_lengths_beyond_the_refined_bound_are_refused(lib):
                                               ctypes.byref(opt), ctypes.byref(n))
             assert rc == -2 and n.value == 0
             assert b"max_len" in lib.sigkernel_last_error()
+
+
+def test_misaligned_device_pointers_are_refused(lib):
+    """Rows misaligned for their element type, offsets, outputs, gradients or pair lists off 8
+    bytes, and a tape off 256 bytes, are refused before any device work."""
+    from paper_2502_08470_gb300 import sigkernel as sk
+    lib.sigkernel_last_error.restype = ctypes.c_char_p
+    for f in ("sigkernel_gram", "sigkernel_pairs", "sigkernel_backward", "sigkernel_backward_tape"):
+        getattr(lib, f).restype = ctypes.c_int
+    ok = sk._Paths(0x10000, 0x20000, 1, 10, 10)
+    opt = sk._options("approx", 6)
+    vp = ctypes.c_void_p
+    cases = [
+        (sk._Paths(0x10004, 0x20000, 1, 10, 10), ok, sk.DTYPES[torch.float64], vp(0x30000), b"X->rows is not 8"),
+        (ok, sk._Paths(0x10002, 0x20000, 1, 10, 10), sk.DTYPES[torch.float32], vp(0x30000), b"Y->rows is not 4"),
+        (sk._Paths(0x10001, 0x20000, 1, 10, 10), ok, sk.DTYPES[torch.bfloat16], vp(0x30000), b"X->rows is not 2"),
+        (sk._Paths(0x10000, 0x20004, 1, 10, 10), ok, sk.DTYPES[torch.float64], vp(0x30000), b"X->offsets"),
+        (ok, ok, sk.DTYPES[torch.float64], vp(0x30004), b"G is not 8"),
+    ]
+    for X, Y, dt, G, msg in cases:
+        rc = lib.sigkernel_gram(ctypes.byref(X), ctypes.byref(Y), 2, dt, ctypes.byref(opt), G, None,
+                                ctypes.c_size_t(0), None)
+        assert rc == -1 and msg in lib.sigkernel_last_error(), (msg, lib.sigkernel_last_error())
+    f64 = sk.DTYPES[torch.float64]
+    rc = lib.sigkernel_pairs(ctypes.byref(ok), ctypes.byref(ok), 2, f64, vp(0x40000), vp(0x40004), ctypes.c_int64(1),
+                             ctypes.byref(opt), vp(0x30000), None, ctypes.c_size_t(0), None)
+    assert rc == -1 and b"pair_b is not 8" in lib.sigkernel_last_error()
+    rc = lib.sigkernel_backward(ctypes.byref(ok), ctypes.byref(ok), 2, f64, None, None, ctypes.c_int64(-1),
+                                ctypes.byref(opt), vp(0x30000), vp(0x50002), None, None, ctypes.c_size_t(0), None)
+    assert rc == -1 and b"grad_X is not 8" in lib.sigkernel_last_error()
+    rc = lib.sigkernel_backward_tape(ctypes.byref(ok), ctypes.byref(ok), 2, f64, None, None, ctypes.c_int64(-1),
+                                     ctypes.byref(opt), vp(0x60010), ctypes.c_size_t(1 << 20), vp(0x30000),
+                                     vp(0x50000), None, None, ctypes.c_size_t(0), None)
+    assert rc == -1 and b"256-byte" in lib.sigkernel_last_error()
 
 
 def _header_constants():
