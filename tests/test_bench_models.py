@@ -71,3 +71,42 @@ def test_clock_samples_are_summarised_and_the_temporary_file_removed(bench, monk
     s = c.summary()
     assert s == {"sm_mhz": 1972.5, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"], "samples": 2}
     assert not os.path.exists(c.path)
+
+
+def test_reference_arm_line_keeps_the_contract(bench, monkeypatch, capsys):
+    """bench.py --impl reference prints one JSON line on the GPU arm's metric, unit and direction
+    (so a ratio of the two arms is defined), its ms_per_step is the time of the steps it ran, and
+    it carries the cpu_baseline and e2e objects with no host-device bytes.  The oracle's timing is
+    stubbed here; the line is built as in a real run."""
+    import argparse
+    import inspect
+    import json
+
+    import numpy as np
+
+    calls = []
+
+    def fake_fwd_bwd(X, Y, points=None):
+        calls.append(points)
+        return 16384.0, 0.25  # cells, seconds
+
+    monkeypatch.setattr(bench, "cpu_fwd_bwd", fake_fwd_bwd)
+    monkeypatch.setattr(bench, "workload", lambda rank, *a: (np.zeros((2, 5, 8)), np.zeros((2, 5, 8))))
+    bench.run_reference(argparse.Namespace(steps=3, warmup=2), 0, 1)
+    line = json.loads(capsys.readouterr().out.strip())
+    assert line["impl"] == "reference"
+    assert line["metric"] == bench.METRIC and line["unit"] == "cell-updates/s"
+    assert line["higher_is_better"] is True
+    assert line["steps"] == 3 and line["warmup"] == 2 and line["n_gpus"] == 1
+    assert calls == [65, 65, 129, 129, 129]  # warm-up steps on shorter prefixes, timed steps at 129 points
+    assert line["ms_per_step"] == pytest.approx(250.0)
+    assert line["value"] == pytest.approx(16384.0 / 0.25)
+    cb = line["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["value"] == line["value"] and cb["cores"] >= 1 and cb["sample"]
+    assert line["e2e"] == {"value": line["value"], "unit": line["unit"], "h2d_bytes_per_step": 0,
+                           "d2h_bytes_per_step": 0}
+    # the GPU arm builds its line on the same metric string
+    assert '"metric": METRIC' in inspect.getsource(bench.main)
+    # other ranks print nothing
+    bench.run_reference(argparse.Namespace(steps=1, warmup=0), 1, 2)
+    assert capsys.readouterr().out == ""
