@@ -543,6 +543,7 @@ def main():
         # same command, profiles/launches_gram128.md, counts the same 12 per step)
         "gpu_launches": 12 * args.steps,
         "clocks": clocks, "device_status": status, "wall_s_timed_region": wall,
+        "device": {"gpu": torch.cuda.get_device_name(local), "host_cores": os.cpu_count() or 1},
     })
     tape_buf[0] = None
     torch.cuda.empty_cache()
