@@ -22,7 +22,13 @@ What it shows:
   FP32 form follows the oracle there, so the loss is the scheme's and not FP32's. The
   interpolation scheme (Section 3.3) keeps such oscillatory kernels: within 1e-7 of 0F1 at
   N = 8.
+* The interpolation scheme's FP32 floor on oscillatory paths (about 1e-5 to 1e-4 on the GPU)
+  comes from FP32 cells as such. The same form in FP32, with J = 6 extra terms and the
+  compiled projection, lands 4e-7 to 7e-5 from the oracle. In FP64 with J = 10 it lands within
+  1e-11.
 """
+import os
+import re
 from math import factorial
 
 import numpy as np
@@ -109,3 +115,61 @@ def test_oscillatory_kernel_lost_by_the_approximation_scheme_not_by_fp32():
     assert abs(scheme - exact) > 1e20                # the order-6 scheme on this grid
     assert fp32_form(x, y, 6) == pytest.approx(scheme, rel=2e-5)
     assert oracle.kernel(x, y, "interp", 8) == pytest.approx(exact, rel=1e-7)
+
+
+TABLE = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "paper_2502_08470_gb300", "csrc",
+                     "sk_projection_table.h")
+
+
+def _projection(N, J):
+    """The generated projection of series terms N+1..N+J onto the degree-N Chebyshev interpolant,
+    as the kernels compile it in."""
+    P = np.zeros((N + 1, J))
+    for key, val in re.findall(r"case (\d+): return ([-+0-9.eE]+);", open(TABLE).read()):
+        key = int(key)
+        if key // 1024 == N and key % 32 < J:
+            P[(key % 1024) // 32, key % 32] = float(val)
+    return P
+
+
+def interp_form(x, y, N, J, dtype):
+    """The interpolation cell as the kernels compute it (the approximation map extended to N + J
+    terms, the right edge taking a_0 as its corner term, then the constant projection), in the
+    given floating type.  It carries no exponents: the kernel values of the paths below stay
+    within FP32's range."""
+    NE = N + J
+    P = _projection(N, J).astype(dtype)
+    hank = np.array([[factorial(n) / factorial(n + k) for k in range(N + 1)] for n in range(NE + 1)]).astype(dtype)
+    M = (np.diff(x, axis=0) @ np.diff(y, axis=0).T).astype(dtype)
+    rows, cols = M.shape
+    unit = np.zeros(N + 1, dtype)
+    unit[0] = 1
+    inv = np.array([1.0 / factorial(n) for n in range(NE + 1)])
+    b_col = [unit.copy() for _ in range(cols)]
+    for i in range(rows):
+        a = unit.copy()
+        for j in range(cols):
+            b = b_col[j]
+            m = float(M[i, j])
+            e = np.array([m ** k / factorial(k) for k in range(NE + 1)]).astype(dtype)
+            bc = b.copy()
+            bc[0] = a[0]
+            ct, cr = np.zeros(NE + 1, dtype), np.zeros(NE + 1, dtype)
+            for n in range(NE + 1):
+                kk = min(n, N)
+                ct[n] = np.dot(a[:kk + 1], e[n::-1][:kk + 1]) + e[n] * np.dot(b[1:], hank[n, 1:])
+                cr[n] = np.dot(bc[:kk + 1], e[n::-1][:kk + 1]) + e[n] * np.dot(a[1:], hank[n, 1:])
+            if i == rows - 1 and j == cols - 1:
+                return 0.5 * (ct.astype(np.float64) @ inv + cr.astype(np.float64) @ inv)
+            a = ct[:N + 1] + P @ ct[N + 1:]
+            b_col[j] = cr[:N + 1] + P @ cr[N + 1:]
+    return 1.0
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_interpolation_fp32_floor_on_oscillatory_paths_is_the_fp32_cells(seed):
+    X = W.oscillatory(1, 65, 4, seed=900 + seed)[0]
+    Y = W.oscillatory(1, 65, 4, seed=950 + seed)[0]
+    want = oracle.kernel(X, Y, "interp", 8)
+    assert interp_form(X, Y, 8, 10, np.float64) == pytest.approx(want, rel=1e-11)
+    assert interp_form(X, Y, 8, 6, np.float32) == pytest.approx(want, rel=2e-4)
