@@ -173,3 +173,14 @@ def test_interpolation_fp32_floor_on_oscillatory_paths_is_the_fp32_cells(seed):
     want = oracle.kernel(X, Y, "interp", 8)
     assert interp_form(X, Y, 8, 10, np.float64) == pytest.approx(want, rel=1e-11)
     assert interp_form(X, Y, 8, 6, np.float32) == pytest.approx(want, rel=2e-4)
+
+
+def test_the_projection_cannot_amplify_rounding():
+    """Every entry of the compiled projection (N = 2..12, J = 6 and 10) is at most 1/2 in
+    magnitude, so applying it in FP32 adds rounding of the order of the projected terms
+    themselves; no ill-conditioned polynomial fit enters the interpolation cells."""
+    for J in (6, 10):
+        for N in range(2, 13):
+            P = _projection(N, J)
+            assert np.count_nonzero(P) > 0
+            assert np.abs(P).max() <= 0.5
