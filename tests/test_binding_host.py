@@ -105,3 +105,13 @@ def test_buffers_passed_as_pointers_are_checked_before_use():
         sk._grad_out(torch.zeros(5), 3, 2, -1)
     with pytest.raises(ValueError, match="one per pair"):
         sk._grad_out([1.0, 2.0], 3, 2, 3)
+
+
+def test_a_missing_library_fails_loudly(monkeypatch, tmp_path):
+    """Without libsigkernel.so every call raises: there is no CPU or library fallback."""
+    monkeypatch.setattr(sk, "_lib", None)
+    monkeypatch.setattr(sk, "LIB_PATH", str(tmp_path / "libsigkernel.so"))
+    with pytest.raises(RuntimeError, match="missing"):
+        sk.load_library()
+    with pytest.raises(RuntimeError, match="missing"):
+        sk.version()
