@@ -479,7 +479,7 @@ def sigkernel_mmd2_test(A, B, permutations=1000, labels=None, seed=0, scheme="ap
         raise ValueError("labels must be a 2-d uint8 CUDA tensor")
     if labels.shape[1] != A.count + B.count:
         raise ValueError("labels must have |A| + |B| columns")
-    labels = labels.contiguous()
+    labels = _device_buffer(labels.contiguous(), "labels", torch.uint8, labels.shape[0] * (A.count + B.count))
     nperm = labels.shape[0]
     cA, cB = _cpaths(A), _cpaths(B)
     opt = _options(scheme, degree, dyadic, compute, _flags(A, FLAG_UNBIASED if unbiased else 0))
