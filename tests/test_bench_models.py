@@ -110,3 +110,19 @@ def test_reference_arm_line_keeps_the_contract(bench, monkeypatch, capsys):
     # other ranks print nothing
     bench.run_reference(argparse.Namespace(steps=1, warmup=0), 1, 2)
     assert capsys.readouterr().out == ""
+
+
+def test_reference_arm_runs_from_the_command_line():
+    """`python bench.py --impl reference` on this machine's cores: one JSON line as the last line
+    of stdout, exit status 0, no GPU needed (one timed step of the oracle, about 10 s)."""
+    import json
+    import subprocess
+    import sys
+
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
+                        "--warmup", "0"], capture_output=True, text=True, timeout=600, cwd=ROOT)
+    assert r.returncode == 0, r.stderr[-2000:]
+    line = json.loads(r.stdout.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["steps"] == 1 and line["warmup"] == 0
+    assert line["value"] > 0 and line["ms_per_step"] > 0
+    assert line["value"] == pytest.approx(16384 / (line["ms_per_step"] / 1e3), rel=1e-9)
