@@ -65,6 +65,43 @@ def test_approx_one_by_two_closed_form(N):
     assert oracle.kernel(y, x, "approx", N) == pytest.approx(want, rel=1e-13)
 
 
+def _first_row_recursion(dx, dys, s, t, N):
+    """The approximation scheme on a grid of one row of cells, from the recursions printed in the
+    proof of Prop. "multistepestimate". Along the first row, the top edge's coefficients (powers of
+    s - s_0) obey p^{0,j+1}_n = sum_k p^{0j}_k (C_0j dt_j)^{n-k} k! / ((n-k)! n!). The right edge
+    gets q^{1,j}_n = sum_k p^{0j}_k C_0j^n ds^{n+k} k! / ((n+k)! n!), with C_0j = <dx, dy_j> /
+    (ds dt_j). Kept to n <= N, these are the scheme's own coefficients: p^{0,j+1}_n depends on
+    p^{0j}_k for k <= n only. The endpoint averages the last cell's top and right edges."""
+    ds = s[1] - s[0]
+    p = np.zeros(N + 1)
+    p[0] = 1.0                                   # k(s, t_0) = 1
+    for j, dy in enumerate(dys):
+        dt = t[j + 1] - t[j]
+        C = float(dx @ dy) / (ds * dt)
+        q = np.array([sum(p[k] * C ** n * ds ** (n + k) * factorial(k) / (factorial(n + k) * factorial(n))
+                          for k in range(N + 1)) for n in range(N + 1)])
+        p = np.array([sum(p[k] * (C * dt) ** (n - k) * factorial(k) / (factorial(n - k) * factorial(n))
+                          for k in range(n + 1)) for n in range(N + 1)])
+    return 0.5 * (sum(p[n] * ds ** n for n in range(N + 1)) + sum(q[n] * dt ** n for n in range(N + 1)))
+
+
+@pytest.mark.parametrize("N", [2, 4, 6, 9])
+@pytest.mark.parametrize("K", [1, 3, 8])
+def test_approx_one_row_follows_the_printed_first_row_recursion(N, K):
+    """One x segment against K y segments, on non-uniform partitions: the oracle's general
+    grid sweep against the paper's first-row recursion (and the mirrored grid against it too)."""
+    rng = np.random.default_rng(100 * N + K)
+    dx = 1.3 * rng.normal(size=3)
+    dys = rng.normal(size=(K, 3)) / np.sqrt(K)
+    x = np.stack([np.zeros(3), dx])
+    y = np.vstack([np.zeros(3), np.cumsum(dys, axis=0)])
+    s = [0.2, 0.2 + rng.uniform(0.5, 2.0)]
+    t = list(np.concatenate([[-1.0], -1.0 + np.cumsum(rng.uniform(0.3, 1.5, K))]))
+    want = _first_row_recursion(dx, dys, s, t, N)
+    assert oracle.kernel(x, y, "approx", N, s=s, t=t) == pytest.approx(want, rel=1e-13)
+    assert oracle.kernel(y, x, "approx", N, s=t, t=s) == pytest.approx(want, rel=1e-13)
+
+
 # --------------------------------------------------------------------------------------------
 # Polynomial interpolation: the single-cell solution is 0F1(1; M) = I_0(2 sqrt M)  (Prop.
 # "propinterp" and the Remark after it); checked against scipy's Bessel functions.
