@@ -1,5 +1,6 @@
-"""CPU models of the two ways the adjoint kernels stream tape rows through shared-memory rings,
-checked over many step counts, ring depths and sequences of work items.
+"""CPU models of the three shared-memory rings through which the adjoint kernels and the FMA
+contraction stream their rows, checked over many step counts, ring depths and sequences of work
+items.
 
 * Per-lane cp.async ring (the checkpointing adjoint's strip tape, K = 4; the FD adjoint, D = 4, 6
   or 8). Each lane copies its own vectors. An item's steps t = n - 1 .. 0 live in slot t mod D.
@@ -10,6 +11,11 @@ checked over many step counts, ring depths and sequences of work items.
   copies. The warp waits on a slot's barrier for the phase parity it tracks in a register that
   persists across items, flips the bit, reads the slot, and then has lane 0 refill it with step
   t - 4.
+* The FMA contraction's ring of three 32-row halves. Per strip and column window of ntiles
+  tiles, half h goes to slot h mod 3: halves 0..min(2, ntiles) first. Tile b waits for half b
+  (tile 0 only; later tiles got it as the upper half of the tile before) and for half b + 1,
+  reads both, then refills slot b mod 3 with half b + 3 while b + 3 <= ntiles. The parity bits
+  persist across strips and windows.
 
 A copy's data may land at any moment until the wait that covers it returns. The model lets
 every copy land as late as possible: at that wait. It then checks three things. A read sees the
@@ -109,3 +115,46 @@ def test_mbarrier_ring_waits_always_find_their_phase():
     for _ in range(500):
         items = [rng.randint(1, 40) for _ in range(rng.randint(2, 8))]
         assert run_mbarrier_ring(items)
+
+
+def run_contraction_ring(ntiles_seq):
+    """The FMA contraction: one warp's sequence of strip-window visits, each with its tile count."""
+    completed = [0] * 3
+    issued = [0] * 3
+    holds = {}              # slot -> half whose load was issued last
+    parity = 0
+
+    def load(h):
+        sl = h % 3
+        assert issued[sl] == completed[sl], ("slot reloaded before its load was awaited", h)
+        issued[sl] += 1
+        holds[sl] = h
+
+    def wait(sl):
+        nonlocal parity
+        want = (parity >> sl) & 1
+        assert issued[sl] == completed[sl] + 1, ("wait with no load in flight: it would hang", sl)
+        completed[sl] += 1
+        assert (completed[sl] - 1) % 2 == want
+        parity ^= 1 << sl
+
+    for ntiles in ntiles_seq:
+        for h in range(min(3, ntiles + 1)):
+            load(h)
+        for b in range(ntiles):
+            if b == 0:
+                wait(0)
+            wait((b + 1) % 3)
+            assert holds[b % 3] == b and holds[(b + 1) % 3] == b + 1
+            if b + 3 <= ntiles:
+                load(b + 3)
+    assert issued == completed   # nothing left in flight or unawaited
+    return True
+
+
+def test_contraction_ring_waits_each_half_once():
+    rng = random.Random(11)
+    for n in range(1, 40):
+        assert run_contraction_ring([n])
+    for _ in range(500):
+        assert run_contraction_ring([rng.randint(1, 40) for _ in range(rng.randint(2, 10))])
