@@ -169,3 +169,46 @@ def test_binding_structs_follow_the_header_field_order():
     from paper_2502_08470_gb300 import sigkernel as sk
     assert [f for f, _ in sk._Options._fields_] == _header_struct_fields("sk_options")
     assert [f for f, _ in sk._Paths._fields_] == _header_struct_fields("sk_paths")
+
+
+def test_a_plain_c_caller_compiles_links_and_gets_argument_errors(lib, tmp_path):
+    """The header is C99 and the library links into a C program: the program reads the version
+    and gets SK_ERR_INVALID_ARG with a message for a bad order, with no device involved."""
+    import shutil
+    import subprocess
+
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    from paper_2502_08470_gb300 import build
+    libdir = os.path.dirname(build.LIB)
+    src = tmp_path / "caller.c"
+    src.write_text(r"""
+#include <stdio.h>
+#include <string.h>
+#include "sigkernel.h"
+int main(void) {
+    sk_paths X;
+    sk_options o;
+    size_t bytes = 1;
+    int rc;
+    memset(&X, 0, sizeof X);
+    memset(&o, 0, sizeof o);
+    if (sigkernel_version() < 100) return 2;
+    o.scheme = SK_POLY_APPROX;
+    o.degree = 1;                      /* the schemes take N >= 2 */
+    o.compute = SK_COMPUTE_F64;
+    rc = sigkernel_workspace_size(SK_OP_PAIRS, &X, &X, 2, 1, &o, &bytes);
+    if (rc != SK_ERR_INVALID_ARG || bytes != 0) return 3;
+    if (strstr(sigkernel_last_error(), "order") == NULL) return 4;
+    puts("ok");
+    return 0;
+}
+""")
+    exe = tmp_path / "caller"
+    r = subprocess.run([cc, "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror", "-I", os.path.join(ROOT, "include"),
+                        str(src), "-L", libdir, "-lsigkernel", f"-Wl,-rpath,{libdir}", "-o", str(exe)],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    r = subprocess.run([str(exe)], capture_output=True, text=True, timeout=120)
+    assert r.returncode == 0 and r.stdout.strip() == "ok", (r.returncode, r.stdout, r.stderr)
