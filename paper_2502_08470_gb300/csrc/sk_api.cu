@@ -1179,7 +1179,8 @@ __global__ void fill_weights_kernel(double* W, int64_t n, int64_t m, double v, i
 // chunk smaller than a block is a whole number of the adjoint's resident warps.  When the budget
 // holds fewer items than half the adjoint's resident warps (very long paths), the block uses the
 // checkpointing adjoint instead, which keeps only the strip hand-offs and one strip's tape per
-// warp (approximation scheme only).  The same budget bounds the chunks of sigkernel_backward for the interpolation scheme.
+// warp (approximation scheme only).  The same budget bounds the chunks of sigkernel_backward for
+// the interpolation scheme.
 // 64 GiB holds the tape of a 128 x 128 Gram of 257-point paths (61 GB at N = 6 in FP32) in one
 // chunk: at 48 GiB it took two (10944 + 5440 pairs), and the second chunk's partial waves cost
 // 2.3 ms of the 29.0 ms backward call.
